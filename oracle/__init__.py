@@ -1,0 +1,15 @@
+"""FP64 CPU oracle of the GENGA II hybrid symplectic step (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline and
+reference legs may import this package.  It is a plain C implementation
+(``genga_oracle.c``) loaded through ctypes; it shares no code with the CUDA
+library.  See ``genga_oracle.c`` for the readings taken where the paper is
+silent.
+"""
+from .core import (OracleParams, OracleStats, accel, accel_rows, bs_groups, build, changeover,
+                   detect, drift, energy, group, hc, kick, lib, make_params, precheck, rcrit,
+                   step)
+
+__all__ = ["OracleParams", "OracleStats", "accel", "accel_rows", "bs_groups", "build",
+           "changeover", "detect", "drift", "energy", "group", "hc", "kick", "lib",
+           "make_params", "precheck", "rcrit", "step"]

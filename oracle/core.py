@@ -1,0 +1,222 @@
+"""ctypes binding of the C oracle (numpy in, numpy out).  Test infrastructure."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "genga_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_lib")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -ffp-contract=off, OpenMP)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-std=c11", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OracleParams(C.Structure):
+    _fields_ = [("G", C.c_double), ("m_star", C.c_double), ("dt", C.c_double),
+                ("n1", C.c_double), ("n2", C.c_double), ("f_pc", C.c_double),
+                ("bs_tol", C.c_double), ("slevels", C.c_int32), ("substeps", C.c_int32),
+                ("kepler_max_iter", C.c_int32), ("bs_max_steps", C.c_int32),
+                ("nthreads", C.c_int32), ("pad", C.c_int32)]
+
+
+class OracleStats(C.Structure):
+    _fields_ = [("n_candidates", C.c_int64), ("n_pairs", C.c_int64 * 8),
+                ("n_groups", C.c_int64), ("max_group", C.c_int64), ("bs_steps", C.c_int64),
+                ("bs_rejects", C.c_int64), ("kepler_fail", C.c_int64), ("bs_fail", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {"n_candidates": self.n_candidates, "n_pairs": list(self.n_pairs),
+                "n_groups": self.n_groups, "max_group": self.max_group,
+                "bs_steps": self.bs_steps, "bs_rejects": self.bs_rejects,
+                "kepler_fail": self.kepler_fail, "bs_fail": self.bs_fail}
+
+
+_D = C.POINTER(C.c_double)
+_U32 = C.POINTER(C.c_uint32)
+_I64 = C.POINTER(C.c_int64)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_changeover.restype = C.c_double
+            L.orc_changeover.argtypes = [C.c_double, C.c_double]
+            L.orc_rcrit.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, _D]
+            L.orc_accel.argtypes = [C.c_int64, _D, _D, _D, C.c_double, _D, C.c_int]
+            L.orc_accel_rows.argtypes = [C.c_int64, _D, _D, _D, C.c_double, _I64, C.c_int64, _D,
+                                         C.c_int]
+            L.orc_kick.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D, C.c_int]
+            L.orc_precheck.restype = C.c_int64
+            L.orc_precheck.argtypes = [C.c_int64, _D, _D, C.c_double, _U32, C.c_int64]
+            L.orc_hc.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double]
+            L.orc_fg.restype = C.c_int64
+            L.orc_fg.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_int]
+            L.orc_detect.restype = C.c_int64
+            L.orc_detect.argtypes = [C.c_int64, _U32, _D, _D, _D, _U32]
+            L.orc_group.argtypes = [C.c_int64, C.c_int64, _U32, _I64]
+            L.orc_step.restype = C.c_int
+            L.orc_step.argtypes = [C.c_int64, _D, _D, _D, C.POINTER(OracleParams), C.c_int64,
+                                   C.POINTER(OracleStats)]
+            L.orc_bs_groups.restype = C.c_int
+            L.orc_bs_groups.argtypes = [C.c_int64, _D, _D, _D, _D, C.c_int, C.c_int64, _U32,
+                                        C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
+                                        C.POINTER(OracleStats)]
+            L.orc_energy.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D, _D]
+            L.orc_sizeof_params.restype = C.c_int64
+            L.orc_sizeof_stats.restype = C.c_int64
+            assert L.orc_sizeof_params() == C.sizeof(OracleParams)
+            assert L.orc_sizeof_stats() == C.sizeof(OracleStats)
+            _lib = L
+    return _lib
+
+
+def _d(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def changeover(r: float, rc: float) -> float:
+    return lib().orc_changeover(float(r), float(rc))
+
+
+def rcrit(x, v, m, m_star, dt, n1=3.0, n2=0.4) -> np.ndarray:
+    x, v, m = _f64(x), _f64(v), _f64(m)
+    rc = np.empty(m.shape[0])
+    lib().orc_rcrit(m.shape[0], _d(x), _d(v), _d(m), m_star, dt, n1, n2, _d(rc))
+    return rc
+
+
+def accel(x, m, rc, G, nthreads: int = 1) -> np.ndarray:
+    x, m, rc = _f64(x), _f64(m), _f64(rc)
+    a = np.empty_like(x)
+    lib().orc_accel(m.shape[0], _d(x), _d(m), _d(rc), G, _d(a), nthreads)
+    return a
+
+
+def accel_rows(x, m, rc, G, rows, nthreads: int = 1) -> np.ndarray:
+    x, m, rc = _f64(x), _f64(m), _f64(rc)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    a = np.empty((rows.shape[0], 3))
+    lib().orc_accel_rows(m.shape[0], _d(x), _d(m), _d(rc), G, rows.ctypes.data_as(_I64),
+                         rows.shape[0], _d(a), nthreads)
+    return a
+
+
+def kick(x, v, m, rc, G, dt_half, nthreads: int = 1) -> np.ndarray:
+    x, m, rc = _f64(x), _f64(m), _f64(rc)
+    v = _f64(v).copy()
+    lib().orc_kick(m.shape[0], _d(x), _d(m), _d(rc), G, dt_half, _d(v), nthreads)
+    return v
+
+
+def precheck(x, rc, f_pc) -> np.ndarray:
+    x, rc = _f64(x), _f64(rc)
+    n = rc.shape[0]
+    cap = 4096
+    while True:
+        out = np.empty((cap, 2), dtype=np.uint32)
+        c = lib().orc_precheck(n, _d(x), _d(rc), f_pc, out.ctypes.data_as(_U32), cap)
+        if c <= cap:
+            return out[:c].copy()
+        cap = int(c)
+
+
+def hc(x, v, m, m_star, dt_half) -> np.ndarray:
+    x = _f64(x).copy()
+    v, m = _f64(v), _f64(m)
+    lib().orc_hc(m.shape[0], _d(x), _d(v), _d(m), m_star, dt_half)
+    return x
+
+
+def drift(x, v, mu, dt, max_iter: int = 50):
+    """Kepler drift of every body; returns (x, v, number of non-converged)."""
+    x, v = _f64(x).copy(), _f64(v).copy()
+    fails = lib().orc_fg(x.shape[0], _d(x), _d(v), mu, dt, max_iter)
+    return x, v, int(fails)
+
+
+def detect(cand, xpre, xpost, rc) -> np.ndarray:
+    cand = np.ascontiguousarray(cand, dtype=np.uint32).reshape(-1, 2)
+    xpre, xpost, rc = _f64(xpre), _f64(xpost), _f64(rc)
+    out = np.empty((max(cand.shape[0], 1), 2), dtype=np.uint32)
+    c = lib().orc_detect(cand.shape[0], cand.ctypes.data_as(_U32), _d(xpre), _d(xpost), _d(rc),
+                         out.ctypes.data_as(_U32))
+    return out[:c].copy()
+
+
+def group(n, pairs) -> np.ndarray:
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    label = np.empty(n, dtype=np.int64)
+    lib().orc_group(n, pairs.shape[0], pairs.ctypes.data_as(_U32), label.ctypes.data_as(_I64))
+    return label
+
+
+def make_params(wl=None, **kw) -> OracleParams:
+    p = OracleParams()
+    defaults = dict(G=0.01720209895 ** 2, m_star=1.0, dt=6.0875, n1=3.0, n2=0.4, f_pc=4.0,
+                    bs_tol=1e-15, slevels=1, substeps=1, kepler_max_iter=50,
+                    bs_max_steps=100000, nthreads=1)
+    if wl is not None:
+        for k in ("G", "m_star", "dt", "n1", "n2", "f_pc", "slevels", "substeps"):
+            defaults[k] = getattr(wl, k)
+    defaults.update(kw)
+    for k, val in defaults.items():
+        setattr(p, k, val)
+    return p
+
+
+def step(x, v, m, params: OracleParams, nsteps: int = 1):
+    """Advance nsteps; returns (x, v, status, stats dict)."""
+    x, v, m = _f64(x).copy(), _f64(v).copy(), _f64(m)
+    st = OracleStats()
+    status = lib().orc_step(m.shape[0], _d(x), _d(v), _d(m), C.byref(params), nsteps,
+                            C.byref(st))
+    return x, v, int(status), st.as_dict()
+
+
+def bs_groups(x, v, m, rc_levels, pairs, G, m_star, dt, tol=1e-15, max_steps=100000):
+    """BS-integrate every group of the ascending pair list over dt.
+
+    rc_levels is (nlev, n); returns (x, v, status, stats dict)."""
+    x, v, m = _f64(x).copy(), _f64(v).copy(), _f64(m)
+    rcl = _f64(np.atleast_2d(rc_levels))
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    st = OracleStats()
+    status = lib().orc_bs_groups(m.shape[0], _d(x), _d(v), _d(m), _d(rcl), rcl.shape[0],
+                                 pairs.shape[0], pairs.ctypes.data_as(_U32), G, m_star, dt, tol,
+                                 max_steps, C.byref(st))
+    return x, v, int(status), st.as_dict()
+
+
+def energy(x, v, m, m_star, G):
+    x, v, m = _f64(x), _f64(v), _f64(m)
+    E = np.zeros(1)
+    L = np.zeros(3)
+    lib().orc_energy(m.shape[0], _d(x), _d(v), _d(m), m_star, G, _d(E), _d(L))
+    return float(E[0]), L

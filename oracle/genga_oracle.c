@@ -1,0 +1,802 @@
+/*
+ * genga_oracle.c -- plain, slow, FP64 CPU oracle of the hybrid symplectic step of
+ * GENGA II (Grimm et al., arXiv:2201.10058).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this file:
+ * only the tests, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+ * arm load it.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * Compile with -O2 -ffp-contract=off so that every a*b+c below is rounded twice,
+ * exactly as written.  All arithmetic is IEEE binary64 unless a comment says
+ * otherwise (energy uses long double with Kahan summation).
+ *
+ * Coordinates: democratic heliocentric (Sec. 2, Eq. H): positions x_i are
+ * heliocentric, velocities v_i barycentric.  Arrays are row-major (n,3).
+ *
+ * Readings taken where the paper is silent (each is listed in the design notes):
+ *  R1  Hill radius in Eq. rcrit: R_H,i = |x_i| (m_i/(3 m_star))^(1/3).
+ *  R2  v_i in Eq. rcrit is the stored (barycentric) speed.
+ *  R3  Pair critical radius rc_ij = max(rc_i, rc_j).
+ *  R4  Changeover function K (Sec. 4.2, footnote on Chambers 1999 Eq. 10):
+ *      y = (r/rc - 0.1)/0.9 clamped to [0,1], K = y^2 / (2y^2 - 2y + 1).
+ *  R5  Force scaling: the kick applies K times the Newtonian pair force and the
+ *      close-encounter part applies (1-K) times it (no dK/dr term).
+ *  R6  Pre-check (Appendix A): candidate pairs i<j with r_ij^2 < (f_pc rc_ij)^2,
+ *      evaluated on the positions of the first half kick.
+ *  R7  Detection (Appendix A): a candidate is an encounter when its distance
+ *      before or after the drift is below rc_ij (r^2 < rc_ij^2).
+ *  R8  Grouping: connected components of the encounter pairs; group label is the
+ *      smallest member index; members ascending (Serial Grouping, App. B).
+ *  R9  Bulirsch-Stoer: modified midpoint with n = 2,4,...,16, polynomial
+ *      extrapolation in h^2; pair forces summed over the group's encounter pairs
+ *      (the partner lists of the BS-A kernel, Sec. 4.1); step halving on failure.
+ *  R10 Higher levels (Sec. 4.3, Appendix A): level bodies restart from the
+ *      pre-drift state of the enclosing level; level-l kicks use the factor
+ *      prod_{k<l}(1-K_k) K_l over the enclosing level's encounter pairs; BS uses
+ *      prod_{k<=l}(1-K_k).
+ *  R11 Kepler drift with mu = G m_star (Eq. Ha), universal variables with
+ *      Stumpff functions evaluated by series and argument quartering.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Parameters of one integration (own definition; not shared with the GPU).  */
+typedef struct orc_params {
+    double G;          /* gravitational constant */
+    double m_star;     /* central mass */
+    double dt;         /* base time step */
+    double n1, n2;     /* Eq. rcrit constants */
+    double f_pc;       /* pre-check factor (R6) */
+    double bs_tol;     /* Bulirsch-Stoer relative tolerance */
+    int32_t slevels;   /* number of symplectic levels (1 = original method) */
+    int32_t substeps;  /* sub-steps per level */
+    int32_t kepler_max_iter;
+    int32_t bs_max_steps; /* limit on BS sub-step attempts per group call */
+    int32_t nthreads;  /* OpenMP threads for the O(N^2) loops (1 = serial) */
+    int32_t pad;
+} orc_params;
+
+/* Statistics of the last step (for tests and reports). */
+typedef struct orc_stats {
+    int64_t n_candidates;
+    int64_t n_pairs[8];      /* encounter pairs found at each level (summed over sub-steps) */
+    int64_t n_groups;        /* BS groups integrated */
+    int64_t max_group;       /* largest BS group */
+    int64_t bs_steps;        /* accepted BS sub-steps */
+    int64_t bs_rejects;      /* rejected BS attempts (step halvings) */
+    int64_t kepler_fail;     /* Kepler solves that hit the iteration limit */
+    int64_t bs_fail;         /* groups that hit bs_max_steps */
+} orc_stats;
+
+#define ORC_MAX_LEVELS 8
+
+/* ------------------------------------------------------------------------- */
+/* R4: the changeover function of Chambers (1999), Eq. 10, as read here.      */
+double orc_changeover(double r, double rc)
+{
+    double y = (r / rc - 0.1) / 0.9;
+    if (y <= 0.0) return 0.0;
+    if (y >= 1.0) return 1.0;
+    double y2 = y * y;
+    return y2 / (2.0 * y2 - 2.0 * y + 1.0);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. rcrit with readings R1, R2: rc_i = max(n1 R_H,i, n2 dt |v_i|).         */
+void orc_rcrit(int64_t n, const double *x, const double *v, const double *m,
+               double m_star, double dt, double n1, double n2, double *rc)
+{
+    for (int64_t i = 0; i < n; i++) {
+        const double *xi = x + 3 * i, *vi = v + 3 * i;
+        double r = sqrt((xi[0] * xi[0] + xi[1] * xi[1]) + xi[2] * xi[2]);
+        double vabs = sqrt((vi[0] * vi[0] + vi[1] * vi[1]) + vi[2] * vi[2]);
+        double hill = r * cbrt(m[i] / (3.0 * m_star));
+        double a = n1 * hill;
+        double b = n2 * dt * vabs;
+        rc[i] = a > b ? a : b;
+    }
+}
+
+/* R3 */
+static double pair_rc(const double *rc, int64_t i, int64_t j)
+{
+    return rc[i] > rc[j] ? rc[i] : rc[j];
+}
+
+/* Squared distance in the prescribed order (dx^2 + dy^2) + dz^2, dx = x_j - x_i. */
+static double dist2(const double *xi, const double *xj)
+{
+    double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+    return (dx * dx + dy * dy) + dz * dz;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. Hb kick acceleration of particle i:
+ *   a_i = G sum_{j != i} m_j K(r_ij) (x_j - x_i) / r_ij^3, j ascending.        */
+static void accel_one(int64_t n, const double *x, const double *m, const double *rc,
+                      double G, int64_t i, double *ai)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    const double *xi = x + 3 * i;
+    for (int64_t j = 0; j < n; j++) {
+        if (j == i) continue;
+        const double *xj = x + 3 * j;
+        double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+        double r2 = (dx * dx + dy * dy) + dz * dz;
+        double r = sqrt(r2);
+        double K = orc_changeover(r, pair_rc(rc, i, j));
+        double f = m[j] * K / (r2 * r);
+        s0 += f * dx;
+        s1 += f * dy;
+        s2 += f * dz;
+    }
+    ai[0] = G * s0;
+    ai[1] = G * s1;
+    ai[2] = G * s2;
+}
+
+void orc_accel(int64_t n, const double *x, const double *m, const double *rc,
+               double G, double *acc, int nthreads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t i = 0; i < n; i++) accel_one(n, x, m, rc, G, i, acc + 3 * i);
+}
+
+/* Acceleration of a subset of rows (for sampled checks at large N). */
+void orc_accel_rows(int64_t n, const double *x, const double *m, const double *rc,
+                    double G, const int64_t *rows, int64_t nrows, double *acc, int nthreads)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t k = 0; k < nrows; k++) accel_one(n, x, m, rc, G, rows[k], acc + 3 * k);
+}
+
+/* Kick(dt/2): v_i += dt_half a_i. */
+void orc_kick(int64_t n, const double *x, const double *m, const double *rc,
+              double G, double dt_half, double *v, int nthreads)
+{
+    double *acc = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    orc_accel(n, x, m, rc, G, acc, nthreads);
+    for (int64_t i = 0; i < 3 * n; i++) v[i] += dt_half * acc[i];
+    free(acc);
+}
+
+/* R6 pre-check: candidates i<j with r_ij^2 < (f_pc rc_ij)^2, ascending (i,j).
+ * Returns the number of candidates; writes at most cap of them.             */
+int64_t orc_precheck(int64_t n, const double *x, const double *rc, double f_pc,
+                     uint32_t *cand, int64_t cap)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = i + 1; j < n; j++) {
+            double t = f_pc * pair_rc(rc, i, j);
+            if (dist2(x + 3 * i, x + 3 * j) < t * t) {
+                if (c < cap) { cand[2 * c] = (uint32_t)i; cand[2 * c + 1] = (uint32_t)j; }
+                c++;
+            }
+        }
+    return c;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. Hc: x_i += dt_half P / m_star, P = sum_j m_j v_j (j ascending).         */
+void orc_hc(int64_t n, double *x, const double *v, const double *m, double m_star,
+            double dt_half)
+{
+    double P[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n; j++)
+        for (int k = 0; k < 3; k++) P[k] += m[j] * v[3 * j + k];
+    double c[3];
+    for (int k = 0; k < 3; k++) c[k] = dt_half * P[k] / m_star;
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) x[3 * i + k] += c[k];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Kepler drift (Eq. Ha, Kepler term), universal variables.
+ * Stumpff functions c_k(z) = sum_{m>=0} (-z)^m / (2m+k)!; for |z| large the
+ * argument is quartered until small, the series is used, and the quadrupling
+ * relations c0(4z)=2c0^2-1, c1(4z)=c0 c1, c2(4z)=c1^2/2, c3(4z)=(c2+c0 c3)/4
+ * map back.  With s the universal variable and beta = 2mu/r0 - v0^2:
+ *   G_k(s) = s^k c_k(beta s^2),
+ *   t(s) = r0 G1 + u G2 + mu G3,    u = x0.v0,
+ *   r(s) = r0 G0 + u G1 + mu G2 = dt/ds,
+ *   f = 1 - mu G2/r0,  g = t - mu G3,  fdot = -mu G1/(r r0),  gdot = 1 - mu G2/r.  */
+static void stumpff(double z, double *c0, double *c1, double *c2, double *c3)
+{
+    int q = 0;
+    while (fabs(z) > 0.1 && q < 60) { z *= 0.25; q++; }
+    /* series for c2 and c3 (|z| <= 0.1: 9 terms reach below 1e-20) */
+    double s2 = 0.0, s3 = 0.0;
+    double fact2[10], fact3[10];
+    {   /* 1/(2m+2)! and 1/(2m+3)! for m = 0..9 */
+        double f = 1.0; /* running factorial */
+        int k = 1;
+        for (int mm = 0; mm < 10; mm++) {
+            while (k < 2 * mm + 2) { k++; f *= k; }
+            fact2[mm] = 1.0 / f;
+            k++; f *= k;
+            fact3[mm] = 1.0 / f;
+        }
+    }
+    for (int mm = 9; mm >= 0; mm--) {
+        s2 = fact2[mm] - z * s2;
+        s3 = fact3[mm] - z * s3;
+    }
+    double C2 = s2, C3 = s3;
+    double C0 = 1.0 - z * C2;
+    double C1 = 1.0 - z * C3;
+    for (int k = 0; k < q; k++) {
+        double n3 = 0.25 * (C2 + C0 * C3);
+        double n2 = 0.5 * C1 * C1;
+        double n1 = C0 * C1;
+        double n0 = 2.0 * C0 * C0 - 1.0;
+        C0 = n0; C1 = n1; C2 = n2; C3 = n3;
+    }
+    *c0 = C0; *c1 = C1; *c2 = C2; *c3 = C3;
+}
+
+/* Drift one body; returns 0 on success, 1 if Newton hit max_iter. */
+static int kepler_one(double *x, double *v, double mu, double dt, int max_iter)
+{
+    double r0 = sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]);
+    double v2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+    double u = (x[0] * v[0] + x[1] * v[1]) + x[2] * v[2];
+    double beta = 2.0 * mu / r0 - v2;
+    /* second-order initial guess of s */
+    double s = dt / r0 - (u * dt * dt) / (2.0 * r0 * r0 * r0);
+    double c0, c1, c2, c3;
+    double ds_prev = 0.0;
+    int it, ok = 0;
+    /* Newton on t(s) = dt.  Converged when |ds| <= 1e-15 |s|, or when the
+     * quadratic phase is over and rounding of t(s) stalls the update at
+     * |ds| <= 1e-12 |s| without halving it any more.                        */
+    for (it = 0; it < max_iter; it++) {
+        double z = beta * s * s;
+        stumpff(z, &c0, &c1, &c2, &c3);
+        double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+        double G0 = c0;
+        double t = r0 * G1 + u * G2 + mu * G3;
+        double rr = r0 * G0 + u * G1 + mu * G2;
+        double ds = (t - dt) / rr;
+        s -= ds;
+        double ads = fabs(ds), as = fabs(s);
+        if (ads <= 1e-15 * as) { ok = 1; break; }
+        if (it > 0 && ads <= 1e-12 * as && ads > 0.5 * ds_prev) { ok = 1; break; }
+        ds_prev = ads;
+    }
+    double z = beta * s * s;
+    stumpff(z, &c0, &c1, &c2, &c3);
+    double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+    double r = r0 * c0 + u * G1 + mu * G2;
+    double fm1 = -mu * G2 / r0;
+    double g = dt - mu * G3;
+    double fd = -mu * G1 / (r * r0);
+    double gdm1 = -mu * G2 / r;
+    double x0[3] = {x[0], x[1], x[2]}, v0[3] = {v[0], v[1], v[2]};
+    for (int k = 0; k < 3; k++) {
+        x[k] = x0[k] + (fm1 * x0[k] + g * v0[k]);
+        v[k] = v0[k] + (fd * x0[k] + gdm1 * v0[k]);
+    }
+    return ok ? 0 : 1;
+}
+
+/* FG(dt) for all bodies, or for the listed ones.  Returns the failure count. */
+int64_t orc_fg(int64_t n, double *x, double *v, double mu, double dt, int max_iter)
+{
+    int64_t fails = 0;
+    for (int64_t i = 0; i < n; i++) fails += kepler_one(x + 3 * i, v + 3 * i, mu, dt, max_iter);
+    return fails;
+}
+
+static int64_t fg_list(const int64_t *idx, int64_t nb, double *x, double *v, double mu,
+                       double dt, int max_iter)
+{
+    int64_t fails = 0;
+    for (int64_t k = 0; k < nb; k++)
+        fails += kepler_one(x + 3 * idx[k], v + 3 * idx[k], mu, dt, max_iter);
+    return fails;
+}
+
+/* ------------------------------------------------------------------------- */
+/* R7 detection: keep candidate (i,j) if r^2 < rc_ij^2 before or after the drift.
+ * Output keeps the candidate order (ascending when the input is ascending).  */
+int64_t orc_detect(int64_t ncand, const uint32_t *cand, const double *xpre,
+                   const double *xpost, const double *rc, uint32_t *pairs)
+{
+    int64_t c = 0;
+    for (int64_t k = 0; k < ncand; k++) {
+        int64_t i = cand[2 * k], j = cand[2 * k + 1];
+        double rcij = pair_rc(rc, i, j);
+        double rc2 = rcij * rcij;
+        if (dist2(xpre + 3 * i, xpre + 3 * j) < rc2 || dist2(xpost + 3 * i, xpost + 3 * j) < rc2) {
+            pairs[2 * c] = (uint32_t)i;
+            pairs[2 * c + 1] = (uint32_t)j;
+            c++;
+        }
+    }
+    return c;
+}
+
+/* ------------------------------------------------------------------------- */
+/* R8 grouping: union-find, label = smallest index in the component; bodies in
+ * no pair get label -1.                                                     */
+static int64_t uf_find(int64_t *p, int64_t a)
+{
+    while (p[a] != a) { p[a] = p[p[a]]; a = p[a]; }
+    return a;
+}
+
+void orc_group(int64_t n, int64_t npairs, const uint32_t *pairs, int64_t *label)
+{
+    int64_t *p = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    char *in = (char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    for (int64_t i = 0; i < n; i++) p[i] = i;
+    for (int64_t k = 0; k < npairs; k++) {
+        int64_t a = uf_find(p, pairs[2 * k]), b = uf_find(p, pairs[2 * k + 1]);
+        in[pairs[2 * k]] = 1; in[pairs[2 * k + 1]] = 1;
+        if (a == b) continue;
+        if (a < b) p[b] = a; else p[a] = b;
+    }
+    for (int64_t i = 0; i < n; i++) label[i] = in[i] ? uf_find(p, i) : -1;
+    free(p);
+    free(in);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Bulirsch-Stoer integration of one close-encounter group (R9, R10).
+ * The group's ODE (Eq. Ha restricted to the group):
+ *   dx_i/dt = v_i
+ *   dv_i/dt = -mu x_i/|x_i|^3
+ *             + G sum_{j in partners(i)} m_j W_ij (x_j - x_i)/r_ij^3,
+ *   W_ij = prod_{k=0..L} (1 - K(r_ij; rc_k,ij)).                             */
+typedef struct bs_group {
+    int64_t nm;            /* members */
+    const int64_t *mem;    /* global indices, ascending */
+    const int64_t *poff;   /* partner offsets, nm+1 */
+    const int64_t *plist;  /* partner local indices, ascending per member */
+    const double *m;       /* masses (global) */
+    const double *const *rcl; /* rc of levels 0..L (global arrays) */
+    int nlev;              /* L+1 */
+    double G, mu;
+} bs_group;
+
+static void bs_deriv(const bs_group *g, const double *y, double *f)
+{
+    /* y[6*k .. 6*k+5] = x, v of member k */
+    for (int64_t a = 0; a < g->nm; a++) {
+        const double *xa = y + 6 * a;
+        double r2 = (xa[0] * xa[0] + xa[1] * xa[1]) + xa[2] * xa[2];
+        double r = sqrt(r2);
+        double s = -g->mu / (r2 * r);
+        double ax = s * xa[0], ay = s * xa[1], az = s * xa[2];
+        double px = 0.0, py = 0.0, pz = 0.0;
+        int64_t ia = g->mem[a];
+        for (int64_t q = g->poff[a]; q < g->poff[a + 1]; q++) {
+            int64_t b = g->plist[q];
+            int64_t ib = g->mem[b];
+            const double *xb = y + 6 * b;
+            double dx = xb[0] - xa[0], dy = xb[1] - xa[1], dz = xb[2] - xa[2];
+            double d2 = (dx * dx + dy * dy) + dz * dz;
+            double d = sqrt(d2);
+            double W = 1.0;
+            for (int l = 0; l < g->nlev; l++) {
+                const double *rc = g->rcl[l];
+                double rcij = rc[ia] > rc[ib] ? rc[ia] : rc[ib];
+                W *= 1.0 - orc_changeover(d, rcij);
+            }
+            double c = g->m[ib] * W / (d2 * d);
+            px += c * dx; py += c * dy; pz += c * dz;
+        }
+        f[6 * a + 0] = xa[3];
+        f[6 * a + 1] = xa[4];
+        f[6 * a + 2] = xa[5];
+        f[6 * a + 3] = ax + g->G * px;
+        f[6 * a + 4] = ay + g->G * py;
+        f[6 * a + 5] = az + g->G * pz;
+    }
+}
+
+/* Modified midpoint over H with nsub steps, starting from y0 with f0 = f(y0). */
+static void bs_midpoint(const bs_group *g, const double *y0, const double *f0, double H,
+                        int nsub, double *out, double *zm, double *zn, double *fz)
+{
+    int64_t d = 6 * g->nm;
+    double h = H / nsub;
+    for (int64_t c = 0; c < d; c++) { zm[c] = y0[c]; zn[c] = y0[c] + h * f0[c]; }
+    for (int m = 1; m < nsub; m++) {
+        bs_deriv(g, zn, fz);
+        for (int64_t c = 0; c < d; c++) {
+            double t = zm[c] + 2.0 * h * fz[c];
+            zm[c] = zn[c];
+            zn[c] = t;
+        }
+    }
+    bs_deriv(g, zn, fz);
+    for (int64_t c = 0; c < d; c++) out[c] = 0.5 * (zn[c] + zm[c] + h * fz[c]);
+}
+
+#define BS_KMAX 8
+
+/* Integrates y (6 nm values) over dt.  Returns 0, or 1 on hitting max_steps. */
+static int bs_integrate(const bs_group *g, double *y, double dt, double tol, int max_steps,
+                        int64_t *n_acc, int64_t *n_rej)
+{
+    int64_t d = 6 * g->nm;
+    double *f0 = (double *)malloc(sizeof(double) * (size_t)d);
+    double *T = (double *)malloc(sizeof(double) * (size_t)d * BS_KMAX);
+    double *yk = (double *)malloc(sizeof(double) * (size_t)d);
+    double *zm = (double *)malloc(sizeof(double) * (size_t)d);
+    double *zn = (double *)malloc(sizeof(double) * (size_t)d);
+    double *fz = (double *)malloc(sizeof(double) * (size_t)d);
+    double *sc = (double *)malloc(sizeof(double) * (size_t)d);
+    double t = 0.0, H = dt;
+    int attempts = 0, status = 0;
+    while (t < dt) {
+        if (attempts >= max_steps) { status = 1; break; }
+        attempts++;
+        if (H > dt - t) H = dt - t;
+        bs_deriv(g, y, f0);
+        for (int64_t c = 0; c < d; c++) sc[c] = fabs(y[c]) + fabs(H * f0[c]) + 1e-300;
+        int accepted = 0, kconv = 0;
+        /* T[(j)*d + c] holds column j of the current row (Neville, in place) */
+        for (int k = 0; k < BS_KMAX; k++) {
+            int nk = 2 * (k + 1);
+            bs_midpoint(g, y, f0, H, nk, yk, zm, zn, fz);
+            double err = 0.0;
+            /* new row: R[0] = yk; R[j] = R[j-1] + (R[j-1] - Tprev[j-1]) / ((nk/n_{k-j})^2 - 1) */
+            for (int64_t c = 0; c < d; c++) {
+                double prev = T[0 * d + c];
+                double cur = yk[c];
+                T[0 * d + c] = cur;
+                for (int j = 1; j <= k; j++) {
+                    double ratio = (double)nk / (double)(2 * (k - j + 1));
+                    double nxt = cur + (cur - prev) / (ratio * ratio - 1.0);
+                    prev = T[j * d + c];
+                    T[j * d + c] = nxt;
+                    cur = nxt;
+                }
+                if (k >= 1) {
+                    double e = fabs(T[k * d + c] - T[(k - 1) * d + c]) / sc[c];
+                    if (e > err) err = e;
+                }
+            }
+            if (k >= 1 && err <= tol) { accepted = 1; kconv = k; break; }
+        }
+        if (accepted) {
+            for (int64_t c = 0; c < d; c++) y[c] = T[kconv * d + c];
+            t += H;
+            (*n_acc)++;
+            if (kconv < 4) H *= 1.5;
+        } else {
+            (*n_rej)++;
+            H *= 0.5;
+        }
+    }
+    free(f0); free(T); free(yk); free(zm); free(zn); free(fz); free(sc);
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Level machinery (Sec. 4.3, Appendix A).                                    */
+typedef struct step_ctx {
+    int64_t n;
+    double *x, *v;
+    const double *m;
+    const orc_params *p;
+    double *rcl[ORC_MAX_LEVELS];  /* rc of each level (full-length arrays) */
+    orc_stats *st;
+    int status;
+} step_ctx;
+
+/* Partner lists (CSR) of a pair list that is ascending in (i,j): appending j to
+ * i's list and i to j's list in pair order gives every list in ascending order
+ * (a body's smaller partners come from earlier pairs than its larger ones).
+ * Returns 0, or -1 if the pairs are not strictly ascending.                 */
+static int build_partners(int64_t n, int64_t npairs, const uint32_t *pairs, int64_t *off,
+                          int64_t *list)
+{
+    for (int64_t k = 1; k < npairs; k++) {
+        uint64_t a = ((uint64_t)pairs[2 * k - 2] << 32) | pairs[2 * k - 1];
+        uint64_t b = ((uint64_t)pairs[2 * k] << 32) | pairs[2 * k + 1];
+        if (!(a < b)) return -1;
+    }
+    for (int64_t i = 0; i <= n; i++) off[i] = 0;
+    for (int64_t k = 0; k < npairs; k++) { off[pairs[2 * k] + 1]++; off[pairs[2 * k + 1] + 1]++; }
+    for (int64_t i = 0; i < n; i++) off[i + 1] += off[i];
+    int64_t *fill = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    for (int64_t k = 0; k < npairs; k++) {
+        int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+        list[off[i] + fill[i]++] = j;
+        list[off[j] + fill[j]++] = i;
+    }
+    free(fill);
+    return 0;
+}
+
+/* Integrate every group of the pair list (ascending pairs) by BS over dt_l,
+ * starting from the saved pre-drift state (xs, vs) of the members.          */
+static void bs_all_groups(step_ctx *cx, int64_t npairs, const uint32_t *pairs, int level,
+                          double dt_l, const double *xs, const double *vs)
+{
+    int64_t n = cx->n;
+    int64_t *label = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    orc_group(n, npairs, pairs, label);
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * npairs + 1));
+    if (build_partners(n, npairs, pairs, off, list) != 0) cx->status |= 4;
+    /* local index of each body inside its group; members ascending */
+    int64_t *loc = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *gsize = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++)
+        if (label[i] >= 0) loc[i] = gsize[label[i]]++;
+    for (int64_t g0 = 0; g0 < n; g0++) {
+        if (gsize[g0] == 0) continue;          /* g0 is a label iff its group is non-empty */
+        int64_t nm = gsize[g0];
+        int64_t *mem = (int64_t *)malloc(sizeof(int64_t) * (size_t)nm);
+        int64_t *poff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nm + 1));
+        for (int64_t i = g0, c = 0; c < nm; i++)
+            if (label[i] == g0) mem[c++] = i;
+        poff[0] = 0;
+        for (int64_t a = 0; a < nm; a++) poff[a + 1] = poff[a] + (off[mem[a] + 1] - off[mem[a]]);
+        int64_t *plist = (int64_t *)malloc(sizeof(int64_t) * (size_t)(poff[nm] > 0 ? poff[nm] : 1));
+        for (int64_t a = 0; a < nm; a++)
+            for (int64_t q = off[mem[a]], c = 0; q < off[mem[a] + 1]; q++, c++)
+                plist[poff[a] + c] = loc[list[q]];
+        double *y = (double *)malloc(sizeof(double) * 6 * (size_t)nm);
+        for (int64_t a = 0; a < nm; a++)
+            for (int k = 0; k < 3; k++) {
+                y[6 * a + k] = xs[3 * mem[a] + k];
+                y[6 * a + 3 + k] = vs[3 * mem[a] + k];
+            }
+        bs_group g;
+        g.nm = nm; g.mem = mem; g.poff = poff; g.plist = plist; g.m = cx->m;
+        g.rcl = (const double *const *)cx->rcl; g.nlev = level + 1;
+        g.G = cx->p->G; g.mu = cx->p->G * cx->p->m_star;
+        int fail = bs_integrate(&g, y, dt_l, cx->p->bs_tol, cx->p->bs_max_steps,
+                                &cx->st->bs_steps, &cx->st->bs_rejects);
+        if (fail) { cx->st->bs_fail++; cx->status |= 2; }
+        for (int64_t a = 0; a < nm; a++)
+            for (int k = 0; k < 3; k++) {
+                cx->x[3 * mem[a] + k] = y[6 * a + k];
+                cx->v[3 * mem[a] + k] = y[6 * a + 3 + k];
+            }
+        cx->st->n_groups++;
+        if (nm > cx->st->max_group) cx->st->max_group = nm;
+        free(y); free(plist); free(poff); free(mem);
+    }
+    free(gsize); free(loc); free(list); free(off); free(label);
+}
+
+/* KickS over a pair list at level l (1..): factor prod_{k<l}(1-K_k) K_l.
+ * Accelerations of all bodies first (partners ascending), then the update.  */
+static void kick_pairs(step_ctx *cx, int64_t nb, const int64_t *bodies, const int64_t *poff,
+                       const int64_t *plist, int level, double dt_half)
+{
+    double *acc = (double *)malloc(sizeof(double) * 3 * (size_t)(nb > 0 ? nb : 1));
+    const double *rcL = cx->rcl[level];
+    for (int64_t a = 0; a < nb; a++) {
+        int64_t i = bodies[a];
+        const double *xi = cx->x + 3 * i;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int64_t q = poff[a]; q < poff[a + 1]; q++) {
+            int64_t j = plist[q];
+            const double *xj = cx->x + 3 * j;
+            double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
+            double r2 = (dx * dx + dy * dy) + dz * dz;
+            double r = sqrt(r2);
+            double W = 1.0;
+            for (int l = 0; l < level; l++) {
+                const double *rc = cx->rcl[l];
+                W *= 1.0 - orc_changeover(r, rc[i] > rc[j] ? rc[i] : rc[j]);
+            }
+            W *= orc_changeover(r, rcL[i] > rcL[j] ? rcL[i] : rcL[j]);
+            double f = cx->m[j] * W / (r2 * r);
+            s0 += f * dx; s1 += f * dy; s2 += f * dz;
+        }
+        acc[3 * a + 0] = cx->p->G * s0;
+        acc[3 * a + 1] = cx->p->G * s1;
+        acc[3 * a + 2] = cx->p->G * s2;
+    }
+    for (int64_t a = 0; a < nb; a++)
+        for (int k = 0; k < 3; k++) cx->v[3 * bodies[a] + k] += dt_half * acc[3 * a + k];
+    free(acc);
+}
+
+/* SEnc (Appendix A) at level `level` >= 1 over the pairs of level-1. */
+static void senc(step_ctx *cx, int64_t npairs, const uint32_t *pairs, int level, double dt_l,
+                 const double *xs_up, const double *vs_up)
+{
+    int64_t n = cx->n;
+    const orc_params *p = cx->p;
+    /* groupS: bodies of this level = members of the upper level's pairs, and
+     * each body's partner list (ascending global index).                     */
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * npairs + 1));
+    if (build_partners(n, npairs, pairs, off, list) != 0) cx->status |= 4;
+    int64_t nb = 0;
+    for (int64_t i = 0; i < n; i++) nb += off[i + 1] > off[i];
+    int64_t *bodies = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    int64_t *poff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb + 1));
+    for (int64_t i = 0, c = 0; i < n; i++) if (off[i + 1] > off[i]) bodies[c++] = i;
+    poff[0] = 0;
+    for (int64_t a = 0; a < nb; a++) poff[a + 1] = poff[a] + (off[bodies[a] + 1] - off[bodies[a]]);
+    int64_t *plist = (int64_t *)malloc(sizeof(int64_t) * (size_t)(poff[nb] > 0 ? poff[nb] : 1));
+    for (int64_t a = 0; a < nb; a++)
+        for (int64_t q = off[bodies[a]], c = 0; q < off[bodies[a] + 1]; q++, c++)
+            plist[poff[a] + c] = list[q];
+    free(list);
+    free(off);
+    /* R10: restart the level bodies from the enclosing level's pre-drift state */
+    for (int64_t a = 0; a < nb; a++)
+        for (int k = 0; k < 3; k++) {
+            cx->x[3 * bodies[a] + k] = xs_up[3 * bodies[a] + k];
+            cx->v[3 * bodies[a] + k] = vs_up[3 * bodies[a] + k];
+        }
+    double *xs = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *vs = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    uint32_t *enc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)(npairs > 0 ? npairs : 1));
+    double *rcL = cx->rcl[level];
+    for (int s = 0; s < p->substeps; s++) {
+        /* RcritS(dt_l) on the level bodies */
+        for (int64_t a = 0; a < nb; a++) {
+            int64_t i = bodies[a];
+            orc_rcrit(1, cx->x + 3 * i, cx->v + 3 * i, cx->m + i, p->m_star, dt_l, p->n1, p->n2,
+                      rcL + i);
+        }
+        kick_pairs(cx, nb, bodies, poff, plist, level, 0.5 * dt_l);
+        for (int64_t a = 0; a < nb; a++)
+            for (int k = 0; k < 3; k++) {
+                xs[3 * bodies[a] + k] = cx->x[3 * bodies[a] + k];
+                vs[3 * bodies[a] + k] = cx->v[3 * bodies[a] + k];
+            }
+        cx->st->kepler_fail += fg_list(bodies, nb, cx->x, cx->v, p->G * p->m_star, dt_l,
+                                       p->kepler_max_iter);
+        int64_t ne = orc_detect(npairs, pairs, xs, cx->x, rcL, enc);
+        cx->st->n_pairs[level] += ne;
+        if (ne > 0) {
+            if (level < p->slevels - 1)
+                senc(cx, ne, enc, level + 1, dt_l / p->substeps, xs, vs);
+            else
+                bs_all_groups(cx, ne, enc, level, dt_l, xs, vs);
+        }
+        kick_pairs(cx, nb, bodies, poff, plist, level, 0.5 * dt_l);
+    }
+    free(enc); free(vs); free(xs); free(plist); free(poff); free(bodies);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Direct entry for tests: group the ascending pair list and integrate every
+ * group by BS over dt from (x, v) in place, with nlev levels of critical radii
+ * rc_levels[l*n + i].  Returns 0, or 2 when a group hit bs_max_steps.        */
+int orc_bs_groups(int64_t n, double *x, double *v, const double *m, const double *rc_levels,
+                  int nlev, int64_t npairs, const uint32_t *pairs, double G, double m_star,
+                  double dt, double tol, int max_steps, orc_stats *st)
+{
+    orc_params p;
+    memset(&p, 0, sizeof(p));
+    p.G = G; p.m_star = m_star; p.bs_tol = tol; p.bs_max_steps = max_steps;
+    step_ctx cx;
+    memset(&cx, 0, sizeof(cx));
+    memset(st, 0, sizeof(*st));
+    cx.n = n; cx.x = x; cx.v = v; cx.m = m; cx.p = &p; cx.st = st;
+    if (nlev < 1 || nlev > ORC_MAX_LEVELS) return -1;
+    for (int l = 0; l < nlev; l++) cx.rcl[l] = (double *)(rc_levels + (size_t)l * (size_t)n);
+    double *xs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *vs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
+    memcpy(vs, v, sizeof(double) * 3 * (size_t)n);
+    bs_all_groups(&cx, npairs, pairs, nlev - 1, dt, xs, vs);
+    free(xs); free(vs);
+    return cx.status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One step of Appendix A (original scheme for slevels == 1, SEnc otherwise).
+ * Returns 0, or a bit mask: 1 Kepler non-convergence, 2 BS limit reached.    */
+int orc_step(int64_t n, double *x, double *v, const double *m, const orc_params *p,
+             int64_t nsteps, orc_stats *st)
+{
+    step_ctx cx;
+    memset(&cx, 0, sizeof(cx));
+    cx.n = n; cx.x = x; cx.v = v; cx.m = m; cx.p = p; cx.st = st;
+    memset(st, 0, sizeof(*st));
+    int L = p->slevels < 1 ? 1 : p->slevels;
+    if (L > ORC_MAX_LEVELS) L = ORC_MAX_LEVELS;
+    for (int l = 0; l < L; l++) cx.rcl[l] = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *xs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *vs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double dt = p->dt, mu = p->G * p->m_star;
+    for (int64_t s = 0; s < nsteps; s++) {
+        orc_rcrit(n, x, v, m, p->m_star, dt, p->n1, p->n2, cx.rcl[0]);
+        int64_t cap = 1024;
+        uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)cap);
+        int64_t nc = orc_precheck(n, x, cx.rcl[0], p->f_pc, cand, cap);
+        if (nc > cap) {
+            free(cand);
+            cap = nc;
+            cand = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)cap);
+            nc = orc_precheck(n, x, cx.rcl[0], p->f_pc, cand, cap);
+        }
+        st->n_candidates += nc;
+        orc_kick(n, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
+        orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
+        memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
+        memcpy(vs, v, sizeof(double) * 3 * (size_t)n);
+        st->kepler_fail += orc_fg(n, x, v, mu, dt, p->kepler_max_iter);
+        if (nc > 0) {
+            uint32_t *enc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)nc);
+            int64_t ne = orc_detect(nc, cand, xs, x, cx.rcl[0], enc);
+            st->n_pairs[0] += ne;
+            if (ne > 0) {
+                if (L > 1)
+                    senc(&cx, ne, enc, 1, dt / p->substeps, xs, vs);
+                else
+                    bs_all_groups(&cx, ne, enc, 0, dt, xs, vs);
+            }
+            free(enc);
+        }
+        free(cand);
+        orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
+        orc_kick(n, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
+    }
+    if (st->kepler_fail) cx.status |= 1;
+    for (int l = 0; l < L; l++) free(cx.rcl[l]);
+    free(xs); free(vs);
+    return cx.status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Total energy (Eq. H = Ha + Hb + Hc, the K terms summing to the full pair
+ * potential) and angular momentum sum_i m_i x_i x v_i, in long double with
+ * Kahan summation.                                                          */
+void orc_energy(int64_t n, const double *x, const double *v, const double *m, double m_star,
+                double G, double *E, double *L)
+{
+    long double sum = 0.0L, comp = 0.0L;
+#define KAHAN_ADD(term) do { long double y_ = (term) - comp; long double t_ = sum + y_; \
+        comp = (t_ - sum) - y_; sum = t_; } while (0)
+    long double P[3] = {0.0L, 0.0L, 0.0L};
+    long double Lx = 0.0L, Ly = 0.0L, Lz = 0.0L;
+    for (int64_t i = 0; i < n; i++) {
+        const double *xi = x + 3 * i, *vi = v + 3 * i;
+        long double v2 = (long double)vi[0] * vi[0] + (long double)vi[1] * vi[1] +
+                         (long double)vi[2] * vi[2];
+        long double r = sqrtl((long double)xi[0] * xi[0] + (long double)xi[1] * xi[1] +
+                              (long double)xi[2] * xi[2]);
+        KAHAN_ADD(0.5L * m[i] * v2);
+        KAHAN_ADD(-(long double)G * m_star * m[i] / r);
+        for (int k = 0; k < 3; k++) P[k] += (long double)m[i] * vi[k];
+        Lx += (long double)m[i] * ((long double)xi[1] * vi[2] - (long double)xi[2] * vi[1]);
+        Ly += (long double)m[i] * ((long double)xi[2] * vi[0] - (long double)xi[0] * vi[2]);
+        Lz += (long double)m[i] * ((long double)xi[0] * vi[1] - (long double)xi[1] * vi[0]);
+    }
+    for (int64_t i = 0; i < n; i++) {
+        const double *xi = x + 3 * i;
+        long double part = 0.0L;
+        for (int64_t j = i + 1; j < n; j++) {
+            const double *xj = x + 3 * j;
+            long double dx = (long double)xj[0] - xi[0], dy = (long double)xj[1] - xi[1],
+                        dz = (long double)xj[2] - xi[2];
+            part += (long double)m[j] / sqrtl(dx * dx + dy * dy + dz * dz);
+        }
+        KAHAN_ADD(-(long double)G * m[i] * part);
+    }
+    KAHAN_ADD((P[0] * P[0] + P[1] * P[1] + P[2] * P[2]) / (2.0L * m_star));
+#undef KAHAN_ADD
+    *E = (double)sum;
+    L[0] = (double)Lx; L[1] = (double)Ly; L[2] = (double)Lz;
+}
+
+/* Size of the parameter and statistics structs, for the loader's layout check. */
+int64_t orc_sizeof_params(void) { return (int64_t)sizeof(orc_params); }
+int64_t orc_sizeof_stats(void) { return (int64_t)sizeof(orc_stats); }
