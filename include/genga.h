@@ -1,0 +1,189 @@
+/*
+ * genga.h -- C ABI of the GB300 (sm_103a) hybrid symplectic N-body hot path of
+ * GENGA II (Grimm et al., arXiv:2201.10058).
+ *
+ * One library object (genga_system_t) integrates N bodies around a central mass
+ * in democratic heliocentric coordinates (Sec. 2, Eq. H = Ha + Hb + Hc):
+ * heliocentric positions, barycentric velocities.  The caller owns the state
+ * arrays (device memory, structure-of-arrays, component-major):
+ *
+ *     pos[0*n + i], pos[1*n + i], pos[2*n + i]   x, y, z of body i   (AU)
+ *     vel[0*n + i], vel[1*n + i], vel[2*n + i]   barycentric velocity (AU/day)
+ *     mass[i]                                    (solar masses)
+ *
+ * The library keeps these pointers and updates pos/vel in place on the stream
+ * given at creation.  It owns all scratch (critical radii, candidate and
+ * encounter pair lists, groups, pre-drift copies, kick partial sums,
+ * Bulirsch-Stoer state) and frees it in genga_destroy.
+ *
+ * Calls are stream-ordered.  Unless a comment says otherwise a call returns
+ * after enqueueing its kernels; errors detected on the device (non-converged
+ * Kepler solve or Bulirsch-Stoer integration, capacity overflow, bad state)
+ * are latched in a device error word and reported by the next call that
+ * synchronises (genga_step, genga_build_encounters, genga_energy, the getters,
+ * genga_sync).  Return value: 0 on success, a negative GENGA_E* code otherwise;
+ * genga_last_error() gives a message.  No call falls back to the CPU.
+ */
+#ifndef GENGA_H
+#define GENGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define GENGA_OK          0
+#define GENGA_EINVAL     -1  /* bad argument (null pointer, n < 1, bad parameter) */
+#define GENGA_ECAPACITY  -2  /* a fixed capacity was exceeded (see genga_get_stats) */
+#define GENGA_ENONCONV   -3  /* Kepler or Bulirsch-Stoer iteration limit reached */
+#define GENGA_ETIMEOUT   -4  /* a bounded device wait gave up */
+#define GENGA_EBADSTATE  -5  /* NaN/Inf in the state, or a body at the origin */
+#define GENGA_ECUDA      -6  /* a CUDA runtime call failed */
+#define GENGA_ENOMEM     -7  /* device allocation failed */
+
+/* ---- kick arithmetic --------------------------------------------------- */
+#define GENGA_FP64   0   /* every pair term in FP64 (CUDA double rsqrt) */
+#define GENGA_MIXED  1   /* FP64 displacement and accumulation, FP32 rsqrt seed +
+                            one FP64 Newton correction, compensated per-tile sums */
+
+/* Integration parameters.  Units are the caller's; the defaults of
+ * genga_default_params are Gaussian units (AU, day, solar mass).            */
+typedef struct genga_params {
+    double G;          /* gravitational constant */
+    double m_star;     /* central mass */
+    double dt;         /* base time step */
+    double n1;         /* Eq. rcrit: Hill-radius factor (paper: 3) */
+    double n2;         /* Eq. rcrit: velocity factor (paper: 0.4) */
+    double f_pc;       /* pre-check factor: candidates have r_ij < f_pc * rc_ij (default 4) */
+    double bs_tol;     /* Bulirsch-Stoer relative tolerance (default 1e-15) */
+    int32_t slevels;   /* symplectic levels, Sec. 4.3 / Appendix A (1 = original method) */
+    int32_t substeps;  /* sub-steps per level (time-step reduction factor per level) */
+    int32_t precision; /* GENGA_FP64 or GENGA_MIXED for the all-pairs kick */
+    int32_t kepler_max_iter; /* Newton iteration limit of the Kepler solve (default 50) */
+    int32_t bs_max_steps;    /* limit on Bulirsch-Stoer step attempts per group (default 100000) */
+    int32_t reserved;
+    int64_t cand_capacity;   /* initial capacity of the candidate pair list (grows on demand) */
+    int64_t pair_capacity;   /* initial capacity of each level's encounter list (grows) */
+} genga_params_t;
+
+/* Counters of the last genga_step call (summed over its steps). */
+typedef struct genga_stats {
+    int64_t n_candidates;    /* pre-check candidate pairs */
+    int64_t n_pairs[8];      /* encounter pairs found per level (summed over sub-steps) */
+    int64_t n_groups;        /* close-encounter groups integrated by Bulirsch-Stoer */
+    int64_t max_group;       /* largest group */
+    int64_t bs_steps;        /* accepted Bulirsch-Stoer sub-steps */
+    int64_t bs_rejects;      /* rejected attempts (step halvings) */
+    int64_t kepler_fail;     /* Kepler solves that hit kepler_max_iter */
+    int64_t bs_fail;         /* groups that hit bs_max_steps */
+} genga_stats_t;
+
+typedef struct genga_system genga_system_t;
+
+/* Fills *p with the paper's defaults (n1 = 3, n2 = 0.4, Sec. 2) and this
+ * library's defaults for the remaining fields; G is k^2 for the Gaussian k.  */
+void genga_default_params(genga_params_t *p);
+
+/* Creates a system of n bodies on the CUDA stream `stream` (a cudaStream_t;
+ * NULL = legacy default stream) of the current device.  pos and vel (3n
+ * doubles each) and mass (n doubles) are caller-owned device arrays that must
+ * outlive the system.  Allocates all library scratch.  Errors: EINVAL, ENOMEM. */
+int genga_create(genga_system_t **out, const genga_params_t *p, int64_t n, double *pos,
+                 double *vel, const double *mass, void *stream);
+
+/* Frees the library scratch (not the caller's arrays).  NULL is a no-op.   */
+void genga_destroy(genga_system_t *sys);
+
+/* Message of the last failed call on this system ("" if none).  The string is
+ * owned by the system and valid until its next call.                       */
+const char *genga_last_error(const genga_system_t *sys);
+
+/* Changes the parameters (same n).  Errors: EINVAL.                         */
+int genga_set_params(genga_system_t *sys, const genga_params_t *p);
+
+/* Blocks until the stream has finished; reports latched device errors.     */
+int genga_sync(genga_system_t *sys);
+
+/* Eq. rcrit (Sec. 2): rc_i = max(n1 R_H,i, n2 dt |v_i|) for every body, with
+ * R_H,i = |x_i| (m_i / 3 m_star)^(1/3), stored as the level-0 critical radii
+ * used by genga_kick, genga_build_encounters and genga_bs.                  */
+int genga_rcrit(genga_system_t *sys, double dt);
+
+/* Replaces the level-0 critical radii with the n values of the host array rc
+ * (a test hook; the derived thresholds are recomputed).  Synchronises.      */
+int genga_set_rcrit(genga_system_t *sys, const double *rc_host);
+
+/* Kick of Eq. Hb (Appendix A "Kick(dt/2)"): for every body
+ *     v_i += dt_half * G * sum_{j != i} m_j K(r_ij; rc_ij) (x_j - x_i) / r_ij^3
+ * with the changeover function K of Chambers (1999), Eq. 10 (Sec. 4.3 fn.),
+ * rc_ij = max(rc_i, rc_j) from genga_rcrit, in the arithmetic selected by
+ * params.precision.  If precheck != 0 the same pass records the close-encounter
+ * candidates (i < j with r_ij^2 < (f_pc rc_ij)^2) for genga_build_encounters.
+ * If acc_out (device, 3n doubles, SoA) is not NULL the accelerations
+ * G sum_j ... are written there and, when dt_half == 0, v is left unchanged. */
+int genga_kick(genga_system_t *sys, double dt_half, int precheck, double *acc_out);
+
+/* Eq. Hc (Appendix A "HC(dt/2)"): x_i += dt_half * (sum_j m_j v_j) / m_star,
+ * the momentum summed in a fixed order.                                     */
+int genga_hc(genga_system_t *sys, double dt_half);
+
+/* Eq. Ha Kepler part (Appendix A "FG(dt)"): saves the pre-drift state, then
+ * drifts every body on its Kepler orbit about mu = G m_star for dt
+ * (universal variables, Stumpff functions by series and argument quartering). */
+int genga_drift(genga_system_t *sys, double dt);
+
+/* Appendix A "close-encounter detection" and "grouping" at level 0: keeps the
+ * candidates of the last pre-check whose distance before (saved pre-drift
+ * state) or after (current state) the drift is below rc_ij, then forms the
+ * connected components of these pairs (group label = smallest member index).
+ * Synchronises; any output pointer may be NULL.                             */
+int genga_build_encounters(genga_system_t *sys, int64_t *n_pairs, int64_t *n_groups,
+                           int64_t *max_group);
+
+/* Appendix A "Bulirsch-Stoer(dt)": restores every member of the level-0 groups
+ * from the pre-drift state and integrates each group over dt (Sec. 4.1) with
+ * the pair forces scaled by 1 - K.  Synchronises.                           */
+int genga_bs(genga_system_t *sys, double dt);
+
+/* nsteps full steps of Appendix A (SEnc recursion when slevels > 1): Rcrit,
+ * Kick + pre-check, HC, FG, detection, grouping, BS or SEnc, HC, Kick.
+ * Synchronises at the end; stats of these steps via genga_get_stats.        */
+int genga_step(genga_system_t *sys, int64_t nsteps);
+
+/* genga_step from host buffers: copies pos_host/vel_host (3n doubles each,
+ * same layout, ideally pinned) to the device arrays, runs nsteps, copies the
+ * result back.  Synchronises.                                               */
+int genga_step_host(genga_system_t *sys, double *pos_host, double *vel_host, int64_t nsteps);
+
+/* Total energy (Eq. H with the K terms summing to the full pair potential)
+ * and angular momentum sum_i m_i x_i x v_i, FP64 with compensated sums.
+ * E and L are host pointers (1 and 3 doubles).  Synchronises.               */
+int genga_energy(genga_system_t *sys, double *E, double *L);
+
+/* Host copies, sorted ascending by (i, j), of the last pre-check candidates
+ * or of the encounter pairs found at `level` (0 = from genga_build_encounters
+ * or the last step's first detection).  ij receives up to cap pairs as
+ * interleaved uint32 (i, j); *n the total count.  Synchronises.             */
+int genga_get_candidates(genga_system_t *sys, uint32_t *ij, int64_t cap, int64_t *n);
+int genga_get_pairs(genga_system_t *sys, int level, uint32_t *ij, int64_t cap, int64_t *n);
+
+/* Host copy of the level-0 group label of every body (smallest member index,
+ * -1 for bodies in no encounter), n int64 values.  Synchronises.            */
+int genga_get_groups(genga_system_t *sys, int64_t *label);
+
+/* Host copy of the level-`level` critical radii (n doubles).  Synchronises. */
+int genga_get_rcrit(genga_system_t *sys, int level, double *rc_host);
+
+/* Replaces the saved pre-drift state (3n doubles each, host, SoA) that
+ * genga_build_encounters and genga_bs read (a test hook).  Synchronises.    */
+int genga_set_predrift(genga_system_t *sys, const double *pos_host, const double *vel_host);
+
+/* Counters of the last genga_step (or of the last build_encounters / bs).   */
+int genga_get_stats(genga_system_t *sys, genga_stats_t *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GENGA_H */

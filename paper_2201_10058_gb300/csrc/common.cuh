@@ -1,0 +1,187 @@
+// common.cuh -- internal declarations of the GB300 hybrid symplectic library.
+// Device helpers, the system object and the kernel launchers shared by the
+// translation units.  Nothing here is part of the public ABI (include/genga.h).
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
+
+#include "../../include/genga.h"
+
+namespace genga {
+
+constexpr int kMaxLevels = 8;
+
+// Device error word bits (latched; read by the host after synchronising).
+enum : unsigned {
+    kErrKepler = 1u,      // Kepler Newton iteration limit
+    kErrBS = 2u,          // Bulirsch-Stoer step-attempt limit
+    kErrCandCap = 4u,     // candidate list overflow (recovered by the host)
+    kErrPairCap = 8u,     // encounter list overflow (recovered by the host)
+    kErrBadState = 16u,   // NaN / Inf / body at the origin
+    kErrUnionFind = 32u,  // bounded union-find retry loop gave up
+};
+
+// Counters that live in device memory.
+struct DevCounters {
+    unsigned long long cand_count;
+    unsigned long long pair_count[kMaxLevels];
+    unsigned long long nbodies[kMaxLevels];
+    unsigned long long kepler_fail;
+    unsigned long long bs_steps;
+    unsigned long long bs_rejects;
+    unsigned long long bs_fail;
+    unsigned long long groups_total;     // groups formed since the last reset
+    unsigned long long max_group_total;  // largest of them
+    unsigned int err;
+    unsigned int ngroups;
+    unsigned int max_group;
+    unsigned int pad;
+    double hc_shift[3];
+};
+
+// Level-independent per-body data of the critical radius (level 0 uses all).
+struct RcritArrays {
+    double *rc;    // rc_i
+    double *rc2;   // rc_i^2 (pair value: max of the two, exact)
+    double *pc2;   // (f_pc rc_i)^2 (level 0 only)
+    float *thr_rc; // conservative FP32 upper bound of rc_i^2 (level 0 only)
+    float *thr_pc; // conservative FP32 upper bound of (f_pc rc_i)^2 (level 0 only)
+};
+
+// CSR partner lists (both directions) of one pair list.
+struct Csr {
+    int *deg = nullptr;    // n+1
+    int *off = nullptr;    // n+1 (exclusive scan of deg)
+    int *fill = nullptr;   // n
+    int *list = nullptr;   // 2 * cap
+    int64_t cap = 0;       // pairs
+};
+
+struct Scratch {
+    // scan temporaries
+    int *scan_blocks = nullptr;
+    int scan_blocks_cap = 0;
+};
+
+}  // namespace genga
+
+struct genga_system {
+    genga_params_t p;
+    int64_t n = 0;
+    double *pos = nullptr;         // caller-owned, 3n
+    double *vel = nullptr;         // caller-owned, 3n
+    const double *mass = nullptr;  // caller-owned, n
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+
+    genga::DevCounters *ctr = nullptr;   // device
+    genga::RcritArrays rcl[genga::kMaxLevels];
+    double *pre_pos[genga::kMaxLevels] = {};  // pre-drift copies, 3n each
+    double *pre_vel[genga::kMaxLevels] = {};
+
+    // all-pairs kick
+    double *kick_part = nullptr;   // [nchunk][6][n]
+    int kick_nchunk = 0;
+    int kick_chunk = 0;
+
+    // candidates and encounter lists
+    uint2 *cand = nullptr;
+    int64_t cand_cap = 0;
+    uint2 *pairs[genga::kMaxLevels] = {};
+    int64_t pair_cap[genga::kMaxLevels] = {};
+    int64_t npairs_host[genga::kMaxLevels] = {};
+    genga::Csr csr[genga::kMaxLevels];
+    int *bodies[genga::kMaxLevels] = {};   // level body lists (ascending)
+    int *flags = nullptr;                  // n+1 scan input
+
+    // grouping
+    int *parent = nullptr;   // n
+    int *label = nullptr;    // n
+    int *gsize = nullptr;    // n+1
+    int *goff = nullptr;     // n+1
+    int *gfill = nullptr;    // n
+    int *glist = nullptr;    // n
+    int *member = nullptr;   // n
+    int *slotof = nullptr;   // n
+    int label_level = -1;    // level whose grouping `label` holds
+
+    // Bulirsch-Stoer scratch: 90 doubles per member slot
+    double *bs_scratch = nullptr;
+
+    // HC / energy reductions
+    double *red = nullptr;   // reduction scratch
+
+    genga::Scratch scr;
+    genga_stats_t stats;
+    char err[512] = {0};
+};
+
+namespace genga {
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+
+// Changeover function of Chambers (1999) Eq. 10 as used in Sec. 4.3:
+// y = (r/rc - 0.1)/0.9 clamped to [0,1], K = y^2/(2y^2 - 2y + 1).  Written with
+// explicit round-to-nearest operations (no contraction).
+__device__ __forceinline__ double changeover(double r, double rc) {
+    double y = __ddiv_rn(__dsub_rn(__ddiv_rn(r, rc), 0.1), 0.9);
+    if (y <= 0.0) return 0.0;
+    if (y >= 1.0) return 1.0;
+    double y2 = __dmul_rn(y, y);
+    double den = __dadd_rn(__dsub_rn(__dmul_rn(2.0, y2), __dmul_rn(2.0, y)), 1.0);
+    return __ddiv_rn(y2, den);
+}
+
+// Squared distance in the detection order (dx^2 + dy^2) + dz^2, no contraction.
+__device__ __forceinline__ double dist2_rn(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Error-free sum: s + e = a + b exactly (Knuth TwoSum).
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    s = __dadd_rn(a, b);
+    double bb = __dsub_rn(s, a);
+    e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void latch_error(DevCounters *c, unsigned bit) { atomicOr(&c->err, bit); }
+
+// ---------------------------------------------------------------------------
+// Host launchers (defined in the .cu files).  All take the system's stream.
+
+// particle.cu
+cudaError_t launch_rcrit(genga_system *s, int level, double dt, const int *bodies, int nb);
+cudaError_t launch_rcrit_derive(genga_system *s);   // thresholds from rcl[0].rc
+cudaError_t launch_hc(genga_system *s, double dt_half);
+cudaError_t launch_drift(genga_system *s, int level, double dt, const int *bodies, int nb);
+cudaError_t launch_restore(genga_system *s, int from_level, const int *bodies, int nb);
+cudaError_t launch_energy(genga_system *s, double *E_host, double *L_host);
+
+// kick.cu
+cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *acc_out);
+cudaError_t launch_precheck_only(genga_system *s);
+int kick_nchunk_for(int n, int num_sms);
+
+// encounter.cu
+cudaError_t launch_detect(genga_system *s, const uint2 *in, int64_t nin, int level,
+                          uint2 *out, int64_t cap, unsigned long long *count);
+cudaError_t build_csr(genga_system *s, int level, int64_t npairs);
+cudaError_t build_bodies(genga_system *s, int level_pairs, int out_level, int *nb_host);
+cudaError_t build_groups(genga_system *s, int level, int64_t npairs);
+cudaError_t exclusive_scan(genga_system *s, const int *in, int *out, int64_t len);
+
+// bs.cu
+cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_groups);
+cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb);
+
+}  // namespace genga
+
+#define GENGA_CUDA_TRY(expr)                                  \
+    do {                                                      \
+        cudaError_t e__ = (expr);                             \
+        if (e__ != cudaSuccess) return e__;                   \
+    } while (0)

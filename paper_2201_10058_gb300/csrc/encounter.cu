@@ -1,0 +1,312 @@
+// encounter.cu -- close-encounter detection, pair compaction and grouping
+// (Appendix A "close-encounter detection", "grouping", "groupS"; Sec. 2).
+//
+//  * detect: one thread per candidate pair; a pair is an encounter when its
+//    squared distance before or after the drift is below rc_ij^2 (exact FP64,
+//    fixed operation order); survivors are appended with one atomic per warp
+//    (ballot + popc prefix).
+//  * CSR: partner lists of a pair list in both directions (degree count,
+//    exclusive scan, atomic fill, per-row insertion sort -> ascending lists,
+//    so every later sum over partners runs in a fixed order: Serial Grouping,
+//    Appendix B).
+//  * level bodies (groupS): bodies with at least one partner, compacted in
+//    ascending order by a scan over flags.
+//  * grouping: union-find with atomicCAS hooking of the larger root under the
+//    smaller one, so every component's root is its smallest member whatever
+//    the order of the races; then group sizes, a scan for offsets and member
+//    slots.
+#include "common.cuh"
+
+namespace genga {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+// ---------------------------------------------------------------- detection
+__global__ void detect_kernel(const uint2 *in, const unsigned long long *nin_dev, long long nin_host,
+                              int n, const double *pre, const double *post, const double *rc2,
+                              uint2 *out, unsigned long long cap, unsigned long long *count) {
+    const long long nin = nin_dev ? (long long)*nin_dev : nin_host;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned lane = threadIdx.x & 31u;
+    bool enc = false;
+    uint2 pr = make_uint2(0, 0);
+    if (k < nin) {
+        pr = in[k];
+        const int i = (int)pr.x, j = (int)pr.y;
+        const size_t N = (size_t)n;
+        const double lim = fmax(rc2[i], rc2[j]);
+        const double d0 = dist2_rn(pre[j] - pre[i], pre[N + j] - pre[N + i], pre[2 * N + j] - pre[2 * N + i]);
+        const double d1 = dist2_rn(post[j] - post[i], post[N + j] - post[N + i], post[2 * N + j] - post[2 * N + i]);
+        enc = (d0 < lim) || (d1 < lim);
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, enc);
+    if (ball == 0u) return;
+    const int leader = __ffs(ball) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(count, (unsigned long long)__popc(ball));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (enc) {
+        const unsigned long long idx = base + __popc(ball & ((1u << lane) - 1u));
+        if (idx < cap) out[idx] = pr;
+    }
+}
+
+// ---------------------------------------------------------------- scan
+// Exclusive scan of int32 in blocks of kScanBlock, then a scan of block sums,
+// then the block offsets are added.  out has len+1 entries (out[len] = total).
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;   // inclusive
+    }
+    __syncthreads();
+    const int before = (warp > 0) ? warp_sums[warp - 1] : 0;
+    total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_blocks_kernel(const int *in, int *out, long long len, int *block_sums) {
+    __shared__ int ws[32];
+    const long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int local = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++) {
+        v[q] = (base + q < len) ? in[base + q] : 0;
+        local += v[q];
+    }
+    int total;
+    int ex = block_exclusive_scan(local, ws, total);
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++) {
+        if (base + q < len) out[base + q] = ex;
+        ex += v[q];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_sums_kernel(int *block_sums, int nblocks, int *total_out) {
+    __shared__ int ws[32];
+    int running = 0;
+    for (int b0 = 0; b0 < nblocks; b0 += kScanThreads) {
+        const int b = b0 + threadIdx.x;
+        const int v = (b < nblocks) ? block_sums[b] : 0;
+        int tot;
+        const int ex = block_exclusive_scan(v, ws, tot);
+        if (b < nblocks) block_sums[b] = running + ex;
+        running += tot;
+    }
+    if (threadIdx.x == 0) *total_out = running;
+}
+
+__global__ void scan_add_kernel(int *out, long long len, const int *block_sums) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < len) out[k] += block_sums[k / kScanBlock];
+}
+
+// ---------------------------------------------------------------- CSR
+__global__ void csr_degree_kernel(const uint2 *pairs, long long np, int *deg) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const uint2 p = pairs[k];
+    atomicAdd(&deg[p.x], 1);
+    atomicAdd(&deg[p.y], 1);
+}
+
+__global__ void csr_fill_kernel(const uint2 *pairs, long long np, const int *off, int *fill, int *list) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const uint2 p = pairs[k];
+    list[off[p.x] + atomicAdd(&fill[p.x], 1)] = (int)p.y;
+    list[off[p.y] + atomicAdd(&fill[p.y], 1)] = (int)p.x;
+}
+
+__global__ void csr_sort_kernel(int n, const int *off, int *list) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int s = off[b], e = off[b + 1];
+    for (int u = s + 1; u < e; u++) {
+        const int key = list[u];
+        int w = u - 1;
+        while (w >= s && list[w] > key) { list[w + 1] = list[w]; w--; }
+        list[w + 1] = key;
+    }
+}
+
+__global__ void flag_nonzero_kernel(int n, const int *deg, int *flags) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) flags[b] = deg[b] > 0 ? 1 : 0;
+}
+
+__global__ void compact_kernel(int n, const int *flags, const int *pos, int *out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n && flags[b]) out[pos[b]] = b;
+}
+
+// ---------------------------------------------------------------- grouping
+__device__ __forceinline__ int uf_find(const int *parent, int a) {
+    // parent pointers only ever decrease, so the chain is finite
+    int p = __ldcg(parent + a);
+    while (p != a) { a = p; p = __ldcg(parent + a); }
+    return a;
+}
+
+__global__ void uf_init_kernel(int n, int *parent) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) parent[b] = b;
+}
+
+__global__ void uf_hook_kernel(const uint2 *pairs, long long np, int *parent, DevCounters *ctr) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const uint2 p = pairs[k];
+    for (int it = 0; it < (1 << 20); it++) {
+        const int ru = uf_find(parent, (int)p.x);
+        const int rv = uf_find(parent, (int)p.y);
+        if (ru == rv) return;
+        const int lo = min(ru, rv), hi = max(ru, rv);
+        if (atomicCAS(&parent[hi], hi, lo) == hi) return;
+    }
+    latch_error(ctr, kErrUnionFind);
+}
+
+__global__ void uf_label_kernel(int n, const int *parent, const int *deg, int *label, int *gsize) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    if (deg[b] > 0) {
+        const int r = uf_find(parent, b);
+        label[b] = r;
+        atomicAdd(&gsize[r], 1);
+    } else {
+        label[b] = -1;
+    }
+}
+
+__global__ void group_members_kernel(int n, const int *label, const int *goff, int *gfill,
+                                     int *member, int *slotof, DevCounters *ctr) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int g = label[b];
+    if (g < 0) return;
+    const int slot = goff[g] + atomicAdd(&gfill[g], 1);
+    member[slot] = b;
+    slotof[b] = slot;
+    if (g == b) {
+        const unsigned sz = (unsigned)(goff[g + 1] - goff[g]);
+        atomicAdd(&ctr->ngroups, 1u);
+        atomicMax(&ctr->max_group, sz);
+        atomicAdd(&ctr->groups_total, 1ull);
+        atomicMax(&ctr->max_group_total, (unsigned long long)sz);
+    }
+}
+
+}  // namespace
+
+cudaError_t exclusive_scan(genga_system *s, const int *in, int *out, int64_t len) {
+    const int nblocks = (int)((len + kScanBlock - 1) / kScanBlock);
+    if (nblocks > s->scr.scan_blocks_cap) return cudaErrorInvalidValue;
+    if (len > 0) {
+        scan_blocks_kernel<<<nblocks, kScanThreads, 0, s->stream>>>(in, out, len, s->scr.scan_blocks);
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    scan_sums_kernel<<<1, kScanThreads, 0, s->stream>>>(s->scr.scan_blocks, nblocks, out + len);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    if (len > 0) {
+        scan_add_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s->stream>>>(out, len, s->scr.scan_blocks);
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_detect(genga_system *s, const uint2 *in, int64_t nin, int level, uint2 *out,
+                          int64_t cap, unsigned long long *count) {
+    GENGA_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s->stream));
+    if (nin <= 0) return cudaSuccess;
+    detect_kernel<<<(unsigned)((nin + 255) / 256), 256, 0, s->stream>>>(in, nullptr, nin, (int)s->n,
+        s->pre_pos[level], s->pos, s->rcl[level].rc2, out, (unsigned long long)cap, count);
+    return cudaGetLastError();
+}
+
+cudaError_t build_csr(genga_system *s, int level, int64_t np) {
+    const int n = (int)s->n;
+    Csr &c = s->csr[level];
+    GENGA_CUDA_TRY(cudaMemsetAsync(c.deg, 0, sizeof(int) * (n + 1), s->stream));
+    GENGA_CUDA_TRY(cudaMemsetAsync(c.fill, 0, sizeof(int) * n, s->stream));
+    if (np > 0) {
+        csr_degree_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.deg);
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    GENGA_CUDA_TRY(exclusive_scan(s, c.deg, c.off, n));
+    if (np > 0) {
+        csr_fill_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.off, c.fill, c.list);
+        GENGA_CUDA_TRY(cudaGetLastError());
+        csr_sort_kernel<<<(n + 127) / 128, 128, 0, s->stream>>>(n, c.off, c.list);
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
+// Bodies with a partner in the pair list of `level_pairs`, ascending, into
+// s->bodies[out_level]; the count is returned through a synchronising copy.
+cudaError_t build_bodies(genga_system *s, int level_pairs, int out_level, int *nb_host) {
+    const int n = (int)s->n;
+    int *pos = s->gfill;   // temporary n+1 ints
+    flag_nonzero_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->csr[level_pairs].deg, s->flags);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    GENGA_CUDA_TRY(exclusive_scan(s, s->flags, pos, n));
+    compact_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->flags, pos, s->bodies[out_level]);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    GENGA_CUDA_TRY(cudaMemcpyAsync(nb_host, pos + n, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    return cudaStreamSynchronize(s->stream);
+}
+
+// Connected components of the pair list of `level` (its CSR must be built).
+cudaError_t build_groups(genga_system *s, int level, int64_t np) {
+    const int n = (int)s->n;
+    GENGA_CUDA_TRY(cudaMemsetAsync(s->gsize, 0, sizeof(int) * (n + 1), s->stream));
+    GENGA_CUDA_TRY(cudaMemsetAsync(s->gfill, 0, sizeof(int) * (n + 1), s->stream));
+    GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->ngroups, 0, 2 * sizeof(unsigned), s->stream));
+    uf_init_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->parent);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    if (np > 0) {
+        uf_hook_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, s->parent, s->ctr);
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    uf_label_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->parent, s->csr[level].deg, s->label, s->gsize);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    GENGA_CUDA_TRY(exclusive_scan(s, s->gsize, s->goff, n));
+    // group list: labels with a non-empty group, ascending
+    flag_nonzero_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->gsize, s->flags);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    int *pos = s->member;   // temporary, rewritten below
+    GENGA_CUDA_TRY(exclusive_scan(s, s->flags, pos, n));
+    compact_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->flags, pos, s->glist);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    group_members_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->label, s->goff, s->gfill,
+                                                                 s->member, s->slotof, s->ctr);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    s->label_level = level;
+    return cudaSuccess;
+}
+
+}  // namespace genga

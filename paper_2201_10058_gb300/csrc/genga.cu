@@ -1,0 +1,522 @@
+// genga.cu -- host side of the C ABI declared in include/genga.h: the system
+// object, its device scratch, and the driver of one step of Appendix A
+//   Rcrit(dt); Kick(dt/2) + pre-check; HC(dt/2); FG(dt);
+//   detection; grouping + Bulirsch-Stoer(dt)   (or SEnc for slevels > 1);
+//   HC(dt/2); Kick(dt/2)
+// with the SEnc recursion of Appendix A for the higher-level changeover
+// scheme (Sec. 4.3).  Every arithmetic step runs in the kernels of kick.cu,
+// particle.cu, encounter.cu and bs.cu; the host only orders launches, reads
+// pair counts to size the next launch, and grows capacities on overflow.
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace genga;
+
+namespace {
+
+int fail(genga_system *s, int code, const char *fmt, ...) {
+    if (s) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(s->err, sizeof(s->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CU(expr)                                                                        \
+    do {                                                                                \
+        cudaError_t e__ = (expr);                                                       \
+        if (e__ != cudaSuccess)                                                         \
+            return fail(s, e__ == cudaErrorMemoryAllocation ? GENGA_ENOMEM : GENGA_ECUDA, \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, __LINE__); \
+    } while (0)
+
+#define TRY(expr)                    \
+    do {                             \
+        int r__ = (expr);            \
+        if (r__ != GENGA_OK) return r__; \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+int levels_of(const genga_params_t &p) {
+    return std::min(std::max(p.slevels, 1), kMaxLevels);
+}
+
+int check_params(genga_system *s, const genga_params_t *p) {
+    if (!p) return fail(s, GENGA_EINVAL, "params is NULL");
+    if (!(p->m_star > 0) || !(p->G > 0)) return fail(s, GENGA_EINVAL, "G and m_star must be > 0");
+    if (p->slevels < 1 || p->slevels > kMaxLevels)
+        return fail(s, GENGA_EINVAL, "slevels must be in [1, %d]", kMaxLevels);
+    if (p->slevels > 1 && p->substeps < 1) return fail(s, GENGA_EINVAL, "substeps must be >= 1");
+    if (p->precision != GENGA_FP64 && p->precision != GENGA_MIXED)
+        return fail(s, GENGA_EINVAL, "precision must be GENGA_FP64 or GENGA_MIXED");
+    if (p->kepler_max_iter < 1 || p->bs_max_steps < 1)
+        return fail(s, GENGA_EINVAL, "iteration limits must be >= 1");
+    if (!(p->bs_tol > 0)) return fail(s, GENGA_EINVAL, "bs_tol must be > 0");
+    return GENGA_OK;
+}
+
+int alloc_pairs(genga_system *s, int level, int64_t cap) {
+    dfree(s->pairs[level]);
+    dfree(s->csr[level].list);
+    CU(dalloc(&s->pairs[level], (size_t)cap));
+    CU(dalloc(&s->csr[level].list, 2 * (size_t)cap));
+    s->pair_cap[level] = cap;
+    s->csr[level].cap = cap;
+    return GENGA_OK;
+}
+
+int alloc_all(genga_system *s) {
+    const size_t n = (size_t)s->n;
+    CU(dalloc(&s->ctr, 1));
+    CU(cudaMemset(s->ctr, 0, sizeof(DevCounters)));
+    for (int l = 0; l < kMaxLevels; l++) {
+        CU(dalloc(&s->rcl[l].rc, n));
+        CU(dalloc(&s->rcl[l].rc2, n));
+        CU(cudaMemset(s->rcl[l].rc, 0, sizeof(double) * n));
+        CU(cudaMemset(s->rcl[l].rc2, 0, sizeof(double) * n));
+        CU(dalloc(&s->pre_pos[l], 3 * n));
+        CU(dalloc(&s->pre_vel[l], 3 * n));
+        CU(dalloc(&s->csr[l].deg, n + 1));
+        CU(dalloc(&s->csr[l].off, n + 1));
+        CU(dalloc(&s->csr[l].fill, n + 1));
+        CU(dalloc(&s->bodies[l], n));
+        const int64_t pc = s->p.pair_capacity > 0 ? s->p.pair_capacity : std::max<int64_t>(1 << 16, 4 * (int64_t)n);
+        TRY(alloc_pairs(s, l, pc));
+        if (l + 1 >= levels_of(s->p)) break;
+    }
+    CU(dalloc(&s->rcl[0].pc2, n));
+    CU(dalloc(&s->rcl[0].thr_rc, n));
+    CU(dalloc(&s->rcl[0].thr_pc, n));
+    s->kick_chunk = 0;
+    s->cand_cap = s->p.cand_capacity > 0 ? s->p.cand_capacity : std::max<int64_t>(1 << 20, 64 * (int64_t)n);
+    CU(dalloc(&s->cand, (size_t)s->cand_cap));
+    CU(dalloc(&s->flags, n + 1));
+    CU(dalloc(&s->parent, n));
+    CU(dalloc(&s->label, n));
+    CU(dalloc(&s->gsize, n + 1));
+    CU(dalloc(&s->goff, n + 1));
+    CU(dalloc(&s->gfill, n + 1));
+    CU(dalloc(&s->glist, n + 1));
+    CU(dalloc(&s->member, n + 1));
+    CU(dalloc(&s->slotof, n));
+    CU(dalloc(&s->bs_scratch, 84 * n));
+    CU(dalloc(&s->red, 9 * n + 16));
+    s->scr.scan_blocks_cap = (int)((n + 1 + 4095) / 4096) + 2;
+    CU(dalloc(&s->scr.scan_blocks, (size_t)s->scr.scan_blocks_cap));
+    return GENGA_OK;
+}
+
+void free_all(genga_system *s) {
+    dfree(s->ctr);
+    for (int l = 0; l < kMaxLevels; l++) {
+        dfree(s->rcl[l].rc); dfree(s->rcl[l].rc2); dfree(s->rcl[l].pc2);
+        dfree(s->rcl[l].thr_rc); dfree(s->rcl[l].thr_pc);
+        dfree(s->pre_pos[l]); dfree(s->pre_vel[l]);
+        dfree(s->pairs[l]);
+        dfree(s->csr[l].deg); dfree(s->csr[l].off); dfree(s->csr[l].fill); dfree(s->csr[l].list);
+        dfree(s->bodies[l]);
+    }
+    dfree(s->kick_part); dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
+    dfree(s->gsize); dfree(s->goff); dfree(s->gfill); dfree(s->glist); dfree(s->member);
+    dfree(s->slotof); dfree(s->bs_scratch); dfree(s->red); dfree(s->scr.scan_blocks);
+}
+
+template <typename T>
+int read_dev(genga_system *s, T *host, const T *dev) {
+    CU(cudaMemcpyAsync(host, dev, sizeof(T), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return GENGA_OK;
+}
+
+int device_errors(genga_system *s) {
+    unsigned err = 0;
+    TRY(read_dev(s, &err, &s->ctr->err));
+    if (!err) return GENGA_OK;
+    CU(cudaMemsetAsync(&s->ctr->err, 0, sizeof(unsigned), s->stream));
+    if (err & kErrBadState) return fail(s, GENGA_EBADSTATE, "non-finite state or body at the origin");
+    if (err & kErrKepler) return fail(s, GENGA_ENONCONV, "Kepler solve hit kepler_max_iter");
+    if (err & kErrBS) return fail(s, GENGA_ENONCONV, "Bulirsch-Stoer hit bs_max_steps");
+    if (err & kErrUnionFind) return fail(s, GENGA_ETIMEOUT, "grouping retry limit reached");
+    return fail(s, GENGA_ECAPACITY, "capacity exceeded (error word 0x%x)", err);
+}
+
+// Stops a step before the encounter phase when the state is already bad.
+int early_errors(genga_system *s) {
+    unsigned err = 0;
+    TRY(read_dev(s, &err, &s->ctr->err));
+    if (err & (kErrBadState | kErrKepler)) return device_errors(s);
+    return GENGA_OK;
+}
+
+// ---------------------------------------------------------------- step pieces
+int kick(genga_system *s, double dt_half, bool precheck, double *acc_out) {
+    if (!s->kick_part) {
+        const int nchunk = kick_nchunk_for((int)s->n, s->num_sms);
+        CU(dalloc(&s->kick_part, (size_t)nchunk * 6 * (size_t)s->n));
+    }
+    CU(launch_kick(s, dt_half, precheck, acc_out));
+    return GENGA_OK;
+}
+
+// Candidate count after a pre-check kick; regrows and recomputes on overflow.
+int settle_candidates(genga_system *s, int64_t *ncand) {
+    unsigned long long c = 0;
+    TRY(read_dev(s, &c, &s->ctr->cand_count));
+    if ((int64_t)c > s->cand_cap) {
+        dfree(s->cand);
+        s->cand_cap = (int64_t)(c + c / 2 + 1024);
+        CU(dalloc(&s->cand, (size_t)s->cand_cap));
+        CU(launch_precheck_only(s));
+        TRY(read_dev(s, &c, &s->ctr->cand_count));
+        if ((int64_t)c > s->cand_cap) return fail(s, GENGA_ECAPACITY, "candidate list overflow");
+    }
+    *ncand = (int64_t)c;
+    return GENGA_OK;
+}
+
+// Detection at `level` over `in`; regrows the level list on overflow.
+int detect(genga_system *s, const uint2 *in, int64_t nin, int level, int64_t *np) {
+    unsigned long long c = 0;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        CU(launch_detect(s, in, nin, level, s->pairs[level], s->pair_cap[level], &s->ctr->pair_count[level]));
+        TRY(read_dev(s, &c, &s->ctr->pair_count[level]));
+        if ((int64_t)c <= s->pair_cap[level]) break;
+        TRY(alloc_pairs(s, level, (int64_t)(c + c / 2 + 1024)));
+    }
+    if ((int64_t)c > s->pair_cap[level]) return fail(s, GENGA_ECAPACITY, "pair list overflow");
+    *np = (int64_t)c;
+    s->npairs_host[level] = *np;
+    return GENGA_OK;
+}
+
+int bs_groups(genga_system *s, int level, int64_t np, double dt_l) {
+    CU(build_groups(s, level, np));
+    CU(launch_bs(s, level, dt_l, std::min<int64_t>(np, s->n / 2 + 1)));
+    return GENGA_OK;
+}
+
+int senc(genga_system *s, int level, double dt_l) {
+    const int L = levels_of(s->p);
+    int nb = 0;
+    CU(build_bodies(s, level - 1, level, &nb));
+    CU(launch_restore(s, level - 1, s->bodies[level], nb));
+    for (int sub = 0; sub < s->p.substeps; sub++) {
+        CU(launch_rcrit(s, level, dt_l, s->bodies[level], nb));
+        CU(launch_kick_pairs(s, level, 0.5 * dt_l, nb));
+        CU(launch_drift(s, level, dt_l, s->bodies[level], nb));
+        int64_t np = 0;
+        TRY(detect(s, s->pairs[level - 1], s->npairs_host[level - 1], level, &np));
+        s->stats.n_pairs[level] += np;
+        if (np > 0) {
+            CU(build_csr(s, level, np));
+            if (level < L - 1) TRY(senc(s, level + 1, dt_l / s->p.substeps));
+            else TRY(bs_groups(s, level, np, dt_l));
+        }
+        CU(launch_kick_pairs(s, level, 0.5 * dt_l, nb));
+    }
+    return GENGA_OK;
+}
+
+int one_step(genga_system *s) {
+    const double dt = s->p.dt;
+    const int n = (int)s->n;
+    const int L = levels_of(s->p);
+    CU(launch_rcrit(s, 0, dt, nullptr, n));
+    TRY(kick(s, 0.5 * dt, true, nullptr));
+    CU(launch_hc(s, 0.5 * dt));
+    CU(launch_drift(s, 0, dt, nullptr, n));
+    int64_t ncand = 0;
+    TRY(settle_candidates(s, &ncand));
+    s->stats.n_candidates += ncand;
+    TRY(early_errors(s));
+    s->npairs_host[0] = 0;
+    if (ncand > 0) {
+        int64_t np = 0;
+        TRY(detect(s, s->cand, ncand, 0, &np));
+        s->stats.n_pairs[0] += np;
+        if (np > 0) {
+            CU(build_csr(s, 0, np));
+            if (L > 1) TRY(senc(s, 1, dt / s->p.substeps));
+            else TRY(bs_groups(s, 0, np, dt));
+        }
+    }
+    CU(launch_hc(s, 0.5 * dt));
+    TRY(kick(s, 0.5 * dt, false, nullptr));
+    return GENGA_OK;
+}
+
+int collect_stats(genga_system *s) {
+    DevCounters c;
+    CU(cudaMemcpyAsync(&c, s->ctr, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    s->stats.n_groups = (int64_t)c.groups_total;
+    s->stats.max_group = (int64_t)c.max_group_total;
+    s->stats.bs_steps = (int64_t)c.bs_steps;
+    s->stats.bs_rejects = (int64_t)c.bs_rejects;
+    s->stats.bs_fail = (int64_t)c.bs_fail;
+    s->stats.kepler_fail = (int64_t)c.kepler_fail;
+    return GENGA_OK;
+}
+
+int reset_stats(genga_system *s) {
+    memset(&s->stats, 0, sizeof(s->stats));
+    CU(cudaMemsetAsync(&s->ctr->kepler_fail, 0, 6 * sizeof(unsigned long long), s->stream));
+    return GENGA_OK;
+}
+
+int copy_pairs_sorted(genga_system *s, const uint2 *dev, int64_t count, uint32_t *ij, int64_t cap,
+                      int64_t *n_out) {
+    if (n_out) *n_out = count;
+    if (!ij || count == 0) return GENGA_OK;
+    std::vector<uint2> h((size_t)count);
+    CU(cudaMemcpyAsync(h.data(), dev, sizeof(uint2) * (size_t)count, cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    std::sort(h.begin(), h.end(), [](const uint2 &a, const uint2 &b) {
+        return a.x < b.x || (a.x == b.x && a.y < b.y);
+    });
+    const int64_t m = std::min(cap, count);
+    for (int64_t k = 0; k < m; k++) { ij[2 * k] = h[k].x; ij[2 * k + 1] = h[k].y; }
+    return GENGA_OK;
+}
+
+}  // namespace
+
+// ============================================================== public ABI
+extern "C" {
+
+void genga_default_params(genga_params_t *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->G = 0.01720209895 * 0.01720209895;
+    p->m_star = 1.0;
+    p->dt = 6.0875;
+    p->n1 = 3.0;
+    p->n2 = 0.4;
+    p->f_pc = 4.0;
+    p->bs_tol = 1e-15;
+    p->slevels = 1;
+    p->substeps = 1;
+    p->precision = GENGA_FP64;
+    p->kepler_max_iter = 50;
+    p->bs_max_steps = 100000;
+}
+
+int genga_create(genga_system_t **out, const genga_params_t *p, int64_t n, double *pos, double *vel,
+                 const double *mass, void *stream) {
+    if (!out) return GENGA_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > (int64_t)1 << 30 || !pos || !vel || !mass) return GENGA_EINVAL;
+    genga_system *s = new (std::nothrow) genga_system();
+    if (!s) return GENGA_ENOMEM;
+    int rc = check_params(s, p);
+    if (rc != GENGA_OK) { delete s; return rc; }
+    s->p = *p;
+    s->n = n;
+    s->pos = pos; s->vel = vel; s->mass = mass;
+    s->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+        delete s;
+        return GENGA_ECUDA;
+    }
+    rc = alloc_all(s);
+    if (rc != GENGA_OK) { free_all(s); delete s; return rc; }
+    *out = s;
+    return GENGA_OK;
+}
+
+void genga_destroy(genga_system_t *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    free_all(s);
+    delete s;
+}
+
+const char *genga_last_error(const genga_system_t *s) { return s ? s->err : "null system"; }
+
+int genga_set_params(genga_system_t *s, const genga_params_t *p) {
+    if (!s) return GENGA_EINVAL;
+    TRY(check_params(s, p));
+    if (levels_of(*p) > levels_of(s->p)) {
+        // allocate the extra levels
+        const size_t n = (size_t)s->n;
+        for (int l = levels_of(s->p); l < levels_of(*p); l++) {
+            CU(dalloc(&s->pre_pos[l], 3 * n));
+            CU(dalloc(&s->pre_vel[l], 3 * n));
+            CU(dalloc(&s->csr[l].deg, n + 1));
+            CU(dalloc(&s->csr[l].off, n + 1));
+            CU(dalloc(&s->csr[l].fill, n + 1));
+            CU(dalloc(&s->bodies[l], n));
+            TRY(alloc_pairs(s, l, s->pair_cap[0]));
+        }
+    }
+    s->p = *p;
+    return GENGA_OK;
+}
+
+int genga_sync(genga_system_t *s) {
+    if (!s) return GENGA_EINVAL;
+    CU(cudaStreamSynchronize(s->stream));
+    return device_errors(s);
+}
+
+int genga_rcrit(genga_system_t *s, double dt) {
+    if (!s) return GENGA_EINVAL;
+    CU(launch_rcrit(s, 0, dt, nullptr, (int)s->n));
+    return GENGA_OK;
+}
+
+int genga_set_rcrit(genga_system_t *s, const double *rc_host) {
+    if (!s || !rc_host) return GENGA_EINVAL;
+    CU(cudaMemcpyAsync(s->rcl[0].rc, rc_host, sizeof(double) * (size_t)s->n, cudaMemcpyHostToDevice, s->stream));
+    CU(launch_rcrit_derive(s));
+    CU(cudaStreamSynchronize(s->stream));
+    return GENGA_OK;
+}
+
+int genga_kick(genga_system_t *s, double dt_half, int precheck, double *acc_out) {
+    if (!s) return GENGA_EINVAL;
+    TRY(kick(s, dt_half, precheck != 0, acc_out));
+    if (precheck) {
+        int64_t nc = 0;
+        TRY(settle_candidates(s, &nc));
+        s->stats.n_candidates = nc;
+    }
+    return GENGA_OK;
+}
+
+int genga_hc(genga_system_t *s, double dt_half) {
+    if (!s) return GENGA_EINVAL;
+    CU(launch_hc(s, dt_half));
+    return GENGA_OK;
+}
+
+int genga_drift(genga_system_t *s, double dt) {
+    if (!s) return GENGA_EINVAL;
+    CU(launch_drift(s, 0, dt, nullptr, (int)s->n));
+    return GENGA_OK;
+}
+
+int genga_build_encounters(genga_system_t *s, int64_t *n_pairs, int64_t *n_groups, int64_t *max_group) {
+    if (!s) return GENGA_EINVAL;
+    int64_t nc = 0, np = 0;
+    TRY(read_dev(s, (unsigned long long *)&nc, &s->ctr->cand_count));
+    TRY(detect(s, s->cand, nc, 0, &np));
+    CU(build_csr(s, 0, np));
+    CU(build_groups(s, 0, np));
+    DevCounters c;
+    CU(cudaMemcpyAsync(&c, s->ctr, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    if (n_pairs) *n_pairs = np;
+    if (n_groups) *n_groups = c.ngroups;
+    if (max_group) *max_group = c.max_group;
+    s->stats.n_pairs[0] = np;
+    s->stats.n_groups = c.ngroups;
+    s->stats.max_group = c.max_group;
+    return device_errors(s);
+}
+
+int genga_bs(genga_system_t *s, double dt) {
+    if (!s) return GENGA_EINVAL;
+    TRY(reset_stats(s));
+    const int64_t np = s->npairs_host[0];
+    if (np > 0) {
+        if (s->label_level != 0) CU(build_groups(s, 0, np));
+        CU(launch_bs(s, 0, dt, std::min<int64_t>(np, s->n / 2 + 1)));
+    }
+    TRY(collect_stats(s));
+    return device_errors(s);
+}
+
+int genga_step(genga_system_t *s, int64_t nsteps) {
+    if (!s || nsteps < 0) return GENGA_EINVAL;
+    TRY(reset_stats(s));
+    for (int64_t k = 0; k < nsteps; k++) {
+        TRY(one_step(s));
+    }
+    TRY(collect_stats(s));
+    return device_errors(s);
+}
+
+int genga_step_host(genga_system_t *s, double *pos_host, double *vel_host, int64_t nsteps) {
+    if (!s || !pos_host || !vel_host) return GENGA_EINVAL;
+    const size_t bytes = sizeof(double) * 3 * (size_t)s->n;
+    CU(cudaMemcpyAsync(s->pos, pos_host, bytes, cudaMemcpyHostToDevice, s->stream));
+    CU(cudaMemcpyAsync(s->vel, vel_host, bytes, cudaMemcpyHostToDevice, s->stream));
+    TRY(genga_step(s, nsteps));
+    CU(cudaMemcpyAsync(pos_host, s->pos, bytes, cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaMemcpyAsync(vel_host, s->vel, bytes, cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return GENGA_OK;
+}
+
+int genga_energy(genga_system_t *s, double *E, double *L) {
+    if (!s || !E || !L) return GENGA_EINVAL;
+    CU(launch_energy(s, E, L));
+    return device_errors(s);
+}
+
+int genga_get_candidates(genga_system_t *s, uint32_t *ij, int64_t cap, int64_t *n) {
+    if (!s) return GENGA_EINVAL;
+    unsigned long long c = 0;
+    TRY(read_dev(s, &c, &s->ctr->cand_count));
+    const int64_t cnt = std::min<int64_t>((int64_t)c, s->cand_cap);
+    return copy_pairs_sorted(s, s->cand, cnt, ij, cap, n);
+}
+
+int genga_get_pairs(genga_system_t *s, int level, uint32_t *ij, int64_t cap, int64_t *n) {
+    if (!s || level < 0 || level >= levels_of(s->p)) return GENGA_EINVAL;
+    return copy_pairs_sorted(s, s->pairs[level], s->npairs_host[level], ij, cap, n);
+}
+
+int genga_get_groups(genga_system_t *s, int64_t *label) {
+    if (!s || !label) return GENGA_EINVAL;
+    std::vector<int> h((size_t)s->n);
+    CU(cudaMemcpyAsync(h.data(), s->label, sizeof(int) * (size_t)s->n, cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    for (int64_t i = 0; i < s->n; i++) label[i] = h[(size_t)i];
+    return GENGA_OK;
+}
+
+int genga_get_rcrit(genga_system_t *s, int level, double *rc_host) {
+    if (!s || !rc_host || level < 0 || level >= levels_of(s->p)) return GENGA_EINVAL;
+    CU(cudaMemcpyAsync(rc_host, s->rcl[level].rc, sizeof(double) * (size_t)s->n, cudaMemcpyDeviceToHost, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return GENGA_OK;
+}
+
+int genga_set_predrift(genga_system_t *s, const double *pos_host, const double *vel_host) {
+    if (!s || !pos_host || !vel_host) return GENGA_EINVAL;
+    const size_t bytes = sizeof(double) * 3 * (size_t)s->n;
+    CU(cudaMemcpyAsync(s->pre_pos[0], pos_host, bytes, cudaMemcpyHostToDevice, s->stream));
+    CU(cudaMemcpyAsync(s->pre_vel[0], vel_host, bytes, cudaMemcpyHostToDevice, s->stream));
+    CU(cudaStreamSynchronize(s->stream));
+    return GENGA_OK;
+}
+
+int genga_get_stats(genga_system_t *s, genga_stats_t *st) {
+    if (!s || !st) return GENGA_EINVAL;
+    *st = s->stats;
+    return GENGA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+// kick.cu -- all-pairs changeover kick of Eq. Hb (Appendix A "Kick(dt/2)"):
+//   a_i = G sum_{j != i} m_j K(r_ij; rc_ij) (x_j - x_i) / r_ij^3
+// with the close-encounter pre-check fused into the same pass.
+//
+// GB300 design.  The kick is bound by the FP64 pipe (about 2 DFMA per clock per
+// SM on GB300, 1/64 of FP32), so the kernel minimises FP64 instructions per
+// pair and keeps everything else on the FP32, MUFU and integer pipes:
+//   * j bodies are staged in shared memory in tiles of 256 (x, y, z, m and the
+//     per-body thresholds); every thread owns one target i;
+//   * the grid is (i-tiles x j-chunks) so that thousands of equal blocks
+//     balance across the 152 SMs; each block writes compensated partial sums
+//     for its chunk, folded in a fixed order by kick_finalize (deterministic);
+//   * the rare pairs inside f_pc rc_ij are found by an FP32 test on the high
+//     bits of r^2 (conservative threshold); only those take the exact FP64
+//     pre-check (operation order identical to the definition, no contraction)
+//     and the changeover function; candidates are appended with one atomic per
+//     warp (ballot + popc);
+//   * MIXED: r^-1 from an FP32 rsqrt seed built from the bits of r^2, one FP64
+//     Newton correction; FP64 displacement and accumulation; per-tile sums
+//     folded with TwoSum.  FP64: CUDA's double rsqrt.
+#include "common.cuh"
+
+namespace genga {
+namespace {
+
+constexpr int kKickThreads = 128;
+constexpr int kTile = 256;
+
+struct KickArgs {
+    const double *x, *y, *z, *m;
+    const double *rc, *rc2, *pc2;
+    const float *thr;           // thr_pc (pre-check) or thr_rc
+    int n;
+    int chunk;
+    double *part;               // [nchunk][6][n]
+    uint2 *cand;
+    unsigned long long *cand_count;
+    unsigned long long cand_cap;
+};
+
+// FP32 value of a positive double, mantissa truncated (never above the input);
+// 0 for inputs below 2^-126 (including 0).
+__device__ __forceinline__ float r2_to_float_trunc(double r2) {
+    unsigned hi = (unsigned)__double2hiint(r2);
+    unsigned lo = (unsigned)__double2loint(r2);
+    unsigned fb = (hi >= 0x38100000u) ? (((hi - 0x38000000u) << 3) | (lo >> 29)) : 0u;
+    return __uint_as_float(fb);
+}
+
+// Double with the value of a positive normal float (exact), and half of it.
+__device__ __forceinline__ double float_to_double_exact(unsigned fb) {
+    return __hiloint2double((int)((fb >> 3) + 0x38000000u), (int)(fb << 29));
+}
+__device__ __forceinline__ double float_to_double_half(unsigned fb) {
+    return __hiloint2double((int)((fb >> 3) + 0x38000000u - 0x00100000u), (int)(fb << 29));
+}
+
+template <bool MIXED, bool PRECHECK, bool FORCE>
+__global__ void __launch_bounds__(kKickThreads)
+kick_kernel(KickArgs A)
+{
+    __shared__ double sx[kTile], sy[kTile], sz[kTile], sm[kTile];
+    __shared__ double src[kTile], src2[kTile], spc2[kTile];
+    __shared__ float sthr[kTile];
+
+    const int n = A.n;
+    const int i = blockIdx.x * kKickThreads + threadIdx.x;
+    const bool valid = i < n;
+    const unsigned lane = threadIdx.x & 31u;
+
+    double xi = 1e15, yi = 1e15, zi = 1e15;
+    double rci = 0.0, rc2i = 0.0, pc2i = 0.0;
+    float thri = 0.0f;
+    if (valid) {
+        xi = A.x[i]; yi = A.y[i]; zi = A.z[i];
+        rci = A.rc[i]; rc2i = A.rc2[i]; thri = A.thr[i];
+        if (PRECHECK) pc2i = A.pc2[i];
+    }
+
+    const int jbeg = blockIdx.y * A.chunk;
+    const int jend = min(n, jbeg + A.chunk);
+
+    double S0 = 0.0, S1 = 0.0, S2 = 0.0;   // compensated chunk totals
+    double C0 = 0.0, C1 = 0.0, C2 = 0.0;
+
+    for (int jt = jbeg; jt < jend; jt += kTile) {
+        const int cnt = min(kTile, jend - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kKickThreads) {
+            const int j = jt + k;
+            sx[k] = A.x[j]; sy[k] = A.y[j]; sz[k] = A.z[j]; sm[k] = A.m[j];
+            src[k] = A.rc[j]; src2[k] = A.rc2[j];
+            if (PRECHECK) spc2[k] = A.pc2[j];
+            sthr[k] = A.thr[j];
+        }
+        __syncthreads();
+
+        double ax = 0.0, ay = 0.0, az = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < cnt; k++) {
+            const int j = jt + k;
+            const double dx = sx[k] - xi;
+            const double dy = sy[k] - yi;
+            const double dz = sz[k] - zi;
+            double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            float r2f = r2_to_float_trunc(r2);
+            double mk = sm[k];
+            if (r2f < fmaxf(thri, sthr[k])) {
+                // Rare path: exact pre-check and changeover function.
+                const double r2e = dist2_rn(dx, dy, dz);
+                if (PRECHECK) {
+                    const bool emit = valid && (j > i) && (r2e < fmax(pc2i, spc2[k]));
+                    const unsigned act = __activemask();
+                    const unsigned ball = __ballot_sync(act, emit);
+                    if (ball) {
+                        const int leader = __ffs(ball) - 1;
+                        unsigned long long base = 0;
+                        if ((int)lane == leader) base = atomicAdd(A.cand_count, (unsigned long long)__popc(ball));
+                        base = __shfl_sync(act, base, leader);
+                        if (emit) {
+                            const unsigned long long idx = base + __popc(ball & ((1u << lane) - 1u));
+                            if (idx < A.cand_cap) A.cand[idx] = make_uint2((unsigned)i, (unsigned)j);
+                        }
+                    }
+                }
+                if (j == i) {
+                    mk = 0.0; r2 = 1.0; r2f = 1.0f;          // self term: zero, finite
+                } else if (FORCE && r2e < fmax(rc2i, src2[k])) {
+                    mk = mk * changeover(sqrt(r2e), fmax(rci, src[k]));
+                }
+            }
+            if (FORCE) {
+                double s;
+                if (MIXED) {
+                    const float y0f = rsqrtf(r2f);
+                    const unsigned yb = __float_as_uint(y0f);
+                    const double y0 = float_to_double_exact(yb);
+                    const double h0 = float_to_double_half(yb);
+                    const double t = r2 * y0;
+                    const double e = fma(-t, y0, 1.0);        // 1 - r^2 y0^2
+                    const double yv = fma(h0, e, y0);          // one Newton correction
+                    s = (mk * yv) * (yv * yv);
+                } else {
+                    const double yv = rsqrt(r2);
+                    s = (mk * yv) * (yv * yv);
+                }
+                ax = fma(s, dx, ax);
+                ay = fma(s, dy, ay);
+                az = fma(s, dz, az);
+            }
+        }
+        if (FORCE) {
+            double t, e;
+            two_sum(S0, ax, t, e); S0 = t; C0 += e;
+            two_sum(S1, ay, t, e); S1 = t; C1 += e;
+            two_sum(S2, az, t, e); S2 = t; C2 += e;
+        }
+    }
+    if (FORCE && valid) {
+        double *p = A.part + (size_t)blockIdx.y * 6 * n;
+        p[0 * (size_t)n + i] = S0;
+        p[1 * (size_t)n + i] = S1;
+        p[2 * (size_t)n + i] = S2;
+        p[3 * (size_t)n + i] = C0;
+        p[4 * (size_t)n + i] = C1;
+        p[5 * (size_t)n + i] = C2;
+    }
+}
+
+// Folds the chunk partials in chunk order (TwoSum), scales by G and applies the
+// kick v += dt_half a; optionally stores a.
+__global__ void kick_finalize(const double *part, int nchunk, int n, double G, double dt_half,
+                              double *vel, double *acc_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        double S = 0.0, C = 0.0;
+        for (int q = 0; q < nchunk; q++) {
+            const double *p = part + (size_t)q * 6 * n;
+            double t, e;
+            two_sum(S, p[(size_t)c * n + i], t, e);
+            S = t;
+            C += e + p[(size_t)(3 + c) * n + i];
+        }
+        const double a = G * (S + C);
+        if (acc_out) acc_out[(size_t)c * n + i] = a;
+        if (dt_half != 0.0) vel[(size_t)c * n + i] += dt_half * a;
+    }
+}
+
+void kick_geometry(int n, int num_sms, int *chunk, int *nchunk) {
+    // (i-tiles x j-chunks) grid
+    const int iblocks = (n + kKickThreads - 1) / kKickThreads;
+    const int max_chunks = (n + kTile - 1) / kTile;
+    // aim for at least 8 blocks per SM, each at least one tile and at most 16
+    int want = (8 * num_sms + iblocks - 1) / iblocks;
+    int tiles_per_chunk = (max_chunks + want - 1) / (want > 0 ? want : 1);
+    if (tiles_per_chunk > 16) tiles_per_chunk = 16;
+    if (tiles_per_chunk < 1) tiles_per_chunk = 1;
+    *chunk = tiles_per_chunk * kTile;
+    *nchunk = (n + *chunk - 1) / *chunk;
+}
+
+}  // namespace
+
+static KickArgs make_args(genga_system *s, bool precheck) {
+    KickArgs A;
+    const int64_t n = s->n;
+    A.x = s->pos; A.y = s->pos + n; A.z = s->pos + 2 * n; A.m = s->mass;
+    A.rc = s->rcl[0].rc; A.rc2 = s->rcl[0].rc2; A.pc2 = s->rcl[0].pc2;
+    A.thr = precheck ? s->rcl[0].thr_pc : s->rcl[0].thr_rc;
+    A.n = (int)n;
+    A.chunk = s->kick_chunk;
+    A.part = s->kick_part;
+    A.cand = s->cand;
+    A.cand_count = &s->ctr->cand_count;
+    A.cand_cap = (unsigned long long)s->cand_cap;
+    return A;
+}
+
+cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *acc_out) {
+    const int n = (int)s->n;
+    if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
+    KickArgs A = make_args(s, precheck);
+    dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
+    if (precheck)
+        GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->cand_count, 0, sizeof(unsigned long long), s->stream));
+    const bool mixed = s->p.precision == GENGA_MIXED;
+    if (mixed && precheck) kick_kernel<true, true, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    else if (mixed) kick_kernel<true, false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    else if (precheck) kick_kernel<false, true, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    else kick_kernel<false, false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    kick_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(s->kick_part, s->kick_nchunk, n, s->p.G,
+                                                          dt_half, s->vel, acc_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precheck_only(genga_system *s) {
+    const int n = (int)s->n;
+    if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
+    KickArgs A = make_args(s, true);
+    dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
+    GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->cand_count, 0, sizeof(unsigned long long), s->stream));
+    kick_kernel<true, true, false><<<grid, kKickThreads, 0, s->stream>>>(A);
+    return cudaGetLastError();
+}
+
+int kick_nchunk_for(int n, int num_sms) {
+    int c, nc;
+    kick_geometry(n, num_sms, &c, &nc);
+    return nc;
+}
+
+}  // namespace genga

@@ -1,0 +1,341 @@
+// particle.cu -- per-body kernels of the hybrid step (Appendix A): Rcrit
+// (Eq. rcrit), HC (Eq. Hc), FG (Kepler part of Eq. Ha) with the pre-drift copy,
+// the level restore of the higher-level scheme (Sec. 4.3), and the energy /
+// angular-momentum report (Eq. H).
+//
+// These kernels are memory/latency bound (a few hundred bytes per body); they
+// use one thread per body, coalesced SoA loads and no shared memory.  FG runs
+// its Newton iteration per thread; its Stumpff functions need no
+// transcendental calls (series + argument quartering).
+#include "common.cuh"
+
+namespace genga {
+namespace {
+
+// ---------------------------------------------------------------- Rcrit
+// rc_i = max(n1 R_H,i, n2 dt |v_i|), R_H,i = |x_i| (m_i/(3 m_star))^(1/3).
+// |x| and |v| use the detection operation order (no contraction) so that the
+// thresholds compare bit-for-bit with a plain CPU evaluation.
+__device__ __forceinline__ void derive_thresholds(double rc, double f_pc, double *rc2, double *pc2,
+                                                  float *thr_rc, float *thr_pc) {
+    const double r2 = __dmul_rn(rc, rc);
+    const double t = __dmul_rn(f_pc, rc);
+    const double p2 = __dmul_rn(t, t);
+    *rc2 = r2;
+    if (pc2) *pc2 = p2;
+    // conservative FP32 bounds (rounded up, then a 2^-16 margin)
+    if (thr_rc) *thr_rc = fmaxf(__double2float_ru(r2) * 1.0000153f, 1.17549435e-38f);
+    if (thr_pc) *thr_pc = fmaxf(__double2float_ru(p2) * 1.0000153f, 1.17549435e-38f);
+}
+
+__global__ void rcrit_kernel(int n, const double *pos, const double *vel, const double *mass,
+                             double m_star, double dt, double n1, double n2, double f_pc,
+                             RcritArrays out, const int *bodies, int nb, DevCounters *ctr) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const int i = bodies ? bodies[k] : k;
+    const double x = pos[i], y = pos[(size_t)n + i], z = pos[2 * (size_t)n + i];
+    const double vx = vel[i], vy = vel[(size_t)n + i], vz = vel[2 * (size_t)n + i];
+    const double r = sqrt(dist2_rn(x, y, z));
+    const double vabs = sqrt(dist2_rn(vx, vy, vz));
+    if (!(r > 0.0) || !isfinite(r) || !isfinite(vabs)) latch_error(ctr, kErrBadState);
+    const double hill = __dmul_rn(r, cbrt(__ddiv_rn(mass[i], __dmul_rn(3.0, m_star))));
+    const double a = __dmul_rn(n1, hill);
+    const double b = __dmul_rn(__dmul_rn(n2, dt), vabs);
+    const double rc = a > b ? a : b;
+    out.rc[i] = rc;
+    derive_thresholds(rc, f_pc, &out.rc2[i], out.pc2 ? &out.pc2[i] : nullptr,
+                      out.thr_rc ? &out.thr_rc[i] : nullptr, out.thr_pc ? &out.thr_pc[i] : nullptr);
+}
+
+__global__ void rcrit_derive_kernel(int n, double f_pc, RcritArrays a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    derive_thresholds(a.rc[i], f_pc, &a.rc2[i], &a.pc2[i], &a.thr_rc[i], &a.thr_pc[i]);
+}
+
+// ---------------------------------------------------------------- HC
+// P = sum_j m_j v_j in a fixed order (strided per-thread sums, then a fixed
+// tree), shift = dt_half P / m_star; then x_i += shift.
+constexpr int kHcThreads = 1024;
+
+__global__ void __launch_bounds__(kHcThreads)
+hc_reduce_kernel(int n, const double *vel, const double *mass, double m_star, double dt_half,
+                 DevCounters *ctr) {
+    __shared__ double sp[3][kHcThreads];
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    for (int j = threadIdx.x; j < n; j += kHcThreads) {
+        const double mj = mass[j];
+        p0 += mj * vel[j];
+        p1 += mj * vel[(size_t)n + j];
+        p2 += mj * vel[2 * (size_t)n + j];
+    }
+    sp[0][threadIdx.x] = p0; sp[1][threadIdx.x] = p1; sp[2][threadIdx.x] = p2;
+    __syncthreads();
+    for (int w = kHcThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sp[0][threadIdx.x] += sp[0][threadIdx.x + w];
+            sp[1][threadIdx.x] += sp[1][threadIdx.x + w];
+            sp[2][threadIdx.x] += sp[2][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) ctr->hc_shift[threadIdx.x] = dt_half * sp[threadIdx.x][0] / m_star;
+}
+
+__global__ void hc_apply_kernel(int n, double *pos, const DevCounters *ctr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pos[i] += ctr->hc_shift[0];
+    pos[(size_t)n + i] += ctr->hc_shift[1];
+    pos[2 * (size_t)n + i] += ctr->hc_shift[2];
+}
+
+// ---------------------------------------------------------------- FG
+// Stumpff functions c_k(z) = sum_m (-z)^m/(2m+k)!: quarter z until |z| <= 0.1,
+// sum the series for c2 and c3 (ten terms), c0 = 1 - z c2, c1 = 1 - z c3, then
+// undo the quartering with c0(4z) = 2c0^2 - 1, c1(4z) = c0 c1,
+// c2(4z) = c1^2/2, c3(4z) = (c2 + c0 c3)/4.
+__device__ __forceinline__ void stumpff(double z, double &c0, double &c1, double &c2, double &c3) {
+    int q = 0;
+    while (fabs(z) > 0.1 && q < 60) { z *= 0.25; q++; }
+    // 1/(2m+2)! and 1/(2m+3)!, m = 0..9
+    const double ic2[10] = {1.0 / 2.0, 1.0 / 24.0, 1.0 / 720.0, 1.0 / 40320.0, 1.0 / 3628800.0,
+                            1.0 / 479001600.0, 1.0 / 87178291200.0, 1.0 / 20922789888000.0,
+                            1.0 / 6402373705728000.0, 1.0 / 2432902008176640000.0};
+    const double ic3[10] = {1.0 / 6.0, 1.0 / 120.0, 1.0 / 5040.0, 1.0 / 362880.0,
+                            1.0 / 39916800.0, 1.0 / 6227020800.0, 1.0 / 1307674368000.0,
+                            1.0 / 355687428096000.0, 1.0 / 121645100408832000.0,
+                            1.0 / 51090942171709440000.0};
+    double s2 = 0.0, s3 = 0.0;
+#pragma unroll
+    for (int m = 9; m >= 0; m--) {
+        s2 = ic2[m] - z * s2;
+        s3 = ic3[m] - z * s3;
+    }
+    double C2 = s2, C3 = s3, C0 = 1.0 - z * C2, C1 = 1.0 - z * C3;
+    for (int k = 0; k < q; k++) {
+        const double n3 = 0.25 * (C2 + C0 * C3);
+        const double n2 = 0.5 * C1 * C1;
+        const double n1 = C0 * C1;
+        const double n0 = 2.0 * C0 * C0 - 1.0;
+        C0 = n0; C1 = n1; C2 = n2; C3 = n3;
+    }
+    c0 = C0; c1 = C1; c2 = C2; c3 = C3;
+}
+
+// Kepler drift of one body over dt about mu.  Universal variable s with
+// beta = 2 mu / r0 - v0^2, G_k = s^k c_k(beta s^2):
+//   t(s) = r0 G1 + u G2 + mu G3 (u = x0.v0),  dt/ds = r(s) = r0 G0 + u G1 + mu G2,
+//   f - 1 = -mu G2 / r0, g = dt - mu G3, fdot = -mu G1/(r r0), gdot - 1 = -mu G2 / r.
+// Newton from s = dt/r0 - u dt^2/(2 r0^3); converged when |ds| <= 1e-15 |s|, or
+// when rounding stalls the update at |ds| <= 1e-12 |s| without halving it.
+__device__ bool kepler_drift(double &x, double &y, double &z, double &vx, double &vy, double &vz,
+                             double mu, double dt, int max_iter) {
+    const double r0 = sqrt(x * x + y * y + z * z);
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double u = x * vx + y * vy + z * vz;
+    const double beta = 2.0 * mu / r0 - v2;
+    double s = dt / r0 - (u * dt * dt) / (2.0 * r0 * r0 * r0);
+    double c0, c1, c2, c3, ds_prev = 0.0;
+    bool ok = false;
+    for (int it = 0; it < max_iter; it++) {
+        stumpff(beta * s * s, c0, c1, c2, c3);
+        const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+        const double t = r0 * G1 + u * G2 + mu * G3;
+        const double rr = r0 * c0 + u * G1 + mu * G2;
+        const double ds = (t - dt) / rr;
+        s -= ds;
+        const double ads = fabs(ds), as = fabs(s);
+        if (ads <= 1e-15 * as) { ok = true; break; }
+        if (it > 0 && ads <= 1e-12 * as && ads > 0.5 * ds_prev) { ok = true; break; }
+        ds_prev = ads;
+    }
+    stumpff(beta * s * s, c0, c1, c2, c3);
+    const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+    const double r = r0 * c0 + u * G1 + mu * G2;
+    const double fm1 = -mu * G2 / r0;
+    const double g = dt - mu * G3;
+    const double fd = -mu * G1 / (r * r0);
+    const double gdm1 = -mu * G2 / r;
+    const double x0 = x, y0 = y, z0 = z, vx0 = vx, vy0 = vy, vz0 = vz;
+    x = x0 + (fm1 * x0 + g * vx0);
+    y = y0 + (fm1 * y0 + g * vy0);
+    z = z0 + (fm1 * z0 + g * vz0);
+    vx = vx0 + (fd * x0 + gdm1 * vx0);
+    vy = vy0 + (fd * y0 + gdm1 * vy0);
+    vz = vz0 + (fd * z0 + gdm1 * vz0);
+    return ok;
+}
+
+__global__ void drift_kernel(int n, double *pos, double *vel, double *pre_pos, double *pre_vel,
+                             double mu, double dt, int max_iter, const int *bodies, int nb,
+                             DevCounters *ctr) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const int i = bodies ? bodies[k] : k;
+    const size_t N = (size_t)n;
+    double x = pos[i], y = pos[N + i], z = pos[2 * N + i];
+    double vx = vel[i], vy = vel[N + i], vz = vel[2 * N + i];
+    if (pre_pos) {
+        pre_pos[i] = x; pre_pos[N + i] = y; pre_pos[2 * N + i] = z;
+        pre_vel[i] = vx; pre_vel[N + i] = vy; pre_vel[2 * N + i] = vz;
+    }
+    if (!kepler_drift(x, y, z, vx, vy, vz, mu, dt, max_iter)) {
+        latch_error(ctr, kErrKepler);
+        atomicAdd(&ctr->kepler_fail, 1ull);
+    }
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(vx) && isfinite(vy) && isfinite(vz)))
+        latch_error(ctr, kErrBadState);
+    pos[i] = x; pos[N + i] = y; pos[2 * N + i] = z;
+    vel[i] = vx; vel[N + i] = vy; vel[2 * N + i] = vz;
+}
+
+__global__ void restore_kernel(int n, double *pos, double *vel, const double *pre_pos,
+                               const double *pre_vel, const int *bodies, int nb) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const int i = bodies[k];
+    const size_t N = (size_t)n;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        pos[c * N + i] = pre_pos[c * N + i];
+        vel[c * N + i] = pre_vel[c * N + i];
+    }
+}
+
+// ---------------------------------------------------------------- energy
+// Per body: kinetic, star potential, half of the pair potential (all j != i),
+// angular momentum and momentum; then a fixed-order compensated reduction.
+constexpr int kEnThreads = 128;
+constexpr int kEnTile = 256;
+
+__global__ void __launch_bounds__(kEnThreads)
+energy_terms_kernel(int n, const double *pos, const double *vel, const double *mass, double G,
+                    double m_star, double *terms /* [8][n] */) {
+    __shared__ double sx[kEnTile], sy[kEnTile], sz[kEnTile], sm[kEnTile];
+    const int i = blockIdx.x * kEnThreads + threadIdx.x;
+    const size_t N = (size_t)n;
+    const bool valid = i < n;
+    double xi = 0, yi = 0, zi = 0;
+    if (valid) { xi = pos[i]; yi = pos[N + i]; zi = pos[2 * N + i]; }
+    double S = 0.0, C = 0.0;
+    for (int jt = 0; jt < n; jt += kEnTile) {
+        const int cnt = min(kEnTile, n - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kEnThreads) {
+            sx[k] = pos[jt + k]; sy[k] = pos[N + jt + k]; sz[k] = pos[2 * N + jt + k]; sm[k] = mass[jt + k];
+        }
+        __syncthreads();
+        double part = 0.0;
+        for (int k = 0; k < cnt; k++) {
+            if (jt + k == i) continue;
+            const double dx = sx[k] - xi, dy = sy[k] - yi, dz = sz[k] - zi;
+            part += sm[k] / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        double t, e;
+        two_sum(S, part, t, e); S = t; C += e;
+    }
+    if (!valid) return;
+    const double m = mass[i];
+    const double vx = vel[i], vy = vel[N + i], vz = vel[2 * N + i];
+    const double r = sqrt(xi * xi + yi * yi + zi * zi);
+    terms[0 * N + i] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
+    terms[1 * N + i] = -G * m_star * m / r;
+    terms[2 * N + i] = -0.5 * G * m * (S + C);
+    terms[3 * N + i] = m * (yi * vz - zi * vy);
+    terms[4 * N + i] = m * (zi * vx - xi * vz);
+    terms[5 * N + i] = m * (xi * vy - yi * vx);
+    terms[6 * N + i] = m * vx;
+    terms[7 * N + i] = m * vy;
+    terms[8 * N + i] = m * vz;
+}
+
+// One block per row: compensated fixed-order sum of terms[row][0..n).
+__global__ void row_sum_kernel(int n, const double *terms, int rows, double *out) {
+    __shared__ double ss[256], sc[256];
+    const int row = blockIdx.x;
+    const double *t = terms + (size_t)row * n;
+    double S = 0.0, C = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) {
+        double a, e;
+        two_sum(S, t[i], a, e); S = a; C += e;
+    }
+    ss[threadIdx.x] = S; sc[threadIdx.x] = C;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S2 = 0.0, C2 = 0.0;
+        for (int k = 0; k < 256; k++) {
+            double a, e;
+            two_sum(S2, ss[k], a, e); S2 = a; C2 += e + sc[k];
+        }
+        out[row] = S2 + C2;
+    }
+}
+
+// E = (kinetic + star + pairs) + |P|^2 / (2 m_star); L as summed.
+__global__ void energy_combine_kernel(double m_star, double *sums) {
+    const double P2 = sums[6] * sums[6] + sums[7] * sums[7] + sums[8] * sums[8];
+    sums[9] = ((sums[0] + sums[1]) + sums[2]) + P2 / (2.0 * m_star);
+}
+
+}  // namespace
+
+cudaError_t launch_rcrit(genga_system *s, int level, double dt, const int *bodies, int nb) {
+    if (nb <= 0) return cudaSuccess;
+    RcritArrays out = s->rcl[level];
+    if (level > 0) { out.pc2 = nullptr; out.thr_rc = nullptr; out.thr_pc = nullptr; }
+    rcrit_kernel<<<(nb + 255) / 256, 256, 0, s->stream>>>((int)s->n, s->pos, s->vel, s->mass,
+        s->p.m_star, dt, s->p.n1, s->p.n2, s->p.f_pc, out, bodies, nb, s->ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rcrit_derive(genga_system *s) {
+    const int n = (int)s->n;
+    rcrit_derive_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->p.f_pc, s->rcl[0]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hc(genga_system *s, double dt_half) {
+    const int n = (int)s->n;
+    hc_reduce_kernel<<<1, kHcThreads, 0, s->stream>>>(n, s->vel, s->mass, s->p.m_star, dt_half, s->ctr);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    hc_apply_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->pos, s->ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_drift(genga_system *s, int level, double dt, const int *bodies, int nb) {
+    if (nb <= 0) return cudaSuccess;
+    drift_kernel<<<(nb + 127) / 128, 128, 0, s->stream>>>((int)s->n, s->pos, s->vel,
+        s->pre_pos[level], s->pre_vel[level], s->p.G * s->p.m_star, dt, s->p.kepler_max_iter,
+        bodies, nb, s->ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restore(genga_system *s, int from_level, const int *bodies, int nb) {
+    if (nb <= 0) return cudaSuccess;
+    restore_kernel<<<(nb + 255) / 256, 256, 0, s->stream>>>((int)s->n, s->pos, s->vel,
+        s->pre_pos[from_level], s->pre_vel[from_level], bodies, nb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(genga_system *s, double *E_host, double *L_host) {
+    const int n = (int)s->n;
+    double *terms = s->red;            // 9 rows of n, then 10 sums
+    energy_terms_kernel<<<(n + kEnThreads - 1) / kEnThreads, kEnThreads, 0, s->stream>>>(
+        n, s->pos, s->vel, s->mass, s->p.G, s->p.m_star, terms);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    double *sums = terms + 9 * (size_t)n;
+    row_sum_kernel<<<9, 256, 0, s->stream>>>(n, terms, 9, sums);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    energy_combine_kernel<<<1, 1, 0, s->stream>>>(s->p.m_star, sums);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    double h[10];
+    GENGA_CUDA_TRY(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    GENGA_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    *E_host = h[9];
+    L_host[0] = h[3]; L_host[1] = h[4]; L_host[2] = h[5];
+    return cudaSuccess;
+}
+
+}  // namespace genga

@@ -1,0 +1,249 @@
+"""Thin Python binding of libgenga.so (include/genga.h).
+
+Argument marshalling only: torch CUDA tensors are passed by device pointer,
+host arrays by numpy pointer; every step of the integrator runs in the
+library's CUDA kernels.  There is no fallback: if the library cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GENGA_FP64 = 0
+GENGA_MIXED = 1
+
+ERRORS = {0: "OK", -1: "EINVAL", -2: "ECAPACITY", -3: "ENONCONV", -4: "ETIMEOUT",
+          -5: "EBADSTATE", -6: "ECUDA", -7: "ENOMEM"}
+
+EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last_error",
+            "genga_set_params", "genga_sync", "genga_rcrit", "genga_set_rcrit", "genga_kick",
+            "genga_hc", "genga_drift", "genga_build_encounters", "genga_bs", "genga_step",
+            "genga_step_host", "genga_energy", "genga_get_candidates", "genga_get_pairs",
+            "genga_get_groups", "genga_get_rcrit", "genga_set_predrift", "genga_get_stats"]
+
+
+class GengaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("G", C.c_double), ("m_star", C.c_double), ("dt", C.c_double),
+                ("n1", C.c_double), ("n2", C.c_double), ("f_pc", C.c_double),
+                ("bs_tol", C.c_double), ("slevels", C.c_int32), ("substeps", C.c_int32),
+                ("precision", C.c_int32), ("kepler_max_iter", C.c_int32),
+                ("bs_max_steps", C.c_int32), ("reserved", C.c_int32),
+                ("cand_capacity", C.c_int64), ("pair_capacity", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_candidates", C.c_int64), ("n_pairs", C.c_int64 * 8),
+                ("n_groups", C.c_int64), ("max_group", C.c_int64), ("bs_steps", C.c_int64),
+                ("bs_rejects", C.c_int64), ("kepler_fail", C.c_int64), ("bs_fail", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {"n_candidates": self.n_candidates, "n_pairs": list(self.n_pairs),
+                "n_groups": self.n_groups, "max_group": self.max_group,
+                "bs_steps": self.bs_steps, "bs_rejects": self.bs_rejects,
+                "kepler_fail": self.kepler_fail, "bs_fail": self.bs_fail}
+
+
+_lib = None
+_lock = threading.Lock()
+_VP = C.c_void_p
+_P = C.POINTER
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libgenga.so (building it first if needed); raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path} (run __graft_entry__.build())")
+        L = C.CDLL(path)
+        sysp = _VP
+        L.genga_default_params.argtypes = [_P(Params)]
+        L.genga_default_params.restype = None
+        L.genga_create.argtypes = [_P(_VP), _P(Params), C.c_int64, _VP, _VP, _VP, _VP]
+        L.genga_destroy.argtypes = [sysp]
+        L.genga_destroy.restype = None
+        L.genga_last_error.argtypes = [sysp]
+        L.genga_last_error.restype = C.c_char_p
+        L.genga_set_params.argtypes = [sysp, _P(Params)]
+        L.genga_sync.argtypes = [sysp]
+        L.genga_rcrit.argtypes = [sysp, C.c_double]
+        L.genga_set_rcrit.argtypes = [sysp, _VP]
+        L.genga_kick.argtypes = [sysp, C.c_double, C.c_int, _VP]
+        L.genga_hc.argtypes = [sysp, C.c_double]
+        L.genga_drift.argtypes = [sysp, C.c_double]
+        L.genga_build_encounters.argtypes = [sysp, _P(C.c_int64), _P(C.c_int64), _P(C.c_int64)]
+        L.genga_bs.argtypes = [sysp, C.c_double]
+        L.genga_step.argtypes = [sysp, C.c_int64]
+        L.genga_step_host.argtypes = [sysp, _VP, _VP, C.c_int64]
+        L.genga_energy.argtypes = [sysp, _P(C.c_double), _P(C.c_double)]
+        L.genga_get_candidates.argtypes = [sysp, _VP, C.c_int64, _P(C.c_int64)]
+        L.genga_get_pairs.argtypes = [sysp, C.c_int, _VP, C.c_int64, _P(C.c_int64)]
+        L.genga_get_groups.argtypes = [sysp, _VP]
+        L.genga_get_rcrit.argtypes = [sysp, C.c_int, _VP]
+        L.genga_set_predrift.argtypes = [sysp, _VP, _VP]
+        L.genga_get_stats.argtypes = [sysp, _P(Stats)]
+        for name in EXPORTED:
+            if name not in ("genga_default_params", "genga_destroy", "genga_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().genga_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _np_ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_VP)
+
+
+class System:
+    """One integrated system on the current CUDA device.
+
+    pos, vel: torch float64 CUDA tensors of shape (3, n) (component-major), mass:
+    (n,).  The tensors are kept referenced and updated in place.
+    """
+
+    def __init__(self, pos, vel, mass, params: Params | None = None, stream=None):
+        import torch
+        self._lib = load()
+        for t, name in ((pos, "pos"), (vel, "vel"), (mass, "mass")):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+        n = mass.shape[0]
+        if tuple(pos.shape) != (3, n) or tuple(vel.shape) != (3, n):
+            raise ValueError("pos and vel must have shape (3, n)")
+        self.pos, self.vel, self.mass = pos, vel, mass
+        self.n = int(n)
+        self.params = params if params is not None else default_params()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _VP()
+        rc = self._lib.genga_create(C.byref(h), C.byref(self.params), self.n, pos.data_ptr(),
+                                    vel.data_ptr(), mass.data_ptr(), _VP(self.stream.cuda_stream))
+        if rc != 0:
+            raise GengaError(rc, "genga_create failed")
+        self._h = h
+
+    # -- helpers
+    def _check(self, rc: int):
+        if rc != 0:
+            msg = self._lib.genga_last_error(self._h)
+            raise GengaError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.genga_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C-ABI calls
+    def set_params(self, params: Params):
+        self._check(self._lib.genga_set_params(self._h, C.byref(params)))
+        self.params = params
+
+    def sync(self):
+        self._check(self._lib.genga_sync(self._h))
+
+    def rcrit(self, dt: float):
+        self._check(self._lib.genga_rcrit(self._h, dt))
+
+    def set_rcrit(self, rc: np.ndarray):
+        rc = np.ascontiguousarray(rc, dtype=np.float64)
+        self._check(self._lib.genga_set_rcrit(self._h, _np_ptr(rc)))
+
+    def kick(self, dt_half: float, precheck: bool = False, acc_out=None):
+        ptr = None if acc_out is None else _VP(acc_out.data_ptr())
+        self._check(self._lib.genga_kick(self._h, dt_half, int(precheck), ptr))
+
+    def hc(self, dt_half: float):
+        self._check(self._lib.genga_hc(self._h, dt_half))
+
+    def drift(self, dt: float):
+        self._check(self._lib.genga_drift(self._h, dt))
+
+    def build_encounters(self):
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self._lib.genga_build_encounters(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def bs(self, dt: float):
+        self._check(self._lib.genga_bs(self._h, dt))
+
+    def step(self, nsteps: int = 1):
+        self._check(self._lib.genga_step(self._h, nsteps))
+
+    def step_host(self, pos_host: np.ndarray, vel_host: np.ndarray, nsteps: int = 1):
+        self._check(self._lib.genga_step_host(self._h, _np_ptr(pos_host), _np_ptr(vel_host), nsteps))
+
+    def step_host_ptr(self, pos_ptr: int, vel_ptr: int, nsteps: int = 1):
+        self._check(self._lib.genga_step_host(self._h, _VP(pos_ptr), _VP(vel_ptr), nsteps))
+
+    def energy(self):
+        E = C.c_double()
+        L = (C.c_double * 3)()
+        self._check(self._lib.genga_energy(self._h, C.byref(E), L))
+        return E.value, np.array(list(L))
+
+    def _pairs(self, fn, *args):
+        n = C.c_int64()
+        self._check(fn(self._h, *args, None, 0, C.byref(n)))
+        out = np.zeros((max(n.value, 1), 2), dtype=np.uint32)
+        self._check(fn(self._h, *args, _np_ptr(out), n.value, C.byref(n)))
+        return out[:n.value].copy()
+
+    def candidates(self) -> np.ndarray:
+        return self._pairs(self._lib.genga_get_candidates)
+
+    def pairs(self, level: int = 0) -> np.ndarray:
+        return self._pairs(self._lib.genga_get_pairs, level)
+
+    def groups(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int64)
+        self._check(self._lib.genga_get_groups(self._h, _np_ptr(out)))
+        return out
+
+    def get_rcrit(self, level: int = 0) -> np.ndarray:
+        out = np.zeros(self.n)
+        self._check(self._lib.genga_get_rcrit(self._h, level, _np_ptr(out)))
+        return out
+
+    def set_predrift(self, pos_soa: np.ndarray, vel_soa: np.ndarray):
+        p = np.ascontiguousarray(pos_soa, dtype=np.float64)
+        v = np.ascontiguousarray(vel_soa, dtype=np.float64)
+        self._check(self._lib.genga_set_predrift(self._h, _np_ptr(p), _np_ptr(v)))
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self._lib.genga_get_stats(self._h, C.byref(st)))
+        return st.as_dict()

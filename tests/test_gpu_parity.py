@@ -1,0 +1,307 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every input is seeded and synthetic; every expected value comes from the
+oracle on the same inputs.  Tolerances:
+  * integer/index results (candidates, encounter pairs, group labels): exact;
+  * FP64 kick: per-particle |da|/|a| <= 1e-12;
+  * mixed kick: per-particle |da|/|a| <= 1e-9 (the target stated for the mixed form);
+  * drift, HC, BS, energy: a few ulp to 1e-12 relative (see each test);
+  * whole steps: max relative position error <= 1e-12 after 100 steps at N = 2048.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import G_GAUSS, config_workload, disk, ring
+
+pytestmark = pytest.mark.gpu
+
+G = G_GAUSS
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _system(g, wl, precision=0, **kw):
+    torch = _torch()
+    dev = torch.device("cuda:0")
+    pos = torch.tensor(np.ascontiguousarray(wl.x.T), device=dev)
+    vel = torch.tensor(np.ascontiguousarray(wl.v.T), device=dev)
+    mass = torch.tensor(wl.m, device=dev)
+    p = g.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc,
+                         slevels=wl.slevels, substeps=wl.substeps, precision=precision)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return g.System(pos, vel, mass, p), pos, vel, mass
+
+
+def _host(t):
+    return t.detach().cpu().numpy().T.copy()
+
+
+@pytest.fixture(scope="module")
+def g(cuda_lib):
+    return cuda_lib
+
+
+SIZES = [("disk2048", lambda: config_workload(0)),
+         ("disk3001_ragged", lambda: disk(3001, 0.5, 2.0, 2.0, 77, name="ragged"))]
+
+
+# ---------------------------------------------------------------- Eq. rcrit
+@pytest.mark.parametrize("name,make", SIZES)
+def test_rcrit_matches_oracle(g, name, make):
+    wl = make()
+    s, *_ = _system(g, wl)
+    s.rcrit(wl.dt)
+    rc = s.get_rcrit(0)
+    ref = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    np.testing.assert_allclose(rc, ref, rtol=4e-16, atol=0)
+
+
+# ---------------------------------------------------------------- Eq. Hb kick
+def _acc(g, wl, precision, rc):
+    torch = _torch()
+    s, pos, vel, mass = _system(g, wl, precision)
+    s.set_rcrit(rc)
+    acc = torch.zeros((3, wl.n), dtype=torch.float64, device="cuda:0")
+    s.kick(0.0, precheck=False, acc_out=acc)
+    torch.cuda.synchronize()
+    return _host(acc)
+
+
+def _abs_sum(wl, rc, rows):
+    """sum_j |a_ij| for the given rows (normalisation for near-cancelling sums)."""
+    out = []
+    for i in rows:
+        d = wl.x - wl.x[i]
+        r = np.linalg.norm(d, axis=1)
+        r[i] = np.inf
+        out.append(G * (wl.m / r ** 2).sum())
+    return np.array(out)
+
+
+@pytest.mark.parametrize("name,make", SIZES)
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_kick_acceleration_matches_oracle(g, name, make, precision, tol):
+    wl = make()
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    a = _acc(g, wl, precision, rc)
+    ref = O.accel(wl.x, wl.m, rc, G, nthreads=8)
+    rel = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() <= tol, (rel.max(), np.argmax(rel))
+    # momentum balance of the GPU kick (force scaling is symmetric)
+    F = wl.m[:, None] * a
+    assert np.abs(F.sum(axis=0)).max() < 1e-11 * np.abs(F).sum(axis=0).max()
+
+
+def test_kick_applies_velocity_update(g):
+    wl = config_workload(0)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    s, pos, vel, mass = _system(g, wl, 0)
+    s.set_rcrit(rc)
+    s.kick(0.5 * wl.dt, precheck=False)
+    ref = O.kick(wl.x, wl.v, wl.m, rc, G, 0.5 * wl.dt, nthreads=8)
+    np.testing.assert_allclose(_host(vel), ref, rtol=0, atol=1e-17)
+
+
+@pytest.mark.parametrize("name,make", SIZES + [("ring64", lambda: ring(64))])
+def test_precheck_candidates_bit_exact(g, name, make):
+    wl = make()
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    s, *_ = _system(g, wl, 1)
+    s.set_rcrit(rc)
+    s.kick(0.5 * wl.dt, precheck=True)
+    cand = s.candidates()
+    ref = O.precheck(wl.x, rc, wl.f_pc)
+    assert len(ref) > 0
+    np.testing.assert_array_equal(cand, ref)
+
+
+def test_candidate_list_grows_on_overflow(g):
+    wl = config_workload(0)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    s, *_ = _system(g, wl, 1, cand_capacity=16)
+    s.set_rcrit(rc)
+    s.kick(0.5 * wl.dt, precheck=True)
+    np.testing.assert_array_equal(s.candidates(), O.precheck(wl.x, rc, wl.f_pc))
+
+
+# ---------------------------------------------------------------- Eq. Hc and Eq. Ha Kepler drift
+def test_hc_matches_oracle(g):
+    wl = config_workload(0)
+    s, pos, vel, mass = _system(g, wl)
+    s.hc(0.5 * wl.dt)
+    ref = O.hc(wl.x, wl.v, wl.m, wl.m_star, 0.5 * wl.dt)
+    np.testing.assert_allclose(_host(pos), ref, rtol=0, atol=4e-16 * np.abs(wl.x).max())
+
+
+@pytest.mark.parametrize("dt", [6.0875, 0.5, 60.0, -6.0875])
+def test_drift_matches_oracle(g, dt):
+    wl = config_workload(0)
+    s, pos, vel, mass = _system(g, wl)
+    s.drift(dt)
+    xr, vr, fails = O.drift(wl.x, wl.v, G * wl.m_star, dt)
+    assert fails == 0
+    np.testing.assert_allclose(_host(pos), xr, rtol=0, atol=2e-15)
+    np.testing.assert_allclose(_host(vel), vr, rtol=0, atol=2e-17)
+
+
+# ---------------------------------------------------------------- detection, grouping, BS
+def _encounter_setup(g, wl):
+    """Oracle states for one step's detection: pre-drift (after Kick + HC) and post-drift."""
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    v1 = O.kick(wl.x, wl.v, wl.m, rc, G, 0.5 * wl.dt, nthreads=8)
+    x1 = O.hc(wl.x, v1, wl.m, wl.m_star, 0.5 * wl.dt)
+    x2, v2, _ = O.drift(x1, v1, G * wl.m_star, wl.dt)
+    cand = O.precheck(wl.x, rc, wl.f_pc)
+    return rc, x1, v1, x2, v2, cand
+
+
+@pytest.mark.parametrize("name,make", SIZES)
+def test_detection_and_grouping_bit_exact(g, name, make):
+    torch = _torch()
+    wl = make()
+    rc, x1, v1, x2, v2, cand = _encounter_setup(g, wl)
+    s, pos, vel, mass = _system(g, wl, 0)
+    s.set_rcrit(rc)
+    s.kick(0.0, precheck=True, acc_out=torch.zeros((3, wl.n), dtype=torch.float64, device="cuda:0"))
+    s.set_predrift(x1.T, v1.T)
+    pos.copy_(torch.tensor(x2.T.copy()))
+    vel.copy_(torch.tensor(v2.T.copy()))
+    npairs, ngroups, maxg = s.build_encounters()
+    ref_pairs = O.detect(cand, x1, x2, rc)
+    assert npairs == len(ref_pairs) > 0
+    np.testing.assert_array_equal(s.pairs(0), ref_pairs)
+    lab = s.groups()
+    ref_lab = O.group(wl.n, ref_pairs)
+    np.testing.assert_array_equal(lab, ref_lab)
+    assert ngroups == len(np.unique(ref_lab[ref_lab >= 0]))
+    assert maxg == np.bincount(ref_lab[ref_lab >= 0]).max()
+
+
+@pytest.mark.parametrize("n", [16, 128, 1000])
+def test_ring_single_group(g, n):
+    torch = _torch()
+    wl = ring(n)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    s, pos, vel, mass = _system(g, wl, 0)
+    s.set_rcrit(rc)
+    s.kick(0.0, precheck=True, acc_out=torch.zeros((3, wl.n), dtype=torch.float64, device="cuda:0"))
+    s.set_predrift(wl.x.T, wl.v.T)
+    npairs, ngroups, maxg = s.build_encounters()
+    assert (npairs, ngroups, maxg) == (4 * n, 1, n)
+    assert np.all(s.groups() == 0)
+
+
+@pytest.mark.parametrize("name,make", SIZES)
+def test_bs_groups_match_oracle(g, name, make):
+    torch = _torch()
+    wl = make()
+    rc, x1, v1, x2, v2, cand = _encounter_setup(g, wl)
+    s, pos, vel, mass = _system(g, wl, 0)
+    s.set_rcrit(rc)
+    s.kick(0.0, precheck=True, acc_out=torch.zeros((3, wl.n), dtype=torch.float64, device="cuda:0"))
+    s.set_predrift(x1.T, v1.T)
+    pos.copy_(torch.tensor(x2.T.copy()))
+    vel.copy_(torch.tensor(v2.T.copy()))
+    s.build_encounters()
+    s.bs(wl.dt)
+    pairs = O.detect(cand, x1, x2, rc)
+    # oracle: BS from the pre-drift state for group members, FG for the others
+    xb, vb, st, stats = O.bs_groups(x1, v1, wl.m, rc[None], pairs, G, wl.m_star, wl.dt)
+    assert st == 0
+    members = np.unique(pairs.ravel())
+    xg, vg = _host(pos), _host(vel)
+    np.testing.assert_allclose(xg[members], xb[members], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(vg[members], vb[members], rtol=0, atol=1e-15)
+    others = np.setdiff1d(np.arange(wl.n), members)
+    np.testing.assert_array_equal(xg[others], x2[others])
+    assert s.stats()["bs_steps"] > 0
+
+
+# ---------------------------------------------------------------- whole steps (Appendix A)
+def _rel_pos_err(xg, xr):
+    return np.linalg.norm(xg - xr, axis=1) / np.linalg.norm(xr, axis=1)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_steps_match_oracle_config0(g, precision):
+    """N = 2048 disk, 100 steps: max relative position error <= 1e-12 (FP64);
+    the mixed kick is compared against the FP64 oracle at 1e-9."""
+    wl = config_workload(0)
+    s, pos, vel, mass = _system(g, wl, precision)
+    s.step(100)
+    st = s.stats()
+    xr, vr, status, ost = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=8), 100)
+    assert status == 0
+    err = _rel_pos_err(_host(pos), xr)
+    print(f"precision={precision} max={err.max():.3e} p99.9={np.quantile(err, 0.999):.3e} "
+          f"gpu_pairs={st['n_pairs'][0]} oracle_pairs={ost['n_pairs'][0]}")
+    assert st["n_pairs"][0] > 0 and st["n_groups"] > 0
+    tol = 1e-12 if precision == 0 else 1e-9
+    assert err.max() <= tol
+
+
+def test_levels_step_matches_oracle(g):
+    """Two symplectic levels with 10 sub-steps (Sec. 4.3) on a dense disk."""
+    wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=2, substeps=10)
+    s, pos, vel, mass = _system(g, wl, 0)
+    s.step(5)
+    st = s.stats()
+    xr, vr, status, ost = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=8), 5)
+    assert status == 0
+    assert st["n_pairs"][0] == ost["n_pairs"][0] > 0
+    assert st["n_pairs"][1] > 0
+    err = _rel_pos_err(_host(pos), xr)
+    assert err.max() <= 1e-12, err.max()
+
+
+def test_energy_matches_oracle(g):
+    wl = config_workload(0)
+    s, *_ = _system(g, wl)
+    E, L = s.energy()
+    Er, Lr = O.energy(wl.x, wl.v, wl.m, wl.m_star, G)
+    assert abs(E - Er) <= 1e-13 * abs(Er)
+    np.testing.assert_allclose(L, Lr, rtol=1e-13)
+
+
+def test_step_host_buffers(g):
+    wl = config_workload(0, n_override=256)
+    s, pos, vel, mass = _system(g, wl, 0)
+    xh = np.ascontiguousarray(wl.x.T)
+    vh = np.ascontiguousarray(wl.v.T)
+    s.step_host(xh, vh, 3)
+    xr, vr, status, _ = O.step(wl.x, wl.v, wl.m, O.make_params(wl), 3)
+    np.testing.assert_allclose(xh.T, xr, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- failure paths (host-visible status)
+def test_kepler_iteration_limit_reports_nonconvergence(g):
+    wl = config_workload(0, n_override=256)
+    s, *_ = _system(g, wl, 0, kepler_max_iter=1)
+    with pytest.raises(g.GengaError) as e:
+        s.step(1)
+    assert e.value.code == -3
+
+
+def test_bs_step_limit_reports_nonconvergence(g):
+    wl = config_workload(0)
+    s, *_ = _system(g, wl, 0, bs_max_steps=1)
+    with pytest.raises(g.GengaError) as e:
+        s.step(1)
+    assert e.value.code == -3
+    # the context stays usable: a fresh system on the same device works
+    s2, *_ = _system(g, config_workload(0, n_override=64), 0)
+    s2.step(1)
+
+
+def test_nan_state_reports_bad_state(g):
+    wl = config_workload(0, n_override=256)
+    wl.x[3, 0] = np.nan
+    s, *_ = _system(g, wl, 0)
+    with pytest.raises(g.GengaError) as e:
+        s.step(1)
+    assert e.value.code == -5
