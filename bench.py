@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark: changeover-kick pair-interactions/s and steps/s of the hybrid
+symplectic step (Appendix A with the two-level changeover of Sec. 4.3) on the
+large planetesimal disk: N = 65,536 equal-mass planetesimals (0.5-4 AU, 5 Earth
+masses, Sigma ~ a^-1.5) plus 4 embryos of 0.1 Earth masses, dt = 6.0875 d,
+2 symplectic levels x 10 sub-steps, FP64 and mixed-precision kick.
+
+One step = genga_step(1): Rcrit, Kick + pre-check, HC, FG, detection, SEnc
+(RcritS, KickS, FGS, detection, grouping, Bulirsch-Stoer per sub-step), HC,
+Kick.  The headline value counts the two all-pairs kick evaluations of a step,
+2 N (N - 1) pair interactions, divided by the measured whole-step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank integrates its own replica of the disk
+(the path has no exchange step: replicas only); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("changeover-kick G pair-interactions/s and steps/s at N=65536 (FP64 vs mixed), "
+          "% of peak")
+UNIT = "Gpair/s"
+# FP64 instructions per pair interaction that each kick form's algorithm needs
+# (FMA counted as one): displacement 3, r^2 3, r^-1 (mixed: one Newton
+# correction of an FP32 seed, 3; FP64: two Newton steps from a ~2^-22 seed, 6),
+# m r^-3 3, accumulation 3.
+FP64_OPS_PER_PAIR = {"mixed": 15, "fp64": 18}
+FP64_OPS_PER_CLK_PER_SM = 2      # measured DFMA throughput per SM per clock on GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=65536, help="planetesimals (embryos: 4 more)")
+    ap.add_argument("--kick-reps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip e2e/cpu/fp64 legs (profiling runs)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+class Dist:
+    def __init__(self, ngpus: int):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(self.local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{self.local}")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and parts[1] != self.uuid:
+                    continue
+                rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k] == "Active"})
+        # only samples under load (clock above 60% of max) enter the median
+        loaded = [v for v in sm if v > 0.6 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def gpu_uuid(dev_index: int) -> str | None:
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(dev_index).uuid
+        return "GPU-" + str(u)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, dist: Dist) -> dict | None:
+    import torch
+
+    from paper_2201_10058_gb300 import genga
+    from workloads import disk
+    from workloads.disk import SEED_BASE
+
+    dev = torch.device("cuda", dist.local)
+    torch.cuda.set_device(dev)
+    genga.load()
+    wl = disk(args.n, 0.5, 4.0, 5.0, SEED_BASE + 2, n_embryos=4, m_embryo_earth=0.1,
+              slevels=2, substeps=10, name=f"disk{args.n}+4emb")
+    n = wl.n
+    pairs_per_step = 2.0 * n * (n - 1)
+    x0 = torch.tensor(np.ascontiguousarray(wl.x.T), device=dev)
+    v0 = torch.tensor(np.ascontiguousarray(wl.v.T), device=dev)
+    mass = torch.tensor(wl.m, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def params(prec):
+        return genga.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2,
+                                    f_pc=wl.f_pc, slevels=wl.slevels, substeps=wl.substeps,
+                                    precision=prec)
+
+    results = {}
+    clocks = None
+    launches = 0
+    precisions = ["mixed"] if args.quick else ["fp64", "mixed"]
+    for name in precisions:
+        prec = genga.GENGA_MIXED if name == "mixed" else genga.GENGA_FP64
+        pos, vel = x0.clone(), v0.clone()
+        sysm = genga.System(pos, vel, mass, params(prec), stream=stream)
+        for _ in range(args.warmup):
+            sysm.step(1)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(gpu_uuid(dist.local)) if name == "mixed" else None
+        if sampler:
+            sampler.start()
+        dist.barrier()
+        torch.cuda.synchronize()
+        total_ms = 0.0
+        nl = 0
+        for _ in range(args.steps):
+            flush.fill_(1.0)                      # L2 flush between timed steps (untimed)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sysm.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            nl += sysm.stats()["kernel_launches"]
+        torch.cuda.synchronize()
+        dist.barrier()
+        stats = sysm.stats()
+        # kick kernel alone (the dominant kernel), same launch configuration
+        sysm.rcrit(wl.dt)
+        sysm.kick(0.0, precheck=False)
+        torch.cuda.synchronize()
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(args.kick_reps):
+            sysm.kick(0.0, precheck=False)
+        k1.record(stream)
+        k1.synchronize()
+        kick_ms = k0.elapsed_time(k1) / args.kick_reps
+        if sampler:
+            clocks = sampler.stop()
+        t_max = dist.max(total_ms)
+        results[name] = {
+            "ms_per_step": t_max / args.steps,
+            "gpairs_per_s": dist.world * pairs_per_step * args.steps / (t_max * 1e-3) / 1e9,
+            "steps_per_s": dist.world * args.steps / (t_max * 1e-3),
+            "kick_ms": kick_ms,
+            "kick_gpairs_per_s": n * (n - 1) / (kick_ms * 1e-3) / 1e9,
+            "kick_share": 2 * kick_ms / (total_ms / args.steps),
+            "encounters": {"candidates_per_step": stats["n_candidates"],
+                           "pairs_level0": stats["n_pairs"][0],
+                           "pairs_level1": stats["n_pairs"][1],
+                           "groups": stats["n_groups"], "max_group": stats["max_group"]},
+        }
+        if name == "mixed":
+            launches = nl
+        sysm.close()
+
+    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.quick:
+        pos, vel = x0.clone(), v0.clone()
+        sysm = genga.System(pos, vel, mass, params(genga.GENGA_MIXED), stream=stream)
+        xh = torch.empty((3, n), dtype=torch.float64).pin_memory()
+        vh = torch.empty((3, n), dtype=torch.float64).pin_memory()
+        xh.copy_(x0.cpu())
+        vh.copy_(v0.cpu())
+        sysm.step_host_ptr(xh.data_ptr(), vh.data_ptr(), 1)    # warm-up
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sysm.step_host_ptr(xh.data_ptr(), vh.data_ptr(), 1)
+        t1 = time.perf_counter()
+        dist.barrier()
+        te = dist.max(t1 - t0)
+        bytes_each = 2 * 3 * n * 8
+        e2e = {"value": dist.world * pairs_per_step * args.steps / te / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": bytes_each, "d2h_bytes_per_step": bytes_each}
+        sysm.close()
+
+    if dist.rank != 0:
+        return None
+
+    head = results["mixed"]
+    sm_clock = (clocks or {}).get("sm_mhz") or 2070.0
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak = FP64_OPS_PER_CLK_PER_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
+    achieved = FP64_OPS_PER_PAIR["mixed"] * head["kick_gpairs_per_s"]
+    line = {
+        "metric": METRIC, "value": round(head["gpairs_per_s"], 4), "unit": UNIT,
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded planetesimal disk, no external data)",
+        "config": {"workload": f"disk N={n} (65536 planetesimals 0.5-4 AU, 5 M_earth, "
+                               f"+4 embryos 0.1 M_earth), dt=6.0875 d, 2 levels x 10 substeps, "
+                               f"mixed-precision kick",
+                   "n_bodies": n, "slevels": 2, "substeps": 10, "kick": "mixed",
+                   "pairs_per_step": pairs_per_step,
+                   "l2": "flushed between timed steps (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{dist.world}"},
+        "steps_per_s": round(head["steps_per_s"], 4),
+        "kick_only": {"mixed_gpairs_per_s": round(head["kick_gpairs_per_s"], 3),
+                      "mixed_kick_ms": round(head["kick_ms"], 3),
+                      "kick_share_of_step": round(head["kick_share"], 3)},
+        "roofline": {"bound": "alu", "kernel": "kick_kernel<mixed> (all-pairs changeover kick)",
+                     "achieved": round(achieved, 2), "peak": round(peak, 2),
+                     "unit": "G FP64-op/s (FMA = 1; FP64 pipe)",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "ops_per_pair": FP64_OPS_PER_PAIR["mixed"],
+                     "peak_basis": f"derived: {FP64_OPS_PER_CLK_PER_SM} FP64 op/clk/SM (measured) x "
+                                   f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz"},
+        "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+        "encounters": head["encounters"],
+    }
+    if "fp64" in results:
+        f = results["fp64"]
+        line["fp64"] = {"value": round(f["gpairs_per_s"], 4), "unit": UNIT,
+                        "ms_per_step": round(f["ms_per_step"], 3),
+                        "steps_per_s": round(f["steps_per_s"], 4),
+                        "kick_gpairs_per_s": round(f["kick_gpairs_per_s"], 3),
+                        "kick_ms": round(f["kick_ms"], 3),
+                        "roofline_frac": round(FP64_OPS_PER_PAIR["fp64"] * f["kick_gpairs_per_s"] / peak, 4)}
+        line["mixed_over_fp64"] = round(head["gpairs_per_s"] / f["gpairs_per_s"], 3)
+    if not args.no_cpu_baseline and not args.quick and dist.world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    return line
+
+
+# ---------------------------------------------------------------- oracle legs
+def _oracle_step_sample(wl, nthreads: int) -> tuple[float, dict]:
+    import oracle as O
+    p = O.make_params(wl, nthreads=nthreads)
+    t0 = time.perf_counter()
+    _, _, status, st = O.step(wl.x, wl.v, wl.m, p, 1)
+    return time.perf_counter() - t0, st
+
+
+def cpu_baseline(wl) -> dict:
+    """The oracle as it stands: one full step of the same workload on all host cores."""
+    cores = os.cpu_count() or 1
+    dt, st = _oracle_step_sample(wl, cores)
+    n = wl.n
+    return {"value": round(2.0 * n * (n - 1) / dt / 1e9, 5), "unit": UNIT, "cores": cores,
+            "kind": "oracle", "sample": f"1 full step (Appendix A, 2 levels x 10 substeps) of the "
+                                        f"N={n} disk; {dt:.1f} s wall on {cores} threads",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args, dist: Dist) -> dict | None:
+    """Reference arm: the FP64 CPU oracle, timed on the host cores on the same
+    workload, metric and unit; each timed step is one full oracle step."""
+    if dist.rank != 0:
+        return None
+    from workloads import disk
+    from workloads.disk import SEED_BASE
+    wl = disk(args.n, 0.5, 4.0, 5.0, SEED_BASE + 2, n_embryos=4, m_embryo_earth=0.1,
+              slevels=2, substeps=10, name=f"disk{args.n}+4emb")
+    import oracle as O
+    cores = os.cpu_count() or 1
+    # untimed warm-up: build and load the oracle, touch the data
+    O.lib()
+    O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt)
+    total = 0.0
+    for _ in range(args.steps):
+        dt, st = _oracle_step_sample(wl, cores)
+        total += dt
+    n = wl.n
+    value = 2.0 * n * (n - 1) * args.steps / total / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded planetesimal disk)",
+            "config": {"workload": f"disk N={n} (65536 planetesimals 0.5-4 AU, 5 M_earth, "
+                                   f"+4 embryos 0.1 M_earth), dt=6.0875 d, 2 levels x 10 substeps",
+                       "n_bodies": n},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full oracle steps of the N={n} disk from the "
+                                       f"initial state, {cores} threads"},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    dist = Dist(args.gpus)
+    try:
+        line = run_reference(args, dist) if args.impl == "reference" else run_ours(args, dist)
+        if line is not None and dist.rank == 0:
+            print(json.dumps(line))
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -254,7 +254,7 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_group
     A.max_steps = s->p.bs_max_steps;
     A.time_limit_ns = 10000000000ull;   // 10 s per group call
     A.ctr = s->ctr;
-    bs_kernel<<<(unsigned)max_groups, kBsThreads, 0, s->stream>>>(A);
+    bs_kernel<<<(unsigned)max_groups, kBsThreads, 0, s->stream>>>(A); ++s->launches;
     return cudaGetLastError();
 }
 
@@ -267,7 +267,7 @@ cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb
     A.pos = s->pos; A.vel = s->vel; A.mass = s->mass;
     for (int l = 0; l < kMaxLevels; l++) A.rc[l] = s->rcl[l].rc;
     A.G = s->p.G; A.dt_half = dt_half;
-    kick_pairs_kernel<<<(nb + 127) / 128, 128, 0, s->stream>>>(A);
+    kick_pairs_kernel<<<(nb + 127) / 128, 128, 0, s->stream>>>(A); ++s->launches;
     return cudaGetLastError();
 }
 

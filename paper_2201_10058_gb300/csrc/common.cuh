@@ -116,6 +116,7 @@ struct genga_system {
 
     genga::Scratch scr;
     genga_stats_t stats;
+    int64_t launches = 0;          // kernels launched by this system (host-side count)
     char err[512] = {0};
 };
 

@@ -226,13 +226,13 @@ cudaError_t exclusive_scan(genga_system *s, const int *in, int *out, int64_t len
     const int nblocks = (int)((len + kScanBlock - 1) / kScanBlock);
     if (nblocks > s->scr.scan_blocks_cap) return cudaErrorInvalidValue;
     if (len > 0) {
-        scan_blocks_kernel<<<nblocks, kScanThreads, 0, s->stream>>>(in, out, len, s->scr.scan_blocks);
+        scan_blocks_kernel<<<nblocks, kScanThreads, 0, s->stream>>>(in, out, len, s->scr.scan_blocks); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
-    scan_sums_kernel<<<1, kScanThreads, 0, s->stream>>>(s->scr.scan_blocks, nblocks, out + len);
+    scan_sums_kernel<<<1, kScanThreads, 0, s->stream>>>(s->scr.scan_blocks, nblocks, out + len); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     if (len > 0) {
-        scan_add_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s->stream>>>(out, len, s->scr.scan_blocks);
+        scan_add_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s->stream>>>(out, len, s->scr.scan_blocks); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -243,7 +243,7 @@ cudaError_t launch_detect(genga_system *s, const uint2 *in, int64_t nin, int lev
     GENGA_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s->stream));
     if (nin <= 0) return cudaSuccess;
     detect_kernel<<<(unsigned)((nin + 255) / 256), 256, 0, s->stream>>>(in, nullptr, nin, (int)s->n,
-        s->pre_pos[level], s->pos, s->rcl[level].rc2, out, (unsigned long long)cap, count);
+        s->pre_pos[level], s->pos, s->rcl[level].rc2, out, (unsigned long long)cap, count); ++s->launches;
     return cudaGetLastError();
 }
 
@@ -253,14 +253,14 @@ cudaError_t build_csr(genga_system *s, int level, int64_t np) {
     GENGA_CUDA_TRY(cudaMemsetAsync(c.deg, 0, sizeof(int) * (n + 1), s->stream));
     GENGA_CUDA_TRY(cudaMemsetAsync(c.fill, 0, sizeof(int) * n, s->stream));
     if (np > 0) {
-        csr_degree_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.deg);
+        csr_degree_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.deg); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     GENGA_CUDA_TRY(exclusive_scan(s, c.deg, c.off, n));
     if (np > 0) {
-        csr_fill_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.off, c.fill, c.list);
+        csr_fill_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.off, c.fill, c.list); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
-        csr_sort_kernel<<<(n + 127) / 128, 128, 0, s->stream>>>(n, c.off, c.list);
+        csr_sort_kernel<<<(n + 127) / 128, 128, 0, s->stream>>>(n, c.off, c.list); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -271,10 +271,10 @@ cudaError_t build_csr(genga_system *s, int level, int64_t np) {
 cudaError_t build_bodies(genga_system *s, int level_pairs, int out_level, int *nb_host) {
     const int n = (int)s->n;
     int *pos = s->gfill;   // temporary n+1 ints
-    flag_nonzero_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->csr[level_pairs].deg, s->flags);
+    flag_nonzero_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->csr[level_pairs].deg, s->flags); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     GENGA_CUDA_TRY(exclusive_scan(s, s->flags, pos, n));
-    compact_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->flags, pos, s->bodies[out_level]);
+    compact_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->flags, pos, s->bodies[out_level]); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     GENGA_CUDA_TRY(cudaMemcpyAsync(nb_host, pos + n, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     return cudaStreamSynchronize(s->stream);
@@ -286,24 +286,24 @@ cudaError_t build_groups(genga_system *s, int level, int64_t np) {
     GENGA_CUDA_TRY(cudaMemsetAsync(s->gsize, 0, sizeof(int) * (n + 1), s->stream));
     GENGA_CUDA_TRY(cudaMemsetAsync(s->gfill, 0, sizeof(int) * (n + 1), s->stream));
     GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->ngroups, 0, 2 * sizeof(unsigned), s->stream));
-    uf_init_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->parent);
+    uf_init_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->parent); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     if (np > 0) {
-        uf_hook_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, s->parent, s->ctr);
+        uf_hook_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, s->parent, s->ctr); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
-    uf_label_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->parent, s->csr[level].deg, s->label, s->gsize);
+    uf_label_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->parent, s->csr[level].deg, s->label, s->gsize); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     GENGA_CUDA_TRY(exclusive_scan(s, s->gsize, s->goff, n));
     // group list: labels with a non-empty group, ascending
-    flag_nonzero_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->gsize, s->flags);
+    flag_nonzero_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->gsize, s->flags); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     int *pos = s->member;   // temporary, rewritten below
     GENGA_CUDA_TRY(exclusive_scan(s, s->flags, pos, n));
-    compact_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->flags, pos, s->glist);
+    compact_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->flags, pos, s->glist); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     group_members_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->label, s->goff, s->gfill,
-                                                                 s->member, s->slotof, s->ctr);
+                                                                 s->member, s->slotof, s->ctr); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     s->label_level = level;
     return cudaSuccess;

@@ -274,11 +274,13 @@ int collect_stats(genga_system *s) {
     s->stats.bs_rejects = (int64_t)c.bs_rejects;
     s->stats.bs_fail = (int64_t)c.bs_fail;
     s->stats.kepler_fail = (int64_t)c.kepler_fail;
+    s->stats.kernel_launches = s->launches;
     return GENGA_OK;
 }
 
 int reset_stats(genga_system *s) {
     memset(&s->stats, 0, sizeof(s->stats));
+    s->launches = 0;
     CU(cudaMemsetAsync(&s->ctr->kepler_fail, 0, 6 * sizeof(unsigned long long), s->stream));
     return GENGA_OK;
 }

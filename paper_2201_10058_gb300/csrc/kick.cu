@@ -232,9 +232,10 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
     else if (mixed) kick_kernel<true, false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
     else if (precheck) kick_kernel<false, true, true><<<grid, kKickThreads, 0, s->stream>>>(A);
     else kick_kernel<false, false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     kick_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(s->kick_part, s->kick_nchunk, n, s->p.G,
-                                                          dt_half, s->vel, acc_out);
+                                                          dt_half, s->vel, acc_out); ++s->launches;
     return cudaGetLastError();
 }
 
@@ -244,7 +245,7 @@ cudaError_t launch_precheck_only(genga_system *s) {
     KickArgs A = make_args(s, true);
     dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
     GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->cand_count, 0, sizeof(unsigned long long), s->stream));
-    kick_kernel<true, true, false><<<grid, kKickThreads, 0, s->stream>>>(A);
+    kick_kernel<true, true, false><<<grid, kKickThreads, 0, s->stream>>>(A); ++s->launches;
     return cudaGetLastError();
 }
 

@@ -286,21 +286,21 @@ cudaError_t launch_rcrit(genga_system *s, int level, double dt, const int *bodie
     RcritArrays out = s->rcl[level];
     if (level > 0) { out.pc2 = nullptr; out.thr_rc = nullptr; out.thr_pc = nullptr; }
     rcrit_kernel<<<(nb + 255) / 256, 256, 0, s->stream>>>((int)s->n, s->pos, s->vel, s->mass,
-        s->p.m_star, dt, s->p.n1, s->p.n2, s->p.f_pc, out, bodies, nb, s->ctr);
+        s->p.m_star, dt, s->p.n1, s->p.n2, s->p.f_pc, out, bodies, nb, s->ctr); ++s->launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_rcrit_derive(genga_system *s) {
     const int n = (int)s->n;
-    rcrit_derive_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->p.f_pc, s->rcl[0]);
+    rcrit_derive_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->p.f_pc, s->rcl[0]); ++s->launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_hc(genga_system *s, double dt_half) {
     const int n = (int)s->n;
-    hc_reduce_kernel<<<1, kHcThreads, 0, s->stream>>>(n, s->vel, s->mass, s->p.m_star, dt_half, s->ctr);
+    hc_reduce_kernel<<<1, kHcThreads, 0, s->stream>>>(n, s->vel, s->mass, s->p.m_star, dt_half, s->ctr); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    hc_apply_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->pos, s->ctr);
+    hc_apply_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->pos, s->ctr); ++s->launches;
     return cudaGetLastError();
 }
 
@@ -308,14 +308,14 @@ cudaError_t launch_drift(genga_system *s, int level, double dt, const int *bodie
     if (nb <= 0) return cudaSuccess;
     drift_kernel<<<(nb + 127) / 128, 128, 0, s->stream>>>((int)s->n, s->pos, s->vel,
         s->pre_pos[level], s->pre_vel[level], s->p.G * s->p.m_star, dt, s->p.kepler_max_iter,
-        bodies, nb, s->ctr);
+        bodies, nb, s->ctr); ++s->launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_restore(genga_system *s, int from_level, const int *bodies, int nb) {
     if (nb <= 0) return cudaSuccess;
     restore_kernel<<<(nb + 255) / 256, 256, 0, s->stream>>>((int)s->n, s->pos, s->vel,
-        s->pre_pos[from_level], s->pre_vel[from_level], bodies, nb);
+        s->pre_pos[from_level], s->pre_vel[from_level], bodies, nb); ++s->launches;
     return cudaGetLastError();
 }
 
@@ -323,12 +323,12 @@ cudaError_t launch_energy(genga_system *s, double *E_host, double *L_host) {
     const int n = (int)s->n;
     double *terms = s->red;            // 9 rows of n, then 10 sums
     energy_terms_kernel<<<(n + kEnThreads - 1) / kEnThreads, kEnThreads, 0, s->stream>>>(
-        n, s->pos, s->vel, s->mass, s->p.G, s->p.m_star, terms);
+        n, s->pos, s->vel, s->mass, s->p.G, s->p.m_star, terms); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     double *sums = terms + 9 * (size_t)n;
-    row_sum_kernel<<<9, 256, 0, s->stream>>>(n, terms, 9, sums);
+    row_sum_kernel<<<9, 256, 0, s->stream>>>(n, terms, 9, sums); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    energy_combine_kernel<<<1, 1, 0, s->stream>>>(s->p.m_star, sums);
+    energy_combine_kernel<<<1, 1, 0, s->stream>>>(s->p.m_star, sums); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     double h[10];
     GENGA_CUDA_TRY(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
