@@ -6,7 +6,9 @@ oracle on the same inputs.  Tolerances:
   * FP64 kick: per-particle |da|/|a| <= 1e-12;
   * mixed kick: per-particle |da|/|a| <= 1e-9 (the target stated for the mixed form);
   * drift, HC, BS, energy: a few ulp to 1e-12 relative (see each test);
-  * whole steps: max relative position error <= 1e-12 after 100 steps at N = 2048.
+  * whole steps: max relative position error <= 1e-12 after 10 steps at N = 2048 and
+    in the encounter-free control after 100 steps; with encounters, 100 steps agree
+    to within 3x the oracle's own spread under a one-ulp input perturbation.
 """
 import numpy as np
 import pytest
@@ -147,8 +149,8 @@ def test_drift_matches_oracle(g, dt):
     assert fails == 0
     # the universal-variable solve's rounding grows with the anomaly swept (|dt|)
     scale = max(1.0, abs(dt) / 6.0875)
-    np.testing.assert_allclose(_host(pos), xr, rtol=0, atol=5e-15 * scale)
-    np.testing.assert_allclose(_host(vel), vr, rtol=0, atol=5e-17 * scale)
+    np.testing.assert_allclose(_host(pos), xr, rtol=0, atol=5e-15 * scale * np.abs(xr).max())
+    np.testing.assert_allclose(_host(vel), vr, rtol=0, atol=5e-15 * scale * np.abs(vr).max())
 
 
 # ---------------------------------------------------------------- detection, grouping, BS
