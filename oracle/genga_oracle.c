@@ -72,6 +72,7 @@ typedef struct orc_stats {
     int64_t bs_rejects;      /* rejected BS attempts (step halvings) */
     int64_t kepler_fail;     /* Kepler solves that hit the iteration limit */
     int64_t bs_fail;         /* groups that hit bs_max_steps */
+    int64_t bs_max_attempts; /* most step attempts any one group needed */
 } orc_stats;
 
 #define ORC_MAX_LEVELS 8
@@ -429,7 +430,7 @@ static void bs_midpoint(const bs_group *g, const double *y0, const double *f0, d
 
 /* Integrates y (6 nm values) over dt.  Returns 0, or 1 on hitting max_steps. */
 static int bs_integrate(const bs_group *g, double *y, double dt, double tol, int max_steps,
-                        int64_t *n_acc, int64_t *n_rej)
+                        int64_t *n_acc, int64_t *n_rej, int64_t *max_att)
 {
     int64_t d = 6 * g->nm;
     double *f0 = (double *)malloc(sizeof(double) * (size_t)d);
@@ -482,6 +483,7 @@ static int bs_integrate(const bs_group *g, double *y, double dt, double tol, int
             H *= 0.5;
         }
     }
+    if (attempts > *max_att) *max_att = attempts;
     free(f0); free(T); free(yk); free(zm); free(zn); free(fz); free(sc);
     return status;
 }
@@ -563,7 +565,7 @@ static void bs_all_groups(step_ctx *cx, int64_t npairs, const uint32_t *pairs, i
         g.rcl = (const double *const *)cx->rcl; g.nlev = level + 1;
         g.G = cx->p->G; g.mu = cx->p->G * cx->p->m_star;
         int fail = bs_integrate(&g, y, dt_l, cx->p->bs_tol, cx->p->bs_max_steps,
-                                &cx->st->bs_steps, &cx->st->bs_rejects);
+                                &cx->st->bs_steps, &cx->st->bs_rejects, &cx->st->bs_max_attempts);
         if (fail) { cx->st->bs_fail++; cx->status |= 2; }
         for (int64_t a = 0; a < nm; a++)
             for (int k = 0; k < 3; k++) {

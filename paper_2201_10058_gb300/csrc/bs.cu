@@ -100,6 +100,7 @@ bs_kernel(BsArgs A) {
     const unsigned long long t_start = global_ns();
     const int g = A.glist[blockIdx.x];
     const int s0 = A.goff[g], s1 = A.goff[g + 1];
+    if (s1 - s0 <= 32) return;                           // bs_warp_kernel's groups
     const size_t N = (size_t)A.n;
 
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
@@ -200,40 +201,239 @@ bs_kernel(BsArgs A) {
     }
 }
 
-// KickS at level l >= 1 over the partner lists of the level-(l-1) pairs:
+// KickS at level l >= 1 over the level-(l-1) encounter pairs:
 //   v_b += dt_half G sum_p m_p prod_{k<l}(1 - K_k) K_l (x_p - x_b)/r^3.
+// Phase 1, one thread per undirected pair (i < j): g (x_j - x_i) with
+// g = prod_{k<l}(1 - K_k) K_l / r^3 (0 when the pair is beyond rc_0, where
+// 1 - K_0 = 0).  Phase 2, one thread per level body: the pair terms of its
+// partners, ascending partner index, times +-m_p -- a fixed summation order.
 struct KickPairsArgs {
     int n, nb, level;
+    long long np;
+    const uint2 *pairs;
     const int *bodies;
-    const int *off, *list;
+    const int *off, *list, *lpair;
+    double *term;          // [3][np]
     const double *pos;
     double *vel;
     const double *mass;
     const double *rc[kMaxLevels];
+    const double *rc2_0;
     double G, dt_half;
 };
 
-__global__ void kick_pairs_kernel(KickPairsArgs A) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= A.nb) return;
-    const int b = A.bodies[k];
+__global__ void kick_pairs_terms_kernel(KickPairsArgs A) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.np) return;
+    const uint2 pr = A.pairs[k];
+    const int i = (int)pr.x, j = (int)pr.y;
     const size_t N = (size_t)A.n;
-    const double x = A.pos[b], y = A.pos[N + b], z = A.pos[2 * N + b];
+    const size_t NP = (size_t)A.np;
+    const double dx = A.pos[j] - A.pos[i], dy = A.pos[N + j] - A.pos[N + i],
+                 dz = A.pos[2 * N + j] - A.pos[2 * N + i];
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    double g = 0.0;
+    // beyond (1 + 1e-13) rc_0 the factor 1 - K_0 is exactly zero
+    if (r2 < 1.0000000000001 * fmax(A.rc2_0[i], A.rc2_0[j])) {
+        const double yv = rsqrt_newton(r2);
+        const double r = r2 * yv;
+        double W = 1.0;
+        for (int l = 0; l < A.level; l++)
+            W *= 1.0 - changeover_fast(r, 1.0 / fmax(A.rc[l][i], A.rc[l][j]));
+        W *= changeover_fast(r, 1.0 / fmax(A.rc[A.level][i], A.rc[A.level][j]));
+        g = W * yv * yv * yv;
+    }
+    A.term[k] = g * dx;
+    A.term[NP + k] = g * dy;
+    A.term[2 * NP + k] = g * dz;
+}
+
+__global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.nb) return;
+    const int b = A.bodies[t];
+    const size_t N = (size_t)A.n;
+    const size_t NP = (size_t)A.np;
     double sx = 0.0, sy = 0.0, sz = 0.0;
     for (int q = A.off[b]; q < A.off[b + 1]; q++) {
         const int p = A.list[q];
-        const double dx = A.pos[p] - x, dy = A.pos[N + p] - y, dz = A.pos[2 * N + p] - z;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        const double r = sqrt(r2);
-        double W = 1.0;
-        for (int l = 0; l < A.level; l++) W *= 1.0 - changeover(r, fmax(A.rc[l][b], A.rc[l][p]));
-        W *= changeover(r, fmax(A.rc[A.level][b], A.rc[A.level][p]));
-        const double f = A.mass[p] * W / (r2 * r);
-        sx += f * dx; sy += f * dy; sz += f * dz;
+        const int k = A.lpair[q];
+        const double w = (p > b) ? A.mass[p] : -A.mass[p];
+        sx = fma(w, A.term[k], sx);
+        sy = fma(w, A.term[NP + k], sy);
+        sz = fma(w, A.term[2 * NP + k], sz);
     }
     A.vel[b] += A.dt_half * (A.G * sx);
     A.vel[N + b] += A.dt_half * (A.G * sy);
     A.vel[2 * N + b] += A.dt_half * (A.G * sz);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-per-group Bulirsch-Stoer for groups of at most 32 members: lane = member
+// (ranked by ascending body index), state and midpoint vectors in registers,
+// positions exchanged through a per-warp shared-memory slice, the Neville
+// table in shared memory, only __syncwarp.  Same integrator and step control
+// as bs_kernel.
+constexpr int kWarpBsWarps = 2;
+
+struct WarpBsShared {
+    double zx[32], zy[32], zz[32];
+    double m[32];
+    double irc[kMaxLevels][32];
+    double T[kBsCols * 6][32];
+    int rank_of_slot[32];
+};
+
+__device__ __forceinline__ void warp_deriv(const BsArgs &A, WarpBsShared &S, int lane, bool active,
+                                           unsigned mask, const double *irc_self, const double z[6],
+                                           double f[6]) {
+    __syncwarp();
+    S.zx[lane] = z[0]; S.zy[lane] = z[1]; S.zz[lane] = z[2];
+    __syncwarp();
+    f[0] = z[3]; f[1] = z[4]; f[2] = z[5];
+    if (!active) { f[3] = f[4] = f[5] = 0.0; return; }
+    const double r2s = fma(z[2], z[2], fma(z[1], z[1], z[0] * z[0]));
+    const double ys = rsqrt_newton(r2s);
+    const double sst = -A.mu * (ys * ys * ys);
+    double px = 0.0, py = 0.0, pz = 0.0;
+    unsigned m = mask;
+    while (m) {
+        const int q = __ffs(m) - 1;
+        m &= m - 1;
+        const double dx = S.zx[q] - z[0], dy = S.zy[q] - z[1], dz = S.zz[q] - z[2];
+        const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double yv = rsqrt_newton(d2);
+        const double d = d2 * yv;
+        double W = 1.0;
+        for (int l = 0; l < A.nlev; l++) {
+            const double K = changeover_fast(d, fmin(irc_self[l], S.irc[l][q]));
+            W *= 1.0 - K;
+        }
+        const double c = S.m[q] * W * (yv * yv * yv);
+        px = fma(c, dx, px); py = fma(c, dy, py); pz = fma(c, dz, pz);
+    }
+    f[3] = fma(sst, z[0], A.G * px);
+    f[4] = fma(sst, z[1], A.G * py);
+    f[5] = fma(sst, z[2], A.G * pz);
+}
+
+__global__ void __launch_bounds__(32 * kWarpBsWarps)
+bs_warp_kernel(BsArgs A) {
+    __shared__ WarpBsShared sh[kWarpBsWarps];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned gi = blockIdx.x * kWarpBsWarps + wib;
+    if (gi >= A.ctr->ngroups) return;                    // warp-uniform
+    const int g = A.glist[gi];
+    const int s0 = A.goff[g], nm = A.goff[g + 1] - s0;
+    if (nm > 32) return;                                 // handled by bs_kernel
+    WarpBsShared &S = sh[wib];
+    const unsigned long long t_start = global_ns();
+
+    // rank the members by body index: lane r takes the member of rank r
+    const int mine = lane < nm ? A.member[s0 + lane] : 0x7fffffff;
+    int rank = 0;
+    for (int q = 0; q < nm; q++) rank += (__shfl_sync(0xffffffffu, mine, q) < mine);
+    if (lane < nm) S.rank_of_slot[lane] = rank;
+    int src = 0;
+    for (int q = 0; q < nm; q++)
+        if (__shfl_sync(0xffffffffu, rank, q) == lane) src = q;
+    const bool active = lane < nm;
+    const int b = __shfl_sync(0xffffffffu, mine, src);
+    __syncwarp();
+
+    const size_t N = (size_t)A.n;
+    double irc_self[kMaxLevels];
+    unsigned pmask = 0;
+    double y[6];
+    if (active) {
+        for (int l = 0; l < kMaxLevels; l++) irc_self[l] = (l < A.nlev) ? 1.0 / A.rc[l][b] : 0.0;
+        for (int q = A.off[b]; q < A.off[b + 1]; q++) {
+            const int slot = A.slotof[A.list[q]] - s0;
+            pmask |= 1u << S.rank_of_slot[slot];
+        }
+        for (int c = 0; c < 3; c++) { y[c] = A.pre_pos[c * N + b]; y[3 + c] = A.pre_vel[c * N + b]; }
+        S.m[lane] = A.mass[b];
+        for (int l = 0; l < A.nlev; l++) S.irc[l][lane] = irc_self[l];
+    } else {
+        for (int l = 0; l < kMaxLevels; l++) irc_self[l] = 0.0;
+        for (int c = 0; c < 6; c++) y[c] = 0.0;
+    }
+    __syncwarp();
+
+    double t = 0.0, H = A.dt;
+    int attempts = 0;
+    long long acc = 0, rej = 0;
+    bool failed = false;
+    double f0[6], sc[6], zm[6], zn[6], fz[6];
+    while (t < A.dt) {
+        if (attempts >= A.max_steps || global_ns() - t_start > A.time_limit_ns) failed = true;
+        failed = __shfl_sync(0xffffffffu, failed, 0);
+        if (failed) break;
+        attempts++;
+        if (H > A.dt - t) H = A.dt - t;
+        warp_deriv(A, S, lane, active, pmask, irc_self, y, f0);
+        for (int c = 0; c < 6; c++) sc[c] = fabs(y[c]) + fabs(H * f0[c]) + 1e-300;
+        bool accepted = false;
+        int kconv = 0;
+        for (int k = 0; k < kBsCols; k++) {
+            const int nk = 2 * (k + 1);
+            const double h = H / nk;
+            for (int c = 0; c < 6; c++) { zm[c] = y[c]; zn[c] = fma(h, f0[c], y[c]); }
+            for (int mm = 1; mm < nk; mm++) {
+                warp_deriv(A, S, lane, active, pmask, irc_self, zn, fz);
+                for (int c = 0; c < 6; c++) {
+                    const double tt = fma(2.0 * h, fz[c], zm[c]);
+                    zm[c] = zn[c];
+                    zn[c] = tt;
+                }
+            }
+            warp_deriv(A, S, lane, active, pmask, irc_self, zn, fz);
+            // Neville: T_j = T_{j-1} + (T_{j-1} - Tprev_{j-1}) / ((n_k/n_{k-j})^2 - 1),
+            // the factor written as (k-j+1)^2 / (j (2k+2-j)) for n_k = 2(k+1)
+            double cur[6], prev[6];
+            for (int c = 0; c < 6; c++) {
+                cur[c] = 0.5 * (zn[c] + zm[c] + h * fz[c]);
+                prev[c] = S.T[c][lane];
+                S.T[c][lane] = cur[c];
+            }
+            for (int j = 1; j <= k; j++) {
+                const double coef = (double)((k - j + 1) * (k - j + 1)) / (double)(j * (2 * k + 2 - j));
+                for (int c = 0; c < 6; c++) {
+                    const double nxt = fma(cur[c] - prev[c], coef, cur[c]);
+                    prev[c] = S.T[j * 6 + c][lane];
+                    S.T[j * 6 + c][lane] = nxt;
+                    cur[c] = nxt;
+                }
+            }
+            double err = 0.0;
+            if (k >= 1 && active)
+                for (int c = 0; c < 6; c++)
+                    err = fmax(err, fabs(S.T[k * 6 + c][lane] - S.T[(k - 1) * 6 + c][lane]) / sc[c]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+            if (k >= 1 && err <= A.tol) { accepted = true; kconv = k; break; }
+        }
+        if (accepted) {
+            for (int c = 0; c < 6; c++) y[c] = S.T[kconv * 6 + c][lane];
+            t += H;
+            acc++;
+            if (kconv < 4) H *= 1.5;
+        } else {
+            rej++;
+            H *= 0.5;
+        }
+    }
+    if (active) {
+        for (int c = 0; c < 3; c++) { A.pos[c * N + b] = y[c]; A.vel[c * N + b] = y[3 + c]; }
+    }
+    if (lane == 0) {
+        atomicAdd(&A.ctr->bs_steps, (unsigned long long)acc);
+        atomicAdd(&A.ctr->bs_rejects, (unsigned long long)rej);
+        if (failed) {
+            atomicAdd(&A.ctr->bs_fail, 1ull);
+            latch_error(A.ctr, kErrBS);
+        }
+    }
 }
 
 }  // namespace
@@ -254,6 +454,8 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_group
     A.max_steps = s->p.bs_max_steps;
     A.time_limit_ns = 10000000000ull;   // 10 s per group call
     A.ctr = s->ctr;
+    bs_warp_kernel<<<(unsigned)((max_groups + kWarpBsWarps - 1) / kWarpBsWarps), 32 * kWarpBsWarps, 0, s->stream>>>(A); ++s->launches;
+    GENGA_CUDA_TRY(cudaGetLastError());
     bs_kernel<<<(unsigned)max_groups, kBsThreads, 0, s->stream>>>(A); ++s->launches;
     return cudaGetLastError();
 }
@@ -262,12 +464,20 @@ cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb
     if (nb <= 0) return cudaSuccess;
     KickPairsArgs A;
     A.n = (int)s->n; A.nb = nb; A.level = level;
+    A.np = s->npairs_host[level - 1];
+    A.pairs = s->pairs[level - 1];
     A.bodies = s->bodies[level];
-    A.off = s->csr[level - 1].off; A.list = s->csr[level - 1].list;
+    A.off = s->csr[level - 1].off; A.list = s->csr[level - 1].list; A.lpair = s->csr[level - 1].lpair;
+    A.term = s->csr[level - 1].term;
     A.pos = s->pos; A.vel = s->vel; A.mass = s->mass;
     for (int l = 0; l < kMaxLevels; l++) A.rc[l] = s->rcl[l].rc;
+    A.rc2_0 = s->rcl[0].rc2;
     A.G = s->p.G; A.dt_half = dt_half;
-    kick_pairs_kernel<<<(nb + 127) / 128, 128, 0, s->stream>>>(A); ++s->launches;
+    if (A.np > 0) {
+        kick_pairs_terms_kernel<<<(unsigned)((A.np + 255) / 256), 256, 0, s->stream>>>(A); ++s->launches;
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    kick_pairs_apply_kernel<<<(nb + 127) / 128, 128, 0, s->stream>>>(A); ++s->launches;
     return cudaGetLastError();
 }
 

@@ -55,7 +55,9 @@ struct Csr {
     int *deg = nullptr;    // n+1
     int *off = nullptr;    // n+1 (exclusive scan of deg)
     int *fill = nullptr;   // n
-    int *list = nullptr;   // 2 * cap
+    int *list = nullptr;   // 2 * cap: partner of each entry
+    int *lpair = nullptr;  // 2 * cap: index of the entry's pair in the pair list
+    double *term = nullptr;  // 3 * cap: per-pair kick terms (KickS)
     int64_t cap = 0;       // pairs
 };
 
@@ -178,6 +180,56 @@ cudaError_t exclusive_scan(genga_system *s, const int *in, int *out, int64_t len
 // bs.cu
 cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_groups);
 cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb);
+
+// ---------------------------------------------------------------------------
+// FP64 reciprocal square root and reciprocal from an FP32 hardware seed plus
+// Newton steps in FP64 (two steps reach full double precision).  The seed's
+// conversions use integer bit manipulation (no FP64 pipe work); inputs must be
+// positive normal doubles within the FP32 exponent range.
+__device__ __forceinline__ float f32_of_f64_trunc(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    return __uint_as_float(((hi - 0x38000000u) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double f64_of_f32(float f) {
+    const unsigned fb = __float_as_uint(f);
+    return __hiloint2double((int)((fb >> 3) + 0x38000000u), (int)(fb << 29));
+}
+__device__ __forceinline__ double half_of(double y) {   // y / 2 for positive normal y
+    return __hiloint2double(__double2hiint(y) - 0x00100000, __double2loint(y));
+}
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    double y = f64_of_f32(rsqrtf(f32_of_f64_trunc(x)));
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const double t = x * y;
+        const double e = fma(-t, y, 1.0);
+        y = fma(half_of(y), e, y);
+    }
+    return y;
+}
+__device__ __forceinline__ double rcp_newton(double d) {
+    float s;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(f32_of_f64_trunc(d)));
+    double x = f64_of_f32(s);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const double e = fma(-d, x, 1.0);
+        x = fma(x, e, x);
+    }
+    return x;
+}
+// Changeover function with the reciprocal 1/rc supplied; same definition as
+// changeover() (y = (r/rc - 0.1)/0.9, K = y^2/(2y^2 - 2y + 1)), evaluated with
+// contracted FP64 arithmetic for force terms (not for decisions).
+__device__ __forceinline__ double changeover_fast(double r, double irc) {
+    const double y = fma(r, irc, -0.1) * (1.0 / 0.9);
+    if (y <= 0.0) return 0.0;
+    if (y >= 1.0) return 1.0;
+    const double y2 = y * y;
+    const double w = 1.0 - y;
+    return y2 * rcp_newton(fma(w, w, y2));
+}
 
 }  // namespace genga
 

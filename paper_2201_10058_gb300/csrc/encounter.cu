@@ -133,23 +133,31 @@ __global__ void csr_degree_kernel(const uint2 *pairs, long long np, int *deg) {
     atomicAdd(&deg[p.y], 1);
 }
 
-__global__ void csr_fill_kernel(const uint2 *pairs, long long np, const int *off, int *fill, int *list) {
+__global__ void csr_fill_kernel(const uint2 *pairs, long long np, const int *off, int *fill, int *list,
+                                int *lpair) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= np) return;
     const uint2 p = pairs[k];
-    list[off[p.x] + atomicAdd(&fill[p.x], 1)] = (int)p.y;
-    list[off[p.y] + atomicAdd(&fill[p.y], 1)] = (int)p.x;
+    const int a = off[p.x] + atomicAdd(&fill[p.x], 1);
+    list[a] = (int)p.y;
+    lpair[a] = (int)k;
+    const int b = off[p.y] + atomicAdd(&fill[p.y], 1);
+    list[b] = (int)p.x;
+    lpair[b] = (int)k;
 }
 
-__global__ void csr_sort_kernel(int n, const int *off, int *list) {
+// Sorts every row by partner index (insertion sort; rows are short), carrying
+// the pair index along.
+__global__ void csr_sort_kernel(int n, const int *off, int *list, int *lpair) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     const int s = off[b], e = off[b + 1];
     for (int u = s + 1; u < e; u++) {
-        const int key = list[u];
+        const int key = list[u], kp = lpair[u];
         int w = u - 1;
-        while (w >= s && list[w] > key) { list[w + 1] = list[w]; w--; }
+        while (w >= s && list[w] > key) { list[w + 1] = list[w]; lpair[w + 1] = lpair[w]; w--; }
         list[w + 1] = key;
+        lpair[w + 1] = kp;
     }
 }
 
@@ -258,9 +266,9 @@ cudaError_t build_csr(genga_system *s, int level, int64_t np) {
     }
     GENGA_CUDA_TRY(exclusive_scan(s, c.deg, c.off, n));
     if (np > 0) {
-        csr_fill_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.off, c.fill, c.list); ++s->launches;
+        csr_fill_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.off, c.fill, c.list, c.lpair); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
-        csr_sort_kernel<<<(n + 127) / 128, 128, 0, s->stream>>>(n, c.off, c.list); ++s->launches;
+        csr_sort_kernel<<<(n + 127) / 128, 128, 0, s->stream>>>(n, c.off, c.list, c.lpair); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;

@@ -77,8 +77,12 @@ int check_params(genga_system *s, const genga_params_t *p) {
 int alloc_pairs(genga_system *s, int level, int64_t cap) {
     dfree(s->pairs[level]);
     dfree(s->csr[level].list);
+    dfree(s->csr[level].lpair);
+    dfree(s->csr[level].term);
     CU(dalloc(&s->pairs[level], (size_t)cap));
     CU(dalloc(&s->csr[level].list, 2 * (size_t)cap));
+    CU(dalloc(&s->csr[level].lpair, 2 * (size_t)cap));
+    CU(dalloc(&s->csr[level].term, 3 * (size_t)cap));
     s->pair_cap[level] = cap;
     s->csr[level].cap = cap;
     return GENGA_OK;
@@ -133,6 +137,7 @@ void free_all(genga_system *s) {
         dfree(s->pre_pos[l]); dfree(s->pre_vel[l]);
         dfree(s->pairs[l]);
         dfree(s->csr[l].deg); dfree(s->csr[l].off); dfree(s->csr[l].fill); dfree(s->csr[l].list);
+        dfree(s->csr[l].lpair); dfree(s->csr[l].term);
         dfree(s->bodies[l]);
     }
     dfree(s->kick_part); dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
