@@ -184,6 +184,30 @@ int genga_set_predrift(genga_system_t *sys, const double *pos_host, const double
 /* Counters of the last genga_step (or of the last build_encounters / bs).   */
 int genga_get_stats(genga_system_t *sys, genga_stats_t *st);
 
+/* ---- allocation-free kick ---------------------------------------------- */
+/* The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory: a caller whose framework's caching allocator
+ * already holds the device's free memory (a cudaMalloc would fail or fragment
+ * that pool), or one on a latency-critical loop where cudaMalloc/cudaFree
+ * would stall every stream of the device.  It performs the same kick as
+ * genga_kick without the pre-check, on arrays the caller passes (device
+ * pointers, layout as in genga_create): pos (3n), mass (n), rc (n critical
+ * radii), vel (3n, updated by dt_half * a when dt_half != 0), acc_out (3n or
+ * NULL; receives the accelerations).  It calls no cudaMalloc/cudaFree: its
+ * scratch is one fixed device array of 16 MiB inside the library, held by
+ * every GPU that loads the library until the process exits.  n may be at most
+ * GENGA_KICK_STATIC_MAX_N (larger n returns GENGA_ECAPACITY before any launch).
+ * The first call on a device looks up that array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (every call rewrites
+ * what it reads); calls that overlap on the GPU race with each other -- issue
+ * them on one stream or synchronise between them.  Returns GENGA_OK, EINVAL,
+ * ECAPACITY or ECUDA.  Enqueued on `stream` (a cudaStream_t, NULL = default). */
+#define GENGA_KICK_STATIC_MAX_N 279616
+int genga_kick_static(int64_t n, const double *pos, const double *mass, const double *rc,
+                      double G, double dt_half, int precision, double *vel, double *acc_out,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

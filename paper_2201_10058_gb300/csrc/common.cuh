@@ -169,6 +169,18 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
 cudaError_t launch_precheck_only(genga_system *s);
 int kick_nchunk_for(int n, int num_sms);
 
+// Kick on caller-provided arrays (no system object, no pre-check).
+struct KickRaw {
+    const double *pos, *mass, *rc, *rc2;
+    const float *thr;
+    double *part;        // partial sums, [nchunk][6][n]
+    int n;
+    double G, dt_half;
+    double *vel, *acc_out;
+    bool mixed;
+};
+cudaError_t launch_kick_raw(const KickRaw &k, int num_sms, int max_nchunk, cudaStream_t stream);
+
 // encounter.cu
 cudaError_t launch_detect(genga_system *s, const uint2 *in, int64_t nin, int level,
                           uint2 *out, int64_t cap, unsigned long long *count);

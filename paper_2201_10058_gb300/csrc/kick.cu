@@ -249,6 +249,30 @@ cudaError_t launch_precheck_only(genga_system *s) {
     return cudaGetLastError();
 }
 
+// Launches the kick (no pre-check) on caller-provided arrays, with the number of
+// j-chunks capped at max_nchunk; used by the allocation-free entry point.
+cudaError_t launch_kick_raw(const KickRaw &k, int num_sms, int max_nchunk, cudaStream_t stream) {
+    int chunk, nchunk;
+    kick_geometry(k.n, num_sms, &chunk, &nchunk);
+    if (nchunk > max_nchunk) {
+        const int tiles = (k.n + kTile - 1) / kTile;
+        const int tiles_per_chunk = (tiles + max_nchunk - 1) / max_nchunk;
+        chunk = tiles_per_chunk * kTile;
+        nchunk = (k.n + chunk - 1) / chunk;
+    }
+    KickArgs A;
+    A.x = k.pos; A.y = k.pos + k.n; A.z = k.pos + 2 * (size_t)k.n; A.m = k.mass;
+    A.rc = k.rc; A.rc2 = k.rc2; A.pc2 = nullptr; A.thr = k.thr;
+    A.n = k.n; A.chunk = chunk; A.part = k.part;
+    A.cand = nullptr; A.cand_count = nullptr; A.cand_cap = 0;
+    dim3 grid((k.n + kKickThreads - 1) / kKickThreads, nchunk);
+    if (k.mixed) kick_kernel<true, false, true><<<grid, kKickThreads, 0, stream>>>(A);
+    else kick_kernel<false, false, true><<<grid, kKickThreads, 0, stream>>>(A);
+    GENGA_CUDA_TRY(cudaGetLastError());
+    kick_finalize<<<(k.n + 255) / 256, 256, 0, stream>>>(k.part, nchunk, k.n, k.G, k.dt_half, k.vel, k.acc_out);
+    return cudaGetLastError();
+}
+
 int kick_nchunk_for(int n, int num_sms) {
     int c, nc;
     kick_geometry(n, num_sms, &c, &nc);

@@ -25,7 +25,10 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_set_params", "genga_sync", "genga_rcrit", "genga_set_rcrit", "genga_kick",
             "genga_hc", "genga_drift", "genga_build_encounters", "genga_bs", "genga_step",
             "genga_step_host", "genga_energy", "genga_get_candidates", "genga_get_pairs",
-            "genga_get_groups", "genga_get_rcrit", "genga_set_predrift", "genga_get_stats"]
+            "genga_get_groups", "genga_get_rcrit", "genga_set_predrift", "genga_get_stats",
+            "genga_kick_static"]
+
+KICK_STATIC_MAX_N = 279616
 
 
 class GengaError(RuntimeError):
@@ -105,6 +108,8 @@ def load(build_if_missing: bool = True):
         L.genga_get_rcrit.argtypes = [sysp, C.c_int, _VP]
         L.genga_set_predrift.argtypes = [sysp, _VP, _VP]
         L.genga_get_stats.argtypes = [sysp, _P(Stats)]
+        L.genga_kick_static.argtypes = [C.c_int64, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int,
+                                        _VP, _VP, _VP]
         for name in EXPORTED:
             if name not in ("genga_default_params", "genga_destroy", "genga_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -118,6 +123,18 @@ def default_params(**kw) -> Params:
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def kick_static(pos, mass, rc, G: float, dt_half: float, precision: int, vel=None, acc_out=None,
+                stream=None) -> int:
+    """genga_kick_static on torch CUDA tensors (pos (3,n), mass (n,), rc (n,));
+    returns the C status code (0 on success)."""
+    import torch
+    L = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ptr = lambda t: None if t is None else _VP(t.data_ptr())
+    return L.genga_kick_static(int(mass.shape[0]), ptr(pos), ptr(mass), ptr(rc), G, dt_half,
+                               precision, ptr(vel), ptr(acc_out), _VP(s.cuda_stream))
 
 
 def _np_ptr(a: np.ndarray):
