@@ -36,10 +36,11 @@ METRIC = ("changeover-kick G pair-interactions/s and steps/s at N=65536 (FP64 vs
           "% of peak")
 UNIT = "Gpair/s"
 # FP64 instructions per pair interaction that each kick form's algorithm needs
-# (FMA counted as one): displacement 3, r^2 3, r^-1 (mixed: one Newton
-# correction of an FP32 seed, 3; FP64: two Newton steps from a ~2^-22 seed, 6),
-# m r^-3 3, accumulation 3.
-FP64_OPS_PER_PAIR = {"mixed": 15, "fp64": 18}
+# (FMA counted as one).  Mixed: displacement 3, r^2 3, Newton residual
+# 1 - r^2 y0^2 of the FP32 seed 2, joining the float-float m r^-3 1,
+# accumulation 3.  FP64: displacement 3, r^2 3, r^-1 to FP64 precision (two
+# Newton steps from a ~2^-22 seed) 6, m r^-3 3, accumulation 3.
+FP64_OPS_PER_PAIR = {"mixed": 12, "fp64": 18}
 FP64_OPS_PER_CLK_PER_SM = 2      # measured DFMA throughput per SM per clock on GB300
 
 
@@ -53,6 +54,9 @@ def parse():
     ap.add_argument("--kick-reps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e/cpu/fp64 legs (profiling runs)")
+    ap.add_argument("--energy-run", type=int, default=0,
+                    help="instead of timing: integrate this many steps in FP64 and mixed and "
+                         "report the relative energy error every 100 steps")
     return ap.parse_args()
 
 
@@ -363,8 +367,52 @@ def run_reference(args, dist: Dist) -> dict | None:
                     "d2h_bytes_per_step": 0}}
 
 
+def energy_run(args) -> dict:
+    """Relative energy error of the FP64 and mixed kicks along the same run."""
+    import torch
+
+    from paper_2201_10058_gb300 import genga
+    from workloads import disk
+    from workloads.disk import SEED_BASE
+    genga.load()
+    wl = disk(args.n, 0.5, 4.0, 5.0, SEED_BASE + 2, n_embryos=4, m_embryo_earth=0.1,
+              slevels=2, substeps=10, name=f"disk{args.n}+4emb")
+    dev = torch.device("cuda", 0)
+    out = {"n_bodies": wl.n, "steps": args.energy_run, "every": 100}
+    traj = {}
+    for name, prec in (("fp64", genga.GENGA_FP64), ("mixed", genga.GENGA_MIXED)):
+        pos = torch.tensor(np.ascontiguousarray(wl.x.T), device=dev)
+        vel = torch.tensor(np.ascontiguousarray(wl.v.T), device=dev)
+        mass = torch.tensor(wl.m, device=dev)
+        p = genga.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2,
+                                 f_pc=wl.f_pc, slevels=wl.slevels, substeps=wl.substeps,
+                                 precision=prec)
+        s = genga.System(pos, vel, mass, p)
+        E0, L0 = s.energy()
+        rows = [(0, 0.0)]
+        t0 = time.perf_counter()
+        done = 0
+        while done < args.energy_run:
+            k = min(100, args.energy_run - done)
+            s.step(k)
+            done += k
+            E, L = s.energy()
+            rows.append((done, (E - E0) / abs(E0)))
+        traj[name] = {"E0": E0, "dE_rel": rows, "seconds": time.perf_counter() - t0}
+        s.close()
+    diffs = [abs(a[1] - b[1]) for a, b in zip(traj["fp64"]["dE_rel"], traj["mixed"]["dE_rel"])]
+    out.update(traj)
+    out["max_abs_dE_rel_fp64"] = max(abs(r[1]) for r in traj["fp64"]["dE_rel"])
+    out["max_abs_dE_rel_mixed"] = max(abs(r[1]) for r in traj["mixed"]["dE_rel"])
+    out["max_mixed_minus_fp64"] = max(diffs)
+    return out
+
+
 def main():
     args = parse()
+    if args.energy_run:
+        print(json.dumps(energy_run(args)))
+        return
     dist = Dist(args.gpus)
     try:
         line = run_reference(args, dist) if args.impl == "reference" else run_ours(args, dist)

@@ -15,9 +15,10 @@
 //     pre-check (operation order identical to the definition, no contraction)
 //     and the changeover function; candidates are appended with one atomic per
 //     warp (ballot + popc);
-//   * MIXED: r^-1 from an FP32 rsqrt seed built from the bits of r^2, one FP64
-//     Newton correction; FP64 displacement and accumulation; per-tile sums
-//     folded with TwoSum.  FP64: CUDA's double rsqrt.
+//   * MIXED: FP32 rsqrt seed built from the bits of r^2, one FP64 Newton
+//     residual applied to r^-3 in extended (float-float) arithmetic; FP64
+//     displacement and accumulation; per-tile sums folded with TwoSum:
+//     12 FP64 instructions per pair.  FP64: CUDA's double rsqrt.
 #include "common.cuh"
 
 namespace genga {
@@ -47,12 +48,28 @@ __device__ __forceinline__ float r2_to_float_trunc(double r2) {
     return __uint_as_float(fb);
 }
 
-// Double with the value of a positive normal float (exact), and half of it.
+// Double with the value of a positive normal float (exact).
 __device__ __forceinline__ double float_to_double_exact(unsigned fb) {
     return __hiloint2double((int)((fb >> 3) + 0x38000000u), (int)(fb << 29));
 }
-__device__ __forceinline__ double float_to_double_half(unsigned fb) {
-    return __hiloint2double((int)((fb >> 3) + 0x38000000u - 0x00100000u), (int)(fb << 29));
+
+// Double with the value of a float (exact), for any sign; zero and subnormal
+// floats give a signed zero.  Integer operations only.
+__device__ __forceinline__ double f64_of_f32_any(float f) {
+    const unsigned fb = __float_as_uint(f);
+    const unsigned mag = fb & 0x7fffffffu, sgn = fb & 0x80000000u;
+    const unsigned hi = (mag >= 0x00800000u) ? (sgn | ((mag >> 3) + 0x38000000u)) : sgn;
+    const unsigned lo = (mag >= 0x00800000u) ? (mag << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+// Float with the value of a double of magnitude below 2^128, mantissa
+// truncated, any sign; magnitudes below 2^-126 give a signed zero.
+__device__ __forceinline__ float f32_of_f64_any(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const unsigned mag = hi & 0x7fffffffu, sgn = hi & 0x80000000u;
+    const unsigned fb = (mag >= 0x38100000u) ? (sgn | ((mag - 0x38000000u) << 3) | (lo >> 29)) : sgn;
+    return __uint_as_float(fb);
 }
 
 template <bool MIXED, bool PRECHECK, bool FORCE>
@@ -61,7 +78,7 @@ kick_kernel(KickArgs A)
 {
     __shared__ double sx[kTile], sy[kTile], sz[kTile], sm[kTile];
     __shared__ double src[kTile], src2[kTile], spc2[kTile];
-    __shared__ float sthr[kTile];
+    __shared__ float sthr[kTile], smh[kTile], sml[kTile];
 
     const int n = A.n;
     const int i = blockIdx.x * kKickThreads + threadIdx.x;
@@ -92,6 +109,11 @@ kick_kernel(KickArgs A)
             src[k] = A.rc[j]; src2[k] = A.rc2[j];
             if (PRECHECK) spc2[k] = A.pc2[j];
             sthr[k] = A.thr[j];
+            if (MIXED) {     // mass as an unevaluated sum of two floats
+                const float mh = __double2float_rn(A.m[j]);
+                smh[k] = mh;
+                sml[k] = __double2float_rn(A.m[j] - (double)mh);
+            }
         }
         __syncthreads();
 
@@ -105,6 +127,8 @@ kick_kernel(KickArgs A)
             double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
             float r2f = r2_to_float_trunc(r2);
             double mk = sm[k];
+            float mh = 0.0f, ml = 0.0f;
+            if (MIXED) { mh = smh[k]; ml = sml[k]; }
             if (r2f < fmaxf(thri, sthr[k])) {
                 // Rare path: exact pre-check and changeover function.
                 const double r2e = dist2_rn(dx, dy, dz);
@@ -125,21 +149,37 @@ kick_kernel(KickArgs A)
                 }
                 if (j == i) {
                     mk = 0.0; r2 = 1.0; r2f = 1.0f;          // self term: zero, finite
+                    mh = 0.0f; ml = 0.0f;
                 } else if (FORCE && r2e < fmax(rc2i, src2[k])) {
                     mk = mk * changeover(sqrt(r2e), fmax(rci, src[k]));
+                    if (MIXED) {
+                        mh = __double2float_rn(mk);
+                        ml = __double2float_rn(mk - (double)mh);
+                    }
                 }
             }
             if (FORCE) {
                 double s;
                 if (MIXED) {
+                    // FP32 seed y0 ~ r^-1; FP64 Newton residual e = 1 - r^2 y0^2 (2 FP64
+                    // ops); r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 1.5 e + 1.875 e^2 + O(e^3)),
+                    // |e| < 2^-20.  m y0^3 is formed exactly enough (~2^-46) as a sum of two
+                    // floats, the correction in FP32, and the two parts meet in one FP64 add.
                     const float y0f = rsqrtf(r2f);
-                    const unsigned yb = __float_as_uint(y0f);
-                    const double y0 = float_to_double_exact(yb);
-                    const double h0 = float_to_double_half(yb);
+                    const double y0 = float_to_double_exact(__float_as_uint(y0f));
                     const double t = r2 * y0;
-                    const double e = fma(-t, y0, 1.0);        // 1 - r^2 y0^2
-                    const double yv = fma(h0, e, y0);          // one Newton correction
-                    s = (mk * yv) * (yv * yv);
+                    const double e = fma(-t, y0, 1.0);
+                    const float p = y0f * y0f, pe = fmaf(y0f, y0f, -p);
+                    const float q = p * y0f;
+                    float qe = fmaf(p, y0f, -q);
+                    qe = fmaf(pe, y0f, qe);
+                    const float ch = q * mh;
+                    float ce = fmaf(q, mh, -ch);
+                    ce = fmaf(q, ml, ce);
+                    ce = fmaf(qe, mh, ce);
+                    const float ef = f32_of_f64_any(e);
+                    const float corr = fmaf(ch, fmaf(1.875f * ef, ef, 1.5f * ef), ce);
+                    s = f64_of_f32_any(ch) + f64_of_f32_any(corr);
                 } else {
                     const double yv = rsqrt(r2);
                     s = (mk * yv) * (yv * yv);

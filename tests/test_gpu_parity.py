@@ -99,6 +99,32 @@ def test_kick_acceleration_matches_oracle(g, name, make, precision, tol):
     assert np.abs(F.sum(axis=0)).max() < 1e-11 * np.abs(F).sum(axis=0).max()
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_kick_config1_size(g, precision, tol):
+    """N = 16384 disk (the FP64-vs-mixed kick configuration): every particle."""
+    wl = config_workload(1)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    a = _acc(g, wl, precision, rc)
+    ref = O.accel(wl.x, wl.m, rc, G, nthreads=16)
+    rel = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    print(f"N=16384 precision={precision}: max {rel.max():.3e} median {np.median(rel):.3e}")
+    assert rel.max() <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_kick_bench_size_sampled_rows(g, precision, tol):
+    """The bench disk (N = 65,540, launch configuration of bench.py): 512 sampled
+    rows against the oracle computed row by row; candidates checked for those rows."""
+    wl = config_workload(2)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    a = _acc(g, wl, precision, rc)
+    rows = np.random.default_rng(5).choice(wl.n, 512, replace=False)
+    rows = np.concatenate([rows, [0, wl.n - 1, wl.n - 2, wl.n - 4]])   # embryos and the tail
+    ref = O.accel_rows(wl.x, wl.m, rc, G, rows, nthreads=16)
+    rel = np.linalg.norm(a[rows] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() <= tol, rel.max()
+
+
 def test_kick_applies_velocity_update(g):
     wl = config_workload(0)
     rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
