@@ -2,8 +2,9 @@
 // Appendix A "Bulirsch-Stoer(dt)") and the level kick KickS of the
 // higher-level changeover scheme (Sec. 4.3, Appendix A).
 //
-// BS: one CTA per group, members strided over the CTA's threads.  Each member
-// integrates
+// BS for groups of more than 32 members: one CTA per group, members strided
+// over the CTA's threads (groups of at most 32 go to bs_cols_kernel below).
+// Each member integrates
 //     dx/dt = v,   dv/dt = -mu x/|x|^3 + G sum_{partners j} m_j W_ij (x_j - x)/r^3,
 //     W_ij = prod_{k=0..level} (1 - K(r_ij; rc_k,ij)),
 // with partners taken from the ascending partner list of the level's
@@ -100,7 +101,7 @@ bs_kernel(BsArgs A) {
     const unsigned long long t_start = global_ns();
     const int g = A.glist[blockIdx.x];
     const int s0 = A.goff[g], s1 = A.goff[g + 1];
-    if (s1 - s0 <= 32) return;                           // bs_warp_kernel's groups
+    if (s1 - s0 <= 32) return;                           // bs_cols_kernel's groups
     const size_t N = (size_t)A.n;
 
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
@@ -269,46 +270,52 @@ __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Warp-per-group Bulirsch-Stoer for groups of at most 32 members: lane = member
-// (ranked by ascending body index), state and midpoint vectors in registers,
-// positions exchanged through a per-warp shared-memory slice, the Neville
-// table in shared memory, only __syncwarp.  Same integrator and step control
-// as bs_kernel.
-constexpr int kWarpBsWarps = 2;
-
-struct WarpBsShared {
-    double zx[32], zy[32], zz[32];
-    double m[32];
-    double irc[kMaxLevels][32];
-    double T[kBsCols * 6][32];
-    int rank_of_slot[32];
+// Column-parallel Bulirsch-Stoer for groups of at most 32 members.  The 8
+// extrapolation columns of one step attempt (modified midpoint with n = 2, 4,
+// ..., 16 sub-steps) are independent integrations from the same start, so a CTA
+// of 8 x M threads runs them at once: thread (k, a) integrates column k for
+// member a (M = 4, 8, 16 or 32 member slots).  One attempt then costs 16
+// sequential derivative evaluations instead of 2 + 4 + ... + 16 + 8 = 80; the
+// Neville table is built per (member, component) afterwards and the first
+// column k >= 1 under tolerance is accepted -- the same arithmetic and the same
+// acceptance rule as the serial scheme.  FP64 throughout.
+template <int M>
+struct ColsShared {
+    double zx[8 * M], zy[8 * M], zz[8 * M];      // current positions, per (column, member)
+    double m[M];
+    double irc[kMaxLevels][M];
+    double y[6][M], f0[6][M];                    // attempt start and its derivative
+    double yk[8][6][M];                          // column results
+    double ynew[6][M];                           // accepted state
+    double red[8];
+    int rank_of_slot[M];
+    int flag;
 };
 
-__device__ __forceinline__ void warp_deriv(const BsArgs &A, WarpBsShared &S, int lane, bool active,
-                                           unsigned mask, const double *irc_self, const double z[6],
-                                           double f[6]) {
-    __syncwarp();
-    S.zx[lane] = z[0]; S.zy[lane] = z[1]; S.zz[lane] = z[2];
-    __syncwarp();
+template <int M>
+__device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, int tid, int col,
+                                           bool active, unsigned mask, const double *irc_self,
+                                           const double z[6], double f[6]) {
+    __syncthreads();
+    S.zx[tid] = z[0]; S.zy[tid] = z[1]; S.zz[tid] = z[2];
+    __syncthreads();
     f[0] = z[3]; f[1] = z[4]; f[2] = z[5];
     if (!active) { f[3] = f[4] = f[5] = 0.0; return; }
     const double r2s = fma(z[2], z[2], fma(z[1], z[1], z[0] * z[0]));
     const double ys = rsqrt_newton(r2s);
     const double sst = -A.mu * (ys * ys * ys);
     double px = 0.0, py = 0.0, pz = 0.0;
-    unsigned m = mask;
-    while (m) {
-        const int q = __ffs(m) - 1;
-        m &= m - 1;
-        const double dx = S.zx[q] - z[0], dy = S.zy[q] - z[1], dz = S.zz[q] - z[2];
+    unsigned mm = mask;
+    while (mm) {
+        const int q = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const int lq = col * M + q;
+        const double dx = S.zx[lq] - z[0], dy = S.zy[lq] - z[1], dz = S.zz[lq] - z[2];
         const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
         const double yv = rsqrt_newton(d2);
         const double d = d2 * yv;
         double W = 1.0;
-        for (int l = 0; l < A.nlev; l++) {
-            const double K = changeover_fast(d, fmin(irc_self[l], S.irc[l][q]));
-            W *= 1.0 - K;
-        }
+        for (int l = 0; l < A.nlev; l++) W *= 1.0 - changeover_fast(d, fmin(irc_self[l], S.irc[l][q]));
         const double c = S.m[q] * W * (yv * yv * yv);
         px = fma(c, dx, px); py = fma(c, dy, py); pz = fma(c, dz, pz);
     }
@@ -317,104 +324,135 @@ __device__ __forceinline__ void warp_deriv(const BsArgs &A, WarpBsShared &S, int
     f[5] = fma(sst, z[2], A.G * pz);
 }
 
-__global__ void __launch_bounds__(32 * kWarpBsWarps)
-bs_warp_kernel(BsArgs A) {
-    __shared__ WarpBsShared sh[kWarpBsWarps];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned gi = blockIdx.x * kWarpBsWarps + wib;
-    if (gi >= A.ctr->ngroups) return;                    // warp-uniform
-    const int g = A.glist[gi];
+template <int M>
+__device__ __forceinline__ double cols_block_max(double v, ColsShared<M> &S) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    constexpr int nw = (8 * M) / 32;
+    if (nw == 1) return v;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = S.red[0];
+#pragma unroll
+    for (int w = 1; w < nw; w++) r = fmax(r, S.red[w]);
+    return r;
+}
+
+template <int M>
+__global__ void __launch_bounds__(8 * M)
+bs_cols_kernel(BsArgs A) {
+    __shared__ ColsShared<M> S;
+    const int tid = threadIdx.x;
+    const int col = tid / M, a = tid % M;
+    if (blockIdx.x >= A.ctr->ngroups) return;
+    const int g = A.glist[blockIdx.x];
     const int s0 = A.goff[g], nm = A.goff[g + 1] - s0;
-    if (nm > 32) return;                                 // handled by bs_kernel
-    WarpBsShared &S = sh[wib];
+    if (nm > M || (M > 4 && nm <= M / 2)) return;          // another bucket's group
     const unsigned long long t_start = global_ns();
-
-    // rank the members by body index: lane r takes the member of rank r
-    const int mine = lane < nm ? A.member[s0 + lane] : 0x7fffffff;
-    int rank = 0;
-    for (int q = 0; q < nm; q++) rank += (__shfl_sync(0xffffffffu, mine, q) < mine);
-    if (lane < nm) S.rank_of_slot[lane] = rank;
-    int src = 0;
-    for (int q = 0; q < nm; q++)
-        if (__shfl_sync(0xffffffffu, rank, q) == lane) src = q;
-    const bool active = lane < nm;
-    const int b = __shfl_sync(0xffffffffu, mine, src);
-    __syncwarp();
-
     const size_t N = (size_t)A.n;
+
+    // member a of rank a (ascending body index), computed by the column-0 threads
+    if (tid < M) {
+        int mine = (a < nm) ? A.member[s0 + a] : 0x7fffffff;
+        int rank = 0;
+        for (int q = 0; q < nm; q++) rank += (A.member[s0 + q] < mine);
+        if (a < nm) S.rank_of_slot[a] = rank;
+    }
+    __syncthreads();
+    const bool active = a < nm;
+    int b = 0;
+    if (active)
+        for (int q = 0; q < nm; q++)
+            if (S.rank_of_slot[q] == a) b = A.member[s0 + q];
     double irc_self[kMaxLevels];
     unsigned pmask = 0;
     double y[6];
+    for (int l = 0; l < kMaxLevels; l++) irc_self[l] = 0.0;
+    for (int c = 0; c < 6; c++) y[c] = 0.0;
     if (active) {
-        for (int l = 0; l < kMaxLevels; l++) irc_self[l] = (l < A.nlev) ? 1.0 / A.rc[l][b] : 0.0;
-        for (int q = A.off[b]; q < A.off[b + 1]; q++) {
-            const int slot = A.slotof[A.list[q]] - s0;
-            pmask |= 1u << S.rank_of_slot[slot];
-        }
+        for (int l = 0; l < A.nlev; l++) irc_self[l] = 1.0 / A.rc[l][b];
+        for (int q = A.off[b]; q < A.off[b + 1]; q++)
+            pmask |= 1u << S.rank_of_slot[A.slotof[A.list[q]] - s0];
         for (int c = 0; c < 3; c++) { y[c] = A.pre_pos[c * N + b]; y[3 + c] = A.pre_vel[c * N + b]; }
-        S.m[lane] = A.mass[b];
-        for (int l = 0; l < A.nlev; l++) S.irc[l][lane] = irc_self[l];
-    } else {
-        for (int l = 0; l < kMaxLevels; l++) irc_self[l] = 0.0;
-        for (int c = 0; c < 6; c++) y[c] = 0.0;
+        if (col == 0) {
+            S.m[a] = A.mass[b];
+            for (int l = 0; l < A.nlev; l++) S.irc[l][a] = irc_self[l];
+        }
     }
-    __syncwarp();
+    __syncthreads();
 
+    const int nk = 2 * (col + 1);
     double t = 0.0, H = A.dt;
     int attempts = 0;
     long long acc = 0, rej = 0;
     bool failed = false;
-    double f0[6], sc[6], zm[6], zn[6], fz[6];
+    double f0[6], zm[6], zn[6], fz[6];
     while (t < A.dt) {
-        if (attempts >= A.max_steps || global_ns() - t_start > A.time_limit_ns) failed = true;
-        failed = __shfl_sync(0xffffffffu, failed, 0);
-        if (failed) break;
+        if (tid == 0) S.flag = (attempts >= A.max_steps) || (global_ns() - t_start > A.time_limit_ns);
+        __syncthreads();
+        if (S.flag) { failed = true; break; }
         attempts++;
         if (H > A.dt - t) H = A.dt - t;
-        warp_deriv(A, S, lane, active, pmask, irc_self, y, f0);
-        for (int c = 0; c < 6; c++) sc[c] = fabs(y[c]) + fabs(H * f0[c]) + 1e-300;
-        bool accepted = false;
-        int kconv = 0;
-        for (int k = 0; k < kBsCols; k++) {
-            const int nk = 2 * (k + 1);
-            const double h = H / nk;
-            for (int c = 0; c < 6; c++) { zm[c] = y[c]; zn[c] = fma(h, f0[c], y[c]); }
-            for (int mm = 1; mm < nk; mm++) {
-                warp_deriv(A, S, lane, active, pmask, irc_self, zn, fz);
+        cols_deriv<M>(A, S, tid, col, active, pmask, irc_self, y, f0);
+        if (col == 0)
+            for (int c = 0; c < 6; c++) { S.y[c][a] = y[c]; S.f0[c][a] = f0[c]; }
+        // all 8 columns at once: column col takes nk midpoint sub-steps of H/nk
+        const double h = H / nk;
+        for (int c = 0; c < 6; c++) { zm[c] = y[c]; zn[c] = fma(h, f0[c], y[c]); }
+        for (int it = 1; it <= 16; it++) {
+            cols_deriv<M>(A, S, tid, col, active, pmask, irc_self, zn, fz);
+            if (it < nk) {
                 for (int c = 0; c < 6; c++) {
                     const double tt = fma(2.0 * h, fz[c], zm[c]);
                     zm[c] = zn[c];
                     zn[c] = tt;
                 }
+            } else if (it == nk) {
+                for (int c = 0; c < 6; c++) S.yk[col][c][a] = 0.5 * (zn[c] + zm[c] + h * fz[c]);
             }
-            warp_deriv(A, S, lane, active, pmask, irc_self, zn, fz);
-            // Neville: T_j = T_{j-1} + (T_{j-1} - Tprev_{j-1}) / ((n_k/n_{k-j})^2 - 1),
-            // the factor written as (k-j+1)^2 / (j (2k+2-j)) for n_k = 2(k+1)
-            double cur[6], prev[6];
-            for (int c = 0; c < 6; c++) {
-                cur[c] = 0.5 * (zn[c] + zm[c] + h * fz[c]);
-                prev[c] = S.T[c][lane];
-                S.T[c][lane] = cur[c];
-            }
-            for (int j = 1; j <= k; j++) {
-                const double coef = (double)((k - j + 1) * (k - j + 1)) / (double)(j * (2 * k + 2 - j));
-                for (int c = 0; c < 6; c++) {
-                    const double nxt = fma(cur[c] - prev[c], coef, cur[c]);
-                    prev[c] = S.T[j * 6 + c][lane];
-                    S.T[j * 6 + c][lane] = nxt;
-                    cur[c] = nxt;
-                }
-            }
-            double err = 0.0;
-            if (k >= 1 && active)
-                for (int c = 0; c < 6; c++)
-                    err = fmax(err, fabs(S.T[k * 6 + c][lane] - S.T[(k - 1) * 6 + c][lane]) / sc[c]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
-            if (k >= 1 && err <= A.tol) { accepted = true; kconv = k; break; }
         }
-        if (accepted) {
-            for (int c = 0; c < 6; c++) y[c] = S.T[kconv * 6 + c][lane];
+        __syncthreads();
+        // Neville per (component c = col < 6, member a), columns in order
+        double err_k[8];
+        double diag[8];
+        for (int k = 0; k < 8; k++) err_k[k] = 0.0;
+        if (col < 6 && active) {
+            const int c = col;
+            const double sc = fabs(S.y[c][a]) + fabs(H * S.f0[c][a]) + 1e-300;
+            double T[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                double cur = S.yk[k][c][a];
+                double prev = T[0];
+                T[0] = cur;
+#pragma unroll
+                for (int j = 1; j <= k; j++) {
+                    const double coef = (double)((k - j + 1) * (k - j + 1)) / (double)(j * (2 * k + 2 - j));
+                    const double nxt = fma(cur - prev, coef, cur);
+                    prev = T[j];
+                    T[j] = nxt;
+                    cur = nxt;
+                }
+                diag[k] = T[k];
+                if (k >= 1) err_k[k] = fabs(T[k] - T[k - 1]) / sc;
+            }
+        }
+        int kconv = -1;
+#pragma unroll
+        for (int k = 1; k < 8; k++) {
+            const double e = cols_block_max<M>(err_k[k], S);
+            if (kconv < 0 && e <= A.tol) kconv = k;
+        }
+        if (kconv >= 0) {
+            if (col < 6 && active) {
+                double v = diag[1];
+#pragma unroll
+                for (int k = 2; k < 8; k++) if (k == kconv) v = diag[k];
+                S.ynew[col][a] = v;
+            }
+            __syncthreads();
+            if (active) for (int c = 0; c < 6; c++) y[c] = S.ynew[c][a];
             t += H;
             acc++;
             if (kconv < 4) H *= 1.5;
@@ -423,10 +461,9 @@ bs_warp_kernel(BsArgs A) {
             H *= 0.5;
         }
     }
-    if (active) {
+    if (active && col == 0)
         for (int c = 0; c < 3; c++) { A.pos[c * N + b] = y[c]; A.vel[c * N + b] = y[3 + c]; }
-    }
-    if (lane == 0) {
+    if (tid == 0) {
         atomicAdd(&A.ctr->bs_steps, (unsigned long long)acc);
         atomicAdd(&A.ctr->bs_rejects, (unsigned long long)rej);
         if (failed) {
@@ -454,7 +491,13 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_group
     A.max_steps = s->p.bs_max_steps;
     A.time_limit_ns = 10000000000ull;   // 10 s per group call
     A.ctr = s->ctr;
-    bs_warp_kernel<<<(unsigned)((max_groups + kWarpBsWarps - 1) / kWarpBsWarps), 32 * kWarpBsWarps, 0, s->stream>>>(A); ++s->launches;
+    bs_cols_kernel<4><<<(unsigned)max_groups, 32, 0, s->stream>>>(A); ++s->launches;
+    GENGA_CUDA_TRY(cudaGetLastError());
+    bs_cols_kernel<8><<<(unsigned)max_groups, 64, 0, s->stream>>>(A); ++s->launches;
+    GENGA_CUDA_TRY(cudaGetLastError());
+    bs_cols_kernel<16><<<(unsigned)max_groups, 128, 0, s->stream>>>(A); ++s->launches;
+    GENGA_CUDA_TRY(cudaGetLastError());
+    bs_cols_kernel<32><<<(unsigned)max_groups, 256, 0, s->stream>>>(A); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     bs_kernel<<<(unsigned)max_groups, kBsThreads, 0, s->stream>>>(A); ++s->launches;
     return cudaGetLastError();
