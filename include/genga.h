@@ -79,6 +79,7 @@ typedef struct genga_stats {
     int64_t kepler_fail;     /* Kepler solves that hit kepler_max_iter */
     int64_t bs_fail;         /* groups that hit bs_max_steps */
     int64_t kernel_launches; /* CUDA kernels this library launched for these steps */
+    int64_t bs_max_attempts; /* most step attempts any one group needed */
 } genga_stats_t;
 
 typedef struct genga_system genga_system_t;

@@ -193,6 +193,7 @@ bs_kernel(BsArgs A) {
         }
     }
     if (threadIdx.x == 0) {
+        atomicMax(&A.ctr->bs_max_attempts, (unsigned long long)attempts);
         atomicAdd(&A.ctr->bs_steps, (unsigned long long)acc);
         atomicAdd(&A.ctr->bs_rejects, (unsigned long long)rej);
         if (failed) {
@@ -464,6 +465,7 @@ bs_cols_kernel(BsArgs A) {
     if (active && col == 0)
         for (int c = 0; c < 3; c++) { A.pos[c * N + b] = y[c]; A.vel[c * N + b] = y[3 + c]; }
     if (tid == 0) {
+        atomicMax(&A.ctr->bs_max_attempts, (unsigned long long)attempts);
         atomicAdd(&A.ctr->bs_steps, (unsigned long long)acc);
         atomicAdd(&A.ctr->bs_rejects, (unsigned long long)rej);
         if (failed) {
@@ -491,15 +493,25 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_group
     A.max_steps = s->p.bs_max_steps;
     A.time_limit_ns = 10000000000ull;   // 10 s per group call
     A.ctr = s->ctr;
-    bs_cols_kernel<4><<<(unsigned)max_groups, 32, 0, s->stream>>>(A); ++s->launches;
+    // the five size buckets run concurrently on library-owned streams so that
+    // their slowest groups overlap
+    GENGA_CUDA_TRY(cudaEventRecord(s->ev_fork, s->stream));
+    for (int q = 0; q < 4; q++) GENGA_CUDA_TRY(cudaStreamWaitEvent(s->side[q], s->ev_fork, 0));
+    const unsigned grid = (unsigned)max_groups;
+    bs_cols_kernel<4><<<grid, 32, 0, s->side[0]>>>(A); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    bs_cols_kernel<8><<<(unsigned)max_groups, 64, 0, s->stream>>>(A); ++s->launches;
+    bs_cols_kernel<8><<<grid, 64, 0, s->side[1]>>>(A); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    bs_cols_kernel<16><<<(unsigned)max_groups, 128, 0, s->stream>>>(A); ++s->launches;
+    bs_cols_kernel<16><<<grid, 128, 0, s->side[2]>>>(A); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    bs_cols_kernel<32><<<(unsigned)max_groups, 256, 0, s->stream>>>(A); ++s->launches;
+    bs_cols_kernel<32><<<grid, 256, 0, s->side[3]>>>(A); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    bs_kernel<<<(unsigned)max_groups, kBsThreads, 0, s->stream>>>(A); ++s->launches;
+    bs_kernel<<<grid, kBsThreads, 0, s->stream>>>(A); ++s->launches;
+    GENGA_CUDA_TRY(cudaGetLastError());
+    for (int q = 0; q < 4; q++) {
+        GENGA_CUDA_TRY(cudaEventRecord(s->ev_join[q], s->side[q]));
+        GENGA_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_join[q], 0));
+    }
     return cudaGetLastError();
 }
 

@@ -34,6 +34,7 @@ struct DevCounters {
     unsigned long long bs_fail;
     unsigned long long groups_total;     // groups formed since the last reset
     unsigned long long max_group_total;  // largest of them
+    unsigned long long bs_max_attempts;  // most step attempts of one group
     unsigned int err;
     unsigned int ngroups;
     unsigned int max_group;
@@ -48,6 +49,7 @@ struct RcritArrays {
     double *pc2;   // (f_pc rc_i)^2 (level 0 only)
     float *thr_rc; // conservative FP32 upper bound of rc_i^2 (level 0 only)
     float *thr_pc; // conservative FP32 upper bound of (f_pc rc_i)^2 (level 0 only)
+    float *thr_pc_lo; // conservative FP32 lower bound of (f_pc rc_i)^2 (level 0 only)
 };
 
 // CSR partner lists (both directions) of one pair list.
@@ -117,6 +119,8 @@ struct genga_system {
     double *red = nullptr;   // reduction scratch
 
     genga::Scratch scr;
+    cudaStream_t side[4] = {};     // library-owned streams for concurrent BS buckets
+    cudaEvent_t ev_fork = nullptr, ev_join[4] = {};
     genga_stats_t stats;
     int64_t launches = 0;          // kernels launched by this system (host-side count)
     char err[512] = {0};

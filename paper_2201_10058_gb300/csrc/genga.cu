@@ -110,6 +110,12 @@ int alloc_all(genga_system *s) {
     CU(dalloc(&s->rcl[0].pc2, n));
     CU(dalloc(&s->rcl[0].thr_rc, n));
     CU(dalloc(&s->rcl[0].thr_pc, n));
+    CU(dalloc(&s->rcl[0].thr_pc_lo, n));
+    for (int k = 0; k < 4; k++) {
+        CU(cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&s->ev_join[k], cudaEventDisableTiming));
+    }
+    CU(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
     s->kick_chunk = 0;
     s->cand_cap = s->p.cand_capacity > 0 ? s->p.cand_capacity : std::max<int64_t>(1 << 20, 64 * (int64_t)n);
     CU(dalloc(&s->cand, (size_t)s->cand_cap));
@@ -133,7 +139,7 @@ void free_all(genga_system *s) {
     dfree(s->ctr);
     for (int l = 0; l < kMaxLevels; l++) {
         dfree(s->rcl[l].rc); dfree(s->rcl[l].rc2); dfree(s->rcl[l].pc2);
-        dfree(s->rcl[l].thr_rc); dfree(s->rcl[l].thr_pc);
+        dfree(s->rcl[l].thr_rc); dfree(s->rcl[l].thr_pc); dfree(s->rcl[l].thr_pc_lo);
         dfree(s->pre_pos[l]); dfree(s->pre_vel[l]);
         dfree(s->pairs[l]);
         dfree(s->csr[l].deg); dfree(s->csr[l].off); dfree(s->csr[l].fill); dfree(s->csr[l].list);
@@ -143,6 +149,13 @@ void free_all(genga_system *s) {
     dfree(s->kick_part); dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
     dfree(s->gsize); dfree(s->goff); dfree(s->gfill); dfree(s->glist); dfree(s->member);
     dfree(s->slotof); dfree(s->bs_scratch); dfree(s->red); dfree(s->scr.scan_blocks);
+    for (int k = 0; k < 4; k++) {
+        if (s->side[k]) cudaStreamDestroy(s->side[k]);
+        if (s->ev_join[k]) cudaEventDestroy(s->ev_join[k]);
+        s->side[k] = nullptr; s->ev_join[k] = nullptr;
+    }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    s->ev_fork = nullptr;
 }
 
 template <typename T>
@@ -276,6 +289,7 @@ int collect_stats(genga_system *s) {
     s->stats.n_groups = (int64_t)c.groups_total;
     s->stats.max_group = (int64_t)c.max_group_total;
     s->stats.bs_steps = (int64_t)c.bs_steps;
+    s->stats.bs_max_attempts = (int64_t)c.bs_max_attempts;
     s->stats.bs_rejects = (int64_t)c.bs_rejects;
     s->stats.bs_fail = (int64_t)c.bs_fail;
     s->stats.kepler_fail = (int64_t)c.kepler_fail;
@@ -286,7 +300,7 @@ int collect_stats(genga_system *s) {
 int reset_stats(genga_system *s) {
     memset(&s->stats, 0, sizeof(s->stats));
     s->launches = 0;
-    CU(cudaMemsetAsync(&s->ctr->kepler_fail, 0, 6 * sizeof(unsigned long long), s->stream));
+    CU(cudaMemsetAsync(&s->ctr->kepler_fail, 0, 7 * sizeof(unsigned long long), s->stream));
     return GENGA_OK;
 }
 

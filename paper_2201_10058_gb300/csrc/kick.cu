@@ -30,7 +30,9 @@ constexpr int kTile = 256;
 struct KickArgs {
     const double *x, *y, *z, *m;
     const double *rc, *rc2, *pc2;
-    const float *thr;           // thr_pc (pre-check) or thr_rc
+    const float *thr_rc;        // FP32 upper bound of rc^2
+    const float *thr_pc;        // FP32 upper bound of (f_pc rc)^2 (pre-check only)
+    const float *thr_pc_lo;     // FP32 lower bound of (f_pc rc)^2 (pre-check only)
     int n;
     int chunk;
     double *part;               // [nchunk][6][n]
@@ -77,8 +79,8 @@ __global__ void __launch_bounds__(kKickThreads)
 kick_kernel(KickArgs A)
 {
     __shared__ double sx[kTile], sy[kTile], sz[kTile], sm[kTile];
-    __shared__ double src[kTile], src2[kTile], spc2[kTile];
-    __shared__ float sthr[kTile], smh[kTile], sml[kTile];
+    __shared__ double src[kTile], spc2[kTile];
+    __shared__ float sthr[kTile], sthr_pc[kTile], sthr_lo[kTile], smh[kTile], sml[kTile];
 
     const int n = A.n;
     const int i = blockIdx.x * kKickThreads + threadIdx.x;
@@ -86,12 +88,12 @@ kick_kernel(KickArgs A)
     const unsigned lane = threadIdx.x & 31u;
 
     double xi = 1e15, yi = 1e15, zi = 1e15;
-    double rci = 0.0, rc2i = 0.0, pc2i = 0.0;
-    float thri = 0.0f;
+    double rci = 0.0, pc2i = 0.0;
+    float thri = 0.0f, thri_pc = 0.0f, thri_lo = 0.0f;
     if (valid) {
         xi = A.x[i]; yi = A.y[i]; zi = A.z[i];
-        rci = A.rc[i]; rc2i = A.rc2[i]; thri = A.thr[i];
-        if (PRECHECK) pc2i = A.pc2[i];
+        rci = A.rc[i]; thri = A.thr_rc[i];
+        if (PRECHECK) { pc2i = A.pc2[i]; thri_pc = A.thr_pc[i]; thri_lo = A.thr_pc_lo[i]; }
     }
 
     const int jbeg = blockIdx.y * A.chunk;
@@ -106,9 +108,9 @@ kick_kernel(KickArgs A)
         for (int k = threadIdx.x; k < cnt; k += kKickThreads) {
             const int j = jt + k;
             sx[k] = A.x[j]; sy[k] = A.y[j]; sz[k] = A.z[j]; sm[k] = A.m[j];
-            src[k] = A.rc[j]; src2[k] = A.rc2[j];
-            if (PRECHECK) spc2[k] = A.pc2[j];
-            sthr[k] = A.thr[j];
+            src[k] = A.rc[j];
+            sthr[k] = A.thr_rc[j];
+            if (PRECHECK) { spc2[k] = A.pc2[j]; sthr_pc[k] = A.thr_pc[j]; sthr_lo[k] = A.thr_pc_lo[j]; }
             if (MIXED) {     // mass as an unevaluated sum of two floats
                 const float mh = __double2float_rn(A.m[j]);
                 smh[k] = mh;
@@ -129,29 +131,34 @@ kick_kernel(KickArgs A)
             double mk = sm[k];
             float mh = 0.0f, ml = 0.0f;
             if (MIXED) { mh = smh[k]; ml = sml[k]; }
-            if (r2f < fmaxf(thri, sthr[k])) {
-                // Rare path: exact pre-check and changeover function.
-                const double r2e = dist2_rn(dx, dy, dz);
-                if (PRECHECK) {
-                    const bool emit = valid && (j > i) && (r2e < fmax(pc2i, spc2[k]));
-                    const unsigned act = __activemask();
-                    const unsigned ball = __ballot_sync(act, emit);
-                    if (ball) {
-                        const int leader = __ffs(ball) - 1;
-                        unsigned long long base = 0;
-                        if ((int)lane == leader) base = atomicAdd(A.cand_count, (unsigned long long)__popc(ball));
-                        base = __shfl_sync(act, base, leader);
-                        if (emit) {
-                            const unsigned long long idx = base + __popc(ball & ((1u << lane) - 1u));
-                            if (idx < A.cand_cap) A.cand[idx] = make_uint2((unsigned)i, (unsigned)j);
-                        }
+            // Pre-check (bit-exact candidate set): pairs surely inside f_pc rc_ij by the
+            // FP32 lower bound are emitted at once; only the thin band between the
+            // FP32 bounds takes the exact FP64 test in the defining operation order.
+            if (PRECHECK && r2f < fmaxf(thri_pc, sthr_pc[k])) {
+                bool emit = valid && (j > i);
+                if (emit && !(r2f < fmaxf(thri_lo, sthr_lo[k])))
+                    emit = dist2_rn(dx, dy, dz) < fmax(pc2i, spc2[k]);
+                const unsigned act = __activemask();
+                const unsigned ball = __ballot_sync(act, emit);
+                if (ball) {
+                    const int leader = __ffs(ball) - 1;
+                    unsigned long long base = 0;
+                    if ((int)lane == leader) base = atomicAdd(A.cand_count, (unsigned long long)__popc(ball));
+                    base = __shfl_sync(act, base, leader);
+                    if (emit) {
+                        const unsigned long long idx = base + __popc(ball & ((1u << lane) - 1u));
+                        if (idx < A.cand_cap) A.cand[idx] = make_uint2((unsigned)i, (unsigned)j);
                     }
                 }
+            }
+            // Changeover band (rare): K < 1 needs r < rc_ij.  K is flat (zero slope) at
+            // r = rc, so the branch may follow the FP32 bound and K uses the r^2 above.
+            if (r2f < fmaxf(thri, sthr[k])) {
                 if (j == i) {
                     mk = 0.0; r2 = 1.0; r2f = 1.0f;          // self term: zero, finite
                     mh = 0.0f; ml = 0.0f;
-                } else if (FORCE && r2e < fmax(rc2i, src2[k])) {
-                    mk = mk * changeover(sqrt(r2e), fmax(rci, src[k]));
+                } else if (FORCE) {
+                    mk = mk * changeover(sqrt(r2), fmax(rci, src[k]));
                     if (MIXED) {
                         mh = __double2float_rn(mk);
                         ml = __double2float_rn(mk - (double)mh);
@@ -250,7 +257,7 @@ static KickArgs make_args(genga_system *s, bool precheck) {
     const int64_t n = s->n;
     A.x = s->pos; A.y = s->pos + n; A.z = s->pos + 2 * n; A.m = s->mass;
     A.rc = s->rcl[0].rc; A.rc2 = s->rcl[0].rc2; A.pc2 = s->rcl[0].pc2;
-    A.thr = precheck ? s->rcl[0].thr_pc : s->rcl[0].thr_rc;
+    A.thr_rc = s->rcl[0].thr_rc; A.thr_pc = s->rcl[0].thr_pc; A.thr_pc_lo = s->rcl[0].thr_pc_lo;
     A.n = (int)n;
     A.chunk = s->kick_chunk;
     A.part = s->kick_part;
@@ -302,7 +309,8 @@ cudaError_t launch_kick_raw(const KickRaw &k, int num_sms, int max_nchunk, cudaS
     }
     KickArgs A;
     A.x = k.pos; A.y = k.pos + k.n; A.z = k.pos + 2 * (size_t)k.n; A.m = k.mass;
-    A.rc = k.rc; A.rc2 = k.rc2; A.pc2 = nullptr; A.thr = k.thr;
+    A.rc = k.rc; A.rc2 = k.rc2; A.pc2 = nullptr; A.thr_rc = k.thr;
+    A.thr_pc = nullptr; A.thr_pc_lo = nullptr;
     A.n = k.n; A.chunk = chunk; A.part = k.part;
     A.cand = nullptr; A.cand_count = nullptr; A.cand_cap = 0;
     dim3 grid((k.n + kKickThreads - 1) / kKickThreads, nchunk);

@@ -50,14 +50,15 @@ class Stats(C.Structure):
     _fields_ = [("n_candidates", C.c_int64), ("n_pairs", C.c_int64 * 8),
                 ("n_groups", C.c_int64), ("max_group", C.c_int64), ("bs_steps", C.c_int64),
                 ("bs_rejects", C.c_int64), ("kepler_fail", C.c_int64), ("bs_fail", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("bs_max_attempts", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {"n_candidates": self.n_candidates, "n_pairs": list(self.n_pairs),
                 "n_groups": self.n_groups, "max_group": self.max_group,
                 "bs_steps": self.bs_steps, "bs_rejects": self.bs_rejects,
                 "kepler_fail": self.kepler_fail, "bs_fail": self.bs_fail,
-                "kernel_launches": self.kernel_launches}
+                "kernel_launches": self.kernel_launches,
+                "bs_max_attempts": self.bs_max_attempts}
 
 
 _lib = None
