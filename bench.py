@@ -233,7 +233,8 @@ def run_ours(args, dist: Dist) -> dict | None:
             "encounters": {"candidates_per_step": stats["n_candidates"],
                            "pairs_level0": stats["n_pairs"][0],
                            "pairs_level1": stats["n_pairs"][1],
-                           "groups": stats["n_groups"], "max_group": stats["max_group"]},
+                           "groups": stats["n_groups"], "max_group": stats["max_group"],
+                           "bs_max_attempts": stats["bs_max_attempts"]},
         }
         if name == "mixed":
             launches = nl
