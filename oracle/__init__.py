@@ -6,10 +6,10 @@ reference legs may import this package.  It is a plain C implementation
 library.  See ``genga_oracle.c`` for the readings taken where the paper is
 silent.
 """
-from .core import (OracleParams, OracleStats, accel, accel_rows, bs_groups, build, changeover,
-                   detect, drift, energy, group, hc, kick, lib, make_params, precheck, rcrit,
-                   step)
+from .core import (OracleNN, OracleParams, OracleStats, accel, accel_rows, angmom_spin, bs_groups,
+                   build, changeover, detect, drift, energy, group, hc, kick, lib, make_nn,
+                   make_params, precheck, rcrit, step, step_nn)
 
-__all__ = ["OracleParams", "OracleStats", "accel", "accel_rows", "bs_groups", "build",
-           "changeover", "detect", "drift", "energy", "group", "hc", "kick", "lib",
-           "make_params", "precheck", "rcrit", "step"]
+__all__ = ["OracleNN", "OracleParams", "OracleStats", "accel", "accel_rows", "angmom_spin",
+           "bs_groups", "build", "changeover", "detect", "drift", "energy", "group", "hc", "kick",
+           "lib", "make_nn", "make_params", "precheck", "rcrit", "step", "step_nn"]

@@ -86,10 +86,18 @@ def lib():
                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
                                         C.POINTER(OracleStats)]
             L.orc_energy.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D, _D]
+            L.orc_step_nn.restype = C.c_int
+            L.orc_step_nn.argtypes = [C.c_int64, _D, _D, _D, C.POINTER(OracleParams),
+                                      C.POINTER(OracleNN), _D, _D, _D, _D, _D, _D, C.c_int64,
+                                      C.POINTER(OracleStats)]
+            L.orc_angmom_spin.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _D, C.c_double,
+                                          C.c_double, C.c_double, _D, _D]
+            L.orc_sizeof_nn.restype = C.c_int64
             L.orc_sizeof_params.restype = C.c_int64
             L.orc_sizeof_stats.restype = C.c_int64
             assert L.orc_sizeof_params() == C.sizeof(OracleParams)
             assert L.orc_sizeof_stats() == C.sizeof(OracleStats)
+            assert L.orc_sizeof_nn() == C.sizeof(OracleNN)
             _lib = L
     return _lib
 
@@ -214,6 +222,42 @@ def bs_groups(x, v, m, rc_levels, pairs, G, m_star, dt, tol=1e-15, max_steps=100
                                  pairs.shape[0], pairs.ctypes.data_as(_U32), G, m_star, dt, tol,
                                  max_steps, C.byref(st))
     return x, v, int(status), st.as_dict()
+
+
+class OracleNN(C.Structure):
+    _fields_ = [("gr", C.c_int32), ("tides", C.c_int32), ("implicit_max_iter", C.c_int32),
+                ("pad", C.c_int32), ("c_light", C.c_double), ("R_star", C.c_double),
+                ("k2_star", C.c_double), ("tau_star", C.c_double), ("rg2_star", C.c_double)]
+
+
+def make_nn(gr=True, tides=True, c_light=173.1446326846693, R_star=0.0, k2_star=0.0,
+            tau_star=0.0, rg2_star=0.0, implicit_max_iter=10) -> OracleNN:
+    nn = OracleNN()
+    nn.gr, nn.tides, nn.implicit_max_iter = int(gr), int(tides), implicit_max_iter
+    nn.c_light, nn.R_star, nn.k2_star, nn.tau_star, nn.rg2_star = (c_light, R_star, k2_star,
+                                                                   tau_star, rg2_star)
+    return nn
+
+
+def step_nn(x, v, m, params: OracleParams, nn: OracleNN, R, k2, tau, rg2, spin, spin_star,
+            nsteps: int = 1):
+    """Steps with GR/tides; returns (x, v, spin, spin_star, status, stats)."""
+    x, v, m = _f64(x).copy(), _f64(v).copy(), _f64(m)
+    R, k2, tau, rg2 = _f64(R), _f64(k2), _f64(tau), _f64(rg2)
+    spin, spin_star = _f64(spin).copy(), _f64(spin_star).copy()
+    st = OracleStats()
+    status = lib().orc_step_nn(m.shape[0], _d(x), _d(v), _d(m), C.byref(params), C.byref(nn),
+                               _d(R), _d(k2), _d(tau), _d(rg2), _d(spin), _d(spin_star), nsteps,
+                               C.byref(st))
+    return x, v, spin, spin_star, int(status), st.as_dict()
+
+
+def angmom_spin(x, v, m, R, rg2, spin, m_star, R_star, rg2_star, spin_star):
+    L = np.zeros(3)
+    args = [_f64(a) for a in (x, v, m, R, rg2, spin)]
+    lib().orc_angmom_spin(m.shape[0], *[_d(a) for a in args], m_star, R_star, rg2_star,
+                          _d(_f64(spin_star)), _d(L))
+    return L
 
 
 def energy(x, v, m, m_star, G):

@@ -677,6 +677,157 @@ static void senc(step_ctx *cx, int64_t npairs, const uint32_t *pairs, int level,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Non-Newtonian forces (Sec. 3 GR, Sec. 4.1-4.2 tides) applied with the implicit
+ * midpoint rule of Sec. 2.3 (Eq. implicit) over each half kick.
+ *
+ * Readings (the paper gives the formulas, not where they enter the step):
+ *  R15 after each level-0 gravitational half kick, velocities are converted to
+ *      heliocentric u_i = v_i + P/m_star (P = sum m_j v_j), the forces act on u for
+ *      dt/2 by the implicit midpoint rule, and u is converted back with
+ *      v_i = u_i - sum_j m_j u_j / (m_star + sum_j m_j);
+ *  R16 GR: a_PN,i of Eq. apn with mu = G (m_star + m_i), r-dot = x.u/|x|;
+ *  R17 tides: the force F_T of Eq. (Bolmont 2015 Eq. 6, corrected) gives the
+ *      heliocentric acceleration F_T / m_i; spins follow
+ *      d(I_i W_i)/dt = -(m_star/(m_star+m_i)) N_Ti and
+ *      d(I_star W_star)/dt = -sum_j (m_star/(m_star+m_j)) N_Tstar,j, I = rg2 m R^2;
+ *      with this reading total angular momentum (orbit + spins) is conserved
+ *      exactly for one planet;
+ *  R18 the implicit iteration updates u, W_i and W_star together from their
+ *      midpoint values until no component changes by more than 1e-16 of its
+ *      size, at most implicit_max_iter (10) times.                           */
+typedef struct orc_nn {
+    int32_t gr, tides;
+    int32_t implicit_max_iter, pad;
+    double c_light;
+    double R_star, k2_star, tau_star, rg2_star;
+} orc_nn;
+
+/* GR (Eq. apn) and tidal (F_T / m_i) heliocentric acceleration of one body and
+ * the tidal torques N_Ti, N_Tstar (Sec. 4.2), from position x, heliocentric
+ * velocity u and spins W (body) and Ws (star).                              */
+static void nn_terms(const double *x, const double *u, const double *W, const double *Ws,
+                     double mi, double Ri, double k2i, double taui, double G, double m_star,
+                     const orc_nn *nn, double *acc, double *Ni, double *Ns)
+{
+    double r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
+    double r = sqrt(r2);
+    double er[3] = {x[0] / r, x[1] / r, x[2] / r};
+    double rdot = ((x[0] * u[0] + x[1] * u[1]) + x[2] * u[2]) / r;
+    double u2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+    for (int k = 0; k < 3; k++) { acc[k] = 0.0; Ni[k] = 0.0; Ns[k] = 0.0; }
+    if (nn->gr) {
+        double mu = G * (m_star + mi);
+        double eta = m_star * mi / ((m_star + mi) * (m_star + mi));
+        double c2 = nn->c_light * nn->c_light;
+        double pre = -mu / (r2 * c2);
+        double cv = -2.0 * (2.0 - eta) * rdot;
+        double cr = (1.0 + 3.0 * eta) * u2 - 1.5 * eta * rdot * rdot - 2.0 * (2.0 + eta) * mu / r;
+        for (int k = 0; k < 3; k++) acc[k] += pre * (cv * u[k] + cr * er[k]);
+    }
+    if (nn->tides) {
+        double r5 = r2 * r2 * r;
+        double r7 = r5 * r2;
+        double Ri5 = Ri * Ri * Ri * Ri * Ri;
+        double Rs5 = nn->R_star * nn->R_star * nn->R_star * nn->R_star * nn->R_star;
+        double Dti = 3.0 * G * m_star * m_star * Ri5 / r7 * k2i;
+        double Dts = 3.0 * G * mi * mi * Rs5 / r7 * nn->k2_star;
+        double Pti = Dti * taui;
+        double Pts = Dts * nn->tau_star;
+        /* F_T = [-(Dts + Dti) - 2 rdot/r (Pts + Pti)] e_r + Pti (W x e_r) + Pts (Ws x e_r)
+         *       - (Pti + Pts) u / r                                              */
+        double fr = -(Dts + Dti) - 2.0 * rdot / r * (Pts + Pti);
+        double wxe[3] = {W[1] * er[2] - W[2] * er[1], W[2] * er[0] - W[0] * er[2],
+                         W[0] * er[1] - W[1] * er[0]};
+        double sxe[3] = {Ws[1] * er[2] - Ws[2] * er[1], Ws[2] * er[0] - Ws[0] * er[2],
+                         Ws[0] * er[1] - Ws[1] * er[0]};
+        double exu[3] = {er[1] * u[2] - er[2] * u[1], er[2] * u[0] - er[0] * u[2],
+                         er[0] * u[1] - er[1] * u[0]};
+        double rW = (x[0] * W[0] + x[1] * W[1]) + x[2] * W[2];
+        double rWs = (x[0] * Ws[0] + x[1] * Ws[1]) + x[2] * Ws[2];
+        for (int k = 0; k < 3; k++) {
+            double F = fr * er[k] + Pti * wxe[k] + Pts * sxe[k] - (Pti + Pts) * u[k] / r;
+            acc[k] += F / mi;
+            /* N = P [W r - (r.W) e_r - e_r x u] */
+            Ni[k] = Pti * (W[k] * r - rW * er[k] - exu[k]);
+            Ns[k] = Pts * (Ws[k] * r - rWs * er[k] - exu[k]);
+        }
+    }
+}
+
+/* Implicit midpoint of the non-Newtonian forces over dt for all bodies. */
+static void nn_implicit(int64_t n, const double *x, double *v, const double *m, double G,
+                        double m_star, const orc_nn *nn, const double *R, const double *k2,
+                        const double *tau, const double *rg2, double *spin, double *spin_star,
+                        double dt)
+{
+    if (!nn || (!nn->gr && !nn->tides) || n == 0) return;
+    double P[3] = {0.0, 0.0, 0.0}, Mp = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+        for (int k = 0; k < 3; k++) P[k] += m[j] * v[3 * j + k];
+        Mp += m[j];
+    }
+    double *u0 = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *u1 = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *W0 = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *W1 = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) {
+            u0[3 * i + k] = v[3 * i + k] + P[k] / m_star;
+            u1[3 * i + k] = u0[3 * i + k];
+            W0[3 * i + k] = spin[3 * i + k];
+            W1[3 * i + k] = spin[3 * i + k];
+        }
+    double Ws0[3] = {spin_star[0], spin_star[1], spin_star[2]};
+    double Ws1[3] = {Ws0[0], Ws0[1], Ws0[2]};
+    double Is = nn->rg2_star * m_star * nn->R_star * nn->R_star;
+    for (int it = 0; it < nn->implicit_max_iter; it++) {
+        int changed = 0;
+        double dLs[3] = {0.0, 0.0, 0.0};
+        double Wsm[3];
+        for (int k = 0; k < 3; k++) Wsm[k] = 0.5 * (Ws0[k] + Ws1[k]);
+        for (int64_t i = 0; i < n; i++) {
+            double um[3], Wm[3], acc[3], Ni[3], Ns[3];
+            for (int k = 0; k < 3; k++) {
+                um[k] = 0.5 * (u0[3 * i + k] + u1[3 * i + k]);
+                Wm[k] = 0.5 * (W0[3 * i + k] + W1[3 * i + k]);
+            }
+            nn_terms(x + 3 * i, um, Wm, Wsm, m[i], R ? R[i] : 0.0, k2 ? k2[i] : 0.0,
+                     tau ? tau[i] : 0.0, G, m_star, nn, acc, Ni, Ns);
+            double fac = m_star / (m_star + m[i]);
+            double Ii = rg2 ? rg2[i] * m[i] * R[i] * R[i] : 0.0;
+            for (int k = 0; k < 3; k++) {
+                double un = u0[3 * i + k] + dt * acc[k];
+                if (fabs(un - u1[3 * i + k]) > 1e-16 * fabs(un)) changed = 1;
+                u1[3 * i + k] = un;
+                if (nn->tides && Ii > 0.0) {
+                    double Wn = W0[3 * i + k] - dt * fac * Ni[k] / Ii;
+                    if (fabs(Wn - W1[3 * i + k]) > 1e-16 * fabs(Wn)) changed = 1;
+                    W1[3 * i + k] = Wn;
+                }
+                dLs[k] += fac * Ns[k];
+            }
+        }
+        if (nn->tides && Is > 0.0)
+            for (int k = 0; k < 3; k++) {
+                double Wn = Ws0[k] - dt * dLs[k] / Is;
+                if (fabs(Wn - Ws1[k]) > 1e-16 * fabs(Wn)) changed = 1;
+                Ws1[k] = Wn;
+            }
+        if (!changed) break;
+    }
+    double Q[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n; j++)
+        for (int k = 0; k < 3; k++) Q[k] += m[j] * u1[3 * j + k];
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) {
+            v[3 * i + k] = u1[3 * i + k] - Q[k] / (m_star + Mp);
+            spin[3 * i + k] = W1[3 * i + k];
+        }
+    for (int k = 0; k < 3; k++) spin_star[k] = Ws1[k];
+    free(u0); free(u1); free(W0); free(W1);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Direct entry for tests: group the ascending pair list and integrate every
  * group by BS over dt from (x, v) in place, with nlev levels of critical radii
  * rc_levels[l*n + i].  Returns 0, or 2 when a group hit bs_max_steps.        */
@@ -705,8 +856,10 @@ int orc_bs_groups(int64_t n, double *x, double *v, const double *m, const double
 /* ------------------------------------------------------------------------- */
 /* One step of Appendix A (original scheme for slevels == 1, SEnc otherwise).
  * Returns 0, or a bit mask: 1 Kepler non-convergence, 2 BS limit reached.    */
-int orc_step(int64_t n, double *x, double *v, const double *m, const orc_params *p,
-             int64_t nsteps, orc_stats *st)
+static int step_impl(int64_t n, double *x, double *v, const double *m, const orc_params *p,
+                     int64_t nsteps, orc_stats *st, const orc_nn *nn, const double *R,
+                     const double *k2, const double *tau, const double *rg2, double *spin,
+                     double *spin_star)
 {
     step_ctx cx;
     memset(&cx, 0, sizeof(cx));
@@ -731,6 +884,7 @@ int orc_step(int64_t n, double *x, double *v, const double *m, const orc_params 
         }
         st->n_candidates += nc;
         orc_kick(n, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
+        nn_implicit(n, x, v, m, p->G, p->m_star, nn, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
         orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
         memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
         memcpy(vs, v, sizeof(double) * 3 * (size_t)n);
@@ -750,11 +904,47 @@ int orc_step(int64_t n, double *x, double *v, const double *m, const orc_params 
         free(cand);
         orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
         orc_kick(n, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
+        nn_implicit(n, x, v, m, p->G, p->m_star, nn, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
     }
     if (st->kepler_fail) cx.status |= 1;
     for (int l = 0; l < L; l++) free(cx.rcl[l]);
     free(xs); free(vs);
     return cx.status;
+}
+
+int orc_step(int64_t n, double *x, double *v, const double *m, const orc_params *p,
+             int64_t nsteps, orc_stats *st)
+{
+    return step_impl(n, x, v, m, p, nsteps, st, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+}
+
+/* One system with GR and/or tides (R15-R18); spin (3n) and spin_star (3) are
+ * updated in place; R, k2, tau, rg2 are per-body arrays (n).                 */
+int orc_step_nn(int64_t n, double *x, double *v, const double *m, const orc_params *p,
+                const orc_nn *nn, const double *R, const double *k2, const double *tau,
+                const double *rg2, double *spin, double *spin_star, int64_t nsteps, orc_stats *st)
+{
+    return step_impl(n, x, v, m, p, nsteps, st, nn, R, k2, tau, rg2, spin, spin_star);
+}
+
+/* Total angular momentum with spins: sum m_i x_i x v_i + sum I_i W_i + I_s W_s. */
+void orc_angmom_spin(int64_t n, const double *x, const double *v, const double *m,
+                     const double *R, const double *rg2, const double *spin, double m_star,
+                     double R_star, double rg2_star, const double *spin_star, double *L)
+{
+    long double Lx = 0.0L, Ly = 0.0L, Lz = 0.0L;
+    for (int64_t i = 0; i < n; i++) {
+        const double *xi = x + 3 * i, *vi = v + 3 * i;
+        Lx += (long double)m[i] * ((long double)xi[1] * vi[2] - (long double)xi[2] * vi[1]);
+        Ly += (long double)m[i] * ((long double)xi[2] * vi[0] - (long double)xi[0] * vi[2]);
+        Lz += (long double)m[i] * ((long double)xi[0] * vi[1] - (long double)xi[1] * vi[0]);
+        long double I = (long double)rg2[i] * m[i] * R[i] * R[i];
+        Lx += I * spin[3 * i + 0]; Ly += I * spin[3 * i + 1]; Lz += I * spin[3 * i + 2];
+    }
+    long double Is = (long double)rg2_star * m_star * R_star * R_star;
+    L[0] = (double)(Lx + Is * spin_star[0]);
+    L[1] = (double)(Ly + Is * spin_star[1]);
+    L[2] = (double)(Lz + Is * spin_star[2]);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -802,3 +992,4 @@ void orc_energy(int64_t n, const double *x, const double *v, const double *m, do
 /* Size of the parameter and statistics structs, for the loader's layout check. */
 int64_t orc_sizeof_params(void) { return (int64_t)sizeof(orc_params); }
 int64_t orc_sizeof_stats(void) { return (int64_t)sizeof(orc_stats); }
+int64_t orc_sizeof_nn(void) { return (int64_t)sizeof(orc_nn); }
