@@ -185,6 +185,58 @@ int genga_set_predrift(genga_system_t *sys, const double *pos_host, const double
 /* Counters of the last genga_step (or of the last build_encounters / bs).   */
 int genga_get_stats(genga_system_t *sys, genga_stats_t *st);
 
+/* ---- batched ensemble (multi-simulation mode) --------------------------- */
+/* Many independent small systems integrated together by the original hybrid
+ * method (Appendix A, slevels = 1) with the post-Newtonian GR acceleration of
+ * Sec. 3 (Eq. apn) and the constant-time-lag tidal force and spin evolution of
+ * Sec. 4.1-4.2, both applied after each half kick by the implicit midpoint
+ * rule of Sec. 2.3 on heliocentric velocities.  All arrays are device memory
+ * owned by the caller, concatenated over systems (system s = bodies
+ * offsets[s] .. offsets[s+1]-1), vectors component-major over all bodies.     */
+#define GENGA_ENSEMBLE_MAX_N 64
+typedef struct genga_ensemble_desc {
+    int64_t n_systems;
+    const int64_t *offsets;   /* host, n_systems + 1; each system 1..GENGA_ENSEMBLE_MAX_N bodies */
+    double *pos, *vel;        /* 3 x n_total each (heliocentric x, barycentric v per system) */
+    const double *mass;       /* n_total */
+    double *spin;             /* 3 x n_total planet spin vectors (rad / time unit), updated */
+    const double *radius, *k2, *tau, *rg2;  /* n_total: radius, Love number k2, time lag, I/(m R^2) */
+    const double *m_star, *dt;              /* n_systems: central mass, time step */
+    double *star;             /* 8 x n_systems, per system: R, k2, tau, rg2, spin x, y, z, unused;
+                                 the spin is updated */
+    double c_light;           /* speed of light in the caller's units */
+    int32_t gr, tides;        /* switches */
+} genga_ensemble_desc_t;
+typedef struct genga_ensemble genga_ensemble_t;
+
+/* Creates the ensemble on `stream` (cudaStream_t).  params supplies G, n1, n2,
+ * f_pc, bs_tol and the iteration limits (slevels must be 1).  Errors: EINVAL
+ * (bad sizes or pointers), ENOMEM, ECUDA.                                    */
+int genga_ensemble_create(genga_ensemble_t **out, const genga_params_t *params,
+                          const genga_ensemble_desc_t *desc, void *stream);
+void genga_ensemble_destroy(genga_ensemble_t *ens);
+const char *genga_ensemble_last_error(const genga_ensemble_t *ens);
+
+/* Advances every system by nsteps of its own dt in one persistent launch
+ * (captured in a CUDA graph on first use for each nsteps and tile shape, then
+ * replayed).  Synchronises; counters via genga_ensemble_get_stats.          */
+int genga_ensemble_step(genga_ensemble_t *ens, int64_t nsteps);
+
+/* Tile shape: threads per CTA (32 only when every system has <= 32 bodies, 64
+ * or 128) and resident CTAs per SM (1..8).                                   */
+int genga_ensemble_set_tile(genga_ensemble_t *ens, int threads, int ctas_per_sm);
+
+/* Self-tuning (Sec. 5.7's kernel-parameter search): times trial_steps with
+ * each tile shape from the same saved state, restores the state and keeps the
+ * fastest.  threads_out / ctas_out (may be NULL) receive the choice.         */
+int genga_ensemble_autotune(genga_ensemble_t *ens, int64_t trial_steps, int *threads_out,
+                            int *ctas_out);
+
+/* Per-system total angular momentum (orbit + planet spins + star spin), 3
+ * doubles per system into the host array L.  Synchronises.                  */
+int genga_ensemble_angmom(genga_ensemble_t *ens, double *L);
+int genga_ensemble_get_stats(genga_ensemble_t *ens, genga_stats_t *st);
+
 /* ---- allocation-free kick ---------------------------------------------- */
 /* The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory: a caller whose framework's caching allocator

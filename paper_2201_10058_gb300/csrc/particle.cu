@@ -94,81 +94,7 @@ __global__ void hc_apply_kernel(int n, double *pos, const DevCounters *ctr) {
 }
 
 // ---------------------------------------------------------------- FG
-// Stumpff functions c_k(z) = sum_m (-z)^m/(2m+k)!: quarter z until |z| <= 0.1,
-// sum the series for c2 and c3 (ten terms), c0 = 1 - z c2, c1 = 1 - z c3, then
-// undo the quartering with c0(4z) = 2c0^2 - 1, c1(4z) = c0 c1,
-// c2(4z) = c1^2/2, c3(4z) = (c2 + c0 c3)/4.
-__device__ __forceinline__ void stumpff(double z, double &c0, double &c1, double &c2, double &c3) {
-    int q = 0;
-    while (fabs(z) > 0.1 && q < 60) { z *= 0.25; q++; }
-    // 1/(2m+2)! and 1/(2m+3)!, m = 0..9
-    const double ic2[10] = {1.0 / 2.0, 1.0 / 24.0, 1.0 / 720.0, 1.0 / 40320.0, 1.0 / 3628800.0,
-                            1.0 / 479001600.0, 1.0 / 87178291200.0, 1.0 / 20922789888000.0,
-                            1.0 / 6402373705728000.0, 1.0 / 2432902008176640000.0};
-    const double ic3[10] = {1.0 / 6.0, 1.0 / 120.0, 1.0 / 5040.0, 1.0 / 362880.0,
-                            1.0 / 39916800.0, 1.0 / 6227020800.0, 1.0 / 1307674368000.0,
-                            1.0 / 355687428096000.0, 1.0 / 121645100408832000.0,
-                            1.0 / 51090942171709440000.0};
-    double s2 = 0.0, s3 = 0.0;
-#pragma unroll
-    for (int m = 9; m >= 0; m--) {
-        s2 = ic2[m] - z * s2;
-        s3 = ic3[m] - z * s3;
-    }
-    double C2 = s2, C3 = s3, C0 = 1.0 - z * C2, C1 = 1.0 - z * C3;
-    for (int k = 0; k < q; k++) {
-        const double n3 = 0.25 * (C2 + C0 * C3);
-        const double n2 = 0.5 * C1 * C1;
-        const double n1 = C0 * C1;
-        const double n0 = 2.0 * C0 * C0 - 1.0;
-        C0 = n0; C1 = n1; C2 = n2; C3 = n3;
-    }
-    c0 = C0; c1 = C1; c2 = C2; c3 = C3;
-}
-
-// Kepler drift of one body over dt about mu.  Universal variable s with
-// beta = 2 mu / r0 - v0^2, G_k = s^k c_k(beta s^2):
-//   t(s) = r0 G1 + u G2 + mu G3 (u = x0.v0),  dt/ds = r(s) = r0 G0 + u G1 + mu G2,
-//   f - 1 = -mu G2 / r0, g = dt - mu G3, fdot = -mu G1/(r r0), gdot - 1 = -mu G2 / r.
-// Newton from s = dt/r0 - u dt^2/(2 r0^3); converged when |ds| <= 1e-15 |s|, or
-// when rounding stalls the update at |ds| <= 1e-12 |s| without halving it.
-__device__ bool kepler_drift(double &x, double &y, double &z, double &vx, double &vy, double &vz,
-                             double mu, double dt, int max_iter) {
-    const double r0 = sqrt(x * x + y * y + z * z);
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double u = x * vx + y * vy + z * vz;
-    const double beta = 2.0 * mu / r0 - v2;
-    double s = dt / r0 - (u * dt * dt) / (2.0 * r0 * r0 * r0);
-    double c0, c1, c2, c3, ds_prev = 0.0;
-    bool ok = false;
-    for (int it = 0; it < max_iter; it++) {
-        stumpff(beta * s * s, c0, c1, c2, c3);
-        const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
-        const double t = r0 * G1 + u * G2 + mu * G3;
-        const double rr = r0 * c0 + u * G1 + mu * G2;
-        const double ds = (t - dt) / rr;
-        s -= ds;
-        const double ads = fabs(ds), as = fabs(s);
-        if (ads <= 1e-15 * as) { ok = true; break; }
-        if (it > 0 && ads <= 1e-12 * as && ads > 0.5 * ds_prev) { ok = true; break; }
-        ds_prev = ads;
-    }
-    stumpff(beta * s * s, c0, c1, c2, c3);
-    const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
-    const double r = r0 * c0 + u * G1 + mu * G2;
-    const double fm1 = -mu * G2 / r0;
-    const double g = dt - mu * G3;
-    const double fd = -mu * G1 / (r * r0);
-    const double gdm1 = -mu * G2 / r;
-    const double x0 = x, y0 = y, z0 = z, vx0 = vx, vy0 = vy, vz0 = vz;
-    x = x0 + (fm1 * x0 + g * vx0);
-    y = y0 + (fm1 * y0 + g * vy0);
-    z = z0 + (fm1 * z0 + g * vz0);
-    vx = vx0 + (fd * x0 + gdm1 * vx0);
-    vy = vy0 + (fd * y0 + gdm1 * vy0);
-    vz = vz0 + (fd * z0 + gdm1 * vz0);
-    return ok;
-}
+// kepler_drift() and stumpff() live in common.cuh (shared with the ensemble).
 
 __global__ void drift_kernel(int n, double *pos, double *vel, double *pre_pos, double *pre_vel,
                              double mu, double dt, int max_iter, const int *bodies, int nb,

@@ -26,7 +26,9 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_hc", "genga_drift", "genga_build_encounters", "genga_bs", "genga_step",
             "genga_step_host", "genga_energy", "genga_get_candidates", "genga_get_pairs",
             "genga_get_groups", "genga_get_rcrit", "genga_set_predrift", "genga_get_stats",
-            "genga_kick_static"]
+            "genga_kick_static", "genga_ensemble_create", "genga_ensemble_destroy",
+            "genga_ensemble_last_error", "genga_ensemble_step", "genga_ensemble_set_tile",
+            "genga_ensemble_autotune", "genga_ensemble_angmom", "genga_ensemble_get_stats"]
 
 KICK_STATIC_MAX_N = 279616
 
@@ -44,6 +46,15 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("kepler_max_iter", C.c_int32),
                 ("bs_max_steps", C.c_int32), ("reserved", C.c_int32),
                 ("cand_capacity", C.c_int64), ("pair_capacity", C.c_int64)]
+
+
+class EnsembleDesc(C.Structure):
+    _fields_ = [("n_systems", C.c_int64), ("offsets", C.c_void_p), ("pos", C.c_void_p),
+                ("vel", C.c_void_p), ("mass", C.c_void_p), ("spin", C.c_void_p),
+                ("radius", C.c_void_p), ("k2", C.c_void_p), ("tau", C.c_void_p),
+                ("rg2", C.c_void_p), ("m_star", C.c_void_p), ("dt", C.c_void_p),
+                ("star", C.c_void_p), ("c_light", C.c_double), ("gr", C.c_int32),
+                ("tides", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -111,8 +122,20 @@ def load(build_if_missing: bool = True):
         L.genga_get_stats.argtypes = [sysp, _P(Stats)]
         L.genga_kick_static.argtypes = [C.c_int64, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int,
                                         _VP, _VP, _VP]
+        L.genga_ensemble_create.argtypes = [_P(_VP), _P(Params), _P(EnsembleDesc), _VP]
+        L.genga_ensemble_destroy.argtypes = [_VP]
+        L.genga_ensemble_destroy.restype = None
+        L.genga_ensemble_last_error.argtypes = [_VP]
+        L.genga_ensemble_last_error.restype = C.c_char_p
+        L.genga_ensemble_step.argtypes = [_VP, C.c_int64]
+        L.genga_ensemble_set_tile.argtypes = [_VP, C.c_int, C.c_int]
+        L.genga_ensemble_autotune.argtypes = [_VP, C.c_int64, _P(C.c_int), _P(C.c_int)]
+        L.genga_ensemble_angmom.argtypes = [_VP, _VP]
+        L.genga_ensemble_get_stats.argtypes = [_VP, _P(Stats)]
+        void_fns = ("genga_default_params", "genga_destroy", "genga_last_error",
+                    "genga_ensemble_destroy", "genga_ensemble_last_error")
         for name in EXPORTED:
-            if name not in ("genga_default_params", "genga_destroy", "genga_last_error"):
+            if name not in void_fns:
                 getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -267,3 +290,75 @@ class System:
         st = Stats()
         self._check(self._lib.genga_get_stats(self._h, C.byref(st)))
         return st.as_dict()
+
+
+class Ensemble:
+    """Batched ensemble (include/genga.h, genga_ensemble_*) on torch CUDA tensors.
+
+    `wl` is a workloads.ensemble.Ensemble (numpy); the tensors are copied to the
+    device and kept here: pos/vel/spin as (3, n_total), star as (S, 8)."""
+
+    def __init__(self, wl, params: Params | None = None, gr: bool = True, tides: bool = True,
+                 stream=None):
+        import torch
+        self._lib = load()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+        self.pos, self.vel, self.spin = T(wl.x.T), T(wl.v.T), T(wl.spin.T)
+        self.mass, self.radius, self.k2, self.tau, self.rg2 = (T(wl.m), T(wl.R), T(wl.k2),
+                                                                T(wl.tau), T(wl.rg2))
+        self.m_star, self.dt, self.star = T(wl.m_star), T(wl.dt), T(wl.star)
+        self.offsets = np.ascontiguousarray(wl.offsets, dtype=np.int64)
+        p = params if params is not None else default_params(G=wl.G)
+        d = EnsembleDesc()
+        d.n_systems = wl.n_systems
+        d.offsets = self.offsets.ctypes.data
+        for name in ("pos", "vel", "mass", "spin", "radius", "k2", "tau", "rg2", "m_star", "dt",
+                     "star"):
+            setattr(d, name, getattr(self, name).data_ptr())
+        d.c_light, d.gr, d.tides = wl.c_light, int(gr), int(tides)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _VP()
+        rc = self._lib.genga_ensemble_create(C.byref(h), C.byref(p), C.byref(d),
+                                             _VP(self.stream.cuda_stream))
+        if rc != 0:
+            raise GengaError(rc, "genga_ensemble_create failed")
+        self._h = h
+        self.n_systems = wl.n_systems
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = self._lib.genga_ensemble_last_error(self._h)
+            raise GengaError(rc, msg.decode() if msg else "")
+
+    def step(self, nsteps: int = 1):
+        self._check(self._lib.genga_ensemble_step(self._h, nsteps))
+
+    def set_tile(self, threads: int, ctas_per_sm: int):
+        self._check(self._lib.genga_ensemble_set_tile(self._h, threads, ctas_per_sm))
+
+    def autotune(self, trial_steps: int = 20):
+        t, c = C.c_int(), C.c_int()
+        self._check(self._lib.genga_ensemble_autotune(self._h, trial_steps, C.byref(t), C.byref(c)))
+        return t.value, c.value
+
+    def angmom(self) -> np.ndarray:
+        out = np.zeros((self.n_systems, 3))
+        self._check(self._lib.genga_ensemble_angmom(self._h, _np_ptr(out)))
+        return out
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self._lib.genga_ensemble_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.genga_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
