@@ -105,11 +105,14 @@ def test_ensemble_close_encounter_inside_a_system(cuda_lib):
     the in-CTA detection, grouping and Bulirsch-Stoer run and match the oracle."""
     g = cuda_lib
     wl = ensemble(6, seed=99, nmin=8, nmax=12)
-    # put planet 1 of every system just outside planet 0 on a nearly identical orbit
+    # planet 1 of every system 4% outside planet 0 in the same direction, on a
+    # circular orbit: about 1.5 mutual Hill radii apart, inside r_crit
     for s in range(wl.n_systems):
         a = wl.offsets[s]
-        wl.x[a + 1] = wl.x[a] * 1.003
-        wl.v[a + 1] = wl.v[a] * (1.0 / np.sqrt(1.003))
+        x1 = wl.x[a] * 1.04
+        wl.x[a + 1] = x1
+        vc = np.sqrt(wl.G * (wl.m_star[s] + wl.m[a + 1]) / np.linalg.norm(x1))
+        wl.v[a + 1] = vc * np.cross([0.0, 0.0, 1.0], x1 / np.linalg.norm(x1))
     ens = g.Ensemble(wl, g.default_params(G=wl.G))
     ens.step(30)
     st = ens.stats()
