@@ -8,8 +8,10 @@ silent.
 """
 from .core import (OracleNN, OracleParams, OracleStats, accel, accel_rows, angmom_spin, bs_groups,
                    build, changeover, detect, drift, energy, group, hc, kick, lib, make_nn,
-                   make_params, precheck, rcrit, step, step_nn)
+                   make_params, precheck, rcrit, step, step_frozen, step_nn,
+                   step_record)
 
 __all__ = ["OracleNN", "OracleParams", "OracleStats", "accel", "accel_rows", "angmom_spin",
            "bs_groups", "build", "changeover", "detect", "drift", "energy", "group", "hc", "kick",
-           "lib", "make_nn", "make_params", "precheck", "rcrit", "step", "step_nn"]
+           "lib", "make_nn", "make_params", "precheck", "rcrit", "step", "step_frozen",
+           "step_nn", "step_record"]

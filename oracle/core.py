@@ -93,6 +93,12 @@ def lib():
             L.orc_angmom_spin.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _D, C.c_double,
                                           C.c_double, C.c_double, _D, _D]
             L.orc_sizeof_nn.restype = C.c_int64
+            L.orc_step_record.restype = C.c_int
+            L.orc_step_record.argtypes = [C.c_int64, _D, _D, _D, C.POINTER(OracleParams), _D, _U32,
+                                          C.c_int64, _I64]
+            L.orc_step_frozen.restype = C.c_int
+            L.orc_step_frozen.argtypes = [C.c_int64, _D, _D, _D, C.POINTER(OracleParams), _D,
+                                          C.c_int64, _U32, _D, _D, _D]
             L.orc_sizeof_params.restype = C.c_int64
             L.orc_sizeof_stats.restype = C.c_int64
             assert L.orc_sizeof_params() == C.sizeof(OracleParams)
@@ -258,6 +264,39 @@ def angmom_spin(x, v, m, R, rg2, spin, m_star, R_star, rg2_star, spin_star):
     lib().orc_angmom_spin(m.shape[0], *[_d(a) for a in args], m_star, R_star, rg2_star,
                           _d(_f64(spin_star)), _d(L))
     return L
+
+
+def step_record(x, v, m, params: OracleParams):
+    """One step (original scheme); returns (x, v, rc, pairs, status)."""
+    x, v, m = _f64(x).copy(), _f64(v).copy(), _f64(m)
+    n = m.shape[0]
+    rc = np.zeros(n)
+    cap = 4096
+    while True:
+        xx, vv = x.copy(), v.copy()
+        pairs = np.zeros((cap, 2), dtype=np.uint32)
+        npairs = C.c_int64()
+        st = lib().orc_step_record(n, _d(xx), _d(vv), _d(m), C.byref(params), _d(rc),
+                                   pairs.ctypes.data_as(_U32), cap, C.byref(npairs))
+        if npairs.value <= cap:
+            return xx, vv, rc, pairs[:npairs.value].copy(), int(st)
+        cap = npairs.value
+
+
+def step_frozen(x, v, m, params: OracleParams, rc, pairs, dx=None, dv=None, dm=None):
+    """One step with frozen rc/pairs; with tangents when dx is given.
+    Returns (x, v, dx, dv, status)."""
+    x, v, m, rc = _f64(x).copy(), _f64(v).copy(), _f64(m), _f64(rc)
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    if dx is not None:
+        dx, dv, dm = _f64(dx).copy(), _f64(dv).copy(), _f64(dm)
+        st = lib().orc_step_frozen(m.shape[0], _d(x), _d(v), _d(m), C.byref(params), _d(rc),
+                                   pairs.shape[0], pairs.ctypes.data_as(_U32), _d(dx), _d(dv),
+                                   _d(dm))
+    else:
+        st = lib().orc_step_frozen(m.shape[0], _d(x), _d(v), _d(m), C.byref(params), _d(rc),
+                                   pairs.shape[0], pairs.ctypes.data_as(_U32), None, None, None)
+    return x, v, dx, dv, int(st)
 
 
 def energy(x, v, m, m_star, G):

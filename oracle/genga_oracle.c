@@ -948,6 +948,345 @@ void orc_angmom_spin(int64_t n, const double *x, const double *v, const double *
 }
 
 /* ------------------------------------------------------------------------- */
+/* Frozen-encounter steps and their tangent-linear (forward-mode) derivative,
+ * for the adjoint configuration.  Readings:
+ *  R20 a step with frozen encounters uses a given level-0 rc array and a given
+ *      ascending pair list instead of Rcrit, pre-check and detection (the
+ *      original scheme, slevels = 1); there is no derivative through rc;
+ *  R21 the derivative of the changeover function is taken (dK/dr), i.e. the
+ *      derivative of the kick and BS forces as defined by R4/R5;
+ *  R22 the tangent of the Kepler drift and of each BS group is the solution of
+ *      the variational equations integrated alongside the state by the same
+ *      Bulirsch-Stoer scheme, with error control on the state only.          */
+
+/* dK/dr of the changeover function R4 (0 outside the band). */
+static double changeover_dr(double r, double rc)
+{
+    double y = (r / rc - 0.1) / 0.9;
+    if (y <= 0.0 || y >= 1.0) return 0.0;
+    double D = 2.0 * y * y - 2.0 * y + 1.0;
+    return 2.0 * y * (1.0 - y) / (D * D) / (0.9 * rc);
+}
+
+/* M = w (I/r^3 - 3 d d^T / r^5) + w' d d^T / r^4 applied to e (3-vector). */
+static void pair_tensor_apply(const double *d, double r, double w, double wp, const double *e,
+                              double *out)
+{
+    double r2 = r * r, r3 = r2 * r;
+    double de = (d[0] * e[0] + d[1] * e[1]) + d[2] * e[2];
+    for (int k = 0; k < 3; k++)
+        out[k] = w * (e[k] / r3 - 3.0 * d[k] * de / (r3 * r2)) + wp * d[k] * de / (r2 * r2);
+}
+
+/* Tangent of the kick acceleration: da_i = G sum_j [m_j M_ij (dx_j - dx_i) + dm_j K d/r^3]. */
+static void kick_tl(int64_t n, const double *x, const double *m, const double *rc, double G,
+                    const double *dx, const double *dm, double *da)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double d[3] = {x[3 * j] - x[3 * i], x[3 * j + 1] - x[3 * i + 1], x[3 * j + 2] - x[3 * i + 2]};
+            double r = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+            double rcij = pair_rc(rc, i, j);
+            double K = orc_changeover(r, rcij);
+            double Kp = changeover_dr(r, rcij);
+            double e[3] = {dx[3 * j] - dx[3 * i], dx[3 * j + 1] - dx[3 * i + 1], dx[3 * j + 2] - dx[3 * i + 2]};
+            double Me[3];
+            pair_tensor_apply(d, r, K, Kp, e, Me);
+            double r3 = r * r * r;
+            for (int k = 0; k < 3; k++) s[k] += m[j] * Me[k] + dm[j] * K * d[k] / r3;
+        }
+        for (int k = 0; k < 3; k++) da[3 * i + k] = G * s[k];
+    }
+}
+
+/* Generic Bulirsch-Stoer (same scheme as bs_integrate) for dim values, of
+ * which the first nerr enter the error norm.                                */
+typedef void (*bs_fn)(const void *ctx, const double *y, double *f);
+
+static int bs_generic(bs_fn fn, const void *ctx, double *y, int64_t dim, int64_t nerr, double dt,
+                      double tol, int max_steps)
+{
+    double *f0 = (double *)malloc(sizeof(double) * (size_t)dim);
+    double *T = (double *)malloc(sizeof(double) * (size_t)dim * BS_KMAX);
+    double *yk = (double *)malloc(sizeof(double) * (size_t)dim);
+    double *zm = (double *)malloc(sizeof(double) * (size_t)dim);
+    double *zn = (double *)malloc(sizeof(double) * (size_t)dim);
+    double *fz = (double *)malloc(sizeof(double) * (size_t)dim);
+    double *sc = (double *)malloc(sizeof(double) * (size_t)dim);
+    double t = 0.0, H = dt;
+    int attempts = 0, status = 0;
+    while (t < dt) {
+        if (attempts >= max_steps) { status = 1; break; }
+        attempts++;
+        if (H > dt - t) H = dt - t;
+        fn(ctx, y, f0);
+        for (int64_t c = 0; c < dim; c++) sc[c] = fabs(y[c]) + fabs(H * f0[c]) + 1e-300;
+        int accepted = 0, kconv = 0;
+        for (int k = 0; k < BS_KMAX; k++) {
+            int nk = 2 * (k + 1);
+            double h = H / nk;
+            for (int64_t c = 0; c < dim; c++) { zm[c] = y[c]; zn[c] = y[c] + h * f0[c]; }
+            for (int mm = 1; mm < nk; mm++) {
+                fn(ctx, zn, fz);
+                for (int64_t c = 0; c < dim; c++) {
+                    double tt = zm[c] + 2.0 * h * fz[c];
+                    zm[c] = zn[c];
+                    zn[c] = tt;
+                }
+            }
+            fn(ctx, zn, fz);
+            for (int64_t c = 0; c < dim; c++) yk[c] = 0.5 * (zn[c] + zm[c] + h * fz[c]);
+            double err = 0.0;
+            for (int64_t c = 0; c < dim; c++) {
+                double prev = T[c];
+                double cur = yk[c];
+                T[c] = cur;
+                for (int j = 1; j <= k; j++) {
+                    double ratio = (double)nk / (double)(2 * (k - j + 1));
+                    double nxt = cur + (cur - prev) / (ratio * ratio - 1.0);
+                    prev = T[j * dim + c];
+                    T[j * dim + c] = nxt;
+                    cur = nxt;
+                }
+                if (k >= 1 && c < nerr) {
+                    double e = fabs(T[k * dim + c] - T[(k - 1) * dim + c]) / sc[c];
+                    if (e > err) err = e;
+                }
+            }
+            if (k >= 1 && err <= tol) { accepted = 1; kconv = k; break; }
+        }
+        if (accepted) {
+            for (int64_t c = 0; c < dim; c++) y[c] = T[kconv * dim + c];
+            t += H;
+            if (kconv < 4) H *= 1.5;
+        } else {
+            H *= 0.5;
+        }
+    }
+    free(f0); free(T); free(yk); free(zm); free(zn); free(fz); free(sc);
+    return status;
+}
+
+/* Group state and its tangent: y = [6 nm state | 6 nm tangent]. */
+typedef struct tl_group {
+    bs_group g;             /* members, partners, masses, rc (level 0), G, mu */
+    const double *dm;       /* mass tangents (global) */
+} tl_group;
+
+static void tl_group_deriv(const void *ctxp, const double *y, double *f)
+{
+    const tl_group *ctx = (const tl_group *)ctxp;
+    const bs_group *g = &ctx->g;
+    int64_t nm = g->nm;
+    bs_deriv(g, y, f);                           /* state part */
+    const double *ty = y + 6 * nm;
+    double *tf = f + 6 * nm;
+    for (int64_t a = 0; a < nm; a++) {
+        const double *xa = y + 6 * a;
+        double r = sqrt((xa[0] * xa[0] + xa[1] * xa[1]) + xa[2] * xa[2]);
+        double acc[3];
+        /* star: d(-mu x/r^3) = -mu (I/r^3 - 3 x x^T / r^5) dx */
+        double xs[3] = {xa[0], xa[1], xa[2]};
+        pair_tensor_apply(xs, r, -g->mu, 0.0, ty + 6 * a, acc);
+        int64_t ia = g->mem[a];
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int64_t q = g->poff[a]; q < g->poff[a + 1]; q++) {
+            int64_t b = g->plist[q], ib = g->mem[b];
+            const double *xb = y + 6 * b;
+            double d[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
+            double dd = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+            double rcij = g->rcl[0][ia] > g->rcl[0][ib] ? g->rcl[0][ia] : g->rcl[0][ib];
+            double W = 1.0 - orc_changeover(dd, rcij);
+            double Wp = -changeover_dr(dd, rcij);
+            double e[3] = {ty[6 * b] - ty[6 * a], ty[6 * b + 1] - ty[6 * a + 1], ty[6 * b + 2] - ty[6 * a + 2]};
+            double Me[3];
+            pair_tensor_apply(d, dd, W, Wp, e, Me);
+            double r3 = dd * dd * dd;
+            for (int k = 0; k < 3; k++) s[k] += g->m[ib] * Me[k] + ctx->dm[ib] * W * d[k] / r3;
+        }
+        for (int k = 0; k < 3; k++) {
+            tf[6 * a + k] = ty[6 * a + 3 + k];
+            tf[6 * a + 3 + k] = acc[k] + g->G * s[k];
+        }
+    }
+}
+
+/* One step of the original scheme with frozen rc and pairs (R20); with the
+ * tangent (dx, dv, dm) when dx != NULL (R21, R22).  rc: n; pairs ascending.  */
+static int frozen_step(int64_t n, double *x, double *v, const double *m, const orc_params *p,
+                       const double *rc, int64_t npairs, const uint32_t *pairs, double *dx,
+                       double *dv, const double *dm)
+{
+    double dt = p->dt, h = 0.5 * dt, G = p->G, mu = p->G * p->m_star;
+    size_t N3 = 3 * (size_t)(n > 0 ? n : 1);
+    double *acc = (double *)malloc(sizeof(double) * N3);
+    double *da = (double *)malloc(sizeof(double) * N3);
+    double *xs = (double *)malloc(sizeof(double) * N3);
+    double *vs = (double *)malloc(sizeof(double) * N3);
+    int status = 0;
+    /* Kick(dt/2) */
+    orc_accel(n, x, m, rc, G, acc, p->nthreads);
+    if (dx) {
+        kick_tl(n, x, m, rc, G, dx, dm, da);
+        for (size_t c = 0; c < 3 * (size_t)n; c++) dv[c] += h * da[c];
+    }
+    for (size_t c = 0; c < 3 * (size_t)n; c++) v[c] += h * acc[c];
+    /* HC(dt/2) */
+    if (dx) {
+        double Q[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; j++)
+            for (int k = 0; k < 3; k++) Q[k] += dm[j] * v[3 * j + k] + m[j] * dv[3 * j + k];
+        for (int64_t i = 0; i < n; i++)
+            for (int k = 0; k < 3; k++) dx[3 * i + k] += h * Q[k] / p->m_star;
+    }
+    orc_hc(n, x, v, m, p->m_star, h);
+    memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
+    memcpy(vs, v, sizeof(double) * 3 * (size_t)n);
+    /* FG(dt) for everybody (members are overwritten by BS below) */
+    int64_t *label = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    orc_group(n, npairs, pairs, label);
+    if (orc_fg(n, x, v, mu, dt, p->kepler_max_iter)) status |= 1;
+    if (dx) {
+        /* tangent of the Kepler drift of non-members: variational equations */
+        for (int64_t i = 0; i < n; i++) {
+            if (label[i] >= 0) continue;
+            int64_t mem = i, poff[2] = {0, 0}, plist = 0;
+            bs_group g;
+            g.nm = 1; g.mem = &mem; g.poff = poff; g.plist = &plist; g.m = m;
+            const double *rcl[1] = {rc};
+            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu;
+            tl_group ctx; ctx.g = g; ctx.dm = dm;
+            double y[12];
+            for (int k = 0; k < 3; k++) {
+                y[k] = xs[3 * i + k]; y[3 + k] = vs[3 * i + k];
+                y[6 + k] = dx[3 * i + k]; y[9 + k] = dv[3 * i + k];
+            }
+            if (bs_generic(tl_group_deriv, &ctx, y, 12, 6, dt, p->bs_tol, p->bs_max_steps)) status |= 2;
+            for (int k = 0; k < 3; k++) { dx[3 * i + k] = y[6 + k]; dv[3 * i + k] = y[9 + k]; }
+        }
+    }
+    /* BS groups from the pre-drift state (with tangents) */
+    if (npairs > 0) {
+        int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+        int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * npairs + 1));
+        if (build_partners(n, npairs, pairs, off, list) != 0) status |= 4;
+        int64_t *loc = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+        int64_t *gsize = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+        for (int64_t i = 0; i < n; i++)
+            if (label[i] >= 0) loc[i] = gsize[label[i]]++;
+        for (int64_t g0 = 0; g0 < n; g0++) {
+            if (gsize[g0] == 0) continue;
+            int64_t nm = gsize[g0];
+            int64_t *mem = (int64_t *)malloc(sizeof(int64_t) * (size_t)nm);
+            int64_t *poff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nm + 1));
+            for (int64_t i = g0, c = 0; c < nm; i++)
+                if (label[i] == g0) mem[c++] = i;
+            poff[0] = 0;
+            for (int64_t a = 0; a < nm; a++) poff[a + 1] = poff[a] + (off[mem[a] + 1] - off[mem[a]]);
+            int64_t *plist = (int64_t *)malloc(sizeof(int64_t) * (size_t)(poff[nm] > 0 ? poff[nm] : 1));
+            for (int64_t a = 0; a < nm; a++)
+                for (int64_t q = off[mem[a]], c = 0; q < off[mem[a] + 1]; q++, c++)
+                    plist[poff[a] + c] = loc[list[q]];
+            bs_group g;
+            const double *rcl[1] = {rc};
+            g.nm = nm; g.mem = mem; g.poff = poff; g.plist = plist; g.m = m;
+            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu;
+            int64_t dim = dx ? 12 * nm : 6 * nm;
+            double *y = (double *)malloc(sizeof(double) * (size_t)dim);
+            for (int64_t a = 0; a < nm; a++)
+                for (int k = 0; k < 3; k++) {
+                    y[6 * a + k] = xs[3 * mem[a] + k];
+                    y[6 * a + 3 + k] = vs[3 * mem[a] + k];
+                    if (dx) {
+                        y[6 * nm + 6 * a + k] = dx[3 * mem[a] + k];
+                        y[6 * nm + 6 * a + 3 + k] = dv[3 * mem[a] + k];
+                    }
+                }
+            int fail;
+            if (dx) {
+                tl_group ctx; ctx.g = g; ctx.dm = dm;
+                fail = bs_generic(tl_group_deriv, &ctx, y, dim, 6 * nm, dt, p->bs_tol, p->bs_max_steps);
+            } else {
+                int64_t a1 = 0, r1 = 0, m1 = 0;
+                fail = bs_integrate(&g, y, dt, p->bs_tol, p->bs_max_steps, &a1, &r1, &m1);
+            }
+            if (fail) status |= 2;
+            for (int64_t a = 0; a < nm; a++)
+                for (int k = 0; k < 3; k++) {
+                    x[3 * mem[a] + k] = y[6 * a + k];
+                    v[3 * mem[a] + k] = y[6 * a + 3 + k];
+                    if (dx) {
+                        dx[3 * mem[a] + k] = y[6 * nm + 6 * a + k];
+                        dv[3 * mem[a] + k] = y[6 * nm + 6 * a + 3 + k];
+                    }
+                }
+            free(y); free(plist); free(poff); free(mem);
+        }
+        free(gsize); free(loc); free(list); free(off);
+    }
+    free(label);
+    /* HC(dt/2) */
+    if (dx) {
+        double Q[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; j++)
+            for (int k = 0; k < 3; k++) Q[k] += dm[j] * v[3 * j + k] + m[j] * dv[3 * j + k];
+        for (int64_t i = 0; i < n; i++)
+            for (int k = 0; k < 3; k++) dx[3 * i + k] += h * Q[k] / p->m_star;
+    }
+    orc_hc(n, x, v, m, p->m_star, h);
+    /* Kick(dt/2) */
+    orc_accel(n, x, m, rc, G, acc, p->nthreads);
+    if (dx) {
+        kick_tl(n, x, m, rc, G, dx, dm, da);
+        for (size_t c = 0; c < 3 * (size_t)n; c++) dv[c] += h * da[c];
+    }
+    for (size_t c = 0; c < 3 * (size_t)n; c++) v[c] += h * acc[c];
+    free(acc); free(da); free(xs); free(vs);
+    return status;
+}
+
+/* One normal step (slevels = 1) that also reports its level-0 rc (n values)
+ * and encounter pairs (ascending, at most cap; *npairs = total).            */
+int orc_step_record(int64_t n, double *x, double *v, const double *m, const orc_params *p,
+                    double *rc_out, uint32_t *pairs_out, int64_t cap, int64_t *npairs)
+{
+    double dt = p->dt;
+    orc_rcrit(n, x, v, m, p->m_star, dt, p->n1, p->n2, rc_out);
+    int64_t nc = orc_precheck(n, x, rc_out, p->f_pc, NULL, 0);
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)(nc > 0 ? nc : 1));
+    orc_precheck(n, x, rc_out, p->f_pc, cand, nc);
+    /* detection needs the pre- and post-drift positions of this step */
+    double *xa = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *va = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    memcpy(xa, x, sizeof(double) * 3 * (size_t)n);
+    memcpy(va, v, sizeof(double) * 3 * (size_t)n);
+    orc_kick(n, xa, m, rc_out, p->G, 0.5 * dt, va, p->nthreads);
+    orc_hc(n, xa, va, m, p->m_star, 0.5 * dt);
+    double *xb = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *vb = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    memcpy(xb, xa, sizeof(double) * 3 * (size_t)n);
+    memcpy(vb, va, sizeof(double) * 3 * (size_t)n);
+    orc_fg(n, xb, vb, p->G * p->m_star, dt, p->kepler_max_iter);
+    uint32_t *enc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)(nc > 0 ? nc : 1));
+    int64_t ne = orc_detect(nc, cand, xa, xb, rc_out, enc);
+    *npairs = ne;
+    for (int64_t k = 0; k < ne && k < cap; k++) { pairs_out[2 * k] = enc[2 * k]; pairs_out[2 * k + 1] = enc[2 * k + 1]; }
+    int st = frozen_step(n, x, v, m, p, rc_out, ne, enc, NULL, NULL, NULL);
+    free(cand); free(xa); free(va); free(xb); free(vb); free(enc);
+    return st;
+}
+
+/* One step with frozen rc and pairs; with the tangent when dx != NULL.       */
+int orc_step_frozen(int64_t n, double *x, double *v, const double *m, const orc_params *p,
+                    const double *rc, int64_t npairs, const uint32_t *pairs, double *dx,
+                    double *dv, const double *dm)
+{
+    return frozen_step(n, x, v, m, p, rc, npairs, pairs, dx, dv, dm);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Total energy (Eq. H = Ha + Hb + Hc, the K terms summing to the full pair
  * potential) and angular momentum sum_i m_i x_i x v_i, in long double with
  * Kahan summation.                                                          */
