@@ -185,6 +185,38 @@ int genga_set_predrift(genga_system_t *sys, const double *pos_host, const double
 /* Counters of the last genga_step (or of the last build_encounters / bs).   */
 int genga_get_stats(genga_system_t *sys, genga_stats_t *st);
 
+/* ---- adjoint of kick-drift-kick steps with frozen encounters ------------ */
+/* Reverse-mode derivative of nsteps steps of the original scheme (Appendix A,
+ * slevels = 1) with every step's level-0 critical radii and encounter pairs
+ * frozen to those of a recorded forward run (no derivative through rc).  The
+ * kick and Bulirsch-Stoer force derivatives include dK/dr of the changeover
+ * function; the Kepler drift uses its exact state-transition matrix; each
+ * encounter group's Bulirsch-Stoer step is differentiated through its
+ * continuous adjoint, integrated backwards by the same scheme.  Checkpoints
+ * of the state every `checkpoint_every` steps bound the memory; the backward
+ * pass recomputes each segment from its checkpoint.                          */
+
+/* Records a forward run: saves the current state as the initial state, runs
+ * nsteps normal steps (leaving the final state in pos/vel) and keeps each
+ * step's rc and pairs and a checkpoint every checkpoint_every steps.
+ * Errors: EINVAL (slevels != 1), the errors of genga_step.                  */
+int genga_adjoint_forward(genga_system_t *sys, int64_t nsteps, int64_t checkpoint_every);
+
+/* Uses a recording made elsewhere: rc_hist (host, nsteps x n doubles, step
+ * major), pair_offsets (host, nsteps + 1) and pairs (host, interleaved uint32
+ * i < j, step k's pairs at pair_offsets[k] .. pair_offsets[k+1]-1).  The
+ * current state is the initial state; the steps are replayed with the frozen
+ * rc and pairs, leaving the final state in pos/vel.  Synchronises.          */
+int genga_adjoint_load(genga_system_t *sys, int64_t nsteps, int64_t checkpoint_every,
+                       const double *rc_hist, const int64_t *pair_offsets, const uint32_t *pairs);
+
+/* Given lam_x, lam_v (device, 3n each: dL/d final positions and velocities)
+ * writes grad_x0, grad_v0 (device, 3n: dL/d initial state) and grad_m
+ * (device, n: dL/d masses).  pos/vel are used as work space and hold the
+ * final state again on return.  Synchronises.                              */
+int genga_adjoint_backward(genga_system_t *sys, const double *lam_x, const double *lam_v,
+                           double *grad_x0, double *grad_v0, double *grad_m);
+
 /* ---- batched ensemble (multi-simulation mode) --------------------------- */
 /* Many independent small systems integrated together by the original hybrid
  * method (Appendix A, slevels = 1) with the post-Newtonian GR acceleration of

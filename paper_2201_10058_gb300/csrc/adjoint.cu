@@ -1,0 +1,741 @@
+// adjoint.cu -- reverse-mode derivative of kick-drift-kick steps with frozen
+// encounters (the adjoint form around the method of Appendix A).
+//
+// Forward: normal steps of the original scheme (slevels = 1) that record each
+// step's level-0 critical radii and encounter pairs, with checkpoints of the
+// state every C steps.  Backward: for each segment (last first) the states at
+// the step starts are recomputed from the checkpoint by replaying the steps
+// with the recorded rc and pairs, then each step is differentiated in reverse:
+//   Kick(dt/2) at x3  -> lx += h (da/dx)^T lv,  lm += h (da/dm)^T lv
+//   HC(dt/2)          -> lv_j += (h/m*) m_j sum(lx), lm_j += (h/m*) v_j . sum(lx)
+//   FG(dt)            -> (lx, lv) = Phi^T (lx, lv), Phi the 6x6 state-transition
+//                        matrix of the Kepler drift (dual numbers, exact)
+//   BS(dt) of a group -> the continuous adjoint: the group ODE, its adjoint
+//                        lambda' = -J^T lambda and the mass gradient integrated
+//                        backwards in time by the same Bulirsch-Stoer scheme
+//   HC(dt/2), Kick(dt/2) at x as above.
+// There is no derivative through rc (frozen), and the changeover function's
+// derivative dK/dr is included in the force derivatives.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace genga {
+namespace {
+
+// ------------------------------------------------------------ dual numbers
+struct D6 {
+    double v;
+    double d[6];
+};
+__device__ __forceinline__ D6 dconst(double a) { D6 r; r.v = a; for (int k = 0; k < 6; k++) r.d[k] = 0.0; return r; }
+__device__ __forceinline__ D6 operator+(const D6 &a, const D6 &b) { D6 r; r.v = a.v + b.v; for (int k = 0; k < 6; k++) r.d[k] = a.d[k] + b.d[k]; return r; }
+__device__ __forceinline__ D6 operator-(const D6 &a, const D6 &b) { D6 r; r.v = a.v - b.v; for (int k = 0; k < 6; k++) r.d[k] = a.d[k] - b.d[k]; return r; }
+__device__ __forceinline__ D6 operator*(const D6 &a, const D6 &b) { D6 r; r.v = a.v * b.v; for (int k = 0; k < 6; k++) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
+__device__ __forceinline__ D6 operator*(double s, const D6 &a) { D6 r; r.v = s * a.v; for (int k = 0; k < 6; k++) r.d[k] = s * a.d[k]; return r; }
+__device__ __forceinline__ D6 operator/(const D6 &a, const D6 &b) {
+    D6 r; r.v = a.v / b.v;
+    const double ib = 1.0 / b.v;
+    for (int k = 0; k < 6; k++) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+    return r;
+}
+__device__ __forceinline__ D6 dsqrt(const D6 &a) {
+    D6 r; r.v = sqrt(a.v);
+    const double h = 0.5 / r.v;
+    for (int k = 0; k < 6; k++) r.d[k] = a.d[k] * h;
+    return r;
+}
+__device__ __forceinline__ D6 operator-(const D6 &a) { return (-1.0) * a; }
+
+// Stumpff functions on duals (same series and quartering as stumpff()).
+__device__ void stumpff_d6(D6 z, D6 &c0, D6 &c1, D6 &c2, D6 &c3) {
+    int q = 0;
+    while (fabs(z.v) > 0.1 && q < 60) { z = 0.25 * z; q++; }
+    const double ic2[10] = {1.0 / 2.0, 1.0 / 24.0, 1.0 / 720.0, 1.0 / 40320.0, 1.0 / 3628800.0,
+                            1.0 / 479001600.0, 1.0 / 87178291200.0, 1.0 / 20922789888000.0,
+                            1.0 / 6402373705728000.0, 1.0 / 2432902008176640000.0};
+    const double ic3[10] = {1.0 / 6.0, 1.0 / 120.0, 1.0 / 5040.0, 1.0 / 362880.0,
+                            1.0 / 39916800.0, 1.0 / 6227020800.0, 1.0 / 1307674368000.0,
+                            1.0 / 355687428096000.0, 1.0 / 121645100408832000.0,
+                            1.0 / 51090942171709440000.0};
+    D6 s2 = dconst(0.0), s3 = dconst(0.0);
+    for (int m = 9; m >= 0; m--) {
+        s2 = dconst(ic2[m]) - z * s2;
+        s3 = dconst(ic3[m]) - z * s3;
+    }
+    D6 C2 = s2, C3 = s3, C0 = dconst(1.0) - z * C2, C1 = dconst(1.0) - z * C3;
+    for (int k = 0; k < q; k++) {
+        const D6 n3 = 0.25 * (C2 + C0 * C3);
+        const D6 n2 = 0.5 * (C1 * C1);
+        const D6 n1 = C0 * C1;
+        const D6 n0 = 2.0 * (C0 * C0) - dconst(1.0);
+        C0 = n0; C1 = n1; C2 = n2; C3 = n3;
+    }
+    c0 = C0; c1 = C1; c2 = C2; c3 = C3;
+}
+
+// ------------------------------------------------------------ drift VJP
+// For bodies outside every group: (lx, lv) <- Phi^T (lx, lv) with Phi the
+// Jacobian of the Kepler drift at the pre-drift state (x1, v1).  The
+// universal variable s is solved in double; one Newton step in dual
+// arithmetic from it gives ds/d(x0, v0) by the implicit function theorem.
+__global__ void drift_vjp_kernel(int n, const double *x1, const double *v1, const int *label,
+                                 double mu, double dt, int max_iter, double *lx, double *lv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (label && label[i] >= 0) return;
+    const size_t N = (size_t)n;
+    D6 X[3], V[3];
+    for (int c = 0; c < 3; c++) {
+        X[c] = dconst(x1[c * N + i]); X[c].d[c] = 1.0;
+        V[c] = dconst(v1[c * N + i]); V[c].d[3 + c] = 1.0;
+    }
+    const D6 r0 = dsqrt(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+    const D6 v2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    const D6 u = X[0] * V[0] + X[1] * V[1] + X[2] * V[2];
+    const D6 beta = (2.0 * mu) * (dconst(1.0) / r0) - v2;
+    double s;
+    kepler_solve_s(r0.v, u.v, beta.v, mu, dt, max_iter, s);
+    // one dual Newton step: s_d = s - (t(s) - dt) / r(s)
+    D6 sd = dconst(s);
+    D6 c0, c1, c2, c3;
+    stumpff_d6(beta * sd * sd, c0, c1, c2, c3);
+    {
+        const D6 G1 = sd * c1, G2 = sd * sd * c2, G3 = sd * sd * sd * c3;
+        const D6 t = r0 * G1 + u * G2 + mu * G3;
+        const D6 rr = r0 * c0 + u * G1 + mu * G2;
+        sd = sd - (t - dconst(dt)) / rr;
+    }
+    stumpff_d6(beta * sd * sd, c0, c1, c2, c3);
+    const D6 G1 = sd * c1, G2 = sd * sd * c2, G3 = sd * sd * sd * c3;
+    const D6 r = r0 * c0 + u * G1 + mu * G2;
+    const D6 fm1 = -(mu * G2 / r0);
+    const D6 g = dconst(dt) - mu * G3;
+    const D6 fd = -(mu * G1 / (r * r0));
+    const D6 gdm1 = -(mu * G2 / r);
+    // outputs x = x0 + fm1 x0 + g v0, v = v0 + fd x0 + gdm1 v0; J[row][col]
+    double J[6][6];
+    for (int c = 0; c < 3; c++) {
+        const D6 xo = X[c] + fm1 * X[c] + g * V[c];
+        const D6 vo = V[c] + fd * X[c] + gdm1 * V[c];
+        for (int k = 0; k < 6; k++) { J[c][k] = xo.d[k]; J[3 + c][k] = vo.d[k]; }
+    }
+    double lo[6], li[6];
+    for (int c = 0; c < 3; c++) { lo[c] = lx[c * N + i]; lo[3 + c] = lv[c * N + i]; }
+    for (int k = 0; k < 6; k++) {
+        double acc = 0.0;
+        for (int row = 0; row < 6; row++) acc += J[row][k] * lo[row];
+        li[k] = acc;
+    }
+    for (int c = 0; c < 3; c++) { lx[c * N + i] = li[c]; lv[c * N + i] = li[3 + c]; }
+}
+
+// ------------------------------------------------------------ kick VJP
+// For each body k (FP64):
+//   gx_k = G sum_j M_kj (m_k lv_j - m_j lv_k),  M = K (I/r^3 - 3 d d^T/r^5) + K' d d^T / r^4
+//   gm_k = -G sum_j K lv_j . d / r^3,            d = x_j - x_k
+constexpr int kAdjThreads = 128;
+constexpr int kAdjTile = 128;
+
+__device__ __forceinline__ double changeover_dr_dev(double r, double rc) {
+    const double y = (r / rc - 0.1) / 0.9;
+    if (y <= 0.0 || y >= 1.0) return 0.0;
+    const double D = 2.0 * y * y - 2.0 * y + 1.0;
+    return 2.0 * y * (1.0 - y) / (D * D) / (0.9 * rc);
+}
+
+__global__ void __launch_bounds__(kAdjThreads)
+kick_vjp_kernel(int n, const double *pos, const double *mass, const double *rc, const double *lv,
+                int chunk, double *part /* [nchunk][4][n] */) {
+    __shared__ double sx[kAdjTile], sy[kAdjTile], sz[kAdjTile], sm[kAdjTile], src[kAdjTile];
+    __shared__ double sl0[kAdjTile], sl1[kAdjTile], sl2[kAdjTile];
+    const size_t N = (size_t)n;
+    const int k = blockIdx.x * kAdjThreads + threadIdx.x;
+    const bool valid = k < n;
+    double xk = 0, yk = 0, zk = 0, mk = 0, rck = 0, l0 = 0, l1 = 0, l2 = 0;
+    if (valid) {
+        xk = pos[k]; yk = pos[N + k]; zk = pos[2 * N + k]; mk = mass[k]; rck = rc[k];
+        l0 = lv[k]; l1 = lv[N + k]; l2 = lv[2 * N + k];
+    }
+    const int jbeg = blockIdx.y * chunk, jend = min(n, jbeg + chunk);
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0, gm = 0.0;
+    for (int jt = jbeg; jt < jend; jt += kAdjTile) {
+        const int cnt = min(kAdjTile, jend - jt);
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += kAdjThreads) {
+            const int j = jt + q;
+            sx[q] = pos[j]; sy[q] = pos[N + j]; sz[q] = pos[2 * N + j]; sm[q] = mass[j]; src[q] = rc[j];
+            sl0[q] = lv[j]; sl1[q] = lv[N + j]; sl2[q] = lv[2 * N + j];
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int q = 0; q < cnt; q++) {
+            if (jt + q == k) continue;
+            const double dx = sx[q] - xk, dy = sy[q] - yk, dz = sz[q] - zk;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double r = sqrt(r2);
+            const double rcij = fmax(rck, src[q]);
+            const double K = changeover(r, rcij);
+            const double Kp = changeover_dr_dev(r, rcij);
+            const double r3 = r2 * r;
+            // e = m_k lv_j - m_j lv_k
+            const double e0 = mk * sl0[q] - sm[q] * l0, e1 = mk * sl1[q] - sm[q] * l1, e2 = mk * sl2[q] - sm[q] * l2;
+            const double de = dx * e0 + dy * e1 + dz * e2;
+            const double a = K / r3;
+            const double b = -3.0 * K * de / (r3 * r2) + Kp * de / (r2 * r2);
+            g0 += a * e0 + b * dx; g1 += a * e1 + b * dy; g2 += a * e2 + b * dz;
+            gm -= K * (sl0[q] * dx + sl1[q] * dy + sl2[q] * dz) / r3;
+        }
+    }
+    if (valid) {
+        double *p = part + (size_t)blockIdx.y * 4 * N;
+        p[k] = g0; p[N + k] = g1; p[2 * N + k] = g2; p[3 * N + k] = gm;
+    }
+}
+
+__global__ void kick_vjp_finalize(int n, int nchunk, const double *part, double G, double h,
+                                  double *lx, double *lm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const size_t N = (size_t)n;
+    double g[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < nchunk; q++)
+        for (int c = 0; c < 4; c++) g[c] += part[(size_t)q * 4 * N + c * N + k];
+    lx[k] += h * G * g[0];
+    lx[N + k] += h * G * g[1];
+    lx[2 * N + k] += h * G * g[2];
+    lm[k] += h * G * g[3];
+}
+
+// ------------------------------------------------------------ HC VJP
+__global__ void __launch_bounds__(1024) sum3_kernel(int n, const double *a, double *out) {
+    __shared__ double sp[3][1024];
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    for (int j = threadIdx.x; j < n; j += 1024) { p0 += a[j]; p1 += a[(size_t)n + j]; p2 += a[2 * (size_t)n + j]; }
+    sp[0][threadIdx.x] = p0; sp[1][threadIdx.x] = p1; sp[2][threadIdx.x] = p2;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int c = 0; c < 3; c++) sp[c][threadIdx.x] += sp[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[threadIdx.x] = sp[threadIdx.x][0];
+}
+
+__global__ void hc_vjp_kernel(int n, const double *sigma, const double *vel, const double *mass,
+                              double h_over_mstar, double *lv, double *lm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const size_t N = (size_t)n;
+    const double s0 = sigma[0], s1 = sigma[1], s2 = sigma[2];
+    lv[j] += h_over_mstar * mass[j] * s0;
+    lv[N + j] += h_over_mstar * mass[j] * s1;
+    lv[2 * N + j] += h_over_mstar * mass[j] * s2;
+    lm[j] += h_over_mstar * (vel[j] * s0 + vel[N + j] * s1 + vel[2 * N + j] * s2);
+}
+
+// ------------------------------------------------------------ BS adjoint
+// Per member: y (6), adjoint lambda (6), mass-gradient integral g (1); in
+// reversed time tau = dt - t:
+//   dy/dtau = -f(y)
+//   dlx/dtau = A^T lv,  dlv/dtau = lx        (J = [[0, I], [A, 0]], A = da/dx)
+//   dg_a/dtau = G sum_p W lv_p . (x_a - x_p)/r^3   (da_p/dm_a)
+// Error control on y only.  One CTA per group, state in a global scratch.
+constexpr int kAD = 13;                      // values per member
+constexpr int kABs = 64;                     // threads per CTA
+
+struct AdjBsArgs {
+    int n;
+    const double *x2, *v2;                   // post-drift state (start of the backward run)
+    double *lx, *lv, *lm;                    // in: adjoint at the end of the drift; out: at its start
+    const double *mass, *rc;
+    const int *off, *list;
+    const int *glist, *goff, *member, *slotof;
+    const unsigned *ngroups;
+    double *scr;                             // [kAD * 14][S]
+    size_t S;
+    double G, mu, dt, tol;
+    int max_steps;
+    DevCounters *ctr;
+};
+
+__device__ __forceinline__ double &AR(const AdjBsArgs &A, int row, int slot) { return A.scr[(size_t)row * A.S + slot]; }
+
+// derivative in reversed time of the augmented state in rows z0..z0+12 into f0..f0+12
+__device__ void adj_deriv(const AdjBsArgs &A, int z0, int f0, int s) {
+    const int b = A.member[s];
+    const double x = AR(A, z0, s), y = AR(A, z0 + 1, s), z = AR(A, z0 + 2, s);
+    const double lvx = AR(A, z0 + 9, s), lvy = AR(A, z0 + 10, s), lvz = AR(A, z0 + 11, s);
+    const double mb = A.mass[b];
+    const double r2 = x * x + y * y + z * z, r = sqrt(r2), r3 = r2 * r;
+    // star: acc = -mu x / r^3; A_star = -mu (I/r^3 - 3 x x^T / r^5) (symmetric)
+    double ax = -A.mu * x / r3, ay = -A.mu * y / r3, az = -A.mu * z / r3;
+    const double xl = x * lvx + y * lvy + z * lvz;
+    double tx = -A.mu * (lvx / r3 - 3.0 * x * xl / (r3 * r2));
+    double ty = -A.mu * (lvy / r3 - 3.0 * y * xl / (r3 * r2));
+    double tz = -A.mu * (lvz / r3 - 3.0 * z * xl / (r3 * r2));
+    double px = 0.0, py = 0.0, pz = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, gm = 0.0;
+    for (int q = A.off[b]; q < A.off[b + 1]; q++) {
+        const int p = A.list[q];
+        const int sp = A.slotof[p];
+        const double dx = AR(A, z0, sp) - x, dy = AR(A, z0 + 1, sp) - y, dz = AR(A, z0 + 2, sp) - z;
+        const double d2 = dx * dx + dy * dy + dz * dz, d = sqrt(d2), d3 = d2 * d;
+        const double rcij = fmax(A.rc[b], A.rc[p]);
+        const double W = 1.0 - changeover(d, rcij);
+        const double Wp = -changeover_dr_dev(d, rcij);
+        const double mp = A.mass[p];
+        px += mp * W * dx / d3; py += mp * W * dy / d3; pz += mp * W * dz / d3;
+        const double qx = AR(A, z0 + 9, sp), qy = AR(A, z0 + 10, sp), qz = AR(A, z0 + 11, sp);
+        const double e0 = mb * qx - mp * lvx, e1 = mb * qy - mp * lvy, e2 = mb * qz - mp * lvz;
+        const double de = dx * e0 + dy * e1 + dz * e2;
+        const double a = W / d3;
+        const double bb = -3.0 * W * de / (d3 * d2) + Wp * de / (d2 * d2);
+        gx += a * e0 + bb * dx; gy += a * e1 + bb * dy; gz += a * e2 + bb * dz;
+        gm -= W * (qx * dx + qy * dy + qz * dz) / d3;
+    }
+    ax += A.G * px; ay += A.G * py; az += A.G * pz;
+    // reversed time
+    AR(A, f0 + 0, s) = -AR(A, z0 + 3, s);
+    AR(A, f0 + 1, s) = -AR(A, z0 + 4, s);
+    AR(A, f0 + 2, s) = -AR(A, z0 + 5, s);
+    AR(A, f0 + 3, s) = -ax;
+    AR(A, f0 + 4, s) = -ay;
+    AR(A, f0 + 5, s) = -az;
+    AR(A, f0 + 6, s) = tx + A.G * gx;
+    AR(A, f0 + 7, s) = ty + A.G * gy;
+    AR(A, f0 + 8, s) = tz + A.G * gz;
+    AR(A, f0 + 9, s) = AR(A, z0 + 6, s);
+    AR(A, f0 + 10, s) = AR(A, z0 + 7, s);
+    AR(A, f0 + 11, s) = AR(A, z0 + 8, s);
+    AR(A, f0 + 12, s) = A.G * gm;
+}
+
+__global__ void __launch_bounds__(kABs) bs_adjoint_kernel(AdjBsArgs A) {
+    enum { Y = 0, F0 = kAD, ZM = 2 * kAD, ZN = 3 * kAD, FZ = 4 * kAD, SC = 5 * kAD, TT = 6 * kAD };
+    __shared__ double red[kABs / 32];
+    __shared__ int stop;
+    __shared__ double st_t, st_H;
+    if (blockIdx.x >= *A.ngroups) return;
+    const int g = A.glist[blockIdx.x];
+    const int s0 = A.goff[g], s1 = A.goff[g + 1];
+    const size_t N = (size_t)A.n;
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const int b = A.member[s];
+        for (int c = 0; c < 3; c++) {
+            AR(A, Y + c, s) = A.x2[c * N + b];
+            AR(A, Y + 3 + c, s) = A.v2[c * N + b];
+            AR(A, Y + 6 + c, s) = A.lx[c * N + b];
+            AR(A, Y + 9 + c, s) = A.lv[c * N + b];
+        }
+        AR(A, Y + 12, s) = 0.0;
+    }
+    if (threadIdx.x == 0) { st_t = 0.0; st_H = A.dt; }
+    int attempts = 0;
+    bool failed = false;
+    __syncthreads();
+    while (st_t < A.dt) {
+        if (threadIdx.x == 0) stop = attempts >= A.max_steps;
+        __syncthreads();
+        if (stop) { failed = true; break; }
+        attempts++;
+        double H = st_H;
+        if (H > A.dt - st_t) H = A.dt - st_t;
+        for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) adj_deriv(A, Y, F0, s);
+        for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
+            for (int c = 0; c < kAD; c++) AR(A, SC + c, s) = fabs(AR(A, Y + c, s)) + fabs(H * AR(A, F0 + c, s)) + 1e-300;
+        int kconv = -1;
+        for (int k = 0; k < 8 && kconv < 0; k++) {
+            const int nk = 2 * (k + 1);
+            const double h = H / nk;
+            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
+                for (int c = 0; c < kAD; c++) {
+                    const double y0 = AR(A, Y + c, s);
+                    AR(A, ZM + c, s) = y0;
+                    AR(A, ZN + c, s) = y0 + h * AR(A, F0 + c, s);
+                }
+            for (int mm = 1; mm < nk; mm++) {
+                __syncthreads();
+                for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) adj_deriv(A, ZN, FZ, s);
+                __syncthreads();
+                for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
+                    for (int c = 0; c < kAD; c++) {
+                        const double tt = AR(A, ZM + c, s) + 2.0 * h * AR(A, FZ + c, s);
+                        AR(A, ZM + c, s) = AR(A, ZN + c, s);
+                        AR(A, ZN + c, s) = tt;
+                    }
+            }
+            __syncthreads();
+            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) adj_deriv(A, ZN, FZ, s);
+            double err = 0.0;
+            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
+                for (int c = 0; c < kAD; c++) {
+                    double cur = 0.5 * (AR(A, ZN + c, s) + AR(A, ZM + c, s) + h * AR(A, FZ + c, s));
+                    double prev = AR(A, TT + c, s);
+                    AR(A, TT + c, s) = cur;
+                    for (int j = 1; j <= k; j++) {
+                        const double coef = (double)((k - j + 1) * (k - j + 1)) / (double)(j * (2 * k + 2 - j));
+                        const double nxt = fma(cur - prev, coef, cur);
+                        prev = AR(A, TT + j * kAD + c, s);
+                        AR(A, TT + j * kAD + c, s) = nxt;
+                        cur = nxt;
+                    }
+                    if (k >= 1 && c < 6)
+                        err = fmax(err, fabs(AR(A, TT + k * kAD + c, s) - AR(A, TT + (k - 1) * kAD + c, s)) / AR(A, SC + c, s));
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = err;
+            __syncthreads();
+            double e = red[0];
+            for (int w = 1; w < kABs / 32; w++) e = fmax(e, red[w]);
+            __syncthreads();
+            if (k >= 1 && e <= A.tol) kconv = k;
+        }
+        if (kconv >= 0) {
+            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
+                for (int c = 0; c < kAD; c++) AR(A, Y + c, s) = AR(A, TT + kconv * kAD + c, s);
+            __syncthreads();
+            if (threadIdx.x == 0) { st_t += H; st_H = (kconv < 4) ? 1.5 * H : H; }
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0) st_H = 0.5 * H;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const int b = A.member[s];
+        for (int c = 0; c < 3; c++) {
+            A.lx[c * N + b] = AR(A, Y + 6 + c, s);
+            A.lv[c * N + b] = AR(A, Y + 9 + c, s);
+        }
+        A.lm[b] += AR(A, Y + 12, s);
+    }
+    if (threadIdx.x == 0 && failed) {
+        atomicAdd(&A.ctr->bs_fail, 1ull);
+        latch_error(A.ctr, kErrBS);
+    }
+}
+
+}  // namespace
+
+// ============================================================== host driver
+struct Adjoint {
+    int64_t nsteps = 0, every = 0;
+    std::vector<int64_t> pair_off;            // host, nsteps + 1
+    double *rc_hist = nullptr;                // device, nsteps * n
+    uint2 *pair_hist = nullptr;               // device
+    int64_t pair_cap = 0;
+    double *x0 = nullptr, *v0 = nullptr;      // initial state, 3n each
+    double *ckpt = nullptr;                   // device, ncheck * 6n
+    double *seg = nullptr;                    // device, every * 6n (step-start states of a segment)
+    double *tmp = nullptr;                    // device, 6n (x2, v2)
+    double *part = nullptr;                   // kick VJP partials
+    int nchunk = 0, chunk = 0;
+    double *sigma = nullptr;                  // 3 doubles
+    double *bs_scr = nullptr;                 // kAD * 14 rows * n
+    double *save_pos = nullptr, *save_vel = nullptr;
+};
+
+}  // namespace genga
+
+using namespace genga;
+
+namespace {
+
+#define ACU(expr)                                                        \
+    do {                                                                 \
+        cudaError_t e__ = (expr);                                        \
+        if (e__ != cudaSuccess) {                                        \
+            snprintf(s->err, sizeof(s->err), "%s: %s", #expr, cudaGetErrorString(e__)); \
+            return e__ == cudaErrorMemoryAllocation ? GENGA_ENOMEM : GENGA_ECUDA; \
+        }                                                                \
+    } while (0)
+
+Adjoint *adj_of(genga_system *s) {
+    if (!s->adj) s->adj = new Adjoint();
+    return (Adjoint *)s->adj;
+}
+
+int adj_alloc(genga_system *s, int64_t nsteps, int64_t every) {
+    Adjoint *a = adj_of(s);
+    const size_t n = (size_t)s->n;
+    auto fr = [](double *&p) { if (p) cudaFree(p); p = nullptr; };
+    fr(a->rc_hist); fr(a->ckpt); fr(a->seg);
+    a->nsteps = nsteps;
+    a->every = every;
+    const int64_t ncheck = (nsteps + every - 1) / every + 1;
+    ACU(cudaMalloc(&a->rc_hist, sizeof(double) * n * (size_t)std::max<int64_t>(nsteps, 1)));
+    ACU(cudaMalloc(&a->ckpt, sizeof(double) * 6 * n * (size_t)ncheck));
+    ACU(cudaMalloc(&a->seg, sizeof(double) * 6 * n * (size_t)every));
+    if (!a->x0) {
+        ACU(cudaMalloc(&a->x0, sizeof(double) * 3 * n));
+        ACU(cudaMalloc(&a->v0, sizeof(double) * 3 * n));
+        ACU(cudaMalloc(&a->tmp, sizeof(double) * 6 * n));
+        ACU(cudaMalloc(&a->sigma, sizeof(double) * 4));
+        ACU(cudaMalloc(&a->bs_scr, sizeof(double) * (size_t)kAD * 14 * n));
+        ACU(cudaMalloc(&a->save_pos, sizeof(double) * 3 * n));
+        ACU(cudaMalloc(&a->save_vel, sizeof(double) * 3 * n));
+        const int iblocks = (int)((n + kAdjThreads - 1) / kAdjThreads);
+        int want = (8 * s->num_sms + iblocks - 1) / iblocks;
+        const int tiles = (int)((n + kAdjTile - 1) / kAdjTile);
+        int tpc = std::max(1, std::min(16, (tiles + want - 1) / std::max(1, want)));
+        a->chunk = tpc * kAdjTile;
+        a->nchunk = (int)((n + a->chunk - 1) / a->chunk);
+        ACU(cudaMalloc(&a->part, sizeof(double) * 4 * n * (size_t)a->nchunk));
+    }
+    a->pair_off.assign(1, 0);
+    return GENGA_OK;
+}
+
+int adj_push_pairs(genga_system *s, const uint2 *dev_pairs, int64_t np, bool from_host) {
+    Adjoint *a = adj_of(s);
+    const int64_t have = a->pair_off.back();
+    if (have + np > a->pair_cap) {
+        const int64_t cap = std::max<int64_t>(2 * (have + np), 1 << 16);
+        uint2 *nb = nullptr;
+        ACU(cudaMalloc(&nb, sizeof(uint2) * (size_t)cap));
+        if (a->pair_hist) {
+            ACU(cudaMemcpyAsync(nb, a->pair_hist, sizeof(uint2) * (size_t)have, cudaMemcpyDeviceToDevice, s->stream));
+            ACU(cudaStreamSynchronize(s->stream));
+            cudaFree(a->pair_hist);
+        }
+        a->pair_hist = nb;
+        a->pair_cap = cap;
+    }
+    if (np > 0)
+        ACU(cudaMemcpyAsync(a->pair_hist + have, dev_pairs, sizeof(uint2) * (size_t)np,
+                            from_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s->stream));
+    a->pair_off.push_back(have + np);
+    return GENGA_OK;
+}
+
+// One step with the recorded rc and pairs of step k (Appendix A, slevels = 1).
+int replay_step(genga_system *s, int64_t k) {
+    Adjoint *a = adj_of(s);
+    const size_t n = (size_t)s->n;
+    const double dt = s->p.dt, h = 0.5 * dt;
+    ACU(cudaMemcpyAsync(s->rcl[0].rc, a->rc_hist + (size_t)k * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(launch_rcrit_derive(s));
+    ACU(launch_kick(s, h, false, nullptr));
+    ACU(launch_hc(s, h));
+    ACU(launch_drift(s, 0, dt, nullptr, (int)n));
+    const int64_t np = a->pair_off[(size_t)k + 1] - a->pair_off[(size_t)k];
+    s->npairs_host[0] = np;
+    if (np > 0) {
+        int rc = ensure_pair_capacity(s, 0, np);
+        if (rc != GENGA_OK) return rc;
+        ACU(cudaMemcpyAsync(s->pairs[0], a->pair_hist + a->pair_off[(size_t)k], sizeof(uint2) * (size_t)np,
+                            cudaMemcpyDeviceToDevice, s->stream));
+        ACU(build_csr(s, 0, np));
+        ACU(build_groups(s, 0, np));
+        ACU(launch_bs(s, 0, dt, std::min<int64_t>(np, s->n / 2 + 1)));
+    }
+    ACU(launch_hc(s, h));
+    ACU(launch_kick(s, h, false, nullptr));
+    return GENGA_OK;
+}
+
+int kick_vjp(genga_system *s, const double *pos, const double *lv, double *lx, double *lm, double h) {
+    Adjoint *a = adj_of(s);
+    const int n = (int)s->n;
+    dim3 grid((n + kAdjThreads - 1) / kAdjThreads, a->nchunk);
+    kick_vjp_kernel<<<grid, kAdjThreads, 0, s->stream>>>(n, pos, s->mass, s->rcl[0].rc, lv, a->chunk, a->part);
+    ++s->launches;
+    ACU(cudaGetLastError());
+    kick_vjp_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(n, a->nchunk, a->part, s->p.G, h, lx, lm);
+    ++s->launches;
+    ACU(cudaGetLastError());
+    return GENGA_OK;
+}
+
+int hc_vjp(genga_system *s, const double *lx, const double *vel, double *lv, double *lm, double h) {
+    Adjoint *a = adj_of(s);
+    const int n = (int)s->n;
+    sum3_kernel<<<1, 1024, 0, s->stream>>>(n, lx, a->sigma);
+    ++s->launches;
+    ACU(cudaGetLastError());
+    hc_vjp_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, a->sigma, vel, s->mass, h / s->p.m_star, lv, lm);
+    ++s->launches;
+    ACU(cudaGetLastError());
+    return GENGA_OK;
+}
+
+// Reverse of step k from the step-start state at `start` (6n: x then v).
+int step_vjp(genga_system *s, int64_t k, const double *start, double *lx, double *lv, double *lm) {
+    Adjoint *a = adj_of(s);
+    const size_t n = (size_t)s->n;
+    const double dt = s->p.dt, h = 0.5 * dt;
+    // recompute the intermediate states of step k
+    ACU(cudaMemcpyAsync(s->pos, start, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(s->vel, start + 3 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(s->rcl[0].rc, a->rc_hist + (size_t)k * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(launch_rcrit_derive(s));
+    ACU(launch_kick(s, h, false, nullptr));
+    ACU(launch_hc(s, h));
+    ACU(launch_drift(s, 0, dt, nullptr, (int)n));          // pre_pos/pre_vel[0] = x1, v1
+    const int64_t np = a->pair_off[(size_t)k + 1] - a->pair_off[(size_t)k];
+    s->npairs_host[0] = np;
+    if (np > 0) {
+        int rc = ensure_pair_capacity(s, 0, np);
+        if (rc != GENGA_OK) return rc;
+        ACU(cudaMemcpyAsync(s->pairs[0], a->pair_hist + a->pair_off[(size_t)k], sizeof(uint2) * (size_t)np,
+                            cudaMemcpyDeviceToDevice, s->stream));
+        ACU(build_csr(s, 0, np));
+        ACU(build_groups(s, 0, np));
+        ACU(launch_bs(s, 0, dt, std::min<int64_t>(np, s->n / 2 + 1)));
+    }
+    // (x2, v2)
+    ACU(cudaMemcpyAsync(a->tmp, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(a->tmp + 3 * n, s->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(launch_hc(s, h));                                  // pos = x3, vel = v2
+    // reverse
+    int rc;
+    if ((rc = kick_vjp(s, s->pos, lv, lx, lm, h)) != GENGA_OK) return rc;
+    if ((rc = hc_vjp(s, lx, s->vel, lv, lm, h)) != GENGA_OK) return rc;
+    drift_vjp_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s->stream>>>((int)n, s->pre_pos[0], s->pre_vel[0],
+        np > 0 ? s->label : nullptr, s->p.G * s->p.m_star, dt, s->p.kepler_max_iter, lx, lv);
+    ++s->launches;
+    ACU(cudaGetLastError());
+    if (np > 0) {
+        AdjBsArgs B;
+        B.n = (int)n; B.x2 = a->tmp; B.v2 = a->tmp + 3 * n;
+        B.lx = lx; B.lv = lv; B.lm = lm;
+        B.mass = s->mass; B.rc = s->rcl[0].rc;
+        B.off = s->csr[0].off; B.list = s->csr[0].list;
+        B.glist = s->glist; B.goff = s->goff; B.member = s->member; B.slotof = s->slotof;
+        B.ngroups = &s->ctr->ngroups;
+        B.scr = a->bs_scr; B.S = n;
+        B.G = s->p.G; B.mu = s->p.G * s->p.m_star; B.dt = dt; B.tol = s->p.bs_tol;
+        B.max_steps = s->p.bs_max_steps; B.ctr = s->ctr;
+        bs_adjoint_kernel<<<(unsigned)std::min<int64_t>(np, s->n / 2 + 1), kABs, 0, s->stream>>>(B);
+        ++s->launches;
+        ACU(cudaGetLastError());
+    }
+    if ((rc = hc_vjp(s, lx, s->pre_vel[0], lv, lm, h)) != GENGA_OK) return rc;
+    if ((rc = kick_vjp(s, start, lv, lx, lm, h)) != GENGA_OK) return rc;
+    return GENGA_OK;
+}
+
+int forward_checkpointed(genga_system *s) {
+    Adjoint *a = adj_of(s);
+    const size_t n = (size_t)s->n;
+    ACU(cudaMemcpyAsync(s->pos, a->x0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(s->vel, a->v0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    for (int64_t k = 0; k < a->nsteps; k++) {
+        if (k % a->every == 0) {
+            double *c = a->ckpt + (size_t)(k / a->every) * 6 * n;
+            ACU(cudaMemcpyAsync(c, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+            ACU(cudaMemcpyAsync(c + 3 * n, s->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+        }
+        int rc = replay_step(s, k);
+        if (rc != GENGA_OK) return rc;
+    }
+    return GENGA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int genga_adjoint_forward(genga_system_t *s, int64_t nsteps, int64_t checkpoint_every) {
+    if (!s || nsteps < 1 || checkpoint_every < 1 || s->p.slevels != 1) return GENGA_EINVAL;
+    int rc = adj_alloc(s, nsteps, checkpoint_every);
+    if (rc != GENGA_OK) return rc;
+    Adjoint *a = adj_of(s);
+    const size_t n = (size_t)s->n;
+    ACU(cudaMemcpyAsync(a->x0, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(a->v0, s->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    for (int64_t k = 0; k < nsteps; k++) {
+        if (k % checkpoint_every == 0) {
+            double *c = a->ckpt + (size_t)(k / checkpoint_every) * 6 * n;
+            ACU(cudaMemcpyAsync(c, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+            ACU(cudaMemcpyAsync(c + 3 * n, s->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+        }
+        rc = genga_step(s, 1);
+        if (rc != GENGA_OK) return rc;
+        ACU(cudaMemcpyAsync(a->rc_hist + (size_t)k * n, s->rcl[0].rc, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+        rc = adj_push_pairs(s, s->pairs[0], s->npairs_host[0], false);
+        if (rc != GENGA_OK) return rc;
+    }
+    ACU(cudaStreamSynchronize(s->stream));
+    return GENGA_OK;
+}
+
+int genga_adjoint_load(genga_system_t *s, int64_t nsteps, int64_t checkpoint_every, const double *rc_hist,
+                       const int64_t *pair_offsets, const uint32_t *pairs) {
+    if (!s || nsteps < 1 || checkpoint_every < 1 || !rc_hist || !pair_offsets || s->p.slevels != 1)
+        return GENGA_EINVAL;
+    int rc = adj_alloc(s, nsteps, checkpoint_every);
+    if (rc != GENGA_OK) return rc;
+    Adjoint *a = adj_of(s);
+    const size_t n = (size_t)s->n;
+    ACU(cudaMemcpyAsync(a->x0, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(a->v0, s->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(a->rc_hist, rc_hist, sizeof(double) * n * (size_t)nsteps, cudaMemcpyHostToDevice, s->stream));
+    for (int64_t k = 0; k < nsteps; k++) {
+        const int64_t np = pair_offsets[k + 1] - pair_offsets[k];
+        if (np < 0) return GENGA_EINVAL;
+        rc = adj_push_pairs(s, (const uint2 *)(pairs + 2 * pair_offsets[k]), np, true);
+        if (rc != GENGA_OK) return rc;
+    }
+    rc = forward_checkpointed(s);
+    if (rc != GENGA_OK) return rc;
+    ACU(cudaStreamSynchronize(s->stream));
+    return genga_sync(s);
+}
+
+int genga_adjoint_backward(genga_system_t *s, const double *lam_x, const double *lam_v, double *grad_x0,
+                           double *grad_v0, double *grad_m) {
+    if (!s || !lam_x || !lam_v || !grad_x0 || !grad_v0 || !grad_m || !s->adj) return GENGA_EINVAL;
+    Adjoint *a = adj_of(s);
+    if (a->nsteps < 1) return GENGA_EINVAL;
+    const size_t n = (size_t)s->n;
+    // keep the caller's (final) state
+    ACU(cudaMemcpyAsync(a->save_pos, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(a->save_vel, s->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(grad_x0, lam_x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(grad_v0, lam_v, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemsetAsync(grad_m, 0, sizeof(double) * n, s->stream));
+    const int64_t nseg = (a->nsteps + a->every - 1) / a->every;
+    for (int64_t seg = nseg - 1; seg >= 0; seg--) {
+        const int64_t k0 = seg * a->every, k1 = std::min(a->nsteps, k0 + a->every);
+        const double *c = a->ckpt + (size_t)seg * 6 * n;
+        ACU(cudaMemcpyAsync(s->pos, c, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+        ACU(cudaMemcpyAsync(s->vel, c + 3 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+        for (int64_t k = k0; k < k1; k++) {
+            double *st = a->seg + (size_t)(k - k0) * 6 * n;
+            ACU(cudaMemcpyAsync(st, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+            ACU(cudaMemcpyAsync(st + 3 * n, s->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+            if (k + 1 < k1) {
+                int rc = replay_step(s, k);
+                if (rc != GENGA_OK) return rc;
+            }
+        }
+        for (int64_t k = k1 - 1; k >= k0; k--) {
+            int rc = step_vjp(s, k, a->seg + (size_t)(k - k0) * 6 * n, grad_x0, grad_v0, grad_m);
+            if (rc != GENGA_OK) return rc;
+        }
+    }
+    ACU(cudaMemcpyAsync(s->pos, a->save_pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaMemcpyAsync(s->vel, a->save_vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    ACU(cudaStreamSynchronize(s->stream));
+    return genga_sync(s);
+}
+
+}  // extern "C"
+
+namespace genga {
+void adjoint_free(genga_system *s) {
+    if (!s->adj) return;
+    Adjoint *a = (Adjoint *)s->adj;
+    double *ps[] = {a->rc_hist, a->x0, a->v0, a->ckpt, a->seg, a->tmp, a->part, a->sigma, a->bs_scr,
+                    a->save_pos, a->save_vel};
+    for (double *p : ps) if (p) cudaFree(p);
+    if (a->pair_hist) cudaFree(a->pair_hist);
+    delete a;
+    s->adj = nullptr;
+}
+}  // namespace genga

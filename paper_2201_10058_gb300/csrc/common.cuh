@@ -122,6 +122,7 @@ struct genga_system {
     cudaStream_t side[4] = {};     // library-owned streams for concurrent BS buckets
     cudaEvent_t ev_fork = nullptr, ev_join[4] = {};
     genga_stats_t stats;
+    void *adj = nullptr;           // adjoint recording (adjoint.cu)
     int64_t launches = 0;          // kernels launched by this system (host-side count)
     char err[512] = {0};
 };
@@ -193,6 +194,11 @@ cudaError_t build_bodies(genga_system *s, int level_pairs, int out_level, int *n
 cudaError_t build_groups(genga_system *s, int level, int64_t npairs);
 cudaError_t exclusive_scan(genga_system *s, const int *in, int *out, int64_t len);
 
+// genga.cu
+int ensure_pair_capacity(genga_system *s, int level, int64_t np);
+// adjoint.cu
+void adjoint_free(genga_system *s);
+
 // bs.cu
 cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_groups);
 cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb);
@@ -237,12 +243,8 @@ __device__ __forceinline__ void stumpff(double z, double &c0, double &c1, double
 //   f - 1 = -mu G2 / r0, g = dt - mu G3, fdot = -mu G1/(r r0), gdot - 1 = -mu G2 / r.
 // Newton from s = dt/r0 - u dt^2/(2 r0^3); converged when |ds| <= 1e-15 |s|, or
 // when rounding stalls the update at |ds| <= 1e-12 |s| without halving it.
-__device__ __forceinline__ bool kepler_drift(double &x, double &y, double &z, double &vx, double &vy, double &vz,
-                             double mu, double dt, int max_iter) {
-    const double r0 = sqrt(x * x + y * y + z * z);
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double u = x * vx + y * vy + z * vz;
-    const double beta = 2.0 * mu / r0 - v2;
+__device__ __forceinline__ bool kepler_solve_s(double r0, double u, double beta, double mu,
+                                               double dt, int max_iter, double &s_out) {
     double s = dt / r0 - (u * dt * dt) / (2.0 * r0 * r0 * r0);
     double c0, c1, c2, c3, ds_prev = 0.0;
     bool ok = false;
@@ -258,6 +260,19 @@ __device__ __forceinline__ bool kepler_drift(double &x, double &y, double &z, do
         if (it > 0 && ads <= 1e-12 * as && ads > 0.5 * ds_prev) { ok = true; break; }
         ds_prev = ads;
     }
+    s_out = s;
+    return ok;
+}
+
+__device__ __forceinline__ bool kepler_drift(double &x, double &y, double &z, double &vx, double &vy, double &vz,
+                                             double mu, double dt, int max_iter) {
+    const double r0 = sqrt(x * x + y * y + z * z);
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double u = x * vx + y * vy + z * vz;
+    const double beta = 2.0 * mu / r0 - v2;
+    double s;
+    const bool ok = kepler_solve_s(r0, u, beta, mu, dt, max_iter, s);
+    double c0, c1, c2, c3;
     stumpff(beta * s * s, c0, c1, c2, c3);
     const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
     const double r = r0 * c0 + u * G1 + mu * G2;

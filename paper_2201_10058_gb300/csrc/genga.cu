@@ -321,6 +321,13 @@ int copy_pairs_sorted(genga_system *s, const uint2 *dev, int64_t count, uint32_t
 
 }  // namespace
 
+namespace genga {
+int ensure_pair_capacity(genga_system *s, int level, int64_t np) {
+    if (np <= s->pair_cap[level]) return GENGA_OK;
+    return alloc_pairs(s, level, np + np / 2 + 1024);
+}
+}  // namespace genga
+
 // ============================================================== public ABI
 extern "C" {
 
@@ -368,6 +375,7 @@ int genga_create(genga_system_t **out, const genga_params_t *p, int64_t n, doubl
 void genga_destroy(genga_system_t *s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    adjoint_free(s);
     free_all(s);
     delete s;
 }

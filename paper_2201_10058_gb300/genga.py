@@ -26,7 +26,8 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_hc", "genga_drift", "genga_build_encounters", "genga_bs", "genga_step",
             "genga_step_host", "genga_energy", "genga_get_candidates", "genga_get_pairs",
             "genga_get_groups", "genga_get_rcrit", "genga_set_predrift", "genga_get_stats",
-            "genga_kick_static", "genga_ensemble_create", "genga_ensemble_destroy",
+            "genga_kick_static", "genga_adjoint_forward", "genga_adjoint_load",
+            "genga_adjoint_backward", "genga_ensemble_create", "genga_ensemble_destroy",
             "genga_ensemble_last_error", "genga_ensemble_step", "genga_ensemble_set_tile",
             "genga_ensemble_autotune", "genga_ensemble_angmom", "genga_ensemble_get_stats"]
 
@@ -122,6 +123,9 @@ def load(build_if_missing: bool = True):
         L.genga_get_stats.argtypes = [sysp, _P(Stats)]
         L.genga_kick_static.argtypes = [C.c_int64, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int,
                                         _VP, _VP, _VP]
+        L.genga_adjoint_forward.argtypes = [_VP, C.c_int64, C.c_int64]
+        L.genga_adjoint_load.argtypes = [_VP, C.c_int64, C.c_int64, _VP, _VP, _VP]
+        L.genga_adjoint_backward.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
         L.genga_ensemble_create.argtypes = [_P(_VP), _P(Params), _P(EnsembleDesc), _VP]
         L.genga_ensemble_destroy.argtypes = [_VP]
         L.genga_ensemble_destroy.restype = None
@@ -290,6 +294,33 @@ class System:
         st = Stats()
         self._check(self._lib.genga_get_stats(self._h, C.byref(st)))
         return st.as_dict()
+
+    # -- adjoint (frozen encounters)
+    def adjoint_forward(self, nsteps: int, checkpoint_every: int):
+        self._check(self._lib.genga_adjoint_forward(self._h, nsteps, checkpoint_every))
+
+    def adjoint_load(self, checkpoint_every: int, rc_hist: np.ndarray, pairs: list):
+        """rc_hist: (nsteps, n) host array; pairs: list of (k_i, 2) uint32 arrays."""
+        rc_hist = np.ascontiguousarray(rc_hist, dtype=np.float64)
+        nsteps = rc_hist.shape[0]
+        offs = np.zeros(nsteps + 1, dtype=np.int64)
+        offs[1:] = np.cumsum([len(p) for p in pairs])
+        flat = (np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.uint32).reshape(-1, 2)
+                                                     for p in pairs]))
+                if offs[-1] > 0 else np.zeros((1, 2), dtype=np.uint32))
+        self._check(self._lib.genga_adjoint_load(self._h, nsteps, checkpoint_every,
+                                                 _np_ptr(rc_hist), _np_ptr(offs), _np_ptr(flat)))
+
+    def adjoint_backward(self, lam_x, lam_v):
+        """lam_x, lam_v: (3, n) CUDA tensors; returns (grad_x0, grad_v0, grad_m)."""
+        import torch
+        gx = torch.empty_like(lam_x)
+        gv = torch.empty_like(lam_v)
+        gm = torch.empty_like(self.mass)
+        self._check(self._lib.genga_adjoint_backward(self._h, _VP(lam_x.data_ptr()),
+                                                     _VP(lam_v.data_ptr()), _VP(gx.data_ptr()),
+                                                     _VP(gv.data_ptr()), _VP(gm.data_ptr())))
+        return gx, gv, gm
 
 
 class Ensemble:
