@@ -117,6 +117,10 @@ int alloc_all(genga_system *s) {
     }
     CU(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
     s->kick_chunk = 0;
+    {
+        const int nchunk = kick_nchunk_for((int)n, s->num_sms);
+        CU(dalloc(&s->kick_part, (size_t)nchunk * 6 * n));
+    }
     s->cand_cap = s->p.cand_capacity > 0 ? s->p.cand_capacity : std::max<int64_t>(1 << 20, 64 * (int64_t)n);
     CU(dalloc(&s->cand, (size_t)s->cand_cap));
     CU(dalloc(&s->flags, n + 1));

@@ -269,6 +269,7 @@ static KickArgs make_args(genga_system *s, bool precheck) {
 
 cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *acc_out) {
     const int n = (int)s->n;
+    if (!s->kick_part) return cudaErrorInvalidValue;
     if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
     KickArgs A = make_args(s, precheck);
     dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
@@ -288,6 +289,7 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
 
 cudaError_t launch_precheck_only(genga_system *s) {
     const int n = (int)s->n;
+    if (!s->kick_part) return cudaErrorInvalidValue;
     if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
     KickArgs A = make_args(s, true);
     dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
