@@ -217,6 +217,12 @@ int genga_adjoint_load(genga_system_t *sys, int64_t nsteps, int64_t checkpoint_e
 int genga_adjoint_backward(genga_system_t *sys, const double *lam_x, const double *lam_v,
                            double *grad_x0, double *grad_v0, double *grad_m);
 
+/* Host copies of the current recording: rc_hist (nsteps x n doubles),
+ * pair_offsets (nsteps + 1), pairs (up to cap interleaved uint32 pairs, in
+ * each step's detection order); any output may be NULL.  Synchronises.      */
+int genga_adjoint_export(genga_system_t *sys, double *rc_hist, int64_t *pair_offsets,
+                         uint32_t *pairs, int64_t cap, int64_t *n_steps, int64_t *n_pairs);
+
 /* ---- batched ensemble (multi-simulation mode) --------------------------- */
 /* Many independent small systems integrated together by the original hybrid
  * method (Appendix A, slevels = 1) with the post-Newtonian GR acceleration of

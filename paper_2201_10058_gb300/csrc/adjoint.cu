@@ -725,6 +725,24 @@ int genga_adjoint_backward(genga_system_t *s, const double *lam_x, const double 
     return genga_sync(s);
 }
 
+int genga_adjoint_export(genga_system_t *s, double *rc_hist, int64_t *pair_offsets, uint32_t *pairs,
+                         int64_t cap, int64_t *n_steps, int64_t *n_pairs) {
+    if (!s || !s->adj) return GENGA_EINVAL;
+    Adjoint *a = adj_of(s);
+    const size_t n = (size_t)s->n;
+    const int64_t total = a->pair_off.back();
+    if (n_steps) *n_steps = a->nsteps;
+    if (n_pairs) *n_pairs = total;
+    if (rc_hist)
+        ACU(cudaMemcpyAsync(rc_hist, a->rc_hist, sizeof(double) * n * (size_t)a->nsteps, cudaMemcpyDeviceToHost, s->stream));
+    if (pair_offsets)
+        for (int64_t k = 0; k <= a->nsteps; k++) pair_offsets[k] = a->pair_off[(size_t)k];
+    if (pairs && total > 0)
+        ACU(cudaMemcpyAsync(pairs, a->pair_hist, sizeof(uint2) * (size_t)std::min(cap, total), cudaMemcpyDeviceToHost, s->stream));
+    ACU(cudaStreamSynchronize(s->stream));
+    return GENGA_OK;
+}
+
 }  // extern "C"
 
 namespace genga {

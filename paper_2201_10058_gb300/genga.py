@@ -27,7 +27,7 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_step_host", "genga_energy", "genga_get_candidates", "genga_get_pairs",
             "genga_get_groups", "genga_get_rcrit", "genga_set_predrift", "genga_get_stats",
             "genga_kick_static", "genga_adjoint_forward", "genga_adjoint_load",
-            "genga_adjoint_backward", "genga_ensemble_create", "genga_ensemble_destroy",
+            "genga_adjoint_backward", "genga_adjoint_export", "genga_ensemble_create", "genga_ensemble_destroy",
             "genga_ensemble_last_error", "genga_ensemble_step", "genga_ensemble_set_tile",
             "genga_ensemble_autotune", "genga_ensemble_angmom", "genga_ensemble_get_stats"]
 
@@ -126,6 +126,8 @@ def load(build_if_missing: bool = True):
         L.genga_adjoint_forward.argtypes = [_VP, C.c_int64, C.c_int64]
         L.genga_adjoint_load.argtypes = [_VP, C.c_int64, C.c_int64, _VP, _VP, _VP]
         L.genga_adjoint_backward.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
+        L.genga_adjoint_export.argtypes = [_VP, _VP, _VP, _VP, C.c_int64, _P(C.c_int64),
+                                           _P(C.c_int64)]
         L.genga_ensemble_create.argtypes = [_P(_VP), _P(Params), _P(EnsembleDesc), _VP]
         L.genga_ensemble_destroy.argtypes = [_VP]
         L.genga_ensemble_destroy.restype = None
@@ -310,6 +312,18 @@ class System:
                 if offs[-1] > 0 else np.zeros((1, 2), dtype=np.uint32))
         self._check(self._lib.genga_adjoint_load(self._h, nsteps, checkpoint_every,
                                                  _np_ptr(rc_hist), _np_ptr(offs), _np_ptr(flat)))
+
+    def adjoint_export(self):
+        """Returns (rc_hist (nsteps, n), list of per-step (k, 2) uint32 pair arrays)."""
+        ns, npairs = C.c_int64(), C.c_int64()
+        self._check(self._lib.genga_adjoint_export(self._h, None, None, None, 0, C.byref(ns),
+                                                   C.byref(npairs)))
+        rc = np.zeros((ns.value, self.n))
+        offs = np.zeros(ns.value + 1, dtype=np.int64)
+        flat = np.zeros((max(npairs.value, 1), 2), dtype=np.uint32)
+        self._check(self._lib.genga_adjoint_export(self._h, _np_ptr(rc), _np_ptr(offs), _np_ptr(flat),
+                                                   npairs.value, C.byref(ns), C.byref(npairs)))
+        return rc, [flat[offs[k]:offs[k + 1]].copy() for k in range(ns.value)]
 
     def adjoint_backward(self, lam_x, lam_v):
         """lam_x, lam_v: (3, n) CUDA tensors; returns (grad_x0, grad_v0, grad_m)."""

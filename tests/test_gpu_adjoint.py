@@ -149,3 +149,15 @@ def test_own_recording_and_autograd(cuda_lib, case):
     gx, gv, gm = s.adjoint_backward(wx, torch.zeros_like(wx))
     np.testing.assert_array_equal(gx.cpu().numpy(), x0.grad.cpu().numpy())
     np.testing.assert_array_equal(gm.cpu().numpy(), m.grad.cpu().numpy())
+
+
+def test_exported_recording_replays_bit_exactly(cuda_lib):
+    wl = disk(200, 0.9, 1.1, 2.0, 41, name="dense2")
+    s, pos, vel, mass = _system(cuda_lib, wl)
+    s.adjoint_forward(5, 2)
+    rc, pairs = s.adjoint_export()
+    assert rc.shape == (5, wl.n) and len(pairs) == 5 and sum(len(q) for q in pairs) > 0
+    s2, pos2, vel2, _ = _system(cuda_lib, wl)
+    s2.adjoint_load(2, rc, pairs)
+    assert np.array_equal(pos.cpu().numpy(), pos2.cpu().numpy())
+    assert np.array_equal(vel.cpu().numpy(), vel2.cpu().numpy())
