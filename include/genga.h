@@ -199,7 +199,8 @@ int genga_get_stats(genga_system_t *sys, genga_stats_t *st);
 /* Records a forward run: saves the current state as the initial state, runs
  * nsteps normal steps (leaving the final state in pos/vel) and keeps each
  * step's rc and pairs and a checkpoint every checkpoint_every steps.
- * Errors: EINVAL (slevels != 1), the errors of genga_step.                  */
+ * genga_get_stats then reports the whole run (sums; maxima for max_group and
+ * bs_max_attempts).  Errors: EINVAL (slevels != 1), the errors of genga_step. */
 int genga_adjoint_forward(genga_system_t *sys, int64_t nsteps, int64_t checkpoint_every);
 
 /* Uses a recording made elsewhere: rc_hist (host, nsteps x n doubles, step

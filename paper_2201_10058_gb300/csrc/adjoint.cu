@@ -139,13 +139,6 @@ __global__ void drift_vjp_kernel(int n, const double *x1, const double *v1, cons
 constexpr int kAdjThreads = 128;
 constexpr int kAdjTile = 128;
 
-__device__ __forceinline__ double changeover_dr_dev(double r, double rc) {
-    const double y = (r / rc - 0.1) / 0.9;
-    if (y <= 0.0 || y >= 1.0) return 0.0;
-    const double D = 2.0 * y * y - 2.0 * y + 1.0;
-    return 2.0 * y * (1.0 - y) / (D * D) / (0.9 * rc);
-}
-
 __global__ void __launch_bounds__(kAdjThreads)
 kick_vjp_kernel(int n, const double *pos, const double *mass, const double *rc, const double *lv,
                 int chunk, double *part /* [nchunk][4][n] */) {
@@ -242,7 +235,8 @@ __global__ void hc_vjp_kernel(int n, const double *sigma, const double *vel, con
 //   dy/dtau = -f(y)
 //   dlx/dtau = A^T lv,  dlv/dtau = lx        (J = [[0, I], [A, 0]], A = da/dx)
 //   dg_a/dtau = G sum_p W lv_p . (x_a - x_p)/r^3   (da_p/dm_a)
-// Error control on y only.  One CTA per group, state in a global scratch.
+// Error control on y only.  One CTA per group of at most kBlockGroupMax
+// members, state in a global scratch (larger groups: bsm.cu).
 constexpr int kAD = 13;                      // values per member
 constexpr int kABs = 64;                     // threads per CTA
 
@@ -320,6 +314,7 @@ __global__ void __launch_bounds__(kABs) bs_adjoint_kernel(AdjBsArgs A) {
     if (blockIdx.x >= *A.ngroups) return;
     const int g = A.glist[blockIdx.x];
     const int s0 = A.goff[g], s1 = A.goff[g + 1];
+    if (s1 - s0 > kBlockGroupMax) return;                // the batched driver's groups
     const size_t N = (size_t)A.n;
     for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
         const int b = A.member[s];
@@ -531,7 +526,10 @@ int replay_step(genga_system *s, int64_t k) {
                             cudaMemcpyDeviceToDevice, s->stream));
         ACU(build_csr(s, 0, np));
         ACU(build_groups(s, 0, np));
-        ACU(launch_bs(s, 0, dt, std::min<int64_t>(np, s->n / 2 + 1)));
+        {
+            const int brc = run_bs(s, 0, dt, np);
+            if (brc != GENGA_OK) return brc;
+        }
     }
     ACU(launch_hc(s, h));
     ACU(launch_kick(s, h, false, nullptr));
@@ -585,7 +583,10 @@ int step_vjp(genga_system *s, int64_t k, const double *start, double *lx, double
                             cudaMemcpyDeviceToDevice, s->stream));
         ACU(build_csr(s, 0, np));
         ACU(build_groups(s, 0, np));
-        ACU(launch_bs(s, 0, dt, std::min<int64_t>(np, s->n / 2 + 1)));
+        {
+            const int brc = run_bs(s, 0, dt, np);
+            if (brc != GENGA_OK) return brc;
+        }
     }
     // (x2, v2)
     ACU(cudaMemcpyAsync(a->tmp, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
@@ -613,6 +614,7 @@ int step_vjp(genga_system *s, int64_t k, const double *start, double *lx, double
         bs_adjoint_kernel<<<(unsigned)std::min<int64_t>(np, s->n / 2 + 1), kABs, 0, s->stream>>>(B);
         ++s->launches;
         ACU(cudaGetLastError());
+        if ((rc = bsm_adjoint_groups(s, a->tmp, a->tmp + 3 * n, lx, lv, lm, dt)) != GENGA_OK) return rc;
     }
     if ((rc = hc_vjp(s, lx, s->pre_vel[0], lv, lm, h)) != GENGA_OK) return rc;
     if ((rc = kick_vjp(s, start, lv, lx, lm, h)) != GENGA_OK) return rc;
@@ -640,6 +642,20 @@ int forward_checkpointed(genga_system *s) {
 
 extern "C" {
 
+// Sums (maxima for the largest group and attempt counts) of per-step statistics.
+static void accumulate_stats(genga_stats_t &t, const genga_stats_t &x) {
+    t.n_candidates += x.n_candidates;
+    for (int l = 0; l < 8; l++) t.n_pairs[l] += x.n_pairs[l];
+    t.n_groups += x.n_groups;
+    t.max_group = std::max(t.max_group, x.max_group);
+    t.bs_steps += x.bs_steps;
+    t.bs_rejects += x.bs_rejects;
+    t.kepler_fail += x.kepler_fail;
+    t.bs_fail += x.bs_fail;
+    t.kernel_launches += x.kernel_launches;
+    t.bs_max_attempts = std::max(t.bs_max_attempts, x.bs_max_attempts);
+}
+
 int genga_adjoint_forward(genga_system_t *s, int64_t nsteps, int64_t checkpoint_every) {
     if (!s || nsteps < 1 || checkpoint_every < 1 || s->p.slevels != 1) return GENGA_EINVAL;
     int rc = adj_alloc(s, nsteps, checkpoint_every);
@@ -648,6 +664,8 @@ int genga_adjoint_forward(genga_system_t *s, int64_t nsteps, int64_t checkpoint_
     const size_t n = (size_t)s->n;
     ACU(cudaMemcpyAsync(a->x0, s->pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
     ACU(cudaMemcpyAsync(a->v0, s->vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s->stream));
+    genga_stats_t total;
+    memset(&total, 0, sizeof(total));
     for (int64_t k = 0; k < nsteps; k++) {
         if (k % checkpoint_every == 0) {
             double *c = a->ckpt + (size_t)(k / checkpoint_every) * 6 * n;
@@ -656,10 +674,12 @@ int genga_adjoint_forward(genga_system_t *s, int64_t nsteps, int64_t checkpoint_
         }
         rc = genga_step(s, 1);
         if (rc != GENGA_OK) return rc;
+        accumulate_stats(total, s->stats);
         ACU(cudaMemcpyAsync(a->rc_hist + (size_t)k * n, s->rcl[0].rc, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
         rc = adj_push_pairs(s, s->pairs[0], s->npairs_host[0], false);
         if (rc != GENGA_OK) return rc;
     }
+    s->stats = total;
     ACU(cudaStreamSynchronize(s->stream));
     return GENGA_OK;
 }

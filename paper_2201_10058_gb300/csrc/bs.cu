@@ -2,28 +2,25 @@
 // Appendix A "Bulirsch-Stoer(dt)") and the level kick KickS of the
 // higher-level changeover scheme (Sec. 4.3, Appendix A).
 //
-// BS for groups of more than 32 members: one CTA per group, members strided
-// over the CTA's threads (groups of at most 32 go to bs_cols_kernel below).
-// Each member integrates
+// BS for groups of at most kBlockGroupMax (32) members: one CTA per group with
+// the 8 extrapolation columns advanced at once (bs_cols_kernel below; larger
+// groups go to the batched grid-wide driver in bsm.cu).  Each member
+// integrates
 //     dx/dt = v,   dv/dt = -mu x/|x|^3 + G sum_{partners j} m_j W_ij (x_j - x)/r^3,
 //     W_ij = prod_{k=0..level} (1 - K(r_ij; rc_k,ij)),
 // with partners taken from the ascending partner list of the level's
 // encounter pairs (the BS-A partner-list scheme of Sec. 4.1; the sum order is
 // fixed, so results do not depend on member layout).  Modified midpoint with
-// n = 2, 4, ..., 16 and polynomial extrapolation in h^2 (Neville, in place);
-// error = max over members and components of |T_kk - T_k,k-1| / scale with
+// n = 2, 4, ..., 16 and polynomial extrapolation in h^2 (Neville); error =
+// max over members and components of |T_kk - T_k,k-1| / scale with
 // scale = |y| + |H dy/dt| + 1e-300; accept at the first column k >= 1 with
 // error <= tol, grow H by 1.5 if k < 4, otherwise halve H.  The step control is
 // evaluated identically by every thread after a CTA-wide max reduction.
-// State lives in a global scratch (84 doubles per member slot, component-major,
-// L2-resident), so the kernel has no group-size limit.
 #include "common.cuh"
 
 namespace genga {
 namespace {
 
-constexpr int kBsThreads = 64;
-constexpr int kBsCols = 8;
 
 struct BsArgs {
     int n;
@@ -34,173 +31,16 @@ struct BsArgs {
     int nlev;
     const int *off, *list;
     const int *glist, *goff, *member, *slotof;
-    double *scr;     // [84][S]
-    size_t S;
     double G, mu, dt, tol;
     int max_steps;
     unsigned long long time_limit_ns;
     DevCounters *ctr;
 };
 
-// scratch rows
-enum { kY = 0, kF0 = 6, kZM = 12, kZN = 18, kFZ = 24, kSC = 30, kT = 36 };  // T: 48 rows
-
-__device__ __forceinline__ double &R(const BsArgs &A, int row, int slot) {
-    return A.scr[(size_t)row * A.S + slot];
-}
-
-// derivative of member slot s from the state rows z0..z0+5 into rows f0..f0+5
-__device__ void bs_deriv(const BsArgs &A, int z0, int f0, int s) {
-    const int b = A.member[s];
-    const double x = R(A, z0 + 0, s), y = R(A, z0 + 1, s), z = R(A, z0 + 2, s);
-    const double r2 = x * x + y * y + z * z;
-    const double sst = -A.mu / (r2 * sqrt(r2));
-    double px = 0.0, py = 0.0, pz = 0.0;
-    for (int q = A.off[b]; q < A.off[b + 1]; q++) {
-        const int p = A.list[q];
-        const int sp = A.slotof[p];
-        const double dx = R(A, z0 + 0, sp) - x, dy = R(A, z0 + 1, sp) - y, dz = R(A, z0 + 2, sp) - z;
-        const double d2 = dx * dx + dy * dy + dz * dz;
-        const double d = sqrt(d2);
-        double W = 1.0;
-        for (int l = 0; l < A.nlev; l++) W *= 1.0 - changeover(d, fmax(A.rc[l][b], A.rc[l][p]));
-        const double c = A.mass[p] * W / (d2 * d);
-        px += c * dx; py += c * dy; pz += c * dz;
-    }
-    R(A, f0 + 0, s) = R(A, z0 + 3, s);
-    R(A, f0 + 1, s) = R(A, z0 + 4, s);
-    R(A, f0 + 2, s) = R(A, z0 + 5, s);
-    R(A, f0 + 3, s) = sst * x + A.G * px;
-    R(A, f0 + 4, s) = sst * y + A.G * py;
-    R(A, f0 + 5, s) = sst * z + A.G * pz;
-}
-
-__device__ double block_max(double v, double *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double m = red[0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); k++) m = fmax(m, red[k]);
-    __syncthreads();
-    return m;
-}
-
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
-}
-
-__global__ void __launch_bounds__(kBsThreads)
-bs_kernel(BsArgs A) {
-    __shared__ double red[kBsThreads / 32];
-    __shared__ int stop;
-    if (blockIdx.x >= A.ctr->ngroups) return;
-    const unsigned long long t_start = global_ns();
-    const int g = A.glist[blockIdx.x];
-    const int s0 = A.goff[g], s1 = A.goff[g + 1];
-    if (s1 - s0 <= 32) return;                           // bs_cols_kernel's groups
-    const size_t N = (size_t)A.n;
-
-    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        const int b = A.member[s];
-        for (int c = 0; c < 3; c++) {
-            R(A, kY + c, s) = A.pre_pos[c * N + b];
-            R(A, kY + 3 + c, s) = A.pre_vel[c * N + b];
-        }
-    }
-    double t = 0.0, H = A.dt;
-    int attempts = 0;
-    long long acc = 0, rej = 0;
-    bool failed = false;
-    while (t < A.dt) {
-        // attempt limit and a wall-clock limit, decided by one thread for the CTA
-        if (threadIdx.x == 0)
-            stop = (attempts >= A.max_steps) || (global_ns() - t_start > A.time_limit_ns);
-        __syncthreads();
-        if (stop) { failed = true; break; }
-        attempts++;
-        if (H > A.dt - t) H = A.dt - t;
-        for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) bs_deriv(A, kY, kF0, s);
-        for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
-            for (int c = 0; c < 6; c++)
-                R(A, kSC + c, s) = fabs(R(A, kY + c, s)) + fabs(H * R(A, kF0 + c, s)) + 1e-300;
-        bool accepted = false;
-        int kconv = 0;
-        for (int k = 0; k < kBsCols; k++) {
-            const int nk = 2 * (k + 1);
-            const double h = H / nk;
-            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
-                for (int c = 0; c < 6; c++) {
-                    const double y0 = R(A, kY + c, s);
-                    R(A, kZM + c, s) = y0;
-                    R(A, kZN + c, s) = y0 + h * R(A, kF0 + c, s);
-                }
-            for (int m = 1; m < nk; m++) {
-                __syncthreads();
-                for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) bs_deriv(A, kZN, kFZ, s);
-                __syncthreads();
-                for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
-                    for (int c = 0; c < 6; c++) {
-                        const double tt = R(A, kZM + c, s) + 2.0 * h * R(A, kFZ + c, s);
-                        R(A, kZM + c, s) = R(A, kZN + c, s);
-                        R(A, kZN + c, s) = tt;
-                    }
-            }
-            __syncthreads();
-            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) bs_deriv(A, kZN, kFZ, s);
-            double err = 0.0;
-            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
-                for (int c = 0; c < 6; c++) {
-                    const double cur0 = 0.5 * (R(A, kZN + c, s) + R(A, kZM + c, s) + h * R(A, kFZ + c, s));
-                    double prev = R(A, kT + 0 * 6 + c, s);
-                    double cur = cur0;
-                    R(A, kT + 0 * 6 + c, s) = cur;
-                    for (int j = 1; j <= k; j++) {
-                        const double ratio = (double)nk / (double)(2 * (k - j + 1));
-                        const double nxt = cur + (cur - prev) / (ratio * ratio - 1.0);
-                        prev = R(A, kT + j * 6 + c, s);
-                        R(A, kT + j * 6 + c, s) = nxt;
-                        cur = nxt;
-                    }
-                    if (k >= 1) {
-                        const double e = fabs(R(A, kT + k * 6 + c, s) - R(A, kT + (k - 1) * 6 + c, s)) / R(A, kSC + c, s);
-                        err = fmax(err, e);
-                    }
-                }
-            err = block_max(err, red);
-            if (k >= 1 && err <= A.tol) { accepted = true; kconv = k; break; }
-        }
-        if (accepted) {
-            for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x)
-                for (int c = 0; c < 6; c++) R(A, kY + c, s) = R(A, kT + kconv * 6 + c, s);
-            t += H;
-            acc++;
-            if (kconv < 4) H *= 1.5;
-        } else {
-            rej++;
-            H *= 0.5;
-        }
-    }
-    __syncthreads();
-    for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        const int b = A.member[s];
-        for (int c = 0; c < 3; c++) {
-            A.pos[c * N + b] = R(A, kY + c, s);
-            A.vel[c * N + b] = R(A, kY + 3 + c, s);
-        }
-    }
-    if (threadIdx.x == 0) {
-        atomicMax(&A.ctr->bs_max_attempts, (unsigned long long)attempts);
-        atomicAdd(&A.ctr->bs_steps, (unsigned long long)acc);
-        atomicAdd(&A.ctr->bs_rejects, (unsigned long long)rej);
-        if (failed) {
-            atomicAdd(&A.ctr->bs_fail, 1ull);
-            latch_error(A.ctr, kErrBS);
-        }
-    }
 }
 
 // KickS at level l >= 1 over the level-(l-1) encounter pairs:
@@ -488,12 +328,11 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_group
     A.nlev = level + 1;
     A.off = s->csr[level].off; A.list = s->csr[level].list;
     A.glist = s->glist; A.goff = s->goff; A.member = s->member; A.slotof = s->slotof;
-    A.scr = s->bs_scratch; A.S = (size_t)s->n;
     A.G = s->p.G; A.mu = s->p.G * s->p.m_star; A.dt = dt_l; A.tol = s->p.bs_tol;
     A.max_steps = s->p.bs_max_steps;
     A.time_limit_ns = 10000000000ull;   // 10 s per group call
     A.ctr = s->ctr;
-    // the five size buckets run concurrently on library-owned streams so that
+    // the four size buckets run concurrently on library-owned streams so that
     // their slowest groups overlap
     GENGA_CUDA_TRY(cudaEventRecord(s->ev_fork, s->stream));
     for (int q = 0; q < 4; q++) GENGA_CUDA_TRY(cudaStreamWaitEvent(s->side[q], s->ev_fork, 0));
@@ -506,8 +345,10 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_group
     GENGA_CUDA_TRY(cudaGetLastError());
     bs_cols_kernel<32><<<grid, 256, 0, s->side[3]>>>(A); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    bs_kernel<<<grid, kBsThreads, 0, s->stream>>>(A); ++s->launches;
-    GENGA_CUDA_TRY(cudaGetLastError());
+    return cudaGetLastError();
+}
+
+cudaError_t join_bs(genga_system *s) {
     for (int q = 0; q < 4; q++) {
         GENGA_CUDA_TRY(cudaEventRecord(s->ev_join[q], s->side[q]));
         GENGA_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_join[q], 0));

@@ -12,6 +12,9 @@
 namespace genga {
 
 constexpr int kMaxLevels = 8;
+// Close-encounter groups with more members than this are integrated by the
+// batched grid-wide Bulirsch-Stoer driver (bsm.cu) instead of one thread block.
+constexpr int kBlockGroupMax = 32;
 
 // Device error word bits (latched; read by the host after synchronising).
 enum : unsigned {
@@ -112,8 +115,8 @@ struct genga_system {
     int *slotof = nullptr;   // n
     int label_level = -1;    // level whose grouping `label` holds
 
-    // Bulirsch-Stoer scratch: 90 doubles per member slot
-    double *bs_scratch = nullptr;
+    // batched grid-wide Bulirsch-Stoer buffers (bsm.cu), grown on demand
+    void *bsm = nullptr;
 
     // HC / energy reductions
     double *red = nullptr;   // reduction scratch
@@ -200,7 +203,18 @@ int ensure_pair_capacity(genga_system *s, int level, int64_t np);
 void adjoint_free(genga_system *s);
 
 // bs.cu
+// Batched grid-wide Bulirsch-Stoer of the groups larger than kBlockGroupMax
+// (bsm.cu); genga error codes.
+int bsm_forward_groups(genga_system *s, int level, double dt_l);
+void bsm_release(genga_system *s);
+// launch_bs, bsm_forward_groups on the system stream meanwhile, join_bs.
+int run_bs(genga_system *s, int level, double dt_l, int64_t np);
+int bsm_adjoint_groups(genga_system *s, const double *x2, const double *v2, double *lx, double *lv,
+                       double *lm, double dt);
+// Launches the in-block BS kernels on the side streams (forked from the
+// system stream); join_bs makes the system stream wait for them.
 cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_groups);
+cudaError_t join_bs(genga_system *s);
 cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb);
 
 // ---------------------------------------------------------------------------
@@ -290,6 +304,14 @@ __device__ __forceinline__ bool kepler_drift(double &x, double &y, double &z, do
     return ok;
 }
 
+// dK/dr of changeover() (zero outside the transition band 0.1 rc < r < rc).
+__device__ __forceinline__ double changeover_dr_dev(double r, double rc) {
+    const double y = (r / rc - 0.1) / 0.9;
+    if (y <= 0.0 || y >= 1.0) return 0.0;
+    const double D = 2.0 * y * y - 2.0 * y + 1.0;
+    return 2.0 * y * (1.0 - y) / (D * D) / (0.9 * rc);
+}
+
 // ---------------------------------------------------------------------------
 // FP64 reciprocal square root and reciprocal from an FP32 hardware seed plus
 // Newton steps in FP64 (two steps reach full double precision).  The seed's
@@ -338,6 +360,19 @@ __device__ __forceinline__ double changeover_fast(double r, double irc) {
     const double y2 = y * y;
     const double w = 1.0 - y;
     return y2 * rcp_newton(fma(w, w, y2));
+}
+// K and dK/dr with 1/rc supplied: the definitions of changeover() and
+// changeover_dr_dev() (dK/dy = 2y(1 - y)/D^2, D = y^2 + (1 - y)^2, dy/dr = 1/(0.9 rc)),
+// in contracted FP64 arithmetic for force terms.
+__device__ __forceinline__ void changeover_fast_dr(double r, double irc, double &K, double &dK) {
+    const double y = fma(r, irc, -0.1) * (1.0 / 0.9);
+    if (y <= 0.0) { K = 0.0; dK = 0.0; return; }
+    if (y >= 1.0) { K = 1.0; dK = 0.0; return; }
+    const double y2 = y * y;
+    const double w = 1.0 - y;
+    const double iD = rcp_newton(fma(w, w, y2));
+    K = y2 * iD;
+    dK = 2.0 * y * w * (iD * iD) * (irc * (1.0 / 0.9));
 }
 
 }  // namespace genga

@@ -132,7 +132,6 @@ int alloc_all(genga_system *s) {
     CU(dalloc(&s->glist, n + 1));
     CU(dalloc(&s->member, n + 1));
     CU(dalloc(&s->slotof, n));
-    CU(dalloc(&s->bs_scratch, 84 * n));
     CU(dalloc(&s->red, 9 * n + 16));
     s->scr.scan_blocks_cap = (int)((n + 1 + 4095) / 4096) + 2;
     CU(dalloc(&s->scr.scan_blocks, (size_t)s->scr.scan_blocks_cap));
@@ -152,7 +151,7 @@ void free_all(genga_system *s) {
     }
     dfree(s->kick_part); dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
     dfree(s->gsize); dfree(s->goff); dfree(s->gfill); dfree(s->glist); dfree(s->member);
-    dfree(s->slotof); dfree(s->bs_scratch); dfree(s->red); dfree(s->scr.scan_blocks);
+    dfree(s->slotof); bsm_release(s); dfree(s->red); dfree(s->scr.scan_blocks);
     for (int k = 0; k < 4; k++) {
         if (s->side[k]) cudaStreamDestroy(s->side[k]);
         if (s->ev_join[k]) cudaEventDestroy(s->ev_join[k]);
@@ -232,8 +231,7 @@ int detect(genga_system *s, const uint2 *in, int64_t nin, int level, int64_t *np
 
 int bs_groups(genga_system *s, int level, int64_t np, double dt_l) {
     CU(build_groups(s, level, np));
-    CU(launch_bs(s, level, dt_l, std::min<int64_t>(np, s->n / 2 + 1)));
-    return GENGA_OK;
+    return run_bs(s, level, dt_l, np);
 }
 
 int senc(genga_system *s, int level, double dt_l) {
@@ -474,7 +472,7 @@ int genga_bs(genga_system_t *s, double dt) {
     const int64_t np = s->npairs_host[0];
     if (np > 0) {
         if (s->label_level != 0) CU(build_groups(s, 0, np));
-        CU(launch_bs(s, 0, dt, std::min<int64_t>(np, s->n / 2 + 1)));
+        TRY(run_bs(s, 0, dt, np));
     }
     TRY(collect_stats(s));
     return device_errors(s);

@@ -22,3 +22,23 @@ def cuda_lib():
     from paper_2201_10058_gb300 import genga
     genga.load()
     return genga
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Logs the candidate pairs found within 1e-12 relative of their critical
+    radius by the detection parity tests (their decisions were compared
+    bit-exactly with the oracle's like all others)."""
+    try:
+        from tests import borderline
+    except ImportError:
+        return
+    if not borderline.LOG:
+        return
+    tr = terminalreporter
+    tr.section(f"encounter pairs within {borderline.REL:g} relative of r_crit")
+    for case, ncand, found in borderline.LOG:
+        tr.write_line(f"{case}: {len(found)} of {ncand} candidates")
+        for tag, i, j, q in found[:20]:
+            tr.write_line(f"    ({i}, {j}) {tag} |r/rc - 1| = {q:.3e}")
+        if len(found) > 20:
+            tr.write_line(f"    ... {len(found) - 20} more")

@@ -1,0 +1,207 @@
+"""Close-encounter groups of more than 32 members: the batched grid-wide
+Bulirsch-Stoer driver (Sec. 4.1, the BS-M case) for the forward step and for
+the adjoint's augmented backward integration, against the oracle, through the
+C ABI.
+
+Inputs: rings of n equal masses whose neighbours lie inside r_crit, so that the
+whole ring forms one group; radii and speeds jittered (seeded) and the time
+step lengthened so that the step control takes tens of attempts with
+rejections.  Several rings at once give several groups whose step controls
+run side by side in one batch.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import G_GAUSS, ring
+
+pytestmark = pytest.mark.gpu
+
+G = G_GAUSS
+CASES = [(300, 60.0), (1000, 40.0)]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ring(n, dt, seed=5):
+    wl = ring(n, dt=dt)
+    rng = np.random.default_rng(seed)
+    wl.x = wl.x * (1 + 2e-4 * rng.standard_normal((n, 1)))
+    wl.v = wl.v * (1 + 1e-3 * rng.standard_normal((n, 1)))
+    return wl
+
+
+def _system(g, wl, x=None, v=None, **kw):
+    torch = _torch()
+    dev = torch.device("cuda:0")
+    pos = torch.tensor(np.ascontiguousarray((wl.x if x is None else x).T), device=dev)
+    vel = torch.tensor(np.ascontiguousarray((wl.v if v is None else v).T), device=dev)
+    mass = torch.tensor(wl.m, device=dev)
+    p = g.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc)
+    for k, val in kw.items():
+        setattr(p, k, val)
+    return g.System(pos, vel, mass, p), pos, vel, mass
+
+
+def _host(t):
+    return t.detach().cpu().numpy().T.copy()
+
+
+@pytest.mark.parametrize("n,dt", CASES)
+def test_giant_group_bs_matches_oracle(cuda_lib, n, dt):
+    torch = _torch()
+    wl = _ring(n, dt)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    v1 = O.kick(wl.x, wl.v, wl.m, rc, G, 0.5 * wl.dt, nthreads=8)
+    x1 = O.hc(wl.x, v1, wl.m, wl.m_star, 0.5 * wl.dt)
+    x2, v2, _ = O.drift(x1, v1, G * wl.m_star, wl.dt)
+    cand = O.precheck(wl.x, rc, wl.f_pc)
+    s, pos, vel, mass = _system(cuda_lib, wl)
+    s.set_rcrit(rc)
+    s.kick(0.0, precheck=True, acc_out=torch.zeros((3, n), dtype=torch.float64, device="cuda:0"))
+    s.set_predrift(x1.T, v1.T)
+    pos.copy_(torch.tensor(x2.T.copy()))
+    vel.copy_(torch.tensor(v2.T.copy()))
+    npairs, ngroups, maxg = s.build_encounters()
+    assert ngroups == 1 and maxg == n > 32
+    s.bs(wl.dt)
+    pairs = O.detect(cand, x1, x2, rc)
+    xb, vb, st, stats = O.bs_groups(x1, v1, wl.m, rc[None], pairs, G, wl.m_star, wl.dt)
+    assert st == 0
+    gs = s.stats()
+    # same step-control decisions as the oracle: attempts and rejections
+    assert (gs["bs_steps"], gs["bs_rejects"]) == (stats["bs_steps"], stats["bs_rejects"])
+    assert gs["bs_rejects"] > 0
+    np.testing.assert_allclose(_host(pos), xb, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(_host(vel), vb, rtol=0, atol=1e-15)
+
+
+def test_batched_groups_bs_match_oracle(cuda_lib):
+    """Three rings (40, 100 and 300 members at 1, 2 and 3.5 AU) integrated in
+    one batch: totals of accepted and rejected attempts equal the oracle's and
+    the states agree."""
+    torch = _torch()
+    dt = 300.0                      # long enough that the groups need 3 to 20 attempts
+    parts = []
+    for n, r, k, seed in ((40, 1.0, 2, 7), (100, 2.0, 4, 8), (300, 3.5, 8, 9)):
+        w = ring(n, r=r, dt=dt, partners=k)
+        rng = np.random.default_rng(seed)
+        w.x = w.x * (1 + 2e-4 * rng.standard_normal((n, 1)))
+        w.v = w.v * (1 + 1e-3 * rng.standard_normal((n, 1)))
+        rcw = O.rcrit(w.x, w.v, w.m, w.m_star, w.dt, w.n1, w.n2)
+        parts.append((w, rcw))
+    wl = parts[0][0]
+    x = np.concatenate([w.x for w, _ in parts])
+    v = np.concatenate([w.v for w, _ in parts])
+    m = np.concatenate([w.m for w, _ in parts])
+    rc = np.concatenate([r for _, r in parts])
+    n = len(m)
+    wl.x, wl.v, wl.m = x, v, m
+    v1 = O.kick(x, v, m, rc, G, 0.5 * dt, nthreads=8)
+    x1 = O.hc(x, v1, m, wl.m_star, 0.5 * dt)
+    x2, v2, _ = O.drift(x1, v1, G * wl.m_star, dt)
+    cand = O.precheck(x, rc, wl.f_pc)
+    s, pos, vel, mass = _system(cuda_lib, wl)
+    s.set_rcrit(rc)
+    s.kick(0.0, precheck=True, acc_out=torch.zeros((3, n), dtype=torch.float64, device="cuda:0"))
+    s.set_predrift(x1.T, v1.T)
+    pos.copy_(torch.tensor(x2.T.copy()))
+    vel.copy_(torch.tensor(v2.T.copy()))
+    npairs, ngroups, maxg = s.build_encounters()
+    assert ngroups == 3 and maxg == 300
+    assert sorted(np.bincount(s.groups()[s.groups() >= 0])[np.bincount(s.groups()[s.groups() >= 0]) > 0]) \
+        == [40, 100, 300]
+    s.bs(dt)
+    pairs = O.detect(cand, x1, x2, rc)
+    xb, vb, st, stats = O.bs_groups(x1, v1, m, rc[None], pairs, G, wl.m_star, dt)
+    assert st == 0
+    gs = s.stats()
+    assert (gs["bs_steps"], gs["bs_rejects"], gs["bs_max_attempts"]) == \
+        (stats["bs_steps"], stats["bs_rejects"], stats["bs_max_attempts"])
+    # 300-day steps amplify rounding: the oracle's own result moves by up to
+    # 6.8e-13 when its input moves by one ulp; allow 3x that spread
+    xs, vs, _, _ = O.bs_groups(np.nextafter(x1, np.inf), v1, m, rc[None], pairs, G, wl.m_star, dt)
+    sx = max(np.abs(xs - xb).max(), 1e-14)
+    sv = max(np.abs(vs - vb).max(), 1e-16)
+    assert np.abs(_host(pos) - xb).max() <= 3 * sx
+    assert np.abs(_host(vel) - vb).max() <= 3 * sv
+
+
+@pytest.mark.parametrize("n,dt", CASES)
+def test_giant_group_steps_match_oracle(cuda_lib, n, dt):
+    wl = _ring(n, dt)
+    p = O.make_params(wl, nthreads=8)
+    xr, vr, st, stats = O.step(wl.x, wl.v, wl.m, p, 3)
+    assert st == 0 and stats["max_group"] == n
+    s, pos, vel, mass = _system(cuda_lib, wl)
+    s.step(3)
+    gs = s.stats()
+    assert gs["max_group"] == n
+    # a column error within rounding of the tolerance may be accepted on one side and
+    # rejected on the other (both results are within the tolerance): allow a few
+    # differing step-control decisions over the 3 steps, then compare the states
+    assert abs(gs["bs_steps"] - stats["bs_steps"]) <= 3
+    assert abs(gs["bs_rejects"] - stats["bs_rejects"]) <= 3
+    err = np.linalg.norm(_host(pos) - xr, axis=1) / np.linalg.norm(xr, axis=1)
+    assert err.max() <= 1e-12, err.max()
+
+
+def test_giant_group_attempt_limit_reports_nonconvergence(cuda_lib):
+    g = cuda_lib
+    wl = _ring(300, 60.0)
+    p = O.make_params(wl, nthreads=8)
+    *_, stats = O.step(wl.x, wl.v, wl.m, p, 1)
+    assert stats["bs_max_attempts"] >= 2            # the first step needs more attempts
+    s, *_ = _system(g, wl, bs_max_steps=stats["bs_max_attempts"] - 1)
+    with pytest.raises(g.GengaError) as e:
+        s.step(1)
+    assert e.value.code == -3
+    s2, *_ = _system(g, _ring(300, 6.0))
+    s2.step(1)
+
+
+@pytest.fixture(scope="module")
+def giant_case():
+    wl = _ring(300, 60.0)
+    p = O.make_params(wl, nthreads=8)
+    x, v = wl.x, wl.v
+    rcs, pairs = [], []
+    for _ in range(3):
+        x, v, rc, pr, st = O.step_record(x, v, wl.m, p)
+        assert st == 0
+        rcs.append(rc)
+        pairs.append(pr)
+    return wl, p, np.array(rcs), pairs, x, v
+
+
+def test_giant_group_replay_matches_oracle(cuda_lib, giant_case):
+    wl, p, rcs, pairs, xN, vN = giant_case
+    s, pos, vel, mass = _system(cuda_lib, wl)
+    s.adjoint_load(2, rcs, pairs)
+    assert np.abs(_host(pos) - xN).max() <= 1e-12 * np.abs(xN).max()
+
+
+def test_giant_group_adjoint_dot_product_identity(cuda_lib, giant_case):
+    torch = _torch()
+    wl, p, rcs, pairs, xN, vN = giant_case
+    rng = np.random.default_rng(11)
+    dx0 = rng.standard_normal(wl.x.shape)
+    dv0 = rng.standard_normal(wl.v.shape) * 0.017
+    dm0 = rng.standard_normal(wl.m.shape) * wl.m
+    x, v, dx, dv = wl.x, wl.v, dx0, dv0
+    for rc, pr in zip(rcs, pairs):
+        x, v, dx, dv, st = O.step_frozen(x, v, wl.m, p, rc, pr, dx, dv, dm0)
+        assert st == 0
+    lx, lv = rng.standard_normal(wl.x.shape), rng.standard_normal(wl.v.shape)
+    lhs = (lx * dx).sum() + (lv * dv).sum()
+    s, pos, vel, mass = _system(cuda_lib, wl)
+    s.adjoint_load(2, rcs, pairs)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a.T), device="cuda:0")
+    gx, gv, gm = s.adjoint_backward(T(lx), T(lv))
+    gx, gv, gm = gx.cpu().numpy().T, gv.cpu().numpy().T, gm.cpu().numpy()
+    rhs = (gx * dx0).sum() + (gv * dv0).sum() + (gm * dm0).sum()
+    scale = abs((gx * dx0).sum()) + abs((gv * dv0).sum()) + abs((gm * dm0).sum())
+    assert abs(lhs - rhs) <= 1e-9 * scale, (lhs, rhs)

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tests import borderline
 from workloads import G_GAUSS, config_workload, disk, ring
 
 pytestmark = pytest.mark.gpu
@@ -203,6 +204,7 @@ def test_detection_and_grouping_bit_exact(g, name, make):
     vel.copy_(torch.tensor(v2.T.copy()))
     npairs, ngroups, maxg = s.build_encounters()
     ref_pairs = O.detect(cand, x1, x2, rc)
+    borderline.record(name, cand, x1, x2, rc)
     assert npairs == len(ref_pairs) > 0
     np.testing.assert_array_equal(s.pairs(0), ref_pairs)
     lab = s.groups()
@@ -210,6 +212,47 @@ def test_detection_and_grouping_bit_exact(g, name, make):
     np.testing.assert_array_equal(lab, ref_lab)
     assert ngroups == len(np.unique(ref_lab[ref_lab >= 0]))
     assert maxg == np.bincount(ref_lab[ref_lab >= 0]).max()
+
+
+def test_detection_at_the_critical_radius(g):
+    """Pairs placed at r = rc (1 + k u), u = 2^-53, k in -8..8, and at 1e-13 and
+    1e-12 relative: the detection decisions (r^2 < rc^2 before or after the drift)
+    equal the oracle's, pair by pair."""
+    torch = _torch()
+    rng = np.random.default_rng(20110058)
+    u = 2.0 ** -53
+    rel = [k * u for k in range(-8, 9)] + [1e-13, -1e-13, 1e-12, -1e-12, 3e-12]
+    npair = len(rel)
+    n = 2 * npair
+    rc = np.full(n, 0.01)
+    x = np.zeros((n, 3))
+    for k, q in enumerate(rel):
+        c = np.array([1.0 + 0.1 * k, 0.3 * k, 0.0])          # pairs 0.1 AU+ apart
+        d = rng.standard_normal(3)
+        d *= 0.01 * (1.0 + q) / np.linalg.norm(d)
+        x[2 * k] = c
+        x[2 * k + 1] = c + d
+    v = np.zeros((n, 3))
+    v[:, 1] = 0.017
+    m = np.full(n, 1e-9)
+    wl = disk(n, 0.5, 2.0, 2.0, 1, name="critical")
+    wl.x, wl.v, wl.m = x, v, m
+    s, pos, vel, mass = _system(g, wl, 0)
+    s.set_rcrit(rc)
+    s.kick(0.0, precheck=True, acc_out=torch.zeros((3, n), dtype=torch.float64, device="cuda:0"))
+    cand = s.candidates()
+    ref_cand = O.precheck(x, rc, wl.f_pc)
+    np.testing.assert_array_equal(cand, ref_cand)
+    assert len(cand) == npair
+    # pre-drift = post-drift = x: the decision is the one comparison per pair
+    s.set_predrift(x.T, v.T)
+    s.build_encounters()
+    ref_pairs = O.detect(cand, x, x, rc)
+    found = borderline.record("critical-radius construction", cand, x, x, rc)
+    assert len(found) >= 17 * 2
+    np.testing.assert_array_equal(s.pairs(0).reshape(-1, 2), ref_pairs.reshape(-1, 2))
+    # both decisions occur among the pairs placed within a few ulp of rc
+    assert 0 < len(ref_pairs) < npair
 
 
 @pytest.mark.parametrize("n", [16, 128, 1000])
