@@ -36,11 +36,12 @@ METRIC = ("changeover-kick G pair-interactions/s and steps/s at N=65536 (FP64 vs
           "% of peak")
 UNIT = "Gpair/s"
 # FP64 instructions per pair interaction that each kick form's algorithm needs
-# (FMA counted as one).  Mixed: displacement 3, r^2 3, Newton residual
-# 1 - r^2 y0^2 of the FP32 seed 2, joining the float-float m r^-3 1,
-# accumulation 3.  FP64: displacement 3, r^2 3, r^-1 to FP64 precision (two
-# Newton steps from a ~2^-22 seed) 6, m r^-3 3, accumulation 3.
-FP64_OPS_PER_PAIR = {"mixed": 12, "fp64": 18}
+# (FMA counted as one).  Mixed: displacement 3, Newton residual
+# 1 - Rh y0^2 of the FP32 seed 2 (r^2 = Rh + Rl is formed in float-float on the
+# FP32 pipe), joining the float-float m r^-3 1, accumulation 3.  FP64:
+# displacement 3, r^2 3, r^-1 to FP64 precision (two Newton steps from a
+# ~2^-22 seed) 6, m r^-3 3, accumulation 3.
+FP64_OPS_PER_PAIR = {"mixed": 9, "fp64": 18}
 FP64_OPS_PER_CLK_PER_SM = 2      # measured DFMA throughput per SM per clock on GB300
 
 

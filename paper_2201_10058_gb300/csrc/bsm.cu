@@ -1,15 +1,15 @@
 // bsm.cu -- Bulirsch-Stoer for close-encounter groups of more than
 // kBlockGroupMax members, spread over the whole GPU (the role of the paper's
 // BS-M, Sec. 4.1), with every such group of the current grouping advanced
-// together.
+// together by one persistent cooperative kernel.
 //
-// One round is one attempt of every still-running group, at its own step H:
+// One round is one attempt of every still-running group, at its own step H,
+// in phases separated by grid-wide barriers:
 //   start      derivative at the attempt's start, error scale, first
 //              midpoint sub-step of all 8 extrapolation columns;
-//   sub-step   launch `it` (1..16) moves every column whose n_k = 2(k+1)
-//              still has sub-steps left, over all (column, member) pairs
-//              (one thread each; ping-pong state buffers, so partner reads
-//              never race with writes);
+//   sub-step   it = 1..16 moves every column whose n_k = 2(k+1) still has
+//              sub-steps left, over all (column, member) pairs (ping-pong
+//              state buffers, so partner reads never race with writes);
 //   Neville    per (component, member): the extrapolation table, its
 //              diagonal, and each column's error folded into the group's 8
 //              error words (atomic max on the bits of non-negative doubles);
@@ -17,12 +17,14 @@
 //              -> accept (grow H by 1.5 if k < 4), else halve H; attempt
 //              and time bookkeeping; done / failed status;
 //   accept     members of accepting groups take the accepted column.
-// The step control never leaves the device.  The host enqueues a batch of
-// rounds and then reads the groups' status words once; rounds enqueued after
-// a group finished return at once for it.  A group fails after bs_max_steps
-// attempts, so at most bs_max_steps rounds run.  Scheme and acceptance rule
+// Step control and iteration stay on the device: the host launches once and
+// reads the result.  A group fails after bs_max_steps attempts, so at most
+// bs_max_steps rounds run; every barrier wait has a time limit (2 s) after
+// which the kernel records a timeout and returns.  Scheme and acceptance rule
 // are those of the in-block kernels (modified midpoint n = 2..16, Neville in
-// h^2, error scale |y| + |H dy/dt| + 1e-300).
+// h^2, error scale |y| + |H dy/dt| + 1e-300, the same force arithmetic).
+// Data written by one block and read by another inside the kernel is read
+// through L2 (ld.global.cg), never from a possibly stale L1 line.
 //
 // The ODE is a template policy: the group's forward ODE (6 values per member)
 // or the adjoint's augmented backward ODE (13 values per member).
@@ -35,42 +37,89 @@
 namespace genga {
 namespace {
 
-constexpr int kMThreads = 64;
+constexpr int kPThreads = 128;
+constexpr unsigned long long kBarrierNs = 2000000000ull;   // 2 s per barrier wait
+
+struct GridBarrier {
+    unsigned count;     // blocks arrived at the current barrier
+    unsigned gen;       // barrier generation
+    unsigned err;       // a wait ran out
+    unsigned running;   // groups still integrating
+};
 
 // Batch of groups: compact member index m in [0, M) over the groups.
 struct BsmArgs {
-    int n;                         // bodies in the system
     int M;                         // members over all batched groups
     int ng;                        // batched groups
-    const int *mbody;              // [M] body of compact member m
+    int nlev;                      // levels whose (1 - K) factors apply
+    // per member, written before the persistent launch
     const int *mgroup;             // [M] batched group of m
-    const double *irc;             // [nlev][M] 1/rc of compact member m per level
-    const int *gbase;              // [ng] first compact index of the group
-    const int *gslot0;             // [ng] first global slot of the group
-    const int *slotof;             // body -> global slot
-    const int *off, *list;         // partner CSR (global ids, ascending per row)
-    const double *mass;
-    int nlev;
+    const int *mq0, *mq1;          // [M] partner range in the level CSR
+    const int *pidx;               // [CSR entries] compact index of each partner
+    const double *mmass;           // [M] mass
+    const double *irc;             // [nlev][M] 1/rc per level
     double G, mu, dt, tol;
     int max_steps;
-    // per-group step control (device)
+    // state, component-major over members ([..][D][M])
+    double *Y, *F0, *SC;           // attempt start, its derivative, error scale
+    double *ZM, *ZA, *ZB;          // [8] per column: previous midpoint state, two current buffers
+    double *OUT, *DIAG;            // [8] column results, Neville diagonal T_kk
+    // per-group step control
     double *gt, *gH;
     int *gstat;                    // 0 running, 1 done, 2 failed
     int *gkconv;                   // accepted column of the last round, -1 none
     long long *gatt, *gacc, *grej;
     unsigned long long *gerr;      // [ng][8]
+    GridBarrier *bar;
 };
 
-// Partners of a member belong to its group (groups are connected components
-// of the same pair graph), so their compact index follows from the slot.
-__device__ __forceinline__ int partner_index(const BsmArgs &A, int g, int p) {
-    return A.gbase[g] + (A.slotof[p] - A.gslot0[g]);
-}
+__device__ __forceinline__ double ldc(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ int ldc(const int *p) { return __ldcg(p); }
 
 __device__ __forceinline__ double step_of(const BsmArgs &A, int g) {
-    const double H = A.gH[g];
-    const double left = A.dt - A.gt[g];
+    const double H = ldc(&A.gH[g]);
+    const double left = A.dt - ldc(&A.gt[g]);
     return H > left ? left : H;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier (all blocks co-resident: cooperative launch).  One
+// thread per block arrives with an atomic and polls the generation word with
+// volatile loads (served by L2); a wait longer than kBarrierNs records a
+// timeout.  Returns false if this or another block's wait ran out.
+__device__ bool grid_barrier(GridBarrier *b) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        volatile unsigned *gen = &b->gen;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned polls = 0;
+            while (*gen == g) {
+                if ((++polls & 1023u) == 0u && global_ns() - t0 > kBarrierNs) {
+                    atomicExch(&b->err, 1u);
+                    good = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok = good && *(volatile unsigned *)&b->err == 0u;
+    }
+    __syncthreads();
+    return ok != 0;
 }
 
 // Forward group ODE: y = (x, v); a = -mu x/r^3 + G sum_p m_p W (x_p - x)/r^3,
@@ -78,27 +127,28 @@ __device__ __forceinline__ double step_of(const BsmArgs &A, int g) {
 struct FwdOde {
     static constexpr int D = 6;
     static constexpr int NERR = 6;
-    __device__ static void deriv(const BsmArgs &A, const double *Z, size_t ld, int m, int g, double *f) {
-        const int b = A.mbody[m];
-        const double x = Z[0 * ld + m], y = Z[1 * ld + m], z = Z[2 * ld + m];
+    __device__ static void deriv(const BsmArgs &A, const double *Z, int m, double *f) {
+        const size_t ld = (size_t)A.M;
+        const double x = ldc(&Z[0 * ld + m]), y = ldc(&Z[1 * ld + m]), z = ldc(&Z[2 * ld + m]);
         const double r2 = fma(z, z, fma(y, y, x * x));
         const double ys = rsqrt_newton(r2);
         const double sst = -A.mu * (ys * ys * ys);
         double px = 0.0, py = 0.0, pz = 0.0;
-        for (int q = A.off[b]; q < A.off[b + 1]; q++) {
-            const int p = A.list[q];
-            const int sp = partner_index(A, g, p);
-            const double dx = Z[0 * ld + sp] - x, dy = Z[1 * ld + sp] - y, dz = Z[2 * ld + sp] - z;
+        const int q1 = A.mq1[m];
+        for (int q = A.mq0[m]; q < q1; q++) {
+            const int sp = A.pidx[q];
+            const double dx = ldc(&Z[0 * ld + sp]) - x, dy = ldc(&Z[1 * ld + sp]) - y,
+                         dz = ldc(&Z[2 * ld + sp]) - z;
             const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
             const double yv = rsqrt_newton(d2);
             const double d = d2 * yv;
             double W = 1.0;
             for (int l = 0; l < A.nlev; l++)
-                W *= 1.0 - changeover_fast(d, fmin(A.irc[(size_t)l * A.M + m], A.irc[(size_t)l * A.M + sp]));
-            const double c = A.mass[p] * W * (yv * yv * yv);
+                W *= 1.0 - changeover_fast(d, fmin(A.irc[(size_t)l * ld + m], A.irc[(size_t)l * ld + sp]));
+            const double c = A.mmass[sp] * W * (yv * yv * yv);
             px = fma(c, dx, px); py = fma(c, dy, py); pz = fma(c, dz, pz);
         }
-        f[0] = Z[3 * ld + m]; f[1] = Z[4 * ld + m]; f[2] = Z[5 * ld + m];
+        f[0] = ldc(&Z[3 * ld + m]); f[1] = ldc(&Z[4 * ld + m]); f[2] = ldc(&Z[5 * ld + m]);
         f[3] = fma(sst, x, A.G * px); f[4] = fma(sst, y, A.G * py); f[5] = fma(sst, z, A.G * pz);
     }
 };
@@ -110,11 +160,11 @@ struct FwdOde {
 struct AdjOde {
     static constexpr int D = 13;
     static constexpr int NERR = 6;
-    __device__ static void deriv(const BsmArgs &A, const double *Z, size_t ld, int m, int g, double *f) {
-        const int b = A.mbody[m];
-        const double x = Z[0 * ld + m], y = Z[1 * ld + m], z = Z[2 * ld + m];
-        const double lvx = Z[9 * ld + m], lvy = Z[10 * ld + m], lvz = Z[11 * ld + m];
-        const double mb = A.mass[b];
+    __device__ static void deriv(const BsmArgs &A, const double *Z, int m, double *f) {
+        const size_t ld = (size_t)A.M;
+        const double x = ldc(&Z[0 * ld + m]), y = ldc(&Z[1 * ld + m]), z = ldc(&Z[2 * ld + m]);
+        const double lvx = ldc(&Z[9 * ld + m]), lvy = ldc(&Z[10 * ld + m]), lvz = ldc(&Z[11 * ld + m]);
+        const double mb = A.mmass[m];
         const double r2 = fma(z, z, fma(y, y, x * x));
         const double ys = rsqrt_newton(r2);
         const double ir2 = ys * ys, ir3 = ir2 * ys;
@@ -124,10 +174,11 @@ struct AdjOde {
         const double ty = -A.mu * ir3 * (lvy - 3.0 * y * xl * ir2);
         const double tz = -A.mu * ir3 * (lvz - 3.0 * z * xl * ir2);
         double px = 0.0, py = 0.0, pz = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, gm = 0.0;
-        for (int q = A.off[b]; q < A.off[b + 1]; q++) {
-            const int p = A.list[q];
-            const int sp = partner_index(A, g, p);
-            const double dx = Z[0 * ld + sp] - x, dy = Z[1 * ld + sp] - y, dz = Z[2 * ld + sp] - z;
+        const int q1 = A.mq1[m];
+        for (int q = A.mq0[m]; q < q1; q++) {
+            const int sp = A.pidx[q];
+            const double dx = ldc(&Z[0 * ld + sp]) - x, dy = ldc(&Z[1 * ld + sp]) - y,
+                         dz = ldc(&Z[2 * ld + sp]) - z;
             const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
             const double yv = rsqrt_newton(d2);
             const double d = d2 * yv, id2 = yv * yv, id3 = id2 * yv;
@@ -135,10 +186,10 @@ struct AdjOde {
             changeover_fast_dr(d, fmin(A.irc[m], A.irc[sp]), K, dK);
             const double W = 1.0 - K;
             const double Wp = -dK;
-            const double mp = A.mass[p];
+            const double mp = A.mmass[sp];
             const double cw = mp * W * id3;
             px = fma(cw, dx, px); py = fma(cw, dy, py); pz = fma(cw, dz, pz);
-            const double qx = Z[9 * ld + sp], qy = Z[10 * ld + sp], qz = Z[11 * ld + sp];
+            const double qx = ldc(&Z[9 * ld + sp]), qy = ldc(&Z[10 * ld + sp]), qz = ldc(&Z[11 * ld + sp]);
             const double e0 = mb * qx - mp * lvx, e1 = mb * qy - mp * lvy, e2 = mb * qz - mp * lvz;
             const double de = dx * e0 + dy * e1 + dz * e2;
             const double aa = W * id3;
@@ -147,77 +198,68 @@ struct AdjOde {
             gm -= W * (qx * dx + qy * dy + qz * dz) * id3;
         }
         ax += A.G * px; ay += A.G * py; az += A.G * pz;
-        f[0] = -Z[3 * ld + m]; f[1] = -Z[4 * ld + m]; f[2] = -Z[5 * ld + m];
+        f[0] = -ldc(&Z[3 * ld + m]); f[1] = -ldc(&Z[4 * ld + m]); f[2] = -ldc(&Z[5 * ld + m]);
         f[3] = -ax; f[4] = -ay; f[5] = -az;
         f[6] = tx + A.G * gx; f[7] = ty + A.G * gy; f[8] = tz + A.G * gz;
-        f[9] = Z[6 * ld + m]; f[10] = Z[7 * ld + m]; f[11] = Z[8 * ld + m];
+        f[9] = ldc(&Z[6 * ld + m]); f[10] = ldc(&Z[7 * ld + m]); f[11] = ldc(&Z[8 * ld + m]);
         f[12] = A.G * gm;
     }
 };
 
-// Buffers, component-major over the M compact members ([..][D][M]):
-//   Y, F0, SC           attempt start, its derivative, error scale
-//   ZM[8], ZA[8], ZB[8] per column: previous midpoint state, two buffers of the current
-//   OUT[8], DIAG[8]     column results and the Neville diagonal T_kk
+// ---------------------------------------------------------------- phases
 template <class Ode>
-__global__ void __launch_bounds__(kMThreads)
-bsm_start_kernel(BsmArgs A, const double *Y, double *F0, double *SC, double *ZM, double *ZA) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= A.M) return;
+__device__ void phase_start(const BsmArgs &A, int m) {
     const int g = A.mgroup[m];
-    if (A.gstat[g] != 0) return;
+    if (ldc(&A.gstat[g]) != 0) return;
     constexpr int D = Ode::D;
     const size_t ld = (size_t)A.M, blk = (size_t)D * ld;
     const double H = step_of(A, g);
     double f[D];
-    Ode::deriv(A, Y, ld, m, g, f);
+    Ode::deriv(A, A.Y, m, f);
     for (int c = 0; c < D; c++) {
-        const double y = Y[c * ld + m];
-        F0[c * ld + m] = f[c];
-        SC[c * ld + m] = fabs(y) + fabs(H * f[c]) + 1e-300;
+        const double y = ldc(&A.Y[c * ld + m]);
+        A.F0[c * ld + m] = f[c];
+        A.SC[c * ld + m] = fabs(y) + fabs(H * f[c]) + 1e-300;
         for (int k = 0; k < 8; k++) {
             const double h = H / (2 * (k + 1));
-            ZM[k * blk + c * ld + m] = y;
-            ZA[k * blk + c * ld + m] = y + h * f[c];
+            A.ZM[k * blk + c * ld + m] = y;
+            A.ZA[k * blk + c * ld + m] = y + h * f[c];
         }
     }
 }
 
-// Sub-step `it` for all (column, member): reads Zcur, writes Znext or OUT.
 template <class Ode>
-__global__ void __launch_bounds__(kMThreads)
-bsm_substep_kernel(BsmArgs A, const double *Zcur, double *Znext, double *ZM, double *OUT, int it) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 8LL * A.M) return;
+__device__ void phase_substep(const BsmArgs &A, long long t, int it) {
     const int k = (int)(t / A.M), m = (int)(t % A.M);
     const int nk = 2 * (k + 1);
     if (it > nk) return;
     const int g = A.mgroup[m];
-    if (A.gstat[g] != 0) return;
+    if (ldc(&A.gstat[g]) != 0) return;
     constexpr int D = Ode::D;
     const size_t ld = (size_t)A.M, blk = (size_t)D * ld;
+    const double *Zcur = ((it & 1) ? A.ZA : A.ZB) + k * blk;
+    double *Znext = ((it & 1) ? A.ZB : A.ZA) + k * blk;
+    double *ZM = A.ZM + k * blk;
     const double h = step_of(A, g) / nk;
-    const double *Z = Zcur + k * blk;
     double f[D];
-    Ode::deriv(A, Z, ld, m, g, f);
+    Ode::deriv(A, Zcur, m, f);
     if (it < nk) {
         for (int c = 0; c < D; c++) {
-            const double tt = ZM[k * blk + c * ld + m] + 2.0 * h * f[c];
-            ZM[k * blk + c * ld + m] = Z[c * ld + m];
-            Znext[k * blk + c * ld + m] = tt;
+            const double zc = ldc(&Zcur[c * ld + m]);
+            const double tt = ldc(&ZM[c * ld + m]) + 2.0 * h * f[c];
+            ZM[c * ld + m] = zc;
+            Znext[c * ld + m] = tt;
         }
     } else {
         for (int c = 0; c < D; c++)
-            OUT[k * blk + c * ld + m] = 0.5 * (Z[c * ld + m] + ZM[k * blk + c * ld + m] + h * f[c]);
+            A.OUT[k * blk + c * ld + m] = 0.5 * (ldc(&Zcur[c * ld + m]) + ldc(&ZM[c * ld + m]) + h * f[c]);
     }
 }
 
-// Neville per (component, member); column errors of the first NERR
-// components folded into the group's error words.
+// Neville for item t; called by every lane of a warp (the reductions need all
+// lanes), items past the end contribute nothing.
 template <class Ode>
-__global__ void __launch_bounds__(kMThreads)
-bsm_neville_kernel(BsmArgs A, const double *OUT, const double *SC, double *DIAG) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ void phase_neville(const BsmArgs &A, long long t) {
     constexpr int D = Ode::D;
     const size_t ld = (size_t)A.M, blk = (size_t)D * ld;
     double e[8];
@@ -226,10 +268,11 @@ bsm_neville_kernel(BsmArgs A, const double *OUT, const double *SC, double *DIAG)
     if (t < (long long)D * A.M) {
         const int c = (int)(t / A.M), m = (int)(t % A.M);
         g = A.mgroup[m];
-        if (A.gstat[g] == 0) {
+        if (ldc(&A.gstat[g]) == 0) {
             double T[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            const double sc = ldc(&A.SC[c * ld + m]);
             for (int k = 0; k < 8; k++) {
-                double cur = OUT[k * blk + c * ld + m];
+                double cur = ldc(&A.OUT[k * blk + c * ld + m]);
                 double prev = T[0];
                 T[0] = cur;
                 for (int j = 1; j <= k; j++) {
@@ -239,14 +282,14 @@ bsm_neville_kernel(BsmArgs A, const double *OUT, const double *SC, double *DIAG)
                     T[j] = nxt;
                     cur = nxt;
                 }
-                DIAG[k * blk + c * ld + m] = T[k];
-                if (k >= 1 && c < Ode::NERR) e[k] = fabs(T[k] - T[k - 1]) / SC[c * ld + m];
+                A.DIAG[k * blk + c * ld + m] = T[k];
+                if (k >= 1 && c < Ode::NERR) e[k] = fabs(T[k] - T[k - 1]) / sc;
             }
         } else {
             g = -1;
         }
     }
-    // one atomic per warp when all its threads belong to one running group
+    // one atomic per warp when all its lanes belong to one running group
     const int g0 = __shfl_sync(0xffffffffu, g, 0);
     const bool uniform = __all_sync(0xffffffffu, g == g0);
     for (int k = 1; k < 8; k++) {
@@ -261,44 +304,78 @@ bsm_neville_kernel(BsmArgs A, const double *OUT, const double *SC, double *DIAG)
     }
 }
 
-// Step control, one thread per group (the in-block kernels' rule).
-__global__ void bsm_decide_kernel(BsmArgs A) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= A.ng) return;
+// Step control of group g (the in-block kernels' rule).  The group's
+// counters are touched only by this thread, so plain accesses suffice for
+// them; the words other blocks read go through L2.
+__device__ void phase_decide(const BsmArgs &A, int g) {
     A.gkconv[g] = -1;
-    if (A.gstat[g] != 0) return;
+    if (ldc(&A.gstat[g]) != 0) return;
     double H = step_of(A, g);
     int kconv = -1;
     for (int k = 1; k < 8 && kconv < 0; k++) {
-        const double e = __longlong_as_double((long long)A.gerr[(size_t)g * 8 + k]);
+        const double e = __longlong_as_double((long long)atomicAdd(&A.gerr[(size_t)g * 8 + k], 0ull));
         if (e <= A.tol) kconv = k;
     }
-    for (int k = 0; k < 8; k++) A.gerr[(size_t)g * 8 + k] = 0ull;
-    A.gatt[g] += 1;
+    for (int k = 0; k < 8; k++) atomicExch(&A.gerr[(size_t)g * 8 + k], 0ull);
+    const long long att = A.gatt[g] + 1;
+    A.gatt[g] = att;
+    double t = ldc(&A.gt[g]);
     if (kconv >= 0) {
-        A.gt[g] += H;
+        t += H;
         A.gacc[g] += 1;
         if (kconv < 4) H *= 1.5;
     } else {
         A.grej[g] += 1;
         H *= 0.5;
     }
+    A.gt[g] = t;
     A.gH[g] = H;
     A.gkconv[g] = kconv;
-    if (!(A.gt[g] < A.dt)) A.gstat[g] = 1;
-    else if (A.gatt[g] >= A.max_steps) A.gstat[g] = 2;
+    int st = 0;
+    if (!(t < A.dt)) st = 1;
+    else if (att >= A.max_steps) st = 2;
+    if (st) {
+        A.gstat[g] = st;
+        atomicSub(&A.bar->running, 1u);
+    }
 }
 
 template <class Ode>
-__global__ void __launch_bounds__(kMThreads)
-bsm_accept_kernel(BsmArgs A, const double *DIAG, double *Y) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ void phase_accept(const BsmArgs &A, long long t) {
     constexpr int D = Ode::D;
     const size_t blk = (size_t)D * A.M;
-    if (t >= (long long)D * A.M) return;
     const int m = (int)(t % A.M);
-    const int k = A.gkconv[A.mgroup[m]];
-    if (k >= 0) Y[t] = DIAG[k * blk + t];
+    const int k = ldc(&A.gkconv[A.mgroup[m]]);
+    if (k >= 0) A.Y[t] = ldc(&A.DIAG[k * blk + t]);
+}
+
+template <class Ode>
+__global__ void __launch_bounds__(kPThreads)
+bsm_persistent_kernel(BsmArgs A) {
+    constexpr int D = Ode::D;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long M = A.M;
+    __shared__ unsigned running;
+    for (int round = 0; round < A.max_steps; round++) {
+        // one read per block; the previous round ended with a barrier
+        if (threadIdx.x == 0) running = atomicAdd(&A.bar->running, 0u);
+        __syncthreads();
+        if (running == 0u) break;
+        for (long long t = tid; t < M; t += nth) phase_start<Ode>(A, (int)t);
+        if (!grid_barrier(A.bar)) return;
+        for (int it = 1; it <= 16; it++) {
+            for (long long t = tid; t < 8 * M; t += nth) phase_substep<Ode>(A, t, it);
+            if (!grid_barrier(A.bar)) return;
+        }
+        for (long long base = (long long)blockIdx.x * blockDim.x; base < D * M; base += nth)
+            phase_neville<Ode>(A, base + threadIdx.x);
+        if (!grid_barrier(A.bar)) return;
+        for (long long g = tid; g < A.ng; g += nth) phase_decide(A, (int)g);
+        if (!grid_barrier(A.bar)) return;
+        for (long long t = tid; t < D * M; t += nth) phase_accept<Ode>(A, t);
+        if (!grid_barrier(A.bar)) return;
+    }
 }
 
 // ---------------------------------------------------------------- set-up
@@ -306,8 +383,11 @@ struct RcPtrs {
     const double *p[kMaxLevels];
 };
 
+// Per member: group, body, partner range, compact partner indices, mass, 1/rc.
 __global__ void bsm_members_kernel(int ng, const int *gbase, const int *gslot0, const int *member,
-                                   int M, int *mbody, int *mgroup, RcPtrs rc, int nlev, double *irc) {
+                                   const int *slotof, const int *off, const int *list, const double *mass,
+                                   RcPtrs rc, int nlev, int M, int *mbody, int *mgroup, int *mq0, int *mq1,
+                                   int *pidx, double *mmass, double *irc) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     int lo = 0, hi = ng - 1;                     // last group with gbase <= m
@@ -318,11 +398,23 @@ __global__ void bsm_members_kernel(int ng, const int *gbase, const int *gslot0, 
     mgroup[m] = lo;
     const int b = member[gslot0[lo] + (m - gbase[lo])];
     mbody[m] = b;
+    mmass[m] = mass[b];
+    const int q0 = off[b], q1 = off[b + 1];
+    mq0[m] = q0;
+    mq1[m] = q1;
+    // partners belong to the same group (connected components of the pair graph)
+    for (int q = q0; q < q1; q++) pidx[q] = gbase[lo] + (slotof[list[q]] - gslot0[lo]);
     for (int l = 0; l < nlev; l++) irc[(size_t)l * M + m] = 1.0 / rc.p[l][b];
 }
 
 __global__ void bsm_init_groups_kernel(BsmArgs A) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0) {
+        A.bar->count = 0u;
+        A.bar->gen = 0u;
+        A.bar->err = 0u;
+        A.bar->running = (unsigned)A.ng;
+    }
     if (g >= A.ng) return;
     A.gt[g] = 0.0;
     A.gH[g] = A.dt;
@@ -400,15 +492,13 @@ __global__ void bsm_stats_kernel(BsmArgs A, DevCounters *ctr, int count_steps) {
     }
 }
 
-// Device and pinned host buffers of the batch, grown on demand, kept by the system.
+// Device buffers of the batch, grown on demand, kept by the system.
 struct BsmBuffers {
     void *raw = nullptr;
     size_t bytes = 0;
-    int *host_stat = nullptr;
-    size_t host_cap = 0;
 };
 
-void *bsm_reserve(genga_system *s, size_t bytes, int ng) {
+void *bsm_reserve(genga_system *s, size_t bytes) {
     BsmBuffers *b = static_cast<BsmBuffers *>(s->bsm);
     if (!b) {
         b = new BsmBuffers;
@@ -420,13 +510,6 @@ void *bsm_reserve(genga_system *s, size_t bytes, int ng) {
         b->bytes = 0;
         if (cudaMalloc(&b->raw, bytes) != cudaSuccess) return nullptr;
         b->bytes = bytes;
-    }
-    if (b->host_cap < (size_t)ng) {
-        if (b->host_stat) cudaFreeHost(b->host_stat);
-        b->host_stat = nullptr;
-        b->host_cap = 0;
-        if (cudaMallocHost(&b->host_stat, sizeof(int) * (size_t)ng) != cudaSuccess) return nullptr;
-        b->host_cap = (size_t)ng;
     }
     return b->raw;
 }
@@ -471,6 +554,7 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
             Gather gather, Scatter scatter) {
     constexpr int D = Ode::D;
     const int ng = (int)groups.size();
+    const int nlev = level + 1;
     std::vector<int> gbase(ng), gslot0(ng);
     int M = 0;
     for (int g = 0; g < ng; g++) {
@@ -479,21 +563,24 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
         M += groups[g].y;
     }
     const size_t blk = (size_t)D * M;
+    const size_t nq = 2 * (size_t)s->csr[level].cap;
     const size_t bytes = aligned(sizeof(double) * blk) * 3 + aligned(sizeof(double) * 8 * blk) * 5 +
-                         aligned(sizeof(double) * (size_t)(level + 1) * M) +
-                         aligned(sizeof(int) * M) * 2 + aligned(sizeof(int) * ng) * 4 +
-                         aligned(sizeof(double) * ng) * 2 + aligned(sizeof(long long) * ng) * 3 +
-                         aligned(sizeof(unsigned long long) * 8 * (size_t)ng);
-    char *p = static_cast<char *>(bsm_reserve(s, bytes, ng));
+                         aligned(sizeof(double) * (size_t)nlev * M) + aligned(sizeof(double) * M) +
+                         aligned(sizeof(int) * M) * 4 + aligned(sizeof(int) * nq) +
+                         aligned(sizeof(int) * ng) * 4 + aligned(sizeof(double) * ng) * 2 +
+                         aligned(sizeof(long long) * ng) * 3 + aligned(sizeof(unsigned long long) * 8 * ng) +
+                         aligned(sizeof(GridBarrier));
+    char *p = static_cast<char *>(bsm_reserve(s, bytes));
     if (!p) return GENGA_ENOMEM;
-    int *host_stat = static_cast<BsmBuffers *>(s->bsm)->host_stat;
-    double *Y = carve<double>(p, blk), *F0 = carve<double>(p, blk), *SC = carve<double>(p, blk);
-    double *ZM = carve<double>(p, 8 * blk), *ZA = carve<double>(p, 8 * blk), *ZB = carve<double>(p, 8 * blk);
-    double *OUT = carve<double>(p, 8 * blk), *DIAG = carve<double>(p, 8 * blk);
-    double *irc = carve<double>(p, (size_t)(level + 1) * M);
-    int *mbody = carve<int>(p, M), *mgroup = carve<int>(p, M);
-    int *d_gbase = carve<int>(p, ng), *d_gslot0 = carve<int>(p, ng);
     BsmArgs A;
+    A.M = M; A.ng = ng; A.nlev = nlev;
+    A.Y = carve<double>(p, blk); A.F0 = carve<double>(p, blk); A.SC = carve<double>(p, blk);
+    A.ZM = carve<double>(p, 8 * blk); A.ZA = carve<double>(p, 8 * blk); A.ZB = carve<double>(p, 8 * blk);
+    A.OUT = carve<double>(p, 8 * blk); A.DIAG = carve<double>(p, 8 * blk);
+    double *irc = carve<double>(p, (size_t)nlev * M), *mmass = carve<double>(p, M);
+    int *mbody = carve<int>(p, M), *mgroup = carve<int>(p, M), *mq0 = carve<int>(p, M), *mq1 = carve<int>(p, M);
+    int *pidx = carve<int>(p, nq);
+    int *d_gbase = carve<int>(p, ng), *d_gslot0 = carve<int>(p, ng);
     A.gstat = carve<int>(p, ng);
     A.gkconv = carve<int>(p, ng);
     A.gt = carve<double>(p, ng);
@@ -502,12 +589,8 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     A.gacc = carve<long long>(p, ng);
     A.grej = carve<long long>(p, ng);
     A.gerr = carve<unsigned long long>(p, 8 * (size_t)ng);
-    A.n = (int)s->n; A.M = M; A.ng = ng;
-    A.mbody = mbody; A.mgroup = mgroup; A.irc = irc; A.gbase = d_gbase; A.gslot0 = d_gslot0;
-    A.slotof = s->slotof;
-    A.off = s->csr[level].off; A.list = s->csr[level].list;
-    A.mass = s->mass;
-    A.nlev = level + 1;
+    A.bar = carve<GridBarrier>(p, 1);
+    A.mgroup = mgroup; A.mq0 = mq0; A.mq1 = mq1; A.pidx = pidx; A.mmass = mmass; A.irc = irc;
     A.G = s->p.G; A.mu = s->p.G * s->p.m_star; A.dt = dt; A.tol = s->p.bs_tol;
     A.max_steps = s->p.bs_max_steps;
 
@@ -515,53 +598,46 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     if (cudaMemcpyAsync(d_gbase, gbase.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(d_gslot0, gslot0.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return GENGA_ECUDA;
-    const unsigned gm = (unsigned)((M + kMThreads - 1) / kMThreads);
-    const unsigned g8 = (unsigned)((8LL * M + kMThreads - 1) / kMThreads);
-    const unsigned gD = (unsigned)(((long long)D * M + kMThreads - 1) / kMThreads);
-    const unsigned gg = (unsigned)((ng + 127) / 128);
     RcPtrs rcp;
     for (int l = 0; l < kMaxLevels; l++) rcp.p[l] = s->rcl[l].rc;
-    bsm_members_kernel<<<gm, kMThreads, 0, st>>>(ng, d_gbase, d_gslot0, s->member, M, mbody, mgroup, rcp,
-                                                 level + 1, irc);
-    bsm_init_groups_kernel<<<gg, 128, 0, st>>>(A);
-    gather(st, A, Y);
+    const unsigned gm = (unsigned)((M + 127) / 128);
+    bsm_members_kernel<<<gm, 128, 0, st>>>(ng, d_gbase, d_gslot0, s->member, s->slotof, s->csr[level].off,
+                                          s->csr[level].list, s->mass, rcp, nlev, M, mbody, mgroup, mq0, mq1,
+                                          pidx, mmass, irc);
+    bsm_init_groups_kernel<<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(A);
+    gather(st, mbody, A.Y);
     s->launches += 3;
     if (cudaGetLastError() != cudaSuccess) return GENGA_ECUDA;
 
-    // rounds in batches (4, 8, ..., 64) between reads of the status words;
-    // the host copies go through pinned memory and the synchronisation
-    long long rounds = 0;
-    int batch = 4;
-    bool running = true;
-    while (running) {
-        for (int r = 0; r < batch; r++) {
-            bsm_start_kernel<Ode><<<gm, kMThreads, 0, st>>>(A, Y, F0, SC, ZM, ZA);
-            double *cur = ZA, *nxt = ZB;
-            for (int it = 1; it <= 16; it++) {
-                bsm_substep_kernel<Ode><<<g8, kMThreads, 0, st>>>(A, cur, nxt, ZM, OUT, it);
-                std::swap(cur, nxt);
-            }
-            bsm_neville_kernel<Ode><<<gD, kMThreads, 0, st>>>(A, OUT, SC, DIAG);
-            bsm_decide_kernel<<<gg, 128, 0, st>>>(A);
-            bsm_accept_kernel<Ode><<<gD, kMThreads, 0, st>>>(A, DIAG, Y);
-            s->launches += 20;
-        }
-        rounds += batch;
-        if (cudaGetLastError() != cudaSuccess) return GENGA_ECUDA;
-        if (cudaMemcpyAsync(host_stat, A.gstat, sizeof(int) * ng, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            return GENGA_ECUDA;
-        running = false;
-        for (int g = 0; g < ng; g++) running = running || host_stat[g] == 0;
-        // each round is one attempt of every running group, and a group stops
-        // after bs_max_steps attempts: more rounds than that cannot happen
-        if (running && rounds > (long long)A.max_steps) return GENGA_ENONCONV;
-        batch = std::min(batch * 2, 64);
-    }
-    scatter(st, A, Y);
+    // one persistent cooperative launch: at most 2 blocks per SM, and no more
+    // blocks than the (column, member) items need
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bsm_persistent_kernel<Ode>, kPThreads, 0) !=
+            cudaSuccess || per_sm < 1)
+        return GENGA_ECUDA;
+    const long long want = (8LL * M + kPThreads - 1) / kPThreads;
+    const long long cap = (long long)std::min(per_sm, 2) * s->num_sms;
+    const unsigned grid = (unsigned)std::max(1LL, std::min(want, cap));
+    void *args[] = {&A};
+    if (cudaLaunchCooperativeKernel((const void *)bsm_persistent_kernel<Ode>, dim3(grid), dim3(kPThreads), args,
+                                    0, st) != cudaSuccess)
+        return GENGA_ECUDA;
+    ++s->launches;
+    GridBarrier hb;
+    if (cudaMemcpyAsync(&hb, A.bar, sizeof(hb), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return GENGA_ECUDA;
+    if (hb.err) return GENGA_ETIMEOUT;
+    scatter(st, mbody, A.Y);
     bsm_stats_kernel<<<1, 1, 0, st>>>(A, s->ctr, count_steps ? 1 : 0);
     s->launches += 2;
     return cudaGetLastError() == cudaSuccess ? GENGA_OK : GENGA_ECUDA;
+}
+
+int members_of(const std::vector<int2> &groups) {
+    int t = 0;
+    for (const int2 &g : groups) t += g.y;
+    return t;
 }
 
 }  // namespace
@@ -570,7 +646,6 @@ void bsm_release(genga_system *s) {
     BsmBuffers *b = static_cast<BsmBuffers *>(s->bsm);
     if (!b) return;
     if (b->raw) cudaFree(b->raw);
-    if (b->host_stat) cudaFreeHost(b->host_stat);
     delete b;
     s->bsm = nullptr;
 }
@@ -584,30 +659,27 @@ int bsm_forward_groups(genga_system *s, int level, double dt_l) {
     const double *pre_pos = s->pre_pos[level], *pre_vel = s->pre_vel[level];
     double *pos = s->pos, *vel = s->vel;
     const int n = (int)s->n;
+    const int M = members_of(groups);
+    const unsigned gr = (unsigned)((M + 127) / 128);
     return bsm_run<FwdOde>(
         s, level, dt_l, groups, true,
-        [&](cudaStream_t st, const BsmArgs &A, double *Y) {
-            bsm_gather_fwd<<<(A.M + 127) / 128, 128, 0, st>>>(n, A.M, A.mbody, pre_pos, pre_vel, Y);
+        [&](cudaStream_t st, const int *mbody, double *Y) {
+            bsm_gather_fwd<<<gr, 128, 0, st>>>(n, M, mbody, pre_pos, pre_vel, Y);
         },
-        [&](cudaStream_t st, const BsmArgs &A, const double *Y) {
-            bsm_scatter_fwd<<<(A.M + 127) / 128, 128, 0, st>>>(n, A.M, A.mbody, Y, pos, vel);
+        [&](cudaStream_t st, const int *mbody, const double *Y) {
+            bsm_scatter_fwd<<<gr, 128, 0, st>>>(n, M, mbody, Y, pos, vel);
         });
 }
 
 // Bulirsch-Stoer of every group of the current grouping at `level`: the
-// in-block kernels for groups of up to kBlockGroupMax members and the
-// batched grid-wide driver for the larger ones, concurrently.
+// in-block kernels for groups of up to kBlockGroupMax members on the side
+// streams, then (joined, so that the cooperative launch has the GPU to
+// itself) the persistent driver for the larger ones.
 int run_bs(genga_system *s, int level, double dt_l, int64_t np) {
     if (np <= 0) return GENGA_OK;
-    if (launch_bs(s, level, dt_l, std::min<int64_t>(np, s->n / 2 + 1)) != cudaSuccess) {
-        join_bs(s);
-        return GENGA_ECUDA;
-    }
-    // the batched groups run on the system stream while the side streams
-    // integrate the small groups (disjoint members)
-    const int rc = bsm_forward_groups(s, level, dt_l);
-    if (join_bs(s) != cudaSuccess) return GENGA_ECUDA;
-    return rc;
+    const cudaError_t e = launch_bs(s, level, dt_l, std::min<int64_t>(np, s->n / 2 + 1));
+    if (join_bs(s) != cudaSuccess || e != cudaSuccess) return GENGA_ECUDA;
+    return bsm_forward_groups(s, level, dt_l);
 }
 
 // Adjoint BS (backward, augmented) of every group larger than kBlockGroupMax.
@@ -617,13 +689,15 @@ int bsm_adjoint_groups(genga_system *s, const double *x2, const double *v2, doub
     if (batched_groups(s, groups) != 0) return GENGA_ECUDA;
     if (groups.empty()) return GENGA_OK;
     const int n = (int)s->n;
+    const int M = members_of(groups);
+    const unsigned gr = (unsigned)((M + 127) / 128);
     return bsm_run<AdjOde>(
         s, 0, dt, groups, false,
-        [&](cudaStream_t st, const BsmArgs &A, double *Y) {
-            bsm_gather_adj<<<(A.M + 127) / 128, 128, 0, st>>>(n, A.M, A.mbody, x2, v2, lx, lv, Y);
+        [&](cudaStream_t st, const int *mbody, double *Y) {
+            bsm_gather_adj<<<gr, 128, 0, st>>>(n, M, mbody, x2, v2, lx, lv, Y);
         },
-        [&](cudaStream_t st, const BsmArgs &A, const double *Y) {
-            bsm_scatter_adj<<<(A.M + 127) / 128, 128, 0, st>>>(n, A.M, A.mbody, Y, lx, lv, lm);
+        [&](cudaStream_t st, const int *mbody, const double *Y) {
+            bsm_scatter_adj<<<gr, 128, 0, st>>>(n, M, mbody, Y, lx, lv, lm);
         });
 }
 

@@ -207,7 +207,7 @@ void adjoint_free(genga_system *s);
 // (bsm.cu); genga error codes.
 int bsm_forward_groups(genga_system *s, int level, double dt_l);
 void bsm_release(genga_system *s);
-// launch_bs, bsm_forward_groups on the system stream meanwhile, join_bs.
+// launch_bs and join_bs, then bsm_forward_groups.
 int run_bs(genga_system *s, int level, double dt_l, int64_t np);
 int bsm_adjoint_groups(genga_system *s, const double *x2, const double *v2, double *lx, double *lv,
                        double *lm, double dt);

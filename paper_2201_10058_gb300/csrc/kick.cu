@@ -15,10 +15,13 @@
 //     pre-check (operation order identical to the definition, no contraction)
 //     and the changeover function; candidates are appended with one atomic per
 //     warp (ballot + popc);
-//   * MIXED: FP32 rsqrt seed built from the bits of r^2, one FP64 Newton
-//     residual applied to r^-3 in extended (float-float) arithmetic; FP64
-//     displacement and accumulation; per-tile sums folded with TwoSum:
-//     12 FP64 instructions per pair.  FP64: CUDA's double rsqrt.
+//   * MIXED: FP64 displacement; r^2 formed as an unevaluated sum of two floats
+//     from an exact integer split of the displacement (no FP64 work); FP32
+//     rsqrt seed y0; one FP64 Newton residual e = 1 - r^2 y0^2 (its leading
+//     part exact in two FP64 operations, the float tail added in FP32);
+//     r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) in float-float; FP64 accumulation,
+//     per-tile sums folded with TwoSum: 9 FP64 instructions per pair.
+//     FP64: CUDA's double rsqrt, 18 FP64 instructions per pair.
 #include "common.cuh"
 
 namespace genga {
@@ -74,6 +77,21 @@ __device__ __forceinline__ float f32_of_f64_any(double v) {
     return __uint_as_float(fb);
 }
 
+// v = hi + lo exactly up to 2^-47 |v|: hi is v with the mantissa truncated
+// to float precision, lo the 29 discarded mantissa bits rounded to a float.
+// Integer operations, one integer-to-float conversion and one FP32 scale;
+// |v| < 2^-74 gives lo = 0, |v| < 2^-126 also hi = 0 (signed zeros).
+__device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    const unsigned mag = hw & 0x7fffffffu, sgn = hw & 0x80000000u;
+    const bool normal = mag >= 0x38100000u;
+    hi = __uint_as_float(normal ? (sgn | ((mag - 0x38000000u) << 3) | (lw >> 29)) : sgn);
+    const unsigned E = mag >> 20;                       // biased double exponent
+    float l = 0.0f;
+    if (E >= 949u) l = __uint2float_rn(lw & 0x1fffffffu) * __uint_as_float((E - 948u) << 23);
+    lo = __uint_as_float(__float_as_uint(l) | sgn);
+}
+
 template <bool MIXED, bool PRECHECK, bool FORCE>
 __global__ void __launch_bounds__(kKickThreads)
 kick_kernel(KickArgs A)
@@ -126,8 +144,33 @@ kick_kernel(KickArgs A)
             const double dx = sx[k] - xi;
             const double dy = sy[k] - yi;
             const double dz = sz[k] - zi;
-            double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-            float r2f = r2_to_float_trunc(r2);
+            // r^2: FP64 (FP64 form) or Rh + Rl, two floats (MIXED: float-float
+            // square sum of the split displacement, relative error ~2^-46).
+            // r2f, used only against thresholds with 2^-16 margins, is a
+            // float within 2^-23 of r^2.
+            double r2 = 0.0;
+            float Rh = 0.0f, Rl = 0.0f, hx = 0.0f, hy = 0.0f, hz = 0.0f;
+            float r2f;
+            if (MIXED) {
+                float lx, ly, lz;
+                split_f64(dx, hx, lx);
+                split_f64(dy, hy, ly);
+                split_f64(dz, hz, lz);
+                const float px = hx * hx, py = hy * hy, pz = hz * hz;
+                const float pxe = fmaf(hx, hx, -px), pye = fmaf(hy, hy, -py), pze = fmaf(hz, hz, -pz);
+                const float s1 = px + py, b1 = s1 - px;
+                const float e1 = (px - (s1 - b1)) + (py - b1);
+                const float s2 = s1 + pz, b2 = s2 - s1;
+                const float e2 = (s1 - (s2 - b2)) + (pz - b2);
+                const float cross = 2.0f * fmaf(hx, lx, fmaf(hy, ly, hz * lz));
+                const float tail = ((e1 + e2) + (pxe + pye + pze)) + cross;
+                Rh = s2 + tail;
+                Rl = tail - (Rh - s2);
+                r2f = Rh;
+            } else {
+                r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                r2f = r2_to_float_trunc(r2);
+            }
             double mk = sm[k];
             float mh = 0.0f, ml = 0.0f;
             if (MIXED) { mh = smh[k]; ml = sml[k]; }
@@ -156,9 +199,11 @@ kick_kernel(KickArgs A)
             if (r2f < fmaxf(thri, sthr[k])) {
                 if (j == i) {
                     mk = 0.0; r2 = 1.0; r2f = 1.0f;          // self term: zero, finite
+                    Rh = 1.0f; Rl = 0.0f;
                     mh = 0.0f; ml = 0.0f;
                 } else if (FORCE) {
-                    mk = mk * changeover(sqrt(r2), fmax(rci, src[k]));
+                    const double r2d = MIXED ? fma(dz, dz, fma(dy, dy, dx * dx)) : r2;
+                    mk = mk * changeover(sqrt(r2d), fmax(rci, src[k]));
                     if (MIXED) {
                         mh = __double2float_rn(mk);
                         ml = __double2float_rn(mk - (double)mh);
@@ -168,14 +213,16 @@ kick_kernel(KickArgs A)
             if (FORCE) {
                 double s;
                 if (MIXED) {
-                    // FP32 seed y0 ~ r^-1; FP64 Newton residual e = 1 - r^2 y0^2 (2 FP64
-                    // ops); r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 1.5 e + 1.875 e^2 + O(e^3)),
-                    // |e| < 2^-20.  m y0^3 is formed exactly enough (~2^-46) as a sum of two
-                    // floats, the correction in FP32, and the two parts meet in one FP64 add.
-                    const float y0f = rsqrtf(r2f);
+                    // FP32 seed y0 ~ r^-1; Newton residual e = 1 - r^2 y0^2 with
+                    // r^2 = Rh + Rl: 1 - Rh y0^2 in FP64 (Rh y0 exact in one DMUL, the
+                    // DFMA rounds once), the tail Rl y0^2 (~2^-24) in FP32.
+                    // r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 1.5 e + 1.875 e^2 + O(e^3)),
+                    // |e| < 2^-20.  m y0^3 is formed exactly enough (~2^-46) as a sum of
+                    // two floats, the correction in FP32, and the parts meet in one FP64 add.
+                    const float y0f = rsqrtf(Rh);
                     const double y0 = float_to_double_exact(__float_as_uint(y0f));
-                    const double t = r2 * y0;
-                    const double e = fma(-t, y0, 1.0);
+                    const double t = float_to_double_exact(__float_as_uint(Rh)) * y0;
+                    const double e1 = fma(-t, y0, 1.0);
                     const float p = y0f * y0f, pe = fmaf(y0f, y0f, -p);
                     const float q = p * y0f;
                     float qe = fmaf(p, y0f, -q);
@@ -184,7 +231,7 @@ kick_kernel(KickArgs A)
                     float ce = fmaf(q, mh, -ch);
                     ce = fmaf(q, ml, ce);
                     ce = fmaf(qe, mh, ce);
-                    const float ef = f32_of_f64_any(e);
+                    const float ef = fmaf(-Rl, p, f32_of_f64_any(e1));
                     const float corr = fmaf(ch, fmaf(1.875f * ef, ef, 1.5f * ef), ce);
                     s = f64_of_f32_any(ch) + f64_of_f32_any(corr);
                 } else {
