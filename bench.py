@@ -36,13 +36,17 @@ METRIC = ("changeover-kick G pair-interactions/s and steps/s at N=65536 (FP64 vs
           "% of peak")
 UNIT = "Gpair/s"
 # FP64 instructions per pair interaction that each kick form's algorithm needs
-# (FMA counted as one).  Mixed: displacement 3, Newton residual
-# 1 - Rh y0^2 of the FP32 seed 2 (r^2 = Rh + Rl is formed in float-float on the
-# FP32 pipe), joining the float-float m r^-3 1, accumulation 3.  FP64:
+# (FMA counted as one).  Mixed: displacement 3, Newton residual of the FP32
+# seed 1 (one FMA on an exact float product; r^2 = Rh + Rl and the residual's
+# tails are float-float on the FP32 pipe), joining the float-float m r^-3 1,
+# accumulation 3.  FP64:
 # displacement 3, r^2 3, r^-1 to FP64 precision (two Newton steps from a
 # ~2^-22 seed) 6, m r^-3 3, accumulation 3.
-FP64_OPS_PER_PAIR = {"mixed": 9, "fp64": 18}
+FP64_OPS_PER_PAIR = {"mixed": 8, "fp64": 18}
 FP64_OPS_PER_CLK_PER_SM = 2      # measured DFMA throughput per SM per clock on GB300
+# dram__bytes_read.sum + dram__bytes_write.sum of one mixed kick launch at
+# N = 65,540 (one ncu capture); valid for the kernel as captured
+KICK_MIXED_DRAM_BYTES = 2.935296e6 + 1.688320e6
 
 
 def parse():
@@ -301,7 +305,10 @@ def run_ours(args, dist: Dist) -> dict | None:
         "roofline": {"bound": "alu", "kernel": "kick_kernel<mixed> (all-pairs changeover kick)",
                      "achieved": round(achieved, 2), "peak": round(peak, 2),
                      "unit": "G FP64-op/s (FMA = 1; FP64 pipe)",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": KICK_MIXED_DRAM_BYTES,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
+                                       "of this kernel at N=65540",
                      "ops_per_pair": FP64_OPS_PER_PAIR["mixed"],
                      "peak_basis": f"derived: {FP64_OPS_PER_CLK_PER_SM} FP64 op/clk/SM (measured) x "
                                    f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz"},

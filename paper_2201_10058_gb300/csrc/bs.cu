@@ -120,9 +120,15 @@ __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
 // Neville table is built per (member, component) afterwards and the first
 // column k >= 1 under tolerance is accepted -- the same arithmetic and the same
 // acceptance rule as the serial scheme.  FP64 throughout.
+// Pairs of a group of M member slots evaluated once each (M <= 16): the
+// upper triangle, a < q, at index a M - a (a + 1) / 2 + q - a - 1.
+template <int M>
+constexpr int kColsPairs = (M <= 16) ? M * (M - 1) / 2 : 1;
+
 template <int M>
 struct ColsShared {
     double zx[8 * M], zy[8 * M], zz[8 * M];      // current positions, per (column, member)
+    double pt[3][8][kColsPairs<M>];              // W r^-3 (x_q - x_a) per column and pair a < q
     double m[M];
     double irc[kMaxLevels][M];
     double y[6][M], f0[6][M];                    // attempt start and its derivative
@@ -141,6 +147,52 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
     S.zx[tid] = z[0]; S.zy[tid] = z[1]; S.zz[tid] = z[2];
     __syncthreads();
     f[0] = z[3]; f[1] = z[4]; f[2] = z[5];
+    if constexpr (M <= 16) {
+        // each pair once, by its lower-ranked member; then every member sums
+        // its partners' terms in ascending rank order (m_q t for q > a,
+        // -m_q t for q < a): exactly antisymmetric pair forces
+        const int a = tid % M;
+        if (active) {
+            unsigned mm = mask & ~((2u << a) - 1u);
+            while (mm) {
+                const int q = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const int lq = col * M + q;
+                const double dx = S.zx[lq] - z[0], dy = S.zy[lq] - z[1], dz = S.zz[lq] - z[2];
+                const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                const double yv = rsqrt_newton(d2);
+                const double d = d2 * yv;
+                double W = 1.0;
+                for (int l = 0; l < A.nlev; l++) W *= 1.0 - changeover_fast(d, fmin(irc_self[l], S.irc[l][q]));
+                const double c = W * (yv * yv * yv);
+                const int pi = a * M - a * (a + 1) / 2 + q - a - 1;
+                S.pt[0][col][pi] = c * dx;
+                S.pt[1][col][pi] = c * dy;
+                S.pt[2][col][pi] = c * dz;
+            }
+        }
+        __syncthreads();
+        if (!active) { f[3] = f[4] = f[5] = 0.0; return; }
+        const double r2s = fma(z[2], z[2], fma(z[1], z[1], z[0] * z[0]));
+        const double ys = rsqrt_newton(r2s);
+        const double sst = -A.mu * (ys * ys * ys);
+        double px = 0.0, py = 0.0, pz = 0.0;
+        unsigned mm = mask;
+        while (mm) {
+            const int q = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const int lo = q < a ? q : a, hi = q < a ? a : q;
+            const int pi = lo * M - lo * (lo + 1) / 2 + hi - lo - 1;
+            const double w = q > a ? S.m[q] : -S.m[q];
+            px = fma(w, S.pt[0][col][pi], px);
+            py = fma(w, S.pt[1][col][pi], py);
+            pz = fma(w, S.pt[2][col][pi], pz);
+        }
+        f[3] = fma(sst, z[0], A.G * px);
+        f[4] = fma(sst, z[1], A.G * py);
+        f[5] = fma(sst, z[2], A.G * pz);
+        return;
+    }
     if (!active) { f[3] = f[4] = f[5] = 0.0; return; }
     const double r2s = fma(z[2], z[2], fma(z[1], z[1], z[0] * z[0]));
     const double ys = rsqrt_newton(r2s);

@@ -122,20 +122,33 @@ __device__ bool grid_barrier(GridBarrier *b) {
     return ok != 0;
 }
 
+// Lanes per item in the derivative phases: the partner loop of one (column,
+// member) item is split over kLanes adjacent lanes (partner q to lane
+// q mod kLanes) and the partial sums are combined by an xor butterfly, which
+// gives every lane the same bits (IEEE addition commutes).
+constexpr int kLanes = 4;
+
+__device__ __forceinline__ unsigned lane_mask() {
+    return 0xfu << ((threadIdx.x & 31u) & ~3u);
+}
+__device__ __forceinline__ double lane_sum(double v) {
+    const unsigned mk = lane_mask();
+    v += __shfl_xor_sync(mk, v, 1);
+    v += __shfl_xor_sync(mk, v, 2);
+    return v;
+}
+
 // Forward group ODE: y = (x, v); a = -mu x/r^3 + G sum_p m_p W (x_p - x)/r^3,
-// W = prod_{levels} (1 - K); partners in ascending order (fixed sum order).
+// W = prod_{levels} (1 - K).  Every lane of the item returns f.
 struct FwdOde {
     static constexpr int D = 6;
     static constexpr int NERR = 6;
-    __device__ static void deriv(const BsmArgs &A, const double *Z, int m, double *f) {
+    __device__ static void deriv(const BsmArgs &A, const double *Z, int m, int lane, double *f) {
         const size_t ld = (size_t)A.M;
         const double x = ldc(&Z[0 * ld + m]), y = ldc(&Z[1 * ld + m]), z = ldc(&Z[2 * ld + m]);
-        const double r2 = fma(z, z, fma(y, y, x * x));
-        const double ys = rsqrt_newton(r2);
-        const double sst = -A.mu * (ys * ys * ys);
         double px = 0.0, py = 0.0, pz = 0.0;
         const int q1 = A.mq1[m];
-        for (int q = A.mq0[m]; q < q1; q++) {
+        for (int q = A.mq0[m] + lane; q < q1; q += kLanes) {
             const int sp = A.pidx[q];
             const double dx = ldc(&Z[0 * ld + sp]) - x, dy = ldc(&Z[1 * ld + sp]) - y,
                          dz = ldc(&Z[2 * ld + sp]) - z;
@@ -148,6 +161,10 @@ struct FwdOde {
             const double c = A.mmass[sp] * W * (yv * yv * yv);
             px = fma(c, dx, px); py = fma(c, dy, py); pz = fma(c, dz, pz);
         }
+        px = lane_sum(px); py = lane_sum(py); pz = lane_sum(pz);
+        const double r2 = fma(z, z, fma(y, y, x * x));
+        const double ys = rsqrt_newton(r2);
+        const double sst = -A.mu * (ys * ys * ys);
         f[0] = ldc(&Z[3 * ld + m]); f[1] = ldc(&Z[4 * ld + m]); f[2] = ldc(&Z[5 * ld + m]);
         f[3] = fma(sst, x, A.G * px); f[4] = fma(sst, y, A.G * py); f[5] = fma(sst, z, A.G * pz);
     }
@@ -160,22 +177,14 @@ struct FwdOde {
 struct AdjOde {
     static constexpr int D = 13;
     static constexpr int NERR = 6;
-    __device__ static void deriv(const BsmArgs &A, const double *Z, int m, double *f) {
+    __device__ static void deriv(const BsmArgs &A, const double *Z, int m, int lane, double *f) {
         const size_t ld = (size_t)A.M;
         const double x = ldc(&Z[0 * ld + m]), y = ldc(&Z[1 * ld + m]), z = ldc(&Z[2 * ld + m]);
         const double lvx = ldc(&Z[9 * ld + m]), lvy = ldc(&Z[10 * ld + m]), lvz = ldc(&Z[11 * ld + m]);
         const double mb = A.mmass[m];
-        const double r2 = fma(z, z, fma(y, y, x * x));
-        const double ys = rsqrt_newton(r2);
-        const double ir2 = ys * ys, ir3 = ir2 * ys;
-        double ax = -A.mu * x * ir3, ay = -A.mu * y * ir3, az = -A.mu * z * ir3;
-        const double xl = x * lvx + y * lvy + z * lvz;
-        const double tx = -A.mu * ir3 * (lvx - 3.0 * x * xl * ir2);
-        const double ty = -A.mu * ir3 * (lvy - 3.0 * y * xl * ir2);
-        const double tz = -A.mu * ir3 * (lvz - 3.0 * z * xl * ir2);
         double px = 0.0, py = 0.0, pz = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, gm = 0.0;
         const int q1 = A.mq1[m];
-        for (int q = A.mq0[m]; q < q1; q++) {
+        for (int q = A.mq0[m] + lane; q < q1; q += kLanes) {
             const int sp = A.pidx[q];
             const double dx = ldc(&Z[0 * ld + sp]) - x, dy = ldc(&Z[1 * ld + sp]) - y,
                          dz = ldc(&Z[2 * ld + sp]) - z;
@@ -197,7 +206,17 @@ struct AdjOde {
             gx += aa * e0 + bb * dx; gy += aa * e1 + bb * dy; gz += aa * e2 + bb * dz;
             gm -= W * (qx * dx + qy * dy + qz * dz) * id3;
         }
-        ax += A.G * px; ay += A.G * py; az += A.G * pz;
+        px = lane_sum(px); py = lane_sum(py); pz = lane_sum(pz);
+        gx = lane_sum(gx); gy = lane_sum(gy); gz = lane_sum(gz); gm = lane_sum(gm);
+        const double r2 = fma(z, z, fma(y, y, x * x));
+        const double ys = rsqrt_newton(r2);
+        const double ir2 = ys * ys, ir3 = ir2 * ys;
+        const double xl = x * lvx + y * lvy + z * lvz;
+        const double tx = -A.mu * ir3 * (lvx - 3.0 * x * xl * ir2);
+        const double ty = -A.mu * ir3 * (lvy - 3.0 * y * xl * ir2);
+        const double tz = -A.mu * ir3 * (lvz - 3.0 * z * xl * ir2);
+        const double ax = -A.mu * x * ir3 + A.G * px, ay = -A.mu * y * ir3 + A.G * py,
+                     az = -A.mu * z * ir3 + A.G * pz;
         f[0] = -ldc(&Z[3 * ld + m]); f[1] = -ldc(&Z[4 * ld + m]); f[2] = -ldc(&Z[5 * ld + m]);
         f[3] = -ax; f[4] = -ay; f[5] = -az;
         f[6] = tx + A.G * gx; f[7] = ty + A.G * gy; f[8] = tz + A.G * gz;
@@ -207,15 +226,17 @@ struct AdjOde {
 };
 
 // ---------------------------------------------------------------- phases
+// start and sub-step: item = kLanes adjacent lanes; lane 0 writes.
 template <class Ode>
-__device__ void phase_start(const BsmArgs &A, int m) {
+__device__ void phase_start(const BsmArgs &A, int m, int lane) {
     const int g = A.mgroup[m];
     if (ldc(&A.gstat[g]) != 0) return;
     constexpr int D = Ode::D;
     const size_t ld = (size_t)A.M, blk = (size_t)D * ld;
     const double H = step_of(A, g);
     double f[D];
-    Ode::deriv(A, A.Y, m, f);
+    Ode::deriv(A, A.Y, m, lane, f);
+    if (lane != 0) return;
     for (int c = 0; c < D; c++) {
         const double y = ldc(&A.Y[c * ld + m]);
         A.F0[c * ld + m] = f[c];
@@ -229,7 +250,7 @@ __device__ void phase_start(const BsmArgs &A, int m) {
 }
 
 template <class Ode>
-__device__ void phase_substep(const BsmArgs &A, long long t, int it) {
+__device__ void phase_substep(const BsmArgs &A, long long t, int it, int lane) {
     const int k = (int)(t / A.M), m = (int)(t % A.M);
     const int nk = 2 * (k + 1);
     if (it > nk) return;
@@ -242,7 +263,8 @@ __device__ void phase_substep(const BsmArgs &A, long long t, int it) {
     double *ZM = A.ZM + k * blk;
     const double h = step_of(A, g) / nk;
     double f[D];
-    Ode::deriv(A, Zcur, m, f);
+    Ode::deriv(A, Zcur, m, lane, f);
+    if (lane != 0) return;
     if (it < nk) {
         for (int c = 0; c < D; c++) {
             const double zc = ldc(&Zcur[c * ld + m]);
@@ -356,16 +378,19 @@ bsm_persistent_kernel(BsmArgs A) {
     const long long nth = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long M = A.M;
+    // derivative phases: kLanes adjacent lanes per item (blockDim is a multiple of 32)
+    const long long item0 = tid / kLanes, nitem = nth / kLanes;
+    const int lane = (int)(threadIdx.x % kLanes);
     __shared__ unsigned running;
     for (int round = 0; round < A.max_steps; round++) {
         // one read per block; the previous round ended with a barrier
         if (threadIdx.x == 0) running = atomicAdd(&A.bar->running, 0u);
         __syncthreads();
         if (running == 0u) break;
-        for (long long t = tid; t < M; t += nth) phase_start<Ode>(A, (int)t);
+        for (long long t = item0; t < M; t += nitem) phase_start<Ode>(A, (int)t, lane);
         if (!grid_barrier(A.bar)) return;
         for (int it = 1; it <= 16; it++) {
-            for (long long t = tid; t < 8 * M; t += nth) phase_substep<Ode>(A, t, it);
+            for (long long t = item0; t < 8 * M; t += nitem) phase_substep<Ode>(A, t, it, lane);
             if (!grid_barrier(A.bar)) return;
         }
         for (long long base = (long long)blockIdx.x * blockDim.x; base < D * M; base += nth)
@@ -615,7 +640,7 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bsm_persistent_kernel<Ode>, kPThreads, 0) !=
             cudaSuccess || per_sm < 1)
         return GENGA_ECUDA;
-    const long long want = (8LL * M + kPThreads - 1) / kPThreads;
+    const long long want = (8LL * M * kLanes + kPThreads - 1) / kPThreads;
     const long long cap = (long long)std::min(per_sm, 2) * s->num_sms;
     const unsigned grid = (unsigned)std::max(1LL, std::min(want, cap));
     void *args[] = {&A};

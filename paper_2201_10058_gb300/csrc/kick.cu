@@ -18,9 +18,10 @@
 //   * MIXED: FP64 displacement; r^2 formed as an unevaluated sum of two floats
 //     from an exact integer split of the displacement (no FP64 work); FP32
 //     rsqrt seed y0; one FP64 Newton residual e = 1 - r^2 y0^2 (its leading
-//     part exact in two FP64 operations, the float tail added in FP32);
-//     r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) in float-float; FP64 accumulation,
-//     per-tile sums folded with TwoSum: 9 FP64 instructions per pair.
+//     part in one FP64 FMA on an exact float product, the float tails added
+//     in FP32); r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) in float-float; FP64
+//     accumulation, per-tile sums folded with TwoSum: 8 FP64 instructions
+//     per pair.
 //     FP64: CUDA's double rsqrt, 18 FP64 instructions per pair.
 #include "common.cuh"
 
@@ -67,13 +68,16 @@ __device__ __forceinline__ double f64_of_f32_any(float f) {
     const unsigned lo = (mag >= 0x00800000u) ? (mag << 29) : 0u;
     return __hiloint2double((int)hi, (int)lo);
 }
-// Float with the value of a double of magnitude below 2^128, mantissa
-// truncated, any sign; magnitudes below 2^-126 give a signed zero.
-__device__ __forceinline__ float f32_of_f64_any(double v) {
+// Float nearest (ties away from zero) to a double of magnitude in
+// [2^-126, 2^128), any sign; smaller magnitudes give a signed zero.  Integer
+// operations only.
+__device__ __forceinline__ float f32_of_f64_rn(double v) {
     const unsigned hi = (unsigned)__double2hiint(v);
     const unsigned lo = (unsigned)__double2loint(v);
     const unsigned mag = hi & 0x7fffffffu, sgn = hi & 0x80000000u;
-    const unsigned fb = (mag >= 0x38100000u) ? (sgn | ((mag - 0x38000000u) << 3) | (lo >> 29)) : sgn;
+    const unsigned fb = (mag >= 0x38100000u)
+                            ? (sgn | ((((mag - 0x38000000u) << 3) | (lo >> 29)) + ((lo >> 28) & 1u)))
+                            : sgn;
     return __uint_as_float(fb);
 }
 
@@ -214,15 +218,16 @@ kick_kernel(KickArgs A)
                 double s;
                 if (MIXED) {
                     // FP32 seed y0 ~ r^-1; Newton residual e = 1 - r^2 y0^2 with
-                    // r^2 = Rh + Rl: 1 - Rh y0^2 in FP64 (Rh y0 exact in one DMUL, the
-                    // DFMA rounds once), the tail Rl y0^2 (~2^-24) in FP32.
+                    // r^2 = Rh + Rl and Rh y0 = u + ue (exact float product): 1 - u y0
+                    // in one FP64 FMA (exact product, one rounding), the tails
+                    // ue y0 + Rl y0^2 (~2^-24) in FP32.
                     // r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 1.5 e + 1.875 e^2 + O(e^3)),
                     // |e| < 2^-20.  m y0^3 is formed exactly enough (~2^-46) as a sum of
                     // two floats, the correction in FP32, and the parts meet in one FP64 add.
                     const float y0f = rsqrtf(Rh);
-                    const double y0 = float_to_double_exact(__float_as_uint(y0f));
-                    const double t = float_to_double_exact(__float_as_uint(Rh)) * y0;
-                    const double e1 = fma(-t, y0, 1.0);
+                    const float u = Rh * y0f, ue = fmaf(Rh, y0f, -u);   // Rh y0 = u + ue exactly
+                    const double e1 = fma(-float_to_double_exact(__float_as_uint(u)),
+                                          float_to_double_exact(__float_as_uint(y0f)), 1.0);
                     const float p = y0f * y0f, pe = fmaf(y0f, y0f, -p);
                     const float q = p * y0f;
                     float qe = fmaf(p, y0f, -q);
@@ -231,7 +236,7 @@ kick_kernel(KickArgs A)
                     float ce = fmaf(q, mh, -ch);
                     ce = fmaf(q, ml, ce);
                     ce = fmaf(qe, mh, ce);
-                    const float ef = fmaf(-Rl, p, f32_of_f64_any(e1));
+                    const float ef = f32_of_f64_rn(e1) - fmaf(ue, y0f, Rl * p);
                     const float corr = fmaf(ch, fmaf(1.875f * ef, ef, 1.5f * ef), ce);
                     s = f64_of_f32_any(ch) + f64_of_f32_any(corr);
                 } else {
