@@ -38,15 +38,17 @@ UNIT = "Gpair/s"
 # FP64 instructions per pair interaction that each kick form's algorithm needs
 # (FMA counted as one).  Mixed: displacement 3, Newton residual of the FP32
 # seed 1 (one FMA on an exact float product; r^2 = Rh + Rl and the residual's
-# tails are float-float on the FP32 pipe), joining the float-float m r^-3 1,
-# accumulation 3.  FP64:
+# tails are float-float on the FP32 pipe), conversion of m y0^3 to FP64 (free:
+# integer operations), accumulation 3 (the float-float corrections are summed
+# on the FP32 pipe and added once per tile).  FP64:
 # displacement 3, r^2 3, r^-1 to FP64 precision (two Newton steps from a
 # ~2^-22 seed) 6, m r^-3 3, accumulation 3.
-FP64_OPS_PER_PAIR = {"mixed": 8, "fp64": 18}
+FP64_OPS_PER_PAIR = {"mixed": 7, "fp64": 18}
 FP64_OPS_PER_CLK_PER_SM = 2      # measured DFMA throughput per SM per clock on GB300
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed kick launch at
-# N = 65,540 (one ncu capture); valid for the kernel as captured
-KICK_MIXED_DRAM_BYTES = 2.935296e6 + 1.688320e6
+# N = 65,540 (one ncu capture of the kernel as it is now); None when the
+# kernel has changed since the capture
+KICK_MIXED_DRAM_BYTES = None
 
 
 def parse():

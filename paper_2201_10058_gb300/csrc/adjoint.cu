@@ -246,8 +246,8 @@ struct AdjBsArgs {
     double *lx, *lv, *lm;                    // in: adjoint at the end of the drift; out: at its start
     const double *mass, *rc;
     const int *off, *list;
-    const int *glist, *goff, *member, *slotof;
-    const unsigned *ngroups;
+    const int *goff, *member, *slotof;
+    const int *blist;                        // group labels of one size bucket, one block each
     double *scr;                             // [kAD * 14][S]
     size_t S;
     double G, mu, dt, tol;
@@ -311,8 +311,7 @@ __global__ void __launch_bounds__(kABs) bs_adjoint_kernel(AdjBsArgs A) {
     __shared__ double red[kABs / 32];
     __shared__ int stop;
     __shared__ double st_t, st_H;
-    if (blockIdx.x >= *A.ngroups) return;
-    const int g = A.glist[blockIdx.x];
+    const int g = A.blist[blockIdx.x];
     const int s0 = A.goff[g], s1 = A.goff[g + 1];
     if (s1 - s0 > kBlockGroupMax) return;                // the batched driver's groups
     const size_t N = (size_t)A.n;
@@ -606,15 +605,22 @@ int step_vjp(genga_system *s, int64_t k, const double *start, double *lx, double
         B.lx = lx; B.lv = lv; B.lm = lm;
         B.mass = s->mass; B.rc = s->rcl[0].rc;
         B.off = s->csr[0].off; B.list = s->csr[0].list;
-        B.glist = s->glist; B.goff = s->goff; B.member = s->member; B.slotof = s->slotof;
-        B.ngroups = &s->ctr->ngroups;
+        B.goff = s->goff; B.member = s->member; B.slotof = s->slotof;
         B.scr = a->bs_scr; B.S = n;
         B.G = s->p.G; B.mu = s->p.G * s->p.m_star; B.dt = dt; B.tol = s->p.bs_tol;
         B.max_steps = s->p.bs_max_steps; B.ctr = s->ctr;
-        bs_adjoint_kernel<<<(unsigned)std::min<int64_t>(np, s->n / 2 + 1), kABs, 0, s->stream>>>(B);
-        ++s->launches;
-        ACU(cudaGetLastError());
-        if ((rc = bsm_adjoint_groups(s, a->tmp, a->tmp + 3 * n, lx, lv, lm, dt)) != GENGA_OK) return rc;
+        unsigned counts[kBuckets];
+        ACU(bucket_groups(s, counts));
+        for (int b = 0; b < kBuckets - 1; b++) {
+            if (!counts[b]) continue;
+            B.blist = s->bucket_list + (size_t)b * s->bucket_stride;
+            bs_adjoint_kernel<<<counts[b], kABs, 0, s->stream>>>(B);
+            ++s->launches;
+            ACU(cudaGetLastError());
+        }
+        if (counts[kBuckets - 1] &&
+            (rc = bsm_adjoint_groups(s, a->tmp, a->tmp + 3 * n, lx, lv, lm, dt)) != GENGA_OK)
+            return rc;
     }
     if ((rc = hc_vjp(s, lx, s->pre_vel[0], lv, lm, h)) != GENGA_OK) return rc;
     if ((rc = kick_vjp(s, start, lv, lx, lm, h)) != GENGA_OK) return rc;

@@ -31,6 +31,7 @@ struct BsArgs {
     int nlev;
     const int *off, *list;
     const int *glist, *goff, *member, *slotof;
+    const int *blist;      // this kernel's bucket: group labels, one block each
     double G, mu, dt, tol;
     int max_steps;
     unsigned long long time_limit_ns;
@@ -238,10 +239,9 @@ bs_cols_kernel(BsArgs A) {
     __shared__ ColsShared<M> S;
     const int tid = threadIdx.x;
     const int col = tid / M, a = tid % M;
-    if (blockIdx.x >= A.ctr->ngroups) return;
-    const int g = A.glist[blockIdx.x];
+    const int g = A.blist[blockIdx.x];
     const int s0 = A.goff[g], nm = A.goff[g + 1] - s0;
-    if (nm > M || (M > 4 && nm <= M / 2)) return;          // another bucket's group
+    if (nm > M || (M > 4 && nm <= M / 2)) return;          // not this bucket (never taken)
     const unsigned long long t_start = global_ns();
     const size_t N = (size_t)A.n;
 
@@ -369,8 +369,7 @@ bs_cols_kernel(BsArgs A) {
 
 }  // namespace
 
-cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_groups) {
-    if (max_groups <= 0) return cudaSuccess;
+cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned counts[kBuckets]) {
     BsArgs A;
     A.n = (int)s->n;
     A.pre_pos = s->pre_pos[level];
@@ -388,15 +387,27 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_group
     // their slowest groups overlap
     GENGA_CUDA_TRY(cudaEventRecord(s->ev_fork, s->stream));
     for (int q = 0; q < 4; q++) GENGA_CUDA_TRY(cudaStreamWaitEvent(s->side[q], s->ev_fork, 0));
-    const unsigned grid = (unsigned)max_groups;
-    bs_cols_kernel<4><<<grid, 32, 0, s->side[0]>>>(A); ++s->launches;
-    GENGA_CUDA_TRY(cudaGetLastError());
-    bs_cols_kernel<8><<<grid, 64, 0, s->side[1]>>>(A); ++s->launches;
-    GENGA_CUDA_TRY(cudaGetLastError());
-    bs_cols_kernel<16><<<grid, 128, 0, s->side[2]>>>(A); ++s->launches;
-    GENGA_CUDA_TRY(cudaGetLastError());
-    bs_cols_kernel<32><<<grid, 256, 0, s->side[3]>>>(A); ++s->launches;
-    GENGA_CUDA_TRY(cudaGetLastError());
+    const size_t st = (size_t)s->bucket_stride;
+    if (counts[0]) {
+        A.blist = s->bucket_list;
+        bs_cols_kernel<4><<<counts[0], 32, 0, s->side[0]>>>(A); ++s->launches;
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    if (counts[1]) {
+        A.blist = s->bucket_list + st;
+        bs_cols_kernel<8><<<counts[1], 64, 0, s->side[1]>>>(A); ++s->launches;
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    if (counts[2]) {
+        A.blist = s->bucket_list + 2 * st;
+        bs_cols_kernel<16><<<counts[2], 128, 0, s->side[2]>>>(A); ++s->launches;
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
+    if (counts[3]) {
+        A.blist = s->bucket_list + 3 * st;
+        bs_cols_kernel<32><<<counts[3], 256, 0, s->side[3]>>>(A); ++s->launches;
+        GENGA_CUDA_TRY(cudaGetLastError());
+    }
     return cudaGetLastError();
 }
 

@@ -702,9 +702,11 @@ int bsm_forward_groups(genga_system *s, int level, double dt_l) {
 // itself) the persistent driver for the larger ones.
 int run_bs(genga_system *s, int level, double dt_l, int64_t np) {
     if (np <= 0) return GENGA_OK;
-    const cudaError_t e = launch_bs(s, level, dt_l, std::min<int64_t>(np, s->n / 2 + 1));
+    unsigned counts[kBuckets];
+    if (bucket_groups(s, counts) != cudaSuccess) return GENGA_ECUDA;
+    const cudaError_t e = launch_bs(s, level, dt_l, counts);
     if (join_bs(s) != cudaSuccess || e != cudaSuccess) return GENGA_ECUDA;
-    return bsm_forward_groups(s, level, dt_l);
+    return counts[kBuckets - 1] ? bsm_forward_groups(s, level, dt_l) : GENGA_OK;
 }
 
 // Adjoint BS (backward, augmented) of every group larger than kBlockGroupMax.

@@ -15,6 +15,8 @@ constexpr int kMaxLevels = 8;
 // Close-encounter groups with more members than this are integrated by the
 // batched grid-wide Bulirsch-Stoer driver (bsm.cu) instead of one thread block.
 constexpr int kBlockGroupMax = 32;
+// Group size buckets: up to 4, 8, 16 and 32 members (in-block kernels), larger.
+constexpr int kBuckets = 5;
 
 // Device error word bits (latched; read by the host after synchronising).
 enum : unsigned {
@@ -43,6 +45,8 @@ struct DevCounters {
     unsigned int max_group;
     unsigned int pad;
     double hc_shift[3];
+    unsigned int bucket_count[kBuckets];   // groups per size bucket (bucket_groups)
+    unsigned int pad2[8 - kBuckets];
 };
 
 // Level-independent per-body data of the critical radius (level 0 uses all).
@@ -113,6 +117,8 @@ struct genga_system {
     int *glist = nullptr;    // n
     int *member = nullptr;   // n
     int *slotof = nullptr;   // n
+    int *bucket_list = nullptr;  // kBuckets x bucket_stride group labels per size bucket
+    int bucket_stride = 0;       // n / 2 + 1 (groups have at least 2 members)
     int label_level = -1;    // level whose grouping `label` holds
 
     // batched grid-wide Bulirsch-Stoer buffers (bsm.cu), grown on demand
@@ -211,9 +217,13 @@ void bsm_release(genga_system *s);
 int run_bs(genga_system *s, int level, double dt_l, int64_t np);
 int bsm_adjoint_groups(genga_system *s, const double *x2, const double *v2, double *lx, double *lv,
                        double *lm, double dt);
+// Sorts the current groups into the size buckets (device lists + counts) and
+// copies the kBuckets counts to the host (synchronises).
+cudaError_t bucket_groups(genga_system *s, unsigned counts[kBuckets]);
 // Launches the in-block BS kernels on the side streams (forked from the
-// system stream); join_bs makes the system stream wait for them.
-cudaError_t launch_bs(genga_system *s, int level, double dt_l, int64_t max_groups);
+// system stream), one block per group of each of the first four buckets;
+// join_bs makes the system stream wait for them.
+cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned counts[kBuckets]);
 cudaError_t join_bs(genga_system *s);
 cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb);
 

@@ -289,6 +289,29 @@ cudaError_t build_bodies(genga_system *s, int level_pairs, int out_level, int *n
 }
 
 // Connected components of the pair list of `level` (its CSR must be built).
+__global__ void bucket_groups_kernel(const DevCounters *ctr, const int *glist, const int *goff, int stride,
+                                     int *blist, unsigned *bcount) {
+    const unsigned ng = ctr->ngroups;
+    for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < ng; q += gridDim.x * blockDim.x) {
+        const int g = glist[q];
+        const int sz = goff[g + 1] - goff[g];
+        const int b = sz <= 4 ? 0 : sz <= 8 ? 1 : sz <= 16 ? 2 : sz <= kBlockGroupMax ? 3 : 4;
+        const unsigned k = atomicAdd(&bcount[b], 1u);
+        blist[(size_t)b * stride + k] = g;
+    }
+}
+
+cudaError_t bucket_groups(genga_system *s, unsigned counts[kBuckets]) {
+    GENGA_CUDA_TRY(cudaMemsetAsync(s->ctr->bucket_count, 0, sizeof(unsigned) * kBuckets, s->stream));
+    bucket_groups_kernel<<<2 * s->num_sms, 256, 0, s->stream>>>(s->ctr, s->glist, s->goff, s->bucket_stride,
+                                                               s->bucket_list, s->ctr->bucket_count);
+    ++s->launches;
+    GENGA_CUDA_TRY(cudaGetLastError());
+    GENGA_CUDA_TRY(cudaMemcpyAsync(counts, s->ctr->bucket_count, sizeof(unsigned) * kBuckets,
+                                   cudaMemcpyDeviceToHost, s->stream));
+    return cudaStreamSynchronize(s->stream);
+}
+
 cudaError_t build_groups(genga_system *s, int level, int64_t np) {
     const int n = (int)s->n;
     GENGA_CUDA_TRY(cudaMemsetAsync(s->gsize, 0, sizeof(int) * (n + 1), s->stream));

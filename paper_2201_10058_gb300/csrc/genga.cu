@@ -132,6 +132,8 @@ int alloc_all(genga_system *s) {
     CU(dalloc(&s->glist, n + 1));
     CU(dalloc(&s->member, n + 1));
     CU(dalloc(&s->slotof, n));
+    s->bucket_stride = (int)(n / 2 + 1);
+    CU(dalloc(&s->bucket_list, (size_t)kBuckets * s->bucket_stride));
     CU(dalloc(&s->red, 9 * n + 16));
     s->scr.scan_blocks_cap = (int)((n + 1 + 4095) / 4096) + 2;
     CU(dalloc(&s->scr.scan_blocks, (size_t)s->scr.scan_blocks_cap));
@@ -151,7 +153,7 @@ void free_all(genga_system *s) {
     }
     dfree(s->kick_part); dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
     dfree(s->gsize); dfree(s->goff); dfree(s->gfill); dfree(s->glist); dfree(s->member);
-    dfree(s->slotof); bsm_release(s); dfree(s->red); dfree(s->scr.scan_blocks);
+    dfree(s->slotof); dfree(s->bucket_list); bsm_release(s); dfree(s->red); dfree(s->scr.scan_blocks);
     for (int k = 0; k < 4; k++) {
         if (s->side[k]) cudaStreamDestroy(s->side[k]);
         if (s->ev_join[k]) cudaEventDestroy(s->ev_join[k]);

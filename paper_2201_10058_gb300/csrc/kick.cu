@@ -19,9 +19,11 @@
 //     from an exact integer split of the displacement (no FP64 work); FP32
 //     rsqrt seed y0; one FP64 Newton residual e = 1 - r^2 y0^2 (its leading
 //     part in one FP64 FMA on an exact float product, the float tails added
-//     in FP32); r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) in float-float; FP64
-//     accumulation, per-tile sums folded with TwoSum: 8 FP64 instructions
-//     per pair.
+//     in FP32); r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) = m y0^3 + corr in
+//     float-float; FP64 accumulation of (m y0^3) dx, the corrections corr dx
+//     (< 2^-19 of each term) summed in float-float per tile and added to the
+//     FP64 sums once per tile; per-tile sums folded with TwoSum:
+//     7 FP64 instructions per pair.
 //     FP64: CUDA's double rsqrt, 18 FP64 instructions per pair.
 #include "common.cuh"
 
@@ -29,6 +31,12 @@ namespace genga {
 namespace {
 
 constexpr int kKickThreads = 128;
+// Resident blocks per SM the register allocation must allow (128 threads
+// each): 5 (at most 96 registers) for the mixed force-only form, 7 (72) for
+// the FP64 one, 4 with the pre-check.
+constexpr int kick_min_blocks(bool mixed, bool precheck) {
+    return precheck ? 4 : (mixed ? 5 : 7);
+}
 constexpr int kTile = 256;
 
 struct KickArgs {
@@ -57,6 +65,14 @@ __device__ __forceinline__ float r2_to_float_trunc(double r2) {
 // Double with the value of a positive normal float (exact).
 __device__ __forceinline__ double float_to_double_exact(unsigned fb) {
     return __hiloint2double((int)((fb >> 3) + 0x38000000u), (int)(fb << 29));
+}
+
+// (hi, lo) += v in float-float: TwoSum of hi and v, the rounding error into lo.
+__device__ __forceinline__ void float_two_sum_acc(float &hi, float &lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
 }
 
 // Double with the value of a float (exact), for any sign; zero and subnormal
@@ -97,7 +113,7 @@ __device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
 }
 
 template <bool MIXED, bool PRECHECK, bool FORCE>
-__global__ void __launch_bounds__(kKickThreads)
+__global__ void __launch_bounds__(kKickThreads, kick_min_blocks(MIXED, PRECHECK))
 kick_kernel(KickArgs A)
 {
     __shared__ double sx[kTile], sy[kTile], sz[kTile], sm[kTile];
@@ -142,6 +158,10 @@ kick_kernel(KickArgs A)
         __syncthreads();
 
         double ax = 0.0, ay = 0.0, az = 0.0;
+        // MIXED: the small correction terms corr * dx (|corr| < 2^-19 m r^-3) of
+        // this tile, summed in float-float (TwoSum) and folded into the FP64
+        // sums once per tile
+        float cxh = 0.0f, cxl = 0.0f, cyh = 0.0f, cyl = 0.0f, czh = 0.0f, czl = 0.0f;
 #pragma unroll 4
         for (int k = 0; k < cnt; k++) {
             const int j = jt + k;
@@ -238,7 +258,10 @@ kick_kernel(KickArgs A)
                     ce = fmaf(qe, mh, ce);
                     const float ef = f32_of_f64_rn(e1) - fmaf(ue, y0f, Rl * p);
                     const float corr = fmaf(ch, fmaf(1.875f * ef, ef, 1.5f * ef), ce);
-                    s = f64_of_f32_any(ch) + f64_of_f32_any(corr);
+                    s = f64_of_f32_any(ch);
+                    float_two_sum_acc(cxh, cxl, corr * hx);
+                    float_two_sum_acc(cyh, cyl, corr * hy);
+                    float_two_sum_acc(czh, czl, corr * hz);
                 } else {
                     const double yv = rsqrt(r2);
                     s = (mk * yv) * (yv * yv);
@@ -247,6 +270,11 @@ kick_kernel(KickArgs A)
                 ay = fma(s, dy, ay);
                 az = fma(s, dz, az);
             }
+        }
+        if (MIXED && FORCE) {
+            ax += f64_of_f32_any(cxh) + f64_of_f32_any(cxl);
+            ay += f64_of_f32_any(cyh) + f64_of_f32_any(cyl);
+            az += f64_of_f32_any(czh) + f64_of_f32_any(czl);
         }
         if (FORCE) {
             double t, e;

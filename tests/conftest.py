@@ -25,9 +25,11 @@ def cuda_lib():
 
 
 def pytest_terminal_summary(terminalreporter):
-    """Logs the candidate pairs found within 1e-12 relative of their critical
-    radius by the detection parity tests (their decisions were compared
-    bit-exactly with the oracle's like all others)."""
+    """Logs the measured parity margins and the candidate pairs found within
+    1e-12 relative of their critical radius by the detection parity tests
+    (their decisions were compared bit-exactly with the oracle's like all
+    others)."""
+    _print_numerics(terminalreporter)
     try:
         from tests import borderline
     except ImportError:
@@ -42,3 +44,16 @@ def pytest_terminal_summary(terminalreporter):
             tr.write_line(f"    ({i}, {j}) {tag} |r/rc - 1| = {q:.3e}")
         if len(found) > 20:
             tr.write_line(f"    ... {len(found) - 20} more")
+
+
+def _print_numerics(terminalreporter):
+    try:
+        from tests import numerics_log
+    except ImportError:
+        return
+    if not numerics_log.LOG:
+        return
+    tr = terminalreporter
+    tr.section("measured parity (largest relative error / tolerance)")
+    for case, quantity, value, tol in numerics_log.LOG:
+        tr.write_line(f"{case}: {quantity} {value:.3e} (tolerance {tol:.0e})")

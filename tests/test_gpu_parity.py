@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from tests import borderline
+from tests import borderline, numerics_log
 from workloads import G_GAUSS, config_workload, disk, ring
 
 pytestmark = pytest.mark.gpu
@@ -94,6 +94,7 @@ def test_kick_acceleration_matches_oracle(g, name, make, precision, tol):
     a = _acc(g, wl, precision, rc)
     ref = O.accel(wl.x, wl.m, rc, G, nthreads=8)
     rel = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    numerics_log.record(f"kick {name} precision={precision}", "per-particle |da|/|a|", rel.max(), tol)
     assert rel.max() <= tol, (rel.max(), np.argmax(rel))
     # momentum balance of the GPU kick (force scaling is symmetric)
     F = wl.m[:, None] * a
@@ -108,7 +109,7 @@ def test_kick_config1_size(g, precision, tol):
     a = _acc(g, wl, precision, rc)
     ref = O.accel(wl.x, wl.m, rc, G, nthreads=16)
     rel = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
-    print(f"N=16384 precision={precision}: max {rel.max():.3e} median {np.median(rel):.3e}")
+    numerics_log.record(f"kick disk16384 precision={precision}", "per-particle |da|/|a|", rel.max(), tol)
     assert rel.max() <= tol
 
 
@@ -123,6 +124,8 @@ def test_kick_bench_size_sampled_rows(g, precision, tol):
     rows = np.concatenate([rows, [0, wl.n - 1, wl.n - 2, wl.n - 4]])   # embryos and the tail
     ref = O.accel_rows(wl.x, wl.m, rc, G, rows, nthreads=16)
     rel = np.linalg.norm(a[rows] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    numerics_log.record(f"kick disk65540 (516 rows) precision={precision}", "per-particle |da|/|a|",
+                        rel.max(), tol)
     assert rel.max() <= tol, rel.max()
 
 
@@ -325,6 +328,7 @@ def test_steps_match_oracle_config0(g, precision):
     xr10, _, status, _ = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=8), 10)
     assert status == 0
     e10 = _rel_pos_err(_host(pos), xr10)
+    numerics_log.record(f"10 steps disk2048 precision={precision}", "max |dx|/|x|", e10.max(), tol)
     assert e10.max() <= tol, e10.max()
     s.step(90)
     st = s.stats()
@@ -332,9 +336,9 @@ def test_steps_match_oracle_config0(g, precision):
     assert status == 0
     err = _rel_pos_err(_host(pos), xr)
     spread = _ulp_sensitivity(wl, 100)
-    print(f"precision={precision} 100 steps: max={err.max():.3e} p99.9={np.quantile(err, 0.999):.3e} "
-          f"median={np.median(err):.3e}; oracle 1-ulp spread max={spread.max():.3e} "
-          f"p99.9={np.quantile(spread, 0.999):.3e}")
+    numerics_log.record(f"100 steps disk2048 precision={precision}", "max |dx|/|x|", err.max(),
+                        3 * spread.max() if precision == 0 else 1e-9)
+    numerics_log.record("100 steps disk2048 oracle one-ulp spread", "max |dx|/|x|", spread.max(), 1.0)
     assert ost["n_pairs"][0] > 0
     if precision == 0:
         assert err.max() <= 3 * spread.max()
