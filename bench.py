@@ -48,7 +48,7 @@ FP64_OPS_PER_CLK_PER_SM = 2      # measured DFMA throughput per SM per clock on 
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed kick launch at
 # N = 65,540 (one ncu capture of the kernel as it is now); None when the
 # kernel has changed since the capture
-KICK_MIXED_DRAM_BYTES = None
+KICK_MIXED_DRAM_BYTES = 2.940416e6 + 1.733376e6
 
 
 def parse():

@@ -121,8 +121,8 @@ __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
 // Neville table is built per (member, component) afterwards and the first
 // column k >= 1 under tolerance is accepted -- the same arithmetic and the same
 // acceptance rule as the serial scheme.  FP64 throughout.
-// Pairs of a group of M member slots evaluated once each (M <= 16): the
-// upper triangle, a < q, at index a M - a (a + 1) / 2 + q - a - 1.
+// Pairs of a group of M member slots evaluated once each (M <= 16), listed
+// in (a, q) order with a < q; at most M (M - 1) / 2.
 template <int M>
 constexpr int kColsPairs = (M <= 16) ? M * (M - 1) / 2 : 1;
 
@@ -130,6 +130,10 @@ template <int M>
 struct ColsShared {
     double zx[8 * M], zy[8 * M], zz[8 * M];      // current positions, per (column, member)
     double pt[3][8][kColsPairs<M>];              // W r^-3 (x_q - x_a) per column and pair a < q
+    unsigned char pa[kColsPairs<M>], pq[kColsPairs<M>];   // the group's pairs (a < q), by a then q
+    unsigned char pidx[M <= 16 ? M * M : 1];     // (a, q) -> pair index, both orders
+    unsigned pmask[M];                           // partner ranks of each member
+    int npairs;
     double m[M];
     double irc[kMaxLevels][M];
     double y[6][M], f0[6][M];                    // attempt start and its derivative
@@ -149,28 +153,24 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
     __syncthreads();
     f[0] = z[3]; f[1] = z[4]; f[2] = z[5];
     if constexpr (M <= 16) {
-        // each pair once, by its lower-ranked member; then every member sums
-        // its partners' terms in ascending rank order (m_q t for q > a,
-        // -m_q t for q < a): exactly antisymmetric pair forces
+        // each pair once; then every member sums its partners' terms in
+        // ascending rank order (m_q t for q > a, -m_q t for q < a): exactly
+        // antisymmetric pair forces
         const int a = tid % M;
-        if (active) {
-            unsigned mm = mask & ~((2u << a) - 1u);
-            while (mm) {
-                const int q = __ffs(mm) - 1;
-                mm &= mm - 1;
-                const int lq = col * M + q;
-                const double dx = S.zx[lq] - z[0], dy = S.zy[lq] - z[1], dz = S.zz[lq] - z[2];
-                const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                const double yv = rsqrt_newton(d2);
-                const double d = d2 * yv;
-                double W = 1.0;
-                for (int l = 0; l < A.nlev; l++) W *= 1.0 - changeover_fast(d, fmin(irc_self[l], S.irc[l][q]));
-                const double c = W * (yv * yv * yv);
-                const int pi = a * M - a * (a + 1) / 2 + q - a - 1;
-                S.pt[0][col][pi] = c * dx;
-                S.pt[1][col][pi] = c * dy;
-                S.pt[2][col][pi] = c * dz;
-            }
+        // the column's pairs round-robin over its M threads (short chains)
+        for (int pi = a; pi < S.npairs; pi += M) {
+            const int pa = S.pa[pi], pq = S.pq[pi];
+            const int la = col * M + pa, lq = col * M + pq;
+            const double dx = S.zx[lq] - S.zx[la], dy = S.zy[lq] - S.zy[la], dz = S.zz[lq] - S.zz[la];
+            const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            const double yv = rsqrt_newton(d2);
+            const double d = d2 * yv;
+            double W = 1.0;
+            for (int l = 0; l < A.nlev; l++) W *= 1.0 - changeover_fast(d, fmin(S.irc[l][pa], S.irc[l][pq]));
+            const double c = W * (yv * yv * yv);
+            S.pt[0][col][pi] = c * dx;
+            S.pt[1][col][pi] = c * dy;
+            S.pt[2][col][pi] = c * dz;
         }
         __syncthreads();
         if (!active) { f[3] = f[4] = f[5] = 0.0; return; }
@@ -182,8 +182,7 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
         while (mm) {
             const int q = __ffs(mm) - 1;
             mm &= mm - 1;
-            const int lo = q < a ? q : a, hi = q < a ? a : q;
-            const int pi = lo * M - lo * (lo + 1) / 2 + hi - lo - 1;
+            const int pi = S.pidx[a * M + q];
             const double w = q > a ? S.m[q] : -S.m[q];
             px = fma(w, S.pt[0][col][pi], px);
             py = fma(w, S.pt[1][col][pi], py);
@@ -271,6 +270,25 @@ bs_cols_kernel(BsArgs A) {
         if (col == 0) {
             S.m[a] = A.mass[b];
             for (int l = 0; l < A.nlev; l++) S.irc[l][a] = irc_self[l];
+        }
+    }
+    if constexpr (M <= 16) {
+        if (col == 0) S.pmask[a] = active ? pmask : 0u;
+        __syncthreads();
+        if (tid == 0) {                          // pair list in (a, q) order
+            int np = 0;
+            for (int aa = 0; aa < M; aa++) {
+                unsigned mm = S.pmask[aa] & ~((2u << aa) - 1u);
+                while (mm) {
+                    const int q = __ffs(mm) - 1;
+                    mm &= mm - 1;
+                    S.pa[np] = (unsigned char)aa;
+                    S.pq[np] = (unsigned char)q;
+                    S.pidx[aa * M + q] = S.pidx[q * M + aa] = (unsigned char)np;
+                    np++;
+                }
+            }
+            S.npairs = np;
         }
     }
     __syncthreads();
