@@ -74,16 +74,25 @@ def parse():
 
 # ---------------------------------------------------------------- distributed plumbing
 class Dist:
-    def __init__(self, ngpus: int):
+    """Replica bookkeeping for N processes (one per GPU): every rank integrates
+    its own copy of the workload; the only collectives are the barriers around
+    the timed region and the max of the ranks' times.  Backend: NCCL on GPUs,
+    gloo for the CPU tests of this logic."""
+
+    def __init__(self, ngpus: int, backend: str | None = None):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
+        self.backend = backend or "nccl"
         if self.world > 1:
             import torch
             import torch.distributed as dist
-            torch.cuda.set_device(self.local)
-            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            if self.backend == "nccl":
+                torch.cuda.set_device(self.local)
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            else:
+                dist.init_process_group(self.backend)
             self.pg = dist
 
     def barrier(self):
@@ -94,13 +103,20 @@ class Dist:
         if not self.pg:
             return v
         import torch
-        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{self.local}")
+        dev = f"cuda:{self.local}" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
         self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
         return float(t.item())
 
     def close(self):
         if self.pg:
             self.pg.destroy_process_group()
+
+
+def replica_throughput(world: int, units_per_step: float, steps: int, t_max_ms: float) -> float:
+    """Whole-job throughput of `world` replicas: the units all ranks processed
+    divided by the slowest rank's time (units per second)."""
+    return world * units_per_step * steps / (t_max_ms * 1e-3)
 
 
 # ---------------------------------------------------------------- clocks
@@ -239,8 +255,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         t_max = dist.max(total_ms)
         results[name] = {
             "ms_per_step": t_max / args.steps,
-            "gpairs_per_s": dist.world * pairs_per_step * args.steps / (t_max * 1e-3) / 1e9,
-            "steps_per_s": dist.world * args.steps / (t_max * 1e-3),
+            "gpairs_per_s": replica_throughput(dist.world, pairs_per_step, args.steps, t_max) / 1e9,
+            "steps_per_s": replica_throughput(dist.world, 1.0, args.steps, t_max),
             "kick_ms": kick_ms,
             "kick_gpairs_per_s": n * (n - 1) / (kick_ms * 1e-3) / 1e9,
             "kick_share": 2 * kick_ms / (total_ms / args.steps),

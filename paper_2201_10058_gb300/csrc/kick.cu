@@ -32,10 +32,11 @@ namespace {
 
 constexpr int kKickThreads = 128;
 // Resident blocks per SM the register allocation must allow (128 threads
-// each): 5 (at most 96 registers) for the mixed force-only form, 7 (72) for
-// the FP64 one, 4 with the pre-check.
+// each), chosen by measurement at N = 65,540: mixed force-only 5 (96
+// registers), mixed with pre-check 6 (80; 61.4 ms against 62.5 ms at 4),
+// FP64 force-only 7 (72), FP64 with pre-check 4.
 constexpr int kick_min_blocks(bool mixed, bool precheck) {
-    return precheck ? 4 : (mixed ? 5 : 7);
+    return precheck ? (mixed ? 6 : 4) : (mixed ? 5 : 7);
 }
 constexpr int kTile = 256;
 
