@@ -121,8 +121,9 @@ int genga_set_rcrit(genga_system_t *sys, const double *rc_host);
  *     v_i += dt_half * G * sum_{j != i} m_j K(r_ij; rc_ij) (x_j - x_i) / r_ij^3
  * with the changeover function K of Chambers (1999), Eq. 10 (Sec. 4.3 fn.),
  * rc_ij = max(rc_i, rc_j) from genga_rcrit, in the arithmetic selected by
- * params.precision.  If precheck != 0 the same pass records the close-encounter
- * candidates (i < j with r_ij^2 < (f_pc rc_ij)^2) for genga_build_encounters.
+ * params.precision.  If precheck != 0 a pass before the kick records the
+ * close-encounter candidates at the same positions (i < j with
+ * r_ij^2 < (f_pc rc_ij)^2, decided exactly in FP64) for genga_build_encounters.
  * If acc_out (device, 3n doubles, SoA) is not NULL the accelerations
  * G sum_j ... are written there and, when dt_half == 0, v is left unchanged. */
 int genga_kick(genga_system_t *sys, double dt_half, int precheck, double *acc_out);

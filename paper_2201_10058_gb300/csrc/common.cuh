@@ -55,8 +55,6 @@ struct RcritArrays {
     double *rc2;   // rc_i^2 (pair value: max of the two, exact)
     double *pc2;   // (f_pc rc_i)^2 (level 0 only)
     float *thr_rc; // conservative FP32 upper bound of rc_i^2 (level 0 only)
-    float *thr_pc; // conservative FP32 upper bound of (f_pc rc_i)^2 (level 0 only)
-    float *thr_pc_lo; // conservative FP32 lower bound of (f_pc rc_i)^2 (level 0 only)
 };
 
 // CSR partner lists (both directions) of one pair list.

@@ -109,8 +109,6 @@ int alloc_all(genga_system *s) {
     }
     CU(dalloc(&s->rcl[0].pc2, n));
     CU(dalloc(&s->rcl[0].thr_rc, n));
-    CU(dalloc(&s->rcl[0].thr_pc, n));
-    CU(dalloc(&s->rcl[0].thr_pc_lo, n));
     for (int k = 0; k < 4; k++) {
         CU(cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&s->ev_join[k], cudaEventDisableTiming));
@@ -144,7 +142,7 @@ void free_all(genga_system *s) {
     dfree(s->ctr);
     for (int l = 0; l < kMaxLevels; l++) {
         dfree(s->rcl[l].rc); dfree(s->rcl[l].rc2); dfree(s->rcl[l].pc2);
-        dfree(s->rcl[l].thr_rc); dfree(s->rcl[l].thr_pc); dfree(s->rcl[l].thr_pc_lo);
+        dfree(s->rcl[l].thr_rc);
         dfree(s->pre_pos[l]); dfree(s->pre_vel[l]);
         dfree(s->pairs[l]);
         dfree(s->csr[l].deg); dfree(s->csr[l].off); dfree(s->csr[l].fill); dfree(s->csr[l].list);

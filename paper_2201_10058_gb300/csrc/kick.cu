@@ -1,6 +1,6 @@
 // kick.cu -- all-pairs changeover kick of Eq. Hb (Appendix A "Kick(dt/2)"):
 //   a_i = G sum_{j != i} m_j K(r_ij; rc_ij) (x_j - x_i) / r_ij^3
-// with the close-encounter pre-check fused into the same pass.
+// and the close-encounter pre-check (Appendix A) as a separate FP32 pass.
 //
 // GB300 design.  The kick is bound by the FP64 pipe (about 2 DFMA per clock per
 // SM on GB300, 1/64 of FP32), so the kernel minimises FP64 instructions per
@@ -10,11 +10,10 @@
 //   * the grid is (i-tiles x j-chunks) so that thousands of equal blocks
 //     balance across the 152 SMs; each block writes compensated partial sums
 //     for its chunk, folded in a fixed order by kick_finalize (deterministic);
-//   * the rare pairs inside f_pc rc_ij are found by an FP32 test on the high
-//     bits of r^2 (conservative threshold); only those take the exact FP64
-//     pre-check (operation order identical to the definition, no contraction)
-//     and the changeover function; candidates are appended with one atomic per
-//     warp (ballot + popc);
+//   * the rare pairs inside rc_ij are found by an FP32 test on r^2 against a
+//     conservative threshold; only those evaluate the changeover function;
+//   * the pre-check runs over the pairs i < j on the FP32 pipe alone
+//     (precheck_kernel below), so the FP64-bound kick carries none of it;
 //   * MIXED: FP64 displacement; r^2 formed as an unevaluated sum of two floats
 //     from an exact integer split of the displacement (no FP64 work); FP32
 //     rsqrt seed y0; one FP64 Newton residual e = 1 - r^2 y0^2 (its leading
@@ -32,11 +31,10 @@ namespace {
 
 constexpr int kKickThreads = 128;
 // Resident blocks per SM the register allocation must allow (128 threads
-// each), chosen by measurement at N = 65,540: mixed force-only 5 (96
-// registers), mixed with pre-check 6 (80; 61.4 ms against 62.5 ms at 4),
-// FP64 force-only 7 (72), FP64 with pre-check 4.
-constexpr int kick_min_blocks(bool mixed, bool precheck) {
-    return precheck ? (mixed ? 6 : 4) : (mixed ? 5 : 7);
+// each), chosen by measurement at N = 65,540: mixed 5 (at most 96
+// registers), FP64 7 (72).
+constexpr int kick_min_blocks(bool mixed) {
+    return mixed ? 5 : 7;
 }
 constexpr int kTile = 256;
 
@@ -44,8 +42,6 @@ struct KickArgs {
     const double *x, *y, *z, *m;
     const double *rc, *rc2, *pc2;
     const float *thr_rc;        // FP32 upper bound of rc^2
-    const float *thr_pc;        // FP32 upper bound of (f_pc rc)^2 (pre-check only)
-    const float *thr_pc_lo;     // FP32 lower bound of (f_pc rc)^2 (pre-check only)
     int n;
     int chunk;
     double *part;               // [nchunk][6][n]
@@ -113,26 +109,24 @@ __device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
     lo = __uint_as_float(__float_as_uint(l) | sgn);
 }
 
-template <bool MIXED, bool PRECHECK, bool FORCE>
-__global__ void __launch_bounds__(kKickThreads, kick_min_blocks(MIXED, PRECHECK))
+template <bool MIXED>
+__global__ void __launch_bounds__(kKickThreads, kick_min_blocks(MIXED))
 kick_kernel(KickArgs A)
 {
     __shared__ double sx[kTile], sy[kTile], sz[kTile], sm[kTile];
-    __shared__ double src[kTile], spc2[kTile];
-    __shared__ float sthr[kTile], sthr_pc[kTile], sthr_lo[kTile], smh[kTile], sml[kTile];
+    __shared__ double src[kTile];
+    __shared__ float sthr[kTile], smh[kTile], sml[kTile];
 
     const int n = A.n;
     const int i = blockIdx.x * kKickThreads + threadIdx.x;
     const bool valid = i < n;
-    const unsigned lane = threadIdx.x & 31u;
 
     double xi = 1e15, yi = 1e15, zi = 1e15;
-    double rci = 0.0, pc2i = 0.0;
-    float thri = 0.0f, thri_pc = 0.0f, thri_lo = 0.0f;
+    double rci = 0.0;
+    float thri = 0.0f;
     if (valid) {
         xi = A.x[i]; yi = A.y[i]; zi = A.z[i];
         rci = A.rc[i]; thri = A.thr_rc[i];
-        if (PRECHECK) { pc2i = A.pc2[i]; thri_pc = A.thr_pc[i]; thri_lo = A.thr_pc_lo[i]; }
     }
 
     const int jbeg = blockIdx.y * A.chunk;
@@ -149,7 +143,6 @@ kick_kernel(KickArgs A)
             sx[k] = A.x[j]; sy[k] = A.y[j]; sz[k] = A.z[j]; sm[k] = A.m[j];
             src[k] = A.rc[j];
             sthr[k] = A.thr_rc[j];
-            if (PRECHECK) { spc2[k] = A.pc2[j]; sthr_pc[k] = A.thr_pc[j]; sthr_lo[k] = A.thr_pc_lo[j]; }
             if (MIXED) {     // mass as an unevaluated sum of two floats
                 const float mh = __double2float_rn(A.m[j]);
                 smh[k] = mh;
@@ -199,26 +192,6 @@ kick_kernel(KickArgs A)
             double mk = sm[k];
             float mh = 0.0f, ml = 0.0f;
             if (MIXED) { mh = smh[k]; ml = sml[k]; }
-            // Pre-check (bit-exact candidate set): pairs surely inside f_pc rc_ij by the
-            // FP32 lower bound are emitted at once; only the thin band between the
-            // FP32 bounds takes the exact FP64 test in the defining operation order.
-            if (PRECHECK && r2f < fmaxf(thri_pc, sthr_pc[k])) {
-                bool emit = valid && (j > i);
-                if (emit && !(r2f < fmaxf(thri_lo, sthr_lo[k])))
-                    emit = dist2_rn(dx, dy, dz) < fmax(pc2i, spc2[k]);
-                const unsigned act = __activemask();
-                const unsigned ball = __ballot_sync(act, emit);
-                if (ball) {
-                    const int leader = __ffs(ball) - 1;
-                    unsigned long long base = 0;
-                    if ((int)lane == leader) base = atomicAdd(A.cand_count, (unsigned long long)__popc(ball));
-                    base = __shfl_sync(act, base, leader);
-                    if (emit) {
-                        const unsigned long long idx = base + __popc(ball & ((1u << lane) - 1u));
-                        if (idx < A.cand_cap) A.cand[idx] = make_uint2((unsigned)i, (unsigned)j);
-                    }
-                }
-            }
             // Changeover band (rare): K < 1 needs r < rc_ij.  K is flat (zero slope) at
             // r = rc, so the branch may follow the FP32 bound and K uses the r^2 above.
             if (r2f < fmaxf(thri, sthr[k])) {
@@ -226,7 +199,7 @@ kick_kernel(KickArgs A)
                     mk = 0.0; r2 = 1.0; r2f = 1.0f;          // self term: zero, finite
                     Rh = 1.0f; Rl = 0.0f;
                     mh = 0.0f; ml = 0.0f;
-                } else if (FORCE) {
+                } else {
                     const double r2d = MIXED ? fma(dz, dz, fma(dy, dy, dx * dx)) : r2;
                     mk = mk * changeover(sqrt(r2d), fmax(rci, src[k]));
                     if (MIXED) {
@@ -235,7 +208,7 @@ kick_kernel(KickArgs A)
                     }
                 }
             }
-            if (FORCE) {
+            {
                 double s;
                 if (MIXED) {
                     // FP32 seed y0 ~ r^-1; Newton residual e = 1 - r^2 y0^2 with
@@ -272,19 +245,19 @@ kick_kernel(KickArgs A)
                 az = fma(s, dz, az);
             }
         }
-        if (MIXED && FORCE) {
+        if (MIXED) {
             ax += f64_of_f32_any(cxh) + f64_of_f32_any(cxl);
             ay += f64_of_f32_any(cyh) + f64_of_f32_any(cyl);
             az += f64_of_f32_any(czh) + f64_of_f32_any(czl);
         }
-        if (FORCE) {
+        {
             double t, e;
             two_sum(S0, ax, t, e); S0 = t; C0 += e;
             two_sum(S1, ay, t, e); S1 = t; C1 += e;
             two_sum(S2, az, t, e); S2 = t; C2 += e;
         }
     }
-    if (FORCE && valid) {
+    if (valid) {
         double *p = A.part + (size_t)blockIdx.y * 6 * n;
         p[0 * (size_t)n + i] = S0;
         p[1 * (size_t)n + i] = S1;
@@ -292,6 +265,81 @@ kick_kernel(KickArgs A)
         p[3 * (size_t)n + i] = C0;
         p[4 * (size_t)n + i] = C1;
         p[5 * (size_t)n + i] = C2;
+    }
+}
+
+// Close-encounter pre-check over the pairs i < j: candidates are the pairs
+// with r_ij^2 < (f_pc rc_ij)^2, the exact FP64 test in the defining operation
+// order (dist2_rn, no contraction).  Most pairs are decided in FP32 from float
+// copies of the positions (round to nearest, |x_f - x| <= 2^-24 |x| per
+// component): the float distance r_f differs from r by at most
+//   m_ij = sqrt(3) 2^-23 (max|x_i| + max|x_j|)   plus relative rounding,
+// so r_f^2 >= ((1 + 2^-20) P + m_ij)^2 (1 + 2^-20) is surely outside and
+// r_f^2 < ((1 - 2^-20) P - m_ij)^2 (1 - 2^-20) surely inside (P = f_pc rc_ij
+// in FP32); only the band between takes the exact test.  Candidates are
+// appended with one atomic per warp (ballot + popc).
+constexpr int kPcThreads = 128;
+constexpr int kPcTile = 512;
+
+__global__ void __launch_bounds__(kPcThreads)
+precheck_kernel(KickArgs A, double f_pc)
+{
+    __shared__ float sxf[kPcTile], syf[kPcTile], szf[kPcTile], sP[kPcTile], sM[kPcTile];
+    const int n = A.n;
+    const int i0 = blockIdx.x * kPcThreads;
+    const int jbeg = max(blockIdx.y * A.chunk, i0 + 1);
+    const int jend = min(n, blockIdx.y * A.chunk + A.chunk);
+    if (jbeg >= jend) return;                            // block below the diagonal
+    const int i = i0 + threadIdx.x;
+    const bool valid = i < n;
+    const unsigned lane = threadIdx.x & 31u;
+    constexpr float kM = 1.7320509f * 1.1920929e-07f;    // sqrt(3) 2^-23
+    float xf = 0.0f, yf = 0.0f, zf = 0.0f, Pi = 0.0f, Mi = 0.0f;
+    double xi = 0.0, yi = 0.0, zi = 0.0, pc2i = 0.0;
+    if (valid) {
+        xi = A.x[i]; yi = A.y[i]; zi = A.z[i];
+        xf = f32_of_f64_rn(xi); yf = f32_of_f64_rn(yi); zf = f32_of_f64_rn(zi);
+        Pi = (float)f_pc * f32_of_f64_rn(A.rc[i]);
+        Mi = kM * fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf)));
+        pc2i = A.pc2[i];
+    }
+    for (int jt = jbeg; jt < jend; jt += kPcTile) {
+        const int cnt = min(kPcTile, jend - jt);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += kPcThreads) {
+            const int j = jt + k;
+            const float x = f32_of_f64_rn(A.x[j]), y = f32_of_f64_rn(A.y[j]), z = f32_of_f64_rn(A.z[j]);
+            sxf[k] = x; syf[k] = y; szf[k] = z;
+            sP[k] = (float)f_pc * f32_of_f64_rn(A.rc[j]);
+            sM[k] = kM * fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
+        }
+        __syncthreads();
+        for (int k = 0; k < cnt; k++) {
+            const int j = jt + k;
+            const float dx = sxf[k] - xf, dy = syf[k] - yf, dz = szf[k] - zf;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float P = fmaxf(Pi, sP[k]), m = Mi + sM[k];
+            const float to = fmaf(P, 1.0f + 9.5367432e-07f, m);
+            bool emit = false;
+            if (valid && j > i && r2 < to * to * (1.0f + 9.5367432e-07f)) {
+                const float ti = fmaf(P, 1.0f - 9.5367432e-07f, -m);
+                if (ti > 0.0f && r2 < ti * ti * (1.0f - 9.5367432e-07f))
+                    emit = true;
+                else
+                    emit = dist2_rn(A.x[j] - xi, A.y[j] - yi, A.z[j] - zi) < fmax(pc2i, A.pc2[j]);
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, emit);
+            if (ball) {
+                const int leader = __ffs(ball) - 1;
+                unsigned long long base = 0;
+                if ((int)lane == leader) base = atomicAdd(A.cand_count, (unsigned long long)__popc(ball));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (emit) {
+                    const unsigned long long idx = base + __popc(ball & ((1u << lane) - 1u));
+                    if (idx < A.cand_cap) A.cand[idx] = make_uint2((unsigned)i, (unsigned)j);
+                }
+            }
+        }
     }
 }
 
@@ -338,7 +386,7 @@ static KickArgs make_args(genga_system *s, bool precheck) {
     const int64_t n = s->n;
     A.x = s->pos; A.y = s->pos + n; A.z = s->pos + 2 * n; A.m = s->mass;
     A.rc = s->rcl[0].rc; A.rc2 = s->rcl[0].rc2; A.pc2 = s->rcl[0].pc2;
-    A.thr_rc = s->rcl[0].thr_rc; A.thr_pc = s->rcl[0].thr_pc; A.thr_pc_lo = s->rcl[0].thr_pc_lo;
+    A.thr_rc = s->rcl[0].thr_rc;
     A.n = (int)n;
     A.chunk = s->kick_chunk;
     A.part = s->kick_part;
@@ -352,15 +400,12 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
     const int n = (int)s->n;
     if (!s->kick_part) return cudaErrorInvalidValue;
     if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
-    KickArgs A = make_args(s, precheck);
+    KickArgs A = make_args(s, false);
     dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
-    if (precheck)
-        GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->cand_count, 0, sizeof(unsigned long long), s->stream));
+    if (precheck) GENGA_CUDA_TRY(launch_precheck_only(s));
     const bool mixed = s->p.precision == GENGA_MIXED;
-    if (mixed && precheck) kick_kernel<true, true, true><<<grid, kKickThreads, 0, s->stream>>>(A);
-    else if (mixed) kick_kernel<true, false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
-    else if (precheck) kick_kernel<false, true, true><<<grid, kKickThreads, 0, s->stream>>>(A);
-    else kick_kernel<false, false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    if (mixed) kick_kernel<true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    else kick_kernel<false><<<grid, kKickThreads, 0, s->stream>>>(A);
     ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     kick_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(s->kick_part, s->kick_nchunk, n, s->p.G,
@@ -373,9 +418,10 @@ cudaError_t launch_precheck_only(genga_system *s) {
     if (!s->kick_part) return cudaErrorInvalidValue;
     if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
     KickArgs A = make_args(s, true);
-    dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
+    // (i-tile x j-chunk) grid like the kick; blocks wholly below the diagonal return at once
+    dim3 grid((n + kPcThreads - 1) / kPcThreads, s->kick_nchunk);
     GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->cand_count, 0, sizeof(unsigned long long), s->stream));
-    kick_kernel<true, true, false><<<grid, kKickThreads, 0, s->stream>>>(A); ++s->launches;
+    precheck_kernel<<<grid, kPcThreads, 0, s->stream>>>(A, s->p.f_pc); ++s->launches;
     return cudaGetLastError();
 }
 
@@ -393,12 +439,11 @@ cudaError_t launch_kick_raw(const KickRaw &k, int num_sms, int max_nchunk, cudaS
     KickArgs A;
     A.x = k.pos; A.y = k.pos + k.n; A.z = k.pos + 2 * (size_t)k.n; A.m = k.mass;
     A.rc = k.rc; A.rc2 = k.rc2; A.pc2 = nullptr; A.thr_rc = k.thr;
-    A.thr_pc = nullptr; A.thr_pc_lo = nullptr;
     A.n = k.n; A.chunk = chunk; A.part = k.part;
     A.cand = nullptr; A.cand_count = nullptr; A.cand_cap = 0;
     dim3 grid((k.n + kKickThreads - 1) / kKickThreads, nchunk);
-    if (k.mixed) kick_kernel<true, false, true><<<grid, kKickThreads, 0, stream>>>(A);
-    else kick_kernel<false, false, true><<<grid, kKickThreads, 0, stream>>>(A);
+    if (k.mixed) kick_kernel<true><<<grid, kKickThreads, 0, stream>>>(A);
+    else kick_kernel<false><<<grid, kKickThreads, 0, stream>>>(A);
     GENGA_CUDA_TRY(cudaGetLastError());
     kick_finalize<<<(k.n + 255) / 256, 256, 0, stream>>>(k.part, nchunk, k.n, k.G, k.dt_half, k.vel, k.acc_out);
     return cudaGetLastError();

@@ -17,16 +17,14 @@ namespace {
 // |x| and |v| use the detection operation order (no contraction) so that the
 // thresholds compare bit-for-bit with a plain CPU evaluation.
 __device__ __forceinline__ void derive_thresholds(double rc, double f_pc, double *rc2, double *pc2,
-                                                  float *thr_rc, float *thr_pc, float *thr_pc_lo) {
+                                                  float *thr_rc) {
     const double r2 = __dmul_rn(rc, rc);
     const double t = __dmul_rn(f_pc, rc);
     const double p2 = __dmul_rn(t, t);
     *rc2 = r2;
     if (pc2) *pc2 = p2;
-    // conservative FP32 bounds: upper (rounded up, + 2^-16), lower (rounded down, - 2^-16)
+    // conservative FP32 upper bound (rounded up, + 2^-16)
     if (thr_rc) *thr_rc = fmaxf(__double2float_ru(r2) * 1.0000153f, 1.17549435e-38f);
-    if (thr_pc) *thr_pc = fmaxf(__double2float_ru(p2) * 1.0000153f, 1.17549435e-38f);
-    if (thr_pc_lo) *thr_pc_lo = __double2float_rd(p2) * 0.9999847f;
 }
 
 __global__ void rcrit_kernel(int n, const double *pos, const double *vel, const double *mass,
@@ -46,14 +44,13 @@ __global__ void rcrit_kernel(int n, const double *pos, const double *vel, const 
     const double rc = a > b ? a : b;
     out.rc[i] = rc;
     derive_thresholds(rc, f_pc, &out.rc2[i], out.pc2 ? &out.pc2[i] : nullptr,
-                      out.thr_rc ? &out.thr_rc[i] : nullptr, out.thr_pc ? &out.thr_pc[i] : nullptr,
-                      out.thr_pc_lo ? &out.thr_pc_lo[i] : nullptr);
+                      out.thr_rc ? &out.thr_rc[i] : nullptr);
 }
 
 __global__ void rcrit_derive_kernel(int n, double f_pc, RcritArrays a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    derive_thresholds(a.rc[i], f_pc, &a.rc2[i], &a.pc2[i], &a.thr_rc[i], &a.thr_pc[i], &a.thr_pc_lo[i]);
+    derive_thresholds(a.rc[i], f_pc, &a.rc2[i], &a.pc2[i], &a.thr_rc[i]);
 }
 
 // ---------------------------------------------------------------- HC
@@ -212,7 +209,7 @@ __global__ void energy_combine_kernel(double m_star, double *sums) {
 cudaError_t launch_rcrit(genga_system *s, int level, double dt, const int *bodies, int nb) {
     if (nb <= 0) return cudaSuccess;
     RcritArrays out = s->rcl[level];
-    if (level > 0) { out.pc2 = nullptr; out.thr_rc = nullptr; out.thr_pc = nullptr; out.thr_pc_lo = nullptr; }
+    if (level > 0) { out.pc2 = nullptr; out.thr_rc = nullptr; }
     rcrit_kernel<<<(nb + 255) / 256, 256, 0, s->stream>>>((int)s->n, s->pos, s->vel, s->mass,
         s->p.m_star, dt, s->p.n1, s->p.n2, s->p.f_pc, out, bodies, nb, s->ctr); ++s->launches;
     return cudaGetLastError();
