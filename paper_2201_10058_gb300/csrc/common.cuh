@@ -337,6 +337,18 @@ __device__ __forceinline__ double f64_of_f32(float f) {
 __device__ __forceinline__ double half_of(double y) {   // y / 2 for positive normal y
     return __hiloint2double(__double2hiint(y) - 0x00100000, __double2loint(y));
 }
+// Float nearest (ties away from zero) to a double of magnitude in
+// [2^-126, 2^128), any sign; smaller magnitudes give a signed zero.  Integer
+// operations only.
+__device__ __forceinline__ float f32_of_f64_rn(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const unsigned mag = hi & 0x7fffffffu, sgn = hi & 0x80000000u;
+    const unsigned fb = (mag >= 0x38100000u)
+                            ? (sgn | ((((mag - 0x38000000u) << 3) | (lo >> 29)) + ((lo >> 28) & 1u)))
+                            : sgn;
+    return __uint_as_float(fb);
+}
 __device__ __forceinline__ double rsqrt_newton(double x) {
     double y = f64_of_f32(rsqrtf(f32_of_f64_trunc(x)));
 #pragma unroll

@@ -24,36 +24,6 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kScanThreads * kScanItems;
 
-// ---------------------------------------------------------------- detection
-__global__ void detect_kernel(const uint2 *in, const unsigned long long *nin_dev, long long nin_host,
-                              int n, const double *pre, const double *post, const double *rc2,
-                              uint2 *out, unsigned long long cap, unsigned long long *count) {
-    const long long nin = nin_dev ? (long long)*nin_dev : nin_host;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned lane = threadIdx.x & 31u;
-    bool enc = false;
-    uint2 pr = make_uint2(0, 0);
-    if (k < nin) {
-        pr = in[k];
-        const int i = (int)pr.x, j = (int)pr.y;
-        const size_t N = (size_t)n;
-        const double lim = fmax(rc2[i], rc2[j]);
-        const double d0 = dist2_rn(pre[j] - pre[i], pre[N + j] - pre[N + i], pre[2 * N + j] - pre[2 * N + i]);
-        const double d1 = dist2_rn(post[j] - post[i], post[N + j] - post[N + i], post[2 * N + j] - post[2 * N + i]);
-        enc = (d0 < lim) || (d1 < lim);
-    }
-    const unsigned ball = __ballot_sync(0xffffffffu, enc);
-    if (ball == 0u) return;
-    const int leader = __ffs(ball) - 1;
-    unsigned long long base = 0;
-    if ((int)lane == leader) base = atomicAdd(count, (unsigned long long)__popc(ball));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (enc) {
-        const unsigned long long idx = base + __popc(ball & ((1u << lane) - 1u));
-        if (idx < cap) out[idx] = pr;
-    }
-}
-
 // ---------------------------------------------------------------- scan
 // Exclusive scan of int32 in blocks of kScanBlock, then a scan of block sums,
 // then the block offsets are added.  out has len+1 entries (out[len] = total).
@@ -81,6 +51,66 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int &
     total = warp_sums[(blockDim.x >> 5) - 1];
     __syncthreads();
     return before + x - v;
+}
+
+// ---------------------------------------------------------------- detection
+// Encounter <=> r_ij^2 < max(rc_i^2, rc_j^2) before (pre-drift state) or after
+// the drift, the exact FP64 test in the defining operation order (dist2_rn).
+// Most candidates are decided in FP32 from float copies of the positions
+// (round to nearest): the float distance differs from r by at most
+// m_ij = sqrt(3) 2^-23 (max|x_i| + max|x_j|) plus relative rounding, so
+// r_f >= R (1 + 2^-20) + m_ij is surely outside and r_f < R (1 - 2^-20) - m_ij
+// surely inside (R = rc_ij in FP32, squared comparisons with a further
+// 1 +- 2^-20); only the band between takes the exact test.  Encounters are
+// compacted with a block-wide scan and one global atomic per block.
+__device__ __forceinline__ int detect_state(const double *p, size_t N, int i, int j, float Rf) {
+    constexpr float kM = 1.7320509f * 1.1920929e-07f;    // sqrt(3) 2^-23
+    constexpr float kUp = 1.0f + 9.5367432e-07f, kDn = 1.0f - 9.5367432e-07f;
+    const float xi = f32_of_f64_rn(p[i]), yi = f32_of_f64_rn(p[N + i]), zi = f32_of_f64_rn(p[2 * N + i]);
+    const float xj = f32_of_f64_rn(p[j]), yj = f32_of_f64_rn(p[N + j]), zj = f32_of_f64_rn(p[2 * N + j]);
+    const float m = kM * (fmaxf(fabsf(xi), fmaxf(fabsf(yi), fabsf(zi))) +
+                          fmaxf(fabsf(xj), fmaxf(fabsf(yj), fabsf(zj))));
+    const float dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    const float to = fmaf(Rf, kUp, m);
+    if (r2 >= to * to * kUp) return 0;                   // surely outside
+    const float ti = fmaf(Rf, kDn, -m);
+    if (ti > 0.0f && r2 < ti * ti * kDn) return 1;       // surely inside
+    return 2;                                            // exact test
+}
+
+__global__ void detect_kernel(const uint2 *in, const unsigned long long *nin_dev, long long nin_host,
+                              int n, const double *pre, const double *post, const double *rc2,
+                              uint2 *out, unsigned long long cap, unsigned long long *count) {
+    __shared__ int warp_sums[32];
+    __shared__ unsigned long long base;
+    const long long nin = nin_dev ? (long long)*nin_dev : nin_host;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool enc = false;
+    uint2 pr = make_uint2(0, 0);
+    if (k < nin) {
+        pr = in[k];
+        const int i = (int)pr.x, j = (int)pr.y;
+        const size_t N = (size_t)n;
+        const double lim = fmax(rc2[i], rc2[j]);
+        const float Rf = sqrtf(f32_of_f64_rn(lim));
+        const int s0 = detect_state(pre, N, i, j, Rf);
+        const int s1 = s0 == 1 ? 1 : detect_state(post, N, i, j, Rf);
+        enc = s0 == 1 || s1 == 1;
+        if (!enc && s0 == 2)
+            enc = dist2_rn(pre[j] - pre[i], pre[N + j] - pre[N + i], pre[2 * N + j] - pre[2 * N + i]) < lim;
+        if (!enc && s1 == 2)
+            enc = dist2_rn(post[j] - post[i], post[N + j] - post[N + i], post[2 * N + j] - post[2 * N + i]) < lim;
+    }
+    int total = 0;
+    const int pos = block_exclusive_scan(enc ? 1 : 0, warp_sums, total);
+    if (total == 0) return;                               // uniform across the block
+    if (threadIdx.x == 0) base = atomicAdd(count, (unsigned long long)total);
+    __syncthreads();
+    if (enc) {
+        const unsigned long long idx = base + (unsigned long long)pos;
+        if (idx < cap) out[idx] = pr;
+    }
 }
 
 __global__ void __launch_bounds__(kScanThreads)

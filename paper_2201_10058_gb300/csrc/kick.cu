@@ -81,18 +81,6 @@ __device__ __forceinline__ double f64_of_f32_any(float f) {
     const unsigned lo = (mag >= 0x00800000u) ? (mag << 29) : 0u;
     return __hiloint2double((int)hi, (int)lo);
 }
-// Float nearest (ties away from zero) to a double of magnitude in
-// [2^-126, 2^128), any sign; smaller magnitudes give a signed zero.  Integer
-// operations only.
-__device__ __forceinline__ float f32_of_f64_rn(double v) {
-    const unsigned hi = (unsigned)__double2hiint(v);
-    const unsigned lo = (unsigned)__double2loint(v);
-    const unsigned mag = hi & 0x7fffffffu, sgn = hi & 0x80000000u;
-    const unsigned fb = (mag >= 0x38100000u)
-                            ? (sgn | ((((mag - 0x38000000u) << 3) | (lo >> 29)) + ((lo >> 28) & 1u)))
-                            : sgn;
-    return __uint_as_float(fb);
-}
 
 // v = hi + lo exactly up to 2^-47 |v|: hi is v with the mantissa truncated
 // to float precision, lo the 29 discarded mantissa bits rounded to a float.
@@ -276,32 +264,59 @@ kick_kernel(KickArgs A)
 //   m_ij = sqrt(3) 2^-23 (max|x_i| + max|x_j|)   plus relative rounding,
 // so r_f^2 >= ((1 + 2^-20) P + m_ij)^2 (1 + 2^-20) is surely outside and
 // r_f^2 < ((1 - 2^-20) P - m_ij)^2 (1 - 2^-20) surely inside (P = f_pc rc_ij
-// in FP32); only the band between takes the exact test.  Candidates are
-// appended with one atomic per warp (ballot + popc).
+// in FP32); only the band between takes the exact test.  Candidates collect
+// in a per-warp shared-memory buffer and go to the global list in batches.
 constexpr int kPcThreads = 128;
+constexpr int kPcI = 4;                         // targets i per thread
 constexpr int kPcTile = 512;
+
+constexpr int kPcWarpBuf = 256;                  // per-warp candidate buffer (shared memory)
+
+// Appends the warp's pending candidates to the global list: one atomic per
+// flush reserves the space (a single global counter serialises on its L2
+// slice, so it is touched about once per hundred candidates).
+__device__ __forceinline__ void precheck_flush(const KickArgs &A, const uint2 *buf, unsigned &cnt,
+                                               unsigned lane) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0 && cnt) base = atomicAdd(A.cand_count, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (unsigned t = lane; t < cnt; t += 32) {
+        const unsigned long long idx = base + t;
+        if (idx < A.cand_cap) A.cand[idx] = buf[t];
+    }
+    __syncwarp();
+    cnt = 0;
+}
 
 __global__ void __launch_bounds__(kPcThreads)
 precheck_kernel(KickArgs A, double f_pc)
 {
-    __shared__ float sxf[kPcTile], syf[kPcTile], szf[kPcTile], sP[kPcTile], sM[kPcTile];
+    __shared__ float4 sj[kPcTile];                   // x, y, z, P = f_pc rc (floats)
+    __shared__ float sM[kPcTile];
+    __shared__ uint2 wbuf[kPcThreads / 32][kPcWarpBuf];
     const int n = A.n;
-    const int i0 = blockIdx.x * kPcThreads;
+    const int i0 = blockIdx.x * (kPcThreads * kPcI);
     const int jbeg = max(blockIdx.y * A.chunk, i0 + 1);
     const int jend = min(n, blockIdx.y * A.chunk + A.chunk);
     if (jbeg >= jend) return;                            // block below the diagonal
-    const int i = i0 + threadIdx.x;
-    const bool valid = i < n;
     const unsigned lane = threadIdx.x & 31u;
+    uint2 *buf = wbuf[threadIdx.x >> 5];
+    unsigned pend = 0;                                   // candidates in buf (warp-uniform)
     constexpr float kM = 1.7320509f * 1.1920929e-07f;    // sqrt(3) 2^-23
-    float xf = 0.0f, yf = 0.0f, zf = 0.0f, Pi = 0.0f, Mi = 0.0f;
-    double xi = 0.0, yi = 0.0, zi = 0.0, pc2i = 0.0;
-    if (valid) {
-        xi = A.x[i]; yi = A.y[i]; zi = A.z[i];
-        xf = f32_of_f64_rn(xi); yf = f32_of_f64_rn(yi); zf = f32_of_f64_rn(zi);
-        Pi = (float)f_pc * f32_of_f64_rn(A.rc[i]);
-        Mi = kM * fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf)));
-        pc2i = A.pc2[i];
+    constexpr float kUp = 1.0f + 9.5367432e-07f, kDn = 1.0f - 9.5367432e-07f;   // 1 +- 2^-20
+    float xf[kPcI], yf[kPcI], zf[kPcI], Pi[kPcI], Mi[kPcI];
+    int ii[kPcI];
+#pragma unroll
+    for (int r = 0; r < kPcI; r++) {
+        const int i = i0 + r * kPcThreads + threadIdx.x;
+        ii[r] = i;
+        xf[r] = yf[r] = zf[r] = 3.0e38f; Pi[r] = 0.0f; Mi[r] = 0.0f;
+        if (i < n) {
+            xf[r] = f32_of_f64_rn(A.x[i]); yf[r] = f32_of_f64_rn(A.y[i]); zf[r] = f32_of_f64_rn(A.z[i]);
+            Pi[r] = (float)f_pc * f32_of_f64_rn(A.rc[i]);
+            Mi[r] = kM * fmaxf(fabsf(xf[r]), fmaxf(fabsf(yf[r]), fabsf(zf[r])));
+        }
     }
     for (int jt = jbeg; jt < jend; jt += kPcTile) {
         const int cnt = min(kPcTile, jend - jt);
@@ -309,38 +324,48 @@ precheck_kernel(KickArgs A, double f_pc)
         for (int k = threadIdx.x; k < cnt; k += kPcThreads) {
             const int j = jt + k;
             const float x = f32_of_f64_rn(A.x[j]), y = f32_of_f64_rn(A.y[j]), z = f32_of_f64_rn(A.z[j]);
-            sxf[k] = x; syf[k] = y; szf[k] = z;
-            sP[k] = (float)f_pc * f32_of_f64_rn(A.rc[j]);
+            sj[k] = make_float4(x, y, z, (float)f_pc * f32_of_f64_rn(A.rc[j]));
             sM[k] = kM * fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)));
         }
         __syncthreads();
         for (int k = 0; k < cnt; k++) {
             const int j = jt + k;
-            const float dx = sxf[k] - xf, dy = syf[k] - yf, dz = szf[k] - zf;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const float P = fmaxf(Pi, sP[k]), m = Mi + sM[k];
-            const float to = fmaf(P, 1.0f + 9.5367432e-07f, m);
-            bool emit = false;
-            if (valid && j > i && r2 < to * to * (1.0f + 9.5367432e-07f)) {
-                const float ti = fmaf(P, 1.0f - 9.5367432e-07f, -m);
-                if (ti > 0.0f && r2 < ti * ti * (1.0f - 9.5367432e-07f))
-                    emit = true;
-                else
-                    emit = dist2_rn(A.x[j] - xi, A.y[j] - yi, A.z[j] - zi) < fmax(pc2i, A.pc2[j]);
+            const float4 q = sj[k];
+            const float Mj = sM[k];
+            bool maybe[kPcI];
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < kPcI; r++) {
+                const float dx = q.x - xf[r], dy = q.y - yf[r], dz = q.z - zf[r];
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const float to = fmaf(fmaxf(Pi[r], q.w), kUp, Mi[r] + Mj);
+                maybe[r] = (j > ii[r]) && (r2 < to * to * kUp);
+                any |= maybe[r];
             }
-            const unsigned ball = __ballot_sync(0xffffffffu, emit);
-            if (ball) {
-                const int leader = __ffs(ball) - 1;
-                unsigned long long base = 0;
-                if ((int)lane == leader) base = atomicAdd(A.cand_count, (unsigned long long)__popc(ball));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (emit) {
-                    const unsigned long long idx = base + __popc(ball & ((1u << lane) - 1u));
-                    if (idx < A.cand_cap) A.cand[idx] = make_uint2((unsigned)i, (unsigned)j);
+            if (!__any_sync(0xffffffffu, any)) continue;
+#pragma unroll
+            for (int r = 0; r < kPcI; r++) {
+                bool emit = false;
+                if (maybe[r]) {
+                    const float dx = q.x - xf[r], dy = q.y - yf[r], dz = q.z - zf[r];
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    const float ti = fmaf(fmaxf(Pi[r], q.w), kDn, -(Mi[r] + Mj));
+                    if (ti > 0.0f && r2 < ti * ti * kDn) {
+                        emit = true;
+                    } else {
+                        const int i = ii[r];
+                        emit = dist2_rn(A.x[j] - A.x[i], A.y[j] - A.y[i], A.z[j] - A.z[i]) <
+                               fmax(A.pc2[i], A.pc2[j]);
+                    }
                 }
+                const unsigned ball = __ballot_sync(0xffffffffu, emit);
+                if (emit) buf[pend + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)ii[r], (unsigned)j);
+                pend += __popc(ball);
             }
+            if (pend > kPcWarpBuf - 32 * kPcI) precheck_flush(A, buf, pend, lane);
         }
     }
+    precheck_flush(A, buf, pend, lane);
 }
 
 // Folds the chunk partials in chunk order (TwoSum), scales by G and applies the
@@ -419,7 +444,7 @@ cudaError_t launch_precheck_only(genga_system *s) {
     if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
     KickArgs A = make_args(s, true);
     // (i-tile x j-chunk) grid like the kick; blocks wholly below the diagonal return at once
-    dim3 grid((n + kPcThreads - 1) / kPcThreads, s->kick_nchunk);
+    dim3 grid((n + kPcThreads * kPcI - 1) / (kPcThreads * kPcI), s->kick_nchunk);
     GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->cand_count, 0, sizeof(unsigned long long), s->stream));
     precheck_kernel<<<grid, kPcThreads, 0, s->stream>>>(A, s->p.f_pc); ++s->launches;
     return cudaGetLastError();
