@@ -385,6 +385,7 @@ bs_cols_kernel(BsArgs A) {
     }
 }
 
+
 }  // namespace
 
 cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned counts[kBuckets]) {
