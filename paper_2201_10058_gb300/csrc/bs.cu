@@ -157,6 +157,14 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
         // ascending rank order (m_q t for q > a, -m_q t for q < a): exactly
         // antisymmetric pair forces
         const int a = tid % M;
+        // own star term first: an independent dependency chain the compiler can
+        // interleave with the first pair's (small-group BS is latency-bound)
+        double sst = 0.0;
+        if (active) {
+            const double r2s = fma(z[2], z[2], fma(z[1], z[1], z[0] * z[0]));
+            const double ys = rsqrt_newton(r2s);
+            sst = -A.mu * (ys * ys * ys);
+        }
         // the column's pairs round-robin over its M threads (short chains)
         for (int pi = a; pi < S.npairs; pi += M) {
             const int pa = S.pa[pi], pq = S.pq[pi];
@@ -174,9 +182,6 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
         }
         __syncthreads();
         if (!active) { f[3] = f[4] = f[5] = 0.0; return; }
-        const double r2s = fma(z[2], z[2], fma(z[1], z[1], z[0] * z[0]));
-        const double ys = rsqrt_newton(r2s);
-        const double sst = -A.mu * (ys * ys * ys);
         double px = 0.0, py = 0.0, pz = 0.0;
         unsigned mm = mask;
         while (mm) {

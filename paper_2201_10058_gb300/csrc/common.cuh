@@ -350,14 +350,14 @@ __device__ __forceinline__ float f32_of_f64_rn(double v) {
     return __uint_as_float(fb);
 }
 __device__ __forceinline__ double rsqrt_newton(double x) {
-    double y = f64_of_f32(rsqrtf(f32_of_f64_trunc(x)));
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const double t = x * y;
-        const double e = fma(-t, y, 1.0);
-        y = fma(half_of(y), e, y);
-    }
-    return y;
+    // one residual e = 1 - x y0^2 of the ~2^-22 seed and the series
+    // x^-1/2 = y0 (1 - e)^-1/2 = y0 (1 + e/2 + 3 e^2/8 + O(e^3)): a chain of 5
+    // dependent FP64 operations (two Newton steps take 6), error ~2^-64 + rounding
+    const double y0 = f64_of_f32(rsqrtf(f32_of_f64_trunc(x)));
+    const double t = x * y0;
+    const double e = fma(-t, y0, 1.0);
+    const double p = fma(0.375, e, 0.5);
+    return fma(y0, e * p, y0);
 }
 __device__ __forceinline__ double rcp_newton(double d) {
     float s;
