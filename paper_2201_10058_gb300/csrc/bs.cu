@@ -237,6 +237,37 @@ __device__ __forceinline__ double cols_block_max(double v, ColsShared<M> &S) {
     return r;
 }
 
+// Row k of the Neville table in h^2 (n_k = 2(k+1)), in place in T:
+// T_k0 = cur, T_kj = T_k,j-1 + (T_k,j-1 - T_k-1,j-1) (n_k-j)^2 / (j (2k+2-j)) with the
+// coefficients as exact compile-time doubles; returns T_kk and T_k,k-1.
+template <int K>
+__device__ __forceinline__ void neville_row_k(double (&T)[8], double cur, double &diag, double &prevdiag) {
+    double prev = T[0];
+    T[0] = cur;
+#pragma unroll
+    for (int j = 1; j <= K; j++) {
+        const double coef = (double)((K - j + 1) * (K - j + 1)) / (double)(j * (2 * K + 2 - j));
+        const double nxt = fma(cur - prev, coef, cur);
+        prev = T[j];
+        T[j] = nxt;
+        cur = nxt;
+    }
+    diag = T[K];
+    prevdiag = K >= 1 ? T[K >= 1 ? K - 1 : 0] : 0.0;
+}
+__device__ __forceinline__ void neville_row(int k, double (&T)[8], double cur, double &diag, double &prevdiag) {
+    switch (k) {
+    case 0: neville_row_k<0>(T, cur, diag, prevdiag); break;
+    case 1: neville_row_k<1>(T, cur, diag, prevdiag); break;
+    case 2: neville_row_k<2>(T, cur, diag, prevdiag); break;
+    case 3: neville_row_k<3>(T, cur, diag, prevdiag); break;
+    case 4: neville_row_k<4>(T, cur, diag, prevdiag); break;
+    case 5: neville_row_k<5>(T, cur, diag, prevdiag); break;
+    case 6: neville_row_k<6>(T, cur, diag, prevdiag); break;
+    default: neville_row_k<7>(T, cur, diag, prevdiag); break;
+    }
+}
+
 template <int M>
 __global__ void __launch_bounds__(8 * M)
 bs_cols_kernel(BsArgs A) {
@@ -313,9 +344,16 @@ bs_cols_kernel(BsArgs A) {
         cols_deriv<M>(A, S, tid, col, active, pmask, irc_self, y, f0);
         if (col == 0)
             for (int c = 0; c < 6; c++) { S.y[c][a] = y[c]; S.f0[c][a] = f0[c]; }
-        // all 8 columns at once: column col takes nk midpoint sub-steps of H/nk
+        // all 8 columns at once: column col takes nk midpoint sub-steps of H/nk.
+        // Column k is complete after sub-step 2(k+1); its Neville row is built at
+        // once (per component c = col < 6 and member a) and the attempt stops at
+        // the first column k >= 1 under tolerance -- the columns beyond it are
+        // never needed, so they are not computed to the end.
         const double h = H / nk;
         for (int c = 0; c < 6; c++) { zm[c] = y[c]; zn[c] = fma(h, f0[c], y[c]); }
+        double T[8];
+        double sc = 1.0, diag = 0.0;
+        int kconv = -1;
         for (int it = 1; it <= 16; it++) {
             cols_deriv<M>(A, S, tid, col, active, pmask, irc_self, zn, fz);
             if (it < nk) {
@@ -327,46 +365,20 @@ bs_cols_kernel(BsArgs A) {
             } else if (it == nk) {
                 for (int c = 0; c < 6; c++) S.yk[col][c][a] = 0.5 * (zn[c] + zm[c] + h * fz[c]);
             }
-        }
-        __syncthreads();
-        // Neville per (component c = col < 6, member a), columns in order
-        double err_k[8];
-        double diag[8];
-        for (int k = 0; k < 8; k++) err_k[k] = 0.0;
-        if (col < 6 && active) {
-            const int c = col;
-            const double sc = fabs(S.y[c][a]) + fabs(H * S.f0[c][a]) + 1e-300;
-            double T[8];
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                double cur = S.yk[k][c][a];
-                double prev = T[0];
-                T[0] = cur;
-#pragma unroll
-                for (int j = 1; j <= k; j++) {
-                    const double coef = (double)((k - j + 1) * (k - j + 1)) / (double)(j * (2 * k + 2 - j));
-                    const double nxt = fma(cur - prev, coef, cur);
-                    prev = T[j];
-                    T[j] = nxt;
-                    cur = nxt;
-                }
-                diag[k] = T[k];
-                if (k >= 1) err_k[k] = fabs(T[k] - T[k - 1]) / sc;
+            if (it & 1) continue;
+            const int k = it / 2 - 1;                    // column just completed
+            __syncthreads();
+            double e = 0.0;
+            if (col < 6 && active) {
+                if (k == 0) sc = fabs(S.y[col][a]) + fabs(H * S.f0[col][a]) + 1e-300;
+                double prevdiag = 0.0;
+                neville_row(k, T, S.yk[k][col][a], diag, prevdiag);
+                if (k >= 1) e = fabs(diag - prevdiag) / sc;
             }
-        }
-        int kconv = -1;
-#pragma unroll
-        for (int k = 1; k < 8; k++) {
-            const double e = cols_block_max<M>(err_k[k], S);
-            if (kconv < 0 && e <= A.tol) kconv = k;
+            if (k >= 1 && cols_block_max<M>(e, S) <= A.tol) { kconv = k; break; }
         }
         if (kconv >= 0) {
-            if (col < 6 && active) {
-                double v = diag[1];
-#pragma unroll
-                for (int k = 2; k < 8; k++) if (k == kconv) v = diag[k];
-                S.ynew[col][a] = v;
-            }
+            if (col < 6 && active) S.ynew[col][a] = diag;
             __syncthreads();
             if (active) for (int c = 0; c < 6; c++) y[c] = S.ynew[c][a];
             t += H;
