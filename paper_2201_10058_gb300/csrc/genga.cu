@@ -198,7 +198,8 @@ int kick(genga_system *s, double dt_half, bool precheck, double *acc_out) {
     return GENGA_OK;
 }
 
-// Candidate count after a pre-check kick; regrows and recomputes on overflow.
+// Candidate count after a pre-check kick; regrows and recomputes on overflow
+// (the positions must still be those of the pre-check).
 int settle_candidates(genga_system *s, int64_t *ncand) {
     unsigned long long c = 0;
     TRY(read_dev(s, &c, &s->ctr->cand_count));
@@ -262,10 +263,12 @@ int one_step(genga_system *s) {
     const int L = levels_of(s->p);
     CU(launch_rcrit(s, 0, dt, nullptr, n));
     TRY(kick(s, 0.5 * dt, true, nullptr));
-    CU(launch_hc(s, 0.5 * dt));
-    CU(launch_drift(s, 0, dt, nullptr, n));
+    // the candidate count before HC and the drift move the bodies: a list
+    // that overflowed is recomputed from the positions the pre-check saw
     int64_t ncand = 0;
     TRY(settle_candidates(s, &ncand));
+    CU(launch_hc(s, 0.5 * dt));
+    CU(launch_drift(s, 0, dt, nullptr, n));
     s->stats.n_candidates += ncand;
     TRY(early_errors(s));
     s->npairs_host[0] = 0;

@@ -10,6 +10,8 @@ oracle on the same inputs.  Tolerances:
     in the encounter-free control after 100 steps; with encounters, 100 steps agree
     to within 3x the oracle's own spread under a one-ulp input perturbation.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -159,6 +161,21 @@ def test_candidate_list_grows_on_overflow(g):
     s.set_rcrit(rc)
     s.kick(0.5 * wl.dt, precheck=True)
     np.testing.assert_array_equal(s.candidates(), O.precheck(wl.x, rc, wl.f_pc))
+
+
+def test_step_candidate_overflow_uses_step_start_positions(g):
+    """Inside a whole step the overflowed list is recomputed before HC and the
+    drift move the bodies: candidates, pairs and positions as without overflow."""
+    wl = config_workload(0)
+    s, pos, vel, mass = _system(g, wl, 0, cand_capacity=16)
+    s.step(1)
+    st = s.stats()
+    xr, vr, status, ost = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=8), 1)
+    assert status == 0 and ost["n_candidates"] > 16
+    assert st["n_candidates"] == ost["n_candidates"]
+    assert st["n_pairs"][0] == ost["n_pairs"][0]
+    err = _rel_pos_err(_host(pos), xr)
+    assert err.max() <= 1e-12, err.max()
 
 
 # ---------------------------------------------------------------- Eq. Hc and Eq. Ha Kepler drift
@@ -375,6 +392,31 @@ def test_levels_step_matches_oracle(g):
     assert st["n_pairs"][1] > 0
     err = _rel_pos_err(_host(pos), xr)
     assert err.max() <= 1e-12, err.max()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_bench_disk_full_step_matches_oracle(g, precision, tol):
+    """The bench workload at full size (N = 65,540, two levels x 10 sub-steps), one
+    whole step in the launch configuration bench.py times, against one oracle step
+    of the same disk: every body's position, and the encounter statistics."""
+    wl = config_workload(2)
+    s, pos, vel, mass = _system(g, wl, precision)
+    s.step(1)
+    st = s.stats()
+    xr, vr, status, ost = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=os.cpu_count() or 8), 1)
+    assert status == 0
+    # candidates and level-0 pairs: exact FP64 decisions on identical inputs
+    assert st["n_candidates"] == ost["n_candidates"] > 0
+    assert st["n_pairs"][0] == ost["n_pairs"][0] > 0
+    # level-1 pairs follow the level-1 sub-steps' states; a decision within
+    # rounding of rc may differ (none expected, a few allowed)
+    assert abs(st["n_pairs"][1] - ost["n_pairs"][1]) <= 2
+    err = _rel_pos_err(_host(pos), xr)
+    verr = np.linalg.norm(_host(vel) - vr, axis=1) / np.linalg.norm(vr, axis=1)
+    numerics_log.record(f"1 step disk65540 (bench config) precision={precision}", "max |dx|/|x|",
+                        err.max(), tol)
+    assert err.max() <= tol, err.max()
+    assert verr.max() <= 100 * tol, verr.max()
 
 
 def test_energy_matches_oracle(g):
