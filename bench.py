@@ -1,6 +1,6 @@
 #!/usr/bin/env python
 """Benchmark: changeover-kick pair-interactions/s and steps/s of the hybrid
-symplectic step (Appendix A with the two-level changeover of Sec. 4.3) on the
+symplectic step (Appendix A with the two-level changeover of Sec. 6.3) on the
 large planetesimal disk: N = 65,536 equal-mass planetesimals (0.5-4 AU, 5 Earth
 masses, Sigma ~ a^-1.5) plus 4 embryos of 0.1 Earth masses, dt = 6.0875 d,
 2 symplectic levels x 10 sub-steps, FP64 and mixed-precision kick.

@@ -58,7 +58,7 @@ typedef struct genga_params {
     double n2;         /* Eq. rcrit: velocity factor (paper: 0.4) */
     double f_pc;       /* pre-check factor: candidates have r_ij < f_pc * rc_ij (default 4) */
     double bs_tol;     /* Bulirsch-Stoer relative tolerance (default 1e-15) */
-    int32_t slevels;   /* symplectic levels, Sec. 4.3 / Appendix A (1 = original method) */
+    int32_t slevels;   /* symplectic levels, Sec. 6.3 / Appendix A (1 = original method) */
     int32_t substeps;  /* sub-steps per level (time-step reduction factor per level) */
     int32_t precision; /* GENGA_FP64 or GENGA_MIXED for the all-pairs kick */
     int32_t kepler_max_iter; /* Newton iteration limit of the Kepler solve (default 50) */
@@ -119,7 +119,7 @@ int genga_set_rcrit(genga_system_t *sys, const double *rc_host);
 
 /* Kick of Eq. Hb (Appendix A "Kick(dt/2)"): for every body
  *     v_i += dt_half * G * sum_{j != i} m_j K(r_ij; rc_ij) (x_j - x_i) / r_ij^3
- * with the changeover function K of Chambers (1999), Eq. 10 (Sec. 4.3 fn.),
+ * with the changeover function K of Chambers (1999), Eq. 10 (Sec. 6.3 fn.),
  * rc_ij = max(rc_i, rc_j) from genga_rcrit, in the arithmetic selected by
  * params.precision.  If precheck != 0 a pass before the kick records the
  * close-encounter candidates at the same positions (i < j with
@@ -146,7 +146,7 @@ int genga_build_encounters(genga_system_t *sys, int64_t *n_pairs, int64_t *n_gro
                            int64_t *max_group);
 
 /* Appendix A "Bulirsch-Stoer(dt)": restores every member of the level-0 groups
- * from the pre-drift state and integrates each group over dt (Sec. 4.1) with
+ * from the pre-drift state and integrates each group over dt (Sec. 6.1) with
  * the pair forces scaled by 1 - K.  Synchronises.                           */
 int genga_bs(genga_system_t *sys, double dt);
 
@@ -266,7 +266,7 @@ int genga_ensemble_step(genga_ensemble_t *ens, int64_t nsteps);
  * or 128) and resident CTAs per SM (1..8).                                   */
 int genga_ensemble_set_tile(genga_ensemble_t *ens, int threads, int ctas_per_sm);
 
-/* Self-tuning (Sec. 5.7's kernel-parameter search): times trial_steps with
+/* Self-tuning (Sec. 8.3's kernel-parameter search): times trial_steps with
  * each tile shape from the same saved state, restores the state and keeps the
  * fastest.  threads_out / ctas_out (may be NULL) receive the choice.         */
 int genga_ensemble_autotune(genga_ensemble_t *ens, int64_t trial_steps, int *threads_out,

@@ -17,7 +17,7 @@
  *  R1  Hill radius in Eq. rcrit: R_H,i = |x_i| (m_i/(3 m_star))^(1/3).
  *  R2  v_i in Eq. rcrit is the stored (barycentric) speed.
  *  R3  Pair critical radius rc_ij = max(rc_i, rc_j).
- *  R4  Changeover function K (Sec. 4.2, footnote on Chambers 1999 Eq. 10):
+ *  R4  Changeover function K (Sec. 6.3, footnote on Chambers 1999 Eq. 10):
  *      y = (r/rc - 0.1)/0.9 clamped to [0,1], K = y^2 / (2y^2 - 2y + 1).
  *  R5  Force scaling: the kick applies K times the Newtonian pair force and the
  *      close-encounter part applies (1-K) times it (no dK/dr term).
@@ -29,8 +29,8 @@
  *      smallest member index; members ascending (Serial Grouping, App. B).
  *  R9  Bulirsch-Stoer: modified midpoint with n = 2,4,...,16, polynomial
  *      extrapolation in h^2; pair forces summed over the group's encounter pairs
- *      (the partner lists of the BS-A kernel, Sec. 4.1); step halving on failure.
- *  R10 Higher levels (Sec. 4.3, Appendix A): level bodies restart from the
+ *      (the partner lists of the BS-A kernel, Sec. 6.1); step halving on failure.
+ *  R10 Higher levels (Sec. 6.3, Appendix A): level bodies restart from the
  *      pre-drift state of the enclosing level; level-l kicks use the factor
  *      prod_{k<l}(1-K_k) K_l over the enclosing level's encounter pairs; BS uses
  *      prod_{k<=l}(1-K_k).
@@ -489,7 +489,7 @@ static int bs_integrate(const bs_group *g, double *y, double dt, double tol, int
 }
 
 /* ------------------------------------------------------------------------- */
-/* Level machinery (Sec. 4.3, Appendix A).                                    */
+/* Level machinery (Sec. 6.3, Appendix A).                                    */
 typedef struct step_ctx {
     int64_t n;
     double *x, *v;

@@ -1,6 +1,6 @@
-// bs.cu -- Bulirsch-Stoer integration of close-encounter groups (Sec. 4.1,
+// bs.cu -- Bulirsch-Stoer integration of close-encounter groups (Sec. 6.1,
 // Appendix A "Bulirsch-Stoer(dt)") and the level kick KickS of the
-// higher-level changeover scheme (Sec. 4.3, Appendix A).
+// higher-level changeover scheme (Sec. 6.3, Appendix A).
 //
 // BS for groups of at most kBlockGroupMax (32) members: one CTA per group with
 // the 8 extrapolation columns advanced at once (bs_cols_kernel below; larger
@@ -9,7 +9,7 @@
 //     dx/dt = v,   dv/dt = -mu x/|x|^3 + G sum_{partners j} m_j W_ij (x_j - x)/r^3,
 //     W_ij = prod_{k=0..level} (1 - K(r_ij; rc_k,ij)),
 // with partners taken from the ascending partner list of the level's
-// encounter pairs (the BS-A partner-list scheme of Sec. 4.1; the sum order is
+// encounter pairs (the BS-A partner-list scheme of Sec. 6.1; the sum order is
 // fixed, so results do not depend on member layout).  Modified midpoint with
 // n = 2, 4, ..., 16 and polynomial extrapolation in h^2 (Neville); error =
 // max over members and components of |T_kk - T_k,k-1| / scale with

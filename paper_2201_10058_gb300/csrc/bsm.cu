@@ -1,6 +1,6 @@
 // bsm.cu -- Bulirsch-Stoer for close-encounter groups of more than
 // kBlockGroupMax members, spread over the whole GPU (the role of the paper's
-// BS-M, Sec. 4.1), with every such group of the current grouping advanced
+// BS-M, Sec. 6.1), with every such group of the current grouping advanced
 // together by one persistent cooperative kernel.
 //
 // One round is one attempt of every still-running group, at its own step H,

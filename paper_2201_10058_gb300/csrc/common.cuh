@@ -139,7 +139,7 @@ namespace genga {
 // ---------------------------------------------------------------------------
 // Device helpers.
 
-// Changeover function of Chambers (1999) Eq. 10 as used in Sec. 4.3:
+// Changeover function of Chambers (1999) Eq. 10 as used in Sec. 6.3:
 // y = (r/rc - 0.1)/0.9 clamped to [0,1], K = y^2/(2y^2 - 2y + 1).  Written with
 // explicit round-to-nearest operations (no contraction).
 __device__ __forceinline__ double changeover(double r, double rc) {

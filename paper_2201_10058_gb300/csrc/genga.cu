@@ -4,7 +4,7 @@
 //   detection; grouping + Bulirsch-Stoer(dt)   (or SEnc for slevels > 1);
 //   HC(dt/2); Kick(dt/2)
 // with the SEnc recursion of Appendix A for the higher-level changeover
-// scheme (Sec. 4.3).  Every arithmetic step runs in the kernels of kick.cu,
+// scheme (Sec. 6.3).  Every arithmetic step runs in the kernels of kick.cu,
 // particle.cu, encounter.cu and bs.cu; the host only orders launches, reads
 // pair counts to size the next launch, and grows capacities on overflow.
 #include <algorithm>

@@ -1,6 +1,6 @@
 // particle.cu -- per-body kernels of the hybrid step (Appendix A): Rcrit
 // (Eq. rcrit), HC (Eq. Hc), FG (Kepler part of Eq. Ha) with the pre-drift copy,
-// the level restore of the higher-level scheme (Sec. 4.3), and the energy /
+// the level restore of the higher-level scheme (Sec. 6.3), and the energy /
 // angular-momentum report (Eq. H).
 //
 // These kernels are memory/latency bound (a few hundred bytes per body); they

@@ -1,5 +1,5 @@
 """Close-encounter groups of more than 32 members: the batched grid-wide
-Bulirsch-Stoer driver (Sec. 4.1, the BS-M case) for the forward step and for
+Bulirsch-Stoer driver (Sec. 6.1, the BS-M case) for the forward step and for
 the adjoint's augmented backward integration, against the oracle, through the
 C ABI.
 

@@ -381,7 +381,7 @@ def test_steps_encounter_free_control(g, precision, tol):
 
 
 def test_levels_step_matches_oracle(g):
-    """Two symplectic levels with 10 sub-steps (Sec. 4.3) on a dense disk."""
+    """Two symplectic levels with 10 sub-steps (Sec. 6.3) on a dense disk."""
     wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=2, substeps=10)
     s, pos, vel, mass = _system(g, wl, 0)
     s.step(5)

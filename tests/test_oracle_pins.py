@@ -16,7 +16,7 @@ from workloads import G_GAUSS, M_EARTH, config_workload, disk, ring
 G = G_GAUSS
 
 
-# ---------------------------------------------------------------- changeover (Sec. 4.3, fn.)
+# ---------------------------------------------------------------- changeover (Sec. 6.3, fn.)
 def test_changeover_outside_band_is_exactly_0_or_1():
     rc = 0.037
     for r in [0.0, 1e-9, 0.05 * rc, 0.1 * rc]:
@@ -189,7 +189,7 @@ def test_group_brute_force_components():
 
 @pytest.mark.parametrize("n", [8, 16, 64, 128])
 def test_ring_is_one_group_with_eight_partners(n):
-    """Sec. 4.2 ring test: every body meets eight neighbours (all others for
+    """Sec. 6.2 ring test: every body meets eight neighbours (all others for
     N < 16) and the ring forms a single close-encounter group."""
     wl = ring(n)
     rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
@@ -299,7 +299,7 @@ def test_drift_iteration_limit_reports_failure():
     assert fails == 8
 
 
-# ---------------------------------------------------------------- Bulirsch-Stoer (Sec. 4.1)
+# ---------------------------------------------------------------- Bulirsch-Stoer (Sec. 6.1)
 def test_bs_pure_two_body_without_star():
     """m_star = 0 and K = 0: the group ODE is the two-body problem."""
     m = np.array([3e-6, 1e-6])
@@ -464,7 +464,7 @@ def test_step_energy_bounded_and_second_order_without_encounters():
 
 
 def test_step_levels_reduce_groups():
-    """Sec. 4.3: a second level at dt/10 shrinks the BS groups."""
+    """Sec. 6.3: a second level at dt/10 shrinks the BS groups."""
     wl = disk(1024, 0.5, 1.0, 2.0, 11, name="dense")
     p1 = O.make_params(wl, slevels=1, substeps=1, nthreads=4)
     p2 = O.make_params(wl, slevels=2, substeps=10, nthreads=4)

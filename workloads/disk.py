@@ -3,7 +3,7 @@
 Units: AU, day, solar mass.  G = k^2 with the Gaussian constant k.
 
 Disk recipe (the planetesimal disks of the paper's performance and
-higher-level-changeover tests, Sec. 4.3 and Sec. 6: N equal-mass bodies between
+higher-level-changeover tests, Sec. 6.3-6.5 and Sec. 9: N equal-mass bodies between
 a_min and a_max with surface density proportional to a^-1.5):
   * a drawn so that dN/da ~ a^-0.5:  a = (sqrt(a_min) + u (sqrt(a_max) - sqrt(a_min)))^2
   * e ~ Rayleigh(sigma_e), i ~ Rayleigh(sigma_i) [rad], Omega, omega, M ~ U[0, 2pi)
@@ -12,7 +12,7 @@ a_min and a_max with surface density proportional to a^-1.5):
   * velocities made barycentric: v_i = v_hel,i - sum_j m_j v_hel,j / (m_star + sum_j m_j)
   * physical radius from the bulk density (2 g/cm^3 by default)
 
-Ring recipe (the close-encounter performance test, Sec. 4.2): N equal masses
+Ring recipe (the close-encounter performance test, Sec. 6.2): N equal masses
 regularly spaced on a circle, on circular orbits; the critical radius is chosen
 so that every body has eight encounter partners (all others for N < 16).
 """
@@ -127,7 +127,7 @@ def disk(n: int, a_min: float, a_max: float, m_disk_earth: float, seed: int,
 
 def ring(n: int, r: float = 1.0, m_body_earth: float = 0.01, dt: float = 6.0875,
          partners: int = 8, m_star: float = 1.0) -> Workload:
-    """Ring of n equal masses on circular orbits at radius r (Sec. 4.2 test).
+    """Ring of n equal masses on circular orbits at radius r (Sec. 6.2 test).
 
     The critical radius comes from the velocity term only (n1 = 0) with n2 set
     so that rc = (partners/2 + 0.5) * chord spacing: each body then has

@@ -1,6 +1,6 @@
 """Batched ensemble of compact planetary systems (seeded).
 
-Recipe (the multi-simulation mode the paper mentions in Sec. 6/7, with the GR
+Recipe (the multi-simulation mode the paper mentions in Sec. 10 and Appendix B, with the GR
 and tidal forces of Sec. 3 and Sec. 4 switched on):
   * star mass m_star ~ U[0.1, 1] Msun; N ~ U{8, ..., 64} planets of
     m ~ U[0.5, 10] Earth masses;
