@@ -187,7 +187,7 @@ def test_group_brute_force_components():
             assert lab[i] == -1
 
 
-@pytest.mark.parametrize("n", [8, 16, 64, 128])
+@pytest.mark.parametrize("n", [8, 12, 16, 64, 128])
 def test_ring_is_one_group_with_eight_partners(n):
     """Sec. 6.2 ring test: every body meets eight neighbours (all others for
     N < 16) and the ring forms a single close-encounter group."""
@@ -195,12 +195,12 @@ def test_ring_is_one_group_with_eight_partners(n):
     rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
     cand = O.precheck(wl.x, rc, wl.f_pc)
     enc = O.detect(cand, wl.x, wl.x, rc)
-    expect = n * (n - 1) // 2 if n <= 9 else 4 * n
+    expect = n * (n - 1) // 2 if n < 16 else 4 * n
     assert len(enc) == expect
     lab = O.group(n, enc)
     assert np.all(lab == 0)
     deg = np.bincount(enc.ravel(), minlength=n)
-    assert np.all(deg == (n - 1 if n <= 9 else 8))
+    assert np.all(deg == (n - 1 if n < 16 else 8))
 
 
 # ---------------------------------------------------------------- Eq. Hc

@@ -130,8 +130,9 @@ def ring(n: int, r: float = 1.0, m_body_earth: float = 0.01, dt: float = 6.0875,
     """Ring of n equal masses on circular orbits at radius r (Sec. 6.2 test).
 
     The critical radius comes from the velocity term only (n1 = 0) with n2 set
-    so that rc = (partners/2 + 0.5) * chord spacing: each body then has
-    `partners` neighbours within rc (all others when n <= partners).
+    so that rc lies between the (partners/2)-th and the next neighbour's chord:
+    each body then has `partners` neighbours within rc (all others when
+    n < 2 partners, i.e. N < 16 for the paper's eight).
     """
     phi = 2 * np.pi * np.arange(n) / n
     x = np.stack([r * np.cos(phi), r * np.sin(phi), np.zeros(n)], axis=-1)
@@ -141,8 +142,8 @@ def ring(n: int, r: float = 1.0, m_body_earth: float = 0.01, dt: float = 6.0875,
     vb = vh - (m[:, None] * vh).sum(axis=0) / (m_star + m.sum())
     spacing = 2 * r * np.sin(np.pi / n)
     half = partners // 2
-    if n <= partners + 1:
-        rc = 2.0 * r * 1.01          # everyone sees everyone
+    if n < 2 * partners:
+        rc = 2.0 * r * 1.01          # everyone sees everyone (N < 16 for eight partners)
     else:
         # between the half-th and (half+1)-th neighbour chord lengths
         c_in = 2 * r * np.sin(np.pi * half / n)
