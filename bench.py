@@ -61,9 +61,11 @@ def parse():
     ap.add_argument("--kick-reps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e/cpu/fp64 legs (profiling runs)")
-    ap.add_argument("--workload", choices=["disk", "ensemble", "adjoint"], default="disk",
+    ap.add_argument("--workload", choices=["disk", "ensemble", "adjoint", "variants"], default="disk",
                     help="disk: the N=65,540 disk (headline); ensemble: 4096 compact systems "
-                         "with GR and tides")
+                         "with GR and tides; adjoint: the 1000-step adjoint at N=4096; "
+                         "variants: FP64 vs mixed on the N=16,384 disk (one level) and the "
+                         "N=65,540 disk at other (levels, sub-steps)")
     ap.add_argument("--ens-steps", type=int, default=1000,
                     help="integration steps per timed ensemble launch")
     ap.add_argument("--energy-run", type=int, default=0,
@@ -573,6 +575,104 @@ def run_adjoint(args) -> dict:
             "dtype": "f64", "data": "synthetic (seeded disk)"}
 
 
+def _timed_steps(genga, sysm, flush, stream, steps: int, warmup: int) -> float:
+    """Mean device time (ms) of one whole step, L2 flushed before each timed step."""
+    import torch
+    for _ in range(warmup):
+        sysm.step(1)
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sysm.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def run_variants(args) -> dict:
+    """Secondary measurements beside the headline: the N = 16,384 disk (0.5-2 AU,
+    2 Earth masses, one level) with the FP64 and the mixed kick, and the N = 65,540
+    disk of the headline at other (levels, sub-steps) choices of Sec. 6.3.  Same
+    timing rules as the headline (device events, L2 flushed between timed steps)."""
+    import torch
+
+    from paper_2201_10058_gb300 import genga
+    from workloads import config_workload, disk
+    from workloads.disk import SEED_BASE
+
+    dev = torch.device("cuda", 0)
+    genga.load()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sampler = ClockSampler(gpu_uuid(0))
+    sampler.start()
+
+    def system(wl, prec, slevels, substeps):
+        pos = torch.tensor(np.ascontiguousarray(wl.x.T), device=dev)
+        vel = torch.tensor(np.ascontiguousarray(wl.v.T), device=dev)
+        mass = torch.tensor(wl.m, device=dev)
+        p = genga.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2,
+                                 f_pc=wl.f_pc, slevels=slevels, substeps=substeps, precision=prec)
+        return genga.System(pos, vel, mass, p, stream=stream)
+
+    def kick_ms(sysm, wl, reps=5):
+        sysm.rcrit(wl.dt)
+        sysm.kick(0.0, precheck=False)
+        torch.cuda.synchronize()
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(reps):
+            sysm.kick(0.0, precheck=False)
+        k1.record(stream)
+        k1.synchronize()
+        return k0.elapsed_time(k1) / reps
+
+    out = {"metric": "secondary measurements (not the headline)", "unit": UNIT, "dtype": "f64",
+           "data": "synthetic (seeded disks)", "l2": "flushed between timed steps (256 MiB write)"}
+    wl = config_workload(1)
+    n = wl.n
+    c1 = {"workload": f"disk N={n} (0.5-2 AU, 2 M_earth), dt=6.0875 d, one level",
+          "steps": args.steps, "warmup": args.warmup}
+    for name, prec in (("fp64", genga.GENGA_FP64), ("mixed", genga.GENGA_MIXED)):
+        sysm = system(wl, prec, 1, 1)
+        ms = _timed_steps(genga, sysm, flush, stream, args.steps, args.warmup)
+        st = sysm.stats()
+        km = kick_ms(sysm, wl)
+        c1[name] = {"gpairs_per_s": round(2.0 * n * (n - 1) / (ms * 1e-3) / 1e9, 3),
+                    "ms_per_step": round(ms, 3), "steps_per_s": round(1e3 / ms, 2),
+                    "kick_ms": round(km, 3),
+                    "kick_gpairs_per_s": round(n * (n - 1) / (km * 1e-3) / 1e9, 3),
+                    "pairs_level0": st["n_pairs"][0], "max_group": st["max_group"]}
+        sysm.close()
+    c1["mixed_over_fp64"] = round(c1["fp64"]["ms_per_step"] / c1["mixed"]["ms_per_step"], 3)
+    out["disk16384"] = c1
+    wl = disk(65536, 0.5, 4.0, 5.0, SEED_BASE + 2, n_embryos=4, m_embryo_earth=0.1,
+              slevels=2, substeps=10, name="disk65536+4emb")
+    n = wl.n
+    lv = []
+    for slevels, substeps in ((1, 1), (2, 10), (3, 2), (3, 10)):
+        sysm = system(wl, genga.GENGA_MIXED, slevels, substeps)
+        ms = _timed_steps(genga, sysm, flush, stream, args.steps, args.warmup)
+        st = sysm.stats()
+        lv.append({"slevels": slevels, "substeps": substeps, "ms_per_step": round(ms, 3),
+                   "gpairs_per_s": round(2.0 * n * (n - 1) / (ms * 1e-3) / 1e9, 3),
+                   "steps_per_s": round(1e3 / ms, 3),
+                   "pairs_per_level": [st["n_pairs"][k] for k in range(slevels)],
+                   "max_group": st["max_group"], "bs_max_attempts": st["bs_max_attempts"]})
+        sysm.close()
+    out["disk65540_levels"] = {"workload": f"disk N={n} (headline disk), mixed kick",
+                               "steps": args.steps, "warmup": args.warmup, "runs": lv}
+    out["clocks"] = sampler.stop()
+    return out
+
+
 def _recording(s):
     """Host copies of a system's recorded rc history and pair lists."""
     return s.adjoint_export()
@@ -582,6 +682,9 @@ def main():
     args = parse()
     if args.workload == "adjoint" and args.impl == "ours":
         print(json.dumps(run_adjoint(args)))
+        return
+    if args.workload == "variants" and args.impl == "ours":
+        print(json.dumps(run_variants(args)))
         return
     if args.workload == "ensemble" and args.impl == "ours":
         print(json.dumps(run_ensemble(args)))

@@ -380,9 +380,11 @@ def test_steps_encounter_free_control(g, precision, tol):
     assert err.max() <= tol, err.max()
 
 
-def test_levels_step_matches_oracle(g):
-    """Two symplectic levels with 10 sub-steps (Sec. 6.3) on a dense disk."""
-    wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=2, substeps=10)
+@pytest.mark.parametrize("slevels,substeps", [(2, 10), (3, 2), (3, 10)])
+def test_levels_step_matches_oracle(g, slevels, substeps):
+    """Symplectic levels and sub-steps of Sec. 6.3 (Fig. K's two- and three-level
+    cases) on a dense disk, against the oracle's level recursion."""
+    wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=slevels, substeps=substeps)
     s, pos, vel, mass = _system(g, wl, 0)
     s.step(5)
     st = s.stats()
@@ -391,6 +393,8 @@ def test_levels_step_matches_oracle(g):
     assert st["n_pairs"][0] == ost["n_pairs"][0] > 0
     assert st["n_pairs"][1] > 0
     err = _rel_pos_err(_host(pos), xr)
+    numerics_log.record(f"5 steps dense disk2048 levels=({slevels},{substeps})", "max |dx|/|x|",
+                        err.max(), 1e-12)
     assert err.max() <= 1e-12, err.max()
 
 
