@@ -669,6 +669,13 @@ def run_variants(args) -> dict:
         sysm.close()
     out["disk65540_levels"] = {"workload": f"disk N={n} (headline disk), mixed kick",
                                "steps": args.steps, "warmup": args.warmup, "runs": lv}
+    # the self-tuner on the same candidates (one untimed and 2 timed steps each)
+    cands = [(r["slevels"], r["substeps"]) for r in lv]
+    sysm = system(wl, genga.GENGA_MIXED, 1, 1)
+    best, ms = sysm.tune_levels(cands, trial_steps=2)
+    sysm.close()
+    out["disk65540_levels"]["tuned"] = {"choice": list(cands[best]),
+                                        "trial_ms_per_step": [round(float(v), 3) for v in ms]}
     out["clocks"] = sampler.stop()
     return out
 

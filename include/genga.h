@@ -155,6 +155,21 @@ int genga_bs(genga_system_t *sys, double dt);
  * Synchronises at the end; stats of these steps via genga_get_stats.        */
 int genga_step(genga_system_t *sys, int64_t nsteps);
 
+/* Self-tuning of the level scheme (Sec. 6.3: the best number of symplectic
+ * levels and sub-steps depends on N and the GPU, so the paper recommends
+ * trying configurations before a long run): from the current state, each
+ * candidate (slevels[c], substeps[c]), c < ncand, takes one untimed step and
+ * then trial_steps timed steps (CUDA events on the system's stream), the state
+ * being restored bit for bit before each; the fastest candidate becomes the
+ * system's setting.  On return the positions, velocities and stats are those
+ * of before the call, so later steps are exactly those of a system created
+ * with the chosen setting.  best_out (may be NULL) receives the chosen index,
+ * ms_out (may be NULL, ncand doubles) each candidate's time per step.
+ * Synchronises.  Errors: EINVAL (bad candidate or counts; nothing run), and
+ * any error of a trial step (the state and the previous setting restored).  */
+int genga_tune_levels(genga_system_t *sys, const int32_t *slevels, const int32_t *substeps,
+                      int32_t ncand, int64_t trial_steps, int32_t *best_out, double *ms_out);
+
 /* genga_step from host buffers: copies pos_host/vel_host (3n doubles each,
  * same layout, ideally pinned) to the device arrays, runs nsteps, copies the
  * result back.  Synchronises.                                               */

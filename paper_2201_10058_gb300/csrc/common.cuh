@@ -51,10 +51,10 @@ struct DevCounters {
 
 // Level-independent per-body data of the critical radius (level 0 uses all).
 struct RcritArrays {
-    double *rc;    // rc_i
-    double *rc2;   // rc_i^2 (pair value: max of the two, exact)
-    double *pc2;   // (f_pc rc_i)^2 (level 0 only)
-    float *thr_rc; // conservative FP32 upper bound of rc_i^2 (level 0 only)
+    double *rc = nullptr;    // rc_i
+    double *rc2 = nullptr;   // rc_i^2 (pair value: max of the two, exact)
+    double *pc2 = nullptr;   // (f_pc rc_i)^2 (level 0 only)
+    float *thr_rc = nullptr; // conservative FP32 upper bound of rc_i^2 (level 0 only)
 };
 
 // CSR partner lists (both directions) of one pair list.

@@ -88,25 +88,36 @@ int alloc_pairs(genga_system *s, int level, int64_t cap) {
     return GENGA_OK;
 }
 
+// Every per-level array of level l; what already exists is kept (a level
+// dropped by genga_set_params and taken up again reuses its arrays).
+int alloc_level(genga_system *s, int l) {
+    const size_t n = (size_t)s->n;
+    if (!s->rcl[l].rc) {
+        CU(dalloc(&s->rcl[l].rc, n));
+        CU(cudaMemset(s->rcl[l].rc, 0, sizeof(double) * n));
+    }
+    if (!s->rcl[l].rc2) {
+        CU(dalloc(&s->rcl[l].rc2, n));
+        CU(cudaMemset(s->rcl[l].rc2, 0, sizeof(double) * n));
+    }
+    if (!s->pre_pos[l]) CU(dalloc(&s->pre_pos[l], 3 * n));
+    if (!s->pre_vel[l]) CU(dalloc(&s->pre_vel[l], 3 * n));
+    if (!s->csr[l].deg) CU(dalloc(&s->csr[l].deg, n + 1));
+    if (!s->csr[l].off) CU(dalloc(&s->csr[l].off, n + 1));
+    if (!s->csr[l].fill) CU(dalloc(&s->csr[l].fill, n + 1));
+    if (!s->bodies[l]) CU(dalloc(&s->bodies[l], n));
+    if (!s->pairs[l]) {
+        const int64_t pc = s->p.pair_capacity > 0 ? s->p.pair_capacity : std::max<int64_t>(1 << 16, 4 * (int64_t)n);
+        TRY(alloc_pairs(s, l, pc));
+    }
+    return GENGA_OK;
+}
+
 int alloc_all(genga_system *s) {
     const size_t n = (size_t)s->n;
     CU(dalloc(&s->ctr, 1));
     CU(cudaMemset(s->ctr, 0, sizeof(DevCounters)));
-    for (int l = 0; l < kMaxLevels; l++) {
-        CU(dalloc(&s->rcl[l].rc, n));
-        CU(dalloc(&s->rcl[l].rc2, n));
-        CU(cudaMemset(s->rcl[l].rc, 0, sizeof(double) * n));
-        CU(cudaMemset(s->rcl[l].rc2, 0, sizeof(double) * n));
-        CU(dalloc(&s->pre_pos[l], 3 * n));
-        CU(dalloc(&s->pre_vel[l], 3 * n));
-        CU(dalloc(&s->csr[l].deg, n + 1));
-        CU(dalloc(&s->csr[l].off, n + 1));
-        CU(dalloc(&s->csr[l].fill, n + 1));
-        CU(dalloc(&s->bodies[l], n));
-        const int64_t pc = s->p.pair_capacity > 0 ? s->p.pair_capacity : std::max<int64_t>(1 << 16, 4 * (int64_t)n);
-        TRY(alloc_pairs(s, l, pc));
-        if (l + 1 >= levels_of(s->p)) break;
-    }
+    for (int l = 0; l < levels_of(s->p); l++) TRY(alloc_level(s, l));
     CU(dalloc(&s->rcl[0].pc2, n));
     CU(dalloc(&s->rcl[0].thr_rc, n));
     for (int k = 0; k < 4; k++) {
@@ -390,19 +401,7 @@ const char *genga_last_error(const genga_system_t *s) { return s ? s->err : "nul
 int genga_set_params(genga_system_t *s, const genga_params_t *p) {
     if (!s) return GENGA_EINVAL;
     TRY(check_params(s, p));
-    if (levels_of(*p) > levels_of(s->p)) {
-        // allocate the extra levels
-        const size_t n = (size_t)s->n;
-        for (int l = levels_of(s->p); l < levels_of(*p); l++) {
-            CU(dalloc(&s->pre_pos[l], 3 * n));
-            CU(dalloc(&s->pre_vel[l], 3 * n));
-            CU(dalloc(&s->csr[l].deg, n + 1));
-            CU(dalloc(&s->csr[l].off, n + 1));
-            CU(dalloc(&s->csr[l].fill, n + 1));
-            CU(dalloc(&s->bodies[l], n));
-            TRY(alloc_pairs(s, l, s->pair_cap[0]));
-        }
-    }
+    for (int l = 0; l < levels_of(*p); l++) TRY(alloc_level(s, l));   // levels not yet held
     s->p = *p;
     return GENGA_OK;
 }
@@ -489,6 +488,78 @@ int genga_step(genga_system_t *s, int64_t nsteps) {
     }
     TRY(collect_stats(s));
     return device_errors(s);
+}
+
+int genga_tune_levels(genga_system_t *s, const int32_t *slevels, const int32_t *substeps, int32_t ncand,
+                      int64_t trial_steps, int32_t *best_out, double *ms_out) {
+    if (!s || !slevels || !substeps || ncand < 1 || trial_steps < 1) return GENGA_EINVAL;
+    const genga_params_t p0 = s->p;
+    for (int c = 0; c < ncand; c++) {
+        genga_params_t q = p0;
+        q.slevels = slevels[c];
+        q.substeps = substeps[c];
+        TRY(check_params(s, &q));
+    }
+    const size_t n3 = 3 * (size_t)s->n;
+    double *save = nullptr;
+    CU(dalloc(&save, 2 * n3));
+    const genga_stats_t st0 = s->stats;
+    const long long l0 = s->launches;
+    auto copy_state = [&](bool to_save) -> cudaError_t {
+        const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+        const size_t b = sizeof(double) * n3;
+        const cudaError_t r = to_save ? cudaMemcpyAsync(save, s->pos, b, k, s->stream)
+                                      : cudaMemcpyAsync(s->pos, save, b, k, s->stream);
+        if (r != cudaSuccess) return r;
+        return to_save ? cudaMemcpyAsync(save + n3, s->vel, b, k, s->stream)
+                       : cudaMemcpyAsync(s->vel, save + n3, b, k, s->stream);
+    };
+    cudaEvent_t a = nullptr, b = nullptr;
+    const bool saved = copy_state(true) == cudaSuccess;
+    int rc = (saved && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+                 ? GENGA_OK : fail(s, GENGA_ECUDA, "tune: set-up failed");
+    int best = 0;
+    double best_ms = 0.0;
+    for (int c = 0; c < ncand && rc == GENGA_OK; c++) {
+        genga_params_t q = p0;
+        q.slevels = slevels[c];
+        q.substeps = substeps[c];
+        rc = genga_set_params(s, &q);
+        if (rc == GENGA_OK) rc = one_step(s);                  // untimed: lists grow here
+        if (rc == GENGA_OK) rc = device_errors(s);
+        if (rc == GENGA_OK && copy_state(false) != cudaSuccess) rc = fail(s, GENGA_ECUDA, "tune: restore");
+        if (rc == GENGA_OK && cudaEventRecord(a, s->stream) != cudaSuccess) rc = fail(s, GENGA_ECUDA, "tune: event");
+        for (int64_t k = 0; k < trial_steps && rc == GENGA_OK; k++) rc = one_step(s);
+        float ms = 0.0f;
+        if (rc == GENGA_OK && (cudaEventRecord(b, s->stream) != cudaSuccess ||
+                               cudaEventSynchronize(b) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+            rc = fail(s, GENGA_ECUDA, "tune: timing");
+        if (rc == GENGA_OK) rc = device_errors(s);
+        if (rc == GENGA_OK && copy_state(false) != cudaSuccess) rc = fail(s, GENGA_ECUDA, "tune: restore");
+        if (rc != GENGA_OK) break;
+        const double per_step = (double)ms / (double)trial_steps;
+        if (ms_out) ms_out[c] = per_step;
+        if (c == 0 || per_step < best_ms) { best_ms = per_step; best = c; }
+    }
+    // the state of before the call and the chosen (or, after an error, the previous) setting
+    if (saved) copy_state(false);
+    cudaStreamSynchronize(s->stream);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    dfree(save);
+    genga_params_t q = p0;
+    if (rc == GENGA_OK) {
+        q.slevels = slevels[best];
+        q.substeps = substeps[best];
+    }
+    const int rs = genga_set_params(s, &q);
+    s->stats = st0;
+    s->launches = l0;
+    if (rc != GENGA_OK) return rc;
+    if (rs != GENGA_OK) return rs;
+    if (best_out) *best_out = best;
+    return GENGA_OK;
 }
 
 int genga_step_host(genga_system_t *s, double *pos_host, double *vel_host, int64_t nsteps) {

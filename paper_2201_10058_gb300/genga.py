@@ -29,7 +29,8 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_kick_static", "genga_adjoint_forward", "genga_adjoint_load",
             "genga_adjoint_backward", "genga_adjoint_export", "genga_ensemble_create", "genga_ensemble_destroy",
             "genga_ensemble_last_error", "genga_ensemble_step", "genga_ensemble_set_tile",
-            "genga_ensemble_autotune", "genga_ensemble_angmom", "genga_ensemble_get_stats"]
+            "genga_ensemble_autotune", "genga_ensemble_angmom", "genga_ensemble_get_stats",
+            "genga_tune_levels"]
 
 KICK_STATIC_MAX_N = 279616
 
@@ -114,6 +115,7 @@ def load(build_if_missing: bool = True):
         L.genga_bs.argtypes = [sysp, C.c_double]
         L.genga_step.argtypes = [sysp, C.c_int64]
         L.genga_step_host.argtypes = [sysp, _VP, _VP, C.c_int64]
+        L.genga_tune_levels.argtypes = [sysp, _VP, _VP, C.c_int32, C.c_int64, _P(C.c_int32), _VP]
         L.genga_energy.argtypes = [sysp, _P(C.c_double), _P(C.c_double)]
         L.genga_get_candidates.argtypes = [sysp, _VP, C.c_int64, _P(C.c_int64)]
         L.genga_get_pairs.argtypes = [sysp, C.c_int, _VP, C.c_int64, _P(C.c_int64)]
@@ -251,6 +253,19 @@ class System:
 
     def step(self, nsteps: int = 1):
         self._check(self._lib.genga_step(self._h, nsteps))
+
+    def tune_levels(self, candidates, trial_steps: int = 2):
+        """genga_tune_levels over [(slevels, substeps), ...]; returns the chosen
+        index and each candidate's time per step (ms).  The setting becomes the
+        system's (self.params follows)."""
+        lv = np.ascontiguousarray([c[0] for c in candidates], dtype=np.int32)
+        ss = np.ascontiguousarray([c[1] for c in candidates], dtype=np.int32)
+        ms = np.zeros(len(candidates), dtype=np.float64)
+        best = C.c_int32()
+        self._check(self._lib.genga_tune_levels(self._h, _np_ptr(lv), _np_ptr(ss), len(candidates),
+                                                trial_steps, C.byref(best), _np_ptr(ms)))
+        self.params.slevels, self.params.substeps = (int(v) for v in candidates[best.value])
+        return best.value, ms
 
     def step_host(self, pos_host: np.ndarray, vel_host: np.ndarray, nsteps: int = 1):
         self._check(self._lib.genga_step_host(self._h, _np_ptr(pos_host), _np_ptr(vel_host), nsteps))

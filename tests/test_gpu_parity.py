@@ -469,3 +469,46 @@ def test_nan_state_reports_bad_state(g):
     with pytest.raises(g.GengaError) as e:
         s.step(1)
     assert e.value.code == -5
+
+
+def test_set_params_adds_levels_beyond_creation(g):
+    """A system created with one level and switched to three (genga_set_params)
+    holds every array of the new levels: steps match the oracle's three-level run."""
+    wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=3, substeps=10)
+    s, pos, vel, mass = _system(g, wl, 0, slevels=1, substeps=1)
+    p = g.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc,
+                         slevels=3, substeps=10, precision=0)
+    s.set_params(p)
+    s.step(3)
+    st = s.stats()
+    xr, vr, status, ost = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=8), 3)
+    assert status == 0 and st["n_pairs"][2] > 0
+    assert st["n_pairs"][0] == ost["n_pairs"][0]
+    # sub-step pairs follow sub-step states: a decision within rounding of rc may differ
+    assert all(abs(st["n_pairs"][k] - ost["n_pairs"][k]) <= 2 for k in (1, 2))
+    assert _rel_pos_err(_host(pos), xr).max() <= 1e-12
+
+
+# ---------------------------------------------------------------- level self-tuning (Sec. 6.3)
+def test_tune_levels_restores_state_and_keeps_fastest(g):
+    """The self-tuner times each (levels, sub-steps) candidate from the same state,
+    keeps the fastest, and leaves the state bit for bit as it found it: later steps
+    equal those of a system created with the chosen setting."""
+    wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=2, substeps=10)
+    s, pos, vel, mass = _system(g, wl, 1)
+    x0, v0 = _host(pos), _host(vel)
+    cands = [(1, 1), (2, 10), (3, 2), (3, 10)]
+    best, ms = s.tune_levels(cands, trial_steps=2)
+    assert np.array_equal(_host(pos), x0) and np.array_equal(_host(vel), v0)
+    assert np.all(ms > 0) and best == int(np.argmin(ms))
+    L, S = cands[best]
+    assert (s.params.slevels, s.params.substeps) == (L, S)
+    s.step(3)
+    wl2 = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=L, substeps=S)
+    s2, pos2, vel2, _ = _system(g, wl2, 1)
+    s2.step(3)
+    assert np.array_equal(_host(pos), _host(pos2)) and np.array_equal(_host(vel), _host(vel2))
+    # an invalid candidate is refused before anything runs
+    with pytest.raises(g.GengaError):
+        s.tune_levels([(2, 10), (0, 1)])
+    assert (s.params.slevels, s.params.substeps) == (L, S)
