@@ -35,7 +35,7 @@ class OracleParams(C.Structure):
                 ("n1", C.c_double), ("n2", C.c_double), ("f_pc", C.c_double),
                 ("bs_tol", C.c_double), ("slevels", C.c_int32), ("substeps", C.c_int32),
                 ("kepler_max_iter", C.c_int32), ("bs_max_steps", C.c_int32),
-                ("nthreads", C.c_int32), ("pad", C.c_int32)]
+                ("nthreads", C.c_int32), ("tp_mode", C.c_int32), ("n_massive", C.c_int64)]
 
 
 class OracleStats(C.Structure):
@@ -67,11 +67,14 @@ def lib():
             L.orc_rcrit.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, C.c_double,
                                     C.c_double, _D]
             L.orc_accel.argtypes = [C.c_int64, _D, _D, _D, C.c_double, _D, C.c_int]
+            L.orc_accel_tp.argtypes = [C.c_int64, C.c_int64, _D, _D, _D, C.c_double, _D, C.c_int]
             L.orc_accel_rows.argtypes = [C.c_int64, _D, _D, _D, C.c_double, _I64, C.c_int64, _D,
                                          C.c_int]
             L.orc_kick.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D, C.c_int]
             L.orc_precheck.restype = C.c_int64
             L.orc_precheck.argtypes = [C.c_int64, _D, _D, C.c_double, _U32, C.c_int64]
+            L.orc_precheck_tp.restype = C.c_int64
+            L.orc_precheck_tp.argtypes = [C.c_int64, C.c_int64, _D, _D, C.c_double, _U32, C.c_int64]
             L.orc_hc.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double]
             L.orc_fg.restype = C.c_int64
             L.orc_fg.argtypes = [C.c_int64, _D, _D, C.c_double, C.c_double, C.c_int]
@@ -86,6 +89,8 @@ def lib():
                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
                                         C.POINTER(OracleStats)]
             L.orc_energy.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D, _D]
+            L.orc_energy_tp.argtypes = [C.c_int64, C.c_int64, _D, _D, _D, C.c_double, C.c_double,
+                                        _D, _D]
             L.orc_step_nn.restype = C.c_int
             L.orc_step_nn.argtypes = [C.c_int64, _D, _D, _D, C.POINTER(OracleParams),
                                       C.POINTER(OracleNN), _D, _D, _D, _D, _D, _D, C.c_int64,
@@ -128,10 +133,14 @@ def rcrit(x, v, m, m_star, dt, n1=3.0, n2=0.4) -> np.ndarray:
     return rc
 
 
-def accel(x, m, rc, G, nthreads: int = 1) -> np.ndarray:
+def accel(x, m, rc, G, nthreads: int = 1, n_massive=None) -> np.ndarray:
+    """Kick accelerations; with n_massive, bodies i >= n_massive are semi-active
+    test particles (no interaction between two of them)."""
     x, m, rc = _f64(x), _f64(m), _f64(rc)
     a = np.empty_like(x)
-    lib().orc_accel(m.shape[0], _d(x), _d(m), _d(rc), G, _d(a), nthreads)
+    n = m.shape[0]
+    nm = n if n_massive is None else int(n_massive)
+    lib().orc_accel_tp(n, nm, _d(x), _d(m), _d(rc), G, _d(a), nthreads)
     return a
 
 
@@ -151,13 +160,14 @@ def kick(x, v, m, rc, G, dt_half, nthreads: int = 1) -> np.ndarray:
     return v
 
 
-def precheck(x, rc, f_pc) -> np.ndarray:
+def precheck(x, rc, f_pc, n_massive=None) -> np.ndarray:
     x, rc = _f64(x), _f64(rc)
     n = rc.shape[0]
+    nm = n if n_massive is None else int(n_massive)
     cap = 4096
     while True:
         out = np.empty((cap, 2), dtype=np.uint32)
-        c = lib().orc_precheck(n, _d(x), _d(rc), f_pc, out.ctypes.data_as(_U32), cap)
+        c = lib().orc_precheck_tp(n, nm, _d(x), _d(rc), f_pc, out.ctypes.data_as(_U32), cap)
         if c <= cap:
             return out[:c].copy()
         cap = int(c)
@@ -197,7 +207,7 @@ def make_params(wl=None, **kw) -> OracleParams:
     p = OracleParams()
     defaults = dict(G=0.01720209895 ** 2, m_star=1.0, dt=6.0875, n1=3.0, n2=0.4, f_pc=4.0,
                     bs_tol=1e-15, slevels=1, substeps=1, kepler_max_iter=50,
-                    bs_max_steps=100000, nthreads=1)
+                    bs_max_steps=100000, nthreads=1, tp_mode=0, n_massive=0)
     if wl is not None:
         for k in ("G", "m_star", "dt", "n1", "n2", "f_pc", "slevels", "substeps"):
             defaults[k] = getattr(wl, k)
@@ -299,9 +309,11 @@ def step_frozen(x, v, m, params: OracleParams, rc, pairs, dx=None, dv=None, dm=N
     return x, v, dx, dv, int(st)
 
 
-def energy(x, v, m, m_star, G):
+def energy(x, v, m, m_star, G, n_massive=None):
     x, v, m = _f64(x), _f64(v), _f64(m)
     E = np.zeros(1)
     L = np.zeros(3)
-    lib().orc_energy(m.shape[0], _d(x), _d(v), _d(m), m_star, G, _d(E), _d(L))
+    n = m.shape[0]
+    nm = n if n_massive is None else int(n_massive)
+    lib().orc_energy_tp(n, nm, _d(x), _d(v), _d(m), m_star, G, _d(E), _d(L))
     return float(E[0]), L

@@ -36,6 +36,11 @@
  *      prod_{k<=l}(1-K_k).
  *  R11 Kepler drift with mu = G m_star (Eq. Ha), universal variables with
  *      Stumpff functions evaluated by series and argument quartering.
+ *  R24 Semi-active test particles (Sec. 8.1, TP 2): the bodies are ordered
+ *      with the large ones first; bodies i >= n_massive are test particles,
+ *      and a pair of two test particles has no interaction at all (no force,
+ *      no candidate, no encounter, no potential term); every other pair is
+ *      treated as in the fully interactive mode.
  */
 #include <math.h>
 #include <stdint.h>
@@ -59,7 +64,8 @@ typedef struct orc_params {
     int32_t kepler_max_iter;
     int32_t bs_max_steps; /* limit on BS sub-step attempts per group call */
     int32_t nthreads;  /* OpenMP threads for the O(N^2) loops (1 = serial) */
-    int32_t pad;
+    int32_t tp_mode;   /* Sec. 8.1: 0 fully interactive; 2 semi-active test particles */
+    int64_t n_massive; /* tp_mode 2: bodies i >= n_massive are test particles */
 } orc_params;
 
 /* Statistics of the last step (for tests and reports). */
@@ -119,13 +125,15 @@ static double dist2(const double *xi, const double *xj)
 
 /* ------------------------------------------------------------------------- */
 /* Eq. Hb kick acceleration of particle i:
- *   a_i = G sum_{j != i} m_j K(r_ij) (x_j - x_i) / r_ij^3, j ascending.        */
-static void accel_one(int64_t n, const double *x, const double *m, const double *rc,
+ *   a_i = G sum_{j != i} m_j K(r_ij) (x_j - x_i) / r_ij^3, j ascending;
+ * with test particles (R24) a test particle i takes only j < nm.             */
+static void accel_one(int64_t n, int64_t nm, const double *x, const double *m, const double *rc,
                       double G, int64_t i, double *ai)
 {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     const double *xi = x + 3 * i;
-    for (int64_t j = 0; j < n; j++) {
+    const int64_t jend = i >= nm ? nm : n;
+    for (int64_t j = 0; j < jend; j++) {
         if (j == i) continue;
         const double *xj = x + 3 * j;
         double dx = xj[0] - xi[0], dy = xj[1] - xi[1], dz = xj[2] - xi[2];
@@ -142,13 +150,20 @@ static void accel_one(int64_t n, const double *x, const double *m, const double 
     ai[2] = G * s2;
 }
 
-void orc_accel(int64_t n, const double *x, const double *m, const double *rc,
-               double G, double *acc, int nthreads)
+/* nm = n: fully interactive; nm < n: bodies i >= nm are test particles (R24). */
+void orc_accel_tp(int64_t n, int64_t nm, const double *x, const double *m, const double *rc,
+                  double G, double *acc, int nthreads)
 {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
-    for (int64_t i = 0; i < n; i++) accel_one(n, x, m, rc, G, i, acc + 3 * i);
+    for (int64_t i = 0; i < n; i++) accel_one(n, nm, x, m, rc, G, i, acc + 3 * i);
+}
+
+void orc_accel(int64_t n, const double *x, const double *m, const double *rc,
+               double G, double *acc, int nthreads)
+{
+    orc_accel_tp(n, n, x, m, rc, G, acc, nthreads);
 }
 
 /* Acceleration of a subset of rows (for sampled checks at large N). */
@@ -158,34 +173,48 @@ void orc_accel_rows(int64_t n, const double *x, const double *m, const double *r
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
-    for (int64_t k = 0; k < nrows; k++) accel_one(n, x, m, rc, G, rows[k], acc + 3 * k);
+    for (int64_t k = 0; k < nrows; k++) accel_one(n, n, x, m, rc, G, rows[k], acc + 3 * k);
 }
 
 /* Kick(dt/2): v_i += dt_half a_i. */
-void orc_kick(int64_t n, const double *x, const double *m, const double *rc,
-              double G, double dt_half, double *v, int nthreads)
+static void kick_tp(int64_t n, int64_t nm, const double *x, const double *m, const double *rc,
+                    double G, double dt_half, double *v, int nthreads)
 {
     double *acc = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
-    orc_accel(n, x, m, rc, G, acc, nthreads);
+    orc_accel_tp(n, nm, x, m, rc, G, acc, nthreads);
     for (int64_t i = 0; i < 3 * n; i++) v[i] += dt_half * acc[i];
     free(acc);
 }
 
+void orc_kick(int64_t n, const double *x, const double *m, const double *rc,
+              double G, double dt_half, double *v, int nthreads)
+{
+    kick_tp(n, n, x, m, rc, G, dt_half, v, nthreads);
+}
+
 /* R6 pre-check: candidates i<j with r_ij^2 < (f_pc rc_ij)^2, ascending (i,j).
  * Returns the number of candidates; writes at most cap of them.             */
-int64_t orc_precheck(int64_t n, const double *x, const double *rc, double f_pc,
-                     uint32_t *cand, int64_t cap)
+int64_t orc_precheck_tp(int64_t n, int64_t nm, const double *x, const double *rc, double f_pc,
+                        uint32_t *cand, int64_t cap)
 {
     int64_t c = 0;
-    for (int64_t i = 0; i < n; i++)
-        for (int64_t j = i + 1; j < n; j++) {
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t jend = i >= nm ? i + 1 : n;   /* no pair of two test particles (R24) */
+        for (int64_t j = i + 1; j < jend; j++) {
             double t = f_pc * pair_rc(rc, i, j);
             if (dist2(x + 3 * i, x + 3 * j) < t * t) {
                 if (c < cap) { cand[2 * c] = (uint32_t)i; cand[2 * c + 1] = (uint32_t)j; }
                 c++;
             }
         }
+    }
     return c;
+}
+
+int64_t orc_precheck(int64_t n, const double *x, const double *rc, double f_pc,
+                     uint32_t *cand, int64_t cap)
+{
+    return orc_precheck_tp(n, n, x, rc, f_pc, cand, cap);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -871,19 +900,21 @@ static int step_impl(int64_t n, double *x, double *v, const double *m, const orc
     double *xs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *vs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double dt = p->dt, mu = p->G * p->m_star;
+    /* R24: bodies i >= nm are semi-active test particles */
+    const int64_t nm = (p->tp_mode == 2 && p->n_massive >= 0 && p->n_massive < n) ? p->n_massive : n;
     for (int64_t s = 0; s < nsteps; s++) {
         orc_rcrit(n, x, v, m, p->m_star, dt, p->n1, p->n2, cx.rcl[0]);
         int64_t cap = 1024;
         uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)cap);
-        int64_t nc = orc_precheck(n, x, cx.rcl[0], p->f_pc, cand, cap);
+        int64_t nc = orc_precheck_tp(n, nm, x, cx.rcl[0], p->f_pc, cand, cap);
         if (nc > cap) {
             free(cand);
             cap = nc;
             cand = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)cap);
-            nc = orc_precheck(n, x, cx.rcl[0], p->f_pc, cand, cap);
+            nc = orc_precheck_tp(n, nm, x, cx.rcl[0], p->f_pc, cand, cap);
         }
         st->n_candidates += nc;
-        orc_kick(n, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
+        kick_tp(n, nm, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
         nn_implicit(n, x, v, m, p->G, p->m_star, nn, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
         orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
         memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
@@ -903,7 +934,7 @@ static int step_impl(int64_t n, double *x, double *v, const double *m, const orc
         }
         free(cand);
         orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
-        orc_kick(n, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
+        kick_tp(n, nm, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
         nn_implicit(n, x, v, m, p->G, p->m_star, nn, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
     }
     if (st->kepler_fail) cx.status |= 1;
@@ -1290,8 +1321,8 @@ int orc_step_frozen(int64_t n, double *x, double *v, const double *m, const orc_
 /* Total energy (Eq. H = Ha + Hb + Hc, the K terms summing to the full pair
  * potential) and angular momentum sum_i m_i x_i x v_i, in long double with
  * Kahan summation.                                                          */
-void orc_energy(int64_t n, const double *x, const double *v, const double *m, double m_star,
-                double G, double *E, double *L)
+void orc_energy_tp(int64_t n, int64_t nm, const double *x, const double *v, const double *m,
+                   double m_star, double G, double *E, double *L)
 {
     long double sum = 0.0L, comp = 0.0L;
 #define KAHAN_ADD(term) do { long double y_ = (term) - comp; long double t_ = sum + y_; \
@@ -1314,7 +1345,8 @@ void orc_energy(int64_t n, const double *x, const double *v, const double *m, do
     for (int64_t i = 0; i < n; i++) {
         const double *xi = x + 3 * i;
         long double part = 0.0L;
-        for (int64_t j = i + 1; j < n; j++) {
+        const int64_t jend = i >= nm ? i + 1 : n;   /* no test-particle pair term (R24) */
+        for (int64_t j = i + 1; j < jend; j++) {
             const double *xj = x + 3 * j;
             long double dx = (long double)xj[0] - xi[0], dy = (long double)xj[1] - xi[1],
                         dz = (long double)xj[2] - xi[2];
@@ -1326,6 +1358,12 @@ void orc_energy(int64_t n, const double *x, const double *v, const double *m, do
 #undef KAHAN_ADD
     *E = (double)sum;
     L[0] = (double)Lx; L[1] = (double)Ly; L[2] = (double)Lz;
+}
+
+void orc_energy(int64_t n, const double *x, const double *v, const double *m, double m_star,
+                double G, double *E, double *L)
+{
+    orc_energy_tp(n, n, x, v, m, m_star, G, E, L);
 }
 
 /* Size of the parameter and statistics structs, for the loader's layout check. */
