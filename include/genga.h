@@ -63,9 +63,16 @@ typedef struct genga_params {
     int32_t precision; /* GENGA_FP64 or GENGA_MIXED for the all-pairs kick */
     int32_t kepler_max_iter; /* Newton iteration limit of the Kepler solve (default 50) */
     int32_t bs_max_steps;    /* limit on Bulirsch-Stoer step attempts per group (default 100000) */
-    int32_t reserved;
+    int32_t tp_mode;         /* Sec. 8.1 test-particle mode: 0 every pair interacts (default);
+                                2 semi-active: bodies i >= n_massive are test particles and two
+                                test particles have no interaction (no force, no candidate, no
+                                encounter, no potential term).  Mode 1 (test particles that act
+                                on nothing) is mode 2 with massless test particles.  The
+                                adjoint calls refuse mode 2. */
     int64_t cand_capacity;   /* initial capacity of the candidate pair list (grows on demand) */
     int64_t pair_capacity;   /* initial capacity of each level's encounter list (grows) */
+    int64_t n_massive;       /* tp_mode 2: the large bodies are 0..n_massive-1 (callers order the
+                                bodies by a mass threshold); >= n means no test particles */
 } genga_params_t;
 
 /* Counters of the last genga_step call (summed over its steps). */
@@ -216,14 +223,16 @@ int genga_get_stats(genga_system_t *sys, genga_stats_t *st);
  * nsteps normal steps (leaving the final state in pos/vel) and keeps each
  * step's rc and pairs and a checkpoint every checkpoint_every steps.
  * genga_get_stats then reports the whole run (sums; maxima for max_group and
- * bs_max_attempts).  Errors: EINVAL (slevels != 1), the errors of genga_step. */
+ * bs_max_attempts).  Errors: EINVAL (slevels != 1 or tp_mode != 0), the errors
+ * of genga_step.                                                             */
 int genga_adjoint_forward(genga_system_t *sys, int64_t nsteps, int64_t checkpoint_every);
 
 /* Uses a recording made elsewhere: rc_hist (host, nsteps x n doubles, step
  * major), pair_offsets (host, nsteps + 1) and pairs (host, interleaved uint32
  * i < j, step k's pairs at pair_offsets[k] .. pair_offsets[k+1]-1).  The
  * current state is the initial state; the steps are replayed with the frozen
- * rc and pairs, leaving the final state in pos/vel.  Synchronises.          */
+ * rc and pairs, leaving the final state in pos/vel.  Synchronises.  Errors:
+ * EINVAL (as genga_adjoint_forward).                                        */
 int genga_adjoint_load(genga_system_t *sys, int64_t nsteps, int64_t checkpoint_every,
                        const double *rc_hist, const int64_t *pair_offsets, const uint32_t *pairs);
 

@@ -663,7 +663,7 @@ static void accumulate_stats(genga_stats_t &t, const genga_stats_t &x) {
 }
 
 int genga_adjoint_forward(genga_system_t *s, int64_t nsteps, int64_t checkpoint_every) {
-    if (!s || nsteps < 1 || checkpoint_every < 1 || s->p.slevels != 1) return GENGA_EINVAL;
+    if (!s || nsteps < 1 || checkpoint_every < 1 || s->p.slevels != 1 || s->p.tp_mode != 0) return GENGA_EINVAL;
     int rc = adj_alloc(s, nsteps, checkpoint_every);
     if (rc != GENGA_OK) return rc;
     Adjoint *a = adj_of(s);
@@ -692,7 +692,8 @@ int genga_adjoint_forward(genga_system_t *s, int64_t nsteps, int64_t checkpoint_
 
 int genga_adjoint_load(genga_system_t *s, int64_t nsteps, int64_t checkpoint_every, const double *rc_hist,
                        const int64_t *pair_offsets, const uint32_t *pairs) {
-    if (!s || nsteps < 1 || checkpoint_every < 1 || !rc_hist || !pair_offsets || s->p.slevels != 1)
+    if (!s || nsteps < 1 || checkpoint_every < 1 || !rc_hist || !pair_offsets || s->p.slevels != 1 ||
+        s->p.tp_mode != 0)
         return GENGA_EINVAL;
     int rc = adj_alloc(s, nsteps, checkpoint_every);
     if (rc != GENGA_OK) return rc;
@@ -715,7 +716,8 @@ int genga_adjoint_load(genga_system_t *s, int64_t nsteps, int64_t checkpoint_eve
 
 int genga_adjoint_backward(genga_system_t *s, const double *lam_x, const double *lam_v, double *grad_x0,
                            double *grad_v0, double *grad_m) {
-    if (!s || !lam_x || !lam_v || !grad_x0 || !grad_v0 || !grad_m || !s->adj) return GENGA_EINVAL;
+    if (!s || !lam_x || !lam_v || !grad_x0 || !grad_v0 || !grad_m || !s->adj || s->p.tp_mode != 0)
+        return GENGA_EINVAL;
     Adjoint *a = adj_of(s);
     if (a->nsteps < 1) return GENGA_EINVAL;
     const size_t n = (size_t)s->n;

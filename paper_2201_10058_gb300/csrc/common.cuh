@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "../../include/genga.h"
@@ -133,6 +134,13 @@ struct genga_system {
     int64_t launches = 0;          // kernels launched by this system (host-side count)
     char err[512] = {0};
 };
+
+// Test-particle boundary (Sec. 8.1 semi-active mode): bodies i >= the bound are
+// test particles that do not interact with one another; n when there are none.
+inline int tp_bound(const genga_system *s) {
+    if (s->p.tp_mode != 2) return (int)s->n;
+    return (int)std::min<int64_t>(std::max<int64_t>(s->p.n_massive, 0), s->n);
+}
 
 namespace genga {
 

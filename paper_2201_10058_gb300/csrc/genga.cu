@@ -71,6 +71,9 @@ int check_params(genga_system *s, const genga_params_t *p) {
     if (p->kepler_max_iter < 1 || p->bs_max_steps < 1)
         return fail(s, GENGA_EINVAL, "iteration limits must be >= 1");
     if (!(p->bs_tol > 0)) return fail(s, GENGA_EINVAL, "bs_tol must be > 0");
+    if (p->tp_mode != 0 && p->tp_mode != 2)
+        return fail(s, GENGA_EINVAL, "tp_mode must be 0 or 2 (mode 1: mode 2 with massless test particles)");
+    if (p->tp_mode == 2 && p->n_massive < 0) return fail(s, GENGA_EINVAL, "n_massive must be >= 0");
     return GENGA_OK;
 }
 

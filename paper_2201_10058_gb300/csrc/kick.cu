@@ -43,6 +43,7 @@ struct KickArgs {
     const double *rc, *rc2, *pc2;
     const float *thr_rc;        // FP32 upper bound of rc^2
     int n;
+    int nm;                     // bodies i >= nm are test particles (nm = n: none)
     int chunk;
     double *part;               // [nchunk][6][n]
     uint2 *cand;
@@ -97,7 +98,10 @@ __device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
     lo = __uint_as_float(__float_as_uint(l) | sgn);
 }
 
-template <bool MIXED>
+// TP: semi-active test particles (Sec. 8.1): a test particle i takes only the
+// sources j < nm; the block that holds the boundary masks the test-particle
+// pairs, the blocks past it shorten their source range.
+template <bool MIXED, bool TP>
 __global__ void __launch_bounds__(kKickThreads, kick_min_blocks(MIXED))
 kick_kernel(KickArgs A)
 {
@@ -118,7 +122,10 @@ kick_kernel(KickArgs A)
     }
 
     const int jbeg = blockIdx.y * A.chunk;
-    const int jend = min(n, jbeg + A.chunk);
+    int jend = min(n, jbeg + A.chunk);
+    const int i0 = blockIdx.x * kKickThreads;
+    const bool straddle = TP && i0 < A.nm && i0 + kKickThreads > A.nm;
+    if (TP && i0 >= A.nm) jend = min(jend, A.nm);
 
     double S0 = 0.0, S1 = 0.0, S2 = 0.0;   // compensated chunk totals
     double C0 = 0.0, C1 = 0.0, C2 = 0.0;
@@ -180,6 +187,9 @@ kick_kernel(KickArgs A)
             double mk = sm[k];
             float mh = 0.0f, ml = 0.0f;
             if (MIXED) { mh = smh[k]; ml = sml[k]; }
+            if (TP && straddle && i >= A.nm && j >= A.nm) {   // two test particles
+                mk = 0.0; mh = 0.0f; ml = 0.0f;
+            }
             // Changeover band (rare): K < 1 needs r < rc_ij.  K is flat (zero slope) at
             // r = rc, so the branch may follow the FP32 bound and K uses the r^2 above.
             if (r2f < fmaxf(thri, sthr[k])) {
@@ -297,6 +307,7 @@ precheck_kernel(KickArgs A, double f_pc)
     __shared__ uint2 wbuf[kPcThreads / 32][kPcWarpBuf];
     const int n = A.n;
     const int i0 = blockIdx.x * (kPcThreads * kPcI);
+    if (i0 >= A.nm) return;                              // only test-particle rows: no pairs
     const int jbeg = max(blockIdx.y * A.chunk, i0 + 1);
     const int jend = min(n, blockIdx.y * A.chunk + A.chunk);
     if (jbeg >= jend) return;                            // block below the diagonal
@@ -312,7 +323,7 @@ precheck_kernel(KickArgs A, double f_pc)
         const int i = i0 + r * kPcThreads + threadIdx.x;
         ii[r] = i;
         xf[r] = yf[r] = zf[r] = 3.0e38f; Pi[r] = 0.0f; Mi[r] = 0.0f;
-        if (i < n) {
+        if (i < n && i < A.nm) {        // a test-particle row pairs only with j > i: none
             xf[r] = f32_of_f64_rn(A.x[i]); yf[r] = f32_of_f64_rn(A.y[i]); zf[r] = f32_of_f64_rn(A.z[i]);
             Pi[r] = (float)f_pc * f32_of_f64_rn(A.rc[i]);
             Mi[r] = kM * fmaxf(fabsf(xf[r]), fmaxf(fabsf(yf[r]), fabsf(zf[r])));
@@ -413,6 +424,7 @@ static KickArgs make_args(genga_system *s, bool precheck) {
     A.rc = s->rcl[0].rc; A.rc2 = s->rcl[0].rc2; A.pc2 = s->rcl[0].pc2;
     A.thr_rc = s->rcl[0].thr_rc;
     A.n = (int)n;
+    A.nm = tp_bound(s);
     A.chunk = s->kick_chunk;
     A.part = s->kick_part;
     A.cand = s->cand;
@@ -429,8 +441,13 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
     dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
     if (precheck) GENGA_CUDA_TRY(launch_precheck_only(s));
     const bool mixed = s->p.precision == GENGA_MIXED;
-    if (mixed) kick_kernel<true><<<grid, kKickThreads, 0, s->stream>>>(A);
-    else kick_kernel<false><<<grid, kKickThreads, 0, s->stream>>>(A);
+    if (A.nm < n) {
+        if (mixed) kick_kernel<true, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+        else kick_kernel<false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    } else {
+        if (mixed) kick_kernel<true, false><<<grid, kKickThreads, 0, s->stream>>>(A);
+        else kick_kernel<false, false><<<grid, kKickThreads, 0, s->stream>>>(A);
+    }
     ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     kick_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(s->kick_part, s->kick_nchunk, n, s->p.G,
@@ -464,11 +481,11 @@ cudaError_t launch_kick_raw(const KickRaw &k, int num_sms, int max_nchunk, cudaS
     KickArgs A;
     A.x = k.pos; A.y = k.pos + k.n; A.z = k.pos + 2 * (size_t)k.n; A.m = k.mass;
     A.rc = k.rc; A.rc2 = k.rc2; A.pc2 = nullptr; A.thr_rc = k.thr;
-    A.n = k.n; A.chunk = chunk; A.part = k.part;
+    A.n = k.n; A.nm = k.n; A.chunk = chunk; A.part = k.part;
     A.cand = nullptr; A.cand_count = nullptr; A.cand_cap = 0;
     dim3 grid((k.n + kKickThreads - 1) / kKickThreads, nchunk);
-    if (k.mixed) kick_kernel<true><<<grid, kKickThreads, 0, stream>>>(A);
-    else kick_kernel<false><<<grid, kKickThreads, 0, stream>>>(A);
+    if (k.mixed) kick_kernel<true, false><<<grid, kKickThreads, 0, stream>>>(A);
+    else kick_kernel<false, false><<<grid, kKickThreads, 0, stream>>>(A);
     GENGA_CUDA_TRY(cudaGetLastError());
     kick_finalize<<<(k.n + 255) / 256, 256, 0, stream>>>(k.part, nchunk, k.n, k.G, k.dt_half, k.vel, k.acc_out);
     return cudaGetLastError();

@@ -136,7 +136,7 @@ constexpr int kEnThreads = 128;
 constexpr int kEnTile = 256;
 
 __global__ void __launch_bounds__(kEnThreads)
-energy_terms_kernel(int n, const double *pos, const double *vel, const double *mass, double G,
+energy_terms_kernel(int n, int nm, const double *pos, const double *vel, const double *mass, double G,
                     double m_star, double *terms /* [8][n] */) {
     __shared__ double sx[kEnTile], sy[kEnTile], sz[kEnTile], sm[kEnTile];
     const int i = blockIdx.x * kEnThreads + threadIdx.x;
@@ -145,6 +145,7 @@ energy_terms_kernel(int n, const double *pos, const double *vel, const double *m
     double xi = 0, yi = 0, zi = 0;
     if (valid) { xi = pos[i]; yi = pos[N + i]; zi = pos[2 * N + i]; }
     double S = 0.0, C = 0.0;
+    const int jlim = i >= nm ? nm : n;     // a test particle has no pair term with another
     for (int jt = 0; jt < n; jt += kEnTile) {
         const int cnt = min(kEnTile, n - jt);
         __syncthreads();
@@ -154,7 +155,7 @@ energy_terms_kernel(int n, const double *pos, const double *vel, const double *m
         __syncthreads();
         double part = 0.0;
         for (int k = 0; k < cnt; k++) {
-            if (jt + k == i) continue;
+            if (jt + k == i || jt + k >= jlim) continue;
             const double dx = sx[k] - xi, dy = sy[k] - yi, dz = sz[k] - zi;
             part += sm[k] / sqrt(dx * dx + dy * dy + dz * dz);
         }
@@ -248,7 +249,7 @@ cudaError_t launch_energy(genga_system *s, double *E_host, double *L_host) {
     const int n = (int)s->n;
     double *terms = s->red;            // 9 rows of n, then 10 sums
     energy_terms_kernel<<<(n + kEnThreads - 1) / kEnThreads, kEnThreads, 0, s->stream>>>(
-        n, s->pos, s->vel, s->mass, s->p.G, s->p.m_star, terms); ++s->launches;
+        n, tp_bound(s), s->pos, s->vel, s->mass, s->p.G, s->p.m_star, terms); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     double *sums = terms + 9 * (size_t)n;
     row_sum_kernel<<<9, 256, 0, s->stream>>>(n, terms, 9, sums); ++s->launches;

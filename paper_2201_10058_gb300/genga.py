@@ -46,8 +46,9 @@ class Params(C.Structure):
                 ("n1", C.c_double), ("n2", C.c_double), ("f_pc", C.c_double),
                 ("bs_tol", C.c_double), ("slevels", C.c_int32), ("substeps", C.c_int32),
                 ("precision", C.c_int32), ("kepler_max_iter", C.c_int32),
-                ("bs_max_steps", C.c_int32), ("reserved", C.c_int32),
-                ("cand_capacity", C.c_int64), ("pair_capacity", C.c_int64)]
+                ("bs_max_steps", C.c_int32), ("tp_mode", C.c_int32),
+                ("cand_capacity", C.c_int64), ("pair_capacity", C.c_int64),
+                ("n_massive", C.c_int64)]
 
 
 class EnsembleDesc(C.Structure):

@@ -512,3 +512,78 @@ def test_tune_levels_restores_state_and_keeps_fastest(g):
     with pytest.raises(g.GengaError):
         s.tune_levels([(2, 10), (0, 1)])
     assert (s.params.slevels, s.params.substeps) == (L, S)
+
+
+# ---------------------------------------------------------------- semi-active test particles (Sec. 8.1)
+TP_CASES = [("disk2048", lambda: config_workload(0), 1000),      # boundary inside a 128-row block
+            ("disk3001_ragged", lambda: disk(3001, 0.5, 2.0, 2.0, 77, name="ragged"), 2560),
+            ("disk2048_all_tp", lambda: config_workload(0), 0)]
+
+
+@pytest.mark.parametrize("name,make,nm", TP_CASES)
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_tp_kick_matches_oracle(g, name, make, nm, precision, tol):
+    torch = _torch()
+    wl = make()
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    s, pos, vel, mass = _system(g, wl, precision, tp_mode=2, n_massive=nm)
+    s.set_rcrit(rc)
+    acc = torch.zeros((3, wl.n), dtype=torch.float64, device="cuda:0")
+    s.kick(0.0, precheck=False, acc_out=acc)
+    torch.cuda.synchronize()
+    a = _host(acc)
+    ref = O.accel(wl.x, wl.m, rc, G, nthreads=8, n_massive=nm)
+    if nm == 0:
+        assert np.all(a == 0.0) and np.all(ref == 0.0)
+        return
+    rel = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    numerics_log.record(f"kick {name} test particles from {nm} precision={precision}",
+                        "per-particle |da|/|a|", rel.max(), tol)
+    assert rel.max() <= tol, rel.max()
+
+
+@pytest.mark.parametrize("name,make,nm", TP_CASES)
+def test_tp_precheck_candidates_bit_exact(g, name, make, nm):
+    wl = make()
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    s, *_ = _system(g, wl, 1, tp_mode=2, n_massive=nm)
+    s.set_rcrit(rc)
+    s.kick(0.5 * wl.dt, precheck=True)
+    ref = O.precheck(wl.x, rc, wl.f_pc, n_massive=nm)
+    np.testing.assert_array_equal(s.candidates().reshape(-1, 2), ref.reshape(-1, 2))
+
+
+@pytest.mark.parametrize("slevels,substeps", [(1, 1), (2, 10)])
+def test_tp_step_matches_oracle(g, slevels, substeps):
+    """Whole steps with 1,500 large bodies and 548 semi-active test particles."""
+    wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=slevels, substeps=substeps)
+    nm = 1500
+    s, pos, vel, mass = _system(g, wl, 0, tp_mode=2, n_massive=nm)
+    s.step(5)
+    st = s.stats()
+    xr, vr, status, ost = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=8, tp_mode=2, n_massive=nm), 5)
+    assert status == 0
+    assert st["n_candidates"] == ost["n_candidates"] > 0
+    assert st["n_pairs"][0] == ost["n_pairs"][0] > 0
+    err = _rel_pos_err(_host(pos), xr)
+    numerics_log.record(f"5 steps dense disk2048 test particles from {nm} levels=({slevels},{substeps})",
+                        "max |dx|/|x|", err.max(), 1e-12)
+    assert err.max() <= 1e-12, err.max()
+
+
+def test_tp_energy_matches_oracle(g):
+    wl = config_workload(0)
+    s, *_ = _system(g, wl, 0, tp_mode=2, n_massive=1200)
+    E, L = s.energy()
+    Er, Lr = O.energy(wl.x, wl.v, wl.m, wl.m_star, G, n_massive=1200)
+    assert abs(E - Er) <= 1e-13 * abs(Er)
+    np.testing.assert_allclose(L, Lr, rtol=1e-13)
+
+
+def test_tp_mode_checks(g):
+    wl = config_workload(0, n_override=256)
+    with pytest.raises(g.GengaError):
+        _system(g, wl, 0, tp_mode=1, n_massive=100)
+    s, *_ = _system(g, wl, 0, tp_mode=2, n_massive=100)
+    with pytest.raises(g.GengaError):
+        s.adjoint_forward(2, 1)
