@@ -61,11 +61,12 @@ def parse():
     ap.add_argument("--kick-reps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e/cpu/fp64 legs (profiling runs)")
-    ap.add_argument("--workload", choices=["disk", "ensemble", "adjoint", "variants"], default="disk",
+    ap.add_argument("--workload", choices=["disk", "ensemble", "adjoint", "variants", "tp"], default="disk",
                     help="disk: the N=65,540 disk (headline); ensemble: 4096 compact systems "
                          "with GR and tides; adjoint: the 1000-step adjoint at N=4096; "
                          "variants: FP64 vs mixed on the N=16,384 disk (one level) and the "
-                         "N=65,540 disk at other (levels, sub-steps)")
+                         "N=65,540 disk at other (levels, sub-steps); tp: the N=65,540 disk "
+                         "with 4,096 large bodies and semi-active test particles")
     ap.add_argument("--ens-steps", type=int, default=1000,
                     help="integration steps per timed ensemble launch")
     ap.add_argument("--energy-run", type=int, default=0,
@@ -680,6 +681,61 @@ def run_variants(args) -> dict:
     return out
 
 
+def run_tp(args) -> dict:
+    """The headline disk in the semi-active test-particle mode (Sec. 8.1): the 4
+    embryos and the first 4,092 planetesimals are the large bodies (moved to the
+    front), the other 61,444 planetesimals test particles.  Mixed kick, 2 levels x
+    10 sub-steps, the headline's timing rules."""
+    import torch
+
+    from paper_2201_10058_gb300 import genga
+    from workloads import disk
+    from workloads.disk import SEED_BASE
+
+    dev = torch.device("cuda", 0)
+    genga.load()
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    wl = disk(65536, 0.5, 4.0, 5.0, SEED_BASE + 2, n_embryos=4, m_embryo_earth=0.1,
+              slevels=2, substeps=10, name="disk65536+4emb")
+    n, nm = wl.n, 4096
+    order = np.r_[np.arange(n - 4, n), np.arange(n - 4)]
+    x, v, m = wl.x[order], wl.v[order], wl.m[order]
+    pos = torch.tensor(np.ascontiguousarray(x.T), device=dev)
+    vel = torch.tensor(np.ascontiguousarray(v.T), device=dev)
+    mass = torch.tensor(m, device=dev)
+    p = genga.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc,
+                             slevels=2, substeps=10, precision=genga.GENGA_MIXED, tp_mode=2,
+                             n_massive=nm)
+    sampler = ClockSampler(gpu_uuid(0))
+    sampler.start()
+    sysm = genga.System(pos, vel, mass, p, stream=stream)
+    ms = _timed_steps(genga, sysm, flush, stream, args.steps, args.warmup)
+    st = sysm.stats()
+    sysm.rcrit(wl.dt)
+    sysm.kick(0.0, precheck=False)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(5):
+        sysm.kick(0.0, precheck=False)
+    k1.record(stream)
+    k1.synchronize()
+    kick_ms = k0.elapsed_time(k1) / 5
+    sysm.close()
+    evals = nm * (n - 1) + (n - nm) * nm        # pair evaluations of one kick
+    return {"metric": "semi-active test-particle mode (secondary measurement)",
+            "workload": f"disk N={n}: {nm} large bodies (4 embryos first), {n - nm} test particles; "
+                        f"mixed kick, 2 levels x 10 sub-steps",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "steps_per_s": round(1e3 / ms, 3), "kick_ms": round(kick_ms, 3),
+            "kick_pair_evaluations": evals,
+            "kick_gpairs_per_s": round(evals / (kick_ms * 1e-3) / 1e9, 3),
+            "candidates_per_step": st["n_candidates"], "pairs_per_level": st["n_pairs"][:2],
+            "max_group": st["max_group"], "clocks": sampler.stop()}
+
+
 def _recording(s):
     """Host copies of a system's recorded rc history and pair lists."""
     return s.adjoint_export()
@@ -689,6 +745,9 @@ def main():
     args = parse()
     if args.workload == "adjoint" and args.impl == "ours":
         print(json.dumps(run_adjoint(args)))
+        return
+    if args.workload == "tp" and args.impl == "ours":
+        print(json.dumps(run_tp(args)))
         return
     if args.workload == "variants" and args.impl == "ours":
         print(json.dumps(run_variants(args)))
