@@ -96,3 +96,22 @@ def test_levels_partition_and_at_most_two_active():
     rcs2 = [rc0 / 2 ** l for l in range(4)]
     assert max(sum(1 for v in _level_factors(r, rcs2) if v > 0.0)
                for r in np.geomspace(1e-3 * rc0, rc0, 2001)) > most
+
+
+def test_semi_active_test_particle_pairs():
+    """Sec. 8.1 (TP 2): which pair kinds keep their interaction, read from the
+    oracle's kick on four bodies (two large, two test particles) with one body's
+    mass switched on at a time."""
+    keep_ll, keep_lt, keep_tt = (bool(v) for v in GOLD["tp2_pairs_kept"])
+    x = np.array([[1.0, 0.0, 0.0], [1.3, 0.1, 0.0], [0.8, -0.2, 0.1], [1.1, 0.3, -0.1]])
+    rc = np.zeros(4)                      # K = 1: plain Newtonian pairs
+    nm = 2                                # bodies 0, 1 large; 2, 3 test particles
+
+    def felt(i, j):
+        m = np.zeros(4)
+        m[j] = 1e-6
+        return bool(np.any(O.accel(x, m, rc, 1.0, n_massive=nm)[i] != 0.0))
+
+    assert felt(0, 1) == felt(1, 0) == keep_ll
+    assert felt(2, 0) == felt(0, 2) == keep_lt
+    assert felt(2, 3) == felt(3, 2) == keep_tt
