@@ -109,7 +109,9 @@ void genga_destroy(genga_system_t *sys);
  * owned by the system and valid until its next call.                       */
 const char *genga_last_error(const genga_system_t *sys);
 
-/* Changes the parameters (same n).  Errors: EINVAL.                         */
+/* Changes the parameters (same n).  Levels beyond those the system already
+ * holds get their arrays here; arrays of levels dropped are kept for reuse.
+ * Errors: EINVAL (invalid parameters; nothing changed), ENOMEM, ECUDA.      */
 int genga_set_params(genga_system_t *sys, const genga_params_t *p);
 
 /* Blocks until the stream has finished; reports latched device errors.     */
