@@ -476,6 +476,7 @@ int adj_alloc(genga_system *s, int64_t nsteps, int64_t every) {
         int want = (8 * s->num_sms + iblocks - 1) / iblocks;
         const int tiles = (int)((n + kAdjTile - 1) / kAdjTile);
         int tpc = std::max(1, std::min(16, (tiles + want - 1) / std::max(1, want)));
+        if ((tiles + tpc - 1) / tpc > kMaxKickChunks) tpc = (tiles + kMaxKickChunks - 1) / kMaxKickChunks;
         a->chunk = tpc * kAdjTile;
         a->nchunk = (int)((n + a->chunk - 1) / a->chunk);
         ACU(cudaMalloc(&a->part, sizeof(double) * 4 * n * (size_t)a->nchunk));

@@ -13,6 +13,10 @@
 namespace genga {
 
 constexpr int kMaxLevels = 8;
+// All-pairs kicks split the sources into at most this many chunks: the chunk
+// partial sums take nchunk x (4 or 6) doubles per body, so beyond it a larger N
+// widens the chunks instead of adding chunks.
+constexpr int kMaxKickChunks = 64;
 // Close-encounter groups with more members than this are integrated by the
 // batched grid-wide Bulirsch-Stoer driver (bsm.cu) instead of one thread block.
 constexpr int kBlockGroupMax = 32;

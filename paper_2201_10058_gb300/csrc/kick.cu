@@ -411,6 +411,8 @@ void kick_geometry(int n, int num_sms, int *chunk, int *nchunk) {
     int tiles_per_chunk = (max_chunks + want - 1) / (want > 0 ? want : 1);
     if (tiles_per_chunk > 16) tiles_per_chunk = 16;
     if (tiles_per_chunk < 1) tiles_per_chunk = 1;
+    if ((max_chunks + tiles_per_chunk - 1) / tiles_per_chunk > kMaxKickChunks)
+        tiles_per_chunk = (max_chunks + kMaxKickChunks - 1) / kMaxKickChunks;
     *chunk = tiles_per_chunk * kTile;
     *nchunk = (n + *chunk - 1) / *chunk;
 }

@@ -131,6 +131,22 @@ def test_kick_bench_size_sampled_rows(g, precision, tol):
     assert rel.max() <= tol, rel.max()
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_kick_large_n_sampled_rows(g, precision, tol):
+    """N = 300,000 (more source chunks than the partial-sum cap allows at 16 tiles
+    each, so the chunks widen): 64 sampled rows, the first and the last, against
+    the oracle row by row."""
+    wl = disk(300000, 0.5, 4.0, 5.0, 91, name="disk300k")
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    a = _acc(g, wl, precision, rc)
+    rows = np.concatenate([np.random.default_rng(9).choice(wl.n, 62, replace=False), [0, wl.n - 1]])
+    ref = O.accel_rows(wl.x, wl.m, rc, G, rows, nthreads=16)
+    rel = np.linalg.norm(a[rows] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    numerics_log.record(f"kick disk300000 (64 rows) precision={precision}", "per-particle |da|/|a|",
+                        rel.max(), tol)
+    assert rel.max() <= tol, rel.max()
+
+
 def test_kick_applies_velocity_update(g):
     wl = config_workload(0)
     rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
