@@ -104,6 +104,20 @@ def lib():
             L.orc_step_frozen.restype = C.c_int
             L.orc_step_frozen.argtypes = [C.c_int64, _D, _D, _D, C.POINTER(OracleParams), _D,
                                           C.c_int64, _U32, _D, _D, _D]
+            L.orc_merge.restype = C.c_double
+            L.orc_merge.argtypes = [C.c_int64, C.c_int64, _D, _D, _D, _D, _D, C.c_double,
+                                    C.POINTER(C.c_int64)]
+            _U8 = C.POINTER(C.c_uint8)
+            L.orc_bs_groups_coll.restype = C.c_int
+            L.orc_bs_groups_coll.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _U8, _D, C.c_int,
+                                             C.c_int64, _U32, C.c_double, C.c_double, C.c_double,
+                                             C.c_double, C.c_int, C.c_double, _D,
+                                             C.POINTER(C.c_int64), _D, C.c_int64,
+                                             C.POINTER(OracleStats)]
+            L.orc_step_coll.restype = C.c_int
+            L.orc_step_coll.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _U8,
+                                        C.POINTER(OracleParams), C.c_int64, C.c_double, _D,
+                                        C.POINTER(C.c_int64), _D, C.c_int64, C.POINTER(OracleStats)]
             L.orc_sizeof_params.restype = C.c_int64
             L.orc_sizeof_stats.restype = C.c_int64
             assert L.orc_sizeof_params() == C.sizeof(OracleParams)
@@ -317,3 +331,56 @@ def energy(x, v, m, m_star, G, n_massive=None):
     nm = n if n_massive is None else int(n_massive)
     lib().orc_energy_tp(n, nm, _d(x), _d(v), _d(m), m_star, G, _d(E), _d(L))
     return float(E[0]), L
+
+
+# ---------------------------------------------------------------- collisions (Sec. 7.1-7.2)
+def merge(i, j, x, v, m, R, S, G):
+    """Sec. 7.1 merger of bodies i and j (copies of the arrays are changed and
+    returned): (x, v, m, R, S, dU, survivor)."""
+    x, v, m, R, S = (_f64(a).copy() for a in (x, v, m, R, S))
+    sv = C.c_int64()
+    dU = lib().orc_merge(int(i), int(j), _d(x), _d(v), _d(m), _d(R), _d(S), G, C.byref(sv))
+    return x, v, m, R, S, float(dU), int(sv.value)
+
+
+def _coll_state(x, v, m, R, S, alive):
+    x, v, m, R, S = (_f64(a).copy() for a in (x, v, m, R, S))
+    n = m.shape[0]
+    alive = np.ones(n, dtype=np.uint8) if alive is None else np.ascontiguousarray(alive, dtype=np.uint8).copy()
+    return x, v, m, R, S, alive
+
+
+def bs_groups_coll(x, v, m, R, S, rc_levels, pairs, G, m_star, dt, tol=1e-15, max_steps=100000,
+                   coll_tol=0.0, alive=None):
+    """BS of every group with collisions (R25).  Returns (x, v, m, R, S, alive,
+    U, log, status, stats); log has one row per merger: time in the call, i, j,
+    r_ij, R_i + R_j, Delta U."""
+    x, v, m, R, S, alive = _coll_state(x, v, m, R, S, alive)
+    rcl = _f64(np.atleast_2d(rc_levels))
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    U = np.zeros(1)
+    nc = C.c_int64(0)
+    log = np.zeros((max(m.shape[0], 1), 6))
+    st = OracleStats()
+    status = lib().orc_bs_groups_coll(m.shape[0], _d(x), _d(v), _d(m), _d(R), _d(S),
+                                      alive.ctypes.data_as(C.POINTER(C.c_uint8)), _d(rcl),
+                                      rcl.shape[0], pairs.shape[0], pairs.ctypes.data_as(_U32),
+                                      G, m_star, dt, tol, max_steps, coll_tol, _d(U), C.byref(nc),
+                                      _d(log), log.shape[0], C.byref(st))
+    return (x, v, m, R, S, alive, float(U[0]), log[:nc.value].copy(), int(status), st.as_dict())
+
+
+def step_coll(x, v, m, R, S, params: OracleParams, nsteps: int = 1, coll_tol=0.0, alive=None):
+    """Steps with collisions (R25).  Returns (x, v, m, R, S, alive, U, log,
+    status, stats) as bs_groups_coll (log times from the start of each BS call)."""
+    x, v, m, R, S, alive = _coll_state(x, v, m, R, S, alive)
+    U = np.zeros(1)
+    nc = C.c_int64(0)
+    log = np.zeros((max(m.shape[0], 1), 6))
+    st = OracleStats()
+    status = lib().orc_step_coll(m.shape[0], _d(x), _d(v), _d(m), _d(R), _d(S),
+                                 alive.ctypes.data_as(C.POINTER(C.c_uint8)), C.byref(params),
+                                 nsteps, coll_tol, _d(U), C.byref(nc), _d(log), log.shape[0],
+                                 C.byref(st))
+    return (x, v, m, R, S, alive, float(U[0]), log[:nc.value].copy(), int(status), st.as_dict())
+

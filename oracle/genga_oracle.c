@@ -41,6 +41,19 @@
  *      and a pair of two test particles has no interaction at all (no force,
  *      no candidate, no encounter, no potential term); every other pair is
  *      treated as in the fully interactive mode.
+ *  R25 Collisions (Sec. 7.1-7.2): checked at the end of every accepted
+ *      Bulirsch-Stoer step over the group's encounter pairs whose bodies are
+ *      both alive, r_ij < R_i + R_j; with a collision precision tol > 0 a step
+ *      that ends with an overlap (R_i + R_j - r_ij)/(R_i + R_j) >= tol is
+ *      rejected and halved, so a merger happens at an overlap below tol; pairs
+ *      overlapping when a group's integration starts merge at once; overlapping
+ *      pairs merge in ascending pair order.  A merger follows Sec. 7.1: the
+ *      survivor is the more massive body (equal masses: the lower index),
+ *      position and velocity are mass-weighted, m and R^3 add, the spin is
+ *      S_i + S_j + mu (r_ij x v_ij), U grows by mu v_ij^2/2 - G m_i m_j/r_ij;
+ *      the other body keeps its position and velocity with m = R = S = 0 and
+ *      is no longer alive: it exerts no force, feels only the star inside a
+ *      group integration, and never collides again.
  */
 #include <math.h>
 #include <stdint.h>
@@ -383,6 +396,75 @@ void orc_group(int64_t n, int64_t npairs, const uint32_t *pairs, int64_t *label)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Collisions (R25).                                                          */
+typedef struct coll_ctx {
+    double *m, *R, *S;        /* masses, physical radii, spins (3 per body), updated by mergers */
+    unsigned char *alive;     /* 0 once merged away */
+    double tol;               /* collision precision (0: merge at the first overlapping step) */
+    double G;
+    double U;                 /* energy moved into U by the mergers so far */
+    int64_t ncoll;
+    double *log;              /* per merger: t, i, j, r_ij, R_i + R_j, Delta U (or NULL) */
+    int64_t log_cap;          /* mergers the log can hold */
+    double t0;                /* time of the current BS call's start */
+} coll_ctx;
+
+/* Sec. 7.1 merger of bodies i and j at positions xi, xj with velocities vi, vj:
+ * the merged position and velocity go to xo, vo; m, R and S of the survivor
+ * are updated and those of the other body zeroed.  Returns the survivor;
+ * *other the removed body, *dU the energy moved into U.                      */
+static int64_t merge_core(int64_t i, int64_t j, const double *xi, const double *vi,
+                          const double *xj, const double *vj, double *m, double *R, double *S,
+                          double G, double *xo, double *vo, int64_t *other, double *dU)
+{
+    const double mi = m[i], mj = m[j], M = mi + mj;
+    double r[3], w[3];
+    for (int k = 0; k < 3; k++) { r[k] = xi[k] - xj[k]; w[k] = vi[k] - vj[k]; }
+    const double rr = sqrt((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]);
+    const double w2 = (w[0] * w[0] + w[1] * w[1]) + w[2] * w[2];
+    double mu = 0.0;
+    if (M > 0.0) {
+        mu = mi * mj / M;
+        for (int k = 0; k < 3; k++) {
+            xo[k] = (xi[k] * mi + xj[k] * mj) / M;
+            vo[k] = (vi[k] * mi + vj[k] * mj) / M;
+        }
+    } else {
+        for (int k = 0; k < 3; k++) { xo[k] = 0.5 * (xi[k] + xj[k]); vo[k] = 0.5 * (vi[k] + vj[k]); }
+    }
+    *dU = 0.5 * mu * w2 - (rr > 0.0 ? G * mi * mj / rr : 0.0);
+    const double L[3] = {mu * (r[1] * w[2] - r[2] * w[1]), mu * (r[2] * w[0] - r[0] * w[2]),
+                         mu * (r[0] * w[1] - r[1] * w[0])};
+    const int64_t sv = (mi > mj || (mi == mj && i < j)) ? i : j, ot = sv == i ? j : i;
+    const double R3 = R[i] * R[i] * R[i] + R[j] * R[j] * R[j];
+    double Sn[3];
+    for (int k = 0; k < 3; k++) Sn[k] = S[3 * i + k] + S[3 * j + k] + L[k];
+    m[sv] = M;
+    R[sv] = cbrt(R3);
+    for (int k = 0; k < 3; k++) S[3 * sv + k] = Sn[k];
+    m[ot] = 0.0;
+    R[ot] = 0.0;
+    for (int k = 0; k < 3; k++) S[3 * ot + k] = 0.0;
+    *other = ot;
+    return sv;
+}
+
+/* Merger of bodies i and j of the row-major arrays x, v (n x 3): the survivor
+ * takes the merged position and velocity, the other keeps its own.  Returns
+ * Delta U; *survivor receives the surviving index.                           */
+double orc_merge(int64_t i, int64_t j, double *x, double *v, double *m, double *R, double *S,
+                 double G, int64_t *survivor)
+{
+    double xo[3], vo[3], dU;
+    int64_t ot;
+    const int64_t sv = merge_core(i, j, x + 3 * i, v + 3 * i, x + 3 * j, v + 3 * j, m, R, S, G,
+                                  xo, vo, &ot, &dU);
+    for (int k = 0; k < 3; k++) { x[3 * sv + k] = xo[k]; v[3 * sv + k] = vo[k]; }
+    if (survivor) *survivor = sv;
+    return dU;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Bulirsch-Stoer integration of one close-encounter group (R9, R10).
  * The group's ODE (Eq. Ha restricted to the group):
  *   dx_i/dt = v_i
@@ -398,6 +480,7 @@ typedef struct bs_group {
     const double *const *rcl; /* rc of levels 0..L (global arrays) */
     int nlev;              /* L+1 */
     double G, mu;
+    const unsigned char *alive; /* collisions (R25): bodies merged away feel only the star; or NULL */
 } bs_group;
 
 static void bs_deriv(const bs_group *g, const double *y, double *f)
@@ -411,9 +494,11 @@ static void bs_deriv(const bs_group *g, const double *y, double *f)
         double ax = s * xa[0], ay = s * xa[1], az = s * xa[2];
         double px = 0.0, py = 0.0, pz = 0.0;
         int64_t ia = g->mem[a];
-        for (int64_t q = g->poff[a]; q < g->poff[a + 1]; q++) {
+        const int64_t q1 = (g->alive && !g->alive[ia]) ? g->poff[a] : g->poff[a + 1];
+        for (int64_t q = g->poff[a]; q < q1; q++) {
             int64_t b = g->plist[q];
             int64_t ib = g->mem[b];
+            if (g->alive && !g->alive[ib]) continue;   /* merged away: no mass */
             const double *xb = y + 6 * b;
             double dx = xb[0] - xa[0], dy = xb[1] - xa[1], dz = xb[2] - xa[2];
             double d2 = (dx * dx + dy * dy) + dz * dz;
@@ -457,9 +542,67 @@ static void bs_midpoint(const bs_group *g, const double *y0, const double *f0, d
 
 #define BS_KMAX 8
 
-/* Integrates y (6 nm values) over dt.  Returns 0, or 1 on hitting max_steps. */
+/* Deepest overlap (R_i + R_j - r_ij)/(R_i + R_j) over the group's pairs of
+ * alive bodies in state y; *any = 1 if some pair overlaps (R25).              */
+static double group_overlap(const bs_group *g, const coll_ctx *cc, const double *y, int *any)
+{
+    double deepest = 0.0;
+    *any = 0;
+    for (int64_t a = 0; a < g->nm; a++) {
+        const int64_t ia = g->mem[a];
+        if (!cc->alive[ia]) continue;
+        for (int64_t q = g->poff[a]; q < g->poff[a + 1]; q++) {
+            const int64_t b = g->plist[q], ib = g->mem[b];
+            if (b <= a || !cc->alive[ib]) continue;
+            const double dx = y[6 * b] - y[6 * a], dy = y[6 * b + 1] - y[6 * a + 1],
+                         dz = y[6 * b + 2] - y[6 * a + 2];
+            const double r = sqrt((dx * dx + dy * dy) + dz * dz);
+            const double Rs = cc->R[ia] + cc->R[ib];
+            if (r < Rs) {
+                *any = 1;
+                const double f = (Rs - r) / Rs;
+                if (f > deepest) deepest = f;
+            }
+        }
+    }
+    return deepest;
+}
+
+/* Mergers of the overlapping pairs of alive bodies in state y at time t of the
+ * BS call, in ascending pair order, each seeing the mergers before it (R25). */
+static void group_merge(const bs_group *g, coll_ctx *cc, double *y, double t)
+{
+    for (int64_t a = 0; a < g->nm; a++) {
+        for (int64_t q = g->poff[a]; q < g->poff[a + 1]; q++) {
+            const int64_t ia = g->mem[a];
+            const int64_t b = g->plist[q], ib = g->mem[b];
+            if (b <= a || !cc->alive[ia] || !cc->alive[ib]) continue;
+            const double dx = y[6 * b] - y[6 * a], dy = y[6 * b + 1] - y[6 * a + 1],
+                         dz = y[6 * b + 2] - y[6 * a + 2];
+            const double r = sqrt((dx * dx + dy * dy) + dz * dz);
+            const double Rs = cc->R[ia] + cc->R[ib];
+            if (!(r < Rs)) continue;
+            double xo[3], vo[3], dU;
+            int64_t ot;
+            const int64_t sv = merge_core(ia, ib, y + 6 * a, y + 6 * a + 3, y + 6 * b, y + 6 * b + 3,
+                                          cc->m, cc->R, cc->S, cc->G, xo, vo, &ot, &dU);
+            double *ys = y + 6 * (sv == ia ? a : b);
+            for (int k = 0; k < 3; k++) { ys[k] = xo[k]; ys[3 + k] = vo[k]; }
+            if (cc->log && cc->ncoll < cc->log_cap) {
+                double *e = cc->log + 6 * cc->ncoll;
+                e[0] = cc->t0 + t; e[1] = (double)ia; e[2] = (double)ib; e[3] = r; e[4] = Rs; e[5] = dU;
+            }
+            cc->alive[ot] = 0;
+            cc->U += dU;
+            cc->ncoll++;
+        }
+    }
+}
+
+/* Integrates y (6 nm values) over dt.  Returns 0, or 1 on hitting max_steps.
+ * With cc, collisions (R25) are resolved on the way.                         */
 static int bs_integrate(const bs_group *g, double *y, double dt, double tol, int max_steps,
-                        int64_t *n_acc, int64_t *n_rej, int64_t *max_att)
+                        int64_t *n_acc, int64_t *n_rej, int64_t *max_att, coll_ctx *cc)
 {
     int64_t d = 6 * g->nm;
     double *f0 = (double *)malloc(sizeof(double) * (size_t)d);
@@ -471,6 +614,7 @@ static int bs_integrate(const bs_group *g, double *y, double dt, double tol, int
     double *sc = (double *)malloc(sizeof(double) * (size_t)d);
     double t = 0.0, H = dt;
     int attempts = 0, status = 0;
+    if (cc) group_merge(g, cc, y, 0.0);       /* pairs overlapping at the start */
     while (t < dt) {
         if (attempts >= max_steps) { status = 1; break; }
         attempts++;
@@ -502,11 +646,18 @@ static int bs_integrate(const bs_group *g, double *y, double dt, double tol, int
             }
             if (k >= 1 && err <= tol) { accepted = 1; kconv = k; break; }
         }
+        if (accepted && cc && cc->tol > 0.0) {
+            /* collision precision: an overlap of tol or more ends the step too late */
+            int any = 0;
+            const double f = group_overlap(g, cc, T + (size_t)kconv * (size_t)d, &any);
+            if (any && f >= cc->tol) accepted = 0;
+        }
         if (accepted) {
             for (int64_t c = 0; c < d; c++) y[c] = T[kconv * d + c];
             t += H;
             (*n_acc)++;
             if (kconv < 4) H *= 1.5;
+            if (cc) group_merge(g, cc, y, t);
         } else {
             (*n_rej)++;
             H *= 0.5;
@@ -527,6 +678,7 @@ typedef struct step_ctx {
     double *rcl[ORC_MAX_LEVELS];  /* rc of each level (full-length arrays) */
     orc_stats *st;
     int status;
+    coll_ctx *cc;                 /* collisions (R25), or NULL */
 } step_ctx;
 
 /* Partner lists (CSR) of a pair list that is ascending in (i,j): appending j to
@@ -590,11 +742,13 @@ static void bs_all_groups(step_ctx *cx, int64_t npairs, const uint32_t *pairs, i
                 y[6 * a + 3 + k] = vs[3 * mem[a] + k];
             }
         bs_group g;
-        g.nm = nm; g.mem = mem; g.poff = poff; g.plist = plist; g.m = cx->m;
+        g.nm = nm; g.mem = mem; g.poff = poff; g.plist = plist; g.m = cx->cc ? cx->cc->m : cx->m;
         g.rcl = (const double *const *)cx->rcl; g.nlev = level + 1;
         g.G = cx->p->G; g.mu = cx->p->G * cx->p->m_star;
+        g.alive = cx->cc ? cx->cc->alive : NULL;
         int fail = bs_integrate(&g, y, dt_l, cx->p->bs_tol, cx->p->bs_max_steps,
-                                &cx->st->bs_steps, &cx->st->bs_rejects, &cx->st->bs_max_attempts);
+                                &cx->st->bs_steps, &cx->st->bs_rejects, &cx->st->bs_max_attempts,
+                                cx->cc);
         if (fail) { cx->st->bs_fail++; cx->status |= 2; }
         for (int64_t a = 0; a < nm; a++)
             for (int k = 0; k < 3; k++) {
@@ -882,17 +1036,51 @@ int orc_bs_groups(int64_t n, double *x, double *v, const double *m, const double
     return cx.status;
 }
 
+/* orc_bs_groups with collisions (R25): m, R, S (3 per body) and alive are
+ * updated by the mergers; *U and *ncoll accumulate; log (may be NULL) takes
+ * up to log_cap mergers, 6 doubles each: time in the call, i, j, r_ij,
+ * R_i + R_j, Delta U.                                                        */
+int orc_bs_groups_coll(int64_t n, double *x, double *v, double *m, double *R, double *S,
+                       unsigned char *alive, const double *rc_levels, int nlev, int64_t npairs,
+                       const uint32_t *pairs, double G, double m_star, double dt, double tol,
+                       int max_steps, double coll_tol, double *U, int64_t *ncoll, double *log,
+                       int64_t log_cap, orc_stats *st)
+{
+    orc_params p;
+    memset(&p, 0, sizeof(p));
+    p.G = G; p.m_star = m_star; p.bs_tol = tol; p.bs_max_steps = max_steps;
+    coll_ctx cc;
+    cc.m = m; cc.R = R; cc.S = S; cc.alive = alive; cc.tol = coll_tol; cc.G = G;
+    cc.U = *U; cc.ncoll = *ncoll; cc.log = log; cc.log_cap = log_cap; cc.t0 = 0.0;
+    step_ctx cx;
+    memset(&cx, 0, sizeof(cx));
+    memset(st, 0, sizeof(*st));
+    cx.n = n; cx.x = x; cx.v = v; cx.m = m; cx.p = &p; cx.st = st; cx.cc = &cc;
+    if (nlev < 1 || nlev > ORC_MAX_LEVELS) return -1;
+    for (int l = 0; l < nlev; l++) cx.rcl[l] = (double *)(rc_levels + (size_t)l * (size_t)n);
+    double *xs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *vs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
+    memcpy(vs, v, sizeof(double) * 3 * (size_t)n);
+    bs_all_groups(&cx, npairs, pairs, nlev - 1, dt, xs, vs);
+    free(xs); free(vs);
+    *U = cc.U;
+    *ncoll = cc.ncoll;
+    return cx.status;
+}
+
 /* ------------------------------------------------------------------------- */
 /* One step of Appendix A (original scheme for slevels == 1, SEnc otherwise).
  * Returns 0, or a bit mask: 1 Kepler non-convergence, 2 BS limit reached.    */
 static int step_impl(int64_t n, double *x, double *v, const double *m, const orc_params *p,
                      int64_t nsteps, orc_stats *st, const orc_nn *nn, const double *R,
                      const double *k2, const double *tau, const double *rg2, double *spin,
-                     double *spin_star)
+                     double *spin_star, coll_ctx *cc)
 {
     step_ctx cx;
     memset(&cx, 0, sizeof(cx));
-    cx.n = n; cx.x = x; cx.v = v; cx.m = m; cx.p = p; cx.st = st;
+    cx.n = n; cx.x = x; cx.v = v; cx.m = cc ? cc->m : m; cx.p = p; cx.st = st; cx.cc = cc;
+    if (cc) m = cc->m;
     memset(st, 0, sizeof(*st));
     int L = p->slevels < 1 ? 1 : p->slevels;
     if (L > ORC_MAX_LEVELS) L = ORC_MAX_LEVELS;
@@ -946,16 +1134,32 @@ static int step_impl(int64_t n, double *x, double *v, const double *m, const orc
 int orc_step(int64_t n, double *x, double *v, const double *m, const orc_params *p,
              int64_t nsteps, orc_stats *st)
 {
-    return step_impl(n, x, v, m, p, nsteps, st, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+    return step_impl(n, x, v, m, p, nsteps, st, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* One system with GR and/or tides (R15-R18); spin (3n) and spin_star (3) are
  * updated in place; R, k2, tau, rg2 are per-body arrays (n).                 */
+/* Steps with collisions (R25): m, R, S (3 per body) and alive are updated by
+ * the mergers; *U and *ncoll accumulate; log as for orc_bs_groups_coll, the
+ * time measured from the start of the BS call of the merger.                */
+int orc_step_coll(int64_t n, double *x, double *v, double *m, double *R, double *S,
+                  unsigned char *alive, const orc_params *p, int64_t nsteps, double coll_tol,
+                  double *U, int64_t *ncoll, double *log, int64_t log_cap, orc_stats *st)
+{
+    coll_ctx cc;
+    cc.m = m; cc.R = R; cc.S = S; cc.alive = alive; cc.tol = coll_tol; cc.G = p->G;
+    cc.U = *U; cc.ncoll = *ncoll; cc.log = log; cc.log_cap = log_cap; cc.t0 = 0.0;
+    const int status = step_impl(n, x, v, m, p, nsteps, st, NULL, NULL, NULL, NULL, NULL, NULL, NULL, &cc);
+    *U = cc.U;
+    *ncoll = cc.ncoll;
+    return status;
+}
+
 int orc_step_nn(int64_t n, double *x, double *v, const double *m, const orc_params *p,
                 const orc_nn *nn, const double *R, const double *k2, const double *tau,
                 const double *rg2, double *spin, double *spin_star, int64_t nsteps, orc_stats *st)
 {
-    return step_impl(n, x, v, m, p, nsteps, st, nn, R, k2, tau, rg2, spin, spin_star);
+    return step_impl(n, x, v, m, p, nsteps, st, nn, R, k2, tau, rg2, spin, spin_star, NULL);
 }
 
 /* Total angular momentum with spins: sum m_i x_i x v_i + sum I_i W_i + I_s W_s. */
@@ -1187,7 +1391,7 @@ static int frozen_step(int64_t n, double *x, double *v, const double *m, const o
             bs_group g;
             g.nm = 1; g.mem = &mem; g.poff = poff; g.plist = &plist; g.m = m;
             const double *rcl[1] = {rc};
-            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu;
+            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu; g.alive = NULL;
             tl_group ctx; ctx.g = g; ctx.dm = dm;
             double y[12];
             for (int k = 0; k < 3; k++) {
@@ -1223,7 +1427,7 @@ static int frozen_step(int64_t n, double *x, double *v, const double *m, const o
             bs_group g;
             const double *rcl[1] = {rc};
             g.nm = nm; g.mem = mem; g.poff = poff; g.plist = plist; g.m = m;
-            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu;
+            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu; g.alive = NULL;
             int64_t dim = dx ? 12 * nm : 6 * nm;
             double *y = (double *)malloc(sizeof(double) * (size_t)dim);
             for (int64_t a = 0; a < nm; a++)
@@ -1241,7 +1445,7 @@ static int frozen_step(int64_t n, double *x, double *v, const double *m, const o
                 fail = bs_generic(tl_group_deriv, &ctx, y, dim, 6 * nm, dt, p->bs_tol, p->bs_max_steps);
             } else {
                 int64_t a1 = 0, r1 = 0, m1 = 0;
-                fail = bs_integrate(&g, y, dt, p->bs_tol, p->bs_max_steps, &a1, &r1, &m1);
+                fail = bs_integrate(&g, y, dt, p->bs_tol, p->bs_max_steps, &a1, &r1, &m1, NULL);
             }
             if (fail) status |= 2;
             for (int64_t a = 0; a < nm; a++)
