@@ -399,7 +399,7 @@ def run_reference(args, dist: Dist) -> dict | None:
             "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded planetesimal disk)",
-            "config": {"workload": f"disk N={n} (65536 planetesimals 0.5-4 AU, 5 M_earth, "
+            "config": {"workload": f"disk N={n} ({n - 4} planetesimals 0.5-4 AU, 5 M_earth, "
                                    f"+4 embryos 0.1 M_earth), dt=6.0875 d, 2 levels x 10 substeps",
                        "n_bodies": n},
             "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
