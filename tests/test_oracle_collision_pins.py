@@ -137,3 +137,18 @@ def test_steps_with_mergers_conserve_mass_and_angular_momentum():
     inside = log[:, 0] > 0.0
     assert inside.any()
     assert np.all((log[inside, 4] - log[inside, 3]) / log[inside, 4] < 1e-3)
+
+
+def test_mergers_with_two_levels():
+    """The same disk under the two-level scheme (Sec. 6.3): the deepest level's BS
+    resolves the collisions; mass and angular momentum stay conserved."""
+    wl = disk(160, 0.9, 1.1, 2.0, 31, name="ring-like", slevels=2, substeps=10)
+    R = np.full(wl.n, 3e-3)
+    p = O.make_params(wl, nthreads=4)
+    x, v, m, R1, S1, alive, U, log, status, st = O.step_coll(wl.x, wl.v, wl.m, R, np.zeros((wl.n, 3)),
+                                                           p, 8, coll_tol=1e-3)
+    assert status == 0 and len(log) >= 1 and st["n_pairs"][1] > 0
+    assert m.sum() == pytest.approx(wl.m.sum(), rel=1e-15)
+    L0 = (wl.m[:, None] * np.cross(wl.x, wl.v)).sum(axis=0)
+    L1 = (m[:, None] * np.cross(x, v)).sum(axis=0) + S1.sum(axis=0)
+    np.testing.assert_allclose(L1, L0, rtol=1e-12, atol=1e-12 * np.abs(L0).max())
