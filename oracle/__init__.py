@@ -8,10 +8,10 @@ silent.
 """
 from .core import (OracleNN, OracleParams, OracleStats, accel, accel_rows, angmom_spin, bs_groups,
                    bs_groups_coll, build, changeover, detect, drift, energy, group, hc, kick, lib,
-                   make_nn, make_params, merge, precheck, rcrit, step, step_coll, step_frozen,
-                   step_nn, step_record)
+                   level_force_parts, make_nn, make_params, merge, precheck, rcrit, step, step_coll,
+                   step_frozen, step_nn, step_record)
 
 __all__ = ["OracleNN", "OracleParams", "OracleStats", "accel", "accel_rows", "angmom_spin",
            "bs_groups", "bs_groups_coll", "build", "changeover", "detect", "drift", "energy",
-           "group", "hc", "kick", "lib", "make_nn", "make_params", "merge", "precheck", "rcrit",
+           "group", "hc", "kick", "level_force_parts", "lib", "make_nn", "make_params", "merge", "precheck", "rcrit",
            "step", "step_coll", "step_frozen", "step_nn", "step_record"]

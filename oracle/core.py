@@ -71,6 +71,8 @@ def lib():
             L.orc_accel_rows.argtypes = [C.c_int64, _D, _D, _D, C.c_double, _I64, C.c_int64, _D,
                                          C.c_int]
             L.orc_kick.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D, C.c_int]
+            L.orc_level_force_parts.argtypes = [C.c_int64, _D, _D, _D, C.c_int, C.c_int64, _U32,
+                                                C.c_double, _D, _D, _D]
             L.orc_precheck.restype = C.c_int64
             L.orc_precheck.argtypes = [C.c_int64, _D, _D, C.c_double, _U32, C.c_int64]
             L.orc_precheck_tp.restype = C.c_int64
@@ -172,6 +174,26 @@ def kick(x, v, m, rc, G, dt_half, nthreads: int = 1) -> np.ndarray:
     v = _f64(v).copy()
     lib().orc_kick(m.shape[0], _d(x), _d(m), _d(rc), G, dt_half, _d(v), nthreads)
     return v
+
+
+def level_force_parts(x, m, rc_levels, pairs, G):
+    """The oracle's level split of the pair accelerations (test hook): returns
+    (kick (n,3), kickS (nlev-1, n, 3), bs (n,3)) for the ascending pair list
+    `pairs` (k, 2) used at every level; rc_levels (nlev, n)."""
+    x = _f64(x)
+    m = _f64(m)
+    rc_levels = _f64(rc_levels)
+    nlev, n = rc_levels.shape
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    pp = pairs if len(pairs) else np.zeros((1, 2), dtype=np.uint32)
+    ak = np.zeros((n, 3))
+    aks = np.zeros((max(nlev - 1, 1), n, 3))
+    ab = np.zeros((n, 3))
+    rc = lib().orc_level_force_parts(n, _d(x), _d(m), _d(rc_levels), nlev, len(pairs),
+                                     pp.ctypes.data_as(_U32), G, _d(ak), _d(aks), _d(ab))
+    if rc != 0:
+        raise ValueError("orc_level_force_parts: bad pair list or level count")
+    return ak, aks[:nlev - 1], ab
 
 
 def precheck(x, rc, f_pc, n_massive=None) -> np.ndarray:

@@ -1036,6 +1036,75 @@ int orc_bs_groups(int64_t n, double *x, double *v, const double *m, const double
     return cx.status;
 }
 
+/* Test hook for the level split of the pair forces (Sec. 6.3, Appendix A):
+ * with one ascending pair list used at every level, the parts of each body's
+ * acceleration that the step's own routines give --
+ *   acc_kick  (3n): the level-0 Kick over all pairs (factor K_0; orc_accel),
+ *   acc_kicks ((nlev-1) x 3n): KickS at levels l = 1..nlev-1 over the list
+ *             (factor prod_{k<l} (1 - K_k) K_l; kick_pairs, from v = 0 with
+ *             dt_half = 1),
+ *   acc_bs    (3n): the pair part of the Bulirsch-Stoer derivative at the
+ *             deepest level (factor prod_{k<nlev} (1 - K_k); bs_deriv with the
+ *             star term off, all bodies one group).
+ * rc_levels: nlev x n.  When the list holds every pair, the parts sum to the
+ * Newtonian pair acceleration.  Returns 0, or -1 for a bad list or nlev.     */
+int orc_level_force_parts(int64_t n, const double *x, const double *m, const double *rc_levels,
+                          int nlev, int64_t npairs, const uint32_t *pairs, double G,
+                          double *acc_kick, double *acc_kicks, double *acc_bs)
+{
+    if (nlev < 1 || nlev > ORC_MAX_LEVELS || n < 1) return -1;
+    orc_accel(n, x, m, rc_levels, G, acc_kick, 1);
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * npairs + 1));
+    if (build_partners(n, npairs, pairs, off, list) != 0) { free(off); free(list); return -1; }
+    orc_params p;
+    memset(&p, 0, sizeof(p));
+    p.G = G;
+    orc_stats st;
+    memset(&st, 0, sizeof(st));
+    step_ctx cx;
+    memset(&cx, 0, sizeof(cx));
+    double *xw = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *vw = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    memcpy(xw, x, sizeof(double) * 3 * (size_t)n);
+    cx.n = n; cx.x = xw; cx.v = vw; cx.m = m; cx.p = &p; cx.st = &st;
+    for (int l = 0; l < nlev; l++) cx.rcl[l] = (double *)(rc_levels + (size_t)l * (size_t)n);
+    /* KickS bodies and partner lists as groupS builds them */
+    int64_t nb = 0;
+    for (int64_t i = 0; i < n; i++) nb += off[i + 1] > off[i];
+    int64_t *bodies = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb > 0 ? nb : 1));
+    int64_t *poff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nb + 1));
+    for (int64_t i = 0, c = 0; i < n; i++) if (off[i + 1] > off[i]) bodies[c++] = i;
+    poff[0] = 0;
+    for (int64_t a = 0; a < nb; a++) poff[a + 1] = poff[a] + (off[bodies[a] + 1] - off[bodies[a]]);
+    int64_t *plist = (int64_t *)malloc(sizeof(int64_t) * (size_t)(poff[nb] > 0 ? poff[nb] : 1));
+    for (int64_t a = 0; a < nb; a++)
+        for (int64_t q = off[bodies[a]], c = 0; q < off[bodies[a] + 1]; q++, c++)
+            plist[poff[a] + c] = list[q];
+    for (int l = 1; l < nlev; l++) {
+        memset(vw, 0, sizeof(double) * 3 * (size_t)n);
+        kick_pairs(&cx, nb, bodies, poff, plist, l, 1.0);
+        memcpy(acc_kicks + (size_t)(l - 1) * 3 * (size_t)n, vw, sizeof(double) * 3 * (size_t)n);
+    }
+    /* Bulirsch-Stoer derivative: every body a member (local = global index) */
+    int64_t *mem = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; i++) mem[i] = i;
+    double *y = (double *)calloc(6 * (size_t)n, sizeof(double));
+    double *f = (double *)malloc(sizeof(double) * 6 * (size_t)n);
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) y[6 * i + k] = x[3 * i + k];
+    bs_group g;
+    g.nm = n; g.mem = mem; g.poff = off; g.plist = list; g.m = m;
+    g.rcl = (const double *const *)cx.rcl; g.nlev = nlev;
+    g.G = G; g.mu = 0.0; g.alive = NULL;
+    bs_deriv(&g, y, f);
+    for (int64_t i = 0; i < n; i++)
+        for (int k = 0; k < 3; k++) acc_bs[3 * i + k] = f[6 * i + 3 + k];
+    free(f); free(y); free(mem); free(plist); free(poff); free(bodies);
+    free(vw); free(xw); free(list); free(off);
+    return 0;
+}
+
 /* orc_bs_groups with collisions (R25): m, R, S (3 per body) and alive are
  * updated by the mergers; *U and *ncoll accumulate; log (may be NULL) takes
  * up to log_cap mergers, 6 doubles each: time in the call, i, j, r_ij,
