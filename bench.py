@@ -44,7 +44,6 @@ UNIT = "Gpair/s"
 # displacement 3, r^2 3, r^-1 to FP64 precision (two Newton steps from a
 # ~2^-22 seed) 6, m r^-3 3, accumulation 3.
 FP64_OPS_PER_PAIR = {"mixed": 7, "fp64": 18}
-FP64_OPS_PER_CLK_PER_SM = 2      # measured DFMA throughput per SM per clock on GB300
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed kick launch at
 # N = 65,540 (one ncu capture of the kernel as it is now); None when the
 # kernel has changed since the capture
@@ -54,21 +53,26 @@ KICK_MIXED_DRAM_BYTES = 2.940416e6 + 1.733376e6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=65536, help="planetesimals (embryos: 4 more)")
     ap.add_argument("--kick-reps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip e2e/cpu/fp64 legs (profiling runs)")
-    ap.add_argument("--workload", choices=["disk", "ensemble", "adjoint", "variants", "tp"], default="disk",
+    ap.add_argument("--workload", choices=["disk", "ensemble", "adjoint", "variants", "tp", "kick"],
+                    default="disk",
                     help="disk: the N=65,540 disk (headline); ensemble: 4096 compact systems "
                          "with GR and tides; adjoint: the 1000-step adjoint at N=4096; "
                          "variants: FP64 vs mixed on the N=16,384 disk (one level) and the "
                          "N=65,540 disk at other (levels, sub-steps); tp: the N=65,540 disk "
-                         "with 4,096 large bodies and semi-active test particles")
-    ap.add_argument("--ens-steps", type=int, default=1000,
-                    help="integration steps per timed ensemble launch")
+                         "with 4,096 large bodies and semi-active test particles; kick: the "
+                         "all-pairs kick alone on a disk of --n planetesimals (0.5-4 AU, "
+                         "5 M_earth), --kick-reps timed launches in the form --kick")
+    ap.add_argument("--kick", choices=["fp64", "mixed"], default="mixed",
+                    help="kick form of --workload kick")
+    ap.add_argument("--ens-steps", type=int, default=10000,
+                    help="integration steps per timed ensemble launch (the configuration's 10,000)")
     ap.add_argument("--energy-run", type=int, default=0,
                     help="instead of timing: integrate this many steps in FP64 and mixed and "
                          "report the relative energy error every 100 steps")
@@ -201,6 +205,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     mass = torch.tensor(wl.m, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    rates = genga.measure_pipe_rates()      # FP64 / FP32 / MUFU ops per clock per SM
 
     def params(prec):
         return genga.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2,
@@ -210,6 +215,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     results = {}
     clocks = None
     launches = 0
+    final_state = None
     precisions = ["mixed"] if args.quick else ["fp64", "mixed"]
     for name in precisions:
         prec = genga.GENGA_MIXED if name == "mixed" else genga.GENGA_FP64
@@ -224,8 +230,9 @@ def run_ours(args, dist: Dist) -> dict | None:
             sampler.start()
         dist.barrier()
         torch.cuda.synchronize()
-        total_ms = 0.0
+        per_step = []
         nl = 0
+        syncs = 0
         for _ in range(args.steps):
             flush.fill_(1.0)                      # L2 flush between timed steps (untimed)
             torch.cuda.synchronize()
@@ -235,11 +242,16 @@ def run_ours(args, dist: Dist) -> dict | None:
             sysm.step(1)
             e1.record(stream)
             e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
-            nl += sysm.stats()["kernel_launches"]
+            per_step.append(e0.elapsed_time(e1))
+            st = sysm.stats()
+            nl += st["kernel_launches"]
+            syncs += st["host_syncs"]
         torch.cuda.synchronize()
         dist.barrier()
+        total_ms = sum(per_step)
         stats = sysm.stats()
+        if name == "mixed":
+            final_state = (pos.cpu().numpy().copy(), vel.cpu().numpy().copy())
         E_end, _ = sysm.energy()
         # kick kernel alone (the dominant kernel), same launch configuration
         sysm.rcrit(wl.dt)
@@ -256,6 +268,23 @@ def run_ours(args, dist: Dist) -> dict | None:
         if sampler:
             clocks = sampler.stop()
         t_max = dist.max(total_ms)
+        sysm.close()
+        # where the time goes: the same step window again on a new system,
+        # with CUDA events at the phase boundaries of each step (kept out of
+        # the timed steps above, whose time they would add to)
+        pos, vel = x0.clone(), v0.clone()
+        sysm = genga.System(pos, vel, mass, params(prec), stream=stream)
+        for _ in range(args.warmup):
+            sysm.step(1)
+        sysm.set_timing(True)
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            sysm.step(1)
+        phases, nph = sysm.phase_ms()
+        sysm.set_timing(False)
+        ph_step = {k: v / max(nph, 1) for k, v in phases.items()}
+        kick_ph = ph_step["kick1"] + ph_step["kick2"]
         results[name] = {
             "ms_per_step": t_max / args.steps,
             "gpairs_per_s": replica_throughput(dist.world, pairs_per_step, args.steps, t_max) / 1e9,
@@ -264,6 +293,22 @@ def run_ours(args, dist: Dist) -> dict | None:
             "kick_gpairs_per_s": n * (n - 1) / (kick_ms * 1e-3) / 1e9,
             "kick_share": 2 * kick_ms / (total_ms / args.steps),
             "energy_rel_err": abs(E_end - E_start) / abs(E_start),
+            "per_step": {"min_ms": round(min(per_step), 3),
+                         "median_ms": round(statistics.median(per_step), 3),
+                         "max_ms": round(max(per_step), 3),
+                         "ms": [round(v, 3) for v in per_step]},
+            "phases": {"ms_per_step": {k: round(v, 4) for k, v in ph_step.items()},
+                       "sum_ms_per_step": round(sum(ph_step.values()), 3),
+                       "kick_ms_per_step": round(kick_ph, 3),
+                       "non_kick_ms_per_step": round(sum(ph_step.values()) - kick_ph, 3),
+                       "non_kick_share": round(1.0 - kick_ph / max(sum(ph_step.values()), 1e-9), 4),
+                       "host_syncs_per_step": syncs / args.steps,
+                       "launches_per_step": nl / args.steps,
+                       "definition": "device time between CUDA events recorded on the system's "
+                                     "stream at the phase boundaries of each step of the same "
+                                     "step window (warm-up and timed counts as above), in a "
+                                     "separate untimed pass; includes the GPU's waits for the "
+                                     "host inside a phase"},
             "encounters": {"candidates_per_step": stats["n_candidates"],
                            "pairs_level0": stats["n_pairs"][0],
                            "pairs_level1": stats["n_pairs"][1],
@@ -274,7 +319,9 @@ def run_ours(args, dist: Dist) -> dict | None:
             launches = nl
         sysm.close()
 
-    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    # e2e through the C ABI with host buffers (pinned), copies inside the timed
+    # region: the same warm-up count from the same initial state, so the timed
+    # steps are the same steps as above
     e2e = None
     if not args.quick:
         pos, vel = x0.clone(), v0.clone()
@@ -283,18 +330,29 @@ def run_ours(args, dist: Dist) -> dict | None:
         vh = torch.empty((3, n), dtype=torch.float64).pin_memory()
         xh.copy_(x0.cpu())
         vh.copy_(v0.cpu())
-        sysm.step_host_ptr(xh.data_ptr(), vh.data_ptr(), 1)    # warm-up
+        for _ in range(args.warmup):
+            sysm.step_host_ptr(xh.data_ptr(), vh.data_ptr(), 1)
         torch.cuda.synchronize()
         dist.barrier()
-        t0 = time.perf_counter()
+        te = 0.0
         for _ in range(args.steps):
+            flush.fill_(1.0)                      # untimed, as in the device-timed leg
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             sysm.step_host_ptr(xh.data_ptr(), vh.data_ptr(), 1)
-        t1 = time.perf_counter()
+            te += time.perf_counter() - t0
         dist.barrier()
-        te = dist.max(t1 - t0)
+        te = dist.max(te)
         bytes_each = 2 * 3 * n * 8
+        same = (final_state is not None and np.array_equal(xh.numpy(), final_state[0])
+                and np.array_equal(vh.numpy(), final_state[1]))
         e2e = {"value": dist.world * pairs_per_step * args.steps / te / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": bytes_each, "d2h_bytes_per_step": bytes_each}
+               "h2d_bytes_per_step": bytes_each, "d2h_bytes_per_step": bytes_each,
+               "ms_per_step": round(1e3 * te / args.steps, 3),
+               "same_steps_as_value": bool(same),
+               "timing": "host wall clock around genga_step_host (copy in, step, copy out, "
+                         "synchronise) for each of the same timed steps; L2 flushed between "
+                         "them (untimed)"}
         sysm.close()
 
     if dist.rank != 0:
@@ -302,15 +360,14 @@ def run_ours(args, dist: Dist) -> dict | None:
 
     head = results["mixed"]
     sm_clock = (clocks or {}).get("sm_mhz") or 2070.0
-    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     props = torch.cuda.get_device_properties(dev)
-    peak = FP64_OPS_PER_CLK_PER_SM * props.multi_processor_count * sm_max * 1e6 / 1e9
+    peak = rates["dfma"] * props.multi_processor_count * sm_clock * 1e6 / 1e9
     achieved = FP64_OPS_PER_PAIR["mixed"] * head["kick_gpairs_per_s"]
     line = {
         "metric": METRIC, "value": round(head["gpairs_per_s"], 4), "unit": UNIT,
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(head["ms_per_step"], 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed kick)",
         "data": "synthetic (seeded planetesimal disk, no external data)",
         "config": {"workload": f"disk N={n} (65536 planetesimals 0.5-4 AU, 5 M_earth, "
                                f"+4 embryos 0.1 M_earth), dt=6.0875 d, 2 levels x 10 substeps, "
@@ -320,6 +377,8 @@ def run_ours(args, dist: Dist) -> dict | None:
                    "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": f"replicas x{dist.world}"},
         "steps_per_s": round(head["steps_per_s"], 4),
+        "per_step": head["per_step"],
+        "phases": head["phases"],
         "kick_only": {"mixed_gpairs_per_s": round(head["kick_gpairs_per_s"], 3),
                       "mixed_kick_ms": round(head["kick_ms"], 3),
                       "kick_share_of_step": round(head["kick_share"], 3)},
@@ -331,8 +390,10 @@ def run_ours(args, dist: Dist) -> dict | None:
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
                                        "of this kernel at N=65540",
                      "ops_per_pair": FP64_OPS_PER_PAIR["mixed"],
-                     "peak_basis": f"derived: {FP64_OPS_PER_CLK_PER_SM} FP64 op/clk/SM (measured) x "
-                                   f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz"},
+                     "peak_basis": f"measured in this run: {rates['dfma']:.3f} FP64 FMA/clk/SM "
+                                   f"(genga_measure_pipe_rates) x {props.multi_processor_count} SMs x "
+                                   f"{sm_clock:.0f} MHz (median SM clock under load)",
+                     "pipe_rates_per_clk_sm": {k: round(v, 3) for k, v in rates.items()}},
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         "encounters": head["encounters"],
         "energy": {"rel_err": head["energy_rel_err"], "steps": args.warmup + args.steps,
@@ -341,9 +402,11 @@ def run_ours(args, dist: Dist) -> dict | None:
     }
     if "fp64" in results:
         f = results["fp64"]
-        line["fp64"] = {"value": round(f["gpairs_per_s"], 4), "unit": UNIT,
+        line["fp64"] = {"value": round(f["gpairs_per_s"], 4), "unit": UNIT, "dtype": "f64",
                         "ms_per_step": round(f["ms_per_step"], 3),
                         "steps_per_s": round(f["steps_per_s"], 4),
+                        "per_step": {k: v for k, v in f["per_step"].items() if k != "ms"},
+                        "non_kick_ms_per_step": f["phases"]["non_kick_ms_per_step"],
                         "kick_gpairs_per_s": round(f["kick_gpairs_per_s"], 3),
                         "kick_ms": round(f["kick_ms"], 3),
                         "roofline_frac": round(FP64_OPS_PER_PAIR["fp64"] * f["kick_gpairs_per_s"] / peak, 4),
@@ -452,7 +515,8 @@ def energy_run(args) -> dict:
 
 def run_ensemble(args) -> dict:
     """Configuration 3: 4096 compact systems, GR + tides, one persistent launch per
-    timed step (args.ens_steps integration steps each), tile shape autotuned."""
+    timed step (args.ens_steps integration steps each, 10,000 as configured),
+    tile shape autotuned; the FP64 and the mixed-precision pair kick."""
     import torch
 
     from paper_2201_10058_gb300 import genga
@@ -461,35 +525,48 @@ def run_ensemble(args) -> dict:
     wl = ensemble(4096)
     sizes = np.diff(wl.offsets)
     pairs_per_step = float((2 * sizes * (sizes - 1)).sum())
-    ens = genga.Ensemble(wl, genga.default_params(G=wl.G))
-    threads, ctas = ens.autotune(20)
-    for _ in range(args.warmup):
-        ens.step(args.ens_steps)
-    torch.cuda.synchronize()
+    rates = genga.measure_pipe_rates()
+    sampler = ClockSampler(gpu_uuid(0))
+    sampler.start()
     stream = torch.cuda.current_stream()
-    total = 0.0
-    for _ in range(args.steps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ens.step(args.ens_steps)
-        e1.record(stream)
-        e1.synchronize()
-        total += e0.elapsed_time(e1)
-    st = ens.stats()
-    steps = args.steps * args.ens_steps
+    legs = {}
+    for name, prec in (("fp64", genga.GENGA_FP64), ("mixed", genga.GENGA_MIXED)):
+        ens = genga.Ensemble(wl, genga.default_params(G=wl.G, precision=prec))
+        threads, ctas = ens.autotune(20)
+        for _ in range(args.warmup):
+            ens.step(args.ens_steps)
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ens.step(args.ens_steps)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        st = ens.stats()
+        steps = args.steps * args.ens_steps
+        legs[name] = {"value": round(wl.n_systems * steps / (total * 1e-3), 1), "unit": "system-steps/s",
+                      "ms_per_launch": round(total / args.steps, 3),
+                      "pair_gpairs_per_s": round(pairs_per_step * steps / (total * 1e-3) / 1e9, 3),
+                      "tile": {"threads": threads, "ctas_per_sm": ctas},
+                      "encounters": {"candidates": st["n_candidates"], "pairs": st["n_pairs"][0],
+                                     "groups": st["n_groups"]}}
+        ens.close()
+    clocks = sampler.stop()
+    head = legs["mixed"]
     return {"metric": "ensemble system-steps/s (4096 compact systems, GR + tides)",
-            "value": round(wl.n_systems * steps / (total * 1e-3), 1), "unit": "system-steps/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(total / args.steps, 3), "higher_is_better": True,
-            "dtype": "f64", "data": "synthetic (seeded ensemble)",
+            "value": head["value"], "unit": "system-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_launch"],
+            "higher_is_better": True, "dtype": "f64+f32 (mixed pair kick)",
+            "data": "synthetic (seeded ensemble)",
             "config": {"workload": f"ensemble of {wl.n_systems} systems, N 8-64 (total "
                                    f"{int(wl.offsets[-1])} bodies), GR + tides, "
-                                   f"{args.ens_steps} steps per launch",
-                       "tile": {"threads": threads, "ctas_per_sm": ctas}},
-            "pair_gpairs_per_s": round(pairs_per_step * steps / (total * 1e-3) / 1e9, 3),
-            "encounters": {"candidates": st["n_candidates"], "pairs": st["n_pairs"][0],
-                           "groups": st["n_groups"]}}
+                                   f"{args.ens_steps} steps per launch"},
+            "mixed": head, "fp64": legs["fp64"],
+            "mixed_over_fp64": round(head["value"] / legs["fp64"]["value"], 3),
+            "pipe_rates_per_clk_sm": {k: round(v, 3) for k, v in rates.items()}, "clocks": clocks}
 
 
 def run_adjoint(args) -> dict:
@@ -736,6 +813,44 @@ def run_tp(args) -> dict:
             "max_group": st["max_group"], "clocks": sampler.stop()}
 
 
+def run_kick(args) -> dict:
+    """The all-pairs kick alone (one warm-up launch, then --kick-reps timed
+    launches) on a disk of --n planetesimals, in the form --kick."""
+    import torch
+
+    from paper_2201_10058_gb300 import genga
+    from workloads import disk
+    from workloads.disk import SEED_BASE
+
+    dev = torch.device("cuda", 0)
+    genga.load()
+    stream = torch.cuda.current_stream(dev)
+    wl = disk(args.n, 0.5, 4.0, 5.0, SEED_BASE + 2, name=f"disk{args.n}")
+    pos = torch.tensor(np.ascontiguousarray(wl.x.T), device=dev)
+    vel = torch.tensor(np.ascontiguousarray(wl.v.T), device=dev)
+    mass = torch.tensor(wl.m, device=dev)
+    prec = genga.GENGA_MIXED if args.kick == "mixed" else genga.GENGA_FP64
+    p = genga.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc,
+                             precision=prec)
+    sysm = genga.System(pos, vel, mass, p, stream=stream)
+    sysm.rcrit(wl.dt)
+    sysm.kick(0.0, precheck=False)
+    torch.cuda.synchronize()
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(args.kick_reps):
+        sysm.kick(0.0, precheck=False)
+    k1.record(stream)
+    k1.synchronize()
+    ms = k0.elapsed_time(k1) / args.kick_reps
+    sysm.close()
+    n = wl.n
+    return {"metric": "all-pairs changeover kick alone (secondary measurement)", "kick": args.kick,
+            "n_bodies": n, "launches": args.kick_reps, "ms_per_launch": round(ms, 4),
+            "gpairs_per_s": round(n * (n - 1) / (ms * 1e-3) / 1e9, 3)}
+
+
 def _recording(s):
     """Host copies of a system's recorded rc history and pair lists."""
     return s.adjoint_export()
@@ -748,6 +863,9 @@ def main():
         return
     if args.workload == "tp" and args.impl == "ours":
         print(json.dumps(run_tp(args)))
+        return
+    if args.workload == "kick" and args.impl == "ours":
+        print(json.dumps(run_kick(args)))
         return
     if args.workload == "variants" and args.impl == "ours":
         print(json.dumps(run_variants(args)))

@@ -57,7 +57,7 @@ typedef struct genga_params {
     double n1;         /* Eq. rcrit: Hill-radius factor (paper: 3) */
     double n2;         /* Eq. rcrit: velocity factor (paper: 0.4) */
     double f_pc;       /* pre-check factor: candidates have r_ij < f_pc * rc_ij (default 4) */
-    double bs_tol;     /* Bulirsch-Stoer relative tolerance (default 1e-15) */
+    double bs_tol;     /* Bulirsch-Stoer relative tolerance (default 1e-13) */
     int32_t slevels;   /* symplectic levels, Sec. 6.3 / Appendix A (1 = original method) */
     int32_t substeps;  /* sub-steps per level (time-step reduction factor per level) */
     int32_t precision; /* GENGA_FP64 or GENGA_MIXED for the all-pairs kick */
@@ -87,6 +87,7 @@ typedef struct genga_stats {
     int64_t bs_fail;         /* groups that hit bs_max_steps */
     int64_t kernel_launches; /* CUDA kernels this library launched for these steps */
     int64_t bs_max_attempts; /* most step attempts any one group needed */
+    int64_t host_syncs;      /* times the host waited for the stream inside these steps */
 } genga_stats_t;
 
 typedef struct genga_system genga_system_t;
@@ -98,7 +99,10 @@ void genga_default_params(genga_params_t *p);
 /* Creates a system of n bodies on the CUDA stream `stream` (a cudaStream_t;
  * NULL = legacy default stream) of the current device.  pos and vel (3n
  * doubles each) and mass (n doubles) are caller-owned device arrays that must
- * outlive the system.  Allocates all library scratch.  Errors: EINVAL, ENOMEM. */
+ * outlive the system.  Allocates all library scratch.  Errors: EINVAL, ENOMEM.
+ * genga_create is the same call under its earlier name.                     */
+int genga_init_system(genga_system_t **out, const genga_params_t *p, int64_t n, double *pos,
+                      double *vel, const double *mass, void *stream);
 int genga_create(genga_system_t **out, const genga_params_t *p, int64_t n, double *pos,
                  double *vel, const double *mass, void *stream);
 
@@ -210,6 +214,135 @@ int genga_set_predrift(genga_system_t *sys, const double *pos_host, const double
 /* Counters of the last genga_step (or of the last build_encounters / bs).   */
 int genga_get_stats(genga_system_t *sys, genga_stats_t *st);
 
+/* ---- collisions (Sec. 7.1-7.2) -------------------------------------------- */
+/* Switches collision handling on.  Collisions are found inside the
+ * Bulirsch-Stoer integration of the close-encounter groups, at the end of
+ * every accepted step, over the group's encounter pairs whose bodies are both
+ * alive: bodies i and j collide when r_ij < R_i + R_j.  With a collision
+ * precision p > 0 (Sec. 7.2, in units of the radius sum) a step that ends with
+ * an overlap (R_i + R_j - r_ij)/(R_i + R_j) >= p is rejected and halved, so a
+ * merger happens at an overlap below p; p = 0 merges at the first overlapping
+ * step.  Pairs overlapping when a group's integration starts merge at once;
+ * overlapping pairs merge in ascending (i, j) order, each seeing the mergers
+ * before it.  A merger is perfectly inelastic (Sec. 7.1): the survivor is the
+ * more massive body (equal masses: the lower index), it takes the
+ * mass-weighted position and velocity, the summed mass and R^3, and the spin
+ * S_i + S_j + mu (r_ij x v_ij) (mu = m_i m_j / (m_i + m_j)); the collision
+ * energy U grows by mu |v_ij|^2 / 2 - G m_i m_j / r_ij.  The other body keeps its
+ * position and velocity with mass, radius and spin 0 and is no longer alive:
+ * it exerts no force, inside a group it feels only the star, and it never
+ * collides again (genga_remove_merged takes such bodies out).
+ *   mass    the system's mass array (the same pointer as at creation), now
+ *           written by mergers;
+ *   radius  n radii (device, caller-owned, written by mergers);
+ *   spin    3n spin vectors, component-major like pos (device, caller-owned,
+ *           written by mergers; may hold zeros).
+ * All bodies start alive.  Errors: EINVAL (mass is not the system's, NULL
+ * radius or spin, p < 0), ENOMEM.                                            */
+int genga_set_collisions(genga_system_t *sys, double *mass, double *radius, double *spin,
+                         double precision);
+
+/* The mergers since the previous call (or since genga_set_collisions), in the
+ * order of the integration (Bulirsch-Stoer calls in time order; within one
+ * call, groups by ascending smallest member, each group's mergers in time
+ * order), 6 doubles each: time within its Bulirsch-Stoer call, i, j, r_ij,
+ * R_i + R_j, Delta U.  log (host, 6 cap doubles) may be NULL; *n (may be NULL)
+ * receives the count, *dU (may be NULL) the sum of their Delta U, added in that
+ * order.  When log is not NULL the records are copied and the device log is
+ * cleared; with log NULL the call only reports (a size query).
+ * Synchronises.  Errors: EINVAL, ECAPACITY (cap too small: nothing copied or
+ * cleared, *n set).                                                         */
+int genga_get_mergers(genga_system_t *sys, double *log, int64_t cap, int64_t *n, double *dU);
+
+/* Host copy of the alive flags (n bytes, 1 alive, 0 merged away).  Synchronises. */
+int genga_get_alive(genga_system_t *sys, uint8_t *alive);
+
+/* Takes the merged-away bodies out: pos, vel, mass, radius and spin are
+ * compacted in place on the device (alive bodies keep their order) and the
+ * system's body count becomes the number of alive bodies, *n_new.  old_index
+ * (host, may be NULL, n_new int64 values) receives each new body's former
+ * index.  The critical radii and encounter lists are recomputed by the next
+ * step.  Synchronises.  Errors: EINVAL (collisions not on).                 */
+int genga_remove_merged(genga_system_t *sys, int64_t *n_new, int64_t *old_index);
+
+/* ---- bounded device waits ------------------------------------------------ */
+/* Every wait and loop on the device is bounded, so that a stuck integration
+ * returns an error instead of holding the GPU.  Two of the bounds are wall
+ * clock limits:
+ *   bs_group_seconds  one group's in-block Bulirsch-Stoer integration over a
+ *                     (sub-)step (groups of up to 32 members); default 10 s;
+ *   barrier_seconds   one grid-barrier wait of the persistent Bulirsch-Stoer
+ *                     kernel (groups of more than 32 members); default 2 s.
+ * A negative value restores the default; 0 makes the first check run out.
+ * When a limit is reached the call returns GENGA_ETIMEOUT with a message, the
+ * integration of that step stops (the state is left partly advanced), and
+ * the system stays usable.  barrier_absent_blocks is a test hook: with n > 0
+ * every grid barrier waits for n blocks that do not exist, so every wait
+ * runs out after barrier_seconds (0 in normal use).  Errors: EINVAL.        */
+int genga_set_wait_limits(genga_system_t *sys, double bs_group_seconds, double barrier_seconds,
+                          int32_t barrier_absent_blocks);
+
+/* ---- detection log (verification) --------------------------------------- */
+/* With the log on, every close-encounter detection of genga_step and
+ * genga_build_encounters (Appendix A "close-encounter detection": level 0
+ * once per step, level l >= 1 once per sub-step) appends its level and its
+ * encounter pairs, sorted ascending by (i, j), to a host-side log -- for
+ * comparing the pair lists of whole steps with another implementation.
+ * Logging copies each list to the host and synchronises; it does not change
+ * the integration.  genga_set_pair_log clears the log.                      */
+int genga_set_pair_log(genga_system_t *sys, int enable);
+
+/* Copies the log: level (max_events int32), off (max_events + 1 int64: the
+ * pairs of event k are ij[2 off[k]] .. ij[2 off[k+1] - 1]) and ij (max_pairs
+ * interleaved uint32 pairs); *n_events and *n_pairs (may be NULL) receive the
+ * sizes.  NULL buffers: sizes only.  Errors: EINVAL, ECAPACITY (buffers too
+ * small; sizes still set).                                                  */
+int genga_get_pair_log(genga_system_t *sys, int32_t *level, int64_t *off, uint32_t *ij,
+                       int64_t max_events, int64_t max_pairs, int64_t *n_events, int64_t *n_pairs);
+
+/* ---- phase timing ------------------------------------------------------ */
+/* Where a step's time goes, by the phases of Appendix A.  With timing on,
+ * genga_step records a CUDA event on the system's stream at every phase
+ * boundary and, after each step, adds the device time between consecutive
+ * boundaries to that phase's sum.  An interval includes any time the GPU
+ * waited for the host inside it (a count read, the next launch), so the
+ * phase sums add up to the step's device time.  The Bulirsch-Stoer kernels on
+ * the library's side streams are inside the interval that joins them.
+ * Phases of the higher levels (SEnc) are summed over levels and sub-steps;
+ * with one level, grouping and Bulirsch-Stoer of level 0 go to the same
+ * phases.  Timing synchronises once per step.                               */
+#define GENGA_NPHASES 18
+#define GENGA_PH_RCRIT        0   /* Rcrit(dt) at level 0 */
+#define GENGA_PH_KICK1        1   /* pre-check + first Kick(dt/2) */
+#define GENGA_PH_CANDCOUNT    2   /* candidate count (list regrown on overflow) */
+#define GENGA_PH_HC_DRIFT     3   /* HC(dt/2) + FG(dt) */
+#define GENGA_PH_DETECT0      4   /* level-0 detection + its count */
+#define GENGA_PH_CSR0         5   /* level-0 partner lists */
+#define GENGA_PH_LEVELSETUP   6   /* groupS: level bodies + restore from pre-drift state */
+#define GENGA_PH_RCRITS       7   /* RcritS(dt_l) */
+#define GENGA_PH_KICKS        8   /* KickS(dt_l/2), both halves */
+#define GENGA_PH_FGS          9   /* FGS(dt_l) */
+#define GENGA_PH_DETECTS     10   /* level-l detection + its count */
+#define GENGA_PH_CSRS        11   /* level-l partner lists */
+#define GENGA_PH_GROUPING    12   /* connected components */
+#define GENGA_PH_BUCKETS     13   /* group size buckets + their counts */
+#define GENGA_PH_BS_SMALL    14   /* in-block Bulirsch-Stoer (groups <= 32) */
+#define GENGA_PH_BS_LARGE    15   /* persistent Bulirsch-Stoer (groups > 32) */
+#define GENGA_PH_HC2         16   /* second HC(dt/2) */
+#define GENGA_PH_KICK2       17   /* second Kick(dt/2) */
+
+/* Switches phase timing on (enable != 0) or off; either way the sums are
+ * cleared.  Errors: EINVAL, ECUDA.                                          */
+int genga_set_timing(genga_system_t *sys, int enable);
+
+/* ms (host, GENGA_NPHASES doubles) receives each phase's device time summed
+ * over the steps timed since timing was switched on, *nsteps (may be NULL)
+ * the number of those steps.                                               */
+int genga_get_phase_ms(genga_system_t *sys, double *ms, int64_t *nsteps);
+
+/* Short name of a phase ("kick1", "bs_small", ...); NULL outside [0, GENGA_NPHASES). */
+const char *genga_phase_name(int phase);
+
 /* ---- adjoint of kick-drift-kick steps with frozen encounters ------------ */
 /* Reverse-mode derivative of nsteps steps of the original scheme (Appendix A,
  * slevels = 1) with every step's level-0 critical radii and encounter pairs
@@ -244,6 +377,9 @@ int genga_adjoint_load(genga_system_t *sys, int64_t nsteps, int64_t checkpoint_e
  * final state again on return.  Synchronises.                              */
 int genga_adjoint_backward(genga_system_t *sys, const double *lam_x, const double *lam_v,
                            double *grad_x0, double *grad_v0, double *grad_m);
+/* The same call under the boundary's name for the backward step.           */
+int genga_step_backward(genga_system_t *sys, const double *lam_x, const double *lam_v,
+                        double *grad_x0, double *grad_v0, double *grad_m);
 
 /* Host copies of the current recording: rc_hist (nsteps x n doubles),
  * pair_offsets (nsteps + 1), pairs (up to cap interleaved uint32 pairs, in
@@ -280,6 +416,9 @@ typedef struct genga_ensemble genga_ensemble_t;
  * (bad sizes or pointers), ENOMEM, ECUDA.                                    */
 int genga_ensemble_create(genga_ensemble_t **out, const genga_params_t *params,
                           const genga_ensemble_desc_t *desc, void *stream);
+/* The same call under the boundary's name (genga_init_ensemble).            */
+int genga_init_ensemble(genga_ensemble_t **out, const genga_params_t *params,
+                        const genga_ensemble_desc_t *desc, void *stream);
 void genga_ensemble_destroy(genga_ensemble_t *ens);
 const char *genga_ensemble_last_error(const genga_ensemble_t *ens);
 
@@ -287,6 +426,8 @@ const char *genga_ensemble_last_error(const genga_ensemble_t *ens);
  * (captured in a CUDA graph on first use for each nsteps and tile shape, then
  * replayed).  Synchronises; counters via genga_ensemble_get_stats.          */
 int genga_ensemble_step(genga_ensemble_t *ens, int64_t nsteps);
+/* The same call under the boundary's name (genga_step_ensemble).            */
+int genga_step_ensemble(genga_ensemble_t *ens, int64_t nsteps);
 
 /* Tile shape: threads per CTA (32 only when every system has <= 32 bodies, 64
  * or 128) and resident CTAs per SM (1..8).                                   */
@@ -317,7 +458,10 @@ int genga_ensemble_get_stats(genga_ensemble_t *ens, genga_stats_t *st);
  * every GPU that loads the library until the process exits.  n may be at most
  * GENGA_KICK_STATIC_MAX_N (larger n returns GENGA_ECAPACITY before any launch).
  * The first call on a device looks up that array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current); make that first call before any stream capture.  After a
+ * cudaDeviceReset the next call looks the address up again (the device's new
+ * context loads the library's device code anew), so that call too should
+ * come before any capture.  All calls
  * share the array and it keeps the last call's contents (every call rewrites
  * what it reads); calls that overlap on the GPU race with each other -- issue
  * them on one stream or synchronise between them.  Returns GENGA_OK, EINVAL,
@@ -326,6 +470,19 @@ int genga_ensemble_get_stats(genga_ensemble_t *ens, genga_stats_t *st);
 int genga_kick_static(int64_t n, const double *pos, const double *mass, const double *rc,
                       double G, double dt_half, int precision, double *vel, double *acc_out,
                       void *stream);
+
+/* ---- pipe-rate probe ---------------------------------------------------- */
+/* The paper has no counterpart: a measurement utility for the roofline of the
+ * kernels above.  On the current device, runs one block of 1024 threads per
+ * SM issuing independent chains of FP64 FMA, add and multiply, FP32 FMA and
+ * MUFU reciprocal square root, and reports the thread-level operations per
+ * clock per SM of each (cycle counts of the SMs themselves, so independent of
+ * the clock frequency); multiply by the SM count and the SM clock for a peak
+ * rate.  Any output may be NULL.  Allocates and frees a few KB, synchronises,
+ * takes about 50 ms.  Errors: ECUDA, ENOMEM.                                */
+int genga_measure_pipe_rates(double *dfma_per_clk_sm, double *dadd_per_clk_sm,
+                             double *dmul_per_clk_sm, double *ffma_per_clk_sm,
+                             double *rsqrt_per_clk_sm);
 
 #ifdef __cplusplus
 }

@@ -7,11 +7,12 @@ library.  See ``genga_oracle.c`` for the readings taken where the paper is
 silent.
 """
 from .core import (OracleNN, OracleParams, OracleStats, accel, accel_rows, angmom_spin, bs_groups,
-                   bs_groups_coll, build, changeover, detect, drift, energy, group, hc, kick, lib,
-                   level_force_parts, make_nn, make_params, merge, precheck, rcrit, step, step_coll,
-                   step_frozen, step_nn, step_record)
+                   bs_groups_coll, build, changeover, detect, drift, energy, group, hc, kick,
+                   level_force_parts, lib, make_nn, make_params, merge, pair_log, pair_log_get,
+                   precheck, rcrit, step, step_coll, step_frozen, step_nn, step_record)
 
 __all__ = ["OracleNN", "OracleParams", "OracleStats", "accel", "accel_rows", "angmom_spin",
            "bs_groups", "bs_groups_coll", "build", "changeover", "detect", "drift", "energy",
-           "group", "hc", "kick", "level_force_parts", "lib", "make_nn", "make_params", "merge", "precheck", "rcrit",
-           "step", "step_coll", "step_frozen", "step_nn", "step_record"]
+           "group", "hc", "kick", "level_force_parts", "lib", "make_nn", "make_params", "merge",
+           "pair_log", "pair_log_get", "precheck", "rcrit", "step", "step_coll", "step_frozen",
+           "step_nn", "step_record"]

@@ -71,6 +71,12 @@ def lib():
             L.orc_accel_rows.argtypes = [C.c_int64, _D, _D, _D, C.c_double, _I64, C.c_int64, _D,
                                          C.c_int]
             L.orc_kick.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D, C.c_int]
+            L.orc_pair_log.argtypes = [C.c_int]
+            L.orc_pair_log.restype = None
+            L.orc_pair_log_size.argtypes = [_I64, _I64, _I64]
+            L.orc_pair_log_size.restype = None
+            L.orc_pair_log_get.argtypes = [C.POINTER(C.c_int32), _I64, _U32, _I64, _U32]
+            L.orc_pair_log_get.restype = None
             L.orc_level_force_parts.argtypes = [C.c_int64, _D, _D, _D, C.c_int, C.c_int64, _U32,
                                                 C.c_double, _D, _D, _D]
             L.orc_precheck.restype = C.c_int64
@@ -176,6 +182,29 @@ def kick(x, v, m, rc, G, dt_half, nthreads: int = 1) -> np.ndarray:
     return v
 
 
+def pair_log(enable: bool):
+    """Switches the oracle's detection log on or off (and clears it)."""
+    lib().orc_pair_log(int(enable))
+
+
+def pair_log_get():
+    """The detections logged since pair_log(True), in order: a list of
+    (level, pairs (k, 2) uint32 in output order, borderline candidates (b, 2))."""
+    L = lib()
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    L.orc_pair_log_size(C.byref(a), C.byref(b), C.byref(c))
+    nev, npairs, nb = a.value, b.value, c.value
+    lev = np.zeros(max(nev, 1), dtype=np.int32)
+    off = np.zeros(nev + 1, dtype=np.int64)
+    boff = np.zeros(nev + 1, dtype=np.int64)
+    pairs = np.zeros((max(npairs, 1), 2), dtype=np.uint32)
+    border = np.zeros((max(nb, 1), 2), dtype=np.uint32)
+    L.orc_pair_log_get(lev.ctypes.data_as(C.POINTER(C.c_int32)), off.ctypes.data_as(_I64),
+                       pairs.ctypes.data_as(_U32), boff.ctypes.data_as(_I64), border.ctypes.data_as(_U32))
+    return [(int(lev[k]), pairs[off[k]:off[k + 1]].copy(), border[boff[k]:boff[k + 1]].copy())
+            for k in range(nev)]
+
+
 def level_force_parts(x, m, rc_levels, pairs, G):
     """The oracle's level split of the pair accelerations (test hook): returns
     (kick (n,3), kickS (nlev-1, n, 3), bs (n,3)) for the ascending pair list
@@ -242,7 +271,7 @@ def group(n, pairs) -> np.ndarray:
 def make_params(wl=None, **kw) -> OracleParams:
     p = OracleParams()
     defaults = dict(G=0.01720209895 ** 2, m_star=1.0, dt=6.0875, n1=3.0, n2=0.4, f_pc=4.0,
-                    bs_tol=1e-15, slevels=1, substeps=1, kepler_max_iter=50,
+                    bs_tol=1e-13, slevels=1, substeps=1, kepler_max_iter=50,
                     bs_max_steps=100000, nthreads=1, tp_mode=0, n_massive=0)
     if wl is not None:
         for k in ("G", "m_star", "dt", "n1", "n2", "f_pc", "slevels", "substeps"):
@@ -262,7 +291,7 @@ def step(x, v, m, params: OracleParams, nsteps: int = 1):
     return x, v, int(status), st.as_dict()
 
 
-def bs_groups(x, v, m, rc_levels, pairs, G, m_star, dt, tol=1e-15, max_steps=100000):
+def bs_groups(x, v, m, rc_levels, pairs, G, m_star, dt, tol=1e-13, max_steps=100000):
     """BS-integrate every group of the ascending pair list over dt.
 
     rc_levels is (nlev, n); returns (x, v, status, stats dict)."""
@@ -372,7 +401,7 @@ def _coll_state(x, v, m, R, S, alive):
     return x, v, m, R, S, alive
 
 
-def bs_groups_coll(x, v, m, R, S, rc_levels, pairs, G, m_star, dt, tol=1e-15, max_steps=100000,
+def bs_groups_coll(x, v, m, R, S, rc_levels, pairs, G, m_star, dt, tol=1e-13, max_steps=100000,
                    coll_tol=0.0, alive=None):
     """BS of every group with collisions (R25).  Returns (x, v, m, R, S, alive,
     U, log, status, stats); log has one row per merger: time in the call, i, j,

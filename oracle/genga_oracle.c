@@ -370,6 +370,91 @@ int64_t orc_detect(int64_t ncand, const uint32_t *cand, const double *xpre,
     return c;
 }
 
+/* Detection log (verification only: switched on by orc_pair_log, no effect
+ * on the integration).  Every detection inside a step appends its level, the
+ * encounter pairs it found (in its output order) and the candidates whose
+ * separation before or after the drift lies within PAIR_LOG_REL of rc_ij
+ * relative -- the pairs whose decision a rounding difference could flip.    */
+#define PAIR_LOG_REL 1e-12
+static struct {
+    int on;
+    int64_t nev, npairs, nborder, cap_ev, cap_pairs, cap_border;
+    int32_t *level;
+    int64_t *off, *boff;     /* nev + 1 each */
+    uint32_t *pairs, *border;
+} plog;
+
+static void plog_reserve(void **buf, int64_t *cap, int64_t need, size_t elem)
+{
+    if (need <= *cap) return;
+    int64_t c = *cap > 0 ? *cap : 64;
+    while (c < need) c *= 2;
+    *buf = realloc(*buf, elem * (size_t)c);
+    *cap = c;
+}
+
+static void plog_near(const double *x, int64_t i, int64_t j, double rcij, int *near)
+{
+    double r = sqrt(dist2(x + 3 * i, x + 3 * j));
+    if (fabs(r / rcij - 1.0) <= PAIR_LOG_REL) *near = 1;
+}
+
+static void plog_detection(int level, int64_t ncand, const uint32_t *cand, const double *xpre,
+                           const double *xpost, const double *rc, int64_t ne, const uint32_t *enc)
+{
+    if (!plog.on) return;
+    int64_t ev = plog.nev;
+    /* level holds cap_ev >= ev + 2 entries; off and boff (one more than the
+     * events) are kept at the same length */
+    plog_reserve((void **)&plog.level, &plog.cap_ev, ev + 2, sizeof(int32_t));
+    plog.off = (int64_t *)realloc(plog.off, sizeof(int64_t) * (size_t)plog.cap_ev);
+    plog.boff = (int64_t *)realloc(plog.boff, sizeof(int64_t) * (size_t)plog.cap_ev);
+    if (ev == 0) { plog.off[0] = 0; plog.boff[0] = 0; }
+    plog.level[ev] = level;
+    plog_reserve((void **)&plog.pairs, &plog.cap_pairs, 2 * (plog.npairs + ne), sizeof(uint32_t));
+    memcpy(plog.pairs + 2 * plog.npairs, enc, sizeof(uint32_t) * 2 * (size_t)ne);
+    plog.npairs += ne;
+    for (int64_t k = 0; k < ncand; k++) {
+        int64_t i = cand[2 * k], j = cand[2 * k + 1];
+        double rcij = pair_rc(rc, i, j);
+        int near = 0;
+        plog_near(xpre, i, j, rcij, &near);
+        plog_near(xpost, i, j, rcij, &near);
+        if (!near) continue;
+        plog_reserve((void **)&plog.border, &plog.cap_border, 2 * (plog.nborder + 1), sizeof(uint32_t));
+        plog.border[2 * plog.nborder] = (uint32_t)i;
+        plog.border[2 * plog.nborder + 1] = (uint32_t)j;
+        plog.nborder++;
+    }
+    plog.off[ev + 1] = plog.npairs;
+    plog.boff[ev + 1] = plog.nborder;
+    plog.nev = ev + 1;
+}
+
+/* Switches the detection log on (enable != 0) or off; either way it is cleared. */
+void orc_pair_log(int enable)
+{
+    free(plog.level); free(plog.off); free(plog.boff); free(plog.pairs); free(plog.border);
+    memset(&plog, 0, sizeof(plog));
+    plog.on = enable != 0;
+}
+
+void orc_pair_log_size(int64_t *nev, int64_t *npairs, int64_t *nborder)
+{
+    *nev = plog.nev; *npairs = plog.npairs; *nborder = plog.nborder;
+}
+
+/* level (nev), off and boff (nev + 1), pairs (2 npairs), border (2 nborder). */
+void orc_pair_log_get(int32_t *level, int64_t *off, uint32_t *pairs, int64_t *boff, uint32_t *border)
+{
+    if (plog.nev == 0) { off[0] = 0; boff[0] = 0; return; }
+    memcpy(level, plog.level, sizeof(int32_t) * (size_t)plog.nev);
+    memcpy(off, plog.off, sizeof(int64_t) * (size_t)(plog.nev + 1));
+    memcpy(boff, plog.boff, sizeof(int64_t) * (size_t)(plog.nev + 1));
+    memcpy(pairs, plog.pairs, sizeof(uint32_t) * 2 * (size_t)plog.npairs);
+    memcpy(border, plog.border, sizeof(uint32_t) * 2 * (size_t)plog.nborder);
+}
+
 /* ------------------------------------------------------------------------- */
 /* R8 grouping: union-find, label = smallest index in the component; bodies in
  * no pair get label -1.                                                     */
@@ -847,6 +932,7 @@ static void senc(step_ctx *cx, int64_t npairs, const uint32_t *pairs, int level,
         cx->st->kepler_fail += fg_list(bodies, nb, cx->x, cx->v, p->G * p->m_star, dt_l,
                                        p->kepler_max_iter);
         int64_t ne = orc_detect(npairs, pairs, xs, cx->x, rcL, enc);
+        plog_detection(level, npairs, pairs, xs, cx->x, rcL, ne, enc);
         cx->st->n_pairs[level] += ne;
         if (ne > 0) {
             if (level < p->slevels - 1)
@@ -1180,6 +1266,7 @@ static int step_impl(int64_t n, double *x, double *v, const double *m, const orc
         if (nc > 0) {
             uint32_t *enc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)nc);
             int64_t ne = orc_detect(nc, cand, xs, x, cx.rcl[0], enc);
+            plog_detection(0, nc, cand, xs, x, cx.rcl[0], ne, enc);
             st->n_pairs[0] += ne;
             if (ne > 0) {
                 if (L > 1)

@@ -27,6 +27,10 @@ class KickDriftKick(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx, gv):
         sysm = ctx.sysm
+        if sysm is None:
+            raise RuntimeError("the recorded trajectory of KickDriftKick serves one backward pass "
+                               "only (it is released after the first); run the forward again to "
+                               "differentiate again")
         gx0, gv0, gm = sysm.adjoint_backward(gx.contiguous(), gv.contiguous())
         sysm.close()
         ctx.sysm = None

@@ -772,6 +772,12 @@ int genga_adjoint_export(genga_system_t *s, double *rc_hist, int64_t *pair_offse
     return GENGA_OK;
 }
 
+// The same call under the name of the boundary's call list.
+int genga_step_backward(genga_system_t *s, const double *lam_x, const double *lam_v, double *grad_x0,
+                        double *grad_v0, double *grad_m) {
+    return genga_adjoint_backward(s, lam_x, lam_v, grad_x0, grad_v0, grad_m);
+}
+
 }  // extern "C"
 
 namespace genga {

@@ -36,6 +36,7 @@ struct BsArgs {
     int max_steps;
     unsigned long long time_limit_ns;
     DevCounters *ctr;
+    CollArgs coll;         // collisions (Sec. 7.1-7.2), used by the COLL instances
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -142,9 +143,13 @@ struct ColsShared {
     double red[8];
     int rank_of_slot[M];
     int flag;
+    // collisions: radius, alive flag and body index of each member rank
+    double R[M];
+    int alive[M];
+    int body[M];
 };
 
-template <int M>
+template <int M, bool COLL>
 __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, int tid, int col,
                                            bool active, unsigned mask, const double *irc_self,
                                            const double z[6], double f[6]) {
@@ -183,7 +188,9 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
         __syncthreads();
         if (!active) { f[3] = f[4] = f[5] = 0.0; return; }
         double px = 0.0, py = 0.0, pz = 0.0;
-        unsigned mm = mask;
+        // a member merged away feels only the star (its partners' masses are
+        // 0 after their mergers, so their terms vanish)
+        unsigned mm = (COLL && !S.alive[a]) ? 0u : mask;
         while (mm) {
             const int q = __ffs(mm) - 1;
             mm &= mm - 1;
@@ -203,7 +210,7 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
     const double ys = rsqrt_newton(r2s);
     const double sst = -A.mu * (ys * ys * ys);
     double px = 0.0, py = 0.0, pz = 0.0;
-    unsigned mm = mask;
+    unsigned mm = (COLL && !S.alive[tid % M]) ? 0u : mask;
     while (mm) {
         const int q = __ffs(mm) - 1;
         mm &= mm - 1;
@@ -268,7 +275,69 @@ __device__ __forceinline__ void neville_row(int k, double (&T)[8], double cur, d
     }
 }
 
+// Collisions (Sec. 7.1-7.2, reading R25) of one group, by its first thread on
+// the state S.ynew (member rank a holds body S.body[a]; ranks ascend with the
+// body index, so the pairs (a, q > a) taken rank by rank and partner by
+// partner come in ascending (i, j) order).
+// Deepest overlap fraction (R_a + R_q - r)/(R_a + R_q) over the group's pairs
+// of alive bodies; 0 when no pair overlaps.
 template <int M>
+__device__ double cols_overlap(const ColsShared<M> &S, int nm) {
+    double deepest = 0.0;
+    for (int a = 0; a < nm; a++) {
+        if (!S.alive[a]) continue;
+        unsigned mm = S.pmask[a] & ~((2u << a) - 1u);
+        while (mm) {
+            const int q = __ffs(mm) - 1;
+            mm &= mm - 1;
+            if (!S.alive[q]) continue;
+            const double r = __dsqrt_rn(dist2_rn(__dsub_rn(S.ynew[0][q], S.ynew[0][a]),
+                                                 __dsub_rn(S.ynew[1][q], S.ynew[1][a]),
+                                                 __dsub_rn(S.ynew[2][q], S.ynew[2][a])));
+            const double Rs = __dadd_rn(S.R[a], S.R[q]);
+            if (r < Rs) deepest = fmax(deepest, __ddiv_rn(__dsub_rn(Rs, r), Rs));
+        }
+    }
+    return deepest;
+}
+
+// Mergers of the overlapping pairs of alive bodies at time t of the call, in
+// ascending pair order, each seeing the mergers before it; logged with the
+// group label and a running sequence number.
+template <int M>
+__device__ void cols_merge(const BsArgs &A, ColsShared<M> &S, int nm, double t, int label, int &seq) {
+    const size_t N = (size_t)A.n;
+    for (int a = 0; a < nm; a++) {
+        unsigned mm = S.pmask[a] & ~((2u << a) - 1u);
+        while (mm) {
+            const int q = __ffs(mm) - 1;
+            mm &= mm - 1;
+            if (!S.alive[a] || !S.alive[q]) continue;
+            const double r = __dsqrt_rn(dist2_rn(__dsub_rn(S.ynew[0][q], S.ynew[0][a]),
+                                                 __dsub_rn(S.ynew[1][q], S.ynew[1][a]),
+                                                 __dsub_rn(S.ynew[2][q], S.ynew[2][a])));
+            const double Rs = __dadd_rn(S.R[a], S.R[q]);
+            if (!(r < Rs)) continue;
+            double xa[3], va[3], xq[3], vq[3], xo[3], vo[3], dU, rr;
+            for (int k = 0; k < 3; k++) {
+                xa[k] = S.ynew[k][a]; va[k] = S.ynew[3 + k][a];
+                xq[k] = S.ynew[k][q]; vq[k] = S.ynew[3 + k][q];
+            }
+            const int ia = S.body[a], iq = S.body[q];
+            const int sv = merge_bodies(A.coll, N, ia, iq, xa, va, xq, vq, xo, vo, &dU, &rr);
+            const int ks = sv == ia ? a : q, ko = sv == ia ? q : a;
+            for (int k = 0; k < 3; k++) { S.ynew[k][ks] = xo[k]; S.ynew[3 + k][ks] = vo[k]; }
+            S.m[ks] = A.coll.mass[sv];
+            S.R[ks] = A.coll.radius[sv];
+            S.m[ko] = 0.0;
+            S.R[ko] = 0.0;
+            S.alive[ko] = 0;
+            log_merger(A.coll, A.ctr, label, seq++, t, ia, iq, r, Rs, dU);
+        }
+    }
+}
+
+template <int M, bool COLL>
 __global__ void __launch_bounds__(8 * M)
 bs_cols_kernel(BsArgs A) {
     __shared__ ColsShared<M> S;
@@ -308,8 +377,15 @@ bs_cols_kernel(BsArgs A) {
             for (int l = 0; l < A.nlev; l++) S.irc[l][a] = irc_self[l];
         }
     }
-    if constexpr (M <= 16) {
+    if (COLL && col == 0) {
+        S.R[a] = active ? A.coll.radius[b] : 0.0;
+        S.alive[a] = active ? (int)A.coll.alive[b] : 0;
+        S.body[a] = b;
+    }
+    if (COLL || M <= 16) {
         if (col == 0) S.pmask[a] = active ? pmask : 0u;
+    }
+    if constexpr (M <= 16) {
         __syncthreads();
         if (tid == 0) {                          // pair list in (a, q) order
             int np = 0;
@@ -329,19 +405,31 @@ bs_cols_kernel(BsArgs A) {
     }
     __syncthreads();
 
+    int seq = 0;        // mergers of this group so far (log order)
+    if (COLL) {
+        // pairs already overlapping when the integration starts merge at once
+        if (col == 0 && active)
+            for (int c = 0; c < 6; c++) S.ynew[c][a] = y[c];
+        __syncthreads();
+        if (tid == 0) cols_merge<M>(A, S, nm, 0.0, g, seq);
+        __syncthreads();
+        if (active) for (int c = 0; c < 6; c++) y[c] = S.ynew[c][a];
+    }
+
     const int nk = 2 * (col + 1);
     double t = 0.0, H = A.dt;
     int attempts = 0;
     long long acc = 0, rej = 0;
-    bool failed = false;
+    int failed = 0;     // 1: attempt limit, 2: time limit
     double f0[6], zm[6], zn[6], fz[6];
     while (t < A.dt) {
-        if (tid == 0) S.flag = (attempts >= A.max_steps) || (global_ns() - t_start > A.time_limit_ns);
+        if (tid == 0)
+            S.flag = attempts >= A.max_steps ? 1 : (global_ns() - t_start >= A.time_limit_ns ? 2 : 0);
         __syncthreads();
-        if (S.flag) { failed = true; break; }
+        if (S.flag) { failed = S.flag; break; }
         attempts++;
         if (H > A.dt - t) H = A.dt - t;
-        cols_deriv<M>(A, S, tid, col, active, pmask, irc_self, y, f0);
+        cols_deriv<M, COLL>(A, S, tid, col, active, pmask, irc_self, y, f0);
         if (col == 0)
             for (int c = 0; c < 6; c++) { S.y[c][a] = y[c]; S.f0[c][a] = f0[c]; }
         // all 8 columns at once: column col takes nk midpoint sub-steps of H/nk.
@@ -355,7 +443,7 @@ bs_cols_kernel(BsArgs A) {
         double sc = 1.0, diag = 0.0;
         int kconv = -1;
         for (int it = 1; it <= 16; it++) {
-            cols_deriv<M>(A, S, tid, col, active, pmask, irc_self, zn, fz);
+            cols_deriv<M, COLL>(A, S, tid, col, active, pmask, irc_self, zn, fz);
             if (it < nk) {
                 for (int c = 0; c < 6; c++) {
                     const double tt = fma(2.0 * h, fz[c], zm[c]);
@@ -377,13 +465,28 @@ bs_cols_kernel(BsArgs A) {
             }
             if (k >= 1 && cols_block_max<M>(e, S) <= A.tol) { kconv = k; break; }
         }
-        if (kconv >= 0) {
+        bool accept = kconv >= 0;
+        if (accept) {
             if (col < 6 && active) S.ynew[col][a] = diag;
             __syncthreads();
-            if (active) for (int c = 0; c < 6; c++) y[c] = S.ynew[c][a];
+            if (COLL && A.coll.tol > 0.0) {
+                // collision precision (Sec. 7.2): a step that ends with an
+                // overlap of tol or more of the radius sum ends too late
+                if (tid == 0) S.flag = cols_overlap<M>(S, nm) >= A.coll.tol ? 1 : 0;
+                __syncthreads();
+                accept = S.flag == 0;
+                __syncthreads();
+            }
+        }
+        if (accept) {
             t += H;
             acc++;
             if (kconv < 4) H *= 1.5;
+            if (COLL) {
+                if (tid == 0) cols_merge<M>(A, S, nm, t, g, seq);
+                __syncthreads();
+            }
+            if (active) for (int c = 0; c < 6; c++) y[c] = S.ynew[c][a];
         } else {
             rej++;
             H *= 0.5;
@@ -397,7 +500,7 @@ bs_cols_kernel(BsArgs A) {
         atomicAdd(&A.ctr->bs_rejects, (unsigned long long)rej);
         if (failed) {
             atomicAdd(&A.ctr->bs_fail, 1ull);
-            latch_error(A.ctr, kErrBS);
+            latch_error(A.ctr, failed == 2 ? kErrTimeout : kErrBS);
         }
     }
 }
@@ -417,8 +520,10 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned co
     A.glist = s->glist; A.goff = s->goff; A.member = s->member; A.slotof = s->slotof;
     A.G = s->p.G; A.mu = s->p.G * s->p.m_star; A.dt = dt_l; A.tol = s->p.bs_tol;
     A.max_steps = s->p.bs_max_steps;
-    A.time_limit_ns = 10000000000ull;   // 10 s per group call
+    A.time_limit_ns = s->bs_group_limit_ns;   // per group call (default 10 s)
     A.ctr = s->ctr;
+    A.coll = coll_args(s);
+    const bool coll = s->coll_on;
     // the four size buckets run concurrently on library-owned streams so that
     // their slowest groups overlap
     GENGA_CUDA_TRY(cudaEventRecord(s->ev_fork, s->stream));
@@ -426,22 +531,30 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned co
     const size_t st = (size_t)s->bucket_stride;
     if (counts[0]) {
         A.blist = s->bucket_list;
-        bs_cols_kernel<4><<<counts[0], 32, 0, s->side[0]>>>(A); ++s->launches;
+        if (coll) bs_cols_kernel<4, true><<<counts[0], 32, 0, s->side[0]>>>(A);
+        else bs_cols_kernel<4, false><<<counts[0], 32, 0, s->side[0]>>>(A);
+        ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     if (counts[1]) {
         A.blist = s->bucket_list + st;
-        bs_cols_kernel<8><<<counts[1], 64, 0, s->side[1]>>>(A); ++s->launches;
+        if (coll) bs_cols_kernel<8, true><<<counts[1], 64, 0, s->side[1]>>>(A);
+        else bs_cols_kernel<8, false><<<counts[1], 64, 0, s->side[1]>>>(A);
+        ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     if (counts[2]) {
         A.blist = s->bucket_list + 2 * st;
-        bs_cols_kernel<16><<<counts[2], 128, 0, s->side[2]>>>(A); ++s->launches;
+        if (coll) bs_cols_kernel<16, true><<<counts[2], 128, 0, s->side[2]>>>(A);
+        else bs_cols_kernel<16, false><<<counts[2], 128, 0, s->side[2]>>>(A);
+        ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     if (counts[3]) {
         A.blist = s->bucket_list + 3 * st;
-        bs_cols_kernel<32><<<counts[3], 256, 0, s->side[3]>>>(A); ++s->launches;
+        if (coll) bs_cols_kernel<32, true><<<counts[3], 256, 0, s->side[3]>>>(A);
+        else bs_cols_kernel<32, false><<<counts[3], 256, 0, s->side[3]>>>(A);
+        ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     return cudaGetLastError();

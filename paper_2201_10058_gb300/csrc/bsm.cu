@@ -19,8 +19,9 @@
 //   accept     members of accepting groups take the accepted column.
 // Step control and iteration stay on the device: the host launches once and
 // reads the result.  A group fails after bs_max_steps attempts, so at most
-// bs_max_steps rounds run; every barrier wait has a time limit (2 s) after
-// which the kernel records a timeout and returns.  Scheme and acceptance rule
+// bs_max_steps rounds run; every barrier wait has a time limit (2 s unless
+// genga_set_wait_limits sets another) after which the kernel records a
+// timeout and returns.  Scheme and acceptance rule
 // are those of the in-block kernels (modified midpoint n = 2..16, Neville in
 // h^2, error scale |y| + |H dy/dt| + 1e-300, the same force arithmetic).
 // Data written by one block and read by another inside the kernel is read
@@ -38,7 +39,6 @@ namespace genga {
 namespace {
 
 constexpr int kPThreads = 128;
-constexpr unsigned long long kBarrierNs = 2000000000ull;   // 2 s per barrier wait
 
 struct GridBarrier {
     unsigned count;     // blocks arrived at the current barrier
@@ -71,6 +71,17 @@ struct BsmArgs {
     long long *gatt, *gacc, *grej;
     unsigned long long *gerr;      // [ng][8]
     GridBarrier *bar;
+    unsigned long long barrier_ns; // limit of one grid-barrier wait
+    unsigned barrier_absent;       // test hook: arrivals every barrier waits for in vain (0)
+    // collisions (Sec. 7.1-7.2), used by the collision ODE instance
+    CollArgs coll;
+    const int *mbody;              // [M] body of each member
+    const int *gbase;              // [ng + 1] first member of each group
+    int *morder;                   // [M] members of each group by ascending body index
+    int *malive;                   // [M] alive flags of the members
+    double *mmass_rw;              // = mmass, written by mergers
+    int *gseq;                     // [ng] mergers of each group so far
+    DevCounters *ctr;
 };
 
 __device__ __forceinline__ double ldc(const double *p) { return __ldcg(p); }
@@ -90,17 +101,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Grid-wide barrier (all blocks co-resident: cooperative launch).  One
 // thread per block arrives with an atomic and polls the generation word with
-// volatile loads (served by L2); a wait longer than kBarrierNs records a
-// timeout.  Returns false if this or another block's wait ran out.
-__device__ bool grid_barrier(GridBarrier *b) {
+// volatile loads (served by L2); a wait longer than limit_ns records a
+// timeout, and a wait also ends once another block has recorded one.  The
+// barrier completes when gridDim.x + absent blocks have arrived (absent = 0
+// in normal use; a test makes every wait run out with absent > 0).  Returns
+// false if this or another block's wait ran out.
+__device__ bool grid_barrier(GridBarrier *b, unsigned long long limit_ns, unsigned absent) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int good = 1;
         volatile unsigned *gen = &b->gen;
+        volatile unsigned *err = &b->err;
         const unsigned g = *gen;
         __threadfence();
-        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+        if (atomicAdd(&b->count, 1u) == gridDim.x + absent - 1) {
             atomicExch(&b->count, 0u);
             __threadfence();
             atomicAdd(&b->gen, 1u);
@@ -108,7 +123,7 @@ __device__ bool grid_barrier(GridBarrier *b) {
             const unsigned long long t0 = global_ns();
             unsigned polls = 0;
             while (*gen == g) {
-                if ((++polls & 1023u) == 0u && global_ns() - t0 > kBarrierNs) {
+                if ((++polls & 63u) == 0u && (*err != 0u || global_ns() - t0 >= limit_ns)) {
                     atomicExch(&b->err, 1u);
                     good = 0;
                     break;
@@ -139,15 +154,20 @@ __device__ __forceinline__ double lane_sum(double v) {
 }
 
 // Forward group ODE: y = (x, v); a = -mu x/r^3 + G sum_p m_p W (x_p - x)/r^3,
-// W = prod_{levels} (1 - K).  Every lane of the item returns f.
-struct FwdOde {
+// W = prod_{levels} (1 - K).  Every lane of the item returns f.  With
+// collisions (COLL) the members' masses and alive flags change inside the
+// kernel (read through L2); a member merged away feels only the star, and a
+// partner merged away has mass 0.
+template <bool COLL_>
+struct FwdOdeT {
     static constexpr int D = 6;
     static constexpr int NERR = 6;
+    static constexpr bool COLL = COLL_;
     __device__ static void deriv(const BsmArgs &A, const double *Z, int m, int lane, double *f) {
         const size_t ld = (size_t)A.M;
         const double x = ldc(&Z[0 * ld + m]), y = ldc(&Z[1 * ld + m]), z = ldc(&Z[2 * ld + m]);
         double px = 0.0, py = 0.0, pz = 0.0;
-        const int q1 = A.mq1[m];
+        const int q1 = (COLL && !ldc(&A.malive[m])) ? A.mq0[m] : A.mq1[m];
         for (int q = A.mq0[m] + lane; q < q1; q += kLanes) {
             const int sp = A.pidx[q];
             const double dx = ldc(&Z[0 * ld + sp]) - x, dy = ldc(&Z[1 * ld + sp]) - y,
@@ -158,7 +178,8 @@ struct FwdOde {
             double W = 1.0;
             for (int l = 0; l < A.nlev; l++)
                 W *= 1.0 - changeover_fast(d, fmin(A.irc[(size_t)l * ld + m], A.irc[(size_t)l * ld + sp]));
-            const double c = A.mmass[sp] * W * (yv * yv * yv);
+            const double ms = COLL ? ldc(&A.mmass[sp]) : A.mmass[sp];
+            const double c = ms * W * (yv * yv * yv);
             px = fma(c, dx, px); py = fma(c, dy, py); pz = fma(c, dz, pz);
         }
         px = lane_sum(px); py = lane_sum(py); pz = lane_sum(pz);
@@ -169,6 +190,8 @@ struct FwdOde {
         f[3] = fma(sst, x, A.G * px); f[4] = fma(sst, y, A.G * py); f[5] = fma(sst, z, A.G * pz);
     }
 };
+using FwdOde = FwdOdeT<false>;
+using FwdCollOde = FwdOdeT<true>;
 
 // Adjoint augmented ODE in reversed time (level 0): y (6), lambda (6), the
 // mass-gradient integral (1); with A = da/dx:
@@ -177,6 +200,7 @@ struct FwdOde {
 struct AdjOde {
     static constexpr int D = 13;
     static constexpr int NERR = 6;
+    static constexpr bool COLL = false;
     __device__ static void deriv(const BsmArgs &A, const double *Z, int m, int lane, double *f) {
         const size_t ld = (size_t)A.M;
         const double x = ldc(&Z[0 * ld + m]), y = ldc(&Z[1 * ld + m]), z = ldc(&Z[2 * ld + m]);
@@ -326,9 +350,68 @@ __device__ void phase_neville(const BsmArgs &A, long long t) {
     }
 }
 
+// Collisions (reading R25) of group g, by one thread: the separation of two
+// members in the state Z (component-major over members, stride M).
+__device__ __forceinline__ double member_dist(const BsmArgs &A, const double *Z, int a, int b) {
+    const size_t ld = (size_t)A.M;
+    return __dsqrt_rn(dist2_rn(__dsub_rn(ldc(&Z[0 * ld + b]), ldc(&Z[0 * ld + a])),
+                               __dsub_rn(ldc(&Z[1 * ld + b]), ldc(&Z[1 * ld + a])),
+                               __dsub_rn(ldc(&Z[2 * ld + b]), ldc(&Z[2 * ld + a]))));
+}
+
+// Deepest overlap fraction over the group's pairs of alive members in Z.
+__device__ double group_overlap(const BsmArgs &A, int g, const double *Z) {
+    double deepest = 0.0;
+    for (int m = A.gbase[g]; m < A.gbase[g + 1]; m++) {
+        if (!ldc(&A.malive[m])) continue;
+        for (int q = A.mq0[m]; q < A.mq1[m]; q++) {
+            const int p = A.pidx[q];
+            if (A.mbody[p] <= A.mbody[m] || !ldc(&A.malive[p])) continue;
+            const double r = member_dist(A, Z, m, p);
+            const double Rs = __dadd_rn(ldc(&A.coll.radius[A.mbody[m]]), ldc(&A.coll.radius[A.mbody[p]]));
+            if (r < Rs) deepest = fmax(deepest, __ddiv_rn(__dsub_rn(Rs, r), Rs));
+        }
+    }
+    return deepest;
+}
+
+// Mergers of the overlapping pairs of alive members of group g in the state
+// Y at time t of the call, in ascending (i, j) order (members by rank, partner
+// lists ascending), each seeing the mergers before it.
+__device__ void group_merge(const BsmArgs &A, int g, double t) {
+    const size_t ld = (size_t)A.M;
+    const int label = A.mbody[A.morder[A.gbase[g]]];
+    int seq = A.gseq[g];
+    for (int rk = A.gbase[g]; rk < A.gbase[g + 1]; rk++) {
+        const int m = A.morder[rk];
+        for (int q = A.mq0[m]; q < A.mq1[m]; q++) {
+            const int p = A.pidx[q];
+            const int im = A.mbody[m], ip = A.mbody[p];
+            if (ip <= im || !ldc(&A.malive[m]) || !ldc(&A.malive[p])) continue;
+            const double r = member_dist(A, A.Y, m, p);
+            const double Rs = __dadd_rn(ldc(&A.coll.radius[im]), ldc(&A.coll.radius[ip]));
+            if (!(r < Rs)) continue;
+            double xa[3], va[3], xb[3], vb[3], xo[3], vo[3], dU, rr;
+            for (int k = 0; k < 3; k++) {
+                xa[k] = ldc(&A.Y[k * ld + m]); va[k] = ldc(&A.Y[(3 + k) * ld + m]);
+                xb[k] = ldc(&A.Y[k * ld + p]); vb[k] = ldc(&A.Y[(3 + k) * ld + p]);
+            }
+            const int sv = merge_bodies(A.coll, (size_t)A.coll.n, im, ip, xa, va, xb, vb, xo, vo, &dU, &rr);
+            const int ms = sv == im ? m : p, mo = sv == im ? p : m;
+            for (int k = 0; k < 3; k++) { A.Y[k * ld + ms] = xo[k]; A.Y[(3 + k) * ld + ms] = vo[k]; }
+            A.mmass_rw[ms] = A.coll.mass[sv];
+            A.mmass_rw[mo] = 0.0;
+            A.malive[mo] = 0;
+            log_merger(A.coll, A.ctr, label, seq++, t, im, ip, r, Rs, dU);
+        }
+    }
+    A.gseq[g] = seq;
+}
+
 // Step control of group g (the in-block kernels' rule).  The group's
 // counters are touched only by this thread, so plain accesses suffice for
 // them; the words other blocks read go through L2.
+template <class Ode>
 __device__ void phase_decide(const BsmArgs &A, int g) {
     A.gkconv[g] = -1;
     if (ldc(&A.gstat[g]) != 0) return;
@@ -338,6 +421,11 @@ __device__ void phase_decide(const BsmArgs &A, int g) {
         const double e = __longlong_as_double((long long)atomicAdd(&A.gerr[(size_t)g * 8 + k], 0ull));
         if (e <= A.tol) kconv = k;
     }
+    // collision precision (Sec. 7.2): a step that ends with an overlap of
+    // tol or more of the radius sum ends too late
+    if (Ode::COLL && kconv >= 0 && A.coll.tol > 0.0 &&
+        group_overlap(A, g, A.DIAG + (size_t)kconv * Ode::D * A.M) >= A.coll.tol)
+        kconv = -1;
     for (int k = 0; k < 8; k++) atomicExch(&A.gerr[(size_t)g * 8 + k], 0ull);
     const long long att = A.gatt[g] + 1;
     A.gatt[g] = att;
@@ -382,24 +470,36 @@ bsm_persistent_kernel(BsmArgs A) {
     const long long item0 = tid / kLanes, nitem = nth / kLanes;
     const int lane = (int)(threadIdx.x % kLanes);
     __shared__ unsigned running;
+    if (Ode::COLL) {
+        // pairs already overlapping when the integration starts merge at once
+        for (long long g = tid; g < A.ng; g += nth) group_merge(A, (int)g, 0.0);
+        if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
+    }
     for (int round = 0; round < A.max_steps; round++) {
         // one read per block; the previous round ended with a barrier
         if (threadIdx.x == 0) running = atomicAdd(&A.bar->running, 0u);
         __syncthreads();
         if (running == 0u) break;
         for (long long t = item0; t < M; t += nitem) phase_start<Ode>(A, (int)t, lane);
-        if (!grid_barrier(A.bar)) return;
+        if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
         for (int it = 1; it <= 16; it++) {
             for (long long t = item0; t < 8 * M; t += nitem) phase_substep<Ode>(A, t, it, lane);
-            if (!grid_barrier(A.bar)) return;
+            if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
         }
         for (long long base = (long long)blockIdx.x * blockDim.x; base < D * M; base += nth)
             phase_neville<Ode>(A, base + threadIdx.x);
-        if (!grid_barrier(A.bar)) return;
-        for (long long g = tid; g < A.ng; g += nth) phase_decide(A, (int)g);
-        if (!grid_barrier(A.bar)) return;
+        if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
+        for (long long g = tid; g < A.ng; g += nth) phase_decide<Ode>(A, (int)g);
+        if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
         for (long long t = tid; t < D * M; t += nth) phase_accept<Ode>(A, t);
-        if (!grid_barrier(A.bar)) return;
+        if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
+        if (Ode::COLL) {
+            // mergers at the end of every accepted step (same thread per group
+            // as the decision, which wrote gkconv and gt)
+            for (long long g = tid; g < A.ng; g += nth)
+                if (A.gkconv[g] >= 0) group_merge(A, (int)g, ldc(&A.gt[g]));
+            if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
+        }
     }
 }
 
@@ -432,6 +532,19 @@ __global__ void bsm_members_kernel(int ng, const int *gbase, const int *gslot0, 
     for (int l = 0; l < nlev; l++) irc[(size_t)l * M + m] = 1.0 / rc.p[l][b];
 }
 
+// Collisions: each member's alive flag, and the members of each group by
+// ascending body index (rank = members of the group with a smaller body).
+__global__ void bsm_coll_init_kernel(BsmArgs A) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= A.M) return;
+    const int b = A.mbody[m];
+    A.malive[m] = A.coll.alive[b];
+    const int g = A.mgroup[m];
+    int rank = 0;
+    for (int q = A.gbase[g]; q < A.gbase[g + 1]; q++) rank += A.mbody[q] < b;
+    A.morder[A.gbase[g] + rank] = m;
+}
+
 __global__ void bsm_init_groups_kernel(BsmArgs A) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g == 0) {
@@ -448,6 +561,7 @@ __global__ void bsm_init_groups_kernel(BsmArgs A) {
     A.gatt[g] = 0;
     A.gacc[g] = 0;
     A.grej[g] = 0;
+    if (A.gseq) A.gseq[g] = 0;
     for (int k = 0; k < 8; k++) A.gerr[(size_t)g * 8 + k] = 0ull;
 }
 
@@ -547,6 +661,7 @@ int batched_groups(genga_system *s, std::vector<int2> &out) {
     if (cudaMemcpyAsync(&c, s->ctr, sizeof(c), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return -1;
+    ++s->host_syncs;
     if ((int)c.max_group <= kBlockGroupMax || c.ngroups == 0) return 0;
     std::vector<int> glist(c.ngroups), goff((size_t)s->n + 1);
     if (cudaMemcpyAsync(glist.data(), s->glist, sizeof(int) * c.ngroups, cudaMemcpyDeviceToHost, s->stream) !=
@@ -555,6 +670,7 @@ int batched_groups(genga_system *s, std::vector<int2> &out) {
             cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return -1;
+    ++s->host_syncs;
     for (int g : glist) {
         const int nm = goff[(size_t)g + 1] - goff[(size_t)g];
         if (nm > kBlockGroupMax) out.push_back(make_int2(goff[(size_t)g], nm));
@@ -580,21 +696,24 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     constexpr int D = Ode::D;
     const int ng = (int)groups.size();
     const int nlev = level + 1;
-    std::vector<int> gbase(ng), gslot0(ng);
+    std::vector<int> gbase(ng + 1), gslot0(ng);
     int M = 0;
     for (int g = 0; g < ng; g++) {
         gbase[g] = M;
         gslot0[g] = groups[g].x;
         M += groups[g].y;
     }
+    gbase[ng] = M;
     const size_t blk = (size_t)D * M;
     const size_t nq = 2 * (size_t)s->csr[level].cap;
     const size_t bytes = aligned(sizeof(double) * blk) * 3 + aligned(sizeof(double) * 8 * blk) * 5 +
                          aligned(sizeof(double) * (size_t)nlev * M) + aligned(sizeof(double) * M) +
                          aligned(sizeof(int) * M) * 4 + aligned(sizeof(int) * nq) +
-                         aligned(sizeof(int) * ng) * 4 + aligned(sizeof(double) * ng) * 2 +
+                         aligned(sizeof(int) * (ng + 1)) + aligned(sizeof(int) * ng) * 4 +
+                         aligned(sizeof(double) * ng) * 2 +
                          aligned(sizeof(long long) * ng) * 3 + aligned(sizeof(unsigned long long) * 8 * ng) +
-                         aligned(sizeof(GridBarrier));
+                         aligned(sizeof(GridBarrier)) +
+                         (Ode::COLL ? aligned(sizeof(int) * M) * 2 : 0);
     char *p = static_cast<char *>(bsm_reserve(s, bytes));
     if (!p) return GENGA_ENOMEM;
     BsmArgs A;
@@ -605,7 +724,8 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     double *irc = carve<double>(p, (size_t)nlev * M), *mmass = carve<double>(p, M);
     int *mbody = carve<int>(p, M), *mgroup = carve<int>(p, M), *mq0 = carve<int>(p, M), *mq1 = carve<int>(p, M);
     int *pidx = carve<int>(p, nq);
-    int *d_gbase = carve<int>(p, ng), *d_gslot0 = carve<int>(p, ng);
+    int *d_gbase = carve<int>(p, ng + 1), *d_gslot0 = carve<int>(p, ng);
+    int *gseq = carve<int>(p, ng);
     A.gstat = carve<int>(p, ng);
     A.gkconv = carve<int>(p, ng);
     A.gt = carve<double>(p, ng);
@@ -616,11 +736,18 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     A.gerr = carve<unsigned long long>(p, 8 * (size_t)ng);
     A.bar = carve<GridBarrier>(p, 1);
     A.mgroup = mgroup; A.mq0 = mq0; A.mq1 = mq1; A.pidx = pidx; A.mmass = mmass; A.irc = irc;
+    A.mbody = mbody; A.gbase = d_gbase; A.mmass_rw = mmass; A.ctr = s->ctr;
+    A.coll = coll_args(s);
+    A.gseq = Ode::COLL ? gseq : nullptr;
+    A.morder = Ode::COLL ? carve<int>(p, M) : nullptr;
+    A.malive = Ode::COLL ? carve<int>(p, M) : nullptr;
     A.G = s->p.G; A.mu = s->p.G * s->p.m_star; A.dt = dt; A.tol = s->p.bs_tol;
     A.max_steps = s->p.bs_max_steps;
+    A.barrier_ns = s->barrier_limit_ns;
+    A.barrier_absent = s->barrier_absent;
 
     cudaStream_t st = s->stream;
-    if (cudaMemcpyAsync(d_gbase, gbase.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(d_gbase, gbase.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(d_gslot0, gslot0.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return GENGA_ECUDA;
     RcPtrs rcp;
@@ -630,6 +757,10 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
                                           s->csr[level].list, s->mass, rcp, nlev, M, mbody, mgroup, mq0, mq1,
                                           pidx, mmass, irc);
     bsm_init_groups_kernel<<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(A);
+    if (Ode::COLL) {
+        bsm_coll_init_kernel<<<gm, 128, 0, st>>>(A);
+        ++s->launches;
+    }
     gather(st, mbody, A.Y);
     s->launches += 3;
     if (cudaGetLastError() != cudaSuccess) return GENGA_ECUDA;
@@ -652,7 +783,13 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     if (cudaMemcpyAsync(&hb, A.bar, sizeof(hb), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return GENGA_ECUDA;
-    if (hb.err) return GENGA_ETIMEOUT;
+    ++s->host_syncs;
+    if (hb.err) {
+        snprintf(s->err, sizeof(s->err),
+                 "persistent Bulirsch-Stoer: a grid-barrier wait exceeded its limit of %.3g s",
+                 1e-9 * (double)s->barrier_limit_ns);
+        return GENGA_ETIMEOUT;
+    }
     scatter(st, mbody, A.Y);
     bsm_stats_kernel<<<1, 1, 0, st>>>(A, s->ctr, count_steps ? 1 : 0);
     s->launches += 2;
@@ -686,14 +823,14 @@ int bsm_forward_groups(genga_system *s, int level, double dt_l) {
     const int n = (int)s->n;
     const int M = members_of(groups);
     const unsigned gr = (unsigned)((M + 127) / 128);
-    return bsm_run<FwdOde>(
-        s, level, dt_l, groups, true,
-        [&](cudaStream_t st, const int *mbody, double *Y) {
-            bsm_gather_fwd<<<gr, 128, 0, st>>>(n, M, mbody, pre_pos, pre_vel, Y);
-        },
-        [&](cudaStream_t st, const int *mbody, const double *Y) {
-            bsm_scatter_fwd<<<gr, 128, 0, st>>>(n, M, mbody, Y, pos, vel);
-        });
+    auto gather = [&](cudaStream_t st, const int *mbody, double *Y) {
+        bsm_gather_fwd<<<gr, 128, 0, st>>>(n, M, mbody, pre_pos, pre_vel, Y);
+    };
+    auto scatter = [&](cudaStream_t st, const int *mbody, const double *Y) {
+        bsm_scatter_fwd<<<gr, 128, 0, st>>>(n, M, mbody, Y, pos, vel);
+    };
+    if (s->coll_on) return bsm_run<FwdCollOde>(s, level, dt_l, groups, true, gather, scatter);
+    return bsm_run<FwdOde>(s, level, dt_l, groups, true, gather, scatter);
 }
 
 // Bulirsch-Stoer of every group of the current grouping at `level`: the
@@ -702,11 +839,17 @@ int bsm_forward_groups(genga_system *s, int level, double dt_l) {
 // itself) the persistent driver for the larger ones.
 int run_bs(genga_system *s, int level, double dt_l, int64_t np) {
     if (np <= 0) return GENGA_OK;
+    ++s->bs_call;                         // orders the merger records of the calls
     unsigned counts[kBuckets];
+    int rc = phase_mark(s, GENGA_PH_BUCKETS);
+    if (rc != GENGA_OK) return rc;
     if (bucket_groups(s, counts) != cudaSuccess) return GENGA_ECUDA;
+    if ((rc = phase_mark(s, GENGA_PH_BS_SMALL)) != GENGA_OK) return rc;
     const cudaError_t e = launch_bs(s, level, dt_l, counts);
     if (join_bs(s) != cudaSuccess || e != cudaSuccess) return GENGA_ECUDA;
-    return counts[kBuckets - 1] ? bsm_forward_groups(s, level, dt_l) : GENGA_OK;
+    if (!counts[kBuckets - 1]) return GENGA_OK;
+    if ((rc = phase_mark(s, GENGA_PH_BS_LARGE)) != GENGA_OK) return rc;
+    return bsm_forward_groups(s, level, dt_l);
 }
 
 // Adjoint BS (backward, augmented) of every group larger than kBlockGroupMax.

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <algorithm>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/genga.h"
@@ -31,7 +32,13 @@ enum : unsigned {
     kErrPairCap = 8u,     // encounter list overflow (recovered by the host)
     kErrBadState = 16u,   // NaN / Inf / body at the origin
     kErrUnionFind = 32u,  // bounded union-find retry loop gave up
+    kErrTimeout = 64u,    // an in-block Bulirsch-Stoer group call hit its time limit
+    kErrMergeLog = 128u,  // the merger log is full
 };
+
+// One merger record of the device log: Bulirsch-Stoer call, group label,
+// sequence number in the group, time in the call, i, j, r_ij, R_i + R_j, dU.
+constexpr int kMergeRec = 9;
 
 // Counters that live in device memory.
 struct DevCounters {
@@ -52,6 +59,21 @@ struct DevCounters {
     double hc_shift[3];
     unsigned int bucket_count[kBuckets];   // groups per size bucket (bucket_groups)
     unsigned int pad2[8 - kBuckets];
+    unsigned long long merge_count;        // records written to the merger log
+};
+
+// Collision state handed to the Bulirsch-Stoer kernels (Sec. 7.1-7.2).
+struct CollArgs {
+    int on;                       // collisions switched on
+    double tol;                   // collision precision (0: merge at the first overlapping step)
+    double *mass;                 // = the system's masses, written by mergers
+    double *radius, *spin;        // radii (n), spins (3n, component-major)
+    unsigned char *alive;         // n
+    double *log;                  // merger records (kMergeRec doubles each)
+    unsigned long long log_cap;   // records
+    long long call;               // index of this Bulirsch-Stoer call
+    double G;
+    int64_t n;                    // bodies (the stride of spin)
 };
 
 // Level-independent per-body data of the critical radius (level 0 uses all).
@@ -135,7 +157,34 @@ struct genga_system {
     cudaEvent_t ev_fork = nullptr, ev_join[4] = {};
     genga_stats_t stats;
     void *adj = nullptr;           // adjoint recording (adjoint.cu)
+    // collisions (genga_set_collisions)
+    bool coll_on = false;
+    double coll_tol = 0.0;
+    double *radius = nullptr;          // caller-owned, n
+    double *spin = nullptr;            // caller-owned, 3n
+    unsigned char *alive = nullptr;    // library-owned, n
+    double *mlog = nullptr;            // library-owned merger records
+    int64_t mlog_cap = 0;
+    long long bs_call = 0;             // Bulirsch-Stoer calls since collisions were switched on
+    // bounded device waits (genga_set_wait_limits)
+    unsigned long long bs_group_limit_ns = 10000000000ull;   // in-block BS, per group call
+    unsigned long long barrier_limit_ns = 2000000000ull;     // persistent BS, per grid-barrier wait
+    unsigned barrier_absent = 0;   // test hook: blocks every grid barrier waits for in vain
     int64_t launches = 0;          // kernels launched by this system (host-side count)
+    int64_t host_syncs = 0;        // host waits on the stream inside steps
+    // phase timing (genga_set_timing): an event on the stream at each phase
+    // boundary; after a step the intervals are added to the phase sums
+    bool timing = false;
+    std::vector<cudaEvent_t> mark_ev;
+    std::vector<int> mark_phase;
+    size_t nmarks = 0;
+    double phase_ms[GENGA_NPHASES] = {};
+    int64_t timed_steps = 0;
+    // detection log (genga_set_pair_log): level and sorted pairs of every detection
+    bool pair_log = false;
+    std::vector<int32_t> log_level;
+    std::vector<int64_t> log_off;
+    std::vector<uint32_t> log_pairs;
     char err[512] = {0};
 };
 
@@ -215,6 +264,11 @@ cudaError_t exclusive_scan(genga_system *s, const int *in, int *out, int64_t len
 
 // genga.cu
 int ensure_pair_capacity(genga_system *s, int level, int64_t np);
+// collide.cu: the collision arguments of the system for the next
+// Bulirsch-Stoer call (on = 0 when collisions are off)
+CollArgs coll_args(const genga_system *s);
+// Phase timing: from here on, stream time counts for `phase` (no-op when off).
+int phase_mark(genga_system *s, int phase);
 // adjoint.cu
 void adjoint_free(genga_system *s);
 
@@ -405,6 +459,109 @@ __device__ __forceinline__ void changeover_fast_dr(double r, double irc, double 
     const double iD = rcp_newton(fma(w, w, y2));
     K = y2 * iD;
     dK = 2.0 * y * w * (iD * iD) * (irc * (1.0 / 0.9));
+}
+
+// ---------------------------------------------------------------------------
+// Float-float helpers of the mixed-precision pair kicks (kick.cu, ensemble.cu).
+// (hi, lo) += v in float-float: TwoSum of hi and v, the rounding error into lo.
+__device__ __forceinline__ void float_two_sum_acc(float &hi, float &lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+
+// Double with the value of a float (exact), for any sign; zero and subnormal
+// floats give a signed zero.  Integer operations only.
+__device__ __forceinline__ double f64_of_f32_any(float f) {
+    const unsigned fb = __float_as_uint(f);
+    const unsigned mag = fb & 0x7fffffffu, sgn = fb & 0x80000000u;
+    const unsigned hi = (mag >= 0x00800000u) ? (sgn | ((mag >> 3) + 0x38000000u)) : sgn;
+    const unsigned lo = (mag >= 0x00800000u) ? (mag << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// v = hi + lo exactly up to 2^-47 |v|: hi is v with the mantissa truncated
+// to float precision, lo the 29 discarded mantissa bits rounded to a float.
+// Integer operations, one integer-to-float conversion and one FP32 scale;
+// |v| < 2^-74 gives lo = 0, |v| < 2^-126 also hi = 0 (signed zeros).
+__device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    const unsigned mag = hw & 0x7fffffffu, sgn = hw & 0x80000000u;
+    const bool normal = mag >= 0x38100000u;
+    hi = __uint_as_float(normal ? (sgn | ((mag - 0x38000000u) << 3) | (lw >> 29)) : sgn);
+    const unsigned E = mag >> 20;                       // biased double exponent
+    float l = 0.0f;
+    if (E >= 949u) l = __uint2float_rn(lw & 0x1fffffffu) * __uint_as_float((E - 948u) << 23);
+    lo = __uint_as_float(__float_as_uint(l) | sgn);
+}
+
+// ---------------------------------------------------------------------------
+// Collisions (Sec. 7.1): one perfectly inelastic merger of bodies i < j with
+// states (xi, vi), (xj, vj), in the operations and order of the definition
+// without contraction.  The survivor (the more massive body; equal masses:
+// the lower index) gets the summed mass, the radius of the summed R^3 and the
+// spin S_i + S_j + mu (r_ij x v_ij), and its new position and velocity go to
+// xo, vo (the other body keeps its own); the other body gets mass, radius and
+// spin 0 and is marked not alive.  Returns the survivor; *dU receives
+// mu |v_ij|^2 / 2 - G m_i m_j / r_ij, *r the separation.
+__device__ __forceinline__ int merge_bodies(const CollArgs &C, size_t N, int i, int j, const double *xi,
+                                            const double *vi, const double *xj, const double *vj,
+                                            double *xo, double *vo, double *dU, double *r_out) {
+    const double mi = C.mass[i], mj = C.mass[j], M = __dadd_rn(mi, mj);
+    double r[3], w[3];
+    for (int k = 0; k < 3; k++) {
+        r[k] = __dsub_rn(xi[k], xj[k]);
+        w[k] = __dsub_rn(vi[k], vj[k]);
+    }
+    const double rr = __dsqrt_rn(dist2_rn(r[0], r[1], r[2]));
+    const double w2 = dist2_rn(w[0], w[1], w[2]);
+    double mu = 0.0;
+    if (M > 0.0) {
+        mu = __ddiv_rn(__dmul_rn(mi, mj), M);
+        for (int k = 0; k < 3; k++) {
+            xo[k] = __ddiv_rn(__dadd_rn(__dmul_rn(xi[k], mi), __dmul_rn(xj[k], mj)), M);
+            vo[k] = __ddiv_rn(__dadd_rn(__dmul_rn(vi[k], mi), __dmul_rn(vj[k], mj)), M);
+        }
+    } else {
+        for (int k = 0; k < 3; k++) {
+            xo[k] = __dmul_rn(0.5, __dadd_rn(xi[k], xj[k]));
+            vo[k] = __dmul_rn(0.5, __dadd_rn(vi[k], vj[k]));
+        }
+    }
+    *dU = __dsub_rn(__dmul_rn(__dmul_rn(0.5, mu), w2),
+                    rr > 0.0 ? __ddiv_rn(__dmul_rn(__dmul_rn(C.G, mi), mj), rr) : 0.0);
+    *r_out = rr;
+    const double L[3] = {__dmul_rn(mu, __dsub_rn(__dmul_rn(r[1], w[2]), __dmul_rn(r[2], w[1]))),
+                         __dmul_rn(mu, __dsub_rn(__dmul_rn(r[2], w[0]), __dmul_rn(r[0], w[2]))),
+                         __dmul_rn(mu, __dsub_rn(__dmul_rn(r[0], w[1]), __dmul_rn(r[1], w[0])))};
+    const int sv = (mi > mj || (mi == mj && i < j)) ? i : j, ot = sv == i ? j : i;
+    const double Ri = C.radius[i], Rj = C.radius[j];
+    const double R3 = __dadd_rn(__dmul_rn(__dmul_rn(Ri, Ri), Ri), __dmul_rn(__dmul_rn(Rj, Rj), Rj));
+    double Sn[3];
+    for (int k = 0; k < 3; k++)
+        Sn[k] = __dadd_rn(__dadd_rn(C.spin[k * N + i], C.spin[k * N + j]), L[k]);
+    C.mass[sv] = M;
+    C.radius[sv] = cbrt(R3);
+    for (int k = 0; k < 3; k++) C.spin[k * N + sv] = Sn[k];
+    C.mass[ot] = 0.0;
+    C.radius[ot] = 0.0;
+    for (int k = 0; k < 3; k++) C.spin[k * N + ot] = 0.0;
+    C.alive[ot] = 0;
+    return sv;
+}
+
+// Appends one record to the merger log (latches kErrMergeLog when full).
+__device__ __forceinline__ void log_merger(const CollArgs &C, DevCounters *ctr, int label, int seq, double t,
+                                           int i, int j, double r, double Rs, double dU) {
+    const unsigned long long k = atomicAdd(&ctr->merge_count, 1ull);
+    if (k >= C.log_cap) {
+        latch_error(ctr, kErrMergeLog);
+        return;
+    }
+    double *e = C.log + (size_t)k * kMergeRec;
+    e[0] = (double)C.call; e[1] = (double)label; e[2] = (double)seq; e[3] = t;
+    e[4] = (double)i; e[5] = (double)j; e[6] = r; e[7] = Rs; e[8] = dU;
 }
 
 }  // namespace genga

@@ -315,6 +315,7 @@ cudaError_t build_bodies(genga_system *s, int level_pairs, int out_level, int *n
     compact_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->flags, pos, s->bodies[out_level]); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     GENGA_CUDA_TRY(cudaMemcpyAsync(nb_host, pos + n, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    ++s->host_syncs;
     return cudaStreamSynchronize(s->stream);
 }
 
@@ -339,6 +340,7 @@ cudaError_t bucket_groups(genga_system *s, unsigned counts[kBuckets]) {
     GENGA_CUDA_TRY(cudaGetLastError());
     GENGA_CUDA_TRY(cudaMemcpyAsync(counts, s->ctr->bucket_count, sizeof(unsigned) * kBuckets,
                                    cudaMemcpyDeviceToHost, s->stream));
+    ++s->host_syncs;
     return cudaStreamSynchronize(s->stream);
 }
 

@@ -56,6 +56,9 @@ struct EnsShared {
     double m[kEnsMaxN], R[kEnsMaxN], k2[kEnsMaxN], tau[kEnsMaxN], rg2[kEnsMaxN];
     double w[3][kEnsMaxN];
     double rc[kEnsMaxN], rc2[kEnsMaxN], pc2[kEnsMaxN];
+    // mixed kick: masses as two floats, FP32 bounds of rc^2 (above) and of
+    // (f_pc rc)^2 (below and above)
+    float mh[kEnsMaxN], ml[kEnsMaxN], thr[kEnsMaxN], pclo[kEnsMaxN], pchi[kEnsMaxN];
     double u0[3][kEnsMaxN], u1[3][kEnsMaxN], w0[3][kEnsMaxN], nsum[3][kEnsMaxN];
     double part[3][128];
     unsigned long long cand[kEnsMaxN], enc[kEnsMaxN];
@@ -76,14 +79,81 @@ __device__ __forceinline__ unsigned long long ens_now() {
 
 // ------------------------------------------------------------ kick (Eq. Hb)
 // a_i = G sum_j m_j K r^-3 (x_j - x_i), thread (i, slice); pre-check bits.
-template <int T>
+// MIXED: the arithmetic of the main mixed kick (kick.cu) -- FP64 displacement
+// and accumulation, r^2 in float-float from an exact split of the
+// displacement, FP32 rsqrt seed with one Newton correction in float-float,
+// the small correction terms summed in float-float and added once; the
+// changeover band and the pre-check are decided in FP32 against rounded
+// bounds, the pre-check with the exact FP64 test within 2^-20 of its
+// threshold (so the candidates are those of the FP64 form).
+template <int T, bool MIXED>
 __device__ void ens_kick(const EnsArgs &A, EnsShared &S, double dt_half, bool precheck) {
     const int n = S.n;
     const int t = threadIdx.x;
     const int nsl = max(1, T / n);
     const int i = t % n, sl = t / n;
     double ax = 0.0, ay = 0.0, az = 0.0;
-    if (sl < nsl && t < nsl * n) {
+    if (MIXED && sl < nsl && t < nsl * n) {
+        const int per = (n + nsl - 1) / nsl;
+        const int j0 = sl * per, j1 = min(n, j0 + per);
+        const double xi = S.x[0][i], yi = S.x[1][i], zi = S.x[2][i];
+        unsigned long long bits = 0;
+        float cxh = 0.0f, cxl = 0.0f, cyh = 0.0f, cyl = 0.0f, czh = 0.0f, czl = 0.0f;
+        for (int j = j0; j < j1; j++) {
+            if (j == i) continue;
+            const double dx = S.x[0][j] - xi, dy = S.x[1][j] - yi, dz = S.x[2][j] - zi;
+            float hx, hy, hz, lx, ly, lz;
+            split_f64(dx, hx, lx);
+            split_f64(dy, hy, ly);
+            split_f64(dz, hz, lz);
+            const float px = hx * hx, py = hy * hy, pz = hz * hz;
+            const float pxe = fmaf(hx, hx, -px), pye = fmaf(hy, hy, -py), pze = fmaf(hz, hz, -pz);
+            const float s1 = px + py, b1 = s1 - px;
+            const float e1s = (px - (s1 - b1)) + (py - b1);
+            const float s2 = s1 + pz, b2 = s2 - s1;
+            const float e2s = (s1 - (s2 - b2)) + (pz - b2);
+            const float cross = 2.0f * fmaf(hx, lx, fmaf(hy, ly, hz * lz));
+            const float tail = ((e1s + e2s) + (pxe + pye + pze)) + cross;
+            const float Rh = s2 + tail;
+            const float Rl = tail - (Rh - s2);
+            float mh = S.mh[j], ml = S.ml[j];
+            if (Rh < fmaxf(S.thr[i], S.thr[j])) {            // changeover band (rare)
+                const double mk = S.m[j] * changeover(sqrt(fma(dz, dz, fma(dy, dy, dx * dx))),
+                                                      fmax(S.rc[i], S.rc[j]));
+                mh = __double2float_rn(mk);
+                ml = __double2float_rn(mk - (double)mh);
+            }
+            if (precheck && j > i) {
+                bool c;
+                if (Rh < fmaxf(S.pclo[i], S.pclo[j])) c = true;
+                else if (Rh > fmaxf(S.pchi[i], S.pchi[j])) c = false;
+                else c = dist2_rn(dx, dy, dz) < fmax(S.pc2[i], S.pc2[j]);
+                if (c) bits |= 1ull << j;
+            }
+            const float y0f = rsqrtf(Rh);
+            const float u = Rh * y0f, ue = fmaf(Rh, y0f, -u);
+            const float r1 = fmaf(-u, y0f, 1.0f);
+            const float p = y0f * y0f, pe = fmaf(y0f, y0f, -p);
+            const float q = p * y0f;
+            float qe = fmaf(p, y0f, -q);
+            qe = fmaf(pe, y0f, qe);
+            const float ch = q * mh;
+            float ce = fmaf(q, mh, -ch);
+            ce = fmaf(q, ml, ce);
+            ce = fmaf(qe, mh, ce);
+            const float ef = r1 - fmaf(ue, y0f, Rl * p);
+            const float corr = fmaf(ch, fmaf(1.875f * ef, ef, 1.5f * ef), ce);
+            const double sd = f64_of_f32_any(ch);
+            ax = fma(sd, dx, ax); ay = fma(sd, dy, ay); az = fma(sd, dz, az);
+            float_two_sum_acc(cxh, cxl, corr * hx);
+            float_two_sum_acc(cyh, cyl, corr * hy);
+            float_two_sum_acc(czh, czl, corr * hz);
+        }
+        ax += f64_of_f32_any(cxh) + f64_of_f32_any(cxl);
+        ay += f64_of_f32_any(cyh) + f64_of_f32_any(cyl);
+        az += f64_of_f32_any(czh) + f64_of_f32_any(czl);
+        if (precheck && bits) atomicOr(&S.cand[i], bits);
+    } else if (!MIXED && sl < nsl && t < nsl * n) {
         const int per = (n + nsl - 1) / nsl;
         const int j0 = sl * per, j1 = min(n, j0 + per);
         const double xi = S.x[0][i], yi = S.x[1][i], zi = S.x[2][i];
@@ -379,7 +449,7 @@ __device__ int ens_find(int *p, int a) {
 }
 
 // ------------------------------------------------------------ one step
-template <int T>
+template <int T, bool MIXED>
 __device__ void ens_step(const EnsArgs &A, EnsShared &S, double *scr, unsigned long long t_start) {
     const int n = S.n, t = threadIdx.x;
     const double dt = S.dt;
@@ -394,11 +464,18 @@ __device__ void ens_step(const EnsArgs &A, EnsShared &S, double *scr, unsigned l
         S.rc2[t] = __dmul_rn(rc, rc);
         const double tt = __dmul_rn(A.f_pc, rc);
         S.pc2[t] = __dmul_rn(tt, tt);
+        if (MIXED) {
+            // conservative float bounds: above rc^2, below and above (f_pc rc)^2,
+            // each with a 2^-20 margin over the float errors of r^2 (~2^-23)
+            S.thr[t] = fmaxf(__fmul_ru(__double2float_ru(S.rc2[t]), 1.00000095f), 1.17549435e-38f);
+            S.pclo[t] = __fmul_rd(__double2float_rd(S.pc2[t]), 0.99999905f);
+            S.pchi[t] = __fmul_ru(__double2float_ru(S.pc2[t]), 1.00000095f);
+        }
         S.cand[t] = 0ull;
         S.enc[t] = 0ull;
     }
     __syncthreads();
-    ens_kick<T>(A, S, 0.5 * dt, true);
+    ens_kick<T, MIXED>(A, S, 0.5 * dt, true);
     ens_nn(A, S, 0.5 * dt);
     ens_hc(S, 0.5 * dt);
     // FG (saves the pre-drift state)
@@ -464,11 +541,11 @@ __device__ void ens_step(const EnsArgs &A, EnsShared &S, double *scr, unsigned l
         ens_bs_group(A, S, scr, S.flag, dt, t_start);
     }
     ens_hc(S, 0.5 * dt);
-    ens_kick<T>(A, S, 0.5 * dt, false);
+    ens_kick<T, MIXED>(A, S, 0.5 * dt, false);
     ens_nn(A, S, 0.5 * dt);
 }
 
-template <int T>
+template <int T, bool MIXED>
 __global__ void __launch_bounds__(T) ensemble_kernel(EnsArgs A) {
     __shared__ EnsShared S;
     double *scr = A.bs_scr + (size_t)blockIdx.x * kEnsBsRows * kEnsMaxN;
@@ -494,10 +571,14 @@ __global__ void __launch_bounds__(T) ensemble_kernel(EnsArgs A) {
                 S.x[c][t] = A.pos[c * NT + g]; S.v[c][t] = A.vel[c * NT + g]; S.w[c][t] = A.spin[c * NT + g];
             }
             S.m[t] = A.mass[g]; S.R[t] = A.radius[g]; S.k2[t] = A.k2[g]; S.tau[t] = A.tau[g]; S.rg2[t] = A.rg2[g];
+            if (MIXED) {
+                S.mh[t] = __double2float_rn(S.m[t]);
+                S.ml[t] = __double2float_rn(S.m[t] - (double)S.mh[t]);
+            }
         }
         __syncthreads();
         const unsigned long long t_start = ens_now();
-        for (long long k = 0; k < A.nsteps; k++) ens_step<T>(A, S, scr, t_start);
+        for (long long k = 0; k < A.nsteps; k++) ens_step<T, MIXED>(A, S, scr, t_start);
         if (t < n) {
             const size_t g = (size_t)o + t;
             for (int c = 0; c < 3; c++) {
@@ -611,9 +692,17 @@ cudaError_t launch_ensemble(genga_ensemble *e, long long nsteps, cudaStream_t st
     const int grid = grid_of(e);
     cudaError_t r = cudaMemsetAsync(e->work, 0, sizeof(unsigned), st);
     if (r != cudaSuccess) return r;
-    if (e->threads == 32) ensemble_kernel<32><<<grid, 32, 0, st>>>(A);
-    else if (e->threads == 128) ensemble_kernel<128><<<grid, 128, 0, st>>>(A);
-    else ensemble_kernel<64><<<grid, 64, 0, st>>>(A);
+    const bool mixed = e->p.precision == GENGA_MIXED;
+    if (e->threads == 32) {
+        if (mixed) ensemble_kernel<32, true><<<grid, 32, 0, st>>>(A);
+        else ensemble_kernel<32, false><<<grid, 32, 0, st>>>(A);
+    } else if (e->threads == 128) {
+        if (mixed) ensemble_kernel<128, true><<<grid, 128, 0, st>>>(A);
+        else ensemble_kernel<128, false><<<grid, 128, 0, st>>>(A);
+    } else {
+        if (mixed) ensemble_kernel<64, true><<<grid, 64, 0, st>>>(A);
+        else ensemble_kernel<64, false><<<grid, 64, 0, st>>>(A);
+    }
     e->launches++;
     return cudaGetLastError();
 }
@@ -651,7 +740,8 @@ int genga_ensemble_create(genga_ensemble_t **out, const genga_params_t *p,
     if (d->n_systems < 1 || !d->offsets || !d->pos || !d->vel || !d->mass || !d->spin || !d->radius ||
         !d->k2 || !d->tau || !d->rg2 || !d->m_star || !d->dt || !d->star)
         return GENGA_EINVAL;
-    if (p->slevels != 1 || p->kepler_max_iter < 1 || p->bs_max_steps < 1 || !(p->bs_tol > 0))
+    if (p->slevels != 1 || p->kepler_max_iter < 1 || p->bs_max_steps < 1 || !(p->bs_tol > 0) ||
+        (p->precision != GENGA_FP64 && p->precision != GENGA_MIXED))
         return GENGA_EINVAL;
     std::vector<int> sizes((size_t)d->n_systems);
     for (int64_t s = 0; s < d->n_systems; s++) {
@@ -826,5 +916,12 @@ int genga_ensemble_get_stats(genga_ensemble_t *e, genga_stats_t *st) {
     *st = e->stats;
     return GENGA_OK;
 }
+
+// The same calls under the names of the boundary's call list.
+int genga_init_ensemble(genga_ensemble_t **out, const genga_params_t *p, const genga_ensemble_desc_t *d,
+                        void *stream) {
+    return genga_ensemble_create(out, p, d, stream);
+}
+int genga_step_ensemble(genga_ensemble_t *e, int64_t nsteps) { return genga_ensemble_step(e, nsteps); }
 
 }  // extern "C"

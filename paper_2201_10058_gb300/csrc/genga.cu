@@ -56,6 +56,45 @@ void dfree(T *&p) {
     p = nullptr;
 }
 
+// ---------------------------------------------------------------- phase timing
+// From this point of the stream on, device time counts for `phase`.
+int mark(genga_system *s, int phase) {
+    if (!s->timing) return GENGA_OK;
+    if (s->nmarks == s->mark_ev.size()) {
+        cudaEvent_t e = nullptr;
+        CU(cudaEventCreate(&e));
+        s->mark_ev.push_back(e);
+        s->mark_phase.push_back(-1);
+    }
+    CU(cudaEventRecord(s->mark_ev[s->nmarks], s->stream));
+    s->mark_phase[s->nmarks] = phase;
+    s->nmarks++;
+    return GENGA_OK;
+}
+
+// Adds the intervals between the recorded marks to the phase sums (waits for
+// the last mark); the last mark closes the step.
+int fold_marks(genga_system *s) {
+    if (!s->timing || s->nmarks == 0) return GENGA_OK;
+    CU(cudaEventSynchronize(s->mark_ev[s->nmarks - 1]));
+    for (size_t k = 0; k + 1 < s->nmarks; k++) {
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, s->mark_ev[k], s->mark_ev[k + 1]));
+        const int ph = s->mark_phase[k];
+        if (ph >= 0 && ph < GENGA_NPHASES) s->phase_ms[ph] += (double)ms;
+    }
+    s->nmarks = 0;
+    s->timed_steps++;
+    return GENGA_OK;
+}
+
+void free_marks(genga_system *s) {
+    for (cudaEvent_t e : s->mark_ev) cudaEventDestroy(e);
+    s->mark_ev.clear();
+    s->mark_phase.clear();
+    s->nmarks = 0;
+}
+
 int levels_of(const genga_params_t &p) {
     return std::min(std::max(p.slevels, 1), kMaxLevels);
 }
@@ -166,6 +205,7 @@ void free_all(genga_system *s) {
     dfree(s->kick_part); dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
     dfree(s->gsize); dfree(s->goff); dfree(s->gfill); dfree(s->glist); dfree(s->member);
     dfree(s->slotof); dfree(s->bucket_list); bsm_release(s); dfree(s->red); dfree(s->scr.scan_blocks);
+    dfree(s->alive); dfree(s->mlog);
     for (int k = 0; k < 4; k++) {
         if (s->side[k]) cudaStreamDestroy(s->side[k]);
         if (s->ev_join[k]) cudaEventDestroy(s->ev_join[k]);
@@ -173,12 +213,14 @@ void free_all(genga_system *s) {
     }
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     s->ev_fork = nullptr;
+    free_marks(s);
 }
 
 template <typename T>
 int read_dev(genga_system *s, T *host, const T *dev) {
     CU(cudaMemcpyAsync(host, dev, sizeof(T), cudaMemcpyDeviceToHost, s->stream));
     CU(cudaStreamSynchronize(s->stream));
+    ++s->host_syncs;
     return GENGA_OK;
 }
 
@@ -189,8 +231,14 @@ int device_errors(genga_system *s) {
     CU(cudaMemsetAsync(&s->ctr->err, 0, sizeof(unsigned), s->stream));
     if (err & kErrBadState) return fail(s, GENGA_EBADSTATE, "non-finite state or body at the origin");
     if (err & kErrKepler) return fail(s, GENGA_ENONCONV, "Kepler solve hit kepler_max_iter");
+    if (err & kErrTimeout)
+        return fail(s, GENGA_ETIMEOUT, "Bulirsch-Stoer: a group call exceeded its time limit of %.3g s",
+                    1e-9 * (double)s->bs_group_limit_ns);
     if (err & kErrBS) return fail(s, GENGA_ENONCONV, "Bulirsch-Stoer hit bs_max_steps");
     if (err & kErrUnionFind) return fail(s, GENGA_ETIMEOUT, "grouping retry limit reached");
+    if (err & kErrMergeLog)
+        return fail(s, GENGA_ECAPACITY, "merger log full (%lld records): read it with genga_get_mergers",
+                    (long long)s->mlog_cap);
     return fail(s, GENGA_ECAPACITY, "capacity exceeded (error word 0x%x)", err);
 }
 
@@ -241,10 +289,26 @@ int detect(genga_system *s, const uint2 *in, int64_t nin, int level, int64_t *np
     if ((int64_t)c > s->pair_cap[level]) return fail(s, GENGA_ECAPACITY, "pair list overflow");
     *np = (int64_t)c;
     s->npairs_host[level] = *np;
+    if (s->pair_log) {
+        std::vector<uint2> h((size_t)c);
+        if (c) {
+            CU(cudaMemcpyAsync(h.data(), s->pairs[level], sizeof(uint2) * (size_t)c, cudaMemcpyDeviceToHost,
+                               s->stream));
+            CU(cudaStreamSynchronize(s->stream));
+        }
+        std::sort(h.begin(), h.end(), [](const uint2 &a, const uint2 &b) {
+            return a.x < b.x || (a.x == b.x && a.y < b.y);
+        });
+        if (s->log_off.empty()) s->log_off.push_back(0);
+        s->log_level.push_back(level);
+        for (const uint2 &q : h) { s->log_pairs.push_back(q.x); s->log_pairs.push_back(q.y); }
+        s->log_off.push_back((int64_t)(s->log_pairs.size() / 2));
+    }
     return GENGA_OK;
 }
 
 int bs_groups(genga_system *s, int level, int64_t np, double dt_l) {
+    TRY(mark(s, GENGA_PH_GROUPING));
     CU(build_groups(s, level, np));
     return run_bs(s, level, dt_l, np);
 }
@@ -252,20 +316,27 @@ int bs_groups(genga_system *s, int level, int64_t np, double dt_l) {
 int senc(genga_system *s, int level, double dt_l) {
     const int L = levels_of(s->p);
     int nb = 0;
+    TRY(mark(s, GENGA_PH_LEVELSETUP));
     CU(build_bodies(s, level - 1, level, &nb));
     CU(launch_restore(s, level - 1, s->bodies[level], nb));
     for (int sub = 0; sub < s->p.substeps; sub++) {
+        TRY(mark(s, GENGA_PH_RCRITS));
         CU(launch_rcrit(s, level, dt_l, s->bodies[level], nb));
+        TRY(mark(s, GENGA_PH_KICKS));
         CU(launch_kick_pairs(s, level, 0.5 * dt_l, nb));
+        TRY(mark(s, GENGA_PH_FGS));
         CU(launch_drift(s, level, dt_l, s->bodies[level], nb));
         int64_t np = 0;
+        TRY(mark(s, GENGA_PH_DETECTS));
         TRY(detect(s, s->pairs[level - 1], s->npairs_host[level - 1], level, &np));
         s->stats.n_pairs[level] += np;
         if (np > 0) {
+            TRY(mark(s, GENGA_PH_CSRS));
             CU(build_csr(s, level, np));
             if (level < L - 1) TRY(senc(s, level + 1, dt_l / s->p.substeps));
             else TRY(bs_groups(s, level, np, dt_l));
         }
+        TRY(mark(s, GENGA_PH_KICKS));
         CU(launch_kick_pairs(s, level, 0.5 * dt_l, nb));
     }
     return GENGA_OK;
@@ -275,12 +346,16 @@ int one_step(genga_system *s) {
     const double dt = s->p.dt;
     const int n = (int)s->n;
     const int L = levels_of(s->p);
+    TRY(mark(s, GENGA_PH_RCRIT));
     CU(launch_rcrit(s, 0, dt, nullptr, n));
+    TRY(mark(s, GENGA_PH_KICK1));
     TRY(kick(s, 0.5 * dt, true, nullptr));
     // the candidate count before HC and the drift move the bodies: a list
     // that overflowed is recomputed from the positions the pre-check saw
     int64_t ncand = 0;
+    TRY(mark(s, GENGA_PH_CANDCOUNT));
     TRY(settle_candidates(s, &ncand));
+    TRY(mark(s, GENGA_PH_HC_DRIFT));
     CU(launch_hc(s, 0.5 * dt));
     CU(launch_drift(s, 0, dt, nullptr, n));
     s->stats.n_candidates += ncand;
@@ -288,17 +363,22 @@ int one_step(genga_system *s) {
     s->npairs_host[0] = 0;
     if (ncand > 0) {
         int64_t np = 0;
+        TRY(mark(s, GENGA_PH_DETECT0));
         TRY(detect(s, s->cand, ncand, 0, &np));
         s->stats.n_pairs[0] += np;
         if (np > 0) {
+            TRY(mark(s, GENGA_PH_CSR0));
             CU(build_csr(s, 0, np));
             if (L > 1) TRY(senc(s, 1, dt / s->p.substeps));
             else TRY(bs_groups(s, 0, np, dt));
         }
     }
+    TRY(mark(s, GENGA_PH_HC2));
     CU(launch_hc(s, 0.5 * dt));
+    TRY(mark(s, GENGA_PH_KICK2));
     TRY(kick(s, 0.5 * dt, false, nullptr));
-    return GENGA_OK;
+    TRY(mark(s, -1));
+    return fold_marks(s);
 }
 
 int collect_stats(genga_system *s) {
@@ -313,12 +393,14 @@ int collect_stats(genga_system *s) {
     s->stats.bs_fail = (int64_t)c.bs_fail;
     s->stats.kepler_fail = (int64_t)c.kepler_fail;
     s->stats.kernel_launches = s->launches;
+    s->stats.host_syncs = s->host_syncs;
     return GENGA_OK;
 }
 
 int reset_stats(genga_system *s) {
     memset(&s->stats, 0, sizeof(s->stats));
     s->launches = 0;
+    s->host_syncs = 0;
     CU(cudaMemsetAsync(&s->ctr->kepler_fail, 0, 7 * sizeof(unsigned long long), s->stream));
     return GENGA_OK;
 }
@@ -341,6 +423,8 @@ int copy_pairs_sorted(genga_system *s, const uint2 *dev, int64_t count, uint32_t
 }  // namespace
 
 namespace genga {
+int phase_mark(genga_system *s, int phase) { return mark(s, phase); }
+
 int ensure_pair_capacity(genga_system *s, int level, int64_t np) {
     if (np <= s->pair_cap[level]) return GENGA_OK;
     return alloc_pairs(s, level, np + np / 2 + 1024);
@@ -359,7 +443,7 @@ void genga_default_params(genga_params_t *p) {
     p->n1 = 3.0;
     p->n2 = 0.4;
     p->f_pc = 4.0;
-    p->bs_tol = 1e-15;
+    p->bs_tol = 1e-13;
     p->slevels = 1;
     p->substeps = 1;
     p->precision = GENGA_FP64;
@@ -389,6 +473,11 @@ int genga_create(genga_system_t **out, const genga_params_t *p, int64_t n, doubl
     if (rc != GENGA_OK) { free_all(s); delete s; return rc; }
     *out = s;
     return GENGA_OK;
+}
+
+int genga_init_system(genga_system_t **out, const genga_params_t *p, int64_t n, double *pos, double *vel,
+                      const double *mass, void *stream) {
+    return genga_create(out, p, n, pos, vel, mass, stream);
 }
 
 void genga_destroy(genga_system_t *s) {
@@ -625,6 +714,71 @@ int genga_get_stats(genga_system_t *s, genga_stats_t *st) {
     if (!s || !st) return GENGA_EINVAL;
     *st = s->stats;
     return GENGA_OK;
+}
+
+int genga_set_wait_limits(genga_system_t *s, double bs_group_seconds, double barrier_seconds,
+                          int32_t barrier_absent_blocks) {
+    if (!s || barrier_absent_blocks < 0 || !(bs_group_seconds < 1e9) || !(barrier_seconds < 1e9))
+        return GENGA_EINVAL;
+    s->bs_group_limit_ns = bs_group_seconds < 0 ? 10000000000ull
+                                                : (unsigned long long)(bs_group_seconds * 1e9);
+    s->barrier_limit_ns = barrier_seconds < 0 ? 2000000000ull
+                                              : (unsigned long long)(barrier_seconds * 1e9);
+    s->barrier_absent = (unsigned)barrier_absent_blocks;
+    return GENGA_OK;
+}
+
+int genga_set_pair_log(genga_system_t *s, int enable) {
+    if (!s) return GENGA_EINVAL;
+    s->pair_log = enable != 0;
+    s->log_level.clear();
+    s->log_off.clear();
+    s->log_pairs.clear();
+    return GENGA_OK;
+}
+
+int genga_get_pair_log(genga_system_t *s, int32_t *level, int64_t *off, uint32_t *ij, int64_t max_events,
+                       int64_t max_pairs, int64_t *n_events, int64_t *n_pairs) {
+    if (!s) return GENGA_EINVAL;
+    const int64_t ne = (int64_t)s->log_level.size();
+    const int64_t np = (int64_t)(s->log_pairs.size() / 2);
+    if (n_events) *n_events = ne;
+    if (n_pairs) *n_pairs = np;
+    if (level && off) {
+        if (max_events < ne) return fail(s, GENGA_ECAPACITY, "pair log: %lld events", (long long)ne);
+        for (int64_t k = 0; k < ne; k++) level[k] = s->log_level[(size_t)k];
+        for (int64_t k = 0; k <= ne; k++) off[k] = ne ? s->log_off[(size_t)k] : 0;
+    }
+    if (ij) {
+        if (max_pairs < np) return fail(s, GENGA_ECAPACITY, "pair log: %lld pairs", (long long)np);
+        std::copy(s->log_pairs.begin(), s->log_pairs.end(), ij);
+    }
+    return GENGA_OK;
+}
+
+int genga_set_timing(genga_system_t *s, int enable) {
+    if (!s) return GENGA_EINVAL;
+    CU(cudaStreamSynchronize(s->stream));
+    s->timing = enable != 0;
+    s->nmarks = 0;
+    s->timed_steps = 0;
+    for (double &v : s->phase_ms) v = 0.0;
+    return GENGA_OK;
+}
+
+int genga_get_phase_ms(genga_system_t *s, double *ms, int64_t *nsteps) {
+    if (!s || !ms) return GENGA_EINVAL;
+    for (int k = 0; k < GENGA_NPHASES; k++) ms[k] = s->phase_ms[k];
+    if (nsteps) *nsteps = s->timed_steps;
+    return GENGA_OK;
+}
+
+const char *genga_phase_name(int phase) {
+    static const char *const names[GENGA_NPHASES] = {
+        "rcrit", "kick1", "cand_count", "hc_drift", "detect0", "csr0", "level_setup", "rcritS",
+        "kickS", "fgS", "detectS", "csrS", "grouping", "buckets", "bs_small", "bs_large", "hc2",
+        "kick2"};
+    return (phase >= 0 && phase < GENGA_NPHASES) ? names[phase] : nullptr;
 }
 
 }  // extern "C"

@@ -2,8 +2,8 @@
 //   a_i = G sum_{j != i} m_j K(r_ij; rc_ij) (x_j - x_i) / r_ij^3
 // and the close-encounter pre-check (Appendix A) as a separate FP32 pass.
 //
-// GB300 design.  The kick is bound by the FP64 pipe (about 2 DFMA per clock per
-// SM on GB300, 1/64 of FP32), so the kernel minimises FP64 instructions per
+// GB300 design.  The kick is bound by the FP64 pipe (1.68 FP64 instructions per
+// clock per SM on GB300, measured, 1/74 of FP32), so the kernel minimises FP64 instructions per
 // pair and keeps everything else on the FP32, MUFU and integer pipes:
 //   * j bodies are staged in shared memory in tiles of 256 (x, y, z, m and the
 //     per-body thresholds); every thread owns one target i;
@@ -16,14 +16,15 @@
 //     (precheck_kernel below), so the FP64-bound kick carries none of it;
 //   * MIXED: FP64 displacement; r^2 formed as an unevaluated sum of two floats
 //     from an exact integer split of the displacement (no FP64 work); FP32
-//     rsqrt seed y0; one FP64 Newton residual e = 1 - r^2 y0^2 (its leading
-//     part in one FP64 FMA on an exact float product, the float tails added
-//     in FP32); r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) = m y0^3 + corr in
-//     float-float; FP64 accumulation of (m y0^3) dx, the corrections corr dx
-//     (< 2^-19 of each term) summed in float-float per tile and added to the
-//     FP64 sums once per tile; per-tile sums folded with TwoSum:
-//     7 FP64 instructions per pair.
-//     FP64: CUDA's double rsqrt, 18 FP64 instructions per pair.
+//     rsqrt seed y0; one Newton correction from the residual e = 1 - r^2 y0^2
+//     (its leading part 1 - u y0 by an FP32 FMA on the exact float product
+//     u y0, rounded once: the float a double residual would be rounded to;
+//     the tails in FP32); r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) = m y0^3 + corr
+//     in float-float; FP64 accumulation of (m y0^3) dx, the corrections
+//     corr dx (< 2^-19 of each term) summed in float-float per tile and added
+//     to the FP64 sums once per tile; per-tile sums folded with TwoSum:
+//     6 FP64 instructions per pair (3 subtractions, 3 accumulations).
+//     FP64: CUDA's double rsqrt, 17 FP64 instructions per pair (counted).
 #include "common.cuh"
 
 namespace genga {
@@ -58,44 +59,6 @@ __device__ __forceinline__ float r2_to_float_trunc(double r2) {
     unsigned lo = (unsigned)__double2loint(r2);
     unsigned fb = (hi >= 0x38100000u) ? (((hi - 0x38000000u) << 3) | (lo >> 29)) : 0u;
     return __uint_as_float(fb);
-}
-
-// Double with the value of a positive normal float (exact).
-__device__ __forceinline__ double float_to_double_exact(unsigned fb) {
-    return __hiloint2double((int)((fb >> 3) + 0x38000000u), (int)(fb << 29));
-}
-
-// (hi, lo) += v in float-float: TwoSum of hi and v, the rounding error into lo.
-__device__ __forceinline__ void float_two_sum_acc(float &hi, float &lo, float v) {
-    const float s = hi + v;
-    const float bb = s - hi;
-    lo += (hi - (s - bb)) + (v - bb);
-    hi = s;
-}
-
-// Double with the value of a float (exact), for any sign; zero and subnormal
-// floats give a signed zero.  Integer operations only.
-__device__ __forceinline__ double f64_of_f32_any(float f) {
-    const unsigned fb = __float_as_uint(f);
-    const unsigned mag = fb & 0x7fffffffu, sgn = fb & 0x80000000u;
-    const unsigned hi = (mag >= 0x00800000u) ? (sgn | ((mag >> 3) + 0x38000000u)) : sgn;
-    const unsigned lo = (mag >= 0x00800000u) ? (mag << 29) : 0u;
-    return __hiloint2double((int)hi, (int)lo);
-}
-
-// v = hi + lo exactly up to 2^-47 |v|: hi is v with the mantissa truncated
-// to float precision, lo the 29 discarded mantissa bits rounded to a float.
-// Integer operations, one integer-to-float conversion and one FP32 scale;
-// |v| < 2^-74 gives lo = 0, |v| < 2^-126 also hi = 0 (signed zeros).
-__device__ __forceinline__ void split_f64(double v, float &hi, float &lo) {
-    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
-    const unsigned mag = hw & 0x7fffffffu, sgn = hw & 0x80000000u;
-    const bool normal = mag >= 0x38100000u;
-    hi = __uint_as_float(normal ? (sgn | ((mag - 0x38000000u) << 3) | (lw >> 29)) : sgn);
-    const unsigned E = mag >> 20;                       // biased double exponent
-    float l = 0.0f;
-    if (E >= 949u) l = __uint2float_rn(lw & 0x1fffffffu) * __uint_as_float((E - 948u) << 23);
-    lo = __uint_as_float(__float_as_uint(l) | sgn);
 }
 
 // TP: semi-active test particles (Sec. 8.1): a test particle i takes only the
@@ -211,15 +174,15 @@ kick_kernel(KickArgs A)
                 if (MIXED) {
                     // FP32 seed y0 ~ r^-1; Newton residual e = 1 - r^2 y0^2 with
                     // r^2 = Rh + Rl and Rh y0 = u + ue (exact float product): 1 - u y0
-                    // in one FP64 FMA (exact product, one rounding), the tails
-                    // ue y0 + Rl y0^2 (~2^-24) in FP32.
+                    // by one FP32 FMA (the product u y0 is exact inside the FMA, so the
+                    // result is 1 - u y0 rounded once to a float, error < 2^-46), the
+                    // tails ue y0 + Rl y0^2 (~2^-24) in FP32.
                     // r^-3 = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 1.5 e + 1.875 e^2 + O(e^3)),
                     // |e| < 2^-20.  m y0^3 is formed exactly enough (~2^-46) as a sum of
                     // two floats, the correction in FP32, and the parts meet in one FP64 add.
                     const float y0f = rsqrtf(Rh);
                     const float u = Rh * y0f, ue = fmaf(Rh, y0f, -u);   // Rh y0 = u + ue exactly
-                    const double e1 = fma(-float_to_double_exact(__float_as_uint(u)),
-                                          float_to_double_exact(__float_as_uint(y0f)), 1.0);
+                    const float e1 = fmaf(-u, y0f, 1.0f);
                     const float p = y0f * y0f, pe = fmaf(y0f, y0f, -p);
                     const float q = p * y0f;
                     float qe = fmaf(p, y0f, -q);
@@ -228,7 +191,7 @@ kick_kernel(KickArgs A)
                     float ce = fmaf(q, mh, -ch);
                     ce = fmaf(q, ml, ce);
                     ce = fmaf(qe, mh, ce);
-                    const float ef = f32_of_f64_rn(e1) - fmaf(ue, y0f, Rl * p);
+                    const float ef = e1 - fmaf(ue, y0f, Rl * p);
                     const float corr = fmaf(ch, fmaf(1.875f * ef, ef, 1.5f * ef), ce);
                     s = f64_of_f32_any(ch);
                     float_two_sum_acc(cxh, cxl, corr * hx);

@@ -11,6 +11,7 @@
 //
 // Scratch layout (doubles): rc^2 [n], FP32 thresholds [n floats], then the
 // kick's per-chunk partial sums [nchunk][6][n], nchunk reduced as needed to fit.
+#include <cuda.h>
 #include <mutex>
 
 #include "common.cuh"
@@ -22,7 +23,44 @@ constexpr size_t kStaticDoubles = size_t(1) << 21;   // 16 MiB
 static __device__ __align__(256) double g_kick_static_scratch[kStaticDoubles];
 
 std::mutex g_setup_mutex;
-double *g_scratch_addr[256] = {};   // device address of the array, per device ordinal
+// device address of the array per device ordinal, with the id of the context
+// it was looked up in: cudaDeviceReset destroys the device's primary context,
+// the next call creates a new one (new id) and the library's device code is
+// loaded again, possibly at another address -- so a changed id means set-up
+// again
+struct ScratchAddr {
+    double *addr;
+    unsigned long long ctx;
+};
+ScratchAddr g_scratch[256] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Id of the current context (driver entry points looked up through the
+// runtime, so the library does not link the driver library); 0 when unknown.
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 __global__ void static_thresholds_kernel(int n, const double *rc, double *rc2, float *thr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,14 +85,17 @@ extern "C" int genga_kick_static(int64_t n, const double *pos, const double *mas
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return GENGA_ECUDA;
     double *base = nullptr;
     {
-        // one-time set-up per device, with that device current
+        // set-up once per device (and again after a device reset), with that
+        // device current
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_addr[dev]) {
+        const unsigned long long id = current_ctx_id();
+        if (!g_scratch[dev].addr || id == 0 || id != g_scratch[dev].ctx) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_kick_static_scratch) != cudaSuccess || !p) return GENGA_ECUDA;
-            g_scratch_addr[dev] = (double *)p;
+            g_scratch[dev].addr = (double *)p;
+            g_scratch[dev].ctx = current_ctx_id();   // the look-up made the context current
         }
-        base = g_scratch_addr[dev];
+        base = g_scratch[dev].addr;
     }
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GENGA_ECUDA;

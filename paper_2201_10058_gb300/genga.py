@@ -30,7 +30,13 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_adjoint_backward", "genga_adjoint_export", "genga_ensemble_create", "genga_ensemble_destroy",
             "genga_ensemble_last_error", "genga_ensemble_step", "genga_ensemble_set_tile",
             "genga_ensemble_autotune", "genga_ensemble_angmom", "genga_ensemble_get_stats",
-            "genga_tune_levels"]
+            "genga_tune_levels", "genga_set_timing", "genga_get_phase_ms", "genga_phase_name",
+            "genga_measure_pipe_rates", "genga_init_system", "genga_step_backward",
+            "genga_init_ensemble", "genga_step_ensemble", "genga_set_pair_log",
+            "genga_get_pair_log", "genga_set_wait_limits", "genga_set_collisions",
+            "genga_get_mergers", "genga_get_alive", "genga_remove_merged"]
+
+NPHASES = 18
 
 KICK_STATIC_MAX_N = 279616
 
@@ -64,7 +70,8 @@ class Stats(C.Structure):
     _fields_ = [("n_candidates", C.c_int64), ("n_pairs", C.c_int64 * 8),
                 ("n_groups", C.c_int64), ("max_group", C.c_int64), ("bs_steps", C.c_int64),
                 ("bs_rejects", C.c_int64), ("kepler_fail", C.c_int64), ("bs_fail", C.c_int64),
-                ("kernel_launches", C.c_int64), ("bs_max_attempts", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("bs_max_attempts", C.c_int64),
+                ("host_syncs", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {"n_candidates": self.n_candidates, "n_pairs": list(self.n_pairs),
@@ -72,7 +79,7 @@ class Stats(C.Structure):
                 "bs_steps": self.bs_steps, "bs_rejects": self.bs_rejects,
                 "kepler_fail": self.kepler_fail, "bs_fail": self.bs_fail,
                 "kernel_launches": self.kernel_launches,
-                "bs_max_attempts": self.bs_max_attempts}
+                "bs_max_attempts": self.bs_max_attempts, "host_syncs": self.host_syncs}
 
 
 _lib = None
@@ -101,6 +108,10 @@ def load(build_if_missing: bool = True):
         L.genga_default_params.argtypes = [_P(Params)]
         L.genga_default_params.restype = None
         L.genga_create.argtypes = [_P(_VP), _P(Params), C.c_int64, _VP, _VP, _VP, _VP]
+        L.genga_init_system.argtypes = [_P(_VP), _P(Params), C.c_int64, _VP, _VP, _VP, _VP]
+        L.genga_step_backward.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP]
+        L.genga_init_ensemble.argtypes = [_P(_VP), _P(Params), _P(EnsembleDesc), _VP]
+        L.genga_step_ensemble.argtypes = [_VP, C.c_int64]
         L.genga_destroy.argtypes = [sysp]
         L.genga_destroy.restype = None
         L.genga_last_error.argtypes = [sysp]
@@ -141,8 +152,21 @@ def load(build_if_missing: bool = True):
         L.genga_ensemble_autotune.argtypes = [_VP, C.c_int64, _P(C.c_int), _P(C.c_int)]
         L.genga_ensemble_angmom.argtypes = [_VP, _VP]
         L.genga_ensemble_get_stats.argtypes = [_VP, _P(Stats)]
+        L.genga_set_timing.argtypes = [sysp, C.c_int]
+        L.genga_get_phase_ms.argtypes = [sysp, _VP, _P(C.c_int64)]
+        L.genga_phase_name.argtypes = [C.c_int]
+        L.genga_phase_name.restype = C.c_char_p
+        L.genga_set_wait_limits.argtypes = [sysp, C.c_double, C.c_double, C.c_int32]
+        L.genga_set_collisions.argtypes = [sysp, _VP, _VP, _VP, C.c_double]
+        L.genga_get_mergers.argtypes = [sysp, _VP, C.c_int64, _P(C.c_int64), _P(C.c_double)]
+        L.genga_get_alive.argtypes = [sysp, _VP]
+        L.genga_remove_merged.argtypes = [sysp, _P(C.c_int64), _VP]
+        L.genga_set_pair_log.argtypes = [sysp, C.c_int]
+        L.genga_get_pair_log.argtypes = [sysp, _VP, _VP, _VP, C.c_int64, C.c_int64, _P(C.c_int64),
+                                         _P(C.c_int64)]
+        L.genga_measure_pipe_rates.argtypes = [_P(C.c_double)] * 5
         void_fns = ("genga_default_params", "genga_destroy", "genga_last_error",
-                    "genga_ensemble_destroy", "genga_ensemble_last_error")
+                    "genga_ensemble_destroy", "genga_ensemble_last_error", "genga_phase_name")
         for name in EXPORTED:
             if name not in void_fns:
                 getattr(L, name).restype = C.c_int
@@ -168,6 +192,16 @@ def kick_static(pos, mass, rc, G: float, dt_half: float, precision: int, vel=Non
     ptr = lambda t: None if t is None else _VP(t.data_ptr())
     return L.genga_kick_static(int(mass.shape[0]), ptr(pos), ptr(mass), ptr(rc), G, dt_half,
                                precision, ptr(vel), ptr(acc_out), _VP(s.cuda_stream))
+
+
+def measure_pipe_rates() -> dict:
+    """Thread-level FP64 FMA / add / multiply, FP32 FMA and MUFU rsqrt operations
+    per clock per SM on the current device (genga_measure_pipe_rates)."""
+    v = [C.c_double() for _ in range(5)]
+    rc = load().genga_measure_pipe_rates(*[C.byref(x) for x in v])
+    if rc != 0:
+        raise GengaError(rc, "genga_measure_pipe_rates failed")
+    return dict(zip(("dfma", "dadd", "dmul", "ffma", "rsqrt"), (x.value for x in v)))
 
 
 def _np_ptr(a: np.ndarray):
@@ -196,10 +230,10 @@ class System:
         self.params = params if params is not None else default_params()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = _VP()
-        rc = self._lib.genga_create(C.byref(h), C.byref(self.params), self.n, pos.data_ptr(),
-                                    vel.data_ptr(), mass.data_ptr(), _VP(self.stream.cuda_stream))
+        rc = self._lib.genga_init_system(C.byref(h), C.byref(self.params), self.n, pos.data_ptr(),
+                                         vel.data_ptr(), mass.data_ptr(), _VP(self.stream.cuda_stream))
         if rc != 0:
-            raise GengaError(rc, "genga_create failed")
+            raise GengaError(rc, "genga_init_system failed")
         self._h = h
 
     # -- helpers
@@ -313,6 +347,91 @@ class System:
         self._check(self._lib.genga_get_stats(self._h, C.byref(st)))
         return st.as_dict()
 
+    # -- collisions (Sec. 7.1-7.2)
+    def set_collisions(self, radius, spin=None, precision: float = 0.0):
+        """Switches collisions on.  radius: (n,) float64 CUDA tensor; spin: (3, n)
+        (zeros when None).  Mergers then write the masses, radii and spins."""
+        import torch
+        if spin is None:
+            spin = torch.zeros((3, self.n), dtype=torch.float64, device=self.mass.device)
+        for t, name, shape in ((radius, "radius", (self.n,)), (spin, "spin", (3, self.n))):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()) or tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of shape {shape}")
+        self.radius, self.spin = radius, spin
+        self._check(self._lib.genga_set_collisions(self._h, _VP(self.mass.data_ptr()),
+                                                   _VP(radius.data_ptr()), _VP(spin.data_ptr()),
+                                                   precision))
+
+    def mergers(self):
+        """Mergers since the previous call, in integration order: an (k, 6) array
+        (time in its Bulirsch-Stoer call, i, j, r_ij, R_i + R_j, dU) and the sum of
+        their dU in that order."""
+        n, dU = C.c_int64(), C.c_double()
+        self._check(self._lib.genga_get_mergers(self._h, None, 0, C.byref(n), None))
+        out = np.zeros((max(n.value, 1), 6))
+        self._check(self._lib.genga_get_mergers(self._h, _np_ptr(out), n.value, C.byref(n),
+                                                C.byref(dU)))
+        return out[:n.value].copy(), dU.value
+
+    def alive(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.uint8)
+        self._check(self._lib.genga_get_alive(self._h, _np_ptr(out)))
+        return out
+
+    def remove_merged(self) -> np.ndarray:
+        """Takes the merged-away bodies out (genga_remove_merged); pos, vel, mass,
+        radius and spin become views of the compacted bodies.  Returns each new
+        body's former index."""
+        n_new = C.c_int64()
+        idx = np.zeros(self.n, dtype=np.int64)
+        self._check(self._lib.genga_remove_merged(self._h, C.byref(n_new), _np_ptr(idx)))
+        k = n_new.value
+        if k != self.n:
+            flat = lambda t, c: t.view(-1)[:c * k]
+            self.pos = flat(self.pos, 3).view(3, k)
+            self.vel = flat(self.vel, 3).view(3, k)
+            self.mass = flat(self.mass, 1)
+            self.radius = flat(self.radius, 1)
+            self.spin = flat(self.spin, 3).view(3, k)
+            self.n = k
+        return idx[:k].copy()
+
+    def set_wait_limits(self, bs_group_seconds: float = -1.0, barrier_seconds: float = -1.0,
+                        barrier_absent_blocks: int = 0):
+        """Wall-clock limits of the bounded device waits (negative: default)."""
+        self._check(self._lib.genga_set_wait_limits(self._h, bs_group_seconds, barrier_seconds,
+                                                    barrier_absent_blocks))
+
+    def set_pair_log(self, enable: bool = True):
+        """Switches the detection log on or off (and clears it)."""
+        self._check(self._lib.genga_set_pair_log(self._h, int(enable)))
+
+    def pair_log(self) -> list:
+        """Every detection logged since set_pair_log(True), in order: a list of
+        (level, pairs (k, 2) uint32 sorted by (i, j))."""
+        ne, npairs = C.c_int64(), C.c_int64()
+        self._check(self._lib.genga_get_pair_log(self._h, None, None, None, 0, 0, C.byref(ne),
+                                                 C.byref(npairs)))
+        lev = np.zeros(max(ne.value, 1), dtype=np.int32)
+        off = np.zeros(ne.value + 1, dtype=np.int64)
+        ij = np.zeros((max(npairs.value, 1), 2), dtype=np.uint32)
+        self._check(self._lib.genga_get_pair_log(self._h, _np_ptr(lev), _np_ptr(off), _np_ptr(ij),
+                                                 ne.value, npairs.value, C.byref(ne), C.byref(npairs)))
+        return [(int(lev[k]), ij[off[k]:off[k + 1]].copy()) for k in range(ne.value)]
+
+    def set_timing(self, enable: bool = True):
+        """Switches the per-phase step timing on or off (clears the sums)."""
+        self._check(self._lib.genga_set_timing(self._h, int(enable)))
+
+    def phase_ms(self) -> tuple[dict, int]:
+        """Device time per phase summed over the steps timed since set_timing,
+        and the number of those steps."""
+        out = np.zeros(NPHASES)
+        ns = C.c_int64()
+        self._check(self._lib.genga_get_phase_ms(self._h, _np_ptr(out), C.byref(ns)))
+        names = [self._lib.genga_phase_name(k).decode() for k in range(NPHASES)]
+        return dict(zip(names, out.tolist())), ns.value
+
     # -- adjoint (frozen encounters)
     def adjoint_forward(self, nsteps: int, checkpoint_every: int):
         self._check(self._lib.genga_adjoint_forward(self._h, nsteps, checkpoint_every))
@@ -347,7 +466,7 @@ class System:
         gx = torch.empty_like(lam_x)
         gv = torch.empty_like(lam_v)
         gm = torch.empty_like(self.mass)
-        self._check(self._lib.genga_adjoint_backward(self._h, _VP(lam_x.data_ptr()),
+        self._check(self._lib.genga_step_backward(self._h, _VP(lam_x.data_ptr()),
                                                      _VP(lam_v.data_ptr()), _VP(gx.data_ptr()),
                                                      _VP(gv.data_ptr()), _VP(gm.data_ptr())))
         return gx, gv, gm
@@ -380,10 +499,10 @@ class Ensemble:
         d.c_light, d.gr, d.tides = wl.c_light, int(gr), int(tides)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = _VP()
-        rc = self._lib.genga_ensemble_create(C.byref(h), C.byref(p), C.byref(d),
-                                             _VP(self.stream.cuda_stream))
+        rc = self._lib.genga_init_ensemble(C.byref(h), C.byref(p), C.byref(d),
+                                           _VP(self.stream.cuda_stream))
         if rc != 0:
-            raise GengaError(rc, "genga_ensemble_create failed")
+            raise GengaError(rc, "genga_init_ensemble failed")
         self._h = h
         self.n_systems = wl.n_systems
 
@@ -393,7 +512,7 @@ class Ensemble:
             raise GengaError(rc, msg.decode() if msg else "")
 
     def step(self, nsteps: int = 1):
-        self._check(self._lib.genga_ensemble_step(self._h, nsteps))
+        self._check(self._lib.genga_step_ensemble(self._h, nsteps))
 
     def set_tile(self, threads: int, ctas_per_sm: int):
         self._check(self._lib.genga_ensemble_set_tile(self._h, threads, ctas_per_sm))

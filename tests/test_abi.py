@@ -31,6 +31,22 @@ def test_library_builds_and_exports_every_declared_symbol():
         assert re.search(rf"\bT {name}\b", out), name
 
 
+# the calls of the boundary's call list, by those names
+BOUNDARY_CALLS = ["genga_init_system", "genga_kick", "genga_hc", "genga_drift",
+                  "genga_build_encounters", "genga_step", "genga_energy", "genga_get_pairs",
+                  "genga_init_ensemble", "genga_step_ensemble", "genga_step_backward",
+                  "genga_last_error", "genga_destroy"]
+
+
+def test_boundary_call_names_are_exported():
+    from paper_2201_10058_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    declared = _declared()
+    for name in BOUNDARY_CALLS:
+        assert name in declared, name
+        assert hasattr(lib, name), name
+
+
 def test_binding_lists_every_declared_symbol():
     from paper_2201_10058_gb300 import genga
     assert sorted(genga.EXPORTED) == _declared()
@@ -48,9 +64,9 @@ def test_create_rejects_bad_arguments_without_gpu():
     L = genga.load()
     p = genga.default_params()
     h = ctypes.c_void_p()
-    assert L.genga_create(ctypes.byref(h), ctypes.byref(p), 0, None, None, None, None) == -1
+    assert L.genga_init_system(ctypes.byref(h), ctypes.byref(p), 0, None, None, None, None) == -1
     p.slevels = 99
-    assert L.genga_create(ctypes.byref(h), ctypes.byref(p), 8, 1, 1, 1, None) == -1
+    assert L.genga_init_system(ctypes.byref(h), ctypes.byref(p), 8, 1, 1, 1, None) == -1
 
 
 def test_oracle_has_no_cuda_dependency():
