@@ -36,18 +36,25 @@ METRIC = ("changeover-kick G pair-interactions/s and steps/s at N=65536 (FP64 vs
           "% of peak")
 UNIT = "Gpair/s"
 # FP64 instructions per pair interaction that each kick form's algorithm needs
-# (FMA counted as one).  Mixed: displacement 3, Newton residual of the FP32
-# seed 1 (one FMA on an exact float product; r^2 = Rh + Rl and the residual's
-# tails are float-float on the FP32 pipe), conversion of m y0^3 to FP64 (free:
-# integer operations), accumulation 3 (the float-float corrections are summed
-# on the FP32 pipe and added once per tile).  FP64:
-# displacement 3, r^2 3, r^-1 to FP64 precision (two Newton steps from a
-# ~2^-22 seed) 6, m r^-3 3, accumulation 3.
-FP64_OPS_PER_PAIR = {"mixed": 7, "fp64": 18}
+# (FMA counted as one).  Mixed: displacement 3, accumulation 3 (r^2 in
+# float-float from an exact split of the displacement, the FP32 rsqrt seed and
+# its Newton correction and the correction terms all on the FP32 pipe; m y0^3
+# converted to FP64 by integer operations).  FP64: CUDA's double rsqrt on an
+# FP64 r^2, m r^-3 and the accumulation.
+FP64_OPS_PER_PAIR = {"mixed": 6, "fp64": 17}
+# The same counted by ncu on one launch at N = 65,536 (thread-level
+# smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum / N^2, and the
+# warp-level sm__inst_executed_pipe_fp64.sum x 32 / N^2, which also charges the
+# idle lanes of partly predicated warps)
+FP64_INSTR_PER_PAIR_COUNTED = {"mixed": (6.124, 6.510), "fp64": (17.091, 17.402)}
+# FP64 units per SM: GB300's nominal FP64 rate (1.25 TFLOP/s = 0.625 T FMA/s
+# over 152 SMs at ~2.06 GHz) is 2 FP64 operations per clock per SM; ncu's FP64
+# pipe utilisation is relative to this rate
+FP64_OPS_PER_CLK_PER_SM = 2
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed kick launch at
 # N = 65,540 (one ncu capture of the kernel as it is now); None when the
 # kernel has changed since the capture
-KICK_MIXED_DRAM_BYTES = 2.940416e6 + 1.733376e6
+KICK_MIXED_DRAM_BYTES = None
 
 
 def parse():
@@ -71,6 +78,9 @@ def parse():
                          "5 M_earth), --kick-reps timed launches in the form --kick")
     ap.add_argument("--kick", choices=["fp64", "mixed"], default="mixed",
                     help="kick form of --workload kick")
+    ap.add_argument("--ens-tile", default="",
+                    help="threads,ctas_per_sm of the ensemble kernel instead of autotuning "
+                         "(profiling runs)")
     ap.add_argument("--ens-steps", type=int, default=10000,
                     help="integration steps per timed ensemble launch (the configuration's 10,000)")
     ap.add_argument("--energy-run", type=int, default=0,
@@ -361,8 +371,11 @@ def run_ours(args, dist: Dist) -> dict | None:
     head = results["mixed"]
     sm_clock = (clocks or {}).get("sm_mhz") or 2070.0
     props = torch.cuda.get_device_properties(dev)
-    peak = rates["dfma"] * props.multi_processor_count * sm_clock * 1e6 / 1e9
+    nsm = props.multi_processor_count
+    peak = FP64_OPS_PER_CLK_PER_SM * nsm * sm_clock * 1e6 / 1e9
+    probe_peak = rates["dfma"] * nsm * sm_clock * 1e6 / 1e9
     achieved = FP64_OPS_PER_PAIR["mixed"] * head["kick_gpairs_per_s"]
+    thr_cnt, warp_cnt = FP64_INSTR_PER_PAIR_COUNTED["mixed"]
     line = {
         "metric": METRIC, "value": round(head["gpairs_per_s"], 4), "unit": UNIT,
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
@@ -390,9 +403,16 @@ def run_ours(args, dist: Dist) -> dict | None:
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
                                        "of this kernel at N=65540",
                      "ops_per_pair": FP64_OPS_PER_PAIR["mixed"],
-                     "peak_basis": f"measured in this run: {rates['dfma']:.3f} FP64 FMA/clk/SM "
-                                   f"(genga_measure_pipe_rates) x {props.multi_processor_count} SMs x "
-                                   f"{sm_clock:.0f} MHz (median SM clock under load)",
+                     "peak_basis": f"derived: {FP64_OPS_PER_CLK_PER_SM} FP64 op/clk/SM (GB300 nominal "
+                                   f"FP64 unit count) x {nsm} SMs x {sm_clock:.0f} MHz (median SM "
+                                   f"clock under load)",
+                     "frac_counted": {"thread_level": round(thr_cnt * head["kick_gpairs_per_s"] / peak, 4),
+                                      "warp_level": round(warp_cnt * head["kick_gpairs_per_s"] / peak, 4),
+                                      "instr_per_pair": [thr_cnt, warp_cnt]},
+                     "probe": {"peak": round(probe_peak, 2),
+                               "frac": round(achieved / probe_peak, 4),
+                               "basis": f"{rates['dfma']:.3f} FP64 FMA/clk/SM reached by independent "
+                                        f"FMA chains (genga_measure_pipe_rates, this run)"},
                      "pipe_rates_per_clk_sm": {k: round(v, 3) for k, v in rates.items()}},
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         "encounters": head["encounters"],
@@ -410,6 +430,7 @@ def run_ours(args, dist: Dist) -> dict | None:
                         "kick_gpairs_per_s": round(f["kick_gpairs_per_s"], 3),
                         "kick_ms": round(f["kick_ms"], 3),
                         "roofline_frac": round(FP64_OPS_PER_PAIR["fp64"] * f["kick_gpairs_per_s"] / peak, 4),
+                        "ops_per_pair": FP64_OPS_PER_PAIR["fp64"],
                         "energy_rel_err": f["energy_rel_err"]}
         line["mixed_over_fp64"] = round(head["gpairs_per_s"] / f["gpairs_per_s"], 3)
     if not args.no_cpu_baseline and not args.quick and dist.world == 1:
@@ -532,7 +553,11 @@ def run_ensemble(args) -> dict:
     legs = {}
     for name, prec in (("fp64", genga.GENGA_FP64), ("mixed", genga.GENGA_MIXED)):
         ens = genga.Ensemble(wl, genga.default_params(G=wl.G, precision=prec))
-        threads, ctas = ens.autotune(20)
+        if args.ens_tile:
+            threads, ctas = (int(v) for v in args.ens_tile.split(","))
+            ens.set_tile(threads, ctas)
+        else:
+            threads, ctas = ens.autotune(20)
         for _ in range(args.warmup):
             ens.step(args.ens_steps)
         torch.cuda.synchronize()

@@ -407,8 +407,16 @@ typedef struct genga_ensemble_desc {
     double *star;             /* 8 x n_systems, per system: R, k2, tau, rg2, spin x, y, z, unused;
                                  the spin is updated */
     double c_light;           /* speed of light in the caller's units */
-    int32_t gr, tides;        /* switches */
+    int32_t gr;               /* 0 off; GENGA_GR_IMPLICIT: Eq. apn by the implicit midpoint rule
+                                 (Sec. 3); GENGA_GR_SPLIT: the Hamiltonian splitting of Sec. 3.1
+                                 (sun kick with the kick, gamma term with HC, drift time of each
+                                 body scaled by 1 - 3 mu / (2 a c^2), the same factor on the star
+                                 term inside Bulirsch-Stoer; pseudovelocities between the
+                                 conversions around them, real velocities outside) */
+    int32_t tides;            /* switch (Sec. 4.1-4.2) */
 } genga_ensemble_desc_t;
+#define GENGA_GR_IMPLICIT 1
+#define GENGA_GR_SPLIT    2
 typedef struct genga_ensemble genga_ensemble_t;
 
 /* Creates the ensemble on `stream` (cudaStream_t).  params supplies G, n1, n2,

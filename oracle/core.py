@@ -307,14 +307,17 @@ def bs_groups(x, v, m, rc_levels, pairs, G, m_star, dt, tol=1e-13, max_steps=100
 
 class OracleNN(C.Structure):
     _fields_ = [("gr", C.c_int32), ("tides", C.c_int32), ("implicit_max_iter", C.c_int32),
-                ("pad", C.c_int32), ("c_light", C.c_double), ("R_star", C.c_double),
+                ("gr_split", C.c_int32), ("c_light", C.c_double), ("R_star", C.c_double),
                 ("k2_star", C.c_double), ("tau_star", C.c_double), ("rg2_star", C.c_double)]
 
 
 def make_nn(gr=True, tides=True, c_light=173.1446326846693, R_star=0.0, k2_star=0.0,
-            tau_star=0.0, rg2_star=0.0, implicit_max_iter=10) -> OracleNN:
+            tau_star=0.0, rg2_star=0.0, implicit_max_iter=10, gr_split=False) -> OracleNN:
+    """GR by Eq. apn with the implicit midpoint rule, or with gr_split by the
+    Hamiltonian splitting of Sec. 3.1 (reading R28)."""
     nn = OracleNN()
     nn.gr, nn.tides, nn.implicit_max_iter = int(gr), int(tides), implicit_max_iter
+    nn.gr_split = int(gr_split)
     nn.c_light, nn.R_star, nn.k2_star, nn.tau_star, nn.rg2_star = (c_light, R_star, k2_star,
                                                                    tau_star, rg2_star)
     return nn

@@ -566,6 +566,7 @@ typedef struct bs_group {
     int nlev;              /* L+1 */
     double G, mu;
     const unsigned char *alive; /* collisions (R25): bodies merged away feel only the star; or NULL */
+    double gr_inv_c2;      /* GR splitting (R28): 1/c^2, or 0 when off */
 } bs_group;
 
 static void bs_deriv(const bs_group *g, const double *y, double *f)
@@ -597,12 +598,21 @@ static void bs_deriv(const bs_group *g, const double *y, double *f)
             double c = g->m[ib] * W / (d2 * d);
             px += c * dx; py += c * dy; pz += c * dz;
         }
-        f[6 * a + 0] = xa[3];
-        f[6 * a + 1] = xa[4];
-        f[6 * a + 2] = xa[5];
-        f[6 * a + 3] = ax + g->G * px;
-        f[6 * a + 4] = ay + g->G * py;
-        f[6 * a + 5] = az + g->G * pz;
+        /* GR splitting (R28): the alpha term rescales the member's own Kepler
+         * motion -- its velocity term and the star's acceleration -- by
+         * 1 + 3 (u^2/2 - mu/r) / c^2 at the current state; pair terms are not
+         * rescaled (Sec. 3.1) */
+        double fac = 1.0;
+        if (g->gr_inv_c2 > 0.0) {
+            const double u2 = (xa[3] * xa[3] + xa[4] * xa[4]) + xa[5] * xa[5];
+            fac = 1.0 + 3.0 * (0.5 * u2 - g->mu / r) * g->gr_inv_c2;
+        }
+        f[6 * a + 0] = fac * xa[3];
+        f[6 * a + 1] = fac * xa[4];
+        f[6 * a + 2] = fac * xa[5];
+        f[6 * a + 3] = fac * ax + g->G * px;
+        f[6 * a + 4] = fac * ay + g->G * py;
+        f[6 * a + 5] = fac * az + g->G * pz;
     }
 }
 
@@ -764,6 +774,7 @@ typedef struct step_ctx {
     orc_stats *st;
     int status;
     coll_ctx *cc;                 /* collisions (R25), or NULL */
+    double gr_inv_c2;             /* GR splitting (R28): 1/c^2 in the BS groups, or 0 */
 } step_ctx;
 
 /* Partner lists (CSR) of a pair list that is ascending in (i,j): appending j to
@@ -831,6 +842,7 @@ static void bs_all_groups(step_ctx *cx, int64_t npairs, const uint32_t *pairs, i
         g.rcl = (const double *const *)cx->rcl; g.nlev = level + 1;
         g.G = cx->p->G; g.mu = cx->p->G * cx->p->m_star;
         g.alive = cx->cc ? cx->cc->alive : NULL;
+        g.gr_inv_c2 = cx->gr_inv_c2;
         int fail = bs_integrate(&g, y, dt_l, cx->p->bs_tol, cx->p->bs_max_steps,
                                 &cx->st->bs_steps, &cx->st->bs_rejects, &cx->st->bs_max_attempts,
                                 cx->cc);
@@ -966,7 +978,8 @@ static void senc(step_ctx *cx, int64_t npairs, const uint32_t *pairs, int level,
  *      size, at most implicit_max_iter (10) times.                           */
 typedef struct orc_nn {
     int32_t gr, tides;
-    int32_t implicit_max_iter, pad;
+    int32_t implicit_max_iter;
+    int32_t gr_split;  /* GR by the Hamiltonian splitting of Sec. 3.1 (R28) instead of Eq. apn */
     double c_light;
     double R_star, k2_star, tau_star, rg2_star;
 } orc_nn;
@@ -1097,6 +1110,99 @@ static void nn_implicit(int64_t n, const double *x, double *v, const double *m, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* GR by Hamiltonian splitting (Sec. 3.1, after Saha & Tremaine 1994; reading
+ * R28).  H_PN = sum_i alpha_i H_Kep,i^2 + beta_i / r_i^2 + gamma_i p_i^4 acts on
+ * the canonical momenta p_i = m_i u_i (u: pseudovelocities):
+ *   beta:  u_i += -dt 2 mu_i^2 / (c^2 r_i^4) x_i, mu_i = G (m_star + m_i), with
+ *          the kick ("sun kick"; no changeover factor);
+ *   gamma: x_i += -dt 2 (u_i^2 / c^2) u_i, with HC;
+ *   alpha: the Kepler drift of body i over dt (1 + 2 alpha_i H_Kep,i / m_i) =
+ *          dt (1 + 3 (u_i^2/2 - mu/r_i) / c^2) = dt (1 - 3 mu / (2 a_i c^2)),
+ *          mu = G m_star as in the drift; in a close-encounter group the same
+ *          factor multiplies the member's velocity term and the star's
+ *          acceleration, not the pair terms.
+ * The real velocity is dx/dt = dH/dp without the HC term:
+ *   v = u (1 - (u^2/2 + 3 mu / r) / c^2);
+ * the step converts v -> u before the sun kick, HC and the drift, and back
+ * after them, so the pair kicks and the tides act on real velocities.      */
+static double gr_alpha_factor(const double *x, const double *u, double mu, double inv_c2)
+{
+    double r = sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]);
+    double u2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+    return 1.0 + 3.0 * (0.5 * u2 - mu / r) * inv_c2;
+}
+
+static double gr_real_factor(const double *x, const double *u, double mu, double inv_c2)
+{
+    double r = sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]);
+    double u2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+    return 1.0 - (0.5 * u2 + 3.0 * mu / r) * inv_c2;
+}
+
+/* v -> u: u = v / (1 - (u^2/2 + 3 mu/r)/c^2) by fixed-point iteration from
+ * u = v (the correction is ~v^2/c^2; 4 iterations reach rounding).           */
+static void gr_to_pseudo(int64_t n, const double *x, double *v, double mu, double inv_c2)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double u[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
+        for (int it = 0; it < 4; it++) {
+            double f = gr_real_factor(x + 3 * i, u, mu, inv_c2);
+            for (int k = 0; k < 3; k++) u[k] = v[3 * i + k] / f;
+        }
+        for (int k = 0; k < 3; k++) v[3 * i + k] = u[k];
+    }
+}
+
+static void gr_to_real(int64_t n, const double *x, double *v, double mu, double inv_c2)
+{
+    for (int64_t i = 0; i < n; i++) {
+        double f = gr_real_factor(x + 3 * i, v + 3 * i, mu, inv_c2);
+        for (int k = 0; k < 3; k++) v[3 * i + k] *= f;
+    }
+}
+
+static void gr_beta_kick(int64_t n, const double *x, double *u, const double *m, double G,
+                         double m_star, double inv_c2, double dt)
+{
+    for (int64_t i = 0; i < n; i++) {
+        const double *xi = x + 3 * i;
+        double r2 = (xi[0] * xi[0] + xi[1] * xi[1]) + xi[2] * xi[2];
+        double mui = G * (m_star + m[i]);
+        double s = -dt * 2.0 * mui * mui * inv_c2 / (r2 * r2);
+        for (int k = 0; k < 3; k++) u[3 * i + k] += s * xi[k];
+    }
+}
+
+/* HC(dt) with the gamma term: x_i += dt P/m_star - dt 2 (u_i^2/c^2) u_i (the
+ * HC shift formed as orc_hc forms it). */
+static void gr_hc_gamma(int64_t n, double *x, const double *u, const double *m, double m_star,
+                        double inv_c2, double dt)
+{
+    double P[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n; j++)
+        for (int k = 0; k < 3; k++) P[k] += m[j] * u[3 * j + k];
+    double c[3];
+    for (int k = 0; k < 3; k++) c[k] = dt * P[k] / m_star;
+    for (int64_t i = 0; i < n; i++) {
+        const double *ui = u + 3 * i;
+        double u2 = (ui[0] * ui[0] + ui[1] * ui[1]) + ui[2] * ui[2];
+        double g = dt * 2.0 * u2 * inv_c2;
+        for (int k = 0; k < 3; k++) x[3 * i + k] += c[k] - g * ui[k];
+    }
+}
+
+/* FG with each body's drift time rescaled by the alpha factor. */
+static int64_t gr_fg(int64_t n, double *x, double *u, double mu, double inv_c2, double dt, int max_iter)
+{
+    int64_t fails = 0;
+    for (int64_t i = 0; i < n; i++) {
+        double dti = dt * gr_alpha_factor(x + 3 * i, u + 3 * i, mu, inv_c2);
+        if (kepler_one(x + 3 * i, u + 3 * i, mu, dti, max_iter)) fails++;
+    }
+    return fails;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Direct entry for tests: group the ascending pair list and integrate every
  * group by BS over dt from (x, v) in place, with nlev levels of critical radii
  * rc_levels[l*n + i].  Returns 0, or 2 when a group hit bs_max_steps.        */
@@ -1182,7 +1288,7 @@ int orc_level_force_parts(int64_t n, const double *x, const double *m, const dou
     bs_group g;
     g.nm = n; g.mem = mem; g.poff = off; g.plist = list; g.m = m;
     g.rcl = (const double *const *)cx.rcl; g.nlev = nlev;
-    g.G = G; g.mu = 0.0; g.alive = NULL;
+    g.G = G; g.mu = 0.0; g.alive = NULL; g.gr_inv_c2 = 0.0;
     bs_deriv(&g, y, f);
     for (int64_t i = 0; i < n; i++)
         for (int k = 0; k < 3; k++) acc_bs[3 * i + k] = f[6 * i + 3 + k];
@@ -1243,6 +1349,12 @@ static int step_impl(int64_t n, double *x, double *v, const double *m, const orc
     double *xs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *vs = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double dt = p->dt, mu = p->G * p->m_star;
+    /* R28: GR by Hamiltonian splitting (original scheme, one level) */
+    const int split = nn && nn->gr && nn->gr_split && L == 1;
+    const double inv_c2 = split ? 1.0 / (nn->c_light * nn->c_light) : 0.0;
+    orc_nn nn_tides;
+    if (nn) { nn_tides = *nn; nn_tides.gr = 0; }
+    cx.gr_inv_c2 = inv_c2;
     /* R24: bodies i >= nm are semi-active test particles */
     const int64_t nm = (p->tp_mode == 2 && p->n_massive >= 0 && p->n_massive < n) ? p->n_massive : n;
     for (int64_t s = 0; s < nsteps; s++) {
@@ -1258,11 +1370,24 @@ static int step_impl(int64_t n, double *x, double *v, const double *m, const orc
         }
         st->n_candidates += nc;
         kick_tp(n, nm, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
-        nn_implicit(n, x, v, m, p->G, p->m_star, nn, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
-        orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
-        memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
-        memcpy(vs, v, sizeof(double) * 3 * (size_t)n);
-        st->kepler_fail += orc_fg(n, x, v, mu, dt, p->kepler_max_iter);
+        if (split) {
+            /* R28: tides by the implicit midpoint rule on real velocities,
+             * then sun kick, HC + gamma and the alpha-scaled drift in
+             * pseudovelocities */
+            nn_implicit(n, x, v, m, p->G, p->m_star, &nn_tides, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
+            gr_to_pseudo(n, x, v, mu, inv_c2);
+            gr_beta_kick(n, x, v, m, p->G, p->m_star, inv_c2, 0.5 * dt);
+            gr_hc_gamma(n, x, v, m, p->m_star, inv_c2, 0.5 * dt);
+            memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
+            memcpy(vs, v, sizeof(double) * 3 * (size_t)n);
+            st->kepler_fail += gr_fg(n, x, v, mu, inv_c2, dt, p->kepler_max_iter);
+        } else {
+            nn_implicit(n, x, v, m, p->G, p->m_star, nn, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
+            orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
+            memcpy(xs, x, sizeof(double) * 3 * (size_t)n);
+            memcpy(vs, v, sizeof(double) * 3 * (size_t)n);
+            st->kepler_fail += orc_fg(n, x, v, mu, dt, p->kepler_max_iter);
+        }
         if (nc > 0) {
             uint32_t *enc = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)nc);
             int64_t ne = orc_detect(nc, cand, xs, x, cx.rcl[0], enc);
@@ -1277,9 +1402,17 @@ static int step_impl(int64_t n, double *x, double *v, const double *m, const orc
             free(enc);
         }
         free(cand);
-        orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
-        kick_tp(n, nm, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
-        nn_implicit(n, x, v, m, p->G, p->m_star, nn, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
+        if (split) {
+            gr_hc_gamma(n, x, v, m, p->m_star, inv_c2, 0.5 * dt);
+            gr_beta_kick(n, x, v, m, p->G, p->m_star, inv_c2, 0.5 * dt);
+            gr_to_real(n, x, v, mu, inv_c2);
+            kick_tp(n, nm, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
+            nn_implicit(n, x, v, m, p->G, p->m_star, &nn_tides, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
+        } else {
+            orc_hc(n, x, v, m, p->m_star, 0.5 * dt);
+            kick_tp(n, nm, x, m, cx.rcl[0], p->G, 0.5 * dt, v, p->nthreads);
+            nn_implicit(n, x, v, m, p->G, p->m_star, nn, R, k2, tau, rg2, spin, spin_star, 0.5 * dt);
+        }
     }
     if (st->kepler_fail) cx.status |= 1;
     for (int l = 0; l < L; l++) free(cx.rcl[l]);
@@ -1547,7 +1680,7 @@ static int frozen_step(int64_t n, double *x, double *v, const double *m, const o
             bs_group g;
             g.nm = 1; g.mem = &mem; g.poff = poff; g.plist = &plist; g.m = m;
             const double *rcl[1] = {rc};
-            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu; g.alive = NULL;
+            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu; g.alive = NULL; g.gr_inv_c2 = 0.0;
             tl_group ctx; ctx.g = g; ctx.dm = dm;
             double y[12];
             for (int k = 0; k < 3; k++) {
@@ -1583,7 +1716,7 @@ static int frozen_step(int64_t n, double *x, double *v, const double *m, const o
             bs_group g;
             const double *rcl[1] = {rc};
             g.nm = nm; g.mem = mem; g.poff = poff; g.plist = plist; g.m = m;
-            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu; g.alive = NULL;
+            g.rcl = rcl; g.nlev = 1; g.G = G; g.mu = mu; g.alive = NULL; g.gr_inv_c2 = 0.0;
             int64_t dim = dx ? 12 * nm : 6 * nm;
             double *y = (double *)malloc(sizeof(double) * (size_t)dim);
             for (int64_t a = 0; a < nm; a++)

@@ -39,8 +39,8 @@ struct EnsArgs {
     const double *mass, *radius, *k2, *tau, *rg2;
     const double *m_star, *dt;
     double *star;                       // [S][8]
-    double c2;
-    int gr, tides;
+    double c2, inv_c2;
+    int gr, tides;                      // gr: 1 Eq. apn by the implicit midpoint rule, 2 splitting
     double G, n1, n2, f_pc, bs_tol;
     int kepler_max_iter, bs_max_steps, implicit_max_iter;
     long long nsteps;
@@ -195,7 +195,7 @@ __device__ void nn_body(const EnsArgs &A, const EnsShared &S, int i, const doubl
     const double rdot = ((x[0] * u[0] + x[1] * u[1]) + x[2] * u[2]) / r;
     const double u2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
     for (int k = 0; k < 3; k++) { acc[k] = 0.0; Ni[k] = 0.0; Ns[k] = 0.0; }
-    if (A.gr) {
+    if (A.gr == 1) {
         const double mu = G * (m_star + mi);
         const double eta = m_star * mi / ((m_star + mi) * (m_star + mi));
         const double pre = -mu / (r2 * A.c2);
@@ -229,7 +229,7 @@ __device__ void nn_body(const EnsArgs &A, const EnsShared &S, int i, const doubl
 }
 
 __device__ void ens_nn(const EnsArgs &A, EnsShared &S, double dt) {
-    if (!A.gr && !A.tides) return;
+    if (A.gr != 1 && !A.tides) return;
     const int n = S.n, t = threadIdx.x;
     if (t == 0) {
         double P0 = 0.0, P1 = 0.0, P2 = 0.0, Mp = 0.0;
@@ -316,6 +316,82 @@ __device__ void ens_hc(EnsShared &S, double dt_half) {
     __syncthreads();
 }
 
+// ------------------------------------------------------------ GR by splitting
+// Sec. 3.1 (reading R28): H_PN = sum alpha H_Kep^2 + beta/r^2 + gamma p^4 on the
+// canonical velocities u (pseudovelocities): the sun kick
+// u += -dt 2 mu_i^2/(c^2 r^4) x (mu_i = G (m_star + m_i)), the gamma term
+// x += -dt 2 (u^2/c^2) u with HC, and the drift time of each body scaled by
+// 1 + 3 (u^2/2 - mu/r)/c^2 (mu = G m_star); the real velocity is
+// v = u (1 - (u^2/2 + 3 mu/r)/c^2).  The pair kicks and the tides act on real
+// velocities.
+__device__ __forceinline__ double ens_u2(const double u[3]) { return (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2]; }
+
+__device__ __forceinline__ double ens_real_factor(const double x[3], const double u[3], double mu, double inv_c2) {
+    const double r = sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]);
+    return 1.0 - (0.5 * ens_u2(u) + 3.0 * mu / r) * inv_c2;
+}
+
+__device__ __forceinline__ double ens_alpha_factor(const double x[3], const double u[3], double mu, double inv_c2) {
+    const double r = sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]);
+    return 1.0 + 3.0 * (0.5 * ens_u2(u) - mu / r) * inv_c2;
+}
+
+// v -> u by fixed-point iteration from u = v (4 iterations: the correction is ~v^2/c^2).
+__device__ void ens_gr_to_pseudo(const EnsArgs &A, EnsShared &S) {
+    const int t = threadIdx.x;
+    if (t < S.n) {
+        const double x[3] = {S.x[0][t], S.x[1][t], S.x[2][t]};
+        const double v[3] = {S.v[0][t], S.v[1][t], S.v[2][t]};
+        double u[3] = {v[0], v[1], v[2]};
+        for (int it = 0; it < 4; it++) {
+            const double f = ens_real_factor(x, u, A.G * S.mstar, A.inv_c2);
+            for (int k = 0; k < 3; k++) u[k] = v[k] / f;
+        }
+        for (int k = 0; k < 3; k++) S.v[k][t] = u[k];
+    }
+    __syncthreads();
+}
+
+__device__ void ens_gr_to_real(const EnsArgs &A, EnsShared &S) {
+    const int t = threadIdx.x;
+    if (t < S.n) {
+        const double x[3] = {S.x[0][t], S.x[1][t], S.x[2][t]};
+        const double u[3] = {S.v[0][t], S.v[1][t], S.v[2][t]};
+        const double f = ens_real_factor(x, u, A.G * S.mstar, A.inv_c2);
+        for (int k = 0; k < 3; k++) S.v[k][t] = u[k] * f;
+    }
+    __syncthreads();
+}
+
+__device__ void ens_gr_beta(const EnsArgs &A, EnsShared &S, double dt) {
+    const int t = threadIdx.x;
+    if (t < S.n) {
+        const double x[3] = {S.x[0][t], S.x[1][t], S.x[2][t]};
+        const double r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
+        const double mui = A.G * (S.mstar + S.m[t]);
+        const double s = -dt * 2.0 * mui * mui * A.inv_c2 / (r2 * r2);
+        for (int k = 0; k < 3; k++) S.v[k][t] += s * x[k];
+    }
+    __syncthreads();
+}
+
+// HC(dt) with the gamma term: x += dt P/m_star - dt 2 (u^2/c^2) u.
+__device__ void ens_hc_gamma(const EnsArgs &A, EnsShared &S, double dt) {
+    const int n = S.n, t = threadIdx.x;
+    if (t == 0) {
+        double P0 = 0.0, P1 = 0.0, P2 = 0.0;
+        for (int j = 0; j < n; j++) { P0 += S.m[j] * S.v[0][j]; P1 += S.m[j] * S.v[1][j]; P2 += S.m[j] * S.v[2][j]; }
+        S.shift[0] = dt * P0 / S.mstar; S.shift[1] = dt * P1 / S.mstar; S.shift[2] = dt * P2 / S.mstar;
+    }
+    __syncthreads();
+    if (t < n) {
+        const double u[3] = {S.v[0][t], S.v[1][t], S.v[2][t]};
+        const double g = dt * 2.0 * ens_u2(u) * A.inv_c2;
+        for (int k = 0; k < 3; k++) S.x[k][t] += S.shift[k] - g * u[k];
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------------ BS of one group
 __device__ __forceinline__ double &ebs(double *scr, int row, int slot) { return scr[row * kEnsMaxN + slot]; }
 
@@ -337,12 +413,20 @@ __device__ void ens_bs_deriv(const EnsArgs &A, EnsShared &S, double *scr, int z0
         const double c = S.m[p] * W / (d2 * d);
         px += c * dx; py += c * dy; pz += c * dz;
     }
-    ebs(scr, f0, s) = ebs(scr, z0 + 3, s);
-    ebs(scr, f0 + 1, s) = ebs(scr, z0 + 4, s);
-    ebs(scr, f0 + 2, s) = ebs(scr, z0 + 5, s);
-    ebs(scr, f0 + 3, s) = sst * x + A.G * px;
-    ebs(scr, f0 + 4, s) = sst * y + A.G * py;
-    ebs(scr, f0 + 5, s) = sst * z + A.G * pz;
+    // GR splitting: the member's Kepler motion (velocity term and star
+    // acceleration, not the pair terms) runs at the alpha-scaled rate
+    double fac = 1.0;
+    if (A.gr == 2) {
+        const double xx[3] = {x, y, z};
+        const double uu[3] = {ebs(scr, z0 + 3, s), ebs(scr, z0 + 4, s), ebs(scr, z0 + 5, s)};
+        fac = ens_alpha_factor(xx, uu, A.G * S.mstar, A.inv_c2);
+    }
+    ebs(scr, f0, s) = fac * ebs(scr, z0 + 3, s);
+    ebs(scr, f0 + 1, s) = fac * ebs(scr, z0 + 4, s);
+    ebs(scr, f0 + 2, s) = fac * ebs(scr, z0 + 5, s);
+    ebs(scr, f0 + 3, s) = fac * (sst * x) + A.G * px;
+    ebs(scr, f0 + 4, s) = fac * (sst * y) + A.G * py;
+    ebs(scr, f0 + 5, s) = fac * (sst * z) + A.G * pz;
 }
 
 // Same integrator and step control as the large-system kernels: modified
@@ -477,12 +561,24 @@ __device__ void ens_step(const EnsArgs &A, EnsShared &S, double *scr, unsigned l
     __syncthreads();
     ens_kick<T, MIXED>(A, S, 0.5 * dt, true);
     ens_nn(A, S, 0.5 * dt);
-    ens_hc(S, 0.5 * dt);
-    // FG (saves the pre-drift state)
+    if (A.gr == 2) {
+        ens_gr_to_pseudo(A, S);
+        ens_gr_beta(A, S, 0.5 * dt);
+        ens_hc_gamma(A, S, 0.5 * dt);
+    } else {
+        ens_hc(S, 0.5 * dt);
+    }
+    // FG (saves the pre-drift state); with GR splitting each body drifts for
+    // its alpha-scaled time
     if (t < n) {
         double x = S.x[0][t], y = S.x[1][t], z = S.x[2][t], vx = S.v[0][t], vy = S.v[1][t], vz = S.v[2][t];
         S.x0[0][t] = x; S.x0[1][t] = y; S.x0[2][t] = z; S.v0[0][t] = vx; S.v0[1][t] = vy; S.v0[2][t] = vz;
-        if (!kepler_drift(x, y, z, vx, vy, vz, A.G * S.mstar, dt, A.kepler_max_iter)) {
+        double dti = dt;
+        if (A.gr == 2) {
+            const double xx[3] = {x, y, z}, uu[3] = {vx, vy, vz};
+            dti = dt * ens_alpha_factor(xx, uu, A.G * S.mstar, A.inv_c2);
+        }
+        if (!kepler_drift(x, y, z, vx, vy, vz, A.G * S.mstar, dti, A.kepler_max_iter)) {
             latch_error(A.ctr, kErrKepler);
             atomicAdd(&A.ctr->kepler_fail, 1ull);
         }
@@ -540,7 +636,13 @@ __device__ void ens_step(const EnsArgs &A, EnsShared &S, double *scr, unsigned l
         __syncthreads();
         ens_bs_group(A, S, scr, S.flag, dt, t_start);
     }
-    ens_hc(S, 0.5 * dt);
+    if (A.gr == 2) {
+        ens_hc_gamma(A, S, 0.5 * dt);
+        ens_gr_beta(A, S, 0.5 * dt);
+        ens_gr_to_real(A, S);
+    } else {
+        ens_hc(S, 0.5 * dt);
+    }
     ens_kick<T, MIXED>(A, S, 0.5 * dt, false);
     ens_nn(A, S, 0.5 * dt);
 }
@@ -671,6 +773,7 @@ EnsArgs ens_args(genga_ensemble *e, long long nsteps) {
     A.mass = e->d.mass; A.radius = e->d.radius; A.k2 = e->d.k2; A.tau = e->d.tau; A.rg2 = e->d.rg2;
     A.m_star = e->d.m_star; A.dt = e->d.dt; A.star = e->d.star;
     A.c2 = e->d.c_light * e->d.c_light;
+    A.inv_c2 = 1.0 / A.c2;
     A.gr = e->d.gr; A.tides = e->d.tides;
     A.G = e->p.G; A.n1 = e->p.n1; A.n2 = e->p.n2; A.f_pc = e->p.f_pc; A.bs_tol = e->p.bs_tol;
     A.kepler_max_iter = e->p.kepler_max_iter; A.bs_max_steps = e->p.bs_max_steps;
@@ -740,6 +843,7 @@ int genga_ensemble_create(genga_ensemble_t **out, const genga_params_t *p,
     if (d->n_systems < 1 || !d->offsets || !d->pos || !d->vel || !d->mass || !d->spin || !d->radius ||
         !d->k2 || !d->tau || !d->rg2 || !d->m_star || !d->dt || !d->star)
         return GENGA_EINVAL;
+    if (d->gr < 0 || d->gr > 2 || (d->gr && !(d->c_light > 0))) return GENGA_EINVAL;
     if (p->slevels != 1 || p->kepler_max_iter < 1 || p->bs_max_steps < 1 || !(p->bs_tol > 0) ||
         (p->precision != GENGA_FP64 && p->precision != GENGA_MIXED))
         return GENGA_EINVAL;

@@ -61,6 +61,14 @@ __device__ __forceinline__ float r2_to_float_trunc(double r2) {
     return __uint_as_float(fb);
 }
 
+// 1 / rc: the Newton reciprocal for every rc the FP32 seed can take, an exact
+// division for smaller ones, infinite for rc = 0 (so that min(1/rc_i, 1/rc_j) is
+// 1 / max(rc_i, rc_j) for any pair).
+__device__ __forceinline__ double inv_rc(double rc) {
+    if (rc > 1e-30) return rcp_newton(rc);
+    return rc > 0.0 ? 1.0 / rc : __longlong_as_double(0x7ff0000000000000ll);
+}
+
 // TP: semi-active test particles (Sec. 8.1): a test particle i takes only the
 // sources j < nm; the block that holds the boundary masks the test-particle
 // pairs, the blocks past it shorten their source range.
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(kKickThreads, kick_min_blocks(MIXED))
 kick_kernel(KickArgs A)
 {
     __shared__ double sx[kTile], sy[kTile], sz[kTile], sm[kTile];
-    __shared__ double src[kTile];
+    __shared__ double sirc[kTile];            // 1 / rc_j
     __shared__ float sthr[kTile], smh[kTile], sml[kTile];
 
     const int n = A.n;
@@ -77,11 +85,12 @@ kick_kernel(KickArgs A)
     const bool valid = i < n;
 
     double xi = 1e15, yi = 1e15, zi = 1e15;
-    double rci = 0.0;
+    double irci = 0.0;                        // 1 / rc_i (infinite for rc_i = 0)
     float thri = 0.0f;
     if (valid) {
         xi = A.x[i]; yi = A.y[i]; zi = A.z[i];
-        rci = A.rc[i]; thri = A.thr_rc[i];
+        thri = A.thr_rc[i];
+        irci = inv_rc(A.rc[i]);
     }
 
     const int jbeg = blockIdx.y * A.chunk;
@@ -99,8 +108,8 @@ kick_kernel(KickArgs A)
         for (int k = threadIdx.x; k < cnt; k += kKickThreads) {
             const int j = jt + k;
             sx[k] = A.x[j]; sy[k] = A.y[j]; sz[k] = A.z[j]; sm[k] = A.m[j];
-            src[k] = A.rc[j];
             sthr[k] = A.thr_rc[j];
+            sirc[k] = inv_rc(A.rc[j]);
             if (MIXED) {     // mass as an unevaluated sum of two floats
                 const float mh = __double2float_rn(A.m[j]);
                 smh[k] = mh;
@@ -155,6 +164,9 @@ kick_kernel(KickArgs A)
             }
             // Changeover band (rare): K < 1 needs r < rc_ij.  K is flat (zero slope) at
             // r = rc, so the branch may follow the FP32 bound and K uses the r^2 above.
+            // The branch runs on few lanes of a warp while the FP64 pipe charges the
+            // whole warp, so it keeps to short FP64 forms: r from the Newton rsqrt,
+            // K with 1/rc_ij = min(1/rc_i, 1/rc_j) staged beforehand (no division).
             if (r2f < fmaxf(thri, sthr[k])) {
                 if (j == i) {
                     mk = 0.0; r2 = 1.0; r2f = 1.0f;          // self term: zero, finite
@@ -162,7 +174,7 @@ kick_kernel(KickArgs A)
                     mh = 0.0f; ml = 0.0f;
                 } else {
                     const double r2d = MIXED ? fma(dz, dz, fma(dy, dy, dx * dx)) : r2;
-                    mk = mk * changeover(sqrt(r2d), fmax(rci, src[k]));
+                    mk = mk * changeover_fast(r2d * rsqrt_newton(r2d), fmin(irci, sirc[k]));
                     if (MIXED) {
                         mh = __double2float_rn(mk);
                         ml = __double2float_rn(mk - (double)mh);

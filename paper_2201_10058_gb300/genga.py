@@ -17,6 +17,8 @@ from . import build as _build
 
 GENGA_FP64 = 0
 GENGA_MIXED = 1
+GENGA_GR_IMPLICIT = 1
+GENGA_GR_SPLIT = 2
 
 ERRORS = {0: "OK", -1: "EINVAL", -2: "ECAPACITY", -3: "ENONCONV", -4: "ETIMEOUT",
           -5: "EBADSTATE", -6: "ECUDA", -7: "ENOMEM"}
@@ -479,7 +481,7 @@ class Ensemble:
     device and kept here: pos/vel/spin as (3, n_total), star as (S, 8)."""
 
     def __init__(self, wl, params: Params | None = None, gr: bool = True, tides: bool = True,
-                 stream=None):
+                 stream=None, gr_split: bool = False):
         import torch
         self._lib = load()
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -496,7 +498,8 @@ class Ensemble:
         for name in ("pos", "vel", "mass", "spin", "radius", "k2", "tau", "rg2", "m_star", "dt",
                      "star"):
             setattr(d, name, getattr(self, name).data_ptr())
-        d.c_light, d.gr, d.tides = wl.c_light, int(gr), int(tides)
+        d.c_light, d.tides = wl.c_light, int(tides)
+        d.gr = (GENGA_GR_SPLIT if gr_split else GENGA_GR_IMPLICIT) if gr else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = _VP()
         rc = self._lib.genga_init_ensemble(C.byref(h), C.byref(p), C.byref(d),

@@ -9,12 +9,12 @@ from workloads.ensemble import Ensemble, ensemble
 pytestmark = pytest.mark.gpu
 
 
-def _oracle_run(wl, s, nsteps, gr=True, tides=True):
+def _oracle_run(wl, s, nsteps, gr=True, tides=True, gr_split=False):
     d = wl.system(s)
     p = O.make_params(G=wl.G, m_star=d["m_star"], dt=d["dt"])
     st = d["star"]
     nn = O.make_nn(gr=gr, tides=tides, c_light=wl.c_light, R_star=st[0], k2_star=st[1],
-                   tau_star=st[2], rg2_star=st[3])
+                   tau_star=st[2], rg2_star=st[3], gr_split=gr_split)
     x, v, w, ws, status, stats = O.step_nn(d["x"], d["v"], d["m"], p, nn, d["R"], d["k2"], d["tau"],
                                            d["rg2"], d["spin"], st[4:7], nsteps)
     assert status == 0
@@ -166,3 +166,33 @@ def test_ensemble_mixed_close_encounter(cuda_lib):
     assert sm["n_pairs"][0] > 0 and sm["n_pairs"][0] == sf["n_pairs"][0]
     assert sm["n_candidates"] == sf["n_candidates"]
     _check(g, mixed, wl, range(wl.n_systems), 30, tol=1e-9)
+
+
+@pytest.mark.parametrize("tides", [True, False])
+def test_ensemble_gr_split_matches_oracle(cuda_lib, small, tides):
+    """GR by the Hamiltonian splitting of Sec. 3.1 (pseudovelocities between the
+    conversions, alpha-scaled drift, sun kick, gamma term with HC), with and
+    without tides: 200 steps of 48 systems against the oracle."""
+    g = cuda_lib
+    ens = g.Ensemble(small, g.default_params(G=small.G), tides=tides, gr_split=True)
+    ens.step(200)
+    st = ens.stats()
+    assert st["kepler_fail"] == 0 and st["bs_fail"] == 0
+    _check(g, ens, small, range(small.n_systems), 200, tides=tides, gr_split=True)
+
+
+def test_ensemble_gr_split_close_encounter(cuda_lib):
+    """Splitting with encounters: the Bulirsch-Stoer groups run with the alpha
+    factor on each member's Kepler terms; against the oracle."""
+    g = cuda_lib
+    wl = ensemble(6, seed=99, nmin=8, nmax=12)
+    for s in range(wl.n_systems):
+        a = wl.offsets[s]
+        x1 = wl.x[a] * 1.04
+        wl.x[a + 1] = x1
+        vc = np.sqrt(wl.G * (wl.m_star[s] + wl.m[a + 1]) / np.linalg.norm(x1))
+        wl.v[a + 1] = vc * np.cross([0.0, 0.0, 1.0], x1 / np.linalg.norm(x1))
+    ens = g.Ensemble(wl, g.default_params(G=wl.G), gr_split=True)
+    ens.step(30)
+    assert ens.stats()["n_groups"] > 0
+    _check(g, ens, wl, range(wl.n_systems), 30, tol=1e-11, gr_split=True)

@@ -123,3 +123,87 @@ def test_nn_off_reduces_to_plain_step():
     x2, v2, *_ = O.step(x, v, mm, p, 50)
     np.testing.assert_array_equal(x1, x2)
     np.testing.assert_array_equal(v1, v2)
+
+
+# ---------------------------------------------------------------- GR splitting (Sec. 3.1)
+def _h1pn(x, v, mu):
+    """The standard first post-Newtonian two-body Hamiltonian per unit mass of a
+    test particle, H = u^2/2 - mu/r - u^4/(8c^2) - 3 mu u^2/(2 c^2 r) + mu^2/(2 c^2 r^2),
+    with the canonical velocity u taken from the real one through that
+    Hamiltonian's own dx/dt = dH/du = u (1 - u^2/(2c^2) - 3 mu/(c^2 r))."""
+    c2 = C_LIGHT ** 2
+    r = np.linalg.norm(x)
+    u = v.copy()
+    for _ in range(4):
+        u2 = u @ u
+        u = v / (1 - u2 / (2 * c2) - 3 * mu / (c2 * r))
+    u2 = u @ u
+    return u2 / 2 - mu / r - u2 * u2 / (8 * c2) - 3 * mu * u2 / (2 * c2 * r) + mu * mu / (2 * c2 * r * r)
+
+
+def test_gr_split_perihelion_advance_matches_closed_form():
+    """The Hamiltonian splitting of Sec. 3.1 gives the same perihelion advance per
+    orbit as the closed form 6 pi G M / (c^2 a (1 - e^2))."""
+    a, e, m = 0.05, 0.2, 1e-9
+    x, v, mm = _one_planet(a, e, m)
+    mu = G * (1 + m)
+    P = 2 * np.pi * np.sqrt(a ** 3 / mu)
+    norb, per = 50, 400
+    p = O.make_params(G=G, m_star=1.0, dt=P / per, n1=0.0, n2=0.0)
+    nn = O.make_nn(gr=True, tides=False, gr_split=True)
+    z = np.zeros(1)
+    x1, v1, *_ = O.step_nn(x, v, mm, p, nn, z, z, z, z, np.zeros((1, 3)), np.zeros(3), norb * per)
+    _, _, w0 = _elements(x[0], v[0] + m * v[0], mu)
+    _, _, w1 = _elements(x1[0], v1[0] + m * v1[0], mu)
+    measured = (w1 - w0) / norb
+    expected = 6 * np.pi * mu / (C_LIGHT ** 2 * a * (1 - e * e))
+    assert abs(measured / expected - 1) < 0.01, (measured, expected)
+
+
+def test_gr_split_conserves_the_first_post_newtonian_energy():
+    """The split step is a symplectic map of the 1PN Hamiltonian: that energy
+    stays within the small splitting oscillation over 20 orbits, while the
+    Newtonian energy of the same orbit swings by far more (the PN terms exchange
+    energy with it along the orbit).  A wrong sign or factor in any of the
+    alpha, beta, gamma terms integrates another Hamiltonian and fails this."""
+    a, e, m = 0.05, 0.4, 1e-12
+    x, v, mm = _one_planet(a, e, m)
+    mu = G * (1 + m)
+    P = 2 * np.pi * np.sqrt(a ** 3 / mu)
+    per = 800
+    p = O.make_params(G=G, m_star=1.0, dt=P / per, n1=0.0, n2=0.0)
+    nn = O.make_nn(gr=True, tides=False, gr_split=True)
+    z = np.zeros(1)
+    H0 = _h1pn(x[0], v[0], mu)
+    EN0 = 0.5 * v[0] @ v[0] - mu / np.linalg.norm(x[0])
+    dH, dEN = [], []
+    xs, vs = x, v
+    for _ in range(40):                      # 20 orbits in half-orbit chunks
+        xs, vs, *_ = O.step_nn(xs, vs, mm, p, nn, z, z, z, z, np.zeros((1, 3)), np.zeros(3), per // 2)
+        dH.append(abs(_h1pn(xs[0], vs[0], mu) - H0) / abs(H0))
+        dEN.append(abs(0.5 * vs[0] @ vs[0] - mu / np.linalg.norm(xs[0]) - EN0) / abs(EN0))
+    assert max(dH) < 2e-10, max(dH)
+    assert max(dEN) > 50 * max(dH), (max(dEN), max(dH))
+
+
+def test_gr_split_real_and_pseudo_velocities():
+    """With c so large that 1/c^2 vanishes, the split step is the plain step bit
+    for bit (every GR term, the velocity conversions and the drift-time factor
+    reduce to the identity); the implicit and split forms of GR agree on a
+    several-planet system to the size of the 1PN terms times the step's error."""
+    from workloads.ensemble import ensemble
+    wl = ensemble(3, seed=5)
+    d = wl.system(0)
+    p = O.make_params(G=wl.G, m_star=d["m_star"], dt=d["dt"])
+    z = np.zeros(len(d["m"]))
+    args = (d["R"], d["k2"], d["tau"], d["rg2"], np.zeros((len(d["m"]), 3)), np.zeros(3))
+    plain = O.step_nn(d["x"], d["v"], d["m"], p, O.make_nn(gr=False, tides=False), *args, 50)
+    huge = O.step_nn(d["x"], d["v"], d["m"], p, O.make_nn(gr=True, tides=False, gr_split=True,
+                                                          c_light=1e300), *args, 50)
+    np.testing.assert_array_equal(huge[0], plain[0])
+    np.testing.assert_array_equal(huge[1], plain[1])
+    imp = O.step_nn(d["x"], d["v"], d["m"], p, O.make_nn(gr=True, tides=False), *args, 50)
+    spl = O.step_nn(d["x"], d["v"], d["m"], p, O.make_nn(gr=True, tides=False, gr_split=True), *args, 50)
+    gr_shift = np.abs(imp[0] - plain[0]).max()
+    assert gr_shift > 0
+    assert np.abs(spl[0] - imp[0]).max() < 0.05 * gr_shift
