@@ -35,18 +35,25 @@ sys.path.insert(0, ROOT)
 METRIC = ("changeover-kick G pair-interactions/s and steps/s at N=65536 (FP64 vs mixed), "
           "% of peak")
 UNIT = "Gpair/s"
-# FP64 instructions per pair interaction that each kick form's algorithm needs
-# (FMA counted as one).  Mixed: displacement 3, accumulation 3 (r^2 in
-# float-float from an exact split of the displacement, the FP32 rsqrt seed and
-# its Newton correction and the correction terms all on the FP32 pipe; m y0^3
-# converted to FP64 by integer operations).  FP64: CUDA's double rsqrt on an
-# FP64 r^2, m r^-3 and the accumulation.
-FP64_OPS_PER_PAIR = {"mixed": 6, "fp64": 17}
+# FP64 instructions per pair interaction (ordered pair i <- j) that each kick
+# form's algorithm needs (FMA counted as one), by layout.  Tiled (every ordered
+# pair): mixed 6 -- displacement 3, accumulation 3 (r^2 in float-float from an
+# exact split of the displacement, the FP32 rsqrt seed and its Newton
+# correction and the correction terms all on the FP32 pipe; m y0^3 converted to
+# FP64 by integer operations); FP64 17 -- CUDA's double rsqrt on an FP64 r^2,
+# m r^-3 and the accumulation.  Symmetric (each unordered pair once, the force
+# to both bodies): mixed 9 per unordered pair = 4.5 per interaction
+# (displacement 3, accumulation 3 + 3); FP64 21 = 10.5 (displacement 3, r^2 3,
+# Newton rsqrt 5, r^-3 2, two mass products 2, accumulation 3 + 3).
+FP64_OPS_PER_PAIR = {("mixed", "tiled"): 6, ("fp64", "tiled"): 17,
+                     ("mixed", "symmetric"): 4.5, ("fp64", "symmetric"): 10.5}
 # The same counted by ncu on one launch at N = 65,536 (thread-level
 # smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum / N^2, and the
 # warp-level sm__inst_executed_pipe_fp64.sum x 32 / N^2, which also charges the
-# idle lanes of partly predicated warps)
-FP64_INSTR_PER_PAIR_COUNTED = {"mixed": (6.124, 6.510), "fp64": (17.091, 17.402)}
+# idle lanes of partly predicated warps); None where the kernel has changed
+# since the count
+FP64_INSTR_PER_PAIR_COUNTED = {("mixed", "tiled"): (6.152, 6.383), ("fp64", "tiled"): (17.091, 17.402),
+                               ("mixed", "symmetric"): (4.555, 4.675), ("fp64", "symmetric"): None}
 # FP64 units per SM: GB300's nominal FP64 rate (1.25 TFLOP/s = 0.625 T FMA/s
 # over 152 SMs at ~2.06 GHz) is 2 FP64 operations per clock per SM; ncu's FP64
 # pipe utilisation is relative to this rate
@@ -78,6 +85,9 @@ def parse():
                          "5 M_earth), --kick-reps timed launches in the form --kick")
     ap.add_argument("--kick", choices=["fp64", "mixed"], default="mixed",
                     help="kick form of --workload kick")
+    ap.add_argument("--kick-layout", choices=["auto", "tiled", "symmetric"], default="auto",
+                    help="kick layout of --workload kick (auto: the library's choice for N)")
+    ap.add_argument("--kick-p", type=int, default=0, help="symmetric layout super-range (0: chosen)")
     ap.add_argument("--ens-tile", default="",
                     help="threads,ctas_per_sm of the ensemble kernel instead of autotuning "
                          "(profiling runs)")
@@ -275,6 +285,8 @@ def run_ours(args, dist: Dist) -> dict | None:
         k1.record(stream)
         k1.synchronize()
         kick_ms = k0.elapsed_time(k1) / args.kick_reps
+        lay = sysm.kick_layout()
+        layout = "symmetric" if lay["layout"] == genga.GENGA_KICK_SYMMETRIC else "tiled"
         if sampler:
             clocks = sampler.stop()
         t_max = dist.max(total_ms)
@@ -300,6 +312,7 @@ def run_ours(args, dist: Dist) -> dict | None:
             "gpairs_per_s": replica_throughput(dist.world, pairs_per_step, args.steps, t_max) / 1e9,
             "steps_per_s": replica_throughput(dist.world, 1.0, args.steps, t_max),
             "kick_ms": kick_ms,
+            "kick_layout": dict(lay, name=layout),
             "kick_gpairs_per_s": n * (n - 1) / (kick_ms * 1e-3) / 1e9,
             "kick_share": 2 * kick_ms / (total_ms / args.steps),
             "energy_rel_err": abs(E_end - E_start) / abs(E_start),
@@ -374,8 +387,11 @@ def run_ours(args, dist: Dist) -> dict | None:
     nsm = props.multi_processor_count
     peak = FP64_OPS_PER_CLK_PER_SM * nsm * sm_clock * 1e6 / 1e9
     probe_peak = rates["dfma"] * nsm * sm_clock * 1e6 / 1e9
-    achieved = FP64_OPS_PER_PAIR["mixed"] * head["kick_gpairs_per_s"]
-    thr_cnt, warp_cnt = FP64_INSTR_PER_PAIR_COUNTED["mixed"]
+    lay = head["kick_layout"]["name"]
+    ops = FP64_OPS_PER_PAIR[("mixed", lay)]
+    achieved = ops * head["kick_gpairs_per_s"]
+    counted = FP64_INSTR_PER_PAIR_COUNTED[("mixed", lay)]
+    kname = "kick_sym_kernel<mixed>" if lay == "symmetric" else "kick_kernel<mixed>"
     line = {
         "metric": METRIC, "value": round(head["gpairs_per_s"], 4), "unit": UNIT,
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
@@ -395,20 +411,24 @@ def run_ours(args, dist: Dist) -> dict | None:
         "kick_only": {"mixed_gpairs_per_s": round(head["kick_gpairs_per_s"], 3),
                       "mixed_kick_ms": round(head["kick_ms"], 3),
                       "kick_share_of_step": round(head["kick_share"], 3)},
-        "roofline": {"bound": "alu", "kernel": "kick_kernel<mixed> (all-pairs changeover kick)",
+        "roofline": {"bound": "alu", "kernel": f"{kname} (all-pairs changeover kick, {lay} layout)",
                      "achieved": round(achieved, 2), "peak": round(peak, 2),
                      "unit": "G FP64-op/s (FMA = 1; FP64 pipe)",
                      "frac": round(achieved / peak, 4),
                      "traffic": KICK_MIXED_DRAM_BYTES,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
                                        "of this kernel at N=65540",
-                     "ops_per_pair": FP64_OPS_PER_PAIR["mixed"],
+                     "ops_per_pair": ops,
+                     "kick_layout": head["kick_layout"],
+                     "duration_basis": "CUDA events around genga_kick (pack, kick, finalize) on the "
+                                       "system's stream, averaged over the repetitions",
                      "peak_basis": f"derived: {FP64_OPS_PER_CLK_PER_SM} FP64 op/clk/SM (GB300 nominal "
                                    f"FP64 unit count) x {nsm} SMs x {sm_clock:.0f} MHz (median SM "
                                    f"clock under load)",
-                     "frac_counted": {"thread_level": round(thr_cnt * head["kick_gpairs_per_s"] / peak, 4),
-                                      "warp_level": round(warp_cnt * head["kick_gpairs_per_s"] / peak, 4),
-                                      "instr_per_pair": [thr_cnt, warp_cnt]},
+                     "frac_counted": None if counted is None else
+                     {"thread_level": round(counted[0] * head["kick_gpairs_per_s"] / peak, 4),
+                      "warp_level": round(counted[1] * head["kick_gpairs_per_s"] / peak, 4),
+                      "instr_per_pair": list(counted)},
                      "probe": {"peak": round(probe_peak, 2),
                                "frac": round(achieved / probe_peak, 4),
                                "basis": f"{rates['dfma']:.3f} FP64 FMA/clk/SM reached by independent "
@@ -429,8 +449,10 @@ def run_ours(args, dist: Dist) -> dict | None:
                         "non_kick_ms_per_step": f["phases"]["non_kick_ms_per_step"],
                         "kick_gpairs_per_s": round(f["kick_gpairs_per_s"], 3),
                         "kick_ms": round(f["kick_ms"], 3),
-                        "roofline_frac": round(FP64_OPS_PER_PAIR["fp64"] * f["kick_gpairs_per_s"] / peak, 4),
-                        "ops_per_pair": FP64_OPS_PER_PAIR["fp64"],
+                        "roofline_frac": round(FP64_OPS_PER_PAIR[("fp64", f["kick_layout"]["name"])]
+                                               * f["kick_gpairs_per_s"] / peak, 4),
+                        "ops_per_pair": FP64_OPS_PER_PAIR[("fp64", f["kick_layout"]["name"])],
+                        "kick_layout": f["kick_layout"],
                         "energy_rel_err": f["energy_rel_err"]}
         line["mixed_over_fp64"] = round(head["gpairs_per_s"] / f["gpairs_per_s"], 3)
     if not args.no_cpu_baseline and not args.quick and dist.world == 1:
@@ -858,6 +880,9 @@ def run_kick(args) -> dict:
     p = genga.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc,
                              precision=prec)
     sysm = genga.System(pos, vel, mass, p, stream=stream)
+    sysm.set_kick_layout({"auto": genga.GENGA_KICK_AUTO, "tiled": genga.GENGA_KICK_TILED,
+                          "symmetric": genga.GENGA_KICK_SYMMETRIC}[args.kick_layout], args.kick_p)
+    lay = sysm.kick_layout()
     sysm.rcrit(wl.dt)
     sysm.kick(0.0, precheck=False)
     torch.cuda.synchronize()
@@ -872,7 +897,7 @@ def run_kick(args) -> dict:
     sysm.close()
     n = wl.n
     return {"metric": "all-pairs changeover kick alone (secondary measurement)", "kick": args.kick,
-            "n_bodies": n, "launches": args.kick_reps, "ms_per_launch": round(ms, 4),
+            "n_bodies": n, "launches": args.kick_reps, "ms_per_launch": round(ms, 4), "layout": lay,
             "gpairs_per_s": round(n * (n - 1) / (ms * 1e-3) / 1e9, 3)}
 
 

@@ -44,7 +44,9 @@ extern "C" {
 #define GENGA_ENOMEM     -7  /* device allocation failed */
 
 /* ---- kick arithmetic --------------------------------------------------- */
-#define GENGA_FP64   0   /* every pair term in FP64 (CUDA double rsqrt) */
+#define GENGA_FP64   0   /* every pair term in FP64 (double rsqrt: CUDA's in the tiled
+                            kick layout, an FP32 seed with an FP64 Newton step and
+                            series of full double precision in the symmetric one) */
 #define GENGA_MIXED  1   /* FP64 displacement and accumulation, FP32 rsqrt seed +
                             one FP64 Newton correction, compensated per-tile sums */
 
@@ -140,6 +142,28 @@ int genga_set_rcrit(genga_system_t *sys, const double *rc_host);
  * If acc_out (device, 3n doubles, SoA) is not NULL the accelerations
  * G sum_j ... are written there and, when dt_half == 0, v is left unchanged. */
 int genga_kick(genga_system_t *sys, double dt_half, int precheck, double *acc_out);
+
+/* ---- kick layout ---------------------------------------------------------- */
+#define GENGA_KICK_AUTO       0  /* the symmetric layout where it is predicted faster */
+#define GENGA_KICK_TILED      1  /* every ordered pair (i, j): grid of i-tiles x j-chunks */
+#define GENGA_KICK_SYMMETRIC  2  /* every unordered pair once, its force to both bodies */
+
+/* Selects how the all-pairs kick (genga_kick and the kicks of genga_step)
+ * traverses the pairs.  The symmetric layout applies Newton's third law: it
+ * evaluates each unordered pair once, in super-tile pairs of P x P tiles of
+ * 128 bodies taken by persistent blocks, and writes one compensated partial
+ * sum per body and super-range, folded in a fixed order (deterministic).
+ * P = 0 lets the library choose P in 1..6 for N (by a schedule of the work
+ * items over the resident blocks); 1..6 fixes it.  Runs with test particles
+ * (tp_mode 2, n_massive < n) use the tiled layout.  The layouts give the same
+ * sums up to the rounding of a different summation order.  Errors: EINVAL. */
+int genga_set_kick_layout(genga_system_t *sys, int32_t layout, int32_t P);
+
+/* The layout of the next kick: *layout (GENGA_KICK_TILED or
+ * GENGA_KICK_SYMMETRIC), *P (0 for tiled), *slots partial sums per body and
+ * *blocks blocks launched.  Any pointer may be NULL.  May allocate.         */
+int genga_get_kick_layout(genga_system_t *sys, int32_t *layout, int32_t *P, int32_t *slots,
+                          int32_t *blocks);
 
 /* Eq. Hc (Appendix A "HC(dt/2)"): x_i += dt_half * (sum_j m_j v_j) / m_star,
  * the momentum summed in a fixed order.                                     */

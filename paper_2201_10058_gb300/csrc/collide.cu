@@ -202,13 +202,9 @@ int genga_remove_merged(genga_system_t *s, int64_t *n_new_out, int64_t *old_inde
     s->n = n_new;
     if (s->p.tp_mode == 2) s->p.n_massive = nm_keep;
     CCU(cudaMemsetAsync(s->alive, 1, (size_t)n_new, s->stream));
-    const int nchunk = kick_nchunk_for(n_new, s->num_sms);
-    if ((size_t)nchunk * 6 * (size_t)n_new > (size_t)kick_nchunk_for(n_old, s->num_sms) * 6 * (size_t)n_old) {
-        cudaFree(s->kick_part);
-        s->kick_part = nullptr;
-        CCU(cudaMalloc((void **)&s->kick_part, sizeof(double) * (size_t)nchunk * 6 * (size_t)n_new));
-    }
-    s->kick_chunk = 0;                    // kick geometry recomputed for the new count
+    s->kick_chunk = 0;                    // kick geometry and buffers redone for the new count
+    s->ksym_n = -1;
+    CCU(kick_reserve(s));
     for (int l = 0; l < kMaxLevels; l++) s->npairs_host[l] = 0;
     s->label_level = -1;
     adjoint_free(s);                      // a recording refers to the old indices

@@ -119,9 +119,25 @@ struct genga_system {
     double *pre_vel[genga::kMaxLevels] = {};
 
     // all-pairs kick
-    double *kick_part = nullptr;   // [nchunk][6][n]
+    double *kick_part = nullptr;   // [max(nchunk, ksym_nS)][6][n]
+    size_t kick_part_cap = 0;      // doubles allocated
     int kick_nchunk = 0;
     int kick_chunk = 0;
+    // symmetric kick (each unordered pair once): geometry for (ksym_n, ksym_prec)
+    int64_t ksym_n = -1;
+    int ksym_prec = -1;
+    int ksym_layout = 0;           // GENGA_KICK_AUTO / _TILED / _SYMMETRIC requested
+    int ksym_req_P = 0;            // requested P (0: chosen)
+    int ksym_P = 0;                // super-range in tiles; 0: not used at this N
+    int ksym_nS = 0;               // partial slots per body
+    int ksym_blocks = 0;           // persistent blocks
+    int ksym_items = 0;
+    int2 *ksym_list = nullptr;     // dispatch order of the super-tile pairs
+    size_t ksym_list_cap = 0;
+    unsigned *ksym_ctr = nullptr;  // dispatch counter
+    double *ksym_irc = nullptr;    // 1 / rc per body
+    float2 *ksym_mhl = nullptr;    // mass as two floats
+    size_t ksym_body_cap = 0;
 
     // candidates and encounter lists
     uint2 *cand = nullptr;
@@ -239,6 +255,7 @@ cudaError_t launch_energy(genga_system *s, double *E_host, double *L_host);
 
 // kick.cu
 cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *acc_out);
+cudaError_t kick_reserve(genga_system *s);
 cudaError_t launch_precheck_only(genga_system *s);
 int kick_nchunk_for(int n, int num_sms);
 

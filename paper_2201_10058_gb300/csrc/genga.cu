@@ -168,10 +168,7 @@ int alloc_all(genga_system *s) {
     }
     CU(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
     s->kick_chunk = 0;
-    {
-        const int nchunk = kick_nchunk_for((int)n, s->num_sms);
-        CU(dalloc(&s->kick_part, (size_t)nchunk * 6 * n));
-    }
+    CU(kick_reserve(s));
     s->cand_cap = s->p.cand_capacity > 0 ? s->p.cand_capacity : std::max<int64_t>(1 << 20, 64 * (int64_t)n);
     CU(dalloc(&s->cand, (size_t)s->cand_cap));
     CU(dalloc(&s->flags, n + 1));
@@ -202,7 +199,9 @@ void free_all(genga_system *s) {
         dfree(s->csr[l].lpair); dfree(s->csr[l].term);
         dfree(s->bodies[l]);
     }
-    dfree(s->kick_part); dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
+    dfree(s->kick_part); dfree(s->ksym_list); dfree(s->ksym_ctr); dfree(s->ksym_irc); dfree(s->ksym_mhl);
+    s->kick_part_cap = 0; s->ksym_list_cap = 0; s->ksym_body_cap = 0; s->ksym_n = -1;
+    dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
     dfree(s->gsize); dfree(s->goff); dfree(s->gfill); dfree(s->glist); dfree(s->member);
     dfree(s->slotof); dfree(s->bucket_list); bsm_release(s); dfree(s->red); dfree(s->scr.scan_blocks);
     dfree(s->alive); dfree(s->mlog);
@@ -252,10 +251,6 @@ int early_errors(genga_system *s) {
 
 // ---------------------------------------------------------------- step pieces
 int kick(genga_system *s, double dt_half, bool precheck, double *acc_out) {
-    if (!s->kick_part) {
-        const int nchunk = kick_nchunk_for((int)s->n, s->num_sms);
-        CU(dalloc(&s->kick_part, (size_t)nchunk * 6 * (size_t)s->n));
-    }
     CU(launch_kick(s, dt_half, precheck, acc_out));
     return GENGA_OK;
 }

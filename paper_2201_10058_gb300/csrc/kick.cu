@@ -25,6 +25,11 @@
 //     to the FP64 sums once per tile; per-tile sums folded with TwoSum:
 //     6 FP64 instructions per pair (3 subtractions, 3 accumulations).
 //     FP64: CUDA's double rsqrt, 17 FP64 instructions per pair (counted).
+#include <algorithm>
+#include <queue>
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 
 namespace genga {
@@ -354,6 +359,319 @@ precheck_kernel(KickArgs A, double f_pc)
     precheck_flush(A, buf, pend, lane);
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric kick: each unordered pair {i, j} is evaluated once and its force
+// goes to both bodies with opposite signs (Newton's third law): the terms
+// m_j K r^-3 (x_j - x_i) of a_i and -m_i K r^-3 (x_j - x_i) of a_j share the
+// displacement, r^-3 and K.  FP64 instructions per unordered pair: MIXED 9
+// (3 subtractions, 3 + 3 accumulations), FP64 form 21 (the Newton rsqrt of
+// common.cuh instead of CUDA's double rsqrt) -- per ordered pair 4.5 and 10.5
+// against 6 and ~17 of kick_kernel.
+//
+// Work decomposition.  Bodies in tiles of 128 (one per thread of a 4-warp
+// block), tiles in super-ranges of P tiles.  A work item is a super-tile pair
+// (X, Y), X <= Y: the rows a of X (the i-tile, one body per thread, sums in
+// registers) against the tiles b of Y (b >= a when X == Y).  In a tile pair,
+// warp w holds i-subtile w (32 bodies, one per lane) and meets the j-subtiles
+// q = (w + s) mod 4 in four phases s.  In a phase, lane L at step t pairs its
+// i with body (L + t) mod 32 of subtile q, whose running sums ride along the
+// lanes (one shuffle per step: every j is handled by one lane at a time); at
+// the end of the phase the lanes add them to the item's j sums in shared
+// memory -- one warp per subtile per phase, so without conflicts and in a fixed
+// order.  A diagonal subtile (q = w, a = b) takes the steps 1..16, step 16 on
+// lanes 0..15 only: every pair inside it once, no self pair.
+//
+// Partial sums.  Every body gets one compensated partial per super-range
+// (nS = ceil(nT / P)): item (X, Y) writes its row sums to slot Y of the X
+// bodies and its j sums to slot X of the Y bodies; a diagonal item (X, X)
+// writes both, added, to slot X as each row completes.  Every (slot, body) is
+// written exactly once, and kick_finalize folds the slots in slot order, so
+// the result is deterministic.
+//
+// Dispatch.  One persistent block per resident block slot takes items from a
+// counter in the host's order (largest first, the diagonal items last); the
+// host picks P for each N by list-scheduling the items over the resident
+// blocks, with the finalize's cost counted.
+constexpr int kSymT = 128;
+constexpr int kSymMaxP = 6;
+
+struct SymArgs {
+    const double *x, *y, *z, *m;
+    const double *irc;          // 1 / rc per body (inv_rc)
+    const float *thr;           // FP32 upper bound of rc^2
+    const float2 *mhl;          // MIXED: mass as an unevaluated sum of two floats
+    int n, nT, P, nItems;
+    const int2 *items;          // (X, Y) super-tile pairs, X <= Y, in dispatch order
+    unsigned *ctr;              // dispatch counter, zero at launch
+    double *part;               // [nS][6][n]
+};
+
+// Resident blocks per SM the register allocation must allow (128 threads each).
+constexpr int sym_min_blocks(bool mixed) {
+    return mixed ? 4 : 4;
+}
+
+// Dynamic shared memory: the staged j tile (x, y, z, m, 1/rc; thr, mh, ml),
+// then the item's j sums (x, y, z; MIXED: float-float corrections).
+constexpr size_t sym_smem(bool mixed, int P) {
+    return (size_t)kSymT * (5 * sizeof(double) + 3 * sizeof(float)) +
+           (size_t)P * kSymT * (3 * sizeof(double) + (mixed ? 6 * sizeof(float) : 0));
+}
+
+// Far-away stand-in position of the k-th padding body of the last tile:
+// distinct for distinct k (no zero separation), massless.
+__device__ __forceinline__ double pad_pos(int k) { return 1.0e15 + 1.0e13 * (double)k; }
+
+__global__ void kick_pack_kernel(const double *m, const double *rc, int n, double *irc, float2 *mhl) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    irc[i] = inv_rc(rc[i]);
+    const float mh = __double2float_rn(m[i]);
+    mhl[i] = make_float2(mh, __double2float_rn(m[i] - (double)mh));
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kSymT, sym_min_blocks(MIXED))
+kick_sym_kernel(SymArgs A)
+{
+    extern __shared__ __align__(16) unsigned char sym_sh[];
+    double *sx = reinterpret_cast<double *>(sym_sh);
+    double *sy = sx + kSymT, *sz = sy + kSymT, *sm = sz + kSymT, *sirc = sm + kSymT;
+    float *sthr = reinterpret_cast<float *>(sirc + kSymT);
+    float *smh = sthr + kSymT, *sml = smh + kSymT;
+    const int PT = A.P * kSymT;
+    double *jax = reinterpret_cast<double *>(sml + kSymT);
+    double *jay = jax + PT, *jaz = jay + PT;
+    float *jc = reinterpret_cast<float *>(jaz + PT);      // [6][PT]: x hi, x lo, y hi, y lo, z hi, z lo
+    __shared__ int s_item;
+
+    const int n = A.n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        __syncthreads();                      // the previous item's shared sums are written out
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(A.ctr, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= A.nItems) break;
+        const int2 XY = A.items[it];
+        const int a0 = XY.x * A.P, a1 = min(A.nT, a0 + A.P);
+        const int b0 = XY.y * A.P, b1 = min(A.nT, b0 + A.P);
+        const bool diag = XY.x == XY.y;
+        const int nj = (b1 - b0) * kSymT;
+        for (int e = threadIdx.x; e < nj; e += kSymT) {
+            jax[e] = 0.0; jay[e] = 0.0; jaz[e] = 0.0;
+            if (MIXED)
+#pragma unroll
+                for (int c = 0; c < 6; c++) jc[c * PT + e] = 0.0f;
+        }
+        for (int a = a0; a < a1; a++) {
+            const int i = a * kSymT + threadIdx.x;
+            const bool valid = i < n;
+            double xi, yi, zi, mi = 0.0, irci = 0.0;
+            float thri = 0.0f, mhi = 0.0f, mli = 0.0f;
+            if (valid) {
+                xi = A.x[i]; yi = A.y[i]; zi = A.z[i]; mi = A.m[i];
+                irci = A.irc[i]; thri = A.thr[i];
+                if (MIXED) { const float2 q = A.mhl[i]; mhi = q.x; mli = q.y; }
+            } else {
+                xi = yi = zi = pad_pos(threadIdx.x);
+            }
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            float cxh = 0.0f, cxl = 0.0f, cyh = 0.0f, cyl = 0.0f, czh = 0.0f, czl = 0.0f;
+
+            for (int b = diag ? a : b0; b < b1; b++) {
+                __syncthreads();              // the tile buffer is free
+                {
+                    const int k = threadIdx.x, j = b * kSymT + k;
+                    if (j < n) {
+                        sx[k] = A.x[j]; sy[k] = A.y[j]; sz[k] = A.z[j]; sm[k] = A.m[j];
+                        sirc[k] = A.irc[j]; sthr[k] = A.thr[j];
+                        if (MIXED) { const float2 q = A.mhl[j]; smh[k] = q.x; sml[k] = q.y; }
+                    } else {
+                        sx[k] = sy[k] = sz[k] = pad_pos(k); sm[k] = 0.0;
+                        sirc[k] = 0.0; sthr[k] = 0.0f; smh[k] = 0.0f; sml[k] = 0.0f;
+                    }
+                }
+                __syncthreads();
+                const bool same = a == b;
+                for (int s = 0; s < 4; s++) {
+                    const int q = (w + s) & 3;
+                    if (!same || q >= w) {
+                        const bool dsub = same && q == w;
+                        const int t0 = dsub ? 1 : 0, t1 = dsub ? 17 : 32;
+                        const int qb = q * 32;
+                        // running sums of the j body this lane holds: (lane + t) mod 32 at step t
+                        double jx = 0.0, jy = 0.0, jz = 0.0;
+                        float jxh = 0.0f, jxl = 0.0f, jyh = 0.0f, jyl = 0.0f, jzh = 0.0f, jzl = 0.0f;
+#pragma unroll 4
+                        for (int t = t0; t < t1; t++) {
+                            const int k = qb + ((lane + t) & 31);
+                            const bool half = dsub && t == 16 && lane >= 16;    // pair taken by lane - 16
+                            const double dx = sx[k] - xi;
+                            const double dy = sy[k] - yi;
+                            const double dz = sz[k] - zi;
+                            if (MIXED) {
+                                float hx, hy, hz, lx, ly, lz;
+                                split_f64(dx, hx, lx);
+                                split_f64(dy, hy, ly);
+                                split_f64(dz, hz, lz);
+                                const float px = hx * hx, py = hy * hy, pz = hz * hz;
+                                const float pxe = fmaf(hx, hx, -px), pye = fmaf(hy, hy, -py), pze = fmaf(hz, hz, -pz);
+                                const float s1 = px + py, bb1 = s1 - px;
+                                const float e1 = (px - (s1 - bb1)) + (py - bb1);
+                                const float s2 = s1 + pz, bb2 = s2 - s1;
+                                const float e2 = (s1 - (s2 - bb2)) + (pz - bb2);
+                                const float cross = 2.0f * fmaf(hx, lx, fmaf(hy, ly, hz * lz));
+                                const float tail = ((e1 + e2) + (pxe + pye + pze)) + cross;
+                                const float Rh = s2 + tail;
+                                const float Rl = tail - (Rh - s2);
+                                float mhj = smh[k], mlj = sml[k], mhI = mhi, mlI = mli;
+                                // changeover band (rare): K from r by the Newton rsqrt and
+                                // 1/rc_ij = min(1/rc_i, 1/rc_j); both masses scaled by K
+                                if (Rh < fmaxf(thri, sthr[k])) {
+                                    const double r2d = fma(dz, dz, fma(dy, dy, dx * dx));
+                                    const double K = changeover_fast(r2d * rsqrt_newton(r2d), fmin(irci, sirc[k]));
+                                    const double mkj = sm[k] * K, mki = mi * K;
+                                    mhj = __double2float_rn(mkj);
+                                    mlj = __double2float_rn(mkj - (double)mhj);
+                                    mhI = __double2float_rn(mki);
+                                    mlI = __double2float_rn(mki - (double)mhI);
+                                }
+                                if (half) { mhj = 0.0f; mlj = 0.0f; mhI = 0.0f; mlI = 0.0f; }
+                                // r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) as in kick_kernel; the
+                                // mass-free parts are shared by the two sides
+                                const float y0f = rsqrtf(Rh);
+                                const float u = Rh * y0f, ue = fmaf(Rh, y0f, -u);
+                                const float r1 = fmaf(-u, y0f, 1.0f);
+                                const float p = y0f * y0f, pe = fmaf(y0f, y0f, -p);
+                                const float qq = p * y0f;
+                                float qe = fmaf(p, y0f, -qq);
+                                qe = fmaf(pe, y0f, qe);
+                                const float ef = r1 - fmaf(ue, y0f, Rl * p);
+                                const float poly = fmaf(1.875f * ef, ef, 1.5f * ef);
+                                // i side: m_j r^-3 dx
+                                {
+                                    const float ch = qq * mhj;
+                                    float ce = fmaf(qq, mhj, -ch);
+                                    ce = fmaf(qq, mlj, ce);
+                                    ce = fmaf(qe, mhj, ce);
+                                    const float corr = fmaf(ch, poly, ce);
+                                    const double sj = f64_of_f32_any(ch);
+                                    ax = fma(sj, dx, ax);
+                                    ay = fma(sj, dy, ay);
+                                    az = fma(sj, dz, az);
+                                    float_two_sum_acc(cxh, cxl, corr * hx);
+                                    float_two_sum_acc(cyh, cyl, corr * hy);
+                                    float_two_sum_acc(czh, czl, corr * hz);
+                                }
+                                // j side: -m_i r^-3 dx
+                                {
+                                    const float ch = qq * mhI;
+                                    float ce = fmaf(qq, mhI, -ch);
+                                    ce = fmaf(qq, mlI, ce);
+                                    ce = fmaf(qe, mhI, ce);
+                                    const float corr = fmaf(ch, poly, ce);
+                                    const double si = f64_of_f32_any(ch);
+                                    jx = fma(-si, dx, jx);
+                                    jy = fma(-si, dy, jy);
+                                    jz = fma(-si, dz, jz);
+                                    float_two_sum_acc(jxh, jxl, -(corr * hx));
+                                    float_two_sum_acc(jyh, jyl, -(corr * hy));
+                                    float_two_sum_acc(jzh, jzl, -(corr * hz));
+                                }
+                            } else {
+                                const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                                const double yv = rsqrt_newton(r2);
+                                double y3 = (yv * yv) * yv;
+                                if (r2_to_float_trunc(r2) < fmaxf(thri, sthr[k]))
+                                    y3 *= changeover_fast(r2 * yv, fmin(irci, sirc[k]));
+                                const double sj = half ? 0.0 : sm[k] * y3;
+                                const double si = half ? 0.0 : mi * y3;
+                                ax = fma(sj, dx, ax);
+                                ay = fma(sj, dy, ay);
+                                az = fma(sj, dz, az);
+                                jx = fma(-si, dx, jx);
+                                jy = fma(-si, dy, jy);
+                                jz = fma(-si, dz, jz);
+                            }
+                            // pass the j sums on: lane L takes over lane L + 1's body
+                            const int src = (lane + 1) & 31;
+                            jx = __shfl_sync(0xffffffffu, jx, src);
+                            jy = __shfl_sync(0xffffffffu, jy, src);
+                            jz = __shfl_sync(0xffffffffu, jz, src);
+                            if (MIXED) {
+                                jxh = __shfl_sync(0xffffffffu, jxh, src);
+                                jxl = __shfl_sync(0xffffffffu, jxl, src);
+                                jyh = __shfl_sync(0xffffffffu, jyh, src);
+                                jyl = __shfl_sync(0xffffffffu, jyl, src);
+                                jzh = __shfl_sync(0xffffffffu, jzh, src);
+                                jzl = __shfl_sync(0xffffffffu, jzl, src);
+                            }
+                        }
+                        // after the last step's hand-over the lane holds body (lane + t1) mod 32
+                        const int e = (b - b0) * kSymT + qb + ((lane + t1) & 31);
+                        jax[e] += jx;
+                        jay[e] += jy;
+                        jaz[e] += jz;
+                        if (MIXED) {
+                            float_two_sum_acc(jc[0 * PT + e], jc[1 * PT + e], jxh);
+                            jc[1 * PT + e] += jxl;
+                            float_two_sum_acc(jc[2 * PT + e], jc[3 * PT + e], jyh);
+                            jc[3 * PT + e] += jyl;
+                            float_two_sum_acc(jc[4 * PT + e], jc[5 * PT + e], jzh);
+                            jc[5 * PT + e] += jzl;
+                        }
+                    }
+                    __syncthreads();          // subtile sums handed to the next warp
+                }
+            }
+            // row a done: its sums over the tiles of Y (slot Y), or, in a
+            // diagonal item, with the j sums of tile a, now complete (slot X)
+            if (valid) {
+                double S[3] = {ax, ay, az};
+                double C[3] = {0.0, 0.0, 0.0};
+                if (MIXED) {
+                    C[0] = f64_of_f32_any(cxh) + f64_of_f32_any(cxl);
+                    C[1] = f64_of_f32_any(cyh) + f64_of_f32_any(cyl);
+                    C[2] = f64_of_f32_any(czh) + f64_of_f32_any(czl);
+                }
+                if (diag) {
+                    const int e = (a - b0) * kSymT + threadIdx.x;
+                    const double J[3] = {jax[e], jay[e], jaz[e]};
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        double t, err;
+                        two_sum(S[c], J[c], t, err);
+                        S[c] = t;
+                        C[c] += err;
+                        if (MIXED) C[c] += f64_of_f32_any(jc[(2 * c) * PT + e]) + f64_of_f32_any(jc[(2 * c + 1) * PT + e]);
+                    }
+                }
+                double *pp = A.part + (size_t)(diag ? XY.x : XY.y) * 6 * n;
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    pp[(size_t)c * n + i] = S[c];
+                    pp[(size_t)(3 + c) * n + i] = C[c];
+                }
+            }
+        }
+        if (!diag) {                          // j sums of the Y tiles: slot X
+            double *pp = A.part + (size_t)XY.x * 6 * n;
+            for (int e = threadIdx.x; e < nj; e += kSymT) {
+                const int j = b0 * kSymT + e;
+                if (j >= n) continue;
+                const double J[3] = {jax[e], jay[e], jaz[e]};
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    pp[(size_t)c * n + j] = J[c];
+                    pp[(size_t)(3 + c) * n + j] =
+                        MIXED ? f64_of_f32_any(jc[(2 * c) * PT + e]) + f64_of_f32_any(jc[(2 * c + 1) * PT + e]) : 0.0;
+                }
+            }
+        }
+    }
+}
+
 // Folds the chunk partials in chunk order (TwoSum), scales by G and applies the
 // kick v += dt_half a; optionally stores a.
 __global__ void kick_finalize(const double *part, int nchunk, int n, double G, double dt_half,
@@ -410,24 +728,163 @@ static KickArgs make_args(genga_system *s, bool precheck) {
     return A;
 }
 
+// Symmetric-kick geometry for the system's N and precision: the super-range P
+// (0: the symmetric kick is not used), chosen by list-scheduling the items,
+// largest first, over the resident blocks and adding the finalize's cost.
+namespace {
+
+struct SymPlan {
+    int P = 0, nS = 0, blocks = 0;
+    std::vector<int2> items;
+};
+
+double sym_item_cost(int nT, int P, int X, int Y) {
+    const int px = std::min(P, nT - X * P), py = std::min(P, nT - Y * P);
+    return X == Y ? 0.5 * px * px : (double)px * py;
+}
+
+// Items in dispatch order and the predicted makespan (tile-pair units per block).
+double sym_schedule(int nT, int P, int slots, std::vector<int2> *order) {
+    const int nS = (nT + P - 1) / P;
+    std::vector<std::pair<double, int2>> it;
+    it.reserve((size_t)nS * (nS + 1) / 2);
+    for (int X = 0; X < nS; X++)
+        for (int Y = X; Y < nS; Y++) it.push_back({sym_item_cost(nT, P, X, Y), make_int2(X, Y)});
+    std::stable_sort(it.begin(), it.end(), [](const std::pair<double, int2> &u, const std::pair<double, int2> &v) {
+        return u.first > v.first;
+    });
+    std::priority_queue<double, std::vector<double>, std::greater<double>> h;
+    for (int k = 0; k < slots; k++) h.push(0.0);
+    double ms = 0.0;
+    for (const auto &e : it) {
+        const double t = h.top() + e.first;
+        h.pop();
+        h.push(t);
+        ms = std::max(ms, t);
+    }
+    if (order) {
+        order->clear();
+        for (const auto &e : it) order->push_back(e.second);
+    }
+    return ms;
+}
+
+template <bool MIXED>
+SymPlan sym_plan(int n, int num_sms, int layout, int req_P) {
+    SymPlan best;
+    const int nT = (n + kSymT - 1) / kSymT;
+    // FP64 instructions per unordered pair (symmetric) and per ordered pair
+    // (kick_kernel), and per partial slot per body in kick_finalize
+    const double c_sym = MIXED ? 9.2 : 21.5, c_old = MIXED ? 6.1 : 17.1, c_fin = 21.0;
+    // predicted time in FP64 instructions per SM: kick_kernel at 95 % balance;
+    // the symmetric kick's makespan (tile pairs per block, each block at 1/nb
+    // of its SM) plus the finalize's slots
+    if (layout == GENGA_KICK_TILED) return best;
+    const double t_old = c_old * (double)n * n / (0.95 * num_sms);
+    double t_best = layout == GENGA_KICK_SYMMETRIC ? 1e300 : t_old;
+    for (int P = req_P > 0 ? req_P : 1; P <= (req_P > 0 ? req_P : kSymMaxP); P++) {
+        const int nS = (nT + P - 1) / P;
+        if ((double)nS * 6.0 * n * sizeof(double) > 16.0 * (1ull << 30)) continue;   // partial sums
+        if ((double)nS * (nS + 1) / 2 > 4.0e6) continue;                                // host schedule
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kick_sym_kernel<MIXED>, kSymT,
+                                                          sym_smem(MIXED, P)) != cudaSuccess || nb < 1)
+            continue;
+        const int slots = nb * num_sms;
+        const double ms = sym_schedule(nT, P, slots, nullptr);
+        const double t = c_sym * (double)kSymT * kSymT * ms * nb + c_fin * (double)nS * n / num_sms;
+        if (t < t_best) {
+            t_best = t;
+            best.P = P; best.nS = nS; best.blocks = slots;
+        }
+    }
+    if (best.P) sym_schedule(nT, best.P, best.blocks, &best.items);
+    return best;
+}
+
+}  // namespace
+
+// Chooses the kick geometry for the current N and precision and makes sure the
+// partial-sum and symmetric-kick buffers are large enough.
+cudaError_t kick_reserve(genga_system *s) {
+    const int n = (int)s->n;
+    if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
+    const int prec = s->p.precision;
+    if (s->ksym_n != s->n || s->ksym_prec != prec) {
+        SymPlan plan = prec == GENGA_MIXED ? sym_plan<true>(n, s->num_sms, s->ksym_layout, s->ksym_req_P)
+                                           : sym_plan<false>(n, s->num_sms, s->ksym_layout, s->ksym_req_P);
+        s->ksym_P = plan.P;
+        s->ksym_nS = plan.nS;
+        s->ksym_blocks = plan.blocks;
+        s->ksym_items = (int)plan.items.size();
+        if (plan.P) {
+            if ((size_t)s->ksym_items > s->ksym_list_cap) {
+                if (s->ksym_list) cudaFree(s->ksym_list);
+                s->ksym_list = nullptr;
+                s->ksym_list_cap = 0;
+                GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_list, sizeof(int2) * plan.items.size()));
+                s->ksym_list_cap = plan.items.size();
+            }
+            GENGA_CUDA_TRY(cudaMemcpy(s->ksym_list, plan.items.data(), sizeof(int2) * plan.items.size(),
+                                      cudaMemcpyHostToDevice));
+            if (!s->ksym_ctr) GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_ctr, sizeof(unsigned)));
+            if ((size_t)n > s->ksym_body_cap) {
+                if (s->ksym_irc) cudaFree(s->ksym_irc);
+                if (s->ksym_mhl) cudaFree(s->ksym_mhl);
+                s->ksym_irc = nullptr; s->ksym_mhl = nullptr; s->ksym_body_cap = 0;
+                GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_irc, sizeof(double) * (size_t)n));
+                GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_mhl, sizeof(float2) * (size_t)n));
+                s->ksym_body_cap = (size_t)n;
+            }
+        }
+        s->ksym_n = s->n;
+        s->ksym_prec = prec;
+    }
+    const size_t need = (size_t)std::max(s->kick_nchunk, s->ksym_nS) * 6 * (size_t)n;
+    if (need > s->kick_part_cap) {
+        if (s->kick_part) cudaFree(s->kick_part);
+        s->kick_part = nullptr;
+        s->kick_part_cap = 0;
+        GENGA_CUDA_TRY(cudaMalloc((void **)&s->kick_part, sizeof(double) * need));
+        s->kick_part_cap = need;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *acc_out) {
     const int n = (int)s->n;
-    if (!s->kick_part) return cudaErrorInvalidValue;
-    if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
+    GENGA_CUDA_TRY(kick_reserve(s));
     KickArgs A = make_args(s, false);
-    dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
     if (precheck) GENGA_CUDA_TRY(launch_precheck_only(s));
     const bool mixed = s->p.precision == GENGA_MIXED;
-    if (A.nm < n) {
-        if (mixed) kick_kernel<true, true><<<grid, kKickThreads, 0, s->stream>>>(A);
-        else kick_kernel<false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+    int nparts = s->kick_nchunk;
+    if (A.nm >= n && s->ksym_P > 0) {
+        kick_pack_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(s->mass, s->rcl[0].rc, n, s->ksym_irc,
+                                                               s->ksym_mhl);
+        ++s->launches;
+        GENGA_CUDA_TRY(cudaMemsetAsync(s->ksym_ctr, 0, sizeof(unsigned), s->stream));
+        SymArgs S;
+        S.x = A.x; S.y = A.y; S.z = A.z; S.m = A.m;
+        S.irc = s->ksym_irc; S.thr = A.thr_rc; S.mhl = s->ksym_mhl;
+        S.n = n; S.nT = (n + kSymT - 1) / kSymT; S.P = s->ksym_P; S.nItems = s->ksym_items;
+        S.items = s->ksym_list; S.ctr = s->ksym_ctr; S.part = s->kick_part;
+        const size_t smem = sym_smem(mixed, s->ksym_P);
+        if (mixed) kick_sym_kernel<true><<<s->ksym_blocks, kSymT, smem, s->stream>>>(S);
+        else kick_sym_kernel<false><<<s->ksym_blocks, kSymT, smem, s->stream>>>(S);
+        nparts = s->ksym_nS;
     } else {
-        if (mixed) kick_kernel<true, false><<<grid, kKickThreads, 0, s->stream>>>(A);
-        else kick_kernel<false, false><<<grid, kKickThreads, 0, s->stream>>>(A);
+        dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
+        if (A.nm < n) {
+            if (mixed) kick_kernel<true, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+            else kick_kernel<false, true><<<grid, kKickThreads, 0, s->stream>>>(A);
+        } else {
+            if (mixed) kick_kernel<true, false><<<grid, kKickThreads, 0, s->stream>>>(A);
+            else kick_kernel<false, false><<<grid, kKickThreads, 0, s->stream>>>(A);
+        }
     }
     ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    kick_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(s->kick_part, s->kick_nchunk, n, s->p.G,
+    kick_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(s->kick_part, nparts, n, s->p.G,
                                                           dt_half, s->vel, acc_out); ++s->launches;
     return cudaGetLastError();
 }
@@ -475,3 +932,29 @@ int kick_nchunk_for(int n, int num_sms) {
 }
 
 }  // namespace genga
+
+using namespace genga;
+
+extern "C" int genga_set_kick_layout(genga_system_t *s, int32_t layout, int32_t P) {
+    if (!s || layout < GENGA_KICK_AUTO || layout > GENGA_KICK_SYMMETRIC || P < 0 || P > kSymMaxP)
+        return GENGA_EINVAL;
+    s->ksym_layout = layout;
+    s->ksym_req_P = P;
+    s->ksym_n = -1;                       // geometry redone by the next kick
+    return GENGA_OK;
+}
+
+extern "C" int genga_get_kick_layout(genga_system_t *s, int32_t *layout, int32_t *P, int32_t *slots,
+                                     int32_t *blocks) {
+    if (!s) return GENGA_EINVAL;
+    if (kick_reserve(s) != cudaSuccess) return GENGA_ECUDA;
+    const bool sym = s->ksym_P > 0 && tp_bound(s) >= s->n;
+    if (layout) *layout = sym ? GENGA_KICK_SYMMETRIC : GENGA_KICK_TILED;
+    if (P) *P = sym ? s->ksym_P : 0;
+    if (slots) *slots = sym ? s->ksym_nS : s->kick_nchunk;
+    if (blocks)
+        *blocks = sym ? s->ksym_blocks
+                      : (int32_t)(((s->n + kKickThreads - 1) / kKickThreads) * (int64_t)s->kick_nchunk);
+    return GENGA_OK;
+}
+

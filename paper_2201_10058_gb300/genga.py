@@ -19,6 +19,9 @@ GENGA_FP64 = 0
 GENGA_MIXED = 1
 GENGA_GR_IMPLICIT = 1
 GENGA_GR_SPLIT = 2
+GENGA_KICK_AUTO = 0
+GENGA_KICK_TILED = 1
+GENGA_KICK_SYMMETRIC = 2
 
 ERRORS = {0: "OK", -1: "EINVAL", -2: "ECAPACITY", -3: "ENONCONV", -4: "ETIMEOUT",
           -5: "EBADSTATE", -6: "ECUDA", -7: "ENOMEM"}
@@ -36,7 +39,8 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_measure_pipe_rates", "genga_init_system", "genga_step_backward",
             "genga_init_ensemble", "genga_step_ensemble", "genga_set_pair_log",
             "genga_get_pair_log", "genga_set_wait_limits", "genga_set_collisions",
-            "genga_get_mergers", "genga_get_alive", "genga_remove_merged"]
+            "genga_get_mergers", "genga_get_alive", "genga_remove_merged", "genga_set_kick_layout",
+            "genga_get_kick_layout"]
 
 NPHASES = 18
 
@@ -164,6 +168,8 @@ def load(build_if_missing: bool = True):
         L.genga_get_alive.argtypes = [sysp, _VP]
         L.genga_remove_merged.argtypes = [sysp, _P(C.c_int64), _VP]
         L.genga_set_pair_log.argtypes = [sysp, C.c_int]
+        L.genga_set_kick_layout.argtypes = [sysp, C.c_int32, C.c_int32]
+        L.genga_get_kick_layout.argtypes = [sysp] + [_P(C.c_int32)] * 4
         L.genga_get_pair_log.argtypes = [sysp, _VP, _VP, _VP, C.c_int64, C.c_int64, _P(C.c_int64),
                                          _P(C.c_int64)]
         L.genga_measure_pipe_rates.argtypes = [_P(C.c_double)] * 5
@@ -403,6 +409,18 @@ class System:
         """Wall-clock limits of the bounded device waits (negative: default)."""
         self._check(self._lib.genga_set_wait_limits(self._h, bs_group_seconds, barrier_seconds,
                                                     barrier_absent_blocks))
+
+    def set_kick_layout(self, layout: int = GENGA_KICK_AUTO, P: int = 0):
+        """How the all-pairs kick traverses the pairs: GENGA_KICK_AUTO,
+        GENGA_KICK_TILED or GENGA_KICK_SYMMETRIC (each unordered pair once),
+        with the super-range P (0: chosen for N)."""
+        self._check(self._lib.genga_set_kick_layout(self._h, int(layout), int(P)))
+
+    def kick_layout(self) -> dict:
+        """The layout the next kick uses: layout, P, partial slots per body, blocks."""
+        v = [C.c_int32() for _ in range(4)]
+        self._check(self._lib.genga_get_kick_layout(self._h, *[C.byref(x) for x in v]))
+        return {"layout": v[0].value, "P": v[1].value, "slots": v[2].value, "blocks": v[3].value}
 
     def set_pair_log(self, enable: bool = True):
         """Switches the detection log on or off (and clears it)."""
