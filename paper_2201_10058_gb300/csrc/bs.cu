@@ -61,7 +61,7 @@ struct KickPairsArgs {
     const double *pos;
     double *vel;
     const double *mass;
-    const double *rc[kMaxLevels];
+    const double *irc[kMaxLevels];   // 1 / rc per level and body
     const double *rc2_0;
     double G, dt_half;
 };
@@ -82,9 +82,10 @@ __global__ void kick_pairs_terms_kernel(KickPairsArgs A) {
         const double yv = rsqrt_newton(r2);
         const double r = r2 * yv;
         double W = 1.0;
+        // 1 / rc_ij = 1 / max(rc_i, rc_j) = min(1/rc_i, 1/rc_j), bit for bit
         for (int l = 0; l < A.level; l++)
-            W *= 1.0 - changeover_fast(r, 1.0 / fmax(A.rc[l][i], A.rc[l][j]));
-        W *= changeover_fast(r, 1.0 / fmax(A.rc[A.level][i], A.rc[A.level][j]));
+            W *= 1.0 - changeover_fast(r, fmin(A.irc[l][i], A.irc[l][j]));
+        W *= changeover_fast(r, fmin(A.irc[A.level][i], A.irc[A.level][j]));
         g = W * yv * yv * yv;
     }
     A.term[k] = g * dx;
@@ -92,14 +93,25 @@ __global__ void kick_pairs_terms_kernel(KickPairsArgs A) {
     A.term[2 * NP + k] = g * dz;
 }
 
+// Phase 2 runs kApplyLanes lanes per body: lane s takes the partners
+// s, s + kApplyLanes, ... of the body's ascending list, and the lane sums meet
+// in a fixed butterfly -- a fixed summation order with the gathers of eight
+// partners in flight at once.
+constexpr int kApplyLanes = 8;
+
 __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= A.nb) return;
-    const int b = A.bodies[t];
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = gt / kApplyLanes, sub = gt % kApplyLanes;
     const size_t N = (size_t)A.n;
     const size_t NP = (size_t)A.np;
+    int b = 0, q0 = 0, q1 = 0;
+    if (t < A.nb) {
+        b = A.bodies[t];
+        q0 = A.off[b];
+        q1 = A.off[b + 1];
+    }
     double sx = 0.0, sy = 0.0, sz = 0.0;
-    for (int q = A.off[b]; q < A.off[b + 1]; q++) {
+    for (int q = q0 + sub; q < q1; q += kApplyLanes) {
         const int p = A.list[q];
         const int k = A.lpair[q];
         const double w = (p > b) ? A.mass[p] : -A.mass[p];
@@ -107,9 +119,17 @@ __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
         sy = fma(w, A.term[NP + k], sy);
         sz = fma(w, A.term[2 * NP + k], sz);
     }
-    A.vel[b] += A.dt_half * (A.G * sx);
-    A.vel[N + b] += A.dt_half * (A.G * sy);
-    A.vel[2 * N + b] += A.dt_half * (A.G * sz);
+#pragma unroll
+    for (int o = kApplyLanes / 2; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (t < A.nb && sub == 0) {
+        A.vel[b] += A.dt_half * (A.G * sx);
+        A.vel[N + b] += A.dt_half * (A.G * sy);
+        A.vel[2 * N + b] += A.dt_half * (A.G * sz);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -578,14 +598,15 @@ cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb
     A.off = s->csr[level - 1].off; A.list = s->csr[level - 1].list; A.lpair = s->csr[level - 1].lpair;
     A.term = s->csr[level - 1].term;
     A.pos = s->pos; A.vel = s->vel; A.mass = s->mass;
-    for (int l = 0; l < kMaxLevels; l++) A.rc[l] = s->rcl[l].rc;
+    for (int l = 0; l < kMaxLevels; l++) A.irc[l] = s->rcl[l].irc;
     A.rc2_0 = s->rcl[0].rc2;
     A.G = s->p.G; A.dt_half = dt_half;
     if (A.np > 0) {
         kick_pairs_terms_kernel<<<(unsigned)((A.np + 255) / 256), 256, 0, s->stream>>>(A); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
-    kick_pairs_apply_kernel<<<(nb + 127) / 128, 128, 0, s->stream>>>(A); ++s->launches;
+    const long long nt = (long long)nb * kApplyLanes;
+    kick_pairs_apply_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s->stream>>>(A); ++s->launches;
     return cudaGetLastError();
 }
 

@@ -82,6 +82,7 @@ struct RcritArrays {
     double *rc2 = nullptr;   // rc_i^2 (pair value: max of the two, exact)
     double *pc2 = nullptr;   // (f_pc rc_i)^2 (level 0 only)
     float *thr_rc = nullptr; // conservative FP32 upper bound of rc_i^2 (level 0 only)
+    double *irc = nullptr;   // 1 / rc_i, correctly rounded (so min(irc_i, irc_j) = 1 / rc_ij exactly)
 };
 
 // CSR partner lists (both directions) of one pair list.
@@ -137,6 +138,7 @@ struct genga_system {
     unsigned *ksym_ctr = nullptr;  // dispatch counter
     double *ksym_irc = nullptr;    // 1 / rc per body
     float2 *ksym_mhl = nullptr;    // mass as two floats
+    float *ksym_thrpc = nullptr;   // FP32 upper bound of (f_pc rc)^2
     size_t ksym_body_cap = 0;
 
     // candidates and encounter lists

@@ -142,6 +142,10 @@ int alloc_level(genga_system *s, int l) {
         CU(dalloc(&s->rcl[l].rc2, n));
         CU(cudaMemset(s->rcl[l].rc2, 0, sizeof(double) * n));
     }
+    if (!s->rcl[l].irc) {
+        CU(dalloc(&s->rcl[l].irc, n));
+        CU(cudaMemset(s->rcl[l].irc, 0, sizeof(double) * n));
+    }
     if (!s->pre_pos[l]) CU(dalloc(&s->pre_pos[l], 3 * n));
     if (!s->pre_vel[l]) CU(dalloc(&s->pre_vel[l], 3 * n));
     if (!s->csr[l].deg) CU(dalloc(&s->csr[l].deg, n + 1));
@@ -191,7 +195,7 @@ int alloc_all(genga_system *s) {
 void free_all(genga_system *s) {
     dfree(s->ctr);
     for (int l = 0; l < kMaxLevels; l++) {
-        dfree(s->rcl[l].rc); dfree(s->rcl[l].rc2); dfree(s->rcl[l].pc2);
+        dfree(s->rcl[l].rc); dfree(s->rcl[l].rc2); dfree(s->rcl[l].pc2); dfree(s->rcl[l].irc);
         dfree(s->rcl[l].thr_rc);
         dfree(s->pre_pos[l]); dfree(s->pre_vel[l]);
         dfree(s->pairs[l]);
@@ -199,7 +203,7 @@ void free_all(genga_system *s) {
         dfree(s->csr[l].lpair); dfree(s->csr[l].term);
         dfree(s->bodies[l]);
     }
-    dfree(s->kick_part); dfree(s->ksym_list); dfree(s->ksym_ctr); dfree(s->ksym_irc); dfree(s->ksym_mhl);
+    dfree(s->kick_part); dfree(s->ksym_list); dfree(s->ksym_ctr); dfree(s->ksym_irc); dfree(s->ksym_mhl); dfree(s->ksym_thrpc);
     s->kick_part_cap = 0; s->ksym_list_cap = 0; s->ksym_body_cap = 0; s->ksym_n = -1;
     dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
     dfree(s->gsize); dfree(s->goff); dfree(s->gfill); dfree(s->glist); dfree(s->member);

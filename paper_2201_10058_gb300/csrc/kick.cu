@@ -404,11 +404,17 @@ struct SymArgs {
     const int2 *items;          // (X, Y) super-tile pairs, X <= Y, in dispatch order
     unsigned *ctr;              // dispatch counter, zero at launch
     double *part;               // [nS][6][n]
+    // fused pre-check (PC): candidates i < j with r^2 < max(pc2_i, pc2_j)
+    const double *pc2;          // (f_pc rc)^2
+    const float *thr_pc;        // FP32 upper bound of pc2 (2^-16 margin)
+    uint2 *cand;
+    unsigned long long *cand_count;
+    unsigned long long cand_cap;
 };
 
 // Resident blocks per SM the register allocation must allow (128 threads each).
-constexpr int sym_min_blocks(bool mixed) {
-    return mixed ? 4 : 4;
+constexpr int sym_min_blocks(bool mixed, bool pc) {
+    return mixed ? 5 : (pc ? 5 : 4);
 }
 
 // Dynamic shared memory: the staged j tile (x, y, z, m, 1/rc; thr, mh, ml),
@@ -422,16 +428,54 @@ constexpr size_t sym_smem(bool mixed, int P) {
 // distinct for distinct k (no zero separation), massless.
 __device__ __forceinline__ double pad_pos(int k) { return 1.0e15 + 1.0e13 * (double)k; }
 
-__global__ void kick_pack_kernel(const double *m, const double *rc, int n, double *irc, float2 *mhl) {
+__global__ void kick_pack_kernel(const double *m, const double *rc, const double *pc2, int n, double *irc,
+                                 float2 *mhl, float *thr_pc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     irc[i] = inv_rc(rc[i]);
+    // rounded up, then 2^-16 more: any float r^2 within 2^-23 of an r^2 below
+    // pc2 is below it
+    thr_pc[i] = fmaxf(__double2float_ru(pc2[i]) * 1.0000153f, 1.17549435e-38f);
     const float mh = __double2float_rn(m[i]);
     mhl[i] = make_float2(mh, __double2float_rn(m[i] - (double)mh));
 }
 
-template <bool MIXED>
-__global__ void __launch_bounds__(kSymT, sym_min_blocks(MIXED))
+constexpr int kSymPcBuf = 128;                 // per-warp candidate buffer (shared memory)
+
+// Appends a warp's buffered candidates to the global list (one atomic per flush).
+__device__ __forceinline__ void sym_pc_flush(const SymArgs &A, const uint2 *buf, int &cnt, int lane) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if (lane == 0 && cnt) base = atomicAdd(A.cand_count, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int t = lane; t < cnt; t += 32) {
+        const unsigned long long idx = base + (unsigned long long)t;
+        if (idx < A.cand_cap) A.cand[idx] = buf[t];
+    }
+    __syncwarp();
+    cnt = 0;
+}
+
+// One pair's pre-check inside the kick (warp-uniform call): lanes with
+// `maybe` take the exact test; the warp appends its candidates (i < j) to its
+// buffer, flushed when it could overflow on the next step.
+__device__ __forceinline__ void sym_precheck(const SymArgs &A, uint2 *buf, int &pend, int lane, bool maybe,
+                                             int i, int j, double dx, double dy, double dz) {
+    if (!__any_sync(0xffffffffu, maybe)) return;
+    bool emit = false;
+    if (maybe && i < A.n && j < A.n) emit = dist2_rn(dx, dy, dz) < fmax(A.pc2[i], A.pc2[j]);
+    const unsigned ball = __ballot_sync(0xffffffffu, emit);
+    if (emit) buf[pend + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)min(i, j), (unsigned)max(i, j));
+    pend += __popc(ball);
+    if (pend > kSymPcBuf - 32) sym_pc_flush(A, buf, pend, lane);
+}
+
+// PC: the close-encounter pre-check of Appendix A fused into the kick: a pair
+// whose float r^2 (within 2^-23 of r^2) is below max(thr_pc_i, thr_pc_j) takes
+// the exact FP64 test of precheck_kernel (dist2_rn, no contraction) -- the same
+// candidates, found on the FP32/INT pipes the FP64-bound kick leaves idle.
+template <bool MIXED, bool PC>
+__global__ void __launch_bounds__(kSymT, sym_min_blocks(MIXED, PC))
 kick_sym_kernel(SymArgs A)
 {
     extern __shared__ __align__(16) unsigned char sym_sh[];
@@ -444,6 +488,9 @@ kick_sym_kernel(SymArgs A)
     double *jay = jax + PT, *jaz = jay + PT;
     float *jc = reinterpret_cast<float *>(jaz + PT);      // [6][PT]: x hi, x lo, y hi, y lo, z hi, z lo
     __shared__ int s_item;
+    __shared__ float sthp[PC ? kSymT : 1];                // thr_pc of the j tile
+    __shared__ uint2 pcb[PC ? kSymT / 32 : 1][PC ? kSymPcBuf : 1];
+    int pend = 0;                                         // candidates in this warp's buffer
 
     const int n = A.n;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -468,10 +515,11 @@ kick_sym_kernel(SymArgs A)
             const int i = a * kSymT + threadIdx.x;
             const bool valid = i < n;
             double xi, yi, zi, mi = 0.0, irci = 0.0;
-            float thri = 0.0f, mhi = 0.0f, mli = 0.0f;
+            float thri = 0.0f, mhi = 0.0f, mli = 0.0f, thpi = 0.0f;
             if (valid) {
                 xi = A.x[i]; yi = A.y[i]; zi = A.z[i]; mi = A.m[i];
                 irci = A.irc[i]; thri = A.thr[i];
+                if (PC) thpi = A.thr_pc[i];
                 if (MIXED) { const float2 q = A.mhl[i]; mhi = q.x; mli = q.y; }
             } else {
                 xi = yi = zi = pad_pos(threadIdx.x);
@@ -487,9 +535,11 @@ kick_sym_kernel(SymArgs A)
                         sx[k] = A.x[j]; sy[k] = A.y[j]; sz[k] = A.z[j]; sm[k] = A.m[j];
                         sirc[k] = A.irc[j]; sthr[k] = A.thr[j];
                         if (MIXED) { const float2 q = A.mhl[j]; smh[k] = q.x; sml[k] = q.y; }
+                        if (PC) sthp[k] = A.thr_pc[j];
                     } else {
                         sx[k] = sy[k] = sz[k] = pad_pos(k); sm[k] = 0.0;
                         sirc[k] = 0.0; sthr[k] = 0.0f; smh[k] = 0.0f; sml[k] = 0.0f;
+                        if (PC) sthp[k] = 0.0f;
                     }
                 }
                 __syncthreads();
@@ -525,6 +575,8 @@ kick_sym_kernel(SymArgs A)
                                 const float tail = ((e1 + e2) + (pxe + pye + pze)) + cross;
                                 const float Rh = s2 + tail;
                                 const float Rl = tail - (Rh - s2);
+                                if (PC) sym_precheck(A, pcb[w], pend, lane, !half && Rh < fmaxf(thpi, sthp[k]), i,
+                                                     b * kSymT + k, dx, dy, dz);
                                 float mhj = smh[k], mlj = sml[k], mhI = mhi, mlI = mli;
                                 // changeover band (rare): K from r by the Newton rsqrt and
                                 // 1/rc_ij = min(1/rc_i, 1/rc_j); both masses scaled by K
@@ -581,9 +633,12 @@ kick_sym_kernel(SymArgs A)
                                 }
                             } else {
                                 const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                                const float r2f = r2_to_float_trunc(r2);
+                                if (PC) sym_precheck(A, pcb[w], pend, lane, !half && r2f < fmaxf(thpi, sthp[k]), i,
+                                                     b * kSymT + k, dx, dy, dz);
                                 const double yv = rsqrt_newton(r2);
                                 double y3 = (yv * yv) * yv;
-                                if (r2_to_float_trunc(r2) < fmaxf(thri, sthr[k]))
+                                if (r2f < fmaxf(thri, sthr[k]))
                                     y3 *= changeover_fast(r2 * yv, fmin(irci, sirc[k]));
                                 const double sj = half ? 0.0 : sm[k] * y3;
                                 const double si = half ? 0.0 : mi * y3;
@@ -670,6 +725,7 @@ kick_sym_kernel(SymArgs A)
             }
         }
     }
+    if (PC) sym_pc_flush(A, pcb[w], pend, lane);
 }
 
 // Folds the chunk partials in chunk order (TwoSum), scales by G and applies the
@@ -787,7 +843,7 @@ SymPlan sym_plan(int n, int num_sms, int layout, int req_P) {
         if ((double)nS * 6.0 * n * sizeof(double) > 16.0 * (1ull << 30)) continue;   // partial sums
         if ((double)nS * (nS + 1) / 2 > 4.0e6) continue;                                // host schedule
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kick_sym_kernel<MIXED>, kSymT,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kick_sym_kernel<MIXED, false>, kSymT,
                                                           sym_smem(MIXED, P)) != cudaSuccess || nb < 1)
             continue;
         const int slots = nb * num_sms;
@@ -831,9 +887,11 @@ cudaError_t kick_reserve(genga_system *s) {
             if ((size_t)n > s->ksym_body_cap) {
                 if (s->ksym_irc) cudaFree(s->ksym_irc);
                 if (s->ksym_mhl) cudaFree(s->ksym_mhl);
-                s->ksym_irc = nullptr; s->ksym_mhl = nullptr; s->ksym_body_cap = 0;
+                if (s->ksym_thrpc) cudaFree(s->ksym_thrpc);
+                s->ksym_irc = nullptr; s->ksym_mhl = nullptr; s->ksym_thrpc = nullptr; s->ksym_body_cap = 0;
                 GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_irc, sizeof(double) * (size_t)n));
                 GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_mhl, sizeof(float2) * (size_t)n));
+                GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_thrpc, sizeof(float) * (size_t)n));
                 s->ksym_body_cap = (size_t)n;
             }
         }
@@ -855,24 +913,35 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
     const int n = (int)s->n;
     GENGA_CUDA_TRY(kick_reserve(s));
     KickArgs A = make_args(s, false);
-    if (precheck) GENGA_CUDA_TRY(launch_precheck_only(s));
     const bool mixed = s->p.precision == GENGA_MIXED;
     int nparts = s->kick_nchunk;
     if (A.nm >= n && s->ksym_P > 0) {
-        kick_pack_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(s->mass, s->rcl[0].rc, n, s->ksym_irc,
-                                                               s->ksym_mhl);
+        // symmetric layout; the pre-check, if asked for, rides along
+        kick_pack_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(s->mass, s->rcl[0].rc, s->rcl[0].pc2, n,
+                                                               s->ksym_irc, s->ksym_mhl, s->ksym_thrpc);
         ++s->launches;
         GENGA_CUDA_TRY(cudaMemsetAsync(s->ksym_ctr, 0, sizeof(unsigned), s->stream));
+        if (precheck)
+            GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->cand_count, 0, sizeof(unsigned long long), s->stream));
         SymArgs S;
         S.x = A.x; S.y = A.y; S.z = A.z; S.m = A.m;
         S.irc = s->ksym_irc; S.thr = A.thr_rc; S.mhl = s->ksym_mhl;
         S.n = n; S.nT = (n + kSymT - 1) / kSymT; S.P = s->ksym_P; S.nItems = s->ksym_items;
         S.items = s->ksym_list; S.ctr = s->ksym_ctr; S.part = s->kick_part;
+        S.pc2 = s->rcl[0].pc2; S.thr_pc = s->ksym_thrpc;
+        S.cand = s->cand; S.cand_count = &s->ctr->cand_count; S.cand_cap = (unsigned long long)s->cand_cap;
         const size_t smem = sym_smem(mixed, s->ksym_P);
-        if (mixed) kick_sym_kernel<true><<<s->ksym_blocks, kSymT, smem, s->stream>>>(S);
-        else kick_sym_kernel<false><<<s->ksym_blocks, kSymT, smem, s->stream>>>(S);
+        const unsigned nb = (unsigned)s->ksym_blocks;
+        if (mixed) {
+            if (precheck) kick_sym_kernel<true, true><<<nb, kSymT, smem, s->stream>>>(S);
+            else kick_sym_kernel<true, false><<<nb, kSymT, smem, s->stream>>>(S);
+        } else {
+            if (precheck) kick_sym_kernel<false, true><<<nb, kSymT, smem, s->stream>>>(S);
+            else kick_sym_kernel<false, false><<<nb, kSymT, smem, s->stream>>>(S);
+        }
         nparts = s->ksym_nS;
     } else {
+        if (precheck) GENGA_CUDA_TRY(launch_precheck_only(s));
         dim3 grid((n + kKickThreads - 1) / kKickThreads, s->kick_nchunk);
         if (A.nm < n) {
             if (mixed) kick_kernel<true, true><<<grid, kKickThreads, 0, s->stream>>>(A);

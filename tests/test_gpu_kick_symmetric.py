@@ -12,6 +12,8 @@ padding of the last tile are few enough to reach every case:
     sides of every neighbour pair);
   * the same result bit for bit on every kick, although the blocks take their
     work items from a counter in whatever order they come;
+  * the pre-check fused into the symmetric kick: candidate lists identical to
+    the oracle's, including an overflowing list that is regrown;
   * whole steps: 10 steps of the N = 2048 disk to 1e-12 (FP64) / 1e-9 (mixed),
     and 100 steps of the encounter-free control.
 """
@@ -129,6 +131,47 @@ def test_symmetric_kick_is_deterministic(g, precision):
     torch.cuda.synchronize()
     for o in outs[1:]:
         assert torch.equal(o, outs[0])
+
+
+@pytest.mark.parametrize("n,P", [(300, 1), (1000, 3), (3001, 2)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_precheck_candidates_bit_exact(g, n, P, precision):
+    """The pre-check rides inside the symmetric kick (float r^2 screen, exact
+    FP64 test in the band): the candidate list equals the oracle's, and the
+    kick equals the kick without the pre-check."""
+    torch = _torch()
+    wl = disk(n, 0.9, 1.1, 2.0, 200 + n, name=f"dense{n}")
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    ref = O.precheck(wl.x, rc, wl.f_pc)
+    assert len(ref) > 0
+    s, pos, vel, mass = _system(g, wl, precision, g.GENGA_KICK_SYMMETRIC, P)
+    s.set_rcrit(rc)
+    s.kick(0.5 * wl.dt, precheck=True)
+    np.testing.assert_array_equal(s.candidates(), ref)
+    s2, pos2, vel2, mass2 = _system(g, wl, precision, g.GENGA_KICK_SYMMETRIC, P)
+    s2.set_rcrit(rc)
+    s2.kick(0.5 * wl.dt, precheck=False)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(_host(vel), _host(vel2), rtol=1e-14, atol=0)
+
+
+def test_fused_precheck_overflow_regrows(g):
+    """A candidate list of capacity 16 overflows inside the fused kick; the
+    list is regrown and recomputed at the same positions."""
+    wl = config_workload(0)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    torch = _torch()
+    dev = torch.device("cuda:0")
+    pos = torch.tensor(np.ascontiguousarray(wl.x.T), device=dev)
+    vel = torch.tensor(np.ascontiguousarray(wl.v.T), device=dev)
+    mass = torch.tensor(wl.m, device=dev)
+    p = g.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc,
+                         precision=1, cand_capacity=16)
+    s = g.System(pos, vel, mass, p)
+    s.set_kick_layout(g.GENGA_KICK_SYMMETRIC, 1)
+    s.set_rcrit(rc)
+    s.kick(0.5 * wl.dt, precheck=True)
+    np.testing.assert_array_equal(s.candidates(), O.precheck(wl.x, rc, wl.f_pc))
 
 
 def test_auto_layout_choice(g):
