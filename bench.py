@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--kick-layout", choices=["auto", "tiled", "symmetric"], default="auto",
                     help="kick layout of --workload kick (auto: the library's choice for N)")
     ap.add_argument("--kick-p", type=int, default=0, help="symmetric layout super-range (0: chosen)")
+    ap.add_argument("--kick-precheck", action="store_true",
+                    help="--workload kick: each kick also records the close-encounter candidates")
     ap.add_argument("--ens-tile", default="",
                     help="threads,ctas_per_sm of the ensemble kernel instead of autotuning "
                          "(profiling runs)")
@@ -888,13 +890,13 @@ def run_kick(args) -> dict:
     lay = sysm.kick_layout()
     sysm.rcrit(wl.dt)
     acc = torch.empty((3, wl.n), dtype=torch.float64, device=dev)
-    sysm.kick(0.0, precheck=False, acc_out=acc)
+    sysm.kick(0.0, precheck=args.kick_precheck, acc_out=acc)
     torch.cuda.synchronize()
     k0 = torch.cuda.Event(enable_timing=True)
     k1 = torch.cuda.Event(enable_timing=True)
     k0.record(stream)
     for _ in range(args.kick_reps):
-        sysm.kick(0.0, precheck=False, acc_out=acc)
+        sysm.kick(0.0, precheck=args.kick_precheck, acc_out=acc)
     k1.record(stream)
     k1.synchronize()
     ms = k0.elapsed_time(k1) / args.kick_reps
@@ -902,6 +904,7 @@ def run_kick(args) -> dict:
     n = wl.n
     return {"metric": "all-pairs changeover kick alone (secondary measurement)", "kick": args.kick,
             "n_bodies": n, "launches": args.kick_reps, "ms_per_launch": round(ms, 4), "layout": lay,
+            "precheck": bool(args.kick_precheck),
             "gpairs_per_s": round(n * (n - 1) / (ms * 1e-3) / 1e9, 3)}
 
 

@@ -137,8 +137,10 @@ struct genga_system {
     size_t ksym_list_cap = 0;
     unsigned *ksym_ctr = nullptr;  // dispatch counter
     double *ksym_irc = nullptr;    // 1 / rc per body
+    float2 *ksym_ircf = nullptr;   // the same as two floats
     float2 *ksym_mhl = nullptr;    // mass as two floats
     float *ksym_thrpc = nullptr;   // FP32 upper bound of (f_pc rc)^2
+    float2 *ksym_pcf = nullptr;    // (f_pc rc)^2 as two floats
     size_t ksym_body_cap = 0;
 
     // candidates and encounter lists

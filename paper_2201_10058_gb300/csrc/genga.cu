@@ -203,7 +203,7 @@ void free_all(genga_system *s) {
         dfree(s->csr[l].lpair); dfree(s->csr[l].term);
         dfree(s->bodies[l]);
     }
-    dfree(s->kick_part); dfree(s->ksym_list); dfree(s->ksym_ctr); dfree(s->ksym_irc); dfree(s->ksym_mhl); dfree(s->ksym_thrpc);
+    dfree(s->kick_part); dfree(s->ksym_list); dfree(s->ksym_ctr); dfree(s->ksym_irc); dfree(s->ksym_mhl); dfree(s->ksym_thrpc); dfree(s->ksym_pcf); dfree(s->ksym_ircf);
     s->kick_part_cap = 0; s->ksym_list_cap = 0; s->ksym_body_cap = 0; s->ksym_n = -1;
     dfree(s->cand); dfree(s->flags); dfree(s->parent); dfree(s->label);
     dfree(s->gsize); dfree(s->goff); dfree(s->gfill); dfree(s->glist); dfree(s->member);

@@ -74,6 +74,72 @@ __device__ __forceinline__ double inv_rc(double rc) {
     return rc > 0.0 ? 1.0 / rc : __longlong_as_double(0x7ff0000000000000ll);
 }
 
+// Float-float helpers of the mixed symmetric kick's changeover band.
+__device__ __forceinline__ void ff_fast2sum(float &h, float &l) {      // |h| >= |l|
+    const float s = h + l;
+    l = l - (s - h);
+    h = s;
+}
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (ah, al) *= (bh, bl)
+__device__ __forceinline__ void ff_mul(float &ah, float &al, float bh, float bl) {
+    const float ph = ah * bh;
+    float pl = fmaf(ah, bh, -ph);
+    pl = fmaf(ah, bl, pl);
+    pl = fmaf(al, bh, pl);
+    ah = ph;
+    al = pl;
+    ff_fast2sum(ah, al);
+}
+
+// The changeover function K of Sec. 6.3 (y = (r/rc - 0.1)/0.9 clamped to
+// [0, 1], K = y^2 / (y^2 + (1 - y)^2)) in float-float, from what the mixed kick
+// already holds: r = r^2 r^-1 with r^2 = Rh + Rl, Rh y0 = u + ue exactly and
+// r^-1 = y0 (1 + e/2 + 3e^2/8) for the residual e, and 1/rc_ij as two floats.
+// Absolute error of K ~2^-44 (the FP64 form's to rounding), on the FP32 pipe:
+// the band's pairs are few and scattered, and the FP64 pipe would charge each
+// one's whole warp.
+__device__ __forceinline__ void changeover_ff(float u, float ue, float Rl, float y0f, float ef, float ih, float il,
+                                              float &Kh, float &Kl) {
+    // 0.1 and 1/0.9 (the doubles of the FP64 form) as float pairs
+    constexpr float c01h = 0.100000001490116119384765625f, c01l = -1.4901161415892261e-09f;
+    constexpr float c9h = 1.1111111640930176f, c9l = -5.298190686175985e-08f;
+    float rh = u;
+    float rl = ue + fmaf(Rl, y0f, u * fmaf(0.375f * ef, ef, 0.5f * ef));
+    ff_fast2sum(rh, rl);
+    ff_mul(rh, rl, ih, il);                                       // r / rc
+    float dh, dl;
+    ff_two_sum(rh, -c01h, dh, dl);
+    dl += rl - c01l;
+    ff_fast2sum(dh, dl);
+    ff_mul(dh, dl, c9h, c9l);                                     // y
+    if (dh <= 0.0f) { Kh = 0.0f; Kl = 0.0f; return; }
+    if (dh >= 1.0f) { Kh = 1.0f; Kl = 0.0f; return; }
+    float ah = dh, al = dl;
+    ff_mul(ah, al, dh, dl);                                       // y^2
+    float wh, wl;
+    ff_two_sum(1.0f, -dh, wh, wl);
+    wl -= dl;
+    ff_fast2sum(wh, wl);
+    ff_mul(wh, wl, wh, wl);                                       // (1 - y)^2
+    float Dh, Dl;
+    ff_two_sum(ah, wh, Dh, Dl);
+    Dl += al + wl;
+    ff_fast2sum(Dh, Dl);                                          // D in [1/2, 1]
+    float qh = ah / Dh;
+    const float ph = qh * Dh;
+    float pl = fmaf(qh, Dh, -ph);
+    pl = fmaf(qh, Dl, pl);
+    float ql = (((ah - ph) - pl) + al) / Dh;
+    ff_fast2sum(qh, ql);
+    Kh = qh;
+    Kl = ql;
+}
+
 // TP: semi-active test particles (Sec. 8.1): a test particle i takes only the
 // sources j < nm; the block that holds the boundary masks the test-particle
 // pairs, the blocks past it shorten their source range.
@@ -398,6 +464,7 @@ constexpr int kSymMaxP = 6;
 struct SymArgs {
     const double *x, *y, *z, *m;
     const double *irc;          // 1 / rc per body (inv_rc)
+    const float2 *ircf;         // MIXED: the same as two floats
     const float *thr;           // FP32 upper bound of rc^2
     const float2 *mhl;          // MIXED: mass as an unevaluated sum of two floats
     int n, nT, P, nItems;
@@ -407,6 +474,7 @@ struct SymArgs {
     // fused pre-check (PC): candidates i < j with r^2 < max(pc2_i, pc2_j)
     const double *pc2;          // (f_pc rc)^2
     const float *thr_pc;        // FP32 upper bound of pc2 (2^-16 margin)
+    const float2 *pcf;          // pc2 as an unevaluated sum of two floats
     uint2 *cand;
     unsigned long long *cand_count;
     unsigned long long cand_cap;
@@ -429,13 +497,18 @@ constexpr size_t sym_smem(bool mixed, int P) {
 __device__ __forceinline__ double pad_pos(int k) { return 1.0e15 + 1.0e13 * (double)k; }
 
 __global__ void kick_pack_kernel(const double *m, const double *rc, const double *pc2, int n, double *irc,
-                                 float2 *mhl, float *thr_pc) {
+                                 float2 *ircf, float2 *mhl, float *thr_pc, float2 *pcf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    irc[i] = inv_rc(rc[i]);
+    const double ir = inv_rc(rc[i]);
+    irc[i] = ir;
+    const float irh = __double2float_rn(ir);
+    ircf[i] = make_float2(irh, isinf(irh) ? 0.0f : __double2float_rn(ir - (double)irh));
     // rounded up, then 2^-16 more: any float r^2 within 2^-23 of an r^2 below
     // pc2 is below it
     thr_pc[i] = fmaxf(__double2float_ru(pc2[i]) * 1.0000153f, 1.17549435e-38f);
+    const float ph = __double2float_rn(pc2[i]);
+    pcf[i] = make_float2(ph, __double2float_rn(pc2[i] - (double)ph));
     const float mh = __double2float_rn(m[i]);
     mhl[i] = make_float2(mh, __double2float_rn(m[i] - (double)mh));
 }
@@ -456,14 +529,27 @@ __device__ __forceinline__ void sym_pc_flush(const SymArgs &A, const uint2 *buf,
     cnt = 0;
 }
 
-// One pair's pre-check inside the kick (warp-uniform call): lanes with
-// `maybe` take the exact test; the warp appends its candidates (i < j) to its
+// One pair's pre-check inside the kick (warp-uniform call).  Lanes with
+// `maybe` decide r^2 < max(pc2_i, pc2_j) from the kick's float r^2 (Rh + Rl,
+// within rel of r^2) against that pc2 as two floats (pc2 = h + l; rounding to
+// nearest is monotone, so the larger pair of floats is the larger pc2): outside
+// a band of width `band` around it the sign of (Rh - h) + (Rl - l) decides, on
+// the FP32 pipe; inside it (never met in practice) the exact FP64 test of
+// precheck_kernel does.  The warp appends its candidates (i < j) to its
 // buffer, flushed when it could overflow on the next step.
 __device__ __forceinline__ void sym_precheck(const SymArgs &A, uint2 *buf, int &pend, int lane, bool maybe,
-                                             int i, int j, double dx, double dy, double dz) {
+                                             int i, int j, double dx, double dy, double dz, float Rh, float Rl,
+                                             float2 pci, float2 pcj, float band) {
     if (!__any_sync(0xffffffffu, maybe)) return;
     bool emit = false;
-    if (maybe && i < A.n && j < A.n) emit = dist2_rn(dx, dy, dz) < fmax(A.pc2[i], A.pc2[j]);
+    if (maybe && i < A.n && j < A.n) {
+        const float2 P = (pci.x > pcj.x || (pci.x == pcj.x && pci.y >= pcj.y)) ? pci : pcj;
+        const float D = (Rh - P.x) + (Rl - P.y);
+        const float w = band * P.x;
+        if (D < -w) emit = true;
+        else if (D > w) emit = false;
+        else emit = dist2_rn(dx, dy, dz) < fmax(A.pc2[i], A.pc2[j]);
+    }
     const unsigned ball = __ballot_sync(0xffffffffu, emit);
     if (emit) buf[pend + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)min(i, j), (unsigned)max(i, j));
     pend += __popc(ball);
@@ -481,6 +567,7 @@ kick_sym_kernel(SymArgs A)
     extern __shared__ __align__(16) unsigned char sym_sh[];
     double *sx = reinterpret_cast<double *>(sym_sh);
     double *sy = sx + kSymT, *sz = sy + kSymT, *sm = sz + kSymT, *sirc = sm + kSymT;
+    float2 *sircf = reinterpret_cast<float2 *>(sirc);     // MIXED: 1/rc as two floats
     float *sthr = reinterpret_cast<float *>(sirc + kSymT);
     float *smh = sthr + kSymT, *sml = smh + kSymT;
     const int PT = A.P * kSymT;
@@ -489,6 +576,7 @@ kick_sym_kernel(SymArgs A)
     float *jc = reinterpret_cast<float *>(jaz + PT);      // [6][PT]: x hi, x lo, y hi, y lo, z hi, z lo
     __shared__ int s_item;
     __shared__ float sthp[PC ? kSymT : 1];                // thr_pc of the j tile
+    __shared__ float2 spcf[PC ? kSymT : 1];               // pc2 of the j tile as two floats
     __shared__ uint2 pcb[PC ? kSymT / 32 : 1][PC ? kSymPcBuf : 1];
     int pend = 0;                                         // candidates in this warp's buffer
 
@@ -516,10 +604,14 @@ kick_sym_kernel(SymArgs A)
             const bool valid = i < n;
             double xi, yi, zi, mi = 0.0, irci = 0.0;
             float thri = 0.0f, mhi = 0.0f, mli = 0.0f, thpi = 0.0f;
+            float2 pcfi = make_float2(0.0f, 0.0f);
+            float2 ircfi = make_float2(0.0f, 0.0f);
             if (valid) {
                 xi = A.x[i]; yi = A.y[i]; zi = A.z[i]; mi = A.m[i];
-                irci = A.irc[i]; thri = A.thr[i];
-                if (PC) thpi = A.thr_pc[i];
+                thri = A.thr[i];
+                if (MIXED) ircfi = A.ircf[i];
+                else irci = A.irc[i];
+                if (PC) { thpi = A.thr_pc[i]; pcfi = A.pcf[i]; }
                 if (MIXED) { const float2 q = A.mhl[i]; mhi = q.x; mli = q.y; }
             } else {
                 xi = yi = zi = pad_pos(threadIdx.x);
@@ -533,13 +625,17 @@ kick_sym_kernel(SymArgs A)
                     const int k = threadIdx.x, j = b * kSymT + k;
                     if (j < n) {
                         sx[k] = A.x[j]; sy[k] = A.y[j]; sz[k] = A.z[j]; sm[k] = A.m[j];
-                        sirc[k] = A.irc[j]; sthr[k] = A.thr[j];
+                        if (MIXED) sircf[k] = A.ircf[j];
+                        else sirc[k] = A.irc[j];
+                        sthr[k] = A.thr[j];
                         if (MIXED) { const float2 q = A.mhl[j]; smh[k] = q.x; sml[k] = q.y; }
-                        if (PC) sthp[k] = A.thr_pc[j];
+                        if (PC) { sthp[k] = A.thr_pc[j]; spcf[k] = A.pcf[j]; }
                     } else {
                         sx[k] = sy[k] = sz[k] = pad_pos(k); sm[k] = 0.0;
-                        sirc[k] = 0.0; sthr[k] = 0.0f; smh[k] = 0.0f; sml[k] = 0.0f;
-                        if (PC) sthp[k] = 0.0f;
+                        if (MIXED) sircf[k] = make_float2(0.0f, 0.0f);
+                        else sirc[k] = 0.0;
+                        sthr[k] = 0.0f; smh[k] = 0.0f; sml[k] = 0.0f;
+                        if (PC) { sthp[k] = 0.0f; spcf[k] = make_float2(0.0f, 0.0f); }
                     }
                 }
                 __syncthreads();
@@ -576,20 +672,9 @@ kick_sym_kernel(SymArgs A)
                                 const float Rh = s2 + tail;
                                 const float Rl = tail - (Rh - s2);
                                 if (PC) sym_precheck(A, pcb[w], pend, lane, !half && Rh < fmaxf(thpi, sthp[k]), i,
-                                                     b * kSymT + k, dx, dy, dz);
-                                float mhj = smh[k], mlj = sml[k], mhI = mhi, mlI = mli;
-                                // changeover band (rare): K from r by the Newton rsqrt and
-                                // 1/rc_ij = min(1/rc_i, 1/rc_j); both masses scaled by K
-                                if (Rh < fmaxf(thri, sthr[k])) {
-                                    const double r2d = fma(dz, dz, fma(dy, dy, dx * dx));
-                                    const double K = changeover_fast(r2d * rsqrt_newton(r2d), fmin(irci, sirc[k]));
-                                    const double mkj = sm[k] * K, mki = mi * K;
-                                    mhj = __double2float_rn(mkj);
-                                    mlj = __double2float_rn(mkj - (double)mhj);
-                                    mhI = __double2float_rn(mki);
-                                    mlI = __double2float_rn(mki - (double)mhI);
-                                }
-                                if (half) { mhj = 0.0f; mlj = 0.0f; mhI = 0.0f; mlI = 0.0f; }
+                                                     b * kSymT + k, dx, dy, dz, Rh, Rl, pcfi, spcf[k],
+                                                     9.094947e-13f);          // 2^-40
+
                                 // r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) as in kick_kernel; the
                                 // mass-free parts are shared by the two sides
                                 const float y0f = rsqrtf(Rh);
@@ -600,6 +685,19 @@ kick_sym_kernel(SymArgs A)
                                 float qe = fmaf(p, y0f, -qq);
                                 qe = fmaf(pe, y0f, qe);
                                 const float ef = r1 - fmaf(ue, y0f, Rl * p);
+                                float mhj = smh[k], mlj = sml[k], mhI = mhi, mlI = mli;
+                                // changeover band (rare): K in float-float from r = r^2 r^-1,
+                                // 1/rc_ij = min(1/rc_i, 1/rc_j) (as float pairs: rounding is
+                                // monotone), both masses scaled by K -- no FP64 work
+                                if (Rh < fmaxf(thri, sthr[k])) {
+                                    const float2 cj = sircf[k];
+                                    const bool ci = ircfi.x < cj.x || (ircfi.x == cj.x && ircfi.y <= cj.y);
+                                    float Kh, Kl;
+                                    changeover_ff(u, ue, Rl, y0f, ef, ci ? ircfi.x : cj.x, ci ? ircfi.y : cj.y, Kh, Kl);
+                                    ff_mul(mhj, mlj, Kh, Kl);
+                                    ff_mul(mhI, mlI, Kh, Kl);
+                                }
+                                if (half) { mhj = 0.0f; mlj = 0.0f; mhI = 0.0f; mlI = 0.0f; }
                                 const float poly = fmaf(1.875f * ef, ef, 1.5f * ef);
                                 // i side: m_j r^-3 dx
                                 {
@@ -635,7 +733,9 @@ kick_sym_kernel(SymArgs A)
                                 const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
                                 const float r2f = r2_to_float_trunc(r2);
                                 if (PC) sym_precheck(A, pcb[w], pend, lane, !half && r2f < fmaxf(thpi, sthp[k]), i,
-                                                     b * kSymT + k, dx, dy, dz);
+                                                     b * kSymT + k, dx, dy, dz, r2f, 0.0f, pcfi, spcf[k],
+                                                     9.536743e-07f);          // 2^-20
+
                                 const double yv = rsqrt_newton(r2);
                                 double y3 = (yv * yv) * yv;
                                 if (r2f < fmaxf(thri, sthr[k]))
@@ -888,10 +988,16 @@ cudaError_t kick_reserve(genga_system *s) {
                 if (s->ksym_irc) cudaFree(s->ksym_irc);
                 if (s->ksym_mhl) cudaFree(s->ksym_mhl);
                 if (s->ksym_thrpc) cudaFree(s->ksym_thrpc);
-                s->ksym_irc = nullptr; s->ksym_mhl = nullptr; s->ksym_thrpc = nullptr; s->ksym_body_cap = 0;
+                if (s->ksym_pcf) cudaFree(s->ksym_pcf);
+                if (s->ksym_ircf) cudaFree(s->ksym_ircf);
+                s->ksym_irc = nullptr; s->ksym_mhl = nullptr; s->ksym_thrpc = nullptr; s->ksym_pcf = nullptr;
+                s->ksym_ircf = nullptr;
+                s->ksym_body_cap = 0;
                 GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_irc, sizeof(double) * (size_t)n));
                 GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_mhl, sizeof(float2) * (size_t)n));
                 GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_thrpc, sizeof(float) * (size_t)n));
+                GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_pcf, sizeof(float2) * (size_t)n));
+                GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_ircf, sizeof(float2) * (size_t)n));
                 s->ksym_body_cap = (size_t)n;
             }
         }
@@ -918,17 +1024,18 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
     if (A.nm >= n && s->ksym_P > 0) {
         // symmetric layout; the pre-check, if asked for, rides along
         kick_pack_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(s->mass, s->rcl[0].rc, s->rcl[0].pc2, n,
-                                                               s->ksym_irc, s->ksym_mhl, s->ksym_thrpc);
+                                                               s->ksym_irc, s->ksym_ircf, s->ksym_mhl,
+                                                               s->ksym_thrpc, s->ksym_pcf);
         ++s->launches;
         GENGA_CUDA_TRY(cudaMemsetAsync(s->ksym_ctr, 0, sizeof(unsigned), s->stream));
         if (precheck)
             GENGA_CUDA_TRY(cudaMemsetAsync(&s->ctr->cand_count, 0, sizeof(unsigned long long), s->stream));
         SymArgs S;
         S.x = A.x; S.y = A.y; S.z = A.z; S.m = A.m;
-        S.irc = s->ksym_irc; S.thr = A.thr_rc; S.mhl = s->ksym_mhl;
+        S.irc = s->ksym_irc; S.ircf = s->ksym_ircf; S.thr = A.thr_rc; S.mhl = s->ksym_mhl;
         S.n = n; S.nT = (n + kSymT - 1) / kSymT; S.P = s->ksym_P; S.nItems = s->ksym_items;
         S.items = s->ksym_list; S.ctr = s->ksym_ctr; S.part = s->kick_part;
-        S.pc2 = s->rcl[0].pc2; S.thr_pc = s->ksym_thrpc;
+        S.pc2 = s->rcl[0].pc2; S.thr_pc = s->ksym_thrpc; S.pcf = s->ksym_pcf;
         S.cand = s->cand; S.cand_count = &s->ctr->cand_count; S.cand_cap = (unsigned long long)s->cand_cap;
         const size_t smem = sym_smem(mixed, s->ksym_P);
         const unsigned nb = (unsigned)s->ksym_blocks;
