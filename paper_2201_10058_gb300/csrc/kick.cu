@@ -1,30 +1,36 @@
 // kick.cu -- all-pairs changeover kick of Eq. Hb (Appendix A "Kick(dt/2)"):
 //   a_i = G sum_{j != i} m_j K(r_ij; rc_ij) (x_j - x_i) / r_ij^3
-// and the close-encounter pre-check (Appendix A) as a separate FP32 pass.
+// and the close-encounter pre-check (Appendix A).
 //
 // GB300 design.  The kick is bound by the FP64 pipe (1.68 FP64 instructions per
-// clock per SM on GB300, measured, 1/74 of FP32), so the kernel minimises FP64 instructions per
-// pair and keeps everything else on the FP32, MUFU and integer pipes:
-//   * j bodies are staged in shared memory in tiles of 256 (x, y, z, m and the
-//     per-body thresholds); every thread owns one target i;
-//   * the grid is (i-tiles x j-chunks) so that thousands of equal blocks
-//     balance across the 152 SMs; each block writes compensated partial sums
-//     for its chunk, folded in a fixed order by kick_finalize (deterministic);
-//   * the rare pairs inside rc_ij are found by an FP32 test on r^2 against a
-//     conservative threshold; only those evaluate the changeover function;
-//   * the pre-check runs over the pairs i < j on the FP32 pipe alone
-//     (precheck_kernel below), so the FP64-bound kick carries none of it;
-//   * MIXED: FP64 displacement; r^2 formed as an unevaluated sum of two floats
-//     from an exact integer split of the displacement (no FP64 work); FP32
-//     rsqrt seed y0; one Newton correction from the residual e = 1 - r^2 y0^2
-//     (its leading part 1 - u y0 by an FP32 FMA on the exact float product
-//     u y0, rounded once: the float a double residual would be rounded to;
-//     the tails in FP32); r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) = m y0^3 + corr
-//     in float-float; FP64 accumulation of (m y0^3) dx, the corrections
-//     corr dx (< 2^-19 of each term) summed in float-float per tile and added
-//     to the FP64 sums once per tile; per-tile sums folded with TwoSum:
-//     6 FP64 instructions per pair (3 subtractions, 3 accumulations).
-//     FP64: CUDA's double rsqrt, 17 FP64 instructions per pair (counted).
+// clock per SM on GB300, measured, 1/74 of FP32), so the kernels minimise FP64
+// instructions per interaction and keep everything else on the FP32, MUFU and
+// integer pipes.  Two layouts:
+//   * symmetric (kick_sym_kernel, below): each unordered pair once, its force to
+//     both bodies (Newton's third law) -- 9 FP64 instructions per pair in the
+//     mixed form, 4.5 per interaction; the pre-check rides along on the FP32
+//     pipe.  Used where it is predicted faster (N of ~8k and more);
+//   * tiled (kick_kernel): every ordered pair, one target per thread against
+//     source tiles in shared memory, an (i-tile x j-chunk) grid of equal blocks;
+//     for small N, test particles and the allocation-free entry point, with the
+//     pre-check as its own FP32 pass over i < j (precheck_kernel).
+// Both write compensated partial sums folded in a fixed order by kick_finalize
+// (deterministic).  The rare pairs inside rc_ij are found by an FP32 test on
+// r^2 against a conservative threshold; only those evaluate the changeover
+// function.
+//
+// MIXED: FP64 displacement; r^2 formed as an unevaluated sum of two floats from
+// an exact integer split of the displacement (no FP64 work); FP32 rsqrt seed
+// y0; one Newton correction from the residual e = 1 - r^2 y0^2 (its leading
+// part 1 - u y0 by an FP32 FMA on the exact float product u y0, rounded once:
+// the float a double residual would be rounded to; the tails in FP32);
+// r^-3 = y0^3 (1 + 1.5 e + 1.875 e^2) = m y0^3 + corr in float-float; FP64
+// accumulation of (m y0^3) dx, the corrections corr dx (< 2^-19 of each term)
+// summed in float-float and added to the FP64 sums with the partials; 6 FP64
+// instructions per ordered pair in the tiled layout (3 subtractions, 3
+// accumulations).  FP64: CUDA's double rsqrt in the tiled layout (17 FP64
+// instructions per pair, counted), the Newton rsqrt of common.cuh in the
+// symmetric one (21 per unordered pair).
 #include <algorithm>
 #include <queue>
 #include <utility>
@@ -74,7 +80,13 @@ __device__ __forceinline__ double inv_rc(double rc) {
     return rc > 0.0 ? 1.0 / rc : __longlong_as_double(0x7ff0000000000000ll);
 }
 
-// Float-float helpers of the mixed symmetric kick's changeover band.
+// 1/rc as two floats (an infinite 1/rc keeps a zero low part).
+__device__ __forceinline__ float2 ff_of_irc(double ir) {
+    const float h = __double2float_rn(ir);
+    return make_float2(h, isinf(h) ? 0.0f : __double2float_rn(ir - (double)h));
+}
+
+// Float-float helpers of the mixed kicks' changeover band.
 __device__ __forceinline__ void ff_fast2sum(float &h, float &l) {      // |h| >= |l|
     const float s = h + l;
     l = l - (s - h);
@@ -149,6 +161,7 @@ kick_kernel(KickArgs A)
 {
     __shared__ double sx[kTile], sy[kTile], sz[kTile], sm[kTile];
     __shared__ double sirc[kTile];            // 1 / rc_j
+    __shared__ float2 sircf[MIXED ? kTile : 1]; // MIXED: 1 / rc_j as two floats
     __shared__ float sthr[kTile], smh[kTile], sml[kTile];
 
     const int n = A.n;
@@ -158,10 +171,12 @@ kick_kernel(KickArgs A)
     double xi = 1e15, yi = 1e15, zi = 1e15;
     double irci = 0.0;                        // 1 / rc_i (infinite for rc_i = 0)
     float thri = 0.0f;
+    float2 ircfi = make_float2(0.0f, 0.0f);
     if (valid) {
         xi = A.x[i]; yi = A.y[i]; zi = A.z[i];
         thri = A.thr_rc[i];
         irci = inv_rc(A.rc[i]);
+        if (MIXED) ircfi = ff_of_irc(irci);
     }
 
     const int jbeg = blockIdx.y * A.chunk;
@@ -181,6 +196,7 @@ kick_kernel(KickArgs A)
             sx[k] = A.x[j]; sy[k] = A.y[j]; sz[k] = A.z[j]; sm[k] = A.m[j];
             sthr[k] = A.thr_rc[j];
             sirc[k] = inv_rc(A.rc[j]);
+            if (MIXED) sircf[k] = ff_of_irc(sirc[k]);
             if (MIXED) {     // mass as an unevaluated sum of two floats
                 const float mh = __double2float_rn(A.m[j]);
                 smh[k] = mh;
@@ -236,22 +252,17 @@ kick_kernel(KickArgs A)
             // Changeover band (rare): K < 1 needs r < rc_ij.  K is flat (zero slope) at
             // r = rc, so the branch may follow the FP32 bound and K uses the r^2 above.
             // The branch runs on few lanes of a warp while the FP64 pipe charges the
-            // whole warp, so it keeps to short FP64 forms: r from the Newton rsqrt,
-            // K with 1/rc_ij = min(1/rc_i, 1/rc_j) staged beforehand (no division).
-            if (r2f < fmaxf(thri, sthr[k])) {
-                if (j == i) {
-                    mk = 0.0; r2 = 1.0; r2f = 1.0f;          // self term: zero, finite
-                    Rh = 1.0f; Rl = 0.0f;
-                    mh = 0.0f; ml = 0.0f;
-                } else {
-                    const double r2d = MIXED ? fma(dz, dz, fma(dy, dy, dx * dx)) : r2;
-                    mk = mk * changeover_fast(r2d * rsqrt_newton(r2d), fmin(irci, sirc[k]));
-                    if (MIXED) {
-                        mh = __double2float_rn(mk);
-                        ml = __double2float_rn(mk - (double)mh);
-                    }
-                }
+            // whole warp: the FP64 form takes r from the Newton rsqrt and
+            // 1/rc_ij = min(1/rc_i, 1/rc_j) staged beforehand (no division); MIXED
+            // evaluates K in float-float on the FP32 pipe (below).
+            const bool band = r2f < fmaxf(thri, sthr[k]);
+            if (band && j == i) {
+                mk = 0.0; r2 = 1.0; r2f = 1.0f;              // self term: zero, finite
+                Rh = 1.0f; Rl = 0.0f;
+                mh = 0.0f; ml = 0.0f;
             }
+            if (!MIXED && band && j != i)
+                mk = mk * changeover_fast(r2 * rsqrt_newton(r2), fmin(irci, sirc[k]));
             {
                 double s;
                 if (MIXED) {
@@ -270,11 +281,18 @@ kick_kernel(KickArgs A)
                     const float q = p * y0f;
                     float qe = fmaf(p, y0f, -q);
                     qe = fmaf(pe, y0f, qe);
+                    const float ef = e1 - fmaf(ue, y0f, Rl * p);
+                    if (band && j != i) {      // K in float-float, the mass scaled by it
+                        const float2 cj = sircf[k];
+                        const bool ci = ircfi.x < cj.x || (ircfi.x == cj.x && ircfi.y <= cj.y);
+                        float Kh, Kl;
+                        changeover_ff(u, ue, Rl, y0f, ef, ci ? ircfi.x : cj.x, ci ? ircfi.y : cj.y, Kh, Kl);
+                        ff_mul(mh, ml, Kh, Kl);
+                    }
                     const float ch = q * mh;
                     float ce = fmaf(q, mh, -ch);
                     ce = fmaf(q, ml, ce);
                     ce = fmaf(qe, mh, ce);
-                    const float ef = e1 - fmaf(ue, y0f, Rl * p);
                     const float corr = fmaf(ch, fmaf(1.875f * ef, ef, 1.5f * ef), ce);
                     s = f64_of_f32_any(ch);
                     float_two_sum_acc(cxh, cxl, corr * hx);
@@ -502,8 +520,7 @@ __global__ void kick_pack_kernel(const double *m, const double *rc, const double
     if (i >= n) return;
     const double ir = inv_rc(rc[i]);
     irc[i] = ir;
-    const float irh = __double2float_rn(ir);
-    ircf[i] = make_float2(irh, isinf(irh) ? 0.0f : __double2float_rn(ir - (double)irh));
+    ircf[i] = ff_of_irc(ir);
     // rounded up, then 2^-16 more: any float r^2 within 2^-23 of an r^2 below
     // pc2 is below it
     thr_pc[i] = fmaxf(__double2float_ru(pc2[i]) * 1.0000153f, 1.17549435e-38f);
