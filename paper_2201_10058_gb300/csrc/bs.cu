@@ -47,17 +47,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // KickS at level l >= 1 over the level-(l-1) encounter pairs:
 //   v_b += dt_half G sum_p m_p prod_{k<l}(1 - K_k) K_l (x_p - x_b)/r^3.
-// Phase 1, one thread per undirected pair (i < j): g (x_j - x_i) with
-// g = prod_{k<l}(1 - K_k) K_l / r^3 (0 when the pair is beyond rc_0, where
-// 1 - K_0 = 0).  Phase 2, one thread per level body: the pair terms of its
-// partners, ascending partner index, times +-m_p -- a fixed summation order.
+// Phase 1, one thread per undirected pair (i < j): g = prod_{k<l}(1 - K_k) K_l / r^3
+// (0 when the pair is beyond rc_0, where 1 - K_0 = 0) and the pair's two
+// mass-weighted terms m_j g (x_j - x_i) (for i) and -m_i g (x_j - x_i) (for j),
+// each a 32-byte record so that phase 2 gathers one sector per partner.
+// Phase 2, one body per kApplyLanes lanes: the records of its partners in
+// ascending partner order per lane, lanes combined in a fixed butterfly -- a
+// fixed summation order.
 struct KickPairsArgs {
     int n, nb, level;
     long long np;
     const uint2 *pairs;
     const int *bodies;
     const int *off, *list, *lpair;
-    double *term;          // [3][np]
+    double4_32a *term;     // [np][2]: the terms for i and for j
     const double *pos;
     double *vel;
     const double *mass;
@@ -72,7 +75,6 @@ __global__ void kick_pairs_terms_kernel(KickPairsArgs A) {
     const uint2 pr = A.pairs[k];
     const int i = (int)pr.x, j = (int)pr.y;
     const size_t N = (size_t)A.n;
-    const size_t NP = (size_t)A.np;
     const double dx = A.pos[j] - A.pos[i], dy = A.pos[N + j] - A.pos[N + i],
                  dz = A.pos[2 * N + j] - A.pos[2 * N + i];
     const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
@@ -88,22 +90,17 @@ __global__ void kick_pairs_terms_kernel(KickPairsArgs A) {
         W *= changeover_fast(r, fmin(A.irc[A.level][i], A.irc[A.level][j]));
         g = W * yv * yv * yv;
     }
-    A.term[k] = g * dx;
-    A.term[NP + k] = g * dy;
-    A.term[2 * NP + k] = g * dz;
+    const double ci = A.mass[j] * g, cj = -A.mass[i] * g;
+    A.term[2 * k] = make_double4_32a(ci * dx, ci * dy, ci * dz, 0.0);
+    A.term[2 * k + 1] = make_double4_32a(cj * dx, cj * dy, cj * dz, 0.0);
 }
 
-// Phase 2 runs kApplyLanes lanes per body: lane s takes the partners
-// s, s + kApplyLanes, ... of the body's ascending list, and the lane sums meet
-// in a fixed butterfly -- a fixed summation order with the gathers of eight
-// partners in flight at once.
 constexpr int kApplyLanes = 8;
 
 __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = gt / kApplyLanes, sub = gt % kApplyLanes;
     const size_t N = (size_t)A.n;
-    const size_t NP = (size_t)A.np;
     int b = 0, q0 = 0, q1 = 0;
     if (t < A.nb) {
         b = A.bodies[t];
@@ -113,11 +110,10 @@ __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
     double sx = 0.0, sy = 0.0, sz = 0.0;
     for (int q = q0 + sub; q < q1; q += kApplyLanes) {
         const int p = A.list[q];
-        const int k = A.lpair[q];
-        const double w = (p > b) ? A.mass[p] : -A.mass[p];
-        sx = fma(w, A.term[k], sx);
-        sy = fma(w, A.term[NP + k], sy);
-        sz = fma(w, A.term[2 * NP + k], sz);
+        const double4_32a w = A.term[2 * (long long)A.lpair[q] + (p > b ? 0 : 1)];
+        sx += w.x;
+        sy += w.y;
+        sz += w.z;
     }
 #pragma unroll
     for (int o = kApplyLanes / 2; o > 0; o >>= 1) {
@@ -596,7 +592,7 @@ cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb
     A.pairs = s->pairs[level - 1];
     A.bodies = s->bodies[level];
     A.off = s->csr[level - 1].off; A.list = s->csr[level - 1].list; A.lpair = s->csr[level - 1].lpair;
-    A.term = s->csr[level - 1].term;
+    A.term = reinterpret_cast<double4_32a *>(s->csr[level - 1].term);
     A.pos = s->pos; A.vel = s->vel; A.mass = s->mass;
     for (int l = 0; l < kMaxLevels; l++) A.irc[l] = s->rcl[l].irc;
     A.rc2_0 = s->rcl[0].rc2;

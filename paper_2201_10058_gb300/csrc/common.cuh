@@ -55,7 +55,7 @@ struct DevCounters {
     unsigned int err;
     unsigned int ngroups;
     unsigned int max_group;
-    unsigned int pad;
+    unsigned int hc_done;                  // blocks of hc_reduce_kernel finished (reset by the last)
     double hc_shift[3];
     unsigned int bucket_count[kBuckets];   // groups per size bucket (bucket_groups)
     unsigned int pad2[8 - kBuckets];
@@ -92,7 +92,7 @@ struct Csr {
     int *fill = nullptr;   // n
     int *list = nullptr;   // 2 * cap: partner of each entry
     int *lpair = nullptr;  // 2 * cap: index of the entry's pair in the pair list
-    double *term = nullptr;  // 3 * cap: per-pair kick terms (KickS)
+    double *term = nullptr;  // 8 * cap: per pair two mass-weighted KickS terms (x, y, z, pad)
     int64_t cap = 0;       // pairs
 };
 

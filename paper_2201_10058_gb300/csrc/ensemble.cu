@@ -59,17 +59,53 @@ struct EnsShared {
     // mixed kick: masses as two floats, FP32 bounds of rc^2 (above) and of
     // (f_pc rc)^2 (below and above)
     float mh[kEnsMaxN], ml[kEnsMaxN], thr[kEnsMaxN], pclo[kEnsMaxN], pchi[kEnsMaxN];
-    double u0[3][kEnsMaxN], u1[3][kEnsMaxN], w0[3][kEnsMaxN], nsum[3][kEnsMaxN];
+    double u0[3][kEnsMaxN], u1[3][kEnsMaxN], w0[3][kEnsMaxN];
     double part[3][128];
     unsigned long long cand[kEnsMaxN], enc[kEnsMaxN];
     int parent[kEnsMaxN], slot[kEnsMaxN], mem[kEnsMaxN];
     int roots[kEnsMaxN];
-    double ws0[3], ws1[3], wsm[3], P[3], shift[3], Mp;
+    double ws0[3], ws1[3], wsm[3];
     double star_R, star_k2, star_tau, star_rg2, mstar, dt;
     int n, nroots, flag, sys;
     double bs_t, bs_H, bs_err;
     int bs_stop, bs_kconv;
+    // per-body constants of the loaded system: cbrt(m/(3 m_star)) of Rcrit,
+    // 1/m, eta = m_star m/(m_star + m)^2, mu = G(m_star + m), m_star/(m_star + m),
+    // the moment of inertia rg^2 m R^2 and the tidal prefactors 3 G m_star^2 k2 R^5
+    // (planet) and 3 G m^2 k2_star R_star^5 (star)
+    double hf[kEnsMaxN], im[kEnsMaxN], eta[kEnsMaxN], mu[kEnsMaxN], fac[kEnsMaxN], Ii[kEnsMaxN];
+    double tdi[kEnsMaxN], tds[kEnsMaxN];
+    double red[4][kEnsMaxN / 32];       // per-warp partial sums of ens_bsum
 };
+
+// Sums over the loaded system's bodies of K per-body values (thread t < n
+// holds body t's), in a fixed order: a butterfly within each warp, then the
+// warps in order.  Every thread receives the sums.  Called by all threads.
+template <int K>
+__device__ __forceinline__ void ens_bsum(EnsShared &S, const double (&v)[K], double (&out)[K]) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int nw = (S.n + 31) >> 5;
+    double a[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = t < S.n ? v[k] : 0.0;
+    if (w < nw) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < K; k++) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < K; k++) S.red[k][w] = a[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double sum = S.red[k][0];
+        for (int q = 1; q < nw; q++) sum += S.red[k][q];
+        out[k] = sum;
+    }
+    __syncthreads();
+}
 
 __device__ __forceinline__ unsigned long long ens_now() {
     unsigned long long t;
@@ -185,43 +221,44 @@ __device__ void ens_kick(const EnsArgs &A, EnsShared &S, double dt_half, bool pr
 }
 
 // ------------------------------------------------------------ GR + tides
+// GR (Eq. apn) and tidal (Sec. 4.1-4.2) acceleration of body i at velocity u
+// (heliocentric) and spin W, with the torques on the body and on the star.
+// Divisions by r are multiplications by 1/r (Newton rsqrt) and the per-body
+// constants come with the system (EnsShared): the FP64 pipe bounds the kernel.
 __device__ void nn_body(const EnsArgs &A, const EnsShared &S, int i, const double u[3],
                         const double W[3], double acc[3], double Ni[3], double Ns[3]) {
     const double x[3] = {S.x[0][i], S.x[1][i], S.x[2][i]};
-    const double mi = S.m[i], m_star = S.mstar, G = A.G;
     const double r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
-    const double r = sqrt(r2);
-    const double er[3] = {x[0] / r, x[1] / r, x[2] / r};
-    const double rdot = ((x[0] * u[0] + x[1] * u[1]) + x[2] * u[2]) / r;
+    const double ir = rsqrt_newton(r2);
+    const double r = r2 * ir;
+    const double er[3] = {x[0] * ir, x[1] * ir, x[2] * ir};
+    const double rdot = ((x[0] * u[0] + x[1] * u[1]) + x[2] * u[2]) * ir;
     const double u2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
     for (int k = 0; k < 3; k++) { acc[k] = 0.0; Ni[k] = 0.0; Ns[k] = 0.0; }
     if (A.gr == 1) {
-        const double mu = G * (m_star + mi);
-        const double eta = m_star * mi / ((m_star + mi) * (m_star + mi));
-        const double pre = -mu / (r2 * A.c2);
+        const double mu = S.mu[i], eta = S.eta[i];
+        const double pre = -mu * (ir * ir) * A.inv_c2;
         const double cv = -2.0 * (2.0 - eta) * rdot;
-        const double cr = (1.0 + 3.0 * eta) * u2 - 1.5 * eta * rdot * rdot - 2.0 * (2.0 + eta) * mu / r;
+        const double cr = (1.0 + 3.0 * eta) * u2 - 1.5 * eta * rdot * rdot - 2.0 * (2.0 + eta) * mu * ir;
         for (int k = 0; k < 3; k++) acc[k] += pre * (cv * u[k] + cr * er[k]);
     }
     if (A.tides) {
-        const double r5 = r2 * r2 * r, r7 = r5 * r2;
-        const double Ri = S.R[i];
-        const double Ri5 = Ri * Ri * Ri * Ri * Ri;
-        const double Rs = S.star_R;
-        const double Rs5 = Rs * Rs * Rs * Rs * Rs;
-        const double Dti = 3.0 * G * m_star * m_star * Ri5 / r7 * S.k2[i];
-        const double Dts = 3.0 * G * mi * mi * Rs5 / r7 * S.star_k2;
+        const double ir2 = ir * ir;
+        const double ir7 = (ir2 * ir2) * (ir2 * ir);
+        const double Dti = S.tdi[i] * ir7;
+        const double Dts = S.tds[i] * ir7;
         const double Pti = Dti * S.tau[i], Pts = Dts * S.star_tau;
-        const double fr = -(Dts + Dti) - 2.0 * rdot / r * (Pts + Pti);
+        const double fr = -(Dts + Dti) - 2.0 * rdot * ir * (Pts + Pti);
         const double *Ws = S.wsm;
         const double wxe[3] = {W[1] * er[2] - W[2] * er[1], W[2] * er[0] - W[0] * er[2], W[0] * er[1] - W[1] * er[0]};
         const double sxe[3] = {Ws[1] * er[2] - Ws[2] * er[1], Ws[2] * er[0] - Ws[0] * er[2], Ws[0] * er[1] - Ws[1] * er[0]};
         const double exu[3] = {er[1] * u[2] - er[2] * u[1], er[2] * u[0] - er[0] * u[2], er[0] * u[1] - er[1] * u[0]};
         const double rW = (x[0] * W[0] + x[1] * W[1]) + x[2] * W[2];
         const double rWs = (x[0] * Ws[0] + x[1] * Ws[1]) + x[2] * Ws[2];
+        const double im = S.im[i], Ptot_ir = (Pti + Pts) * ir;
         for (int k = 0; k < 3; k++) {
-            const double F = fr * er[k] + Pti * wxe[k] + Pts * sxe[k] - (Pti + Pts) * u[k] / r;
-            acc[k] += F / mi;
+            const double F = fr * er[k] + Pti * wxe[k] + Pts * sxe[k] - Ptot_ir * u[k];
+            acc[k] += F * im;
             Ni[k] = Pti * (W[k] * r - rW * er[k] - exu[k]);
             Ns[k] = Pts * (Ws[k] * r - rWs * er[k] - exu[k]);
         }
@@ -231,19 +268,18 @@ __device__ void nn_body(const EnsArgs &A, const EnsShared &S, int i, const doubl
 __device__ void ens_nn(const EnsArgs &A, EnsShared &S, double dt) {
     if (A.gr != 1 && !A.tides) return;
     const int n = S.n, t = threadIdx.x;
-    if (t == 0) {
-        double P0 = 0.0, P1 = 0.0, P2 = 0.0, Mp = 0.0;
-        for (int j = 0; j < n; j++) {
-            P0 += S.m[j] * S.v[0][j]; P1 += S.m[j] * S.v[1][j]; P2 += S.m[j] * S.v[2][j];
-            Mp += S.m[j];
-        }
-        S.P[0] = P0; S.P[1] = P1; S.P[2] = P2; S.Mp = Mp;
-        for (int k = 0; k < 3; k++) S.ws1[k] = S.ws0[k];
+    const int b = t < n ? t : 0;
+    double P[4];
+    {
+        const double mv[4] = {S.m[b] * S.v[0][b], S.m[b] * S.v[1][b], S.m[b] * S.v[2][b], S.m[b]};
+        ens_bsum<4>(S, mv, P);
     }
-    __syncthreads();
+    const double Mp = P[3];
+    if (t == 0)
+        for (int k = 0; k < 3; k++) S.ws1[k] = S.ws0[k];
     if (t < n)
         for (int k = 0; k < 3; k++) {
-            S.u0[k][t] = S.v[k][t] + S.P[k] / S.mstar;
+            S.u0[k][t] = S.v[k][t] + P[k] / S.mstar;
             S.u1[k][t] = S.u0[k][t];
             S.w0[k][t] = S.w[k][t];
         }
@@ -254,6 +290,7 @@ __device__ void ens_nn(const EnsArgs &A, EnsShared &S, double dt) {
             for (int k = 0; k < 3; k++) S.wsm[k] = 0.5 * (S.ws0[k] + S.ws1[k]);
         }
         __syncthreads();
+        double nsv[3] = {0.0, 0.0, 0.0};
         if (t < n) {
             double um[3], Wm[3], acc[3], Ni[3], Ns[3];
             for (int k = 0; k < 3; k++) {
@@ -261,8 +298,8 @@ __device__ void ens_nn(const EnsArgs &A, EnsShared &S, double dt) {
                 Wm[k] = 0.5 * (S.w0[k][t] + S.w[k][t]);
             }
             nn_body(A, S, t, um, Wm, acc, Ni, Ns);
-            const double fac = S.mstar / (S.mstar + S.m[t]);
-            const double Ii = S.rg2[t] * S.m[t] * S.R[t] * S.R[t];
+            const double fac = S.fac[t];
+            const double Ii = S.Ii[t];
             bool changed = false;
             for (int k = 0; k < 3; k++) {
                 const double un = S.u0[k][t] + dt * acc[k];
@@ -273,46 +310,47 @@ __device__ void ens_nn(const EnsArgs &A, EnsShared &S, double dt) {
                     if (fabs(Wn - S.w[k][t]) > 1e-16 * fabs(Wn)) changed = true;
                     S.w[k][t] = Wn;
                 }
-                S.nsum[k][t] = fac * Ns[k];
+                nsv[k] = fac * Ns[k];
             }
             if (changed) S.flag = 1;
         }
-        __syncthreads();
-        if (t == 0 && A.tides && Is > 0.0) {
-            for (int k = 0; k < 3; k++) {
-                double d = 0.0;
-                for (int j = 0; j < n; j++) d += S.nsum[k][j];
-                const double Wn = S.ws0[k] - dt * d / Is;
-                if (fabs(Wn - S.ws1[k]) > 1e-16 * fabs(Wn)) S.flag = 1;
-                S.ws1[k] = Wn;
-            }
+        if (A.tides && Is > 0.0) {
+            double d[3];
+            ens_bsum<3>(S, nsv, d);
+            if (t == 0)
+                for (int k = 0; k < 3; k++) {
+                    const double Wn = S.ws0[k] - dt * d[k] / Is;
+                    if (fabs(Wn - S.ws1[k]) > 1e-16 * fabs(Wn)) S.flag = 1;
+                    S.ws1[k] = Wn;
+                }
         }
         __syncthreads();
         if (!S.flag) break;
         __syncthreads();
     }
-    if (t == 0) {
-        double Q0 = 0.0, Q1 = 0.0, Q2 = 0.0;
-        for (int j = 0; j < n; j++) { Q0 += S.m[j] * S.u1[0][j]; Q1 += S.m[j] * S.u1[1][j]; Q2 += S.m[j] * S.u1[2][j]; }
-        S.P[0] = Q0 / (S.mstar + S.Mp); S.P[1] = Q1 / (S.mstar + S.Mp); S.P[2] = Q2 / (S.mstar + S.Mp);
-        for (int k = 0; k < 3; k++) S.ws0[k] = S.ws1[k];
+    double Q[3];
+    {
+        const double mu1[3] = {S.m[b] * S.u1[0][b], S.m[b] * S.u1[1][b], S.m[b] * S.u1[2][b]};
+        ens_bsum<3>(S, mu1, Q);
     }
-    __syncthreads();
+    if (t == 0)
+        for (int k = 0; k < 3; k++) S.ws0[k] = S.ws1[k];
     if (t < n)
-        for (int k = 0; k < 3; k++) S.v[k][t] = S.u1[k][t] - S.P[k];
+        for (int k = 0; k < 3; k++) S.v[k][t] = S.u1[k][t] - Q[k] / (S.mstar + Mp);
     __syncthreads();
 }
 
 // ------------------------------------------------------------ HC (Eq. Hc)
 __device__ void ens_hc(EnsShared &S, double dt_half) {
     const int n = S.n, t = threadIdx.x;
-    if (t == 0) {
-        double P0 = 0.0, P1 = 0.0, P2 = 0.0;
-        for (int j = 0; j < n; j++) { P0 += S.m[j] * S.v[0][j]; P1 += S.m[j] * S.v[1][j]; P2 += S.m[j] * S.v[2][j]; }
-        S.shift[0] = dt_half * P0 / S.mstar; S.shift[1] = dt_half * P1 / S.mstar; S.shift[2] = dt_half * P2 / S.mstar;
+    double P[3];
+    {
+        const int b = t < n ? t : 0;
+        const double mv[3] = {S.m[b] * S.v[0][b], S.m[b] * S.v[1][b], S.m[b] * S.v[2][b]};
+        ens_bsum<3>(S, mv, P);
     }
-    __syncthreads();
-    if (t < n) for (int k = 0; k < 3; k++) S.x[k][t] += S.shift[k];
+    const double f = dt_half / S.mstar;
+    if (t < n) for (int k = 0; k < 3; k++) S.x[k][t] += f * P[k];
     __syncthreads();
 }
 
@@ -378,16 +416,17 @@ __device__ void ens_gr_beta(const EnsArgs &A, EnsShared &S, double dt) {
 // HC(dt) with the gamma term: x += dt P/m_star - dt 2 (u^2/c^2) u.
 __device__ void ens_hc_gamma(const EnsArgs &A, EnsShared &S, double dt) {
     const int n = S.n, t = threadIdx.x;
-    if (t == 0) {
-        double P0 = 0.0, P1 = 0.0, P2 = 0.0;
-        for (int j = 0; j < n; j++) { P0 += S.m[j] * S.v[0][j]; P1 += S.m[j] * S.v[1][j]; P2 += S.m[j] * S.v[2][j]; }
-        S.shift[0] = dt * P0 / S.mstar; S.shift[1] = dt * P1 / S.mstar; S.shift[2] = dt * P2 / S.mstar;
+    double P[3];
+    {
+        const int b = t < n ? t : 0;
+        const double mv[3] = {S.m[b] * S.v[0][b], S.m[b] * S.v[1][b], S.m[b] * S.v[2][b]};
+        ens_bsum<3>(S, mv, P);
     }
-    __syncthreads();
+    const double f = dt / S.mstar;
     if (t < n) {
         const double u[3] = {S.v[0][t], S.v[1][t], S.v[2][t]};
         const double g = dt * 2.0 * ens_u2(u) * A.inv_c2;
-        for (int k = 0; k < 3; k++) S.x[k][t] += S.shift[k] - g * u[k];
+        for (int k = 0; k < 3; k++) S.x[k][t] += f * P[k] - g * u[k];
     }
     __syncthreads();
 }
@@ -541,7 +580,7 @@ __device__ void ens_step(const EnsArgs &A, EnsShared &S, double *scr, unsigned l
     if (t < n) {
         const double r = sqrt(dist2_rn(S.x[0][t], S.x[1][t], S.x[2][t]));
         const double va = sqrt(dist2_rn(S.v[0][t], S.v[1][t], S.v[2][t]));
-        const double hill = r * cbrt(S.m[t] / (3.0 * S.mstar));
+        const double hill = r * S.hf[t];
         const double a1 = A.n1 * hill, b1 = A.n2 * dt * va;
         const double rc = a1 > b1 ? a1 : b1;
         S.rc[t] = rc;
@@ -677,6 +716,19 @@ __global__ void __launch_bounds__(T) ensemble_kernel(EnsArgs A) {
                 S.mh[t] = __double2float_rn(S.m[t]);
                 S.ml[t] = __double2float_rn(S.m[t] - (double)S.mh[t]);
             }
+        }
+        __syncthreads();
+        if (t < n) {
+            const double ms = S.mstar, mi = S.m[t];
+            const double Ri = S.R[t], Rs = S.star_R;
+            S.hf[t] = cbrt(mi / (3.0 * ms));
+            S.im[t] = mi > 0.0 ? 1.0 / mi : 0.0;
+            S.eta[t] = ms * mi / ((ms + mi) * (ms + mi));
+            S.mu[t] = A.G * (ms + mi);
+            S.fac[t] = ms / (ms + mi);
+            S.Ii[t] = S.rg2[t] * mi * Ri * Ri;
+            S.tdi[t] = 3.0 * A.G * ms * ms * (Ri * Ri * Ri * Ri * Ri) * S.k2[t];
+            S.tds[t] = 3.0 * A.G * mi * mi * (Rs * Rs * Rs * Rs * Rs) * S.star_k2;
         }
         __syncthreads();
         const unsigned long long t_start = ens_now();

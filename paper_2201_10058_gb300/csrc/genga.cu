@@ -124,7 +124,7 @@ int alloc_pairs(genga_system *s, int level, int64_t cap) {
     CU(dalloc(&s->pairs[level], (size_t)cap));
     CU(dalloc(&s->csr[level].list, 2 * (size_t)cap));
     CU(dalloc(&s->csr[level].lpair, 2 * (size_t)cap));
-    CU(dalloc(&s->csr[level].term, 3 * (size_t)cap));
+    CU(dalloc(&s->csr[level].term, 8 * (size_t)cap));
     s->pair_cap[level] = cap;
     s->csr[level].cap = cap;
     return GENGA_OK;

@@ -7,6 +7,8 @@
 // use one thread per body, coalesced SoA loads and no shared memory.  FG runs
 // its Newton iteration per thread; its Stumpff functions need no
 // transcendental calls (series + argument quartering).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace genga {
@@ -57,14 +59,21 @@ __global__ void rcrit_derive_kernel(int n, double f_pc, RcritArrays a) {
 // ---------------------------------------------------------------- HC
 // P = sum_j m_j v_j in a fixed order (strided per-thread sums, then a fixed
 // tree), shift = dt_half P / m_star; then x_i += shift.
-constexpr int kHcThreads = 1024;
+constexpr int kHcThreads = 256;
 
+// P = sum_j m_j v_j in a fixed order: each block sums a contiguous range of
+// bodies (strided per-thread sums, then a fixed tree), and the last block to
+// finish adds the block sums in block order; shift = dt_half P / m_star.  One
+// launch over every SM (a single block was bound by one SM's FP64 rate).
 __global__ void __launch_bounds__(kHcThreads)
 hc_reduce_kernel(int n, const double *vel, const double *mass, double m_star, double dt_half,
-                 DevCounters *ctr) {
+                 double *part, DevCounters *ctr) {
     __shared__ double sp[3][kHcThreads];
+    __shared__ bool last;
+    const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int j0 = (int)blockIdx.x * per, j1 = min(n, j0 + per);
     double p0 = 0.0, p1 = 0.0, p2 = 0.0;
-    for (int j = threadIdx.x; j < n; j += kHcThreads) {
+    for (int j = j0 + (int)threadIdx.x; j < j1; j += kHcThreads) {
         const double mj = mass[j];
         p0 += mj * vel[j];
         p1 += mj * vel[(size_t)n + j];
@@ -80,7 +89,20 @@ hc_reduce_kernel(int n, const double *vel, const double *mass, double m_star, do
         }
         __syncthreads();
     }
-    if (threadIdx.x < 3) ctr->hc_shift[threadIdx.x] = dt_half * sp[threadIdx.x][0] / m_star;
+    if (threadIdx.x < 3) part[3 * blockIdx.x + threadIdx.x] = sp[threadIdx.x][0];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctr->hc_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 3) {
+        const volatile double *vp = part;
+        double sum = 0.0;
+        for (unsigned q = 0; q < gridDim.x; q++) sum += vp[3 * q + threadIdx.x];
+        ctr->hc_shift[threadIdx.x] = dt_half * sum / m_star;
+    }
+    if (threadIdx.x == 0) ctr->hc_done = 0;
 }
 
 __global__ void hc_apply_kernel(int n, double *pos, const DevCounters *ctr) {
@@ -225,7 +247,9 @@ cudaError_t launch_rcrit_derive(genga_system *s) {
 
 cudaError_t launch_hc(genga_system *s, double dt_half) {
     const int n = (int)s->n;
-    hc_reduce_kernel<<<1, kHcThreads, 0, s->stream>>>(n, s->vel, s->mass, s->p.m_star, dt_half, s->ctr); ++s->launches;
+    const int nblk = std::max(1, std::min(s->num_sms, (n + kHcThreads - 1) / kHcThreads));
+    hc_reduce_kernel<<<nblk, kHcThreads, 0, s->stream>>>(n, s->vel, s->mass, s->p.m_star, dt_half, s->red,
+                                                        s->ctr); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     hc_apply_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->pos, s->ctr); ++s->launches;
     return cudaGetLastError();
