@@ -52,7 +52,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // mass-weighted terms m_j g (x_j - x_i) (for i) and -m_i g (x_j - x_i) (for j),
 // each a 32-byte record so that phase 2 gathers one sector per partner.
 // Phase 2, one body per kApplyLanes lanes: the records of its partners in
-// ascending partner order, one lane per component -- a fixed summation order.
+// ascending partner order per lane, lanes combined in a fixed butterfly -- a
+// fixed summation order.
 struct KickPairsArgs {
     int n, nb, level;
     long long np;
@@ -94,25 +95,37 @@ __global__ void kick_pairs_terms_kernel(KickPairsArgs A) {
     A.term[2 * k + 1] = make_double4_32a(cj * dx, cj * dy, cj * dz, 0.0);
 }
 
-// Phase 2: four lanes per body, lane c < 3 sums component c of its partners'
-// records in ascending partner order (the three lanes read one 32-byte record
-// per partner together) -- no cross-lane reduction, one FP64 add per partner
-// and component.
-constexpr int kApplyLanes = 4;
+constexpr int kApplyLanes = 8;
 
 __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = gt / kApplyLanes, c = gt % kApplyLanes;
-    if (t >= A.nb || c >= 3) return;
-    const int b = A.bodies[t];
-    const int q1 = A.off[b + 1];
-    double sum = 0.0;
-    for (int q = A.off[b]; q < q1; q++) {
-        const int p = A.list[q];
-        const double *w = reinterpret_cast<const double *>(&A.term[2 * (long long)A.lpair[q] + (p > b ? 0 : 1)]);
-        sum += w[c];
+    const int t = gt / kApplyLanes, sub = gt % kApplyLanes;
+    const size_t N = (size_t)A.n;
+    int b = 0, q0 = 0, q1 = 0;
+    if (t < A.nb) {
+        b = A.bodies[t];
+        q0 = A.off[b];
+        q1 = A.off[b + 1];
     }
-    A.vel[(size_t)c * A.n + b] += A.dt_half * (A.G * sum);
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int q = q0 + sub; q < q1; q += kApplyLanes) {
+        const int p = A.list[q];
+        const double4_32a w = A.term[2 * (long long)A.lpair[q] + (p > b ? 0 : 1)];
+        sx += w.x;
+        sy += w.y;
+        sz += w.z;
+    }
+#pragma unroll
+    for (int o = kApplyLanes / 2; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (t < A.nb && sub == 0) {
+        A.vel[b] += A.dt_half * (A.G * sx);
+        A.vel[N + b] += A.dt_half * (A.G * sy);
+        A.vel[2 * N + b] += A.dt_half * (A.G * sz);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -94,6 +94,27 @@ def test_symmetric_kick_matches_oracle(g, n, P, precision, tol):
     assert np.abs(F.sum(axis=0)).max() < 1e-11 * np.abs(F).sum(axis=0).max()
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 33])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_symmetric_kick_tiny_systems(g, n, precision, tol):
+    """One ragged tile (one diagonal work item, most of the tile padding): a
+    single body feels nothing; two, three and 33 bodies match the oracle."""
+    wl = disk(max(n, 2), 0.5, 2.0, 2.0, 40 + n, name=f"disk{n}")
+    if n == 1:
+        from workloads.disk import Workload
+        wl = Workload(name="one", x=wl.x[:1], v=wl.v[:1], m=wl.m[:1], R=wl.R[:1], m_star=wl.m_star, dt=wl.dt,
+                      n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    a, s = _acc(g, wl, precision, rc, g.GENGA_KICK_SYMMETRIC, 1)
+    assert s.kick_layout()["slots"] == 1
+    if n == 1:
+        assert np.all(a == 0.0)
+        return
+    ref = O.accel(wl.x, wl.m, rc, G, nthreads=1)
+    rel = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert rel.max() <= tol, rel.max()
+
+
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
 def test_symmetric_kick_changeover_band(g, precision, tol):
     """A 300-body ring whose neighbours sit inside the changeover band: the
