@@ -83,6 +83,7 @@ struct RcritArrays {
     double *pc2 = nullptr;   // (f_pc rc_i)^2 (level 0 only)
     float *thr_rc = nullptr; // conservative FP32 upper bound of rc_i^2 (level 0 only)
     double *irc = nullptr;   // 1 / rc_i, correctly rounded (so min(irc_i, irc_j) = 1 / rc_ij exactly)
+    float2 *ircf = nullptr;  // 1 / rc_i as two floats (mixed KickS)
 };
 
 // CSR partner lists (both directions) of one pair list.
@@ -500,6 +501,78 @@ __device__ __forceinline__ double f64_of_f32_any(float f) {
     const unsigned hi = (mag >= 0x00800000u) ? (sgn | ((mag >> 3) + 0x38000000u)) : sgn;
     const unsigned lo = (mag >= 0x00800000u) ? (mag << 29) : 0u;
     return __hiloint2double((int)hi, (int)lo);
+}
+
+// 1/rc as two floats (an infinite 1/rc keeps a zero low part).
+__device__ __forceinline__ float2 ff_of_irc(double ir) {
+    const float h = __double2float_rn(ir);
+    return make_float2(h, isinf(h) ? 0.0f : __double2float_rn(ir - (double)h));
+}
+
+// Float-float helpers of the mixed kicks' changeover band (kick.cu, bs.cu).
+__device__ __forceinline__ void ff_fast2sum(float &h, float &l) {      // |h| >= |l|
+    const float s = h + l;
+    l = l - (s - h);
+    h = s;
+}
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (ah, al) *= (bh, bl)
+__device__ __forceinline__ void ff_mul(float &ah, float &al, float bh, float bl) {
+    const float ph = ah * bh;
+    float pl = fmaf(ah, bh, -ph);
+    pl = fmaf(ah, bl, pl);
+    pl = fmaf(al, bh, pl);
+    ah = ph;
+    al = pl;
+    ff_fast2sum(ah, al);
+}
+
+// The changeover function K of Sec. 6.3 (y = (r/rc - 0.1)/0.9 clamped to
+// [0, 1], K = y^2 / (y^2 + (1 - y)^2)) in float-float, from what the mixed kick
+// already holds: r = r^2 r^-1 with r^2 = Rh + Rl, Rh y0 = u + ue exactly and
+// r^-1 = y0 (1 + e/2 + 3e^2/8) for the residual e, and 1/rc_ij as two floats.
+// Absolute error of K ~2^-44 (the FP64 form's to rounding), on the FP32 pipe:
+// the band's pairs are few and scattered, and the FP64 pipe would charge each
+// one's whole warp.
+__device__ __forceinline__ void changeover_ff(float u, float ue, float Rl, float y0f, float ef, float ih, float il,
+                                              float &Kh, float &Kl) {
+    // 0.1 and 1/0.9 (the doubles of the FP64 form) as float pairs
+    constexpr float c01h = 0.100000001490116119384765625f, c01l = -1.4901161415892261e-09f;
+    constexpr float c9h = 1.1111111640930176f, c9l = -5.298190686175985e-08f;
+    float rh = u;
+    float rl = ue + fmaf(Rl, y0f, u * fmaf(0.375f * ef, ef, 0.5f * ef));
+    ff_fast2sum(rh, rl);
+    ff_mul(rh, rl, ih, il);                                       // r / rc
+    float dh, dl;
+    ff_two_sum(rh, -c01h, dh, dl);
+    dl += rl - c01l;
+    ff_fast2sum(dh, dl);
+    ff_mul(dh, dl, c9h, c9l);                                     // y
+    if (dh <= 0.0f) { Kh = 0.0f; Kl = 0.0f; return; }
+    if (dh >= 1.0f) { Kh = 1.0f; Kl = 0.0f; return; }
+    float ah = dh, al = dl;
+    ff_mul(ah, al, dh, dl);                                       // y^2
+    float wh, wl;
+    ff_two_sum(1.0f, -dh, wh, wl);
+    wl -= dl;
+    ff_fast2sum(wh, wl);
+    ff_mul(wh, wl, wh, wl);                                       // (1 - y)^2
+    float Dh, Dl;
+    ff_two_sum(ah, wh, Dh, Dl);
+    Dl += al + wl;
+    ff_fast2sum(Dh, Dl);                                          // D in [1/2, 1]
+    float qh = ah / Dh;
+    const float ph = qh * Dh;
+    float pl = fmaf(qh, Dh, -ph);
+    pl = fmaf(qh, Dl, pl);
+    float ql = (((ah - ph) - pl) + al) / Dh;
+    ff_fast2sum(qh, ql);
+    Kh = qh;
+    Kl = ql;
 }
 
 // v = hi + lo exactly up to 2^-47 |v|: hi is v with the mantissa truncated

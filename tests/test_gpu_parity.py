@@ -452,12 +452,14 @@ def test_steps_encounter_free_control(g, precision, tol):
     assert err.max() <= tol, err.max()
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
 @pytest.mark.parametrize("slevels,substeps", [(2, 10), (3, 2), (3, 10)])
-def test_levels_step_matches_oracle(g, slevels, substeps):
+def test_levels_step_matches_oracle(g, slevels, substeps, precision, tol):
     """Symplectic levels and sub-steps of Sec. 6.3 (Fig. K's two- and three-level
-    cases) on a dense disk, against the oracle's level recursion."""
+    cases) on a dense disk, against the oracle's level recursion; the mixed form
+    also takes KickS in mixed arithmetic."""
     wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=slevels, substeps=substeps)
-    s, pos, vel, mass = _system(g, wl, 0)
+    s, pos, vel, mass = _system(g, wl, precision)
     s.step(5)
     st = s.stats()
     xr, vr, status, ost = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=8), 5)
@@ -465,9 +467,9 @@ def test_levels_step_matches_oracle(g, slevels, substeps):
     assert st["n_pairs"][0] == ost["n_pairs"][0] > 0
     assert st["n_pairs"][1] > 0
     err = _rel_pos_err(_host(pos), xr)
-    numerics_log.record(f"5 steps dense disk2048 levels=({slevels},{substeps})", "max |dx|/|x|",
-                        err.max(), 1e-12)
-    assert err.max() <= 1e-12, err.max()
+    numerics_log.record(f"5 steps dense disk2048 levels=({slevels},{substeps}) precision={precision}",
+                        "max |dx|/|x|", err.max(), tol)
+    assert err.max() <= tol, err.max()
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
