@@ -229,6 +229,7 @@ def run_ours(args, dist: Dist) -> dict | None:
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     rates = genga.measure_pipe_rates()      # FP64 / FP32 / MUFU ops per clock per SM
+    fp64_lat = genga.measure_fp64_latency()  # cycles per dependent FP64 FMA (warp, one lane)
 
     def params(prec):
         return genga.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2,
@@ -439,7 +440,8 @@ def run_ours(args, dist: Dist) -> dict | None:
                                "frac": round(achieved / probe_peak, 4),
                                "basis": f"{rates['dfma']:.3f} FP64 FMA/clk/SM reached by independent "
                                         f"FMA chains (genga_measure_pipe_rates, this run)"},
-                     "pipe_rates_per_clk_sm": {k: round(v, 3) for k, v in rates.items()}},
+                     "pipe_rates_per_clk_sm": {k: round(v, 3) for k, v in rates.items()},
+                     "fp64_dependent_fma_cycles": {k: round(v, 2) for k, v in fp64_lat.items()}},
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         "encounters": head["encounters"],
         "energy": {"rel_err": head["energy_rel_err"], "steps": args.warmup + args.steps,

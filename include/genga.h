@@ -516,6 +516,14 @@ int genga_measure_pipe_rates(double *dfma_per_clk_sm, double *dadd_per_clk_sm,
                              double *dmul_per_clk_sm, double *ffma_per_clk_sm,
                              double *rsqrt_per_clk_sm);
 
+/* Latency of dependent FP64 arithmetic: one block alone on the device runs a
+ * chain of dependent FP64 FMAs, as a full warp (*warp_cycles) and as a single
+ * thread (*lane_cycles); each is the SM cycles per instruction of the chain --
+ * the time an instruction on the critical path of a latency-bound kernel (a
+ * Bulirsch-Stoer group integrated alone) costs.  Any output may be NULL.
+ * Synchronises, a few ms.  Errors: ECUDA, ENOMEM.                           */
+int genga_measure_fp64_latency(double *warp_cycles, double *lane_cycles);
+
 #ifdef __cplusplus
 }
 #endif

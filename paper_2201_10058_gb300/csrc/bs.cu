@@ -65,7 +65,6 @@ struct KickPairsArgs {
     double *vel;
     const double *mass;
     const double *irc[kMaxLevels];   // 1 / rc per level and body
-    const float2 *ircf[kMaxLevels];  // the same as two floats (mixed form)
     const double *rc2_0;
     double G, dt_half;
 };
@@ -126,112 +125,6 @@ __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
         A.vel[b] += A.dt_half * (A.G * sx);
         A.vel[N + b] += A.dt_half * (A.G * sy);
         A.vel[2 * N + b] += A.dt_half * (A.G * sz);
-    }
-}
-
-// KickS in the mixed form (params.precision == GENGA_MIXED): one kernel,
-// kApplyLanes lanes per body, each lane evaluating the terms of its partners
-// itself (a pair is met from both of its bodies) in the arithmetic of the
-// mixed kick -- FP64 displacement and accumulation, r^2 in float-float from the
-// exact split of the displacement, r^-3 from the FP32 rsqrt seed with its
-// Newton correction, the factor prod_{k<l}(1 - K_k) K_l and the partner's mass
-// in float-float (reading R29): 6 FP64 instructions per (body, partner), so
-// evaluating every pair twice costs less than writing and gathering its terms.
-// The lanes' sums meet in a fixed butterfly.
-__global__ void kick_pairs_mixed_kernel(KickPairsArgs A) {
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = gt / kApplyLanes, sub = gt % kApplyLanes;
-    const size_t N = (size_t)A.n;
-    int b = 0, q0 = 0, q1 = 0;
-    double xb = 0.0, yb = 0.0, zb = 0.0;
-    if (t < A.nb) {
-        b = A.bodies[t];
-        q0 = A.off[b];
-        q1 = A.off[b + 1];
-        xb = A.pos[b]; yb = A.pos[N + b]; zb = A.pos[2 * N + b];
-    }
-    double sx = 0.0, sy = 0.0, sz = 0.0;
-    float cxh = 0.0f, cxl = 0.0f, cyh = 0.0f, cyl = 0.0f, czh = 0.0f, czl = 0.0f;
-    for (int q = q0 + sub; q < q1; q += kApplyLanes) {
-        const int p = A.list[q];
-        const double dx = A.pos[p] - xb, dy = A.pos[N + p] - yb, dz = A.pos[2 * N + p] - zb;
-        float hx, hy, hz, lx, ly, lz;
-        split_f64(dx, hx, lx);
-        split_f64(dy, hy, ly);
-        split_f64(dz, hz, lz);
-        const float px = hx * hx, py = hy * hy, pz = hz * hz;
-        const float pxe = fmaf(hx, hx, -px), pye = fmaf(hy, hy, -py), pze = fmaf(hz, hz, -pz);
-        const float s1 = px + py, bb1 = s1 - px;
-        const float e1s = (px - (s1 - bb1)) + (py - bb1);
-        const float s2 = s1 + pz, bb2 = s2 - s1;
-        const float e2s = (s1 - (s2 - bb2)) + (pz - bb2);
-        const float cross = 2.0f * fmaf(hx, lx, fmaf(hy, ly, hz * lz));
-        const float tail = ((e1s + e2s) + (pxe + pye + pze)) + cross;
-        const float Rh = s2 + tail;
-        const float Rl = tail - (Rh - s2);
-        const float y0f = rsqrtf(Rh);
-        const float u = Rh * y0f, ue = fmaf(Rh, y0f, -u);
-        const float r1 = fmaf(-u, y0f, 1.0f);
-        const float pp = y0f * y0f, ppe = fmaf(y0f, y0f, -pp);
-        const float q3 = pp * y0f;
-        float q3e = fmaf(pp, y0f, -q3);
-        q3e = fmaf(ppe, y0f, q3e);
-        const float ef = r1 - fmaf(ue, y0f, Rl * pp);
-        // W = prod_{k<l} (1 - K_k) K_l, 1/rc_ij = min(1/rc_b, 1/rc_p) per level
-        float Wh = 1.0f, Wl = 0.0f;
-        for (int l = 0; l <= A.level; l++) {
-            const float2 ip = A.ircf[l][p], ibl = A.ircf[l][b];
-            const bool cb = ibl.x < ip.x || (ibl.x == ip.x && ibl.y <= ip.y);
-            float Kh, Kl;
-            changeover_ff(u, ue, Rl, y0f, ef, cb ? ibl.x : ip.x, cb ? ibl.y : ip.y, Kh, Kl);
-            if (l < A.level) {
-                float oh, ol;
-                ff_two_sum(1.0f, -Kh, oh, ol);
-                ol -= Kl;
-                ff_fast2sum(oh, ol);
-                ff_mul(Wh, Wl, oh, ol);
-            } else {
-                ff_mul(Wh, Wl, Kh, Kl);
-            }
-        }
-        float mh, ml;
-        split_f64(A.mass[p], mh, ml);
-        ff_mul(mh, ml, Wh, Wl);                                   // m_p W
-        const float ch = q3 * mh;
-        float ce = fmaf(q3, mh, -ch);
-        ce = fmaf(q3, ml, ce);
-        ce = fmaf(q3e, mh, ce);
-        const float corr = fmaf(ch, fmaf(1.875f * ef, ef, 1.5f * ef), ce);
-        const double sd = f64_of_f32_any(ch);
-        sx = fma(sd, dx, sx);
-        sy = fma(sd, dy, sy);
-        sz = fma(sd, dz, sz);
-        float_two_sum_acc(cxh, cxl, corr * hx);
-        float_two_sum_acc(cyh, cyl, corr * hy);
-        float_two_sum_acc(czh, czl, corr * hz);
-    }
-#pragma unroll
-    for (int o = kApplyLanes / 2; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-        const float hx2 = __shfl_xor_sync(0xffffffffu, cxh, o), lx2 = __shfl_xor_sync(0xffffffffu, cxl, o);
-        const float hy2 = __shfl_xor_sync(0xffffffffu, cyh, o), ly2 = __shfl_xor_sync(0xffffffffu, cyl, o);
-        const float hz2 = __shfl_xor_sync(0xffffffffu, czh, o), lz2 = __shfl_xor_sync(0xffffffffu, czl, o);
-        float_two_sum_acc(cxh, cxl, hx2);
-        cxl += lx2;
-        float_two_sum_acc(cyh, cyl, hy2);
-        cyl += ly2;
-        float_two_sum_acc(czh, czl, hz2);
-        czl += lz2;
-    }
-    if (t < A.nb && sub == 0) {
-        const double ax = sx + (f64_of_f32_any(cxh) + f64_of_f32_any(cxl));
-        const double ay = sy + (f64_of_f32_any(cyh) + f64_of_f32_any(cyl));
-        const double az = sz + (f64_of_f32_any(czh) + f64_of_f32_any(czl));
-        A.vel[b] += A.dt_half * (A.G * ax);
-        A.vel[N + b] += A.dt_half * (A.G * ay);
-        A.vel[2 * N + b] += A.dt_half * (A.G * az);
     }
 }
 
@@ -701,21 +594,14 @@ cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb
     A.off = s->csr[level - 1].off; A.list = s->csr[level - 1].list; A.lpair = s->csr[level - 1].lpair;
     A.term = reinterpret_cast<double4_32a *>(s->csr[level - 1].term);
     A.pos = s->pos; A.vel = s->vel; A.mass = s->mass;
-    for (int l = 0; l < kMaxLevels; l++) {
-        A.irc[l] = s->rcl[l].irc;
-        A.ircf[l] = s->rcl[l].ircf;
-    }
+    for (int l = 0; l < kMaxLevels; l++) A.irc[l] = s->rcl[l].irc;
     A.rc2_0 = s->rcl[0].rc2;
     A.G = s->p.G; A.dt_half = dt_half;
-    const long long nt = (long long)nb * kApplyLanes;
-    if (s->p.precision == GENGA_MIXED) {
-        kick_pairs_mixed_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s->stream>>>(A); ++s->launches;
-        return cudaGetLastError();
-    }
     if (A.np > 0) {
         kick_pairs_terms_kernel<<<(unsigned)((A.np + 255) / 256), 256, 0, s->stream>>>(A); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
+    const long long nt = (long long)nb * kApplyLanes;
     kick_pairs_apply_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s->stream>>>(A); ++s->launches;
     return cudaGetLastError();
 }

@@ -83,7 +83,6 @@ struct RcritArrays {
     double *pc2 = nullptr;   // (f_pc rc_i)^2 (level 0 only)
     float *thr_rc = nullptr; // conservative FP32 upper bound of rc_i^2 (level 0 only)
     double *irc = nullptr;   // 1 / rc_i, correctly rounded (so min(irc_i, irc_j) = 1 / rc_ij exactly)
-    float2 *ircf = nullptr;  // 1 / rc_i as two floats (mixed KickS)
 };
 
 // CSR partner lists (both directions) of one pair list.

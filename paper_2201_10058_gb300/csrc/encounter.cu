@@ -149,29 +149,6 @@ scan_sums_kernel(int *block_sums, int nblocks, int *total_out) {
     if (threadIdx.x == 0) *total_out = running;
 }
 
-// The whole scan in one block, for len <= kScanSingleMax (one launch instead of
-// three): thread t takes a contiguous run of ceil(len / kScanThreads) entries,
-// the runs' sums are scanned across the block, and each thread writes its run.
-// in and out must not overlap.
-constexpr long long kScanSingleMax = (long long)kScanThreads * 128;
-
-__global__ void __launch_bounds__(kScanThreads)
-scan_single_kernel(const int *in, int *out, long long len) {
-    __shared__ int ws[32];
-    const long long per = (len + kScanThreads - 1) / kScanThreads;
-    const long long a = (long long)threadIdx.x * per, b = a + per < len ? a + per : len;
-    int sum = 0;
-    for (long long i = a; i < b; i++) sum += in[i];
-    int total;
-    int run = block_exclusive_scan(sum, ws, total);
-    for (long long i = a; i < b; i++) {
-        const int v = in[i];
-        out[i] = run;
-        run += v;
-    }
-    if (threadIdx.x == 0) out[len] = total;
-}
-
 __global__ void scan_add_kernel(int *out, long long len, const int *block_sums) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < len) out[k] += block_sums[k / kScanBlock];
@@ -199,16 +176,31 @@ __global__ void csr_fill_kernel(const uint2 *pairs, long long np, const int *off
     lpair[b] = (int)k;
 }
 
-// Sorts every row by partner index, carrying the pair index along: one warp
-// per row; a row of up to kSortMax entries is held in registers (lane k takes
-// entries k, k + 32, ...), each entry's rank is the number of smaller keys in
-// the row (the partners of a row are distinct, so the ranks are a permutation
-// and the result is the sorted row), and the entries are written to their
-// ranks.  Longer rows (rare) take an insertion sort on one lane.
-constexpr int kSortPer = 4;
+// Sorts every row by partner index, carrying the pair index along.  Sparse
+// lists (most rows empty or short, as at the higher levels): one thread per
+// row, insertion sort.  Dense lists: one warp per row; a row of up to kSortMax
+// entries is held in registers (lane k takes entries k, k + 32, ...), each
+// entry's rank is the number of smaller keys in the row (the partners of a row
+// are distinct, so the ranks are a permutation and the result is the sorted
+// row), and the entries are written to their ranks; longer rows take the
+// insertion sort on one lane.  Both give the same sorted rows.
+__global__ void csr_sort_rows_kernel(int n, const int *off, int *list, int *lpair) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int s = off[b], e = off[b + 1];
+    for (int u = s + 1; u < e; u++) {
+        const int key = list[u], kp = lpair[u];
+        int w = u - 1;
+        while (w >= s && list[w] > key) { list[w + 1] = list[w]; lpair[w + 1] = lpair[w]; w--; }
+        list[w + 1] = key;
+        lpair[w + 1] = kp;
+    }
+}
+
+constexpr int kSortPer = 8;
 constexpr int kSortMax = 32 * kSortPer;
 
-__global__ void csr_sort_kernel(int n, const int *off, int *list, int *lpair) {
+__global__ void csr_sort_warp_kernel(int n, const int *off, int *list, int *lpair) {
     const int b = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= n) return;                                   // whole warps leave together
@@ -323,10 +315,6 @@ __global__ void group_members_kernel(int n, const int *label, const int *goff, i
 }  // namespace
 
 cudaError_t exclusive_scan(genga_system *s, const int *in, int *out, int64_t len) {
-    if (len <= kScanSingleMax) {
-        scan_single_kernel<<<1, kScanThreads, 0, s->stream>>>(in, out, (long long)len); ++s->launches;
-        return cudaGetLastError();
-    }
     const int nblocks = (int)((len + kScanBlock - 1) / kScanBlock);
     if (nblocks > s->scr.scan_blocks_cap) return cudaErrorInvalidValue;
     if (len > 0) {
@@ -364,7 +352,11 @@ cudaError_t build_csr(genga_system *s, int level, int64_t np) {
     if (np > 0) {
         csr_fill_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.off, c.fill, c.list, c.lpair); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
-        csr_sort_kernel<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, s->stream>>>(n, c.off, c.list, c.lpair);
+        if (2 * np >= n)         // dense: a warp per row
+            csr_sort_warp_kernel<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, s->stream>>>(
+                n, c.off, c.list, c.lpair);
+        else
+            csr_sort_rows_kernel<<<(n + 127) / 128, 128, 0, s->stream>>>(n, c.off, c.list, c.lpair);
         ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }

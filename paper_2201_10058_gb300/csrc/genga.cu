@@ -146,10 +146,6 @@ int alloc_level(genga_system *s, int l) {
         CU(dalloc(&s->rcl[l].irc, n));
         CU(cudaMemset(s->rcl[l].irc, 0, sizeof(double) * n));
     }
-    if (!s->rcl[l].ircf) {
-        CU(dalloc(&s->rcl[l].ircf, n));
-        CU(cudaMemset(s->rcl[l].ircf, 0, sizeof(float2) * n));
-    }
     if (!s->pre_pos[l]) CU(dalloc(&s->pre_pos[l], 3 * n));
     if (!s->pre_vel[l]) CU(dalloc(&s->pre_vel[l], 3 * n));
     if (!s->csr[l].deg) CU(dalloc(&s->csr[l].deg, n + 1));
@@ -199,7 +195,7 @@ int alloc_all(genga_system *s) {
 void free_all(genga_system *s) {
     dfree(s->ctr);
     for (int l = 0; l < kMaxLevels; l++) {
-        dfree(s->rcl[l].rc); dfree(s->rcl[l].rc2); dfree(s->rcl[l].pc2); dfree(s->rcl[l].irc); dfree(s->rcl[l].ircf);
+        dfree(s->rcl[l].rc); dfree(s->rcl[l].rc2); dfree(s->rcl[l].pc2); dfree(s->rcl[l].irc);
         dfree(s->rcl[l].thr_rc);
         dfree(s->pre_pos[l]); dfree(s->pre_vel[l]);
         dfree(s->pairs[l]);

@@ -19,9 +19,8 @@ namespace {
 // |x| and |v| use the detection operation order (no contraction) so that the
 // thresholds compare bit-for-bit with a plain CPU evaluation.
 __device__ __forceinline__ void derive_thresholds(double rc, double f_pc, double *rc2, double *pc2,
-                                                  float *thr_rc, double *irc, float2 *ircf) {
+                                                  float *thr_rc, double *irc) {
     *irc = __ddiv_rn(1.0, rc);
-    *ircf = ff_of_irc(*irc);
     const double r2 = __dmul_rn(rc, rc);
     const double t = __dmul_rn(f_pc, rc);
     const double p2 = __dmul_rn(t, t);
@@ -48,13 +47,13 @@ __global__ void rcrit_kernel(int n, const double *pos, const double *vel, const 
     const double rc = a > b ? a : b;
     out.rc[i] = rc;
     derive_thresholds(rc, f_pc, &out.rc2[i], out.pc2 ? &out.pc2[i] : nullptr,
-                      out.thr_rc ? &out.thr_rc[i] : nullptr, &out.irc[i], &out.ircf[i]);
+                      out.thr_rc ? &out.thr_rc[i] : nullptr, &out.irc[i]);
 }
 
 __global__ void rcrit_derive_kernel(int n, double f_pc, RcritArrays a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    derive_thresholds(a.rc[i], f_pc, &a.rc2[i], &a.pc2[i], &a.thr_rc[i], &a.irc[i], &a.ircf[i]);
+    derive_thresholds(a.rc[i], f_pc, &a.rc2[i], &a.pc2[i], &a.thr_rc[i], &a.irc[i]);
 }
 
 // ---------------------------------------------------------------- HC

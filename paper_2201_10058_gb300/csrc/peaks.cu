@@ -9,7 +9,9 @@
 // thread 0 reads the SM cycle counter before and after, between barriers.  The
 // host adds the work of the blocks that ran on each SM and divides by that SM's
 // cycle span: thread-level operations per clock per SM, independent of the
-// clock frequency.
+// clock frequency.  A second probe (fp64_chain_kernel) times a chain of
+// dependent FP64 FMAs in one warp, and in one thread, alone on the device: the
+// cost of an instruction on the critical path of a latency-bound kernel.
 #include <vector>
 
 #include "common.cuh"
@@ -92,10 +94,55 @@ cudaError_t probe(int sms, int iters, double *rate, std::vector<ProbeRec> &h, Pr
     return cudaSuccess;
 }
 
+// Latency of a chain of dependent FP64 FMAs in a warp that is alone on its SM
+// (one block of `threads` threads): SM cycles per instruction of the chain.
+__global__ void fp64_chain_kernel(int iters, double seed, long long *cycles, double *sink) {
+    double d = seed + 1e-3 * threadIdx.x;
+    const double b = 0.999999, c = 1e-7;
+    __syncwarp();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) asm volatile("fma.rn.f64 %0, %0, %1, %2;" : "+d"(d) : "d"(b), "d"(c));
+    }
+    const long long t1 = clock64();
+    if (d == 12345.678) sink[threadIdx.x] = d;
+    if (threadIdx.x == 0) *cycles = t1 - t0;
+}
+
 }  // namespace
 }  // namespace genga
 
 using namespace genga;
+
+extern "C" int genga_measure_fp64_latency(double *warp_cycles, double *lane_cycles) {
+    long long *dc = nullptr;
+    double *sink = nullptr;
+    if (cudaMalloc(&dc, sizeof(long long)) != cudaSuccess) return GENGA_ENOMEM;
+    if (cudaMalloc(&sink, sizeof(double) * 32) != cudaSuccess) {
+        cudaFree(dc);
+        return GENGA_ENOMEM;
+    }
+    const int iters = 4096;
+    double r[2] = {0.0, 0.0};
+    cudaError_t e = cudaSuccess;
+    const int threads[2] = {32, 1};
+    for (int q = 0; q < 2 && e == cudaSuccess; q++) {
+        long long cyc = 0;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {       // the first launch warms up
+            fp64_chain_kernel<<<1, threads[q]>>>(iters, 1.0, dc, sink);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpy(&cyc, dc, sizeof(cyc), cudaMemcpyDeviceToHost);
+        }
+        r[q] = (double)cyc / (16.0 * iters);
+    }
+    cudaFree(dc);
+    cudaFree(sink);
+    if (e != cudaSuccess) return GENGA_ECUDA;
+    if (warp_cycles) *warp_cycles = r[0];
+    if (lane_cycles) *lane_cycles = r[1];
+    return GENGA_OK;
+}
 
 extern "C" int genga_measure_pipe_rates(double *dfma, double *dadd, double *dmul, double *ffma,
                                         double *mufu_rsqrt) {

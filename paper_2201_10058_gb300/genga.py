@@ -40,7 +40,7 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_init_ensemble", "genga_step_ensemble", "genga_set_pair_log",
             "genga_get_pair_log", "genga_set_wait_limits", "genga_set_collisions",
             "genga_get_mergers", "genga_get_alive", "genga_remove_merged", "genga_set_kick_layout",
-            "genga_get_kick_layout"]
+            "genga_get_kick_layout", "genga_measure_fp64_latency"]
 
 NPHASES = 18
 
@@ -173,6 +173,7 @@ def load(build_if_missing: bool = True):
         L.genga_get_pair_log.argtypes = [sysp, _VP, _VP, _VP, C.c_int64, C.c_int64, _P(C.c_int64),
                                          _P(C.c_int64)]
         L.genga_measure_pipe_rates.argtypes = [_P(C.c_double)] * 5
+        L.genga_measure_fp64_latency.argtypes = [_P(C.c_double)] * 2
         void_fns = ("genga_default_params", "genga_destroy", "genga_last_error",
                     "genga_ensemble_destroy", "genga_ensemble_last_error", "genga_phase_name")
         for name in EXPORTED:
@@ -210,6 +211,16 @@ def measure_pipe_rates() -> dict:
     if rc != 0:
         raise GengaError(rc, "genga_measure_pipe_rates failed")
     return dict(zip(("dfma", "dadd", "dmul", "ffma", "rsqrt"), (x.value for x in v)))
+
+
+def measure_fp64_latency() -> dict:
+    """SM cycles per instruction of a dependent FP64 FMA chain, for a full warp
+    and for a single thread alone on the device (genga_measure_fp64_latency)."""
+    v = [C.c_double() for _ in range(2)]
+    rc = load().genga_measure_fp64_latency(*[C.byref(x) for x in v])
+    if rc != 0:
+        raise GengaError(rc, "genga_measure_fp64_latency failed")
+    return {"warp": v[0].value, "lane": v[1].value}
 
 
 def _np_ptr(a: np.ndarray):

@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "genga.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(genga_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(genga_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_builds_and_exports_every_declared_symbol():

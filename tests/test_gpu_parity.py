@@ -456,8 +456,8 @@ def test_steps_encounter_free_control(g, precision, tol):
 @pytest.mark.parametrize("slevels,substeps", [(2, 10), (3, 2), (3, 10)])
 def test_levels_step_matches_oracle(g, slevels, substeps, precision, tol):
     """Symplectic levels and sub-steps of Sec. 6.3 (Fig. K's two- and three-level
-    cases) on a dense disk, against the oracle's level recursion; the mixed form
-    also takes KickS in mixed arithmetic."""
+    cases) on a dense disk, against the oracle's level recursion, in both kick
+    forms."""
     wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=slevels, substeps=substeps)
     s, pos, vel, mass = _system(g, wl, precision)
     s.step(5)
