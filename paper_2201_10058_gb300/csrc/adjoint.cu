@@ -139,17 +139,22 @@ __global__ void drift_vjp_kernel(int n, const double *x1, const double *v1, cons
 constexpr int kAdjThreads = 128;
 constexpr int kAdjTile = 128;
 
+// Inverse distances from the Newton rsqrt; K and dK/dr only for the pairs whose
+// FP32 r^2 is below the conservative bound of rc_ij^2 (K = 1, K' = 0 beyond
+// rc_ij), from the changeover function with 1/rc_ij = min(1/rc_k, 1/rc_j).
 __global__ void __launch_bounds__(kAdjThreads)
-kick_vjp_kernel(int n, const double *pos, const double *mass, const double *rc, const double *lv,
-                int chunk, double *part /* [nchunk][4][n] */) {
-    __shared__ double sx[kAdjTile], sy[kAdjTile], sz[kAdjTile], sm[kAdjTile], src[kAdjTile];
+kick_vjp_kernel(int n, const double *pos, const double *mass, const double *irc, const float *thr,
+                const double *lv, int chunk, double *part /* [nchunk][4][n] */) {
+    __shared__ double sx[kAdjTile], sy[kAdjTile], sz[kAdjTile], sm[kAdjTile], sirc[kAdjTile];
     __shared__ double sl0[kAdjTile], sl1[kAdjTile], sl2[kAdjTile];
+    __shared__ float sthr[kAdjTile];
     const size_t N = (size_t)n;
     const int k = blockIdx.x * kAdjThreads + threadIdx.x;
     const bool valid = k < n;
-    double xk = 0, yk = 0, zk = 0, mk = 0, rck = 0, l0 = 0, l1 = 0, l2 = 0;
+    double xk = 0, yk = 0, zk = 0, mk = 0, irck = 0, l0 = 0, l1 = 0, l2 = 0;
+    float thrk = 0.0f;
     if (valid) {
-        xk = pos[k]; yk = pos[N + k]; zk = pos[2 * N + k]; mk = mass[k]; rck = rc[k];
+        xk = pos[k]; yk = pos[N + k]; zk = pos[2 * N + k]; mk = mass[k]; irck = irc[k]; thrk = thr[k];
         l0 = lv[k]; l1 = lv[N + k]; l2 = lv[2 * N + k];
     }
     const int jbeg = blockIdx.y * chunk, jend = min(n, jbeg + chunk);
@@ -159,7 +164,8 @@ kick_vjp_kernel(int n, const double *pos, const double *mass, const double *rc, 
         __syncthreads();
         for (int q = threadIdx.x; q < cnt; q += kAdjThreads) {
             const int j = jt + q;
-            sx[q] = pos[j]; sy[q] = pos[N + j]; sz[q] = pos[2 * N + j]; sm[q] = mass[j]; src[q] = rc[j];
+            sx[q] = pos[j]; sy[q] = pos[N + j]; sz[q] = pos[2 * N + j]; sm[q] = mass[j];
+            sirc[q] = irc[j]; sthr[q] = thr[j];
             sl0[q] = lv[j]; sl1[q] = lv[N + j]; sl2[q] = lv[2 * N + j];
         }
         __syncthreads();
@@ -167,19 +173,18 @@ kick_vjp_kernel(int n, const double *pos, const double *mass, const double *rc, 
         for (int q = 0; q < cnt; q++) {
             if (jt + q == k) continue;
             const double dx = sx[q] - xk, dy = sy[q] - yk, dz = sz[q] - zk;
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const double r = sqrt(r2);
-            const double rcij = fmax(rck, src[q]);
-            const double K = changeover(r, rcij);
-            const double Kp = changeover_dr_dev(r, rcij);
-            const double r3 = r2 * r;
+            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            const double id = rsqrt_newton(r2), id2 = id * id, id3 = id2 * id;
+            double K = 1.0, Kp = 0.0;
+            if (f32_of_f64_trunc(r2) < fmaxf(thrk, sthr[q]))
+                changeover_fast_dr(r2 * id, fmin(irck, sirc[q]), K, Kp);
             // e = m_k lv_j - m_j lv_k
             const double e0 = mk * sl0[q] - sm[q] * l0, e1 = mk * sl1[q] - sm[q] * l1, e2 = mk * sl2[q] - sm[q] * l2;
-            const double de = dx * e0 + dy * e1 + dz * e2;
-            const double a = K / r3;
-            const double b = -3.0 * K * de / (r3 * r2) + Kp * de / (r2 * r2);
+            const double de = fma(dz, e2, fma(dy, e1, dx * e0));
+            const double a = K * id3;
+            const double b = (-3.0 * K * id3 + Kp * id2) * id2 * de;   // -3 K de / r^5 + K' de / r^4
             g0 += a * e0 + b * dx; g1 += a * e1 + b * dy; g2 += a * e2 + b * dz;
-            gm -= K * (sl0[q] * dx + sl1[q] * dy + sl2[q] * dz) / r3;
+            gm -= a * fma(sl2[q], dz, fma(sl1[q], dy, sl0[q] * dx));
         }
     }
     if (valid) {
@@ -245,6 +250,7 @@ struct AdjBsArgs {
     const double *x2, *v2;                   // post-drift state (start of the backward run)
     double *lx, *lv, *lm;                    // in: adjoint at the end of the drift; out: at its start
     const double *mass, *rc;
+    const double *irc;                       // 1 / rc (level 0)
     const int *off, *list;
     const int *goff, *member, *slotof;
     const int *blist;                        // group labels of one size bucket, one block each
@@ -257,37 +263,45 @@ struct AdjBsArgs {
 
 __device__ __forceinline__ double &AR(const AdjBsArgs &A, int row, int slot) { return A.scr[(size_t)row * A.S + slot]; }
 
-// derivative in reversed time of the augmented state in rows z0..z0+12 into f0..f0+12
+// derivative in reversed time of the augmented state in rows z0..z0+12 into
+// f0..f0+12.  Inverse distances from the Newton rsqrt, K and dK/dr from the
+// changeover function with 1/rc_ij = min(1/rc_b, 1/rc_p) (no divisions): the
+// kernel is bound by the latency of this chain of dependent FP64 instructions.
 __device__ void adj_deriv(const AdjBsArgs &A, int z0, int f0, int s) {
     const int b = A.member[s];
     const double x = AR(A, z0, s), y = AR(A, z0 + 1, s), z = AR(A, z0 + 2, s);
     const double lvx = AR(A, z0 + 9, s), lvy = AR(A, z0 + 10, s), lvz = AR(A, z0 + 11, s);
     const double mb = A.mass[b];
-    const double r2 = x * x + y * y + z * z, r = sqrt(r2), r3 = r2 * r;
+    const double r2 = fma(z, z, fma(y, y, x * x));
+    const double ir = rsqrt_newton(r2), ir2 = ir * ir, mir3 = A.mu * (ir2 * ir);
     // star: acc = -mu x / r^3; A_star = -mu (I/r^3 - 3 x x^T / r^5) (symmetric)
-    double ax = -A.mu * x / r3, ay = -A.mu * y / r3, az = -A.mu * z / r3;
-    const double xl = x * lvx + y * lvy + z * lvz;
-    double tx = -A.mu * (lvx / r3 - 3.0 * x * xl / (r3 * r2));
-    double ty = -A.mu * (lvy / r3 - 3.0 * y * xl / (r3 * r2));
-    double tz = -A.mu * (lvz / r3 - 3.0 * z * xl / (r3 * r2));
+    double ax = -mir3 * x, ay = -mir3 * y, az = -mir3 * z;
+    const double c3 = 3.0 * fma(z, lvz, fma(y, lvy, x * lvx)) * ir2;
+    double tx = -mir3 * (lvx - c3 * x);
+    double ty = -mir3 * (lvy - c3 * y);
+    double tz = -mir3 * (lvz - c3 * z);
     double px = 0.0, py = 0.0, pz = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, gm = 0.0;
+    const double ircb = A.irc[b];
     for (int q = A.off[b]; q < A.off[b + 1]; q++) {
         const int p = A.list[q];
         const int sp = A.slotof[p];
         const double dx = AR(A, z0, sp) - x, dy = AR(A, z0 + 1, sp) - y, dz = AR(A, z0 + 2, sp) - z;
-        const double d2 = dx * dx + dy * dy + dz * dz, d = sqrt(d2), d3 = d2 * d;
-        const double rcij = fmax(A.rc[b], A.rc[p]);
-        const double W = 1.0 - changeover(d, rcij);
-        const double Wp = -changeover_dr_dev(d, rcij);
+        const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double id = rsqrt_newton(d2), id2 = id * id, id3 = id2 * id;
+        double K, dK;
+        changeover_fast_dr(d2 * id, fmin(ircb, A.irc[p]), K, dK);
+        const double W = 1.0 - K;                    // Wp = dW/dr = -dK
         const double mp = A.mass[p];
-        px += mp * W * dx / d3; py += mp * W * dy / d3; pz += mp * W * dz / d3;
+        const double mw = mp * W * id3;
+        px = fma(mw, dx, px); py = fma(mw, dy, py); pz = fma(mw, dz, pz);
         const double qx = AR(A, z0 + 9, sp), qy = AR(A, z0 + 10, sp), qz = AR(A, z0 + 11, sp);
         const double e0 = mb * qx - mp * lvx, e1 = mb * qy - mp * lvy, e2 = mb * qz - mp * lvz;
-        const double de = dx * e0 + dy * e1 + dz * e2;
-        const double a = W / d3;
-        const double bb = -3.0 * W * de / (d3 * d2) + Wp * de / (d2 * d2);
+        const double de = fma(dz, e2, fma(dy, e1, dx * e0));
+        const double a = W * id3;
+        // -3 W de / d^5 + (dW/dr) de / d^4, dW/dr = -dK
+        const double bb = (-3.0 * W * id3 - dK * id2) * id2 * de;
         gx += a * e0 + bb * dx; gy += a * e1 + bb * dy; gz += a * e2 + bb * dz;
-        gm -= W * (qx * dx + qy * dy + qz * dz) / d3;
+        gm -= W * fma(qz, dz, fma(qy, dy, qx * dx)) * id3;
     }
     ax += A.G * px; ay += A.G * py; az += A.G * pz;
     // reversed time
@@ -540,7 +554,8 @@ int kick_vjp(genga_system *s, const double *pos, const double *lv, double *lx, d
     Adjoint *a = adj_of(s);
     const int n = (int)s->n;
     dim3 grid((n + kAdjThreads - 1) / kAdjThreads, a->nchunk);
-    kick_vjp_kernel<<<grid, kAdjThreads, 0, s->stream>>>(n, pos, s->mass, s->rcl[0].rc, lv, a->chunk, a->part);
+    kick_vjp_kernel<<<grid, kAdjThreads, 0, s->stream>>>(n, pos, s->mass, s->rcl[0].irc, s->rcl[0].thr_rc, lv,
+                                                         a->chunk, a->part);
     ++s->launches;
     ACU(cudaGetLastError());
     kick_vjp_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(n, a->nchunk, a->part, s->p.G, h, lx, lm);
@@ -604,7 +619,7 @@ int step_vjp(genga_system *s, int64_t k, const double *start, double *lx, double
         AdjBsArgs B;
         B.n = (int)n; B.x2 = a->tmp; B.v2 = a->tmp + 3 * n;
         B.lx = lx; B.lv = lv; B.lm = lm;
-        B.mass = s->mass; B.rc = s->rcl[0].rc;
+        B.mass = s->mass; B.rc = s->rcl[0].rc; B.irc = s->rcl[0].irc;
         B.off = s->csr[0].off; B.list = s->csr[0].list;
         B.goff = s->goff; B.member = s->member; B.slotof = s->slotof;
         B.scr = a->bs_scr; B.S = n;
