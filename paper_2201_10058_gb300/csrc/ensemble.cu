@@ -74,6 +74,7 @@ struct EnsShared {
     // the moment of inertia rg^2 m R^2 and the tidal prefactors 3 G m_star^2 k2 R^5
     // (planet) and 3 G m^2 k2_star R_star^5 (star)
     double hf[kEnsMaxN], im[kEnsMaxN], eta[kEnsMaxN], mu[kEnsMaxN], fac[kEnsMaxN], Ii[kEnsMaxN];
+    double fiI[kEnsMaxN];               // m_star / ((m_star + m) I): the spin update's factor
     double tdi[kEnsMaxN], tds[kEnsMaxN];
     double red[4][kEnsMaxN / 32];       // per-warp partial sums of ens_bsum
 };
@@ -275,11 +276,12 @@ __device__ void ens_nn(const EnsArgs &A, EnsShared &S, double dt) {
         ens_bsum<4>(S, mv, P);
     }
     const double Mp = P[3];
+    const double ims = 1.0 / S.mstar;
     if (t == 0)
         for (int k = 0; k < 3; k++) S.ws1[k] = S.ws0[k];
     if (t < n)
         for (int k = 0; k < 3; k++) {
-            S.u0[k][t] = S.v[k][t] + P[k] / S.mstar;
+            S.u0[k][t] = S.v[k][t] + P[k] * ims;
             S.u1[k][t] = S.u0[k][t];
             S.w0[k][t] = S.w[k][t];
         }
@@ -299,14 +301,14 @@ __device__ void ens_nn(const EnsArgs &A, EnsShared &S, double dt) {
             }
             nn_body(A, S, t, um, Wm, acc, Ni, Ns);
             const double fac = S.fac[t];
-            const double Ii = S.Ii[t];
+            const double Ii = S.Ii[t], fiI = S.fiI[t];
             bool changed = false;
             for (int k = 0; k < 3; k++) {
                 const double un = S.u0[k][t] + dt * acc[k];
                 if (fabs(un - S.u1[k][t]) > 1e-16 * fabs(un)) changed = true;
                 S.u1[k][t] = un;
                 if (A.tides && Ii > 0.0) {
-                    const double Wn = S.w0[k][t] - dt * fac * Ni[k] / Ii;
+                    const double Wn = S.w0[k][t] - dt * fiI * Ni[k];
                     if (fabs(Wn - S.w[k][t]) > 1e-16 * fabs(Wn)) changed = true;
                     S.w[k][t] = Wn;
                 }
@@ -335,8 +337,9 @@ __device__ void ens_nn(const EnsArgs &A, EnsShared &S, double dt) {
     }
     if (t == 0)
         for (int k = 0; k < 3; k++) S.ws0[k] = S.ws1[k];
+    const double itot = 1.0 / (S.mstar + Mp);
     if (t < n)
-        for (int k = 0; k < 3; k++) S.v[k][t] = S.u1[k][t] - Q[k] / (S.mstar + Mp);
+        for (int k = 0; k < 3; k++) S.v[k][t] = S.u1[k][t] - Q[k] * itot;
     __syncthreads();
 }
 
@@ -727,6 +730,7 @@ __global__ void __launch_bounds__(T) ensemble_kernel(EnsArgs A) {
             S.mu[t] = A.G * (ms + mi);
             S.fac[t] = ms / (ms + mi);
             S.Ii[t] = S.rg2[t] * mi * Ri * Ri;
+            S.fiI[t] = S.Ii[t] > 0.0 ? S.fac[t] / S.Ii[t] : 0.0;
             S.tdi[t] = 3.0 * A.G * ms * ms * (Ri * Ri * Ri * Ri * Ri) * S.k2[t];
             S.tds[t] = 3.0 * A.G * mi * mi * (Rs * Rs * Rs * Rs * Rs) * S.star_k2;
         }
