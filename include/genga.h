@@ -154,9 +154,11 @@ int genga_kick(genga_system_t *sys, double dt_half, int precheck, double *acc_ou
  * 128 bodies taken by persistent blocks, and writes one compensated partial
  * sum per body and super-range, folded in a fixed order (deterministic).
  * P = 0 lets the library choose P in 1..6 for N (by a schedule of the work
- * items over the resident blocks); 1..6 fixes it.  Runs with test particles
- * (tp_mode 2, n_massive < n) use the tiled layout.  The layouts give the same
- * sums up to the rounding of a different summation order.  Errors: EINVAL. */
+ * items over the resident blocks); 1..6 fixes it.  With test particles
+ * (tp_mode 2, n_massive < n) the symmetric layout leaves out the work items
+ * made of test particles only and masks the pairs of two test particles.  The
+ * layouts give the same sums up to the rounding of a different summation
+ * order.  Errors: EINVAL.                                                    */
 int genga_set_kick_layout(genga_system_t *sys, int32_t layout, int32_t P);
 
 /* The layout of the next kick: *layout (GENGA_KICK_TILED or

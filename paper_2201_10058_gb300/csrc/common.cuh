@@ -127,6 +127,8 @@ struct genga_system {
     // symmetric kick (each unordered pair once): geometry for (ksym_n, ksym_prec)
     int64_t ksym_n = -1;
     int ksym_prec = -1;
+    int ksym_nm = -1;              // large bodies (tp_bound) the geometry was chosen for
+    int ksym_R = 0;                // super-ranges holding large bodies: slots a test particle has
     int ksym_layout = 0;           // GENGA_KICK_AUTO / _TILED / _SYMMETRIC requested
     int ksym_req_P = 0;            // requested P (0: chosen)
     int ksym_P = 0;                // super-range in tiles; 0: not used at this N

@@ -414,6 +414,7 @@ struct SymArgs {
     const float *thr;           // FP32 upper bound of rc^2
     const float2 *mhl;          // MIXED: mass as an unevaluated sum of two floats
     int n, nT, P, nItems;
+    int nm;                     // TP: bodies i >= nm are test particles (no pair of two)
     const int2 *items;          // (X, Y) super-tile pairs, X <= Y, in dispatch order
     unsigned *ctr;              // dispatch counter, zero at launch
     double *part;               // [nS][6][n]
@@ -505,7 +506,7 @@ __device__ __forceinline__ void sym_precheck(const SymArgs &A, uint2 *buf, int &
 // whose float r^2 (within 2^-23 of r^2) is below max(thr_pc_i, thr_pc_j) takes
 // the exact FP64 test of precheck_kernel (dist2_rn, no contraction) -- the same
 // candidates, found on the FP32/INT pipes the FP64-bound kick leaves idle.
-template <bool MIXED, bool PC>
+template <bool MIXED, bool PC, bool TP>
 __global__ void __launch_bounds__(kSymT, sym_min_blocks(MIXED, PC))
 kick_sym_kernel(SymArgs A)
 {
@@ -597,7 +598,10 @@ kick_sym_kernel(SymArgs A)
 #pragma unroll 4
                         for (int t = t0; t < t1; t++) {
                             const int k = qb + ((lane + t) & 31);
-                            const bool half = dsub && t == 16 && lane >= 16;    // pair taken by lane - 16
+                            // no contribution and no candidate: the pair lane - 16 takes in
+                            // a diagonal subtile's step 16; TP, a pair of two test particles
+                            const bool half = (dsub && t == 16 && lane >= 16) ||
+                                              (TP && i >= A.nm && b * kSymT + k >= A.nm);
                             const double dx = sx[k] - xi;
                             const double dy = sy[k] - yi;
                             const double dz = sz[k] - zi;
@@ -775,11 +779,14 @@ kick_sym_kernel(SymArgs A)
 
 // Folds the chunk partials in chunk order (TwoSum), scales by G and applies the
 // kick v += dt_half a; optionally stores a.
-__global__ void kick_finalize(const double *part, int nchunk, int n, double G, double dt_half,
-                              double *vel, double *acc_out)
+__global__ void kick_finalize(const double *part, int nchunk, int tp_first, int tp_slots, int n, double G,
+                              double dt_half, double *vel, double *acc_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    // symmetric kick with test particles: the bodies of the test-particle
+    // super-ranges have partials only from the ranges holding large bodies
+    if (i >= tp_first) nchunk = tp_slots;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         double S = 0.0, C = 0.0;
@@ -836,6 +843,7 @@ namespace {
 
 struct SymPlan {
     int P = 0, nS = 0, blocks = 0;
+    int R = 0;                     // super-ranges holding large bodies (TP); nS otherwise
     std::vector<int2> items;
 };
 
@@ -844,12 +852,14 @@ double sym_item_cost(int nT, int P, int X, int Y) {
     return X == Y ? 0.5 * px * px : (double)px * py;
 }
 
-// Items in dispatch order and the predicted makespan (tile-pair units per block).
-double sym_schedule(int nT, int P, int slots, std::vector<int2> *order) {
+// Items in dispatch order and the predicted makespan (tile-pair units per
+// block).  Only rows X < Xmax: with test particles, a super-range made only of
+// test particles has no pair left with a later one.
+double sym_schedule(int nT, int P, int slots, int Xmax, std::vector<int2> *order) {
     const int nS = (nT + P - 1) / P;
     std::vector<std::pair<double, int2>> it;
     it.reserve((size_t)nS * (nS + 1) / 2);
-    for (int X = 0; X < nS; X++)
+    for (int X = 0; X < std::min(nS, Xmax); X++)
         for (int Y = X; Y < nS; Y++) it.push_back({sym_item_cost(nT, P, X, Y), make_int2(X, Y)});
     std::stable_sort(it.begin(), it.end(), [](const std::pair<double, int2> &u, const std::pair<double, int2> &v) {
         return u.first > v.first;
@@ -871,7 +881,7 @@ double sym_schedule(int nT, int P, int slots, std::vector<int2> *order) {
 }
 
 template <bool MIXED>
-SymPlan sym_plan(int n, int num_sms, int layout, int req_P) {
+SymPlan sym_plan(int n, int nm, int num_sms, int layout, int req_P) {
     SymPlan best;
     const int nT = (n + kSymT - 1) / kSymT;
     // FP64 instructions per unordered pair (symmetric) and per ordered pair
@@ -881,25 +891,27 @@ SymPlan sym_plan(int n, int num_sms, int layout, int req_P) {
     // the symmetric kick's makespan (tile pairs per block, each block at 1/nb
     // of its SM) plus the finalize's slots
     if (layout == GENGA_KICK_TILED) return best;
-    const double t_old = c_old * (double)n * n / (0.95 * num_sms);
+    // tiled: the large bodies' rows meet every source, the test particles' rows the large ones
+    const double t_old = c_old * (2.0 * n * nm - (double)nm * nm) / (0.95 * num_sms);
     double t_best = layout == GENGA_KICK_SYMMETRIC ? 1e300 : t_old;
     for (int P = req_P > 0 ? req_P : 1; P <= (req_P > 0 ? req_P : kSymMaxP); P++) {
         const int nS = (nT + P - 1) / P;
         if ((double)nS * 6.0 * n * sizeof(double) > 16.0 * (1ull << 30)) continue;   // partial sums
         if ((double)nS * (nS + 1) / 2 > 4.0e6) continue;                                // host schedule
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kick_sym_kernel<MIXED, false>, kSymT,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kick_sym_kernel<MIXED, false, false>, kSymT,
                                                           sym_smem(MIXED, P)) != cudaSuccess || nb < 1)
             continue;
         const int slots = nb * num_sms;
-        const double ms = sym_schedule(nT, P, slots, nullptr);
+        const int R = (nm + P * kSymT - 1) / (P * kSymT);
+        const double ms = sym_schedule(nT, P, slots, R, nullptr);
         const double t = c_sym * (double)kSymT * kSymT * ms * nb + c_fin * (double)nS * n / num_sms;
         if (t < t_best) {
             t_best = t;
-            best.P = P; best.nS = nS; best.blocks = slots;
+            best.P = P; best.nS = nS; best.blocks = slots; best.R = R;
         }
     }
-    if (best.P) sym_schedule(nT, best.P, best.blocks, &best.items);
+    if (best.P) sym_schedule(nT, best.P, best.blocks, best.R, &best.items);
     return best;
 }
 
@@ -911,13 +923,15 @@ cudaError_t kick_reserve(genga_system *s) {
     const int n = (int)s->n;
     if (s->kick_chunk == 0) kick_geometry(n, s->num_sms, &s->kick_chunk, &s->kick_nchunk);
     const int prec = s->p.precision;
-    if (s->ksym_n != s->n || s->ksym_prec != prec) {
-        SymPlan plan = prec == GENGA_MIXED ? sym_plan<true>(n, s->num_sms, s->ksym_layout, s->ksym_req_P)
-                                           : sym_plan<false>(n, s->num_sms, s->ksym_layout, s->ksym_req_P);
+    const int nm = tp_bound(s);
+    if (s->ksym_n != s->n || s->ksym_prec != prec || s->ksym_nm != nm) {
+        SymPlan plan = prec == GENGA_MIXED ? sym_plan<true>(n, nm, s->num_sms, s->ksym_layout, s->ksym_req_P)
+                                           : sym_plan<false>(n, nm, s->num_sms, s->ksym_layout, s->ksym_req_P);
         s->ksym_P = plan.P;
         s->ksym_nS = plan.nS;
         s->ksym_blocks = plan.blocks;
         s->ksym_items = (int)plan.items.size();
+        s->ksym_R = plan.R;
         if (plan.P) {
             if ((size_t)s->ksym_items > s->ksym_list_cap) {
                 if (s->ksym_list) cudaFree(s->ksym_list);
@@ -926,8 +940,9 @@ cudaError_t kick_reserve(genga_system *s) {
                 GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_list, sizeof(int2) * plan.items.size()));
                 s->ksym_list_cap = plan.items.size();
             }
-            GENGA_CUDA_TRY(cudaMemcpy(s->ksym_list, plan.items.data(), sizeof(int2) * plan.items.size(),
-                                      cudaMemcpyHostToDevice));
+            if (!plan.items.empty())
+                GENGA_CUDA_TRY(cudaMemcpy(s->ksym_list, plan.items.data(), sizeof(int2) * plan.items.size(),
+                                          cudaMemcpyHostToDevice));
             if (!s->ksym_ctr) GENGA_CUDA_TRY(cudaMalloc((void **)&s->ksym_ctr, sizeof(unsigned)));
             if ((size_t)n > s->ksym_body_cap) {
                 if (s->ksym_irc) cudaFree(s->ksym_irc);
@@ -948,6 +963,7 @@ cudaError_t kick_reserve(genga_system *s) {
         }
         s->ksym_n = s->n;
         s->ksym_prec = prec;
+        s->ksym_nm = nm;
     }
     const size_t need = (size_t)std::max(s->kick_nchunk, s->ksym_nS) * 6 * (size_t)n;
     if (need > s->kick_part_cap) {
@@ -966,7 +982,8 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
     KickArgs A = make_args(s, false);
     const bool mixed = s->p.precision == GENGA_MIXED;
     int nparts = s->kick_nchunk;
-    if (A.nm >= n && s->ksym_P > 0) {
+    int tp_first = n, tp_slots = 0;               // bodies from tp_first fold tp_slots partials
+    if (s->ksym_P > 0) {
         // symmetric layout; the pre-check, if asked for, rides along
         kick_pack_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(s->mass, s->rcl[0].rc, s->rcl[0].pc2, n,
                                                                s->ksym_irc, s->ksym_ircf, s->ksym_mhl,
@@ -979,17 +996,25 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
         S.x = A.x; S.y = A.y; S.z = A.z; S.m = A.m;
         S.irc = s->ksym_irc; S.ircf = s->ksym_ircf; S.thr = A.thr_rc; S.mhl = s->ksym_mhl;
         S.n = n; S.nT = (n + kSymT - 1) / kSymT; S.P = s->ksym_P; S.nItems = s->ksym_items;
+        S.nm = A.nm;
         S.items = s->ksym_list; S.ctr = s->ksym_ctr; S.part = s->kick_part;
         S.pc2 = s->rcl[0].pc2; S.thr_pc = s->ksym_thrpc; S.pcf = s->ksym_pcf;
         S.cand = s->cand; S.cand_count = &s->ctr->cand_count; S.cand_cap = (unsigned long long)s->cand_cap;
         const size_t smem = sym_smem(mixed, s->ksym_P);
         const unsigned nb = (unsigned)s->ksym_blocks;
+        const bool tp = A.nm < n;
+#define GENGA_SYM_LAUNCH(M, PCK, TPK) kick_sym_kernel<M, PCK, TPK><<<nb, kSymT, smem, s->stream>>>(S)
         if (mixed) {
-            if (precheck) kick_sym_kernel<true, true><<<nb, kSymT, smem, s->stream>>>(S);
-            else kick_sym_kernel<true, false><<<nb, kSymT, smem, s->stream>>>(S);
+            if (tp) { if (precheck) GENGA_SYM_LAUNCH(true, true, true); else GENGA_SYM_LAUNCH(true, false, true); }
+            else { if (precheck) GENGA_SYM_LAUNCH(true, true, false); else GENGA_SYM_LAUNCH(true, false, false); }
         } else {
-            if (precheck) kick_sym_kernel<false, true><<<nb, kSymT, smem, s->stream>>>(S);
-            else kick_sym_kernel<false, false><<<nb, kSymT, smem, s->stream>>>(S);
+            if (tp) { if (precheck) GENGA_SYM_LAUNCH(false, true, true); else GENGA_SYM_LAUNCH(false, false, true); }
+            else { if (precheck) GENGA_SYM_LAUNCH(false, true, false); else GENGA_SYM_LAUNCH(false, false, false); }
+        }
+#undef GENGA_SYM_LAUNCH
+        if (tp) {
+            tp_first = (int)std::min<int64_t>((int64_t)s->ksym_R * s->ksym_P * kSymT, n);
+            tp_slots = s->ksym_R;
         }
         nparts = s->ksym_nS;
     } else {
@@ -1005,7 +1030,7 @@ cudaError_t launch_kick(genga_system *s, double dt_half, bool precheck, double *
     }
     ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    kick_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(s->kick_part, nparts, n, s->p.G,
+    kick_finalize<<<(n + 255) / 256, 256, 0, s->stream>>>(s->kick_part, nparts, tp_first, tp_slots, n, s->p.G,
                                                           dt_half, s->vel, acc_out); ++s->launches;
     return cudaGetLastError();
 }
@@ -1042,7 +1067,8 @@ cudaError_t launch_kick_raw(const KickRaw &k, int num_sms, int max_nchunk, cudaS
     if (k.mixed) kick_kernel<true, false><<<grid, kKickThreads, 0, stream>>>(A);
     else kick_kernel<false, false><<<grid, kKickThreads, 0, stream>>>(A);
     GENGA_CUDA_TRY(cudaGetLastError());
-    kick_finalize<<<(k.n + 255) / 256, 256, 0, stream>>>(k.part, nchunk, k.n, k.G, k.dt_half, k.vel, k.acc_out);
+    kick_finalize<<<(k.n + 255) / 256, 256, 0, stream>>>(k.part, nchunk, k.n, 0, k.n, k.G, k.dt_half, k.vel,
+                                                         k.acc_out);
     return cudaGetLastError();
 }
 
@@ -1069,7 +1095,7 @@ extern "C" int genga_get_kick_layout(genga_system_t *s, int32_t *layout, int32_t
                                      int32_t *blocks) {
     if (!s) return GENGA_EINVAL;
     if (kick_reserve(s) != cudaSuccess) return GENGA_ECUDA;
-    const bool sym = s->ksym_P > 0 && tp_bound(s) >= s->n;
+    const bool sym = s->ksym_P > 0;
     if (layout) *layout = sym ? GENGA_KICK_SYMMETRIC : GENGA_KICK_TILED;
     if (P) *P = sym ? s->ksym_P : 0;
     if (slots) *slots = sym ? s->ksym_nS : s->kick_nchunk;

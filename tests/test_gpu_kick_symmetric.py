@@ -14,6 +14,7 @@ padding of the last tile are few enough to reach every case:
     work items from a counter in whatever order they come;
   * the pre-check fused into the symmetric kick: candidate lists identical to
     the oracle's, including an overflowing list that is regrown;
+  * semi-active test particles: kick, candidates and whole steps;
   * whole steps: 10 steps of the N = 2048 disk to 1e-12 (FP64) / 1e-9 (mixed),
     and 100 steps of the encounter-free control.
 """
@@ -40,7 +41,7 @@ def g(cuda_lib):
     return cuda_lib
 
 
-def _system(g, wl, precision, layout, P=0):
+def _system(g, wl, precision, layout, P=0, **kw):
     torch = _torch()
     dev = torch.device("cuda:0")
     pos = torch.tensor(np.ascontiguousarray(wl.x.T), device=dev)
@@ -48,6 +49,8 @@ def _system(g, wl, precision, layout, P=0):
     mass = torch.tensor(wl.m, device=dev)
     p = g.default_params(G=wl.G, m_star=wl.m_star, dt=wl.dt, n1=wl.n1, n2=wl.n2, f_pc=wl.f_pc,
                          slevels=wl.slevels, substeps=wl.substeps, precision=precision)
+    for k, v in kw.items():
+        setattr(p, k, v)
     s = g.System(pos, vel, mass, p)
     s.set_kick_layout(layout, P)
     return s, pos, vel, mass
@@ -193,6 +196,51 @@ def test_fused_precheck_overflow_regrows(g):
     s.set_rcrit(rc)
     s.kick(0.5 * wl.dt, precheck=True)
     np.testing.assert_array_equal(s.candidates(), O.precheck(wl.x, rc, wl.f_pc))
+
+
+@pytest.mark.parametrize("nm,P", [(0, 1), (129, 1), (1500, 1), (1500, 2), (3001, 2)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_symmetric_kick_test_particles(g, nm, P, precision, tol):
+    """Semi-active test particles (Sec. 8.1, bodies from n_massive on) in the
+    symmetric layout: work items of test particles only are left out, pairs of
+    two test particles are masked in the tiles that straddle n_massive, and a
+    test particle folds only the partial sums of the ranges holding large
+    bodies."""
+    wl = disk(3001, 0.5, 2.0, 2.0, 60, name="disk3001")
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    torch = _torch()
+    s, *_ = _system(g, wl, precision, g.GENGA_KICK_SYMMETRIC, P, tp_mode=2, n_massive=nm)
+    s.set_rcrit(rc)
+    assert s.kick_layout()["layout"] == g.GENGA_KICK_SYMMETRIC
+    acc = torch.zeros((3, wl.n), dtype=torch.float64, device="cuda:0")
+    s.kick(0.0, precheck=True, acc_out=acc)
+    torch.cuda.synchronize()
+    a = _host(acc)
+    ref = O.accel(wl.x, wl.m, rc, G, nthreads=8, n_massive=nm)
+    np.testing.assert_array_equal(s.candidates(), O.precheck(wl.x, rc, wl.f_pc, n_massive=nm))
+    if nm == 0:
+        assert np.all(a == 0.0)
+        return
+    rel = np.linalg.norm(a - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    numerics_log.record(f"symmetric kick disk3001 test particles from {nm} P={P} precision={precision}",
+                        "per-particle |da|/|a|", rel.max(), tol)
+    assert rel.max() <= tol, rel.max()
+
+
+@pytest.mark.parametrize("slevels,substeps", [(1, 1), (2, 10)])
+def test_symmetric_test_particle_steps_match_oracle(g, slevels, substeps):
+    """5 whole steps of a dense 2048-body disk with test particles from 1500,
+    every kick in the symmetric layout, against the oracle (FP64)."""
+    wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=slevels, substeps=substeps)
+    s, pos, vel, mass = _system(g, wl, 0, g.GENGA_KICK_SYMMETRIC, 2, tp_mode=2, n_massive=1500)
+    s.step(5)
+    xr, vr, status, ost = O.step(wl.x, wl.v, wl.m, O.make_params(wl, nthreads=8, tp_mode=2, n_massive=1500), 5)
+    assert status == 0
+    x = _host(pos)
+    err = np.linalg.norm(x - xr, axis=1) / np.linalg.norm(xr, axis=1)
+    numerics_log.record(f"5 steps dense disk2048 symmetric kick, test particles from 1500, levels=({slevels},{substeps})",
+                        "max |dx|/|x|", err.max(), 1e-12)
+    assert err.max() <= 1e-12, err.max()
 
 
 def test_auto_layout_choice(g):
