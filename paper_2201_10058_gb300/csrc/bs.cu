@@ -50,8 +50,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Phase 1, one thread per undirected pair (i < j): g = prod_{k<l}(1 - K_k) K_l / r^3
 // (0 when the pair is beyond rc_0, where 1 - K_0 = 0) and the pair's two
 // mass-weighted terms m_j g (x_j - x_i) (for i) and -m_i g (x_j - x_i) (for j),
-// each a 32-byte record so that phase 2 gathers one sector per partner.
-// Phase 2, one body per kApplyLanes lanes: the records of its partners in
+// each a 32-byte record written to the pair's entry in the row of its body
+// (ent), so that phase 2 reads every row as one contiguous run.  Factors
+// outside their changeover band (K = 0 or 1 exactly) are decided from FP32
+// copies, so they cost no FP64 operation.
+// Phase 2, one body per kApplyLanes lanes: the records of its row, in
 // ascending partner order per lane, lanes combined in a fixed butterfly -- a
 // fixed summation order.
 struct KickPairsArgs {
@@ -59,15 +62,25 @@ struct KickPairsArgs {
     long long np;
     const uint2 *pairs;
     const int *bodies;
-    const int *off, *list, *lpair;
-    double4_32a *term;     // [np][2]: the terms for i and for j
+    const int *off, *ent;
+    double4_32a *term;     // one record per entry
     const double *pos;
     double *vel;
     const double *mass;
     const double *irc[kMaxLevels];   // 1 / rc per level and body
-    const double *rc2_0;
+    const float *thr_rc0;            // FP32 upper bound of rc_0^2 per body
     double G, dt_half;
 };
+
+// Float copy of a positive double, truncated, saturating: +inf at or above
+// 2^128, 0 below 2^-126 (integer operations only).  Monotone, and never above
+// its argument except where that is >= 2^128.
+__device__ __forceinline__ float f32_of_f64_trunc_sat(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v);
+    if (hi >= 0x47f00000u) return __int_as_float(0x7f800000);
+    if (hi < 0x38100000u) return 0.0f;
+    return __uint_as_float(((hi - 0x38000000u) << 3) | ((unsigned)__double2loint(v) >> 29));
+}
 
 __global__ void kick_pairs_terms_kernel(KickPairsArgs A) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -79,20 +92,34 @@ __global__ void kick_pairs_terms_kernel(KickPairsArgs A) {
                  dz = A.pos[2 * N + j] - A.pos[2 * N + i];
     const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
     double g = 0.0;
-    // beyond (1 + 1e-13) rc_0 the factor 1 - K_0 is exactly zero
-    if (r2 < 1.0000000000001 * fmax(A.rc2_0[i], A.rc2_0[j])) {
+    // beyond the FP32 bound of rc_0^2 (> rc_0^2 (1 + 2^-16)) the factor 1 - K_0
+    // is exactly zero
+    if (f32_of_f64_trunc_sat(r2) <= fmaxf(A.thr_rc0[i], A.thr_rc0[j])) {
         const double yv = rsqrt_newton(r2);
         const double r = r2 * yv;
+        const float rf = f32_of_f64_trunc_sat(r);
         double W = 1.0;
+        bool zero = false;
         // 1 / rc_ij = 1 / max(rc_i, rc_j) = min(1/rc_i, 1/rc_j), bit for bit
-        for (int l = 0; l < A.level; l++)
+        for (int l = 0; l < A.level; l++) {
+            const int side = changeover_side_f32(
+                rf, fminf(f32_of_f64_trunc_sat(A.irc[l][i]), f32_of_f64_trunc_sat(A.irc[l][j])));
+            if (side < 0) continue;
+            if (side > 0) { zero = true; break; }
             W *= 1.0 - changeover_fast(r, fmin(A.irc[l][i], A.irc[l][j]));
-        W *= changeover_fast(r, fmin(A.irc[A.level][i], A.irc[A.level][j]));
-        g = W * yv * yv * yv;
+        }
+        if (!zero) {
+            const int l = A.level;
+            const int side = changeover_side_f32(
+                rf, fminf(f32_of_f64_trunc_sat(A.irc[l][i]), f32_of_f64_trunc_sat(A.irc[l][j])));
+            if (side == 0) W *= changeover_fast(r, fmin(A.irc[l][i], A.irc[l][j]));
+            if (side >= 0) g = W * (yv * yv * yv);
+        }
     }
     const double ci = A.mass[j] * g, cj = -A.mass[i] * g;
-    A.term[2 * k] = make_double4_32a(ci * dx, ci * dy, ci * dz, 0.0);
-    A.term[2 * k + 1] = make_double4_32a(cj * dx, cj * dy, cj * dz, 0.0);
+    const int2 e = reinterpret_cast<const int2 *>(A.ent)[k];
+    A.term[e.x] = make_double4_32a(ci * dx, ci * dy, ci * dz, 0.0);
+    A.term[e.y] = make_double4_32a(cj * dx, cj * dy, cj * dz, 0.0);
 }
 
 constexpr int kApplyLanes = 8;
@@ -109,8 +136,7 @@ __global__ void kick_pairs_apply_kernel(KickPairsArgs A) {
     }
     double sx = 0.0, sy = 0.0, sz = 0.0;
     for (int q = q0 + sub; q < q1; q += kApplyLanes) {
-        const int p = A.list[q];
-        const double4_32a w = A.term[2 * (long long)A.lpair[q] + (p > b ? 0 : 1)];
+        const double4_32a w = A.term[q];
         sx += w.x;
         sy += w.y;
         sz += w.z;
@@ -153,10 +179,11 @@ struct ColsShared {
     int npairs;
     double m[M];
     double irc[kMaxLevels][M];
+    float ircf[kMaxLevels][M];                   // 1/rc rounded to float towards zero (band side tests)
     double y[6][M], f0[6][M];                    // attempt start and its derivative
-    double yk[8][6][M];                          // column results
+    double zf[3][6][M];                          // the completing column's z_n, z_{n-1}, f(z_n)
+    double hcol[8];                              // sub-step H / n_k of each column
     double ynew[6][M];                           // accepted state
-    double red[8];
     int rank_of_slot[M];
     int flag;
     // collisions: radius, alive flag and body index of each member rank
@@ -194,8 +221,15 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
             const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
             const double yv = rsqrt_newton(d2);
             const double d = d2 * yv;
+            const float df = f32_of_f64_trunc(d);
             double W = 1.0;
-            for (int l = 0; l < A.nlev; l++) W *= 1.0 - changeover_fast(d, fmin(S.irc[l][pa], S.irc[l][pq]));
+            // factors 1 - K outside the band (1 or 0) decided in FP32, exactly
+            for (int l = 0; l < A.nlev; l++) {
+                const int side = changeover_side_f32(df, fminf(S.ircf[l][pa], S.ircf[l][pq]));
+                if (side < 0) continue;
+                if (side > 0) { W = 0.0; break; }
+                W *= 1.0 - changeover_fast(d, fmin(S.irc[l][pa], S.irc[l][pq]));
+            }
             const double c = W * (yv * yv * yv);
             S.pt[0][col][pi] = c * dx;
             S.pt[1][col][pi] = c * dy;
@@ -235,29 +269,20 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
         const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
         const double yv = rsqrt_newton(d2);
         const double d = d2 * yv;
+        const float df = f32_of_f64_trunc(d);
         double W = 1.0;
-        for (int l = 0; l < A.nlev; l++) W *= 1.0 - changeover_fast(d, fmin(irc_self[l], S.irc[l][q]));
+        for (int l = 0; l < A.nlev; l++) {
+            const int side = changeover_side_f32(df, fminf(S.ircf[l][tid % M], S.ircf[l][q]));
+            if (side < 0) continue;
+            if (side > 0) { W = 0.0; break; }
+            W *= 1.0 - changeover_fast(d, fmin(irc_self[l], S.irc[l][q]));
+        }
         const double c = S.m[q] * W * (yv * yv * yv);
         px = fma(c, dx, px); py = fma(c, dy, py); pz = fma(c, dz, pz);
     }
     f[3] = fma(sst, z[0], A.G * px);
     f[4] = fma(sst, z[1], A.G * py);
     f[5] = fma(sst, z[2], A.G * pz);
-}
-
-template <int M>
-__device__ __forceinline__ double cols_block_max(double v, ColsShared<M> &S) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    constexpr int nw = (8 * M) / 32;
-    if (nw == 1) return v;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double r = S.red[0];
-#pragma unroll
-    for (int w = 1; w < nw; w++) r = fmax(r, S.red[w]);
-    return r;
 }
 
 // Row k of the Neville table in h^2 (n_k = 2(k+1)), in place in T:
@@ -390,7 +415,10 @@ bs_cols_kernel(BsArgs A) {
         for (int c = 0; c < 3; c++) { y[c] = A.pre_pos[c * N + b]; y[3 + c] = A.pre_vel[c * N + b]; }
         if (col == 0) {
             S.m[a] = A.mass[b];
-            for (int l = 0; l < A.nlev; l++) S.irc[l][a] = irc_self[l];
+            for (int l = 0; l < A.nlev; l++) {
+                S.irc[l][a] = irc_self[l];
+                S.ircf[l][a] = __double2float_rz(irc_self[l]);
+            }
         }
     }
     if (COLL && col == 0) {
@@ -454,9 +482,10 @@ bs_cols_kernel(BsArgs A) {
         // the first column k >= 1 under tolerance -- the columns beyond it are
         // never needed, so they are not computed to the end.
         const double h = H / nk;
+        if (a == 0) S.hcol[col] = h;
         for (int c = 0; c < 6; c++) { zm[c] = y[c]; zn[c] = fma(h, f0[c], y[c]); }
         double T[8];
-        double sc = 1.0, diag = 0.0;
+        double tsc = 0.0, diag = 0.0;
         int kconv = -1;
         for (int it = 1; it <= 16; it++) {
             cols_deriv<M, COLL>(A, S, tid, col, active, pmask, irc_self, zn, fz);
@@ -467,19 +496,30 @@ bs_cols_kernel(BsArgs A) {
                     zn[c] = tt;
                 }
             } else if (it == nk) {
-                for (int c = 0; c < 6; c++) S.yk[col][c][a] = 0.5 * (zn[c] + zm[c] + h * fz[c]);
+                // the column's final smoothing step is formed by the Neville
+                // lanes below (one component each), not by this column's lanes
+                // while the others take midpoint sub-steps
+                for (int c = 0; c < 6; c++) {
+                    S.zf[0][c][a] = zn[c];
+                    S.zf[1][c][a] = zm[c];
+                    S.zf[2][c][a] = fz[c];
+                }
             }
             if (it & 1) continue;
             const int k = it / 2 - 1;                    // column just completed
             __syncthreads();
-            double e = 0.0;
+            // error |T_kk - T_k,k-1| / scale <= tol for every member and
+            // component, tested as |T_kk - T_k,k-1| <= tol scale and combined
+            // by a block-wide vote
+            bool ok = true;
             if (col < 6 && active) {
-                if (k == 0) sc = fabs(S.y[col][a]) + fabs(H * S.f0[col][a]) + 1e-300;
+                if (k == 0) tsc = A.tol * (fabs(S.y[col][a]) + fabs(H * S.f0[col][a]) + 1e-300);
                 double prevdiag = 0.0;
-                neville_row(k, T, S.yk[k][col][a], diag, prevdiag);
-                if (k >= 1) e = fabs(diag - prevdiag) / sc;
+                const double yk = 0.5 * (S.zf[0][col][a] + S.zf[1][col][a] + S.hcol[k] * S.zf[2][col][a]);
+                neville_row(k, T, yk, diag, prevdiag);
+                ok = fabs(diag - prevdiag) <= tsc;
             }
-            if (k >= 1 && cols_block_max<M>(e, S) <= A.tol) { kconv = k; break; }
+            if (k >= 1 && __syncthreads_and(ok)) { kconv = k; break; }
         }
         bool accept = kconv >= 0;
         if (accept) {
@@ -591,11 +631,11 @@ cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb
     A.np = s->npairs_host[level - 1];
     A.pairs = s->pairs[level - 1];
     A.bodies = s->bodies[level];
-    A.off = s->csr[level - 1].off; A.list = s->csr[level - 1].list; A.lpair = s->csr[level - 1].lpair;
+    A.off = s->csr[level - 1].off; A.ent = s->csr[level - 1].ent;
     A.term = reinterpret_cast<double4_32a *>(s->csr[level - 1].term);
     A.pos = s->pos; A.vel = s->vel; A.mass = s->mass;
     for (int l = 0; l < kMaxLevels; l++) A.irc[l] = s->rcl[l].irc;
-    A.rc2_0 = s->rcl[0].rc2;
+    A.thr_rc0 = s->rcl[0].thr_rc;
     A.G = s->p.G; A.dt_half = dt_half;
     if (A.np > 0) {
         kick_pairs_terms_kernel<<<(unsigned)((A.np + 255) / 256), 256, 0, s->stream>>>(A); ++s->launches;

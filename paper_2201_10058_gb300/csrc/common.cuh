@@ -91,8 +91,9 @@ struct Csr {
     int *off = nullptr;    // n+1 (exclusive scan of deg)
     int *fill = nullptr;   // n
     int *list = nullptr;   // 2 * cap: partner of each entry
-    int *lpair = nullptr;  // 2 * cap: index of the entry's pair in the pair list
-    double *term = nullptr;  // 8 * cap: per pair two mass-weighted KickS terms (x, y, z, pad)
+    int *lpair = nullptr;  // 2 * cap: 2 k + d for the entry of pair k in the row of its body d (0: pairs[k].x, 1: pairs[k].y)
+    int *ent = nullptr;    // 2 * cap: the inverse, entry of 2 k + d in the sorted rows
+    double *term = nullptr;  // 8 * cap: the mass-weighted KickS term (x, y, z, pad) of each entry
     int64_t cap = 0;       // pairs
 };
 
@@ -244,6 +245,21 @@ __device__ __forceinline__ void two_sum(double a, double b, double &s, double &e
     s = __dadd_rn(a, b);
     double bb = __dsub_rn(s, a);
     e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// The same error-free sum in 3 FP64 operations: Dekker's Fast2Sum on the
+// operands ordered by exponent.  The high words with the sign cleared compare
+// as unsigned integers in the order of the exponents (ties: equal exponents,
+// where either order is exact), so the ordering costs no FP64 operation.  For
+// finite a and b the rounding error is representable and unique, so s and e
+// equal two_sum()'s (up to the sign of a zero e).
+__device__ __forceinline__ void two_sum_ordered(double a, double b, double &s, double &e) {
+    const unsigned ha = (unsigned)__double2hiint(a) & 0x7fffffffu;
+    const unsigned hb = (unsigned)__double2hiint(b) & 0x7fffffffu;
+    const bool ge = ha >= hb;
+    const double big = ge ? a : b, small = ge ? b : a;
+    s = __dadd_rn(big, small);
+    e = __dsub_rn(small, __dsub_rn(s, big));
 }
 
 __device__ __forceinline__ void latch_error(DevCounters *c, unsigned bit) { atomicOr(&c->err, bit); }
@@ -470,6 +486,19 @@ __device__ __forceinline__ double changeover_fast(double r, double irc) {
     const double w = 1.0 - y;
     return y2 * rcp_newton(fma(w, w, y2));
 }
+// Side of the changeover band from FP32 copies of r (f32_of_f64_trunc of a
+// positive normal double in the FP32 range) and of 1/rc (__double2float_rz):
+// -1 when r/rc < 0.1 for certain (K = 0 exactly in changeover_fast), +1 when
+// r/rc > 1 for certain (K = 1 exactly), 0 otherwise (evaluate K).  Both copies
+// are truncations, < 2^-23 low each, and the product rounds by <= 2^-24, so the
+// float product lies in [x (1 - 2^-22), x (1 + 2^-24)] of x = r/rc; the
+// margins 0.09999 and 1.0001 are far wider, so both decisions are exact.  An
+// infinite 1/rc (rc = 0) gives +1, as K = 1 there.
+__device__ __forceinline__ int changeover_side_f32(float rf, float ircf) {
+    const float p = rf * ircf;
+    return p < 0.09999f ? -1 : (p > 1.0001f ? 1 : 0);
+}
+
 // K and dK/dr with 1/rc supplied: the definitions of changeover() and
 // changeover_dr_dev() (dK/dy = 2y(1 - y)/D^2, D = y^2 + (1 - y)^2, dy/dr = 1/(0.9 rc)),
 // in contracted FP64 arithmetic for force terms.

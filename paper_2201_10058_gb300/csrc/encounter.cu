@@ -170,10 +170,10 @@ __global__ void csr_fill_kernel(const uint2 *pairs, long long np, const int *off
     const uint2 p = pairs[k];
     const int a = off[p.x] + atomicAdd(&fill[p.x], 1);
     list[a] = (int)p.y;
-    lpair[a] = (int)k;
+    lpair[a] = (int)(2 * k);
     const int b = off[p.y] + atomicAdd(&fill[p.y], 1);
     list[b] = (int)p.x;
-    lpair[b] = (int)k;
+    lpair[b] = (int)(2 * k + 1);
 }
 
 // Sorts every row by partner index, carrying the pair index along.  Sparse
@@ -183,8 +183,10 @@ __global__ void csr_fill_kernel(const uint2 *pairs, long long np, const int *off
 // entry's rank is the number of smaller keys in the row (the partners of a row
 // are distinct, so the ranks are a permutation and the result is the sorted
 // row), and the entries are written to their ranks; longer rows take the
-// insertion sort on one lane.  Both give the same sorted rows.
-__global__ void csr_sort_rows_kernel(int n, const int *off, int *list, int *lpair) {
+// insertion sort on one lane.  Both give the same sorted rows, and both record
+// where each pair direction 2 k + d ended up (ent), so that per-pair results can
+// be written straight to their entries and read row by row.
+__global__ void csr_sort_rows_kernel(int n, const int *off, int *list, int *lpair, int *ent) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     const int s = off[b], e = off[b + 1];
@@ -195,17 +197,22 @@ __global__ void csr_sort_rows_kernel(int n, const int *off, int *list, int *lpai
         list[w + 1] = key;
         lpair[w + 1] = kp;
     }
+    for (int u = s; u < e; u++) ent[lpair[u]] = u;
 }
 
 constexpr int kSortPer = 8;
 constexpr int kSortMax = 32 * kSortPer;
 
-__global__ void csr_sort_warp_kernel(int n, const int *off, int *list, int *lpair) {
+__global__ void csr_sort_warp_kernel(int n, const int *off, int *list, int *lpair, int *ent) {
     const int b = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= n) return;                                   // whole warps leave together
     const int s = off[b], e = off[b + 1], L = e - s;
-    if (L <= 1) return;
+    if (L == 0) return;
+    if (L == 1) {
+        if (lane == 0) ent[lpair[s]] = s;
+        return;
+    }
     if (L > kSortMax) {
         if (lane == 0)
             for (int u = s + 1; u < e; u++) {
@@ -215,6 +222,8 @@ __global__ void csr_sort_warp_kernel(int n, const int *off, int *list, int *lpai
                 list[w + 1] = key;
                 lpair[w + 1] = kp;
             }
+        __syncwarp();
+        for (int u = s + lane; u < e; u += 32) ent[lpair[u]] = u;
         return;
     }
     int key[kSortPer], kp[kSortPer], rank[kSortPer];
@@ -241,6 +250,7 @@ __global__ void csr_sort_warp_kernel(int n, const int *off, int *list, int *lpai
         if (u < L) {
             list[s + rank[c]] = key[c];
             lpair[s + rank[c]] = kp[c];
+            ent[kp[c]] = s + rank[c];
         }
     }
 }
@@ -354,9 +364,9 @@ cudaError_t build_csr(genga_system *s, int level, int64_t np) {
         GENGA_CUDA_TRY(cudaGetLastError());
         if (2 * np >= n)         // dense: a warp per row
             csr_sort_warp_kernel<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, s->stream>>>(
-                n, c.off, c.list, c.lpair);
+                n, c.off, c.list, c.lpair, c.ent);
         else
-            csr_sort_rows_kernel<<<(n + 127) / 128, 128, 0, s->stream>>>(n, c.off, c.list, c.lpair);
+            csr_sort_rows_kernel<<<(n + 127) / 128, 128, 0, s->stream>>>(n, c.off, c.list, c.lpair, c.ent);
         ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }

@@ -117,13 +117,19 @@ int check_params(genga_system *s, const genga_params_t *p) {
 }
 
 int alloc_pairs(genga_system *s, int level, int64_t cap) {
+    // partner-list entries (2 per pair) and their directions 2 k + d are ints
+    if (cap > (int64_t)0x3fffffff)
+        return fail(s, GENGA_ECAPACITY, "level %d: %lld encounter pairs exceed the 2^30 limit", level,
+                    (long long)cap);
     dfree(s->pairs[level]);
     dfree(s->csr[level].list);
     dfree(s->csr[level].lpair);
+    dfree(s->csr[level].ent);
     dfree(s->csr[level].term);
     CU(dalloc(&s->pairs[level], (size_t)cap));
     CU(dalloc(&s->csr[level].list, 2 * (size_t)cap));
     CU(dalloc(&s->csr[level].lpair, 2 * (size_t)cap));
+    CU(dalloc(&s->csr[level].ent, 2 * (size_t)cap));
     CU(dalloc(&s->csr[level].term, 8 * (size_t)cap));
     s->pair_cap[level] = cap;
     s->csr[level].cap = cap;
@@ -200,7 +206,7 @@ void free_all(genga_system *s) {
         dfree(s->pre_pos[l]); dfree(s->pre_vel[l]);
         dfree(s->pairs[l]);
         dfree(s->csr[l].deg); dfree(s->csr[l].off); dfree(s->csr[l].fill); dfree(s->csr[l].list);
-        dfree(s->csr[l].lpair); dfree(s->csr[l].term);
+        dfree(s->csr[l].lpair); dfree(s->csr[l].ent); dfree(s->csr[l].term);
         dfree(s->bodies[l]);
     }
     dfree(s->kick_part); dfree(s->ksym_list); dfree(s->ksym_ctr); dfree(s->ksym_irc); dfree(s->ksym_mhl); dfree(s->ksym_thrpc); dfree(s->ksym_pcf); dfree(s->ksym_ircf);

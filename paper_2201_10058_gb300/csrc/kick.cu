@@ -793,7 +793,7 @@ __global__ void kick_finalize(const double *part, int nchunk, int tp_first, int 
         for (int q = 0; q < nchunk; q++) {
             const double *p = part + (size_t)q * 6 * n;
             double t, e;
-            two_sum(S, p[(size_t)c * n + i], t, e);
+            two_sum_ordered(S, p[(size_t)c * n + i], t, e);
             S = t;
             C += e + p[(size_t)(3 + c) * n + i];
         }
