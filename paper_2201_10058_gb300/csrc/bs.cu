@@ -31,7 +31,8 @@ struct BsArgs {
     int nlev;
     const int *off, *list;
     const int *glist, *goff, *member, *slotof;
-    const int *blist;      // this kernel's bucket: group labels, one block each
+    const int *blist;      // this kernel's bucket: group labels
+    int bucket;            // its index (device count and claim counter)
     double G, mu, dt, tol;
     int max_steps;
     unsigned long long time_limit_ns;
@@ -171,7 +172,7 @@ constexpr int kColsPairs = (M <= 16) ? M * (M - 1) / 2 : 1;
 
 template <int M>
 struct ColsShared {
-    double zx[8 * M], zy[8 * M], zz[8 * M];      // current positions, per (column, member)
+    double zx[8 * M + 1], zy[8 * M + 1], zz[8 * M + 1];   // current positions, per (column, member); + a zero
     double pt[3][8][kColsPairs<M>];              // W r^-3 (x_q - x_a) per column and pair a < q
     unsigned char pa[kColsPairs<M>], pq[kColsPairs<M>];   // the group's pairs (a < q), by a then q
     unsigned char pidx[M <= 16 ? M * M : 1];     // (a, q) -> pair index, both orders
@@ -200,6 +201,51 @@ __device__ __forceinline__ void cols_deriv(const BsArgs &A, ColsShared<M> &S, in
     S.zx[tid] = z[0]; S.zy[tid] = z[1]; S.zz[tid] = z[2];
     __syncthreads();
     f[0] = z[3]; f[1] = z[4]; f[2] = z[5];
+    if constexpr (M == 4) {
+        if (S.npairs == 1) {
+            // two members and their pair in one instruction stream: lane a
+            // (a = 0, 1) takes the star term of member a as the displacement
+            // from a zero slot, lane 2 the pair (0, 1) -- the operations of the
+            // general form below on the same values, so the same results
+            const int a = tid % M;
+            const bool pl = a == 2;
+            const int i1 = col * M + (pl ? 1 : a), i0 = pl ? col * M : 8 * M;
+            const double ex = S.zx[i1] - S.zx[i0], ey = S.zy[i1] - S.zy[i0], ez = S.zz[i1] - S.zz[i0];
+            const double r2 = fma(ez, ez, fma(ey, ey, ex * ex));
+            const double yv = rsqrt_newton(r2);
+            double sst = 0.0;
+            if (pl) {
+                const double d = r2 * yv;
+                const float df = f32_of_f64_trunc(d);
+                double W = 1.0;
+                for (int l = 0; l < A.nlev; l++) {
+                    const int side = changeover_side_f32(df, fminf(S.ircf[l][0], S.ircf[l][1]));
+                    if (side < 0) continue;
+                    if (side > 0) { W = 0.0; break; }
+                    W *= 1.0 - changeover_fast(d, fmin(S.irc[l][0], S.irc[l][1]));
+                }
+                const double c = W * (yv * yv * yv);
+                S.pt[0][col][0] = c * ex;
+                S.pt[1][col][0] = c * ey;
+                S.pt[2][col][0] = c * ez;
+            } else if (active) {
+                sst = -A.mu * (yv * yv * yv);
+            }
+            __syncthreads();
+            if (!active) { f[3] = f[4] = f[5] = 0.0; return; }
+            double px = 0.0, py = 0.0, pz = 0.0;
+            if (!(COLL && !S.alive[a]) && mask) {
+                const double w = a == 0 ? S.m[1] : -S.m[0];
+                px = fma(w, S.pt[0][col][0], px);
+                py = fma(w, S.pt[1][col][0], py);
+                pz = fma(w, S.pt[2][col][0], pz);
+            }
+            f[3] = fma(sst, z[0], A.G * px);
+            f[4] = fma(sst, z[1], A.G * py);
+            f[5] = fma(sst, z[2], A.G * pz);
+            return;
+        }
+    }
     if constexpr (M <= 16) {
         // each pair once; then every member sums its partners' terms in
         // ascending rank order (m_q t for q > a, -m_q t for q < a): exactly
@@ -378,13 +424,11 @@ __device__ void cols_merge(const BsArgs &A, ColsShared<M> &S, int nm, double t, 
     }
 }
 
+// One group g on the whole block.
 template <int M, bool COLL>
-__global__ void __launch_bounds__(8 * M)
-bs_cols_kernel(BsArgs A) {
-    __shared__ ColsShared<M> S;
+__device__ __forceinline__ void cols_group(const BsArgs &A, ColsShared<M> &S, int g) {
     const int tid = threadIdx.x;
     const int col = tid / M, a = tid % M;
-    const int g = A.blist[blockIdx.x];
     const int s0 = A.goff[g], nm = A.goff[g + 1] - s0;
     if (nm > M || (M > 4 && nm <= M / 2)) return;          // not this bucket (never taken)
     const unsigned long long t_start = global_ns();
@@ -445,6 +489,7 @@ bs_cols_kernel(BsArgs A) {
                 }
             }
             S.npairs = np;
+            S.zx[8 * M] = S.zy[8 * M] = S.zz[8 * M] = 0.0;   // the zero slot
         }
     }
     __syncthreads();
@@ -561,10 +606,65 @@ bs_cols_kernel(BsArgs A) {
     }
 }
 
+// Block b takes group b of its bucket, then claims the groups beyond the grid
+// one at a time, until the bucket's count (left on the device by
+// bucket_groups) is reached: the grid need not match the count, so the host
+// launches it without reading the count first.  The first groups keep the
+// block order, which the hardware spreads over the SMs (claims in arrival
+// order would pile some SMs up).  Groups are independent, so which block
+// takes which group does not change any result.
+template <int M, bool COLL>
+__global__ void __launch_bounds__(8 * M)
+bs_cols_kernel(BsArgs A) {
+    __shared__ ColsShared<M> S;
+    __shared__ int claim;
+    for (bool first = true;; first = false) {
+        if (threadIdx.x == 0) {
+            const unsigned q = first ? blockIdx.x : gridDim.x + atomicAdd(&A.ctr->bucket_next[A.bucket], 1u);
+            claim = q < A.ctr->bucket_count[A.bucket] ? A.blist[q] : -1;
+        }
+        __syncthreads();
+        const int g = claim;
+        __syncthreads();                  // claim read by all before it is rewritten
+        if (g < 0) return;
+        cols_group<M, COLL>(A, S, g);
+        __syncthreads();                  // S free for the next group
+    }
+}
+
 
 }  // namespace
 
-cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned counts[kBuckets]) {
+// Resident blocks of one in-block BS instance on the whole GPU (the
+// per-SM figure depends only on the kernel, so it is asked for once).
+template <int M, bool COLL>
+int cols_capacity(const genga_system *s) {
+    static int per_sm = 0;
+    if (per_sm < 1) {
+        int q = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, bs_cols_kernel<M, COLL>, 8 * M, 0) != cudaSuccess)
+            q = 0;
+        per_sm = q < 1 ? 1 : q;
+    }
+    return per_sm * s->num_sms;
+}
+
+template <int M>
+cudaError_t launch_cols(genga_system *s, BsArgs A, int q, const unsigned *counts, bool coll) {
+    const int cap = coll ? cols_capacity<M, true>(s) : cols_capacity<M, false>(s);
+    // with the counts known: one block per group up to the resident capacity;
+    // without: the resident capacity, the blocks claiming the device count
+    const unsigned grid = counts ? std::min<unsigned>(counts[q], (unsigned)cap) : (unsigned)cap;
+    if (grid == 0) return cudaSuccess;
+    A.blist = s->bucket_list + (size_t)q * s->bucket_stride;
+    A.bucket = q;
+    if (coll) bs_cols_kernel<M, true><<<grid, 8 * M, 0, s->side[q]>>>(A);
+    else bs_cols_kernel<M, false><<<grid, 8 * M, 0, s->side[q]>>>(A);
+    ++s->launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned *counts) {
     BsArgs A;
     A.n = (int)s->n;
     A.pre_pos = s->pre_pos[level];
@@ -584,35 +684,10 @@ cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned co
     // their slowest groups overlap
     GENGA_CUDA_TRY(cudaEventRecord(s->ev_fork, s->stream));
     for (int q = 0; q < 4; q++) GENGA_CUDA_TRY(cudaStreamWaitEvent(s->side[q], s->ev_fork, 0));
-    const size_t st = (size_t)s->bucket_stride;
-    if (counts[0]) {
-        A.blist = s->bucket_list;
-        if (coll) bs_cols_kernel<4, true><<<counts[0], 32, 0, s->side[0]>>>(A);
-        else bs_cols_kernel<4, false><<<counts[0], 32, 0, s->side[0]>>>(A);
-        ++s->launches;
-        GENGA_CUDA_TRY(cudaGetLastError());
-    }
-    if (counts[1]) {
-        A.blist = s->bucket_list + st;
-        if (coll) bs_cols_kernel<8, true><<<counts[1], 64, 0, s->side[1]>>>(A);
-        else bs_cols_kernel<8, false><<<counts[1], 64, 0, s->side[1]>>>(A);
-        ++s->launches;
-        GENGA_CUDA_TRY(cudaGetLastError());
-    }
-    if (counts[2]) {
-        A.blist = s->bucket_list + 2 * st;
-        if (coll) bs_cols_kernel<16, true><<<counts[2], 128, 0, s->side[2]>>>(A);
-        else bs_cols_kernel<16, false><<<counts[2], 128, 0, s->side[2]>>>(A);
-        ++s->launches;
-        GENGA_CUDA_TRY(cudaGetLastError());
-    }
-    if (counts[3]) {
-        A.blist = s->bucket_list + 3 * st;
-        if (coll) bs_cols_kernel<32, true><<<counts[3], 256, 0, s->side[3]>>>(A);
-        else bs_cols_kernel<32, false><<<counts[3], 256, 0, s->side[3]>>>(A);
-        ++s->launches;
-        GENGA_CUDA_TRY(cudaGetLastError());
-    }
+    GENGA_CUDA_TRY(launch_cols<4>(s, A, 0, counts, coll));
+    GENGA_CUDA_TRY(launch_cols<8>(s, A, 1, counts, coll));
+    GENGA_CUDA_TRY(launch_cols<16>(s, A, 2, counts, coll));
+    GENGA_CUDA_TRY(launch_cols<32>(s, A, 3, counts, coll));
     return cudaGetLastError();
 }
 

@@ -852,6 +852,23 @@ int run_bs(genga_system *s, int level, double dt_l, int64_t np) {
     return bsm_forward_groups(s, level, dt_l);
 }
 
+int run_bs_dev(genga_system *s, int level, double dt_l) {
+    ++s->bs_call;
+    int rc = phase_mark(s, GENGA_PH_BUCKETS);
+    if (rc != GENGA_OK) return rc;
+    if (bucket_groups_async(s) != cudaSuccess) return GENGA_ECUDA;
+    if ((rc = phase_mark(s, GENGA_PH_BS_SMALL)) != GENGA_OK) return rc;
+    const cudaError_t e = launch_bs(s, level, dt_l, nullptr);
+    if (join_bs(s) != cudaSuccess || e != cudaSuccess) return GENGA_ECUDA;
+    // the counts were copied before the kernels above run: the GPU keeps
+    // working while the host reads them
+    if (cudaEventSynchronize(s->ev_counts) != cudaSuccess) return GENGA_ECUDA;
+    ++s->host_syncs;
+    if (!s->bucket_host[kBuckets - 1]) return GENGA_OK;
+    if ((rc = phase_mark(s, GENGA_PH_BS_LARGE)) != GENGA_OK) return rc;
+    return bsm_forward_groups(s, level, dt_l);
+}
+
 // Adjoint BS (backward, augmented) of every group larger than kBlockGroupMax.
 int bsm_adjoint_groups(genga_system *s, const double *x2, const double *v2, double *lx, double *lv,
                        double *lm, double dt) {

@@ -3,6 +3,7 @@
 // translation units.  Nothing here is part of the public ABI (include/genga.h).
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <algorithm>
@@ -52,6 +53,7 @@ struct DevCounters {
     unsigned long long groups_total;     // groups formed since the last reset
     unsigned long long max_group_total;  // largest of them
     unsigned long long bs_max_attempts;  // most step attempts of one group
+    unsigned long long pair_total[kMaxLevels];   // pairs found at levels whose count stays on the device
     unsigned int err;
     unsigned int ngroups;
     unsigned int max_group;
@@ -59,6 +61,8 @@ struct DevCounters {
     double hc_shift[3];
     unsigned int bucket_count[kBuckets];   // groups per size bucket (bucket_groups)
     unsigned int pad2[8 - kBuckets];
+    unsigned int bucket_next[kBuckets];    // next group of each bucket to claim (persistent BS kernels)
+    unsigned int pad3[8 - kBuckets];
     unsigned long long merge_count;        // records written to the merger log
 };
 
@@ -167,6 +171,9 @@ struct genga_system {
     int *slotof = nullptr;   // n
     int *bucket_list = nullptr;  // kBuckets x bucket_stride group labels per size bucket
     int bucket_stride = 0;       // n / 2 + 1 (groups have at least 2 members)
+    unsigned *bucket_host = nullptr;  // pinned copy of the bucket counts
+    unsigned long long *np_host = nullptr;  // pinned copies of the levels' last pair counts (kMaxLevels)
+    cudaEvent_t ev_counts = nullptr;  // recorded after that copy
     int label_level = -1;    // level whose grouping `label` holds
 
     // batched grid-wide Bulirsch-Stoer buffers (bsm.cu), grown on demand
@@ -296,9 +303,14 @@ cudaError_t launch_kick_raw(const KickRaw &k, int num_sms, int max_nchunk, cudaS
 // encounter.cu
 cudaError_t launch_detect(genga_system *s, const uint2 *in, int64_t nin, int level,
                           uint2 *out, int64_t cap, unsigned long long *count);
-cudaError_t build_csr(genga_system *s, int level, int64_t npairs);
+// npairs: the pair count, or, with npd (the count the detection left on the
+// device), a bound on it that sizes the grids; total: a device sum the count
+// is added to (levels whose count the host does not read); np_hint: with npd,
+// a recent count of the level that picks the row sort.
+cudaError_t build_csr(genga_system *s, int level, int64_t npairs, const unsigned long long *npd = nullptr,
+                      unsigned long long *total = nullptr, int64_t np_hint = 0);
 cudaError_t build_bodies(genga_system *s, int level_pairs, int out_level, int *nb_host);
-cudaError_t build_groups(genga_system *s, int level, int64_t npairs);
+cudaError_t build_groups(genga_system *s, int level, int64_t npairs, const unsigned long long *npd = nullptr);
 cudaError_t exclusive_scan(genga_system *s, const int *in, int *out, int64_t len);
 
 // genga.cu
@@ -318,15 +330,23 @@ int bsm_forward_groups(genga_system *s, int level, double dt_l);
 void bsm_release(genga_system *s);
 // launch_bs and join_bs, then bsm_forward_groups.
 int run_bs(genga_system *s, int level, double dt_l, int64_t np);
+// The same without reading the group counts first: the in-block kernels take
+// the device counts; the host waits only for the counts' copy (made before the
+// kernels run) to decide on the groups larger than kBlockGroupMax.
+int run_bs_dev(genga_system *s, int level, double dt_l);
 int bsm_adjoint_groups(genga_system *s, const double *x2, const double *v2, double *lx, double *lv,
                        double *lm, double dt);
 // Sorts the current groups into the size buckets (device lists + counts) and
 // copies the kBuckets counts to the host (synchronises).
 cudaError_t bucket_groups(genga_system *s, unsigned counts[kBuckets]);
+// The same, the counts copied to s->bucket_host behind the event s->ev_counts
+// (no wait).
+cudaError_t bucket_groups_async(genga_system *s);
 // Launches the in-block BS kernels on the side streams (forked from the
-// system stream), one block per group of each of the first four buckets;
-// join_bs makes the system stream wait for them.
-cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned counts[kBuckets]);
+// system stream) for the first four buckets: with counts, one block per group
+// (up to the resident capacity); without, the resident capacity, the blocks
+// claiming the device counts.  join_bs makes the system stream wait for them.
+cudaError_t launch_bs(genga_system *s, int level, double dt_l, const unsigned *counts);
 cudaError_t join_bs(genga_system *s);
 cudaError_t launch_kick_pairs(genga_system *s, int level, double dt_half, int nb);
 

@@ -155,25 +155,40 @@ __global__ void scan_add_kernel(int *out, long long len, const int *block_sums) 
 }
 
 // ---------------------------------------------------------------- CSR
-__global__ void csr_degree_kernel(const uint2 *pairs, long long np, int *deg) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= np) return;
-    const uint2 p = pairs[k];
-    atomicAdd(&deg[p.x], 1);
-    atomicAdd(&deg[p.y], 1);
+// Pairs in a list: np, or the count the detection left on the device (npd,
+// at most np, the bound the grid was sized for) when the host has not read it.
+__device__ __forceinline__ long long pairs_in(long long np, const unsigned long long *npd) {
+    return npd ? min(np, (long long)*npd) : np;
 }
 
-__global__ void csr_fill_kernel(const uint2 *pairs, long long np, const int *off, int *fill, int *list,
-                                int *lpair) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= np) return;
-    const uint2 p = pairs[k];
-    const int a = off[p.x] + atomicAdd(&fill[p.x], 1);
-    list[a] = (int)p.y;
-    lpair[a] = (int)(2 * k);
-    const int b = off[p.y] + atomicAdd(&fill[p.y], 1);
-    list[b] = (int)p.x;
-    lpair[b] = (int)(2 * k + 1);
+// The pair kernels stride over the list, so that a grid sized for a bound
+// (the count on the device) stays small.
+__global__ void csr_degree_kernel(const uint2 *pairs, long long np, const unsigned long long *npd, int *deg,
+                                  unsigned long long *total) {
+    const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    np = pairs_in(np, npd);
+    if (total && k0 == 0) *total += (unsigned long long)np;
+    for (long long k = k0; k < np; k += stride) {
+        const uint2 p = pairs[k];
+        atomicAdd(&deg[p.x], 1);
+        atomicAdd(&deg[p.y], 1);
+    }
+}
+
+__global__ void csr_fill_kernel(const uint2 *pairs, long long np, const unsigned long long *npd, const int *off,
+                                int *fill, int *list, int *lpair) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    np = pairs_in(np, npd);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride) {
+        const uint2 p = pairs[k];
+        const int a = off[p.x] + atomicAdd(&fill[p.x], 1);
+        list[a] = (int)p.y;
+        lpair[a] = (int)(2 * k);
+        const int b = off[p.y] + atomicAdd(&fill[p.y], 1);
+        list[b] = (int)p.x;
+        lpair[b] = (int)(2 * k + 1);
+    }
 }
 
 // Sorts every row by partner index, carrying the pair index along.  Sparse
@@ -278,18 +293,24 @@ __global__ void uf_init_kernel(int n, int *parent) {
     if (b < n) parent[b] = b;
 }
 
-__global__ void uf_hook_kernel(const uint2 *pairs, long long np, int *parent, DevCounters *ctr) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= np) return;
-    const uint2 p = pairs[k];
+// Joins the sets of one pair's bodies (bounded retries); false if it gave up.
+__device__ bool uf_hook_pair(int *parent, uint2 p) {
     for (int it = 0; it < (1 << 20); it++) {
         const int ru = uf_find(parent, (int)p.x);
         const int rv = uf_find(parent, (int)p.y);
-        if (ru == rv) return;
+        if (ru == rv) return true;
         const int lo = min(ru, rv), hi = max(ru, rv);
-        if (atomicCAS(&parent[hi], hi, lo) == hi) return;
+        if (atomicCAS(&parent[hi], hi, lo) == hi) return true;
     }
-    latch_error(ctr, kErrUnionFind);
+    return false;
+}
+
+__global__ void uf_hook_kernel(const uint2 *pairs, long long np, const unsigned long long *npd, int *parent,
+                               DevCounters *ctr) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    np = pairs_in(np, npd);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += stride)
+        if (!uf_hook_pair(parent, pairs[k])) latch_error(ctr, kErrUnionFind);
 }
 
 __global__ void uf_label_kernel(int n, const int *parent, const int *deg, int *label, int *gsize) {
@@ -349,20 +370,32 @@ cudaError_t launch_detect(genga_system *s, const uint2 *in, int64_t nin, int lev
     return cudaGetLastError();
 }
 
-cudaError_t build_csr(genga_system *s, int level, int64_t np) {
+// Blocks of 256 for a pair kernel over np pairs (a bound when the count is on
+// the device: then at most a few per SM, the kernels striding).
+static unsigned pair_grid(const genga_system *s, int64_t np, const unsigned long long *npd) {
+    const long long g = (np + 255) / 256;
+    return (unsigned)(npd ? std::min<long long>(g, 4LL * s->num_sms) : g);
+}
+
+cudaError_t build_csr(genga_system *s, int level, int64_t np, const unsigned long long *npd,
+                      unsigned long long *total, int64_t np_hint) {
     const int n = (int)s->n;
     Csr &c = s->csr[level];
     GENGA_CUDA_TRY(cudaMemsetAsync(c.deg, 0, sizeof(int) * (n + 1), s->stream));
     GENGA_CUDA_TRY(cudaMemsetAsync(c.fill, 0, sizeof(int) * n, s->stream));
     if (np > 0) {
-        csr_degree_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.deg); ++s->launches;
+        csr_degree_kernel<<<pair_grid(s, np, npd), 256, 0, s->stream>>>(s->pairs[level], np, npd, c.deg,
+                                                                         total); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     GENGA_CUDA_TRY(exclusive_scan(s, c.deg, c.off, n));
     if (np > 0) {
-        csr_fill_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, c.off, c.fill, c.list, c.lpair); ++s->launches;
+        csr_fill_kernel<<<pair_grid(s, np, npd), 256, 0, s->stream>>>(s->pairs[level], np, npd, c.off, c.fill,
+                                                                       c.list, c.lpair); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
-        if (2 * np >= n)         // dense: a warp per row
+        // dense: a warp per row (with the count on the device, judged by a
+        // recent count of the same level; both sorts give the same rows)
+        if (2 * (npd ? np_hint : np) >= n)
             csr_sort_warp_kernel<<<(unsigned)(((long long)n * 32 + 255) / 256), 256, 0, s->stream>>>(
                 n, c.off, c.list, c.lpair, c.ent);
         else
@@ -401,19 +434,31 @@ __global__ void bucket_groups_kernel(const DevCounters *ctr, const int *glist, c
     }
 }
 
-cudaError_t bucket_groups(genga_system *s, unsigned counts[kBuckets]) {
-    GENGA_CUDA_TRY(cudaMemsetAsync(s->ctr->bucket_count, 0, sizeof(unsigned) * kBuckets, s->stream));
+static_assert(offsetof(DevCounters, bucket_next) == offsetof(DevCounters, bucket_count) + 8 * sizeof(unsigned) &&
+                  offsetof(DevCounters, pad3) == offsetof(DevCounters, bucket_next) + kBuckets * sizeof(unsigned),
+              "bucket counts and claim counters must be contiguous");
+
+cudaError_t bucket_groups_async(genga_system *s) {
+    // the counts and the BS kernels' claim counters
+    GENGA_CUDA_TRY(cudaMemsetAsync(s->ctr->bucket_count, 0, 16 * sizeof(unsigned), s->stream));
     bucket_groups_kernel<<<2 * s->num_sms, 256, 0, s->stream>>>(s->ctr, s->glist, s->goff, s->bucket_stride,
                                                                s->bucket_list, s->ctr->bucket_count);
     ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
-    GENGA_CUDA_TRY(cudaMemcpyAsync(counts, s->ctr->bucket_count, sizeof(unsigned) * kBuckets,
+    GENGA_CUDA_TRY(cudaMemcpyAsync(s->bucket_host, s->ctr->bucket_count, sizeof(unsigned) * kBuckets,
                                    cudaMemcpyDeviceToHost, s->stream));
-    ++s->host_syncs;
-    return cudaStreamSynchronize(s->stream);
+    return cudaEventRecord(s->ev_counts, s->stream);
 }
 
-cudaError_t build_groups(genga_system *s, int level, int64_t np) {
+cudaError_t bucket_groups(genga_system *s, unsigned counts[kBuckets]) {
+    GENGA_CUDA_TRY(bucket_groups_async(s));
+    GENGA_CUDA_TRY(cudaEventSynchronize(s->ev_counts));
+    ++s->host_syncs;
+    for (int q = 0; q < kBuckets; q++) counts[q] = s->bucket_host[q];
+    return cudaSuccess;
+}
+
+cudaError_t build_groups(genga_system *s, int level, int64_t np, const unsigned long long *npd) {
     const int n = (int)s->n;
     GENGA_CUDA_TRY(cudaMemsetAsync(s->gsize, 0, sizeof(int) * (n + 1), s->stream));
     GENGA_CUDA_TRY(cudaMemsetAsync(s->gfill, 0, sizeof(int) * (n + 1), s->stream));
@@ -421,7 +466,8 @@ cudaError_t build_groups(genga_system *s, int level, int64_t np) {
     uf_init_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->parent); ++s->launches;
     GENGA_CUDA_TRY(cudaGetLastError());
     if (np > 0) {
-        uf_hook_kernel<<<(unsigned)((np + 255) / 256), 256, 0, s->stream>>>(s->pairs[level], np, s->parent, s->ctr); ++s->launches;
+        uf_hook_kernel<<<pair_grid(s, np, npd), 256, 0, s->stream>>>(s->pairs[level], np, npd, s->parent,
+                                                                      s->ctr); ++s->launches;
         GENGA_CUDA_TRY(cudaGetLastError());
     }
     uf_label_kernel<<<(n + 255) / 256, 256, 0, s->stream>>>(n, s->parent, s->csr[level].deg, s->label, s->gsize); ++s->launches;

@@ -177,6 +177,10 @@ int alloc_all(genga_system *s) {
         CU(cudaEventCreateWithFlags(&s->ev_join[k], cudaEventDisableTiming));
     }
     CU(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&s->ev_counts, cudaEventDisableTiming));
+    CU(cudaMallocHost((void **)&s->bucket_host, sizeof(unsigned) * kBuckets));
+    CU(cudaMallocHost((void **)&s->np_host, sizeof(unsigned long long) * kMaxLevels));
+    for (int l = 0; l < kMaxLevels; l++) s->np_host[l] = 0;
     s->kick_chunk = 0;
     CU(kick_reserve(s));
     s->cand_cap = s->p.cand_capacity > 0 ? s->p.cand_capacity : std::max<int64_t>(1 << 20, 64 * (int64_t)n);
@@ -222,6 +226,12 @@ void free_all(genga_system *s) {
     }
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     s->ev_fork = nullptr;
+    if (s->ev_counts) cudaEventDestroy(s->ev_counts);
+    s->ev_counts = nullptr;
+    if (s->bucket_host) cudaFreeHost(s->bucket_host);
+    s->bucket_host = nullptr;
+    if (s->np_host) cudaFreeHost(s->np_host);
+    s->np_host = nullptr;
     free_marks(s);
 }
 
@@ -312,6 +322,20 @@ int detect(genga_system *s, const uint2 *in, int64_t nin, int level, int64_t *np
     return GENGA_OK;
 }
 
+// Detection at `level` over `in` with the pair count left on the device: the
+// level's list is first made as large as the input (the pairs found are a
+// subset of it), so it cannot overflow and the host need not read the count.
+int detect_dev(genga_system *s, const uint2 *in, int64_t nin, int level) {
+    if (s->pair_cap[level] < nin) TRY(alloc_pairs(s, level, nin + nin / 2 + 1024));
+    CU(launch_detect(s, in, nin, level, s->pairs[level], s->pair_cap[level], &s->ctr->pair_count[level]));
+    s->npairs_host[level] = -1;          // the count is on the device only
+    // a copy for the host, read once a later wait has passed it (it picks
+    // the next partner-list sort; nothing else depends on it)
+    CU(cudaMemcpyAsync(&s->np_host[level], &s->ctr->pair_count[level], sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s->stream));
+    return GENGA_OK;
+}
+
 int bs_groups(genga_system *s, int level, int64_t np, double dt_l) {
     TRY(mark(s, GENGA_PH_GROUPING));
     CU(build_groups(s, level, np));
@@ -333,13 +357,30 @@ int senc(genga_system *s, int level, double dt_l) {
         CU(launch_drift(s, level, dt_l, s->bodies[level], nb));
         int64_t np = 0;
         TRY(mark(s, GENGA_PH_DETECTS));
-        TRY(detect(s, s->pairs[level - 1], s->npairs_host[level - 1], level, &np));
-        s->stats.n_pairs[level] += np;
-        if (np > 0) {
+        if (level == L - 1 && !s->pair_log) {
+            // the deepest level: detection, partner lists, groups and BS take
+            // the pair count from the device (grids sized by the input count),
+            // so the host queues the sub-step without waiting for the GPU
+            const int64_t bound = s->npairs_host[level - 1];
+            const unsigned long long *npd = &s->ctr->pair_count[level];
+            // the previous sub-step's count (its copy was passed by the wait
+            // in that sub-step's run_bs_dev)
+            const int64_t hint = (int64_t)s->np_host[level];
+            TRY(detect_dev(s, s->pairs[level - 1], bound, level));
             TRY(mark(s, GENGA_PH_CSRS));
-            CU(build_csr(s, level, np));
-            if (level < L - 1) TRY(senc(s, level + 1, dt_l / s->p.substeps));
-            else TRY(bs_groups(s, level, np, dt_l));
+            CU(build_csr(s, level, bound, npd, &s->ctr->pair_total[level], hint));
+            TRY(mark(s, GENGA_PH_GROUPING));
+            CU(build_groups(s, level, bound, npd));
+            TRY(run_bs_dev(s, level, dt_l));
+        } else {
+            TRY(detect(s, s->pairs[level - 1], s->npairs_host[level - 1], level, &np));
+            s->stats.n_pairs[level] += np;
+            if (np > 0) {
+                TRY(mark(s, GENGA_PH_CSRS));
+                CU(build_csr(s, level, np));
+                if (level < L - 1) TRY(senc(s, level + 1, dt_l / s->p.substeps));
+                else TRY(bs_groups(s, level, np, dt_l));
+            }
         }
         TRY(mark(s, GENGA_PH_KICKS));
         CU(launch_kick_pairs(s, level, 0.5 * dt_l, nb));
@@ -397,6 +438,7 @@ int collect_stats(genga_system *s) {
     s->stats.bs_rejects = (int64_t)c.bs_rejects;
     s->stats.bs_fail = (int64_t)c.bs_fail;
     s->stats.kepler_fail = (int64_t)c.kepler_fail;
+    for (int l = 0; l < kMaxLevels; l++) s->stats.n_pairs[l] += (int64_t)c.pair_total[l];
     s->stats.kernel_launches = s->launches;
     s->stats.host_syncs = s->host_syncs;
     return GENGA_OK;
@@ -406,7 +448,8 @@ int reset_stats(genga_system *s) {
     memset(&s->stats, 0, sizeof(s->stats));
     s->launches = 0;
     s->host_syncs = 0;
-    CU(cudaMemsetAsync(&s->ctr->kepler_fail, 0, 7 * sizeof(unsigned long long), s->stream));
+    // kepler_fail .. bs_max_attempts and pair_total (contiguous)
+    CU(cudaMemsetAsync(&s->ctr->kepler_fail, 0, (7 + kMaxLevels) * sizeof(unsigned long long), s->stream));
     return GENGA_OK;
 }
 
@@ -687,7 +730,13 @@ int genga_get_candidates(genga_system_t *s, uint32_t *ij, int64_t cap, int64_t *
 
 int genga_get_pairs(genga_system_t *s, int level, uint32_t *ij, int64_t cap, int64_t *n) {
     if (!s || level < 0 || level >= levels_of(s->p)) return GENGA_EINVAL;
-    return copy_pairs_sorted(s, s->pairs[level], s->npairs_host[level], ij, cap, n);
+    int64_t cnt = s->npairs_host[level];
+    if (cnt < 0) {                       // left on the device by the last detection
+        unsigned long long c = 0;
+        TRY(read_dev(s, &c, &s->ctr->pair_count[level]));
+        cnt = std::min<int64_t>((int64_t)c, s->pair_cap[level]);
+    }
+    return copy_pairs_sorted(s, s->pairs[level], cnt, ij, cap, n);
 }
 
 int genga_get_groups(genga_system_t *s, int64_t *label) {

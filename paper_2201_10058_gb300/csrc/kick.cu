@@ -427,9 +427,12 @@ struct SymArgs {
     unsigned long long cand_cap;
 };
 
-// Resident blocks per SM the register allocation must allow (128 threads each).
+// Resident blocks per SM the register allocation must allow (128 threads each):
+// 6 (80 registers) for the mixed form and the FP64 form with the pre-check,
+// without spills; the FP64 form without it needs only 72.  (The mixed form
+// also fits 72 registers, 7 blocks, but ran no faster.)
 constexpr int sym_min_blocks(bool mixed, bool pc) {
-    return mixed ? 5 : (pc ? 5 : 4);
+    return mixed ? 6 : (pc ? 6 : 4);
 }
 
 // Dynamic shared memory: the staged j tile (x, y, z, m, 1/rc; thr, mh, ml),
@@ -853,9 +856,10 @@ double sym_item_cost(int nT, int P, int X, int Y) {
 }
 
 // Items in dispatch order and the predicted makespan (tile-pair units per
-// block).  Only rows X < Xmax: with test particles, a super-range made only of
-// test particles has no pair left with a later one.
-double sym_schedule(int nT, int P, int slots, int Xmax, std::vector<int2> *order) {
+// block), each item also costing `ovh` units of fixed work (its tile loads,
+// partial-sum writes and dispatch).  Only rows X < Xmax: with test particles,
+// a super-range made only of test particles has no pair left with a later one.
+double sym_schedule(int nT, int P, int slots, int Xmax, double ovh, std::vector<int2> *order) {
     const int nS = (nT + P - 1) / P;
     std::vector<std::pair<double, int2>> it;
     it.reserve((size_t)nS * (nS + 1) / 2);
@@ -868,7 +872,7 @@ double sym_schedule(int nT, int P, int slots, int Xmax, std::vector<int2> *order
     for (int k = 0; k < slots; k++) h.push(0.0);
     double ms = 0.0;
     for (const auto &e : it) {
-        const double t = h.top() + e.first;
+        const double t = h.top() + e.first + ovh;
         h.pop();
         h.push(t);
         ms = std::max(ms, t);
@@ -885,8 +889,13 @@ SymPlan sym_plan(int n, int nm, int num_sms, int layout, int req_P) {
     SymPlan best;
     const int nT = (n + kSymT - 1) / kSymT;
     // FP64 instructions per unordered pair (symmetric) and per ordered pair
-    // (kick_kernel), and per partial slot per body in kick_finalize
-    const double c_sym = MIXED ? 9.2 : 21.5, c_old = MIXED ? 6.1 : 17.1, c_fin = 21.0;
+    // (kick_kernel), and per partial slot per body in kick_finalize (15 in its
+    // loop; 17 fits the measured fold, which also streams the slots from DRAM)
+    const double c_sym = MIXED ? 9.2 : 21.5, c_old = MIXED ? 6.1 : 17.1, c_fin = 17.0;
+    // fixed work per item, in FP64-instruction equivalents of one block,
+    // fitted to the mixed kick's measured times over P at N = 65,536 and
+    // 65,540; the FP64 form's measured times follow the model without it
+    const double ovh = MIXED ? 7500.0 / (c_sym * kSymT * kSymT) : 0.0;
     // predicted time in FP64 instructions per SM: kick_kernel at 95 % balance;
     // the symmetric kick's makespan (tile pairs per block, each block at 1/nb
     // of its SM) plus the finalize's slots
@@ -904,14 +913,14 @@ SymPlan sym_plan(int n, int nm, int num_sms, int layout, int req_P) {
             continue;
         const int slots = nb * num_sms;
         const int R = (nm + P * kSymT - 1) / (P * kSymT);
-        const double ms = sym_schedule(nT, P, slots, R, nullptr);
+        const double ms = sym_schedule(nT, P, slots, R, ovh, nullptr);
         const double t = c_sym * (double)kSymT * kSymT * ms * nb + c_fin * (double)nS * n / num_sms;
         if (t < t_best) {
             t_best = t;
             best.P = P; best.nS = nS; best.blocks = slots; best.R = R;
         }
     }
-    if (best.P) sym_schedule(nT, best.P, best.blocks, best.R, &best.items);
+    if (best.P) sym_schedule(nT, best.P, best.blocks, best.R, ovh, &best.items);
     return best;
 }
 
