@@ -50,19 +50,20 @@ FP64_OPS_PER_PAIR = {("mixed", "tiled"): 6, ("fp64", "tiled"): 17,
 # The same counted by ncu on one launch at N = 65,536 (thread-level
 # smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum / N^2, and the
 # warp-level sm__inst_executed_pipe_fp64.sum x 32 / N^2, which also charges the
-# idle lanes of partly predicated warps); None where the kernel has changed
-# since the count
+# idle lanes of partly predicated warps); the mixed symmetric kick at the
+# bench's N = 65,540 per interaction N (N - 1), where the padding of the last
+# 128-body tile adds 0.4 % (4.553 at N = 65,536, thread and warp level alike);
+# None where the kernel has changed since the count
 FP64_INSTR_PER_PAIR_COUNTED = {("mixed", "tiled"): (6.152, 6.383), ("fp64", "tiled"): (17.091, 17.402),
-                               ("mixed", "symmetric"): (4.552, 4.552), ("fp64", "symmetric"): (10.549, 10.605)}
+                               ("mixed", "symmetric"): (4.571, 4.571), ("fp64", "symmetric"): (10.549, 10.605)}
 # FP64 units per SM: GB300's nominal FP64 rate (1.25 TFLOP/s = 0.625 T FMA/s
 # over 152 SMs at ~2.06 GHz) is 2 FP64 operations per clock per SM; ncu's FP64
 # pipe utilisation is relative to this rate
 FP64_OPS_PER_CLK_PER_SM = 2
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the mixed
-# symmetric kick kernel at N = 65,536 (P = 5, 103 partial slots: the traffic is
-# the partial sums, the same at N = 65,540); None when the kernel has changed
-# since the capture
-KICK_MIXED_DRAM_BYTES = 275483904
+# symmetric kick kernel at N = 65,540 (P = 4, 129 partial slots: the traffic is
+# the partial sums); None when the kernel has changed since the capture
+KICK_MIXED_DRAM_BYTES = 358854400
 
 
 def parse():
@@ -423,7 +424,7 @@ def run_ours(args, dist: Dist) -> dict | None:
                      "frac": round(achieved / peak, 4),
                      "traffic": KICK_MIXED_DRAM_BYTES,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch "
-                                       "of this kernel (no pre-check) at N=65536, P=5: the partial sums",
+                                       "of this kernel (no pre-check) at N=65540, P=4: the partial sums",
                      "ops_per_pair": ops,
                      "kick_layout": head["kick_layout"],
                      "duration_basis": "CUDA events on the system's stream around genga_kick writing the "
