@@ -510,6 +510,39 @@ def test_bench_disk_full_step_matches_oracle(g, precision, tol):
                         verr.max(), tol)
     assert err.max() <= tol, err.max()
     assert verr.max() <= tol, verr.max()
+    # the pair log makes the host read every level's count; bench.py runs without
+    # it, the deepest level then keeping its counts on the device: the same step
+    # that way gives the same state, bit for bit
+    s2, pos2, vel2, _ = _system(g, wl, precision)
+    s2.step(1)
+    np.testing.assert_array_equal(_host(pos2), _host(pos))
+    np.testing.assert_array_equal(_host(vel2), _host(vel))
+    assert s2.stats()["n_pairs"] == st["n_pairs"]
+
+
+@pytest.mark.parametrize("slevels,substeps", [(2, 10), (3, 2)])
+def test_device_counts_match_host_counts(g, slevels, substeps):
+    """The deepest level takes its pair and group counts from the device: its
+    list sized to its input, the partner-list and grouping kernels reading the
+    detection's count, the in-block Bulirsch-Stoer kernels claiming their
+    bucket's groups.  With the pair log on, the host reads every count and sizes
+    every launch from it.  Three steps of the dense disk both ways: the same
+    positions and velocities bit for bit, the same last pair list of the deepest
+    level, the same pair totals per level."""
+    wl = disk(2048, 0.5, 1.0, 2.0, 11, name="dense", slevels=slevels, substeps=substeps)
+    out = []
+    for log in (True, False):
+        s, pos, vel, _ = _system(g, wl, 0)
+        s.set_pair_log(log)
+        s.step(3)
+        out.append((_host(pos), _host(vel), s.pairs(slevels - 1), s.stats()))
+    (p1, v1, l1, st1), (p2, v2, l2, st2) = out
+    np.testing.assert_array_equal(p1, p2)
+    np.testing.assert_array_equal(v1, v2)
+    assert len(l1) > 0
+    np.testing.assert_array_equal(l1, l2)
+    assert st1["n_pairs"] == st2["n_pairs"] and st1["n_pairs"][slevels - 1] > 0
+    assert st1["n_groups"] == st2["n_groups"] and st1["bs_steps"] == st2["bs_steps"]
 
 
 def test_energy_matches_oracle(g):
