@@ -427,6 +427,239 @@ __global__ void __launch_bounds__(kABs) bs_adjoint_kernel(AdjBsArgs A) {
     }
 }
 
+// ------------------------------------------------------------ BS adjoint, column-parallel
+// The same integration for groups of at most M <= 16 members with the 8
+// extrapolation columns of an attempt advanced at once (as bs_cols_kernel does
+// for the forward ODE): thread (k, a) takes column k for member a, so an
+// attempt costs at most 16 sequential derivative evaluations instead of
+// 1 + 2 + 4 + ... + 16.  The arithmetic is the serial kernel's (the same
+// derivative with the partners in ascending body order, the same midpoint,
+// smoothing and Neville expressions, the same acceptance test); the column of
+// an attempt's first converged extrapolation is taken as there.
+template <int M>
+struct AdjColsShared {
+    double zp[6][8 * M];            // per (column, member): x, y, z, lv of the current state
+    double y[kAD][M], f0[6][M];     // attempt start (accepted state) and its derivative (y part)
+    double zf[3][kAD][M];           // the completing column's z_n, z_{n-1}, f(z_n)
+    double hcol[8];
+    double m[M], irc[M];
+    unsigned pmask[M];
+    int rank_of_slot[M];
+    int stop;
+};
+
+// Derivative (reversed time) of member a's augmented state z in column col;
+// the partners' positions and lv from the column's shared copy.
+template <int M>
+__device__ __forceinline__ void adj_cols_deriv(const AdjBsArgs &A, const AdjColsShared<M> &S, int col, int a,
+                                               unsigned pmask, const double (&z)[kAD], double (&f)[kAD]) {
+    const double x = z[0], y = z[1], zz = z[2];
+    const double lvx = z[9], lvy = z[10], lvz = z[11];
+    const double mb = S.m[a];
+    const double r2 = fma(zz, zz, fma(y, y, x * x));
+    const double ir = rsqrt_newton(r2), ir2 = ir * ir, mir3 = A.mu * (ir2 * ir);
+    double ax = -mir3 * x, ay = -mir3 * y, az = -mir3 * zz;
+    const double c3 = 3.0 * fma(zz, lvz, fma(y, lvy, x * lvx)) * ir2;
+    const double tx = -mir3 * (lvx - c3 * x);
+    const double ty = -mir3 * (lvy - c3 * y);
+    const double tz = -mir3 * (lvz - c3 * zz);
+    double px = 0.0, py = 0.0, pz = 0.0, gx = 0.0, gy = 0.0, gz = 0.0, gm = 0.0;
+    const double ircb = S.irc[a];
+    unsigned mm = pmask;
+    while (mm) {
+        const int q = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const int l = col * M + q;
+        const double dx = S.zp[0][l] - x, dy = S.zp[1][l] - y, dz = S.zp[2][l] - zz;
+        const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double id = rsqrt_newton(d2), id2 = id * id, id3 = id2 * id;
+        double K, dK;
+        changeover_fast_dr(d2 * id, fmin(ircb, S.irc[q]), K, dK);
+        const double W = 1.0 - K;
+        const double mp = S.m[q];
+        const double mw = mp * W * id3;
+        px = fma(mw, dx, px); py = fma(mw, dy, py); pz = fma(mw, dz, pz);
+        const double qx = S.zp[3][l], qy = S.zp[4][l], qz = S.zp[5][l];
+        const double e0 = mb * qx - mp * lvx, e1 = mb * qy - mp * lvy, e2 = mb * qz - mp * lvz;
+        const double de = fma(dz, e2, fma(dy, e1, dx * e0));
+        const double aa = W * id3;
+        const double bb = (-3.0 * W * id3 - dK * id2) * id2 * de;
+        gx += aa * e0 + bb * dx; gy += aa * e1 + bb * dy; gz += aa * e2 + bb * dz;
+        gm -= W * fma(qz, dz, fma(qy, dy, qx * dx)) * id3;
+    }
+    ax += A.G * px; ay += A.G * py; az += A.G * pz;
+    f[0] = -z[3]; f[1] = -z[4]; f[2] = -z[5];
+    f[3] = -ax; f[4] = -ay; f[5] = -az;
+    f[6] = tx + A.G * gx; f[7] = ty + A.G * gy; f[8] = tz + A.G * gz;
+    f[9] = z[6]; f[10] = z[7]; f[11] = z[8];
+    f[12] = A.G * gm;
+}
+
+// Row k of the Neville table of one component (T in place, cur the column's
+// smoothed value), with the serial kernel's expressions; returns T_kk, T_k,k-1.
+template <int K>
+__device__ __forceinline__ void adj_neville_k(double (&T)[8], double cur, double &diag, double &prevdiag) {
+    double prev = T[0];
+    T[0] = cur;
+#pragma unroll
+    for (int j = 1; j <= K; j++) {
+        const double coef = (double)((K - j + 1) * (K - j + 1)) / (double)(j * (2 * K + 2 - j));
+        const double nxt = fma(cur - prev, coef, cur);
+        prev = T[j];
+        T[j] = nxt;
+        cur = nxt;
+    }
+    diag = T[K];
+    prevdiag = T[K >= 1 ? K - 1 : 0];
+}
+__device__ __forceinline__ void adj_neville(int k, double (&T)[8], double cur, double &diag, double &prevdiag) {
+    switch (k) {
+    case 0: adj_neville_k<0>(T, cur, diag, prevdiag); break;
+    case 1: adj_neville_k<1>(T, cur, diag, prevdiag); break;
+    case 2: adj_neville_k<2>(T, cur, diag, prevdiag); break;
+    case 3: adj_neville_k<3>(T, cur, diag, prevdiag); break;
+    case 4: adj_neville_k<4>(T, cur, diag, prevdiag); break;
+    case 5: adj_neville_k<5>(T, cur, diag, prevdiag); break;
+    case 6: adj_neville_k<6>(T, cur, diag, prevdiag); break;
+    default: adj_neville_k<7>(T, cur, diag, prevdiag); break;
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(8 * M) bs_adj_cols_kernel(AdjBsArgs A) {
+    __shared__ AdjColsShared<M> S;
+    const int tid = threadIdx.x;
+    const int col = tid / M, a = tid % M;
+    const int g = A.blist[blockIdx.x];
+    const int s0 = A.goff[g], nm = A.goff[g + 1] - s0;
+    if (nm > M || (M > 4 && nm <= M / 2)) return;          // not this bucket (never taken)
+    const size_t N = (size_t)A.n;
+    // member of rank a (ascending body index)
+    if (tid < M) {
+        const int mine = (a < nm) ? A.member[s0 + a] : 0x7fffffff;
+        int rank = 0;
+        for (int q = 0; q < nm; q++) rank += (A.member[s0 + q] < mine);
+        if (a < nm) S.rank_of_slot[a] = rank;
+    }
+    __syncthreads();
+    const bool active = a < nm;
+    int b = 0;
+    if (active)
+        for (int q = 0; q < nm; q++)
+            if (S.rank_of_slot[q] == a) b = A.member[s0 + q];
+    unsigned pmask = 0;
+    if (active)
+        for (int q = A.off[b]; q < A.off[b + 1]; q++) pmask |= 1u << S.rank_of_slot[A.slotof[A.list[q]] - s0];
+    if (col == 0) {
+        S.m[a] = active ? A.mass[b] : 0.0;
+        S.irc[a] = active ? A.irc[b] : 0.0;
+        for (int c = 0; c < 3; c++) {
+            S.y[c][a] = active ? A.x2[c * N + b] : 0.0;
+            S.y[3 + c][a] = active ? A.v2[c * N + b] : 0.0;
+            S.y[6 + c][a] = active ? A.lx[c * N + b] : 0.0;
+            S.y[9 + c][a] = active ? A.lv[c * N + b] : 0.0;
+        }
+        S.y[12][a] = 0.0;
+    }
+    // the Neville lanes: component c0 = col (and c1 = col + 8 while < kAD) of member a
+    const int c0 = col, c1 = col + 8;
+    const bool has1 = c1 < kAD;
+    double T0[8], T1[8];
+    double sc0 = 1.0, sc1 = 1.0, d0 = 0.0, d1 = 0.0;
+    const int nk = 2 * (col + 1);
+    double t = 0.0, H = A.dt;
+    int attempts = 0;
+    bool failed = false;
+    __syncthreads();
+    while (t < A.dt) {
+        if (tid == 0) S.stop = attempts >= A.max_steps;
+        __syncthreads();
+        if (S.stop) { failed = true; break; }
+        attempts++;
+        if (H > A.dt - t) H = A.dt - t;
+        double zm[kAD], zn[kAD], fz[kAD];
+        // the attempt's start and its derivative, in every column
+#pragma unroll
+        for (int c = 0; c < kAD; c++) zm[c] = S.y[c][a];
+        S.zp[0][tid] = zm[0]; S.zp[1][tid] = zm[1]; S.zp[2][tid] = zm[2];
+        S.zp[3][tid] = zm[9]; S.zp[4][tid] = zm[10]; S.zp[5][tid] = zm[11];
+        __syncthreads();
+        adj_cols_deriv<M>(A, S, col, a, pmask, zm, fz);
+        if (col == 0)
+#pragma unroll
+            for (int c = 0; c < 6; c++) S.f0[c][a] = fz[c];
+        const double h = H / nk;
+        if (a == 0) S.hcol[col] = h;
+#pragma unroll
+        for (int c = 0; c < kAD; c++) zn[c] = zm[c] + h * fz[c];
+        int kconv = -1;
+        for (int it = 1; it <= 16; it++) {
+            __syncthreads();                          // the previous reads of zp are done
+            S.zp[0][tid] = zn[0]; S.zp[1][tid] = zn[1]; S.zp[2][tid] = zn[2];
+            S.zp[3][tid] = zn[9]; S.zp[4][tid] = zn[10]; S.zp[5][tid] = zn[11];
+            __syncthreads();
+            adj_cols_deriv<M>(A, S, col, a, pmask, zn, fz);
+            if (it < nk) {
+#pragma unroll
+                for (int c = 0; c < kAD; c++) {
+                    const double tt = zm[c] + 2.0 * h * fz[c];
+                    zm[c] = zn[c];
+                    zn[c] = tt;
+                }
+            } else if (it == nk) {
+#pragma unroll
+                for (int c = 0; c < kAD; c++) {
+                    S.zf[0][c][a] = zn[c];
+                    S.zf[1][c][a] = zm[c];
+                    S.zf[2][c][a] = fz[c];
+                }
+            }
+            if (it & 1) continue;
+            const int k = it / 2 - 1;                 // column just completed
+            __syncthreads();
+            bool ok = true;
+            if (active) {
+                const double hk = S.hcol[k];
+                if (k == 0) {
+                    if (c0 < 6) sc0 = fabs(S.y[c0][a]) + fabs(H * S.f0[c0][a]) + 1e-300;
+                    if (has1 && c1 < 6) sc1 = fabs(S.y[c1][a]) + fabs(H * S.f0[c1][a]) + 1e-300;
+                }
+                double p0 = 0.0, p1 = 0.0;
+                adj_neville(k, T0, 0.5 * (S.zf[0][c0][a] + S.zf[1][c0][a] + hk * S.zf[2][c0][a]), d0, p0);
+                if (k >= 1 && c0 < 6) ok = fabs(d0 - p0) / sc0 <= A.tol;
+                if (has1) {
+                    adj_neville(k, T1, 0.5 * (S.zf[0][c1][a] + S.zf[1][c1][a] + hk * S.zf[2][c1][a]), d1, p1);
+                    if (k >= 1 && c1 < 6) ok = ok && fabs(d1 - p1) / sc1 <= A.tol;
+                }
+            }
+            if (k >= 1 && __syncthreads_and(ok)) { kconv = k; break; }
+        }
+        __syncthreads();                              // every read of S.y is done
+        if (kconv >= 0) {
+            if (active) {
+                S.y[c0][a] = d0;
+                if (has1) S.y[c1][a] = d1;
+            }
+            t += H;
+            if (kconv < 4) H *= 1.5;
+        } else {
+            H *= 0.5;
+        }
+        __syncthreads();
+    }
+    if (active && col == 0) {
+        for (int c = 0; c < 3; c++) {
+            A.lx[c * N + b] = S.y[6 + c][a];
+            A.lv[c * N + b] = S.y[9 + c][a];
+        }
+        A.lm[b] += S.y[12][a];
+    }
+    if (tid == 0 && failed) {
+        atomicAdd(&A.ctr->bs_fail, 1ull);
+        latch_error(A.ctr, kErrBS);
+    }
+}
+
 }  // namespace
 
 // ============================================================== host driver
@@ -630,7 +863,11 @@ int step_vjp(genga_system *s, int64_t k, const double *start, double *lx, double
         for (int b = 0; b < kBuckets - 1; b++) {
             if (!counts[b]) continue;
             B.blist = s->bucket_list + (size_t)b * s->bucket_stride;
-            bs_adjoint_kernel<<<counts[b], kABs, 0, s->stream>>>(B);
+            // groups of up to 16 members: the columns of an attempt at once
+            if (b == 0) bs_adj_cols_kernel<4><<<counts[b], 32, 0, s->stream>>>(B);
+            else if (b == 1) bs_adj_cols_kernel<8><<<counts[b], 64, 0, s->stream>>>(B);
+            else if (b == 2) bs_adj_cols_kernel<16><<<counts[b], 128, 0, s->stream>>>(B);
+            else bs_adjoint_kernel<<<counts[b], kABs, 0, s->stream>>>(B);
             ++s->launches;
             ACU(cudaGetLastError());
         }
