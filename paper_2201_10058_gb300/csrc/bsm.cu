@@ -765,14 +765,15 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     s->launches += 3;
     if (cudaGetLastError() != cudaSuccess) return GENGA_ECUDA;
 
-    // one persistent cooperative launch: at most 2 blocks per SM, and no more
-    // blocks than the (column, member) items need
+    // one persistent cooperative launch: as many blocks as fit on the GPU (more
+    // warps to hide the partner reads from L2 outweigh the barrier's extra
+    // arrivals), and no more than the (column, member) items need
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bsm_persistent_kernel<Ode>, kPThreads, 0) !=
             cudaSuccess || per_sm < 1)
         return GENGA_ECUDA;
     const long long want = (8LL * M * kLanes + kPThreads - 1) / kPThreads;
-    const long long cap = (long long)std::min(per_sm, 2) * s->num_sms;
+    const long long cap = (long long)per_sm * s->num_sms;
     const unsigned grid = (unsigned)std::max(1LL, std::min(want, cap));
     void *args[] = {&A};
     if (cudaLaunchCooperativeKernel((const void *)bsm_persistent_kernel<Ode>, dim3(grid), dim3(kPThreads), args,
