@@ -167,6 +167,21 @@ int genga_set_kick_layout(genga_system_t *sys, int32_t layout, int32_t P);
 int genga_get_kick_layout(genga_system_t *sys, int32_t *layout, int32_t *P, int32_t *slots,
                           int32_t *blocks);
 
+/* ---- derivative form of the batched Bulirsch-Stoer (Sec. 6.1, groups of
+ * more than 32 members) ------------------------------------------------------ */
+#define GENGA_BS_PAIRS_AUTO  0  /* pair-centric where a sub-step phase takes several passes */
+#define GENGA_BS_PAIRS_OFF   1  /* every member evaluates its partner terms */
+#define GENGA_BS_PAIRS_ON    2  /* every pair once per column, its terms to both members */
+
+/* Selects how the persistent Bulirsch-Stoer kernel forms the group ODE's
+ * derivative (forward integration without collisions; the adjoint and the
+ * collision variant always take the member form).  The pair form evaluates
+ * each partner pair once per extrapolation column and writes its two terms
+ * into the two partner-list entries, which the members then sum with the
+ * member form's lanes and order: the results are bit-identical in every mode,
+ * only the time differs.  Errors: EINVAL.                                    */
+int genga_set_bs_pair_mode(genga_system_t *sys, int32_t mode);
+
 /* Eq. Hc (Appendix A "HC(dt/2)"): x_i += dt_half * (sum_j m_j v_j) / m_star,
  * the momentum summed in a fixed order.                                     */
 int genga_hc(genga_system_t *sys, double dt_half);

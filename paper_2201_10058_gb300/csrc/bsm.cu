@@ -10,6 +10,10 @@
 //   sub-step   it = 1..16 moves every column whose n_k = 2(k+1) still has
 //              sub-steps left, over all (column, member) pairs (ping-pong
 //              state buffers, so partner reads never race with writes);
+//              for large batches of the forward ODE a pair phase first
+//              evaluates each partner pair once per column and writes its two
+//              terms to the pair's partner-list entries, which the sub-step
+//              then sums per member (the same values, in the same order);
 //   Neville    per (component, member): the extrapolation table, its
 //              diagonal, and each column's error folded into the group's 8
 //              error words (atomic max on the bits of non-negative doubles);
@@ -82,6 +86,15 @@ struct BsmArgs {
     double *mmass_rw;              // = mmass, written by mergers
     int *gseq;                     // [ng] mergers of each group so far
     DevCounters *ctr;
+    // pair-centric derivative (forward ODE without collisions, large batches):
+    // each unordered pair once per column, its two terms written to the two
+    // partner-list entries, then summed per member
+    int pairs;                     // 1: this mode
+    const int *pcount;             // pairs listed
+    const int *pq, *pm;            // [pairs] entry q (member m -> partner) and member m, partner > m
+    const int *prev;               // [entries] the reverse entry of each entry of a batched member
+    double2 *rec;                  // [8][entries][2]: (c, dx), (dy, dz) of each entry per column
+    size_t nq;                     // entries (the stride of rec per column)
 };
 
 __device__ __forceinline__ double ldc(const double *p) { return __ldcg(p); }
@@ -190,6 +203,26 @@ struct FwdOdeT {
         f[3] = fma(sst, x, A.G * px); f[4] = fma(sst, y, A.G * py); f[5] = fma(sst, z, A.G * pz);
     }
 };
+// The forward derivative of member m in column k from the entries' records
+// (pair-centric mode): the same terms, summed in the same lane split and order.
+__device__ __forceinline__ void fwd_deriv_rec(const BsmArgs &A, const double *Z, int k, int m, int lane,
+                                              double *f) {
+    const size_t ld = (size_t)A.M;
+    const double x = ldc(&Z[0 * ld + m]), y = ldc(&Z[1 * ld + m]), z = ldc(&Z[2 * ld + m]);
+    const double2 *R = A.rec + (size_t)k * 2 * A.nq;
+    double px = 0.0, py = 0.0, pz = 0.0;
+    for (int q = A.mq0[m] + lane; q < A.mq1[m]; q += kLanes) {
+        const double2 u = __ldcg(&R[2 * (size_t)q]), w = __ldcg(&R[2 * (size_t)q + 1]);
+        px = fma(u.x, u.y, px); py = fma(u.x, w.x, py); pz = fma(u.x, w.y, pz);
+    }
+    px = lane_sum(px); py = lane_sum(py); pz = lane_sum(pz);
+    const double r2 = fma(z, z, fma(y, y, x * x));
+    const double ys = rsqrt_newton(r2);
+    const double sst = -A.mu * (ys * ys * ys);
+    f[0] = ldc(&Z[3 * ld + m]); f[1] = ldc(&Z[4 * ld + m]); f[2] = ldc(&Z[5 * ld + m]);
+    f[3] = fma(sst, x, A.G * px); f[4] = fma(sst, y, A.G * py); f[5] = fma(sst, z, A.G * pz);
+}
+
 using FwdOde = FwdOdeT<false>;
 using FwdCollOde = FwdOdeT<true>;
 
@@ -287,7 +320,12 @@ __device__ void phase_substep(const BsmArgs &A, long long t, int it, int lane) {
     double *ZM = A.ZM + k * blk;
     const double h = step_of(A, g) / nk;
     double f[D];
-    Ode::deriv(A, Zcur, m, lane, f);
+    if constexpr (D == 6 && !Ode::COLL) {
+        if (A.pairs) fwd_deriv_rec(A, Zcur, k, m, lane, f);
+        else Ode::deriv(A, Zcur, m, lane, f);
+    } else {
+        Ode::deriv(A, Zcur, m, lane, f);
+    }
     if (lane != 0) return;
     if (it < nk) {
         for (int c = 0; c < D; c++) {
@@ -300,6 +338,36 @@ __device__ void phase_substep(const BsmArgs &A, long long t, int it, int lane) {
         for (int c = 0; c < D; c++)
             A.OUT[k * blk + c * ld + m] = 0.5 * (ldc(&Zcur[c * ld + m]) + ldc(&ZM[c * ld + m]) + h * f[c]);
     }
+}
+
+// Pair-centric mode, before each sub-step: pair t of column k computes the
+// terms member m's partner loop would (displacement from m to its partner p,
+// W, m_p W / r^3) and those p's would (the displacement negated, exactly, and
+// m_m W / r^3), into the records of entries m -> p and p -> m.
+__device__ void phase_pairs(const BsmArgs &A, long long t, long long P, int it) {
+    const int k = (int)(t / P);
+    const long long pi = t - (long long)k * P;
+    if (it > 2 * (k + 1)) return;
+    const int q = A.pq[pi], m = A.pm[pi];
+    if (ldc(&A.gstat[A.mgroup[m]]) != 0) return;
+    const int sp = A.pidx[q], q2 = A.prev[q];
+    const size_t ld = (size_t)A.M, blk = 6 * ld;
+    const double *Z = ((it & 1) ? A.ZA : A.ZB) + k * blk;
+    const double x = ldc(&Z[0 * ld + m]), y = ldc(&Z[1 * ld + m]), z = ldc(&Z[2 * ld + m]);
+    const double dx = ldc(&Z[0 * ld + sp]) - x, dy = ldc(&Z[1 * ld + sp]) - y, dz = ldc(&Z[2 * ld + sp]) - z;
+    const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const double yv = rsqrt_newton(d2);
+    const double d = d2 * yv;
+    double W = 1.0;
+    for (int l = 0; l < A.nlev; l++)
+        W *= 1.0 - changeover_fast(d, fmin(A.irc[(size_t)l * ld + m], A.irc[(size_t)l * ld + sp]));
+    const double cm = A.mmass[sp] * W * (yv * yv * yv);
+    const double cp = A.mmass[m] * W * (yv * yv * yv);
+    double2 *R = A.rec + (size_t)k * 2 * A.nq;
+    R[2 * (size_t)q] = make_double2(cm, dx);
+    R[2 * (size_t)q + 1] = make_double2(dy, dz);
+    R[2 * (size_t)q2] = make_double2(cp, -dx);
+    R[2 * (size_t)q2 + 1] = make_double2(-dy, -dz);
 }
 
 // Neville for item t; called by every lane of a warp (the reductions need all
@@ -469,6 +537,8 @@ bsm_persistent_kernel(BsmArgs A) {
     // derivative phases: kLanes adjacent lanes per item (blockDim is a multiple of 32)
     const long long item0 = tid / kLanes, nitem = nth / kLanes;
     const int lane = (int)(threadIdx.x % kLanes);
+    // pairs of the pair-centric mode (listed by bsm_pairs_kernel before the launch)
+    const long long P = (D == 6 && !Ode::COLL && A.pairs) ? (long long)*A.pcount : 0;
     __shared__ unsigned running;
     if (Ode::COLL) {
         // pairs already overlapping when the integration starts merge at once
@@ -483,6 +553,10 @@ bsm_persistent_kernel(BsmArgs A) {
         for (long long t = item0; t < M; t += nitem) phase_start<Ode>(A, (int)t, lane);
         if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
         for (int it = 1; it <= 16; it++) {
+            if (P > 0) {
+                for (long long t = tid; t < 8 * P; t += nth) phase_pairs(A, t, P, it);
+                if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
+            }
             for (long long t = item0; t < 8 * M; t += nitem) phase_substep<Ode>(A, t, it, lane);
             if (!grid_barrier(A.bar, A.barrier_ns, A.barrier_absent)) return;
         }
@@ -530,6 +604,30 @@ __global__ void bsm_members_kernel(int ng, const int *gbase, const int *gslot0, 
     // partners belong to the same group (connected components of the pair graph)
     for (int q = q0; q < q1; q++) pidx[q] = gbase[lo] + (slotof[list[q]] - gslot0[lo]);
     for (int l = 0; l < nlev; l++) irc[(size_t)l * M + m] = 1.0 / rc.p[l][b];
+}
+
+// Pair-centric mode: the unordered pairs of the batched members (each listed
+// from its lower member, in any order) and every entry's reverse entry (the
+// rows are ascending in body index, so a binary search finds it).
+__global__ void bsm_pairs_kernel(int M, const int *mq0, const int *mq1, const int *pidx, const int *mbody,
+                                 const int *list, int *pcount, int *pq, int *pm, int *prev) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int bm = mbody[m];
+    for (int q = mq0[m]; q < mq1[m]; q++) {
+        const int p = pidx[q];
+        int lo = mq0[p], hi = mq1[p] - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (list[mid] < bm) lo = mid + 1; else hi = mid;
+        }
+        prev[q] = lo;
+        if (p > m) {
+            const int k = atomicAdd(pcount, 1);
+            pq[k] = q;
+            pm[k] = m;
+        }
+    }
 }
 
 // Collisions: each member's alive flag, and the members of each group by
@@ -706,7 +804,26 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     gbase[ng] = M;
     const size_t blk = (size_t)D * M;
     const size_t nq = 2 * (size_t)s->csr[level].cap;
-    const size_t bytes = aligned(sizeof(double) * blk) * 3 + aligned(sizeof(double) * 8 * blk) * 5 +
+    // one persistent cooperative launch: as many blocks as fit on the GPU (more
+    // warps to hide the partner reads from L2 outweigh the barrier's extra
+    // arrivals), and no more than the (column, member) items need
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bsm_persistent_kernel<Ode>, kPThreads, 0) !=
+            cudaSuccess || per_sm < 1)
+        return GENGA_ECUDA;
+    const long long want = (8LL * M * kLanes + kPThreads - 1) / kPThreads;
+    const long long cap = (long long)per_sm * s->num_sms;
+    const unsigned grid = (unsigned)std::max(1LL, std::min(want, cap));
+    // pair-centric derivative where a sub-step phase takes more than two passes
+    // over its (column, member) items: there the FP64 work of the partner
+    // terms, halved, outweighs a second barrier per sub-step
+    const bool pairs = D == 6 && !Ode::COLL &&
+                       (s->bs_pairs == GENGA_BS_PAIRS_ON ||
+                        (s->bs_pairs == GENGA_BS_PAIRS_AUTO && 8LL * M > 2LL * grid * (kPThreads / kLanes)));
+    const size_t pbytes = pairs ? aligned(sizeof(double2) * 2 * 8 * nq) + aligned(sizeof(int) * nq) * 3 +
+                                      aligned(sizeof(int))
+                                : 0;
+    const size_t bytes = pbytes + aligned(sizeof(double) * blk) * 3 + aligned(sizeof(double) * 8 * blk) * 5 +
                          aligned(sizeof(double) * (size_t)nlev * M) + aligned(sizeof(double) * M) +
                          aligned(sizeof(int) * M) * 4 + aligned(sizeof(int) * nq) +
                          aligned(sizeof(int) * (ng + 1)) + aligned(sizeof(int) * ng) * 4 +
@@ -718,6 +835,18 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     if (!p) return GENGA_ENOMEM;
     BsmArgs A;
     A.M = M; A.ng = ng; A.nlev = nlev;
+    A.pairs = pairs ? 1 : 0;
+    A.nq = nq;
+    int *pcount = nullptr, *pq = nullptr, *pm = nullptr, *prev = nullptr;
+    A.rec = nullptr;
+    if (pairs) {
+        A.rec = carve<double2>(p, 2 * 8 * nq);
+        pq = carve<int>(p, nq);
+        pm = carve<int>(p, nq);
+        prev = carve<int>(p, nq);
+        pcount = carve<int>(p, 1);
+    }
+    A.pcount = pcount; A.pq = pq; A.pm = pm; A.prev = prev;
     A.Y = carve<double>(p, blk); A.F0 = carve<double>(p, blk); A.SC = carve<double>(p, blk);
     A.ZM = carve<double>(p, 8 * blk); A.ZA = carve<double>(p, 8 * blk); A.ZB = carve<double>(p, 8 * blk);
     A.OUT = carve<double>(p, 8 * blk); A.DIAG = carve<double>(p, 8 * blk);
@@ -757,6 +886,11 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
                                           s->csr[level].list, s->mass, rcp, nlev, M, mbody, mgroup, mq0, mq1,
                                           pidx, mmass, irc);
     bsm_init_groups_kernel<<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(A);
+    if (pairs) {
+        if (cudaMemsetAsync(pcount, 0, sizeof(int), st) != cudaSuccess) return GENGA_ECUDA;
+        bsm_pairs_kernel<<<gm, 128, 0, st>>>(M, mq0, mq1, pidx, mbody, s->csr[level].list, pcount, pq, pm, prev);
+        ++s->launches;
+    }
     if (Ode::COLL) {
         bsm_coll_init_kernel<<<gm, 128, 0, st>>>(A);
         ++s->launches;
@@ -765,16 +899,6 @@ int bsm_run(genga_system *s, int level, double dt, const std::vector<int2> &grou
     s->launches += 3;
     if (cudaGetLastError() != cudaSuccess) return GENGA_ECUDA;
 
-    // one persistent cooperative launch: as many blocks as fit on the GPU (more
-    // warps to hide the partner reads from L2 outweigh the barrier's extra
-    // arrivals), and no more than the (column, member) items need
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bsm_persistent_kernel<Ode>, kPThreads, 0) !=
-            cudaSuccess || per_sm < 1)
-        return GENGA_ECUDA;
-    const long long want = (8LL * M * kLanes + kPThreads - 1) / kPThreads;
-    const long long cap = (long long)per_sm * s->num_sms;
-    const unsigned grid = (unsigned)std::max(1LL, std::min(want, cap));
     void *args[] = {&A};
     if (cudaLaunchCooperativeKernel((const void *)bsm_persistent_kernel<Ode>, dim3(grid), dim3(kPThreads), args,
                                     0, st) != cudaSuccess)
@@ -851,6 +975,12 @@ int run_bs(genga_system *s, int level, double dt_l, int64_t np) {
     if (!counts[kBuckets - 1]) return GENGA_OK;
     if ((rc = phase_mark(s, GENGA_PH_BS_LARGE)) != GENGA_OK) return rc;
     return bsm_forward_groups(s, level, dt_l);
+}
+
+extern "C" int genga_set_bs_pair_mode(genga_system_t *s, int32_t mode) {
+    if (!s || mode < GENGA_BS_PAIRS_AUTO || mode > GENGA_BS_PAIRS_ON) return GENGA_EINVAL;
+    s->bs_pairs = mode;
+    return GENGA_OK;
 }
 
 int run_bs_dev(genga_system *s, int level, double dt_l) {

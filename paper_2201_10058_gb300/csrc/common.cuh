@@ -200,6 +200,7 @@ struct genga_system {
     unsigned long long bs_group_limit_ns = 10000000000ull;   // in-block BS, per group call
     unsigned long long barrier_limit_ns = 2000000000ull;     // persistent BS, per grid-barrier wait
     unsigned barrier_absent = 0;   // test hook: blocks every grid barrier waits for in vain
+    int bs_pairs = 0;              // GENGA_BS_PAIRS_*: derivative form of the persistent BS kernel
     int64_t launches = 0;          // kernels launched by this system (host-side count)
     int64_t host_syncs = 0;        // host waits on the stream inside steps
     // phase timing (genga_set_timing): an event on the stream at each phase

@@ -22,6 +22,9 @@ GENGA_GR_SPLIT = 2
 GENGA_KICK_AUTO = 0
 GENGA_KICK_TILED = 1
 GENGA_KICK_SYMMETRIC = 2
+GENGA_BS_PAIRS_AUTO = 0
+GENGA_BS_PAIRS_OFF = 1
+GENGA_BS_PAIRS_ON = 2
 
 ERRORS = {0: "OK", -1: "EINVAL", -2: "ECAPACITY", -3: "ENONCONV", -4: "ETIMEOUT",
           -5: "EBADSTATE", -6: "ECUDA", -7: "ENOMEM"}
@@ -40,6 +43,7 @@ EXPORTED = ["genga_default_params", "genga_create", "genga_destroy", "genga_last
             "genga_init_ensemble", "genga_step_ensemble", "genga_set_pair_log",
             "genga_get_pair_log", "genga_set_wait_limits", "genga_set_collisions",
             "genga_get_mergers", "genga_get_alive", "genga_remove_merged", "genga_set_kick_layout",
+            "genga_set_bs_pair_mode",
             "genga_get_kick_layout", "genga_measure_fp64_latency"]
 
 NPHASES = 18
@@ -169,6 +173,7 @@ def load(build_if_missing: bool = True):
         L.genga_remove_merged.argtypes = [sysp, _P(C.c_int64), _VP]
         L.genga_set_pair_log.argtypes = [sysp, C.c_int]
         L.genga_set_kick_layout.argtypes = [sysp, C.c_int32, C.c_int32]
+        L.genga_set_bs_pair_mode.argtypes = [sysp, C.c_int32]
         L.genga_get_kick_layout.argtypes = [sysp] + [_P(C.c_int32)] * 4
         L.genga_get_pair_log.argtypes = [sysp, _VP, _VP, _VP, C.c_int64, C.c_int64, _P(C.c_int64),
                                          _P(C.c_int64)]
@@ -426,6 +431,12 @@ class System:
         GENGA_KICK_TILED or GENGA_KICK_SYMMETRIC (each unordered pair once),
         with the super-range P (0: chosen for N)."""
         self._check(self._lib.genga_set_kick_layout(self._h, int(layout), int(P)))
+
+    def set_bs_pair_mode(self, mode: int = GENGA_BS_PAIRS_AUTO):
+        """Derivative form of the batched Bulirsch-Stoer kernel (groups of more
+        than 32 members): GENGA_BS_PAIRS_AUTO, _OFF (member form) or _ON (each
+        pair once per column); the results are bit-identical in every mode."""
+        self._check(self._lib.genga_set_bs_pair_mode(self._h, int(mode)))
 
     def kick_layout(self) -> dict:
         """The layout the next kick uses: layout, P, partial slots per body, blocks."""

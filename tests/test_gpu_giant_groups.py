@@ -207,3 +207,51 @@ def test_giant_group_adjoint_dot_product_identity(cuda_lib, giant_case):
     rhs = (gx * dx0).sum() + (gv * dv0).sum() + (gm * dm0).sum()
     scale = abs((gx * dx0).sum()) + abs((gv * dv0).sum()) + abs((gm * dm0).sum())
     assert abs(lhs - rhs) <= 1e-9 * scale, (lhs, rhs)
+
+
+@pytest.mark.parametrize("n,dt", [(300, 60.0), (1000, 40.0), (6000, 5.0)])
+def test_pair_form_is_bit_identical(cuda_lib, n, dt):
+    """The batched kernel's pair-centric derivative (each partner pair once per
+    extrapolation column, its two terms written to the two partner-list
+    entries and summed per member in the member form's lanes and order) gives
+    the member form's results bit for bit: the same positions, velocities and
+    step-control counts.  At 6,000 members the automatic choice takes the pair
+    form (the sub-step phases take several passes over their items)."""
+    torch = _torch()
+    g = cuda_lib
+    wl = _ring(n, dt)
+    rc = O.rcrit(wl.x, wl.v, wl.m, wl.m_star, wl.dt, wl.n1, wl.n2)
+    v1 = O.kick(wl.x, wl.v, wl.m, rc, G, 0.5 * wl.dt, nthreads=8)
+    x1 = O.hc(wl.x, v1, wl.m, wl.m_star, 0.5 * wl.dt)
+    x2, v2, _ = O.drift(x1, v1, G * wl.m_star, wl.dt)
+    out = []
+    for mode in (g.GENGA_BS_PAIRS_OFF, g.GENGA_BS_PAIRS_ON, g.GENGA_BS_PAIRS_AUTO):
+        s, pos, vel, mass = _system(g, wl, bs_max_steps=5000)
+        s.set_bs_pair_mode(mode)
+        s.set_rcrit(rc)
+        s.kick(0.0, precheck=True, acc_out=torch.zeros((3, n), dtype=torch.float64, device="cuda:0"))
+        s.set_predrift(x1.T, v1.T)
+        pos.copy_(torch.tensor(x2.T.copy()))
+        vel.copy_(torch.tensor(v2.T.copy()))
+        npairs, ngroups, maxg = s.build_encounters()
+        assert ngroups == 1 and maxg == n > 32
+        s.bs(wl.dt)
+        st = s.stats()
+        out.append((_host(pos), _host(vel), st["bs_steps"], st["bs_rejects"]))
+        s.close()
+    for x, v, acc, rej in out[1:]:
+        np.testing.assert_array_equal(x, out[0][0])
+        np.testing.assert_array_equal(v, out[0][1])
+        assert (acc, rej) == out[0][2:]
+    assert out[0][3] > 0
+
+
+def test_pair_mode_rejects_bad_values(cuda_lib):
+    g = cuda_lib
+    wl = _ring(64, 10.0)
+    s, *_ = _system(g, wl)
+    with pytest.raises(g.GengaError):
+        s.set_bs_pair_mode(3)
+    with pytest.raises(g.GengaError):
+        s.set_bs_pair_mode(-1)
+    s.close()
