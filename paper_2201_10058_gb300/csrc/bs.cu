@@ -2,9 +2,10 @@
 // Appendix A "Bulirsch-Stoer(dt)") and the level kick KickS of the
 // higher-level changeover scheme (Sec. 6.3, Appendix A).
 //
-// BS for groups of at most kBlockGroupMax (32) members: one CTA per group with
-// the 8 extrapolation columns advanced at once (bs_cols_kernel below; larger
-// groups go to the batched grid-wide driver in bsm.cu).  Each member
+// BS for groups of at most kBlockGroupMax (32) members: one CTA per group at a
+// time (the CTAs claim their bucket's groups) with the 8 extrapolation columns
+// advanced at once (bs_cols_kernel below; larger groups go to the batched
+// grid-wide driver in bsm.cu).  Each member
 // integrates
 //     dx/dt = v,   dv/dt = -mu x/|x|^3 + G sum_{partners j} m_j W_ij (x_j - x)/r^3,
 //     W_ij = prod_{k=0..level} (1 - K(r_ij; rc_k,ij)),
